@@ -1,0 +1,186 @@
+/*
+ * gmmnlse.h -- C ABI of the B300 (sm_103a) solver for the generalized
+ * multimode nonlinear Schroedinger equation (GMMNLSE) by the massively
+ * parallel algorithm (MPA).
+ *
+ * Method: Wright et al., "Multimode Nonlinear Fiber Optics: Massively
+ * Parallel Numerical Solver, Tutorial and Outlook", arXiv:1708.05324.
+ *   - the equation solved is Eq. 1 (Sec. III) with S^K, S^R of Eq. 2;
+ *   - the solver is the MPA of Sec. III.D: the interaction-picture change of
+ *     variables (Eq. cov), the integral form (Eq. MPA_eq), a long step
+ *     L = M dz split into M substeps solved together by fixed-point iteration
+ *     with the trapezoid rule over z'.
+ *
+ * Conventions (all arrays row-major, FP64, owned by the caller; the library
+ * copies what it keeps):
+ *   - Fields vary as exp(-i w t).  The spectrum is
+ *     A~(w_q) = sum_k A(t_k) exp(+i w_q t_k), w_q = 2 pi q / T in FFT order
+ *     (q < Nt/2, else q - Nt), T = Nt dt.  D_w = i beta_p(w).
+ *   - Time samples t_k = (k - Nt/2) dt for A0/Aout; h_R at t_k = k dt.
+ *   - Complex arrays are interleaved (re, im) doubles: [N][Nt][2].
+ *
+ * Every call returns an int status: GMMNLSE_OK (0), GMMNLSE_PENDING (1, poll
+ * only) or a negative GMMNLSE_E_* code.  No call aborts the process; CUDA
+ * failures are reported as GMMNLSE_E_CUDA.  All calls are thread-safe except
+ * that one context must not run two gmmnlse_propagate calls at once (use the
+ * server for concurrency).
+ */
+#ifndef GMMNLSE_H
+#define GMMNLSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMMNLSE_OK                0
+#define GMMNLSE_PENDING           1
+#define GMMNLSE_E_INVALID        -1  /* bad argument (shape, NaN input, null) */
+#define GMMNLSE_E_NOMEM          -2  /* device allocation failed / over budget */
+#define GMMNLSE_E_UNSUPPORTED    -3  /* valid input outside what is built */
+#define GMMNLSE_E_NOT_CONVERGED  -4  /* max_iter reached above tol */
+#define GMMNLSE_E_NONFINITE      -5  /* NaN/Inf appeared in the field */
+#define GMMNLSE_E_CUDA           -6  /* a CUDA call failed */
+#define GMMNLSE_E_BUSY           -7  /* server queue full */
+#define GMMNLSE_E_CANCELLED      -8  /* request cancelled at server shutdown */
+
+/* Arithmetic of the MPA iteration.  The running field between long steps,
+ * the dispersion phase beta*z (reduced mod 2 pi), the convergence norm and
+ * the energy / photon-number sums are FP64 in every mode. */
+typedef enum gmmnlse_precision {
+    GMMNLSE_FP64 = 0,       /* everything FP64 */
+    GMMNLSE_FP32 = 1,       /* FFTs, contraction and iterates FP32 */
+    GMMNLSE_MIXED_BF16 = 2, /* FP32, coupling contraction on tensor cores in
+                               BF16 with hi/lo split operands, FP32 accumulate */
+    GMMNLSE_MIXED_FP16 = 3  /* as MIXED_BF16 with FP16 operands */
+} gmmnlse_precision;
+
+typedef struct gmmnlse_params {
+    int N;               /* number of modes, 1 <= N <= 64 */
+    int Nt;              /* time samples: power of two, 16 <= Nt <= 16384
+                            (FP64: Nt <= 8192) */
+    double dt;           /* sample spacing [s] */
+    double lambda0;      /* centre wavelength [m] (omega0 = 2 pi c / lambda0) */
+    double n2;           /* nonlinear index [m^2/W] */
+    int self_steepening; /* 1: factor (1 + w/w0) of Eq. MPA_eq; 0: factor 1 */
+    int precision;       /* gmmnlse_precision */
+    int max_iter;        /* cap on updates per long step (0 -> 50) */
+    int fixed_iters;     /* > 0: exactly this many updates per long step,
+                            tol ignored (for bit-comparable runs) */
+    int device;          /* CUDA device ordinal */
+    void* stream;        /* cudaStream_t for gmmnlse_propagate; NULL -> a
+                            stream owned by the context */
+    int io_device;       /* 1: A0/Aout of gmmnlse_propagate are device
+                            pointers (FP64 complex, same layout) */
+} gmmnlse_params;
+
+typedef struct gmmnlse_stats {
+    double z;             /* fiber position reached [m] */
+    int long_steps;       /* long steps completed */
+    int iters_total;      /* MPA updates over all long steps */
+    int iters_min;        /* fewest updates in one long step */
+    int iters_max;        /* most updates in one long step */
+    int iter_hist[33];    /* [k]: long steps that took k updates (k >= 32 in [32]) */
+    double eps_max;       /* largest final convergence measure of a long step */
+    double eps_last;      /* final convergence measure of the last long step */
+    double energy_in;     /* dt sum_{p,k} |A_p(t_k)|^2 of A0 [J] */
+    double energy_out;    /* the same of Aout [J] */
+    double photons_in;    /* sum_{p,q: w0+w_q>0} |A~_p(w_q)|^2 / (w0 + w_q) of A0 */
+    double photons_out;   /* the same of Aout */
+    double ms;            /* device time of the propagation [ms] */
+} gmmnlse_stats;
+
+typedef struct gmmnlse_ctx gmmnlse_ctx;
+typedef struct gmmnlse_server gmmnlse_server;
+
+/*
+ * gmmnlse_create -- upload a fiber (Eq. 1 coefficients) to the device.
+ *
+ *   prm   problem size, physical constants, precision, device, stream.
+ *   beta  [N][Nt] rad/m in FFT order, already in the frame of mode 1: the
+ *         Taylor-series dispersion of Eq. 1, beta_p(w) = db0_p + db1_p w +
+ *         sum_{n>=2} beta_n^(p) w^n / n!, so that D_w = i beta_p(w)
+ *         (Sec. III.D).  Host pointer.
+ *   SK    [N][N][N][N] Kerr coupling S^K_plmn [1/m^2] (Eq. 2).  Host.
+ *   SR    [N][N][N][N] Raman coupling S^R_plmn, or NULL (then S^R = S^K).
+ *   fR    Raman fraction f_R of Eq. 1 (0 <= fR < 1).
+ *   hR    [Nt] Raman response h_R(t_k), t_k = k dt [1/s], normalised by the
+ *         caller; NULL allowed when fR == 0.  Host.
+ *   out   receives the context.
+ *
+ * S^K and S^R must be real and symmetric under p<->l and m<->n, as Eq. 2
+ * makes them; otherwise GMMNLSE_E_UNSUPPORTED.  Non-finite inputs or a
+ * non-power-of-two Nt give GMMNLSE_E_INVALID.  The context owns its device
+ * memory until gmmnlse_destroy; it is read-only after creation and may be
+ * shared by concurrent server requests.
+ */
+int gmmnlse_create(const gmmnlse_params* prm, const double* beta, const double* SK,
+                   const double* SR, double fR, const double* hR, gmmnlse_ctx** out);
+
+/* Free a context and all its device memory.  NULL is accepted. */
+int gmmnlse_destroy(gmmnlse_ctx* ctx);
+
+/*
+ * gmmnlse_propagate -- propagate A0 over a fiber of length L (Sec. III.D).
+ *
+ *   A0    [N][Nt] complex launched field A_p(0, t_k) [sqrt(W)]; host pointer
+ *         unless prm.io_device.
+ *   L     fiber length [m]; must be a whole number of dz (to 1e-9 relative).
+ *   dz    substep Delta z [m].
+ *   M     substeps per long step (L_long = M dz); the last long step is
+ *         shorter when M does not divide L/dz.  1 <= M <= 64.
+ *   tol   convergence threshold on eps = ||psi^(n+1) - psi^(n)||_2 /
+ *         ||psi^(n+1)||_2 over all substeps, modes and frequencies.
+ *   Aout  [N][Nt] complex output A_p(L, t_k); may alias A0.
+ *   st    optional statistics (NULL allowed).
+ *
+ * Synchronous: returns after Aout is written.  On GMMNLSE_E_NOT_CONVERGED
+ * or GMMNLSE_E_NONFINITE, Aout holds the field at the end of the last
+ * completed long step and st->z says where that is.
+ */
+int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, int M,
+                      double tol, double* Aout, gmmnlse_stats* st);
+
+/* Static, human-readable text for a status code. */
+const char* gmmnlse_strerror(int status);
+
+/* Device bytes one in-flight propagation of this context with M substeps
+ * keeps resident (its workspace). */
+size_t gmmnlse_request_bytes(const gmmnlse_ctx* ctx, int M);
+
+/*
+ * Serving: continuous batching of propagation requests.
+ *
+ * gmmnlse_server_create(hbm_budget, max_inflight, out): a server whose
+ * in-flight requests together hold at most hbm_budget device bytes (as
+ * gmmnlse_request_bytes counts them) and at most max_inflight requests.
+ * Requests beyond that wait in a FIFO queue and are admitted as earlier ones
+ * finish; each admitted request runs on its own stream, so requests that
+ * arrive while others are on the GPU overlap with them.
+ *
+ * gmmnlse_submit copies A0 (host) and returns at once with a ticket.  The
+ * context must outlive the request.  GMMNLSE_E_BUSY if 65536 requests are
+ * queued; GMMNLSE_E_NOMEM if one request alone exceeds the budget.
+ *
+ * gmmnlse_poll(server, ticket, Aout, st): GMMNLSE_PENDING while the request
+ * runs; otherwise its final status, with Aout (host, [N][Nt] complex) and st
+ * (NULL allowed) filled as gmmnlse_propagate would.  A finished ticket is
+ * released by the poll that reports it; polling it again is
+ * GMMNLSE_E_INVALID.
+ *
+ * gmmnlse_server_destroy waits for admitted requests, cancels queued ones
+ * and frees the server.
+ */
+int gmmnlse_server_create(size_t hbm_budget, int max_inflight, gmmnlse_server** out);
+int gmmnlse_submit(gmmnlse_server* srv, gmmnlse_ctx* ctx, const double* A0, double L,
+                   double dz, int M, double tol, uint64_t* ticket);
+int gmmnlse_poll(gmmnlse_server* srv, uint64_t ticket, double* Aout, gmmnlse_stats* st);
+int gmmnlse_server_destroy(gmmnlse_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMMNLSE_H */

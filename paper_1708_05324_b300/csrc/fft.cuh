@@ -1,0 +1,219 @@
+// One-block, shared-memory Stockham auto-sort FFT of length n = 2^k
+// (16 <= n <= 16384): one leading radix-2/4/8 pass when log2 n is not a
+// multiple of 4, then radix-16 passes.
+//
+// Formulation: the radix-R Stockham iteration of Govindaraju et al.
+// ("High performance discrete Fourier transforms on graphics processors",
+// SC 2008).  A pass with sub-transform size Ns reads x[j + r n/R], applies
+// the twiddles exp(DIR 2 pi i r (j mod Ns) / (Ns R)), does an R-point DFT in
+// registers and writes y[(j/Ns) Ns R + (j mod Ns) + r Ns].
+//
+// DIR = +1 computes X_q = sum_k x_k exp(+2 pi i q k / n), DIR = -1 the
+// conjugate kernel; neither is scaled.  The first pass reads through a caller
+// functor (fusing whatever produces the input), the last pass writes through
+// another (fusing whatever consumes the output); both see natural indices and
+// their global accesses are coalesced.  Each thread holds EPT elements; the
+// block must have exactly n / EPT threads.
+//
+// Shared memory: n + n/16 elements (one padding slot per 16 removes the
+// stride-16 bank pattern of the Ns = 1 pass).  The functors may read or
+// write that same shared buffer (by pad16 of the natural index): every pass
+// separates its reads from its writes with a barrier.
+#pragma once
+
+#include "common.cuh"
+
+namespace gm {
+
+__host__ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int fft_smem_elems(int n) { return n + (n >> 4); }
+
+template <typename R, int DIR, int RAD> struct Dft;
+
+template <typename R, int DIR> struct Dft<R, DIR, 2> {
+  __device__ __forceinline__ static void run(cplx<R>* v) {
+    cplx<R> a = v[0], b = v[1];
+    v[0] = cadd<R>(a, b);
+    v[1] = csub<R>(a, b);
+  }
+};
+
+template <typename R, int DIR> struct Dft<R, DIR, 4> {
+  __device__ __forceinline__ static void run(cplx<R>* v) {
+    cplx<R> s02 = cadd<R>(v[0], v[2]), d02 = csub<R>(v[0], v[2]);
+    cplx<R> s13 = cadd<R>(v[1], v[3]), d13 = mul_i<R, DIR>(csub<R>(v[1], v[3]));
+    v[0] = cadd<R>(s02, s13);
+    v[2] = csub<R>(s02, s13);
+    v[1] = cadd<R>(d02, d13);
+    v[3] = csub<R>(d02, d13);
+  }
+};
+
+// a * exp(DIR 2 pi i m / 8), m = 0..3
+template <typename R, int DIR, int m> __device__ __forceinline__ cplx<R> w8(cplx<R> a) {
+  const R h = (R)0.70710678118654752440;
+  if (m == 0) return a;
+  if (m == 2) return mul_i<R, DIR>(a);
+  if (m == 1)  // (1 + DIR i) / sqrt 2
+    return DIR > 0 ? mk<R>((a.x - a.y) * h, (a.x + a.y) * h) : mk<R>((a.x + a.y) * h, (a.y - a.x) * h);
+  // m == 3: (-1 + DIR i) / sqrt 2
+  return DIR > 0 ? mk<R>((-a.x - a.y) * h, (a.x - a.y) * h) : mk<R>((a.y - a.x) * h, (-a.x - a.y) * h);
+}
+
+template <typename R, int DIR> struct Dft<R, DIR, 8> {
+  // 8 = 2 x 4: X[k1 + 2 k2] = sum_n2 W4^{n2 k2} W8^{n2 k1} sum_n1 x[4 n1 + n2] W2^{n1 k1}
+  __device__ __forceinline__ static void run(cplx<R>* v) {
+    cplx<R> y0[4], y1[4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y0[n2] = cadd<R>(v[n2], v[n2 + 4]);
+      y1[n2] = csub<R>(v[n2], v[n2 + 4]);
+    }
+    y1[1] = w8<R, DIR, 1>(y1[1]);
+    y1[2] = w8<R, DIR, 2>(y1[2]);
+    y1[3] = w8<R, DIR, 3>(y1[3]);
+    Dft<R, DIR, 4>::run(y0);
+    Dft<R, DIR, 4>::run(y1);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      v[2 * k2] = y0[k2];
+      v[2 * k2 + 1] = y1[k2];
+    }
+  }
+};
+
+// exp(DIR 2 pi i m / 16), m = 0..15, from the first-octant values
+template <typename R, int DIR> __device__ __forceinline__ cplx<R> w16(int m) {
+  const R c0 = (R)1.0, c1 = (R)0.92387953251128675613, c2 = (R)0.70710678118654752440,
+          c3 = (R)0.38268343236508977173;
+  R cs, sn;
+  switch (m & 3) {
+    case 0: cs = c0; sn = (R)0; break;
+    case 1: cs = c1; sn = c3; break;
+    case 2: cs = c2; sn = c2; break;
+    default: cs = c3; sn = c1; break;
+  }
+  R x, y;
+  switch ((m >> 2) & 3) {
+    case 0: x = cs; y = sn; break;
+    case 1: x = -sn; y = cs; break;
+    case 2: x = -cs; y = -sn; break;
+    default: x = sn; y = -cs; break;
+  }
+  return mk<R>(x, DIR > 0 ? y : -y);
+}
+
+template <typename R, int DIR> struct Dft<R, DIR, 16> {
+  // 16 = 4 x 4: X[k1 + 4 k2] = sum_n2 W4^{n2 k2} [W16^{n2 k1} sum_n1 x[4 n1 + n2] W4^{n1 k1}]
+  __device__ __forceinline__ static void run(cplx<R>* v) {
+    cplx<R> y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+      Dft<R, DIR, 4>::run(y[n2]);
+    }
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) {
+        const int m = n2 * k1;
+        if (m == 4) y[n2][k1] = mul_i<R, DIR>(y[n2][k1]);
+        else if (m == 2) y[n2][k1] = w8<R, DIR, 1>(y[n2][k1]);
+        else if (m == 6) y[n2][k1] = w8<R, DIR, 3>(y[n2][k1]);
+        else y[n2][k1] = cmul<R>(y[n2][k1], w16<R, DIR>(m));
+      }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      cplx<R> t[4];
+#pragma unroll
+      for (int n2 = 0; n2 < 4; ++n2) t[n2] = y[n2][k1];
+      Dft<R, DIR, 4>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+  }
+};
+
+// One radix-RAD pass.  tw[m] = exp(-2 pi i m / n), m < n.
+template <typename R, int DIR, int RAD, int EPT, bool FIRST, bool LAST, class Load, class Store>
+__device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<R>* __restrict__ tw,
+                                         const Load& load, const Store& store) {
+  constexpr int B = EPT / RAD;  // butterflies per thread
+  const int T = blockDim.x;
+  const int stride = n / RAD;
+  cplx<R> v[B][RAD];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = threadIdx.x + b * T;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      const int idx = j + r * stride;
+      v[b][r] = FIRST ? load(idx) : sm[pad16(idx)];
+    }
+  }
+  __syncthreads();  // every read of this pass precedes every write
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = threadIdx.x + b * T;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const int step = n / (Ns * RAD);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        cplx<R> w = tw[(r * k) * step];
+        if (DIR > 0) w.y = -w.y;
+        v[b][r] = cmul<R>(v[b][r], w);
+      }
+    }
+    Dft<R, DIR, RAD>::run(v[b]);
+    const int base = (j - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      const int idx = base + r * Ns;
+      if (LAST) store(idx, v[b][r]);
+      else sm[pad16(idx)] = v[b][r];
+    }
+  }
+  if (!LAST) __syncthreads();
+}
+
+// Full transform: load(i) gives input element i (natural order), store(i, x)
+// takes output element i.  Starts with a barrier, so the buffer may have been
+// used just before by the same block.
+template <typename R, int DIR, int EPT, class Load, class Store>
+__device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __restrict__ tw,
+                                          const Load& load, const Store& store) {
+  __syncthreads();
+  const int logn = 31 - __clz(n);
+  const int lead = logn & 3;
+  const int passes = (logn >> 2) + (lead ? 1 : 0);
+  auto no_load = [](int) { return mk<R>(0, 0); };
+  auto no_store = [](int, cplx<R>) {};
+  int Ns = 1, p = 0;
+  if (lead) {
+    const bool last = (passes == 1);
+    if (lead == 1) {
+      if (last) fft_pass<R, DIR, 2, EPT, true, true>(sm, n, Ns, tw, load, store);
+      else fft_pass<R, DIR, 2, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+    } else if (lead == 2) {
+      if (last) fft_pass<R, DIR, 4, EPT, true, true>(sm, n, Ns, tw, load, store);
+      else fft_pass<R, DIR, 4, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+    } else {
+      if (last) fft_pass<R, DIR, 8, EPT, true, true>(sm, n, Ns, tw, load, store);
+      else fft_pass<R, DIR, 8, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+    }
+    Ns <<= lead;
+    ++p;
+  }
+  for (; p < passes; ++p) {
+    const bool first = (p == 0), last = (p == passes - 1);
+    if (first && last) fft_pass<R, DIR, 16, EPT, true, true>(sm, n, Ns, tw, load, store);
+    else if (first) fft_pass<R, DIR, 16, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+    else if (last) fft_pass<R, DIR, 16, EPT, false, true>(sm, n, Ns, tw, no_load, store);
+    else fft_pass<R, DIR, 16, EPT, false, false>(sm, n, Ns, tw, no_load, no_store);
+    Ns <<= 4;
+  }
+}
+
+}  // namespace gm
