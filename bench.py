@@ -1,0 +1,309 @@
+"""Benchmark of the MPA hot path: mode * sample * z-steps per second.
+
+Workload (the GMMNLSE Kerr + Raman propagation the metric is quoted on):
+parabolic GRIN fiber (a = 25 um, NA = 0.2, 1030 nm, n2 = 2.3e-20 m^2/W),
+N = 6 Hermite-Gauss modes, Nt = 2^13 over 10 ps, f_R = 0.18 (tau1 = 12.2 fs,
+tau2 = 32 fs), self-steepening on, 200 fs Gaussian pulse of 50 nJ with seeded
+random complex mode weights, L = 0.5 m, dz = 25 um, M = 10, tol = 1e-8.
+One bench step = one full propagation over the 0.5 m fiber (20000 substeps,
+2000 long steps) through the C ABI.  Synthetic inputs (no dataset).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+    python bench.py --impl reference     # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1708_05324_b300 import inputs as I  # noqa: E402
+
+METRIC = "mode*sample*z-steps/s"
+WORKLOAD = ("GRIN a=25um NA=0.2 1030nm, N=6 HG modes, Nt=2^13 over 10 ps, Kerr+Raman fR=0.18, "
+            "self-steepening, 200 fs Gaussian 50 nJ seeded weights, L=0.5 m, dz=25 um, M=10, tol=1e-8")
+
+
+def problem(seed=2, L=0.5):
+    return I.workload("C2", L=L, seed=seed)
+
+
+def units(prob, L=None):
+    return prob.N * prob.Nt * int(round((L or prob.L) / prob.dz))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def launches_per_step(st, raman, graph=True):
+    """Kernel launches of one propagate call, from its statistics."""
+    per_iter = 5 if raman else 4
+    fft = 1  # Nt <= 8192
+    n = 1 + fft + 1          # non-finite check, forward transform, input sums
+    n += 1 + fft             # output sums, inverse transform
+    n += st["iters_total"] * per_iter + st["long_steps"] * (2 if graph else 1)
+    return n
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on a bounded sample of the workload."""
+    import oracle as O
+    prob = problem()
+    fib = O.Fiber.from_problem(prob)
+    sample_L = 2 * prob.M * prob.dz  # two long steps per bench step
+    for _ in range(max(args.warmup, 0)):
+        O.mpa_propagate(fib, prob.A0, sample_L, prob.dz, prob.M, prob.tol)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.mpa_propagate(fib, prob.A0, sample_L, prob.dz, prob.M, prob.tol)
+        times.append(time.perf_counter() - t0)
+    u = units(prob, sample_L)
+    value = u * len(times) / sum(times)
+    cores = _blas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64-cpu-oracle"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": "first 2 long steps (20 substeps, 0.5 mm) of the 0.5 m run per step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([d.get("num_threads", 1) for d in info] or [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(seconds=15.0):
+    """Oracle rate on the host cores for as many long steps as fit in ~seconds."""
+    import oracle as O
+    prob = problem()
+    fib = O.Fiber.from_problem(prob)
+    psi = O.freq_from_time(prob.A0)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        psi, n, trace, status = O.mpa_long_step(fib, psi, prob.dz, prob.M, prob.tol)
+        steps += 1
+    dt = time.perf_counter() - t0
+    rate = prob.N * prob.Nt * prob.M * steps / dt
+    return {"value": rate, "unit": METRIC, "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"first {steps} long steps ({steps * prob.M} substeps) of the 0.5 m run, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--length", type=float, default=0.5, help="fiber length per step [m]")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    from paper_1708_05324_b300 import binding as B
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local
+    torch.cuda.set_device(dev)
+
+    prob = problem(seed=2 + rank, L=args.length)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream,
+                                 io_device=True)
+    a0 = torch.from_numpy(prob.A0).to(f"cuda:{dev}")
+    out = torch.empty_like(a0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    u = units(prob)
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)  # L2 flush (256 MiB write), outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st, rc = ctx.propagate(a0, prob.L, prob.dz, prob.M, prob.tol, out=out, check=False)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != B.OK:
+            raise B.GmmnlseError(rc, "propagate")
+        return e0.elapsed_time(e1), st
+
+    for _ in range(args.warmup):
+        one_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    stats = []
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ms, st = one_step()
+            step_ms.append(ms)
+            stats.append(st)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+    dev_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([dev_s], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = u * args.steps * world / dev_s
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    ctx_h = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream)
+    h_in = np.ascontiguousarray(prob.A0)
+    h_out = np.empty_like(h_in)
+    ctx_h.propagate(h_in, prob.L, prob.dz, prob.M, prob.tol, out=h_out)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        ctx_h.propagate(h_in, prob.L, prob.dz, prob.M, prob.tol, out=h_out)
+        e2e_t.append(time.perf_counter() - t1)
+    ctx_h.close()
+    e2e = {"value": u * args.steps * world / sum(e2e_t), "unit": METRIC,
+           "h2d_bytes_per_step": int(h_in.nbytes), "d2h_bytes_per_step": int(h_out.nbytes)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # error of this path against the FP64 GPU path on a 5 mm prefix (200 long steps)
+    pre = I.workload("C2", L=5e-3)
+    c64 = B.Context.from_problem(pre, precision="fp64", device=dev)
+    ref64, st64, _ = c64.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
+    c64.close()
+    cx = B.Context.from_problem(pre, precision=args.precision, device=dev)
+    mine, _, _ = cx.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
+    cx.close()
+    err = float(np.linalg.norm(mine - ref64) / np.linalg.norm(ref64))
+    fp64_rate = units(pre) / (st64["ms"] / 1e3)
+
+    # roofline of the dominant kernel (CUDA events on the context's stream)
+    prof = ctx.profile(prob.M, reps=20)
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms_dom, bytes_dom = prof[dom]
+    peaks, src = measured_peaks()
+    achieved = bytes_dom / (ms_dom * 1e-3) / 1e9
+    raman = prob.fR != 0
+    launches = sum(launches_per_step(st, raman) for st in stats)
+    ctx.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                   "units_per_step": u, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "long_steps_per_step": stats[-1]["long_steps"],
+                   "iters_per_long_step": stats[-1]["iters_total"] / max(stats[-1]["long_steps"], 1),
+                   "rel_l2_err_vs_fp64_gpu_5mm": err, "fp64_gpu_value": fp64_rate,
+                   "wall_s": wall},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": src, "kernel_ms": ms_dom, "algorithmic_bytes": bytes_dom,
+                     "all_kernels_ms": {k: v[0] for k, v in prof.items()}},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,24 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
 /* Static, human-readable text for a status code. */
 const char* gmmnlse_strerror(int status);
 
+/* Text of the last CUDA failure seen by the calling thread (for
+ * GMMNLSE_E_CUDA); empty if none.  Valid until the thread's next call. */
+const char* gmmnlse_last_error(void);
+
+/*
+ * gmmnlse_profile -- time each kernel of one MPA iteration of this context
+ * (Sec. III.D: phase x inverse FFT; pair products + Raman convolution;
+ * coupling contraction; forward FFT x integrand prefactor; trapezoid +
+ * convergence norm; long-step advance) on the workspace of its last
+ * gmmnlse_propagate, which must have used at least M substeps.  Each kernel
+ * is launched reps times (after one untimed launch) on the context's stream,
+ * bracketed by CUDA events.  ms[6] receives the mean duration of each kernel
+ * [ms]; bytes[6] its algorithmic bytes per launch (each operand read or
+ * written once).  Leaves the workspace iterate in an arbitrary state (the
+ * next gmmnlse_propagate starts afresh).
+ */
+int gmmnlse_profile(gmmnlse_ctx* ctx, int M, int reps, double* ms, double* bytes);
+
 /* Device bytes one in-flight propagation of this context with M substeps
  * keeps resident (its workspace). */
 size_t gmmnlse_request_bytes(const gmmnlse_ctx* ctx, int M);

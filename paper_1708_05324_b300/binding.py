@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libgmmnlse.so (include/gmmnlse.h).
+
+Argument marshalling only: every step of the propagation runs in the CUDA
+library.  Host arrays are numpy complex128 [N][Nt]; device arrays may be
+torch complex128 CUDA tensors (used only for memory and streams).  If the
+library is missing this module raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgmmnlse.so")
+
+OK, PENDING = 0, 1
+E_INVALID, E_NOMEM, E_UNSUPPORTED, E_NOT_CONVERGED = -1, -2, -3, -4
+E_NONFINITE, E_CUDA, E_BUSY, E_CANCELLED = -5, -6, -7, -8
+FP64, FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
+
+# every function include/gmmnlse.h declares
+EXPORTS = [
+    "gmmnlse_create", "gmmnlse_destroy", "gmmnlse_propagate", "gmmnlse_strerror",
+    "gmmnlse_last_error", "gmmnlse_request_bytes", "gmmnlse_server_create",
+    "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
+]
+KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("Nt", C.c_int), ("dt", C.c_double), ("lambda0", C.c_double),
+        ("n2", C.c_double), ("self_steepening", C.c_int), ("precision", C.c_int),
+        ("max_iter", C.c_int), ("fixed_iters", C.c_int), ("device", C.c_int),
+        ("stream", C.c_void_p), ("io_device", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("z", C.c_double), ("long_steps", C.c_int), ("iters_total", C.c_int),
+        ("iters_min", C.c_int), ("iters_max", C.c_int), ("iter_hist", C.c_int * 33),
+        ("eps_max", C.c_double), ("eps_last", C.c_double),
+        ("energy_in", C.c_double), ("energy_out", C.c_double),
+        ("photons_in", C.c_double), ("photons_out", C.c_double), ("ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "iter_hist"}
+        d["iter_hist"] = list(self.iter_hist)
+        return d
+
+
+_lib = None
+
+
+class GmmnlseError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = _lib.gmmnlse_strerror(status).decode() if _lib else str(status)
+        if status == E_CUDA and _lib:
+            msg += ": " + _lib.gmmnlse_last_error().decode()
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with python -m paper_1708_05324_b300.build")
+    lib = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    vp = C.c_void_p
+    lib.gmmnlse_create.argtypes = [C.POINTER(Params), vp, vp, vp, C.c_double, vp, C.POINTER(vp)]
+    lib.gmmnlse_destroy.argtypes = [vp]
+    lib.gmmnlse_propagate.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, vp,
+                                      C.POINTER(Stats)]
+    lib.gmmnlse_strerror.restype = C.c_char_p
+    lib.gmmnlse_strerror.argtypes = [C.c_int]
+    lib.gmmnlse_last_error.restype = C.c_char_p
+    lib.gmmnlse_request_bytes.restype = C.c_size_t
+    lib.gmmnlse_request_bytes.argtypes = [vp, C.c_int]
+    lib.gmmnlse_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
+    lib.gmmnlse_submit.argtypes = [vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                   C.POINTER(C.c_uint64)]
+    lib.gmmnlse_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(Stats)]
+    lib.gmmnlse_server_destroy.argtypes = [vp]
+    lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    del dp
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Data pointer of a C-contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+class Context:
+    """A fiber uploaded to the device (gmmnlse_create)."""
+
+    def __init__(self, N, Nt, dt, lambda0, n2, beta, SK, SR=None, fR=0.0, hR=None,
+                 self_steepening=True, precision="fp64", max_iter=0, fixed_iters=0,
+                 device=0, stream=None, io_device=False):
+        self.lib = load()
+        self.N, self.Nt = int(N), int(Nt)
+        self._keep = []
+        self.beta = np.ascontiguousarray(beta, dtype=np.float64)
+        self.SK = np.ascontiguousarray(SK, dtype=np.float64)
+        self.SR = None if SR is None else np.ascontiguousarray(SR, dtype=np.float64)
+        self.hR = None if hR is None else np.ascontiguousarray(hR, dtype=np.float64)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.params = Params(self.N, self.Nt, float(dt), float(lambda0), float(n2),
+                             1 if self_steepening else 0, prec, int(max_iter), int(fixed_iters),
+                             int(device), stream, 1 if io_device else 0)
+        h = C.c_void_p()
+        st = self.lib.gmmnlse_create(C.byref(self.params), _ptr(self.beta), _ptr(self.SK),
+                                     _ptr(self.SR), float(fR), _ptr(self.hR), C.byref(h))
+        if st != OK:
+            raise GmmnlseError(st, "gmmnlse_create")
+        self.handle = h
+
+    @classmethod
+    def from_problem(cls, prob, precision="fp64", **kw):
+        return cls(prob.N, prob.Nt, prob.dt, prob.lam0, prob.n2, prob.beta, prob.SK,
+                   None if prob.SR is prob.SK else prob.SR, prob.fR,
+                   prob.hR if prob.fR else None, prob.self_steepening, precision, **kw)
+
+    def propagate(self, A0, L, dz, M, tol, out=None, check=True):
+        """Returns (Aout, stats dict, status).  A0/out: numpy complex128 [N][Nt]
+        (or device tensors when the context was made with io_device=True)."""
+        if isinstance(A0, np.ndarray):
+            A0 = np.ascontiguousarray(A0, dtype=np.complex128)
+            if A0.shape != (self.N, self.Nt):
+                raise ValueError(f"A0 must be [{self.N}][{self.Nt}]")
+            if out is None:
+                out = np.empty_like(A0)
+        st = Stats()
+        rc = self.lib.gmmnlse_propagate(self.handle, _ptr(A0), float(L), float(dz), int(M),
+                                        float(tol), _ptr(out), C.byref(st))
+        if check and rc not in (OK,):
+            raise GmmnlseError(rc, "gmmnlse_propagate")
+        return out, st.as_dict(), rc
+
+    def profile(self, M, reps=20):
+        """Mean device time [ms] and algorithmic bytes per launch of each
+        kernel of one iteration, keyed by KERNELS."""
+        ms = np.zeros(6)
+        by = np.zeros(6)
+        st = self.lib.gmmnlse_profile(self.handle, int(M), int(reps), _ptr(ms), _ptr(by))
+        if st != OK:
+            raise GmmnlseError(st, "gmmnlse_profile")
+        return {k: (float(ms[i]), float(by[i])) for i, k in enumerate(KERNELS)}
+
+    def request_bytes(self, M):
+        return int(self.lib.gmmnlse_request_bytes(self.handle, int(M)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gmmnlse_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (gmmnlse_server_*)."""
+
+    def __init__(self, hbm_budget, max_inflight):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.gmmnlse_server_create(int(hbm_budget), int(max_inflight), C.byref(h))
+        if st != OK:
+            raise GmmnlseError(st, "gmmnlse_server_create")
+        self.handle = h
+
+    def submit(self, ctx: Context, A0, L, dz, M, tol):
+        A0 = np.ascontiguousarray(A0, dtype=np.complex128)
+        t = C.c_uint64()
+        st = self.lib.gmmnlse_submit(self.handle, ctx.handle, _ptr(A0), float(L), float(dz),
+                                     int(M), float(tol), C.byref(t))
+        if st != OK:
+            raise GmmnlseError(st, "gmmnlse_submit")
+        return int(t.value)
+
+    def poll(self, ticket, N, Nt):
+        out = np.empty((N, Nt), dtype=np.complex128)
+        st = Stats()
+        rc = self.lib.gmmnlse_poll(self.handle, C.c_uint64(ticket), _ptr(out), C.byref(st))
+        return rc, out, st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gmmnlse_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

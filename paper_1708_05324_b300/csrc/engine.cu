@@ -1,0 +1,883 @@
+// Host side of the MPA solver: contexts (fiber data on the device), per-
+// propagation workspaces, and the long-step driver (Sec. III.D).
+//
+// One long step is the kernel chain K1 -> K2 -> K3 -> K4 -> K5 repeated until
+// K5's last block decides that the iteration has converged, followed by K6.
+// The repetition is a CUDA-graph while-node whose condition K5 sets on the
+// device, and the long steps themselves are an outer while-node that K6
+// re-arms, so a whole fiber is one graph launch with no host round trip per
+// iteration.  A host-driven loop over the same kernels is kept for graphs
+// that fail to build (and for debugging, GMMNLSE_NO_GRAPH=1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/gmmnlse.h"
+#include "engine.h"
+#include "kernels.cuh"
+
+using namespace gm;
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) {                                            \
+      gm_set_last_cuda_error(e_, #call, __FILE__, __LINE__);            \
+      return GMMNLSE_E_CUDA;                                            \
+    }                                                                   \
+  } while (0)
+
+static thread_local char g_last_err[512];
+
+void gm_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_err, sizeof g_last_err, "%s at %s:%d: %s", cudaGetErrorString(e), file, line, what);
+  if (getenv("GMMNLSE_VERBOSE")) fprintf(stderr, "gmmnlse: %s\n", g_last_err);
+}
+
+extern "C" const char* gmmnlse_last_error(void) { return g_last_err; }
+
+namespace {
+
+constexpr int kMaxN = 64;
+constexpr int kMaxM = 64;
+
+int ept_for(int n, bool fp64) {
+  (void)fp64;
+  return n > 8192 ? 32 : 16;
+}
+
+template <typename R> size_t fft_smem(int n) { return (size_t)fft_smem_elems(n) * sizeof(cplx<R>); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Workspace of one propagation in flight
+// ---------------------------------------------------------------------------
+struct gm_job {
+  gmmnlse_ctx* ctx = nullptr;
+  int Mcap = 0;
+  double2* psi0 = nullptr;  // [N][n]
+  void* dpsi = nullptr;     // [M][N][n]
+  void* A = nullptr;        // [M+1][N][n]
+  void* V = nullptr;        // [M+1][KK][n]
+  void* NL = nullptr;       // [M+1][N][n]
+  void* I = nullptr;        // [M+1][N][n]
+  void* E = nullptr;        // [M+1][N][n]
+  double2* EM64 = nullptr;  // [2][N][n]
+  double2* io = nullptr;    // [2][N][n] staging / FP64 FFT scratch
+  int* flag = nullptr;
+  LoopState* ls = nullptr;      // device
+  LoopState* h_ls = nullptr;    // pinned host mirror
+  double2* h_io = nullptr;      // pinned host staging [N][n]
+  cudaStream_t cap = nullptr;   // private stream for graph capture
+  // phase tables currently in E
+  double tab_dz = -1.0;
+  int tab_M = -1, tab_Mrem = -1;
+  // cached graphs: for substep counts M and Mrem
+  struct G {
+    int Mj = -1;
+    int which = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+  } graphs[2];
+  size_t bytes = 0;
+};
+
+struct gmmnlse_ctx {
+  gmmnlse_params prm;
+  int N, n, K, P, KK, raman_mode, ept;
+  bool fp64;
+  double fR, omega0, gamma0;
+  double* beta = nullptr;       // [N][n]
+  double2* tw64 = nullptr;      // [n]
+  double2* tw64h = nullptr;     // [n/2]
+  float2* tw32 = nullptr;       // [n]
+  void* H = nullptr;            // [n] cplx<R>
+  void* G = nullptr;            // [P][KK] R
+  int2* rows = nullptr;         // [P]
+  int2* pairs = nullptr;        // [K]
+  int contract_threads = 128;
+  size_t contract_smem = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  gm_job* job = nullptr;        // workspace of gmmnlse_propagate
+  std::mutex mu;
+};
+
+// ---------------------------------------------------------------------------
+// Helpers
+// ---------------------------------------------------------------------------
+static int set_device(int dev) {
+  CK(cudaSetDevice(dev));
+  return GMMNLSE_OK;
+}
+
+// Forward (DIR +1, unscaled) or inverse (DIR -1, scale) FP64 transform of the
+// N rows of a [N][n] field.  n = 16384 goes through two half-length
+// transforms and a combination step (the full FP64 transform would not fit
+// in one block's shared memory).
+static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* out, int rows, int dir,
+                 double scale, cudaStream_t s) {
+  const int n = c->n;
+  if (n <= 8192) {
+    const int ept = 16;
+    const size_t sm = fft_smem<double>(n);
+    if (dir > 0) k_fft64_rows<+1, 16><<<rows, n / ept, sm, s>>>(in, out, n, scale, c->tw64);
+    else k_fft64_rows<-1, 16><<<rows, n / ept, sm, s>>>(in, out, n, scale, c->tw64);
+  } else {
+    const int h = n / 2;
+    const size_t sm = fft_smem<double>(h);
+    dim3 grid(rows, 2);
+    if (dir > 0) {
+      k_fft64_halves<+1, 16><<<grid, h / 16, sm, s>>>(in, scratch, n, c->tw64h);
+      k_fft64_combine<+1><<<(rows * n + 255) / 256, 256, 0, s>>>(scratch, out, rows, n, scale, c->tw64);
+    } else {
+      k_fft64_halves<-1, 16><<<grid, h / 16, sm, s>>>(in, scratch, n, c->tw64h);
+      k_fft64_combine<-1><<<(rows * n + 255) / 256, 256, 0, s>>>(scratch, out, rows, n, scale, c->tw64);
+    }
+  }
+  CK(cudaGetLastError());
+  return GMMNLSE_OK;
+}
+
+template <typename R> static int set_smem_attrs(gmmnlse_ctx* c) {
+  const int n = c->n;
+  const int sm = (int)fft_smem<R>(n);
+  if (c->ept == 16) {
+    CK(cudaFuncSetAttribute(k_ip_to_time<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_integrand<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  } else {
+    CK(cudaFuncSetAttribute(k_ip_to_time<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CK(cudaFuncSetAttribute(k_integrand<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  }
+  CK(cudaFuncSetAttribute(k_contract<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->contract_smem));
+  const int sm64 = (int)fft_smem<double>(std::min(n, 8192));
+  CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+  CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+  CK(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+  CK(cudaFuncSetAttribute(k_fft64_halves<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+  return GMMNLSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Context creation
+// ---------------------------------------------------------------------------
+static bool finite_all(const double* x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+// S real with S_plmn = S_plnm = S_lpmn (Eq. 2 gives full symmetry).
+static bool symmetric_enough(const double* S, int N) {
+  double mx = 0.0;
+  const size_t tot = (size_t)N * N * N * N;
+  for (size_t i = 0; i < tot; ++i) mx = std::max(mx, std::fabs(S[i]));
+  const double tol = 1e-12 * (mx > 0 ? mx : 1.0);
+  auto at = [&](int p, int l, int m, int n) { return S[(((size_t)p * N + l) * N + m) * N + n]; };
+  for (int p = 0; p < N; ++p)
+    for (int l = 0; l < N; ++l)
+      for (int m = 0; m < N; ++m)
+        for (int n = 0; n < N; ++n) {
+          const double v = at(p, l, m, n);
+          if (std::fabs(v - at(p, l, n, m)) > tol) return false;
+          if (std::fabs(v - at(l, p, m, n)) > tol) return false;
+        }
+  return true;
+}
+
+static void free_job(gm_job* jb);
+
+static void free_ctx(gmmnlse_ctx* c) {
+  if (!c) return;
+  if (c->job) free_job(c->job);
+  cudaFree(c->beta);
+  cudaFree(c->tw64);
+  cudaFree(c->tw64h);
+  cudaFree(c->tw32);
+  cudaFree(c->H);
+  cudaFree(c->G);
+  cudaFree(c->rows);
+  cudaFree(c->pairs);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+template <typename R>
+static int upload_tables(gmmnlse_ctx* c, const std::vector<double>& Gd) {
+  std::vector<R> Gr(Gd.size());
+  for (size_t i = 0; i < Gd.size(); ++i) Gr[i] = (R)Gd[i];
+  CK(cudaMalloc(&c->G, Gr.size() * sizeof(R) + 16));
+  CK(cudaMemcpy(c->G, Gr.data(), Gr.size() * sizeof(R), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&c->H, (size_t)c->n * sizeof(cplx<R>)));
+  return GMMNLSE_OK;
+}
+
+template <typename R>
+static int compute_H(gmmnlse_ctx* c, const double* hR) {
+  const int n = c->n;
+  double2 *hin = nullptr, *hsp = nullptr, *scr = nullptr;
+  std::vector<double2> h(n);
+  for (int i = 0; i < n; ++i) h[i] = make_double2(hR ? hR[i] : 0.0, 0.0);
+  CK(cudaMalloc(&hin, n * sizeof(double2)));
+  CK(cudaMalloc(&hsp, n * sizeof(double2)));
+  CK(cudaMalloc(&scr, n * sizeof(double2)));
+  CK(cudaMemcpy(hin, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+  int rc = fft64(c, scr, hin, hsp, 1, -1, 1.0, 0);
+  if (rc) return rc;
+  k_raman_H<R><<<(n + 255) / 256, 256>>>(hsp, (cplx<R>*)c->H, n, c->prm.dt);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  cudaFree(hin);
+  cudaFree(hsp);
+  cudaFree(scr);
+  return GMMNLSE_OK;
+}
+
+extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, const double* SK,
+                              const double* SR, double fR, const double* hR, gmmnlse_ctx** out) {
+  if (!prm || !beta || !SK || !out) return GMMNLSE_E_INVALID;
+  *out = nullptr;
+  const int N = prm->N, n = prm->Nt;
+  if (N < 1 || N > kMaxN) return GMMNLSE_E_INVALID;
+  if (n < 16 || n > 16384 || (n & (n - 1))) return GMMNLSE_E_INVALID;
+  if (!(prm->dt > 0) || !(prm->lambda0 > 0) || !std::isfinite(prm->n2)) return GMMNLSE_E_INVALID;
+  if (!(fR >= 0.0 && fR < 1.0)) return GMMNLSE_E_INVALID;
+  if (fR > 0 && !hR) return GMMNLSE_E_INVALID;
+  if (prm->precision < GMMNLSE_FP64 || prm->precision > GMMNLSE_MIXED_FP16) return GMMNLSE_E_INVALID;
+  if (prm->max_iter < 0 || prm->fixed_iters < 0) return GMMNLSE_E_INVALID;
+  const size_t S4 = (size_t)N * N * N * N;
+  if (!finite_all(beta, (size_t)N * n) || !finite_all(SK, S4) || (SR && !finite_all(SR, S4)) ||
+      (hR && !finite_all(hR, n)))
+    return GMMNLSE_E_INVALID;
+  if (!symmetric_enough(SK, N) || (SR && !symmetric_enough(SR, N))) return GMMNLSE_E_UNSUPPORTED;
+  const bool fp64 = prm->precision == GMMNLSE_FP64;
+  if (fp64 && n > 8192) return GMMNLSE_E_UNSUPPORTED;
+  if (prm->precision >= GMMNLSE_MIXED_BF16) return GMMNLSE_E_UNSUPPORTED;  // tensor-core path: see engine_tc
+  int rc = set_device(prm->device);
+  if (rc) return rc;
+
+  gmmnlse_ctx* c = new (std::nothrow) gmmnlse_ctx();
+  if (!c) return GMMNLSE_E_NOMEM;
+  c->prm = *prm;
+  c->N = N;
+  c->n = n;
+  c->fp64 = fp64;
+  c->ept = ept_for(n, fp64);
+  c->fR = fR;
+  c->omega0 = 2.0 * M_PI * C_LIGHT / prm->lambda0;
+  c->gamma0 = prm->n2 * c->omega0 / C_LIGHT;
+  c->K = N * (N + 1) / 2;
+  c->P = c->K;
+  bool same = (SR == nullptr) || (SR == SK) || std::memcmp(SR, SK, S4 * sizeof(double)) == 0;
+  c->raman_mode = (fR == 0.0) ? 0 : (same ? 1 : 2);
+  c->KK = (c->raman_mode == 2) ? 2 * c->K : c->K;
+
+  // pair / row enumeration (m <= n), reduced coupling matrix G [P][KK]
+  std::vector<int2> pairs;
+  for (int m = 0; m < N; ++m)
+    for (int q = m; q < N; ++q) pairs.push_back(make_int2(m, q));
+  std::vector<double> Gd((size_t)c->P * c->KK);
+  auto S_at = [&](const double* S, int p, int l, int m, int q) {
+    return S[(((size_t)p * N + l) * N + m) * N + q];
+  };
+  for (int r = 0; r < c->P; ++r) {
+    const int p = pairs[r].x, l = pairs[r].y;
+    for (int k = 0; k < c->K; ++k) {
+      const int m = pairs[k].x, q = pairs[k].y;
+      if (c->raman_mode == 2) {
+        Gd[(size_t)r * c->KK + k] = (1.0 - fR) * S_at(SK, p, l, m, q);
+        Gd[(size_t)r * c->KK + c->K + k] = fR * S_at(SR, p, l, m, q);
+      } else {
+        Gd[(size_t)r * c->KK + k] = S_at(SK, p, l, m, q);
+      }
+    }
+  }
+
+  // contraction kernel shared memory; shrink the block until it fits
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, prm->device);
+  const size_t rsz = fp64 ? 8 : 4;
+  int T = 128;
+  auto need = [&](int t) {
+    return (size_t)c->P * 8 + ((size_t)c->P * c->KK + (size_t)(4 * N + c->KK) * t) * rsz;
+  };
+  while (T > 32 && need(T) > (size_t)maxsm) T /= 2;
+  if (need(T) > (size_t)maxsm) {
+    delete c;
+    return GMMNLSE_E_UNSUPPORTED;
+  }
+  c->contract_threads = T;
+  c->contract_smem = need(T);
+
+  // device copies
+  std::vector<double2> tw(n), twh(n / 2);
+  std::vector<float2> tw32(n);
+  for (int m = 0; m < n; ++m) {
+    const double a = 2.0 * M_PI * (double)m / (double)n;
+    tw[m] = make_double2(std::cos(a), -std::sin(a));
+    tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
+  }
+  for (int m = 0; m < n / 2; ++m) twh[m] = tw[2 * m];
+#define CKC(call)                     \
+  do {                                \
+    cudaError_t e_ = (call);          \
+    if (e_ != cudaSuccess) {          \
+      gm_set_last_cuda_error(e_, #call, __FILE__, __LINE__); \
+      free_ctx(c);                    \
+      return GMMNLSE_E_CUDA;          \
+    }                                 \
+  } while (0)
+  CKC(cudaMalloc(&c->beta, (size_t)N * n * sizeof(double)));
+  CKC(cudaMemcpy(c->beta, beta, (size_t)N * n * sizeof(double), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->tw64, n * sizeof(double2)));
+  CKC(cudaMemcpy(c->tw64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->tw64h, (n / 2) * sizeof(double2)));
+  CKC(cudaMemcpy(c->tw64h, twh.data(), (n / 2) * sizeof(double2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->tw32, n * sizeof(float2)));
+  CKC(cudaMemcpy(c->tw32, tw32.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->rows, c->P * sizeof(int2)));
+  CKC(cudaMemcpy(c->rows, pairs.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->pairs, c->K * sizeof(int2)));
+  CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
+  rc = fp64 ? upload_tables<double>(c, Gd) : upload_tables<float>(c, Gd);
+  if (!rc) rc = fp64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
+  if (!rc) rc = fp64 ? compute_H<double>(c, hR) : compute_H<float>(c, hR);
+  if (rc) {
+    free_ctx(c);
+    return rc;
+  }
+  if (prm->stream) {
+    c->stream = (cudaStream_t)prm->stream;
+  } else {
+    CKC(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+#undef CKC
+  *out = c;
+  return GMMNLSE_OK;
+}
+
+extern "C" int gmmnlse_destroy(gmmnlse_ctx* c) {
+  if (!c) return GMMNLSE_OK;
+  cudaSetDevice(c->prm.device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  return GMMNLSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspaces
+// ---------------------------------------------------------------------------
+static size_t job_bytes(const gmmnlse_ctx* c, int M) {
+  const size_t rs = c->fp64 ? 8 : 4, cs = 2 * rs;
+  const size_t Nn = (size_t)c->N * c->n;
+  size_t b = 0;
+  b += Nn * 16;                                  // psi0
+  b += (size_t)M * Nn * cs;                      // dpsi
+  b += 4 * (size_t)(M + 1) * Nn * cs;            // A, NL, I, E
+  if (c->raman_mode) b += (size_t)(M + 1) * c->KK * c->n * rs;  // V
+  b += 2 * Nn * 16 * 2;                          // EM64, io
+  b += sizeof(LoopState) + 64;
+  return b;
+}
+
+extern "C" size_t gmmnlse_request_bytes(const gmmnlse_ctx* c, int M) { return c ? job_bytes(c, M) : 0; }
+
+static void free_job(gm_job* jb) {
+  if (!jb) return;
+  for (auto& g : jb->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  cudaFree(jb->psi0);
+  cudaFree(jb->dpsi);
+  cudaFree(jb->A);
+  cudaFree(jb->V);
+  cudaFree(jb->NL);
+  cudaFree(jb->I);
+  cudaFree(jb->E);
+  cudaFree(jb->EM64);
+  cudaFree(jb->io);
+  cudaFree(jb->flag);
+  cudaFree(jb->ls);
+  cudaFreeHost(jb->h_ls);
+  cudaFreeHost(jb->h_io);
+  if (jb->cap) cudaStreamDestroy(jb->cap);
+  delete jb;
+}
+
+int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
+  *out = nullptr;
+  gm_job* jb = new (std::nothrow) gm_job();
+  if (!jb) return GMMNLSE_E_NOMEM;
+  jb->ctx = c;
+  jb->Mcap = M;
+  const size_t rs = c->fp64 ? 8 : 4, cs = 2 * rs;
+  const size_t Nn = (size_t)c->N * c->n;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b ? b : 16);
+  };
+  al((void**)&jb->psi0, Nn * 16);
+  al(&jb->dpsi, (size_t)M * Nn * cs);
+  al(&jb->A, (size_t)(M + 1) * Nn * cs);
+  al(&jb->NL, (size_t)(M + 1) * Nn * cs);
+  al(&jb->I, (size_t)(M + 1) * Nn * cs);
+  al(&jb->E, (size_t)(M + 1) * Nn * cs);
+  if (c->raman_mode) al(&jb->V, (size_t)(M + 1) * c->KK * c->n * rs);
+  al((void**)&jb->EM64, 2 * Nn * 16);
+  al((void**)&jb->io, 2 * Nn * 16);
+  al((void**)&jb->flag, sizeof(int));
+  al((void**)&jb->ls, sizeof(LoopState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_ls, sizeof(LoopState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_io, Nn * 16);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&jb->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    gm_set_last_cuda_error(e, "workspace allocation", __FILE__, __LINE__);
+    cudaGetLastError();
+    free_job(jb);
+    return e == cudaErrorMemoryAllocation ? GMMNLSE_E_NOMEM : GMMNLSE_E_CUDA;
+  }
+  jb->bytes = job_bytes(c, M);
+  *out = jb;
+  return GMMNLSE_OK;
+}
+
+void gm_job_destroy(gm_job* jb) { free_job(jb); }
+
+// ---------------------------------------------------------------------------
+// Kernel chain of one iteration and the long-step driver
+// ---------------------------------------------------------------------------
+template <typename R>
+static Geo make_geo(const gmmnlse_ctx* c, int Mj, double dz) {
+  Geo g;
+  g.N = c->N;
+  g.n = c->n;
+  g.K = c->K;
+  g.P = c->P;
+  g.KK = c->KK;
+  g.M = Mj;
+  g.raman_mode = c->raman_mode;
+  g.ss = c->prm.self_steepening ? 1 : 0;
+  g.fR = c->fR;
+  g.gamma0 = c->gamma0;
+  g.omega0 = c->omega0;
+  g.dt = c->prm.dt;
+  g.hdz = 0.5 * dz;
+  return g;
+}
+
+template <typename R> static const cplx<R>* twid(const gmmnlse_ctx* c);
+template <> const cplx<float>* twid<float>(const gmmnlse_ctx* c) { return c->tw32; }
+template <> const cplx<double>* twid<double>(const gmmnlse_ctx* c) { return c->tw64; }
+
+static int elementwise_blocks(size_t count) {
+  const size_t b = (count + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
+}
+
+template <typename R, int EPT>
+static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n, N = c->N, Mj = g.M;
+  const size_t sm = fft_smem<R>(n);
+  const int T = n / EPT;
+  const cplx<R>* tw = twid<R>(c);
+  dim3 gridNM(N, Mj + 1);
+  k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, jb->psi0, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E,
+                                              (cplx<R>*)jb->A, tw, jb->ls);
+  if (c->raman_mode) {
+    dim3 gridK((c->K + 1) / 2, Mj + 1);
+    k_pairs_raman<R, EPT><<<gridK, T, sm, s>>>(g, (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, tw,
+                                               c->pairs, jb->ls);
+  }
+  const int CT = c->contract_threads;
+  const size_t pts = (size_t)(Mj + 1) * n;
+  k_contract<R><<<(unsigned)((pts + CT - 1) / CT), CT, c->contract_smem, s>>>(
+      g, (const cplx<R>*)jb->A, (const R*)jb->V, (const R*)c->G, c->rows, c->pairs, (cplx<R>*)jb->NL, jb->ls);
+  k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E, (cplx<R>*)jb->I,
+                                            tw, jb->ls);
+  k_trapz_norm<R><<<elementwise_blocks((size_t)N * n), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->dpsi,
+                                                                    (const cplx<R>*)jb->I, jb->ls, h, use_cond);
+}
+
+template <typename R>
+static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle h,
+                           int use_cond) {
+  gmmnlse_ctx* c = jb->ctx;
+  const size_t Nn = (size_t)c->N * c->n;
+  k_advance<R><<<elementwise_blocks(Nn), 256, 0, s>>>(g, jb->psi0, (const cplx<R>*)jb->dpsi,
+                                                      jb->EM64 + (size_t)which * Nn, jb->ls, h, use_cond);
+}
+
+template <typename R, int EPT>
+static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
+  cudaStream_t cs = jb->cap;
+  cudaGraph_t root = nullptr;
+  CK(cudaGraphCreate(&root, 0));
+  cudaGraphConditionalHandle hStep, hIter;
+  CK(cudaGraphConditionalHandleCreate(&hStep, root, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hStep;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t nStep;
+  CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
+  cudaGraph_t gS = cp.conditional.phGraph_out[0];
+  CK(cudaGraphConditionalHandleCreate(&hIter, gS, 0, 0));
+  // long-step body: re-arm the iteration loop
+  CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  k_step_begin<<<1, 32, 0, cs>>>(hIter);
+  CK(cudaStreamEndCapture(cs, &gS));
+  cudaGraphNode_t nBegin;
+  size_t cnt = 1;
+  CK(cudaGraphGetNodes(gS, &nBegin, &cnt));
+  cudaGraphNodeParams ci = {};
+  ci.type = cudaGraphNodeTypeConditional;
+  ci.conditional.handle = hIter;
+  ci.conditional.type = cudaGraphCondTypeWhile;
+  ci.conditional.size = 1;
+  cudaGraphNode_t nIter;
+  CK(cudaGraphAddNode(&nIter, gS, &nBegin, nullptr, 1, &ci));
+  cudaGraph_t gI = ci.conditional.phGraph_out[0];
+  // iteration body: K1..K5
+  CK(cudaStreamBeginCaptureToGraph(cs, gI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_iteration<R, EPT>(jb, g, cs, hIter, 1);
+  CK(cudaStreamEndCapture(cs, &gI));
+  // after the loop: K6
+  CK(cudaStreamBeginCaptureToGraph(cs, gS, &nIter, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  launch_advance<R>(jb, g, which, cs, hStep, 1);
+  CK(cudaStreamEndCapture(cs, &gS));
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphInstantiate(&exec, root, 0));
+  out.graph = root;
+  out.exec = exec;
+  out.Mj = g.M;
+  out.which = which;
+  return GMMNLSE_OK;
+}
+
+static bool graphs_disabled() {
+  const char* v = getenv("GMMNLSE_NO_GRAPH");
+  return v && v[0] == '1';
+}
+
+// Run `count` long steps of Mj substeps starting from the current psi0.
+template <typename R, int EPT>
+static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, cudaStream_t s) {
+  if (count <= 0) return GMMNLSE_OK;
+  const Geo g = make_geo<R>(jb->ctx, Mj, dz);
+  // the step target for this launch
+  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (jb->h_ls->status != ST_OK) return GMMNLSE_OK;
+  const int target = jb->h_ls->step + count;
+  CK(cudaMemcpyAsync(&jb->ls->nsteps, &target, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (!graphs_disabled()) {
+    gm_job::G* gr = nullptr;
+    for (auto& x : jb->graphs)
+      if (x.exec && x.Mj == Mj && x.which == which) gr = &x;
+    if (!gr) {
+      gm_job::G& slot = jb->graphs[which];
+      if (slot.exec) {
+        cudaGraphExecDestroy(slot.exec);
+        cudaGraphDestroy(slot.graph);
+        slot = gm_job::G();
+      }
+      if (build_graph<R, EPT>(jb, g, which, slot) == GMMNLSE_OK) gr = &slot;
+      else {
+        cudaGetLastError();
+        if (getenv("GMMNLSE_VERBOSE")) fprintf(stderr, "gmmnlse: graph build failed, host loop\n");
+      }
+    }
+    if (gr) {
+      CK(cudaGraphLaunch(gr->exec, s));
+      return GMMNLSE_OK;
+    }
+  }
+  // host-driven loop over the same kernels
+  for (int st = 0; st < count; ++st) {
+    for (;;) {
+      launch_iteration<R, EPT>(jb, g, s, 0, 0);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (jb->h_ls->done) break;
+    }
+    launch_advance<R>(jb, g, which, s, 0, 0);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (jb->h_ls->status != ST_OK) break;
+  }
+  return GMMNLSE_OK;
+}
+
+// Substep schedule: round(L/dz) substeps of dz, long steps of M, remainder last.
+int gm_schedule(double L, double dz, int M, long* nfull, int* Mrem) {
+  if (!(L > 0) || !(dz > 0) || M < 1 || M > kMaxM || !std::isfinite(L) || !std::isfinite(dz))
+    return GMMNLSE_E_INVALID;
+  const double r = L / dz;
+  if (r > 1e12) return GMMNLSE_E_INVALID;
+  const long total = (long)std::llround(r);
+  if (total < 1 || std::fabs((double)total * dz - L) > 1e-9 * std::max(L, dz)) return GMMNLSE_E_INVALID;
+  *nfull = total / M;
+  *Mrem = (int)(total % M);
+  return GMMNLSE_OK;
+}
+
+template <typename R, int EPT>
+static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                          double* Aout, gmmnlse_stats* st, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  long nfull = 0;
+  int Mrem = 0;
+  int rc = gm_schedule(L, dz, M, &nfull, &Mrem);
+  if (rc) return rc;
+  if (!(tol >= 0) || !std::isfinite(tol)) return GMMNLSE_E_INVALID;
+  const size_t Nn = (size_t)c->N * c->n;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // input: time-domain FP64 field -> io[0]
+  double2* tin = jb->io;
+  if (dev_io) {
+    CK(cudaMemcpyAsync(tin, A0, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::memcpy(jb->h_io, A0, Nn * 16);
+    CK(cudaMemcpyAsync(tin, jb->h_io, Nn * 16, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(jb->flag, 0, sizeof(int), s));
+  k_nonfinite<<<elementwise_blocks(Nn), 256, 0, s>>>(tin, Nn, jb->flag);
+  int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, jb->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hflag) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GMMNLSE_E_INVALID;
+  }
+  // psi0 = F{A0} (FP64)
+  rc = fft64(c, jb->io + Nn, tin, jb->psi0, c->N, +1, 1.0, s);
+  if (rc) return rc;
+  // phase tables for (dz, M, Mrem)
+  if (jb->tab_dz != dz || jb->tab_M != M || jb->tab_Mrem != Mrem) {
+    k_phase_tables<R><<<elementwise_blocks((size_t)(M + 1) * Nn), 256, 0, s>>>(
+        c->beta, (int)Nn, M, dz, Mrem, (cplx<R>*)jb->E, jb->EM64);
+    CK(cudaGetLastError());
+    jb->tab_dz = dz;
+    jb->tab_M = M;
+    jb->tab_Mrem = Mrem;
+  }
+  // loop state
+  LoopState h = {};
+  h.tol = tol;
+  h.floor_eps = c->fp64 ? 1e-14 : (c->prm.precision == GMMNLSE_FP32 ? 1e-6 : 1e-5);
+  h.max_iter = c->prm.max_iter > 0 ? c->prm.max_iter : 50;
+  h.fixed_iters = c->prm.fixed_iters;
+  h.prev_eps = INFINITY;
+  h.iters_min = 1 << 30;
+  h.status = ST_OK;
+  *jb->h_ls = h;
+  CK(cudaMemcpyAsync(jb->ls, jb->h_ls, sizeof(LoopState), cudaMemcpyHostToDevice, s));
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0, jb->ls->spec);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  rc = run_long_steps<R, EPT>(jb, M, 0, dz, (int)nfull, s);
+  if (rc) return rc;
+  if (Mrem > 0) {
+    rc = run_long_steps<R, EPT>(jb, Mrem, 1, dz, 1, s);
+    if (rc) return rc;
+  }
+  // output sums and Aout = F^-1{psi0}
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0,
+                                                     jb->ls->spec + 2);
+  rc = fft64(c, jb->io + Nn, jb->psi0, jb->io, c->N, -1, 1.0 / c->n, s);
+  if (rc) return rc;
+  if (dev_io) {
+    CK(cudaMemcpyAsync(Aout, jb->io, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(jb->h_io, jb->io, Nn * 16, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  if (!dev_io) std::memcpy(Aout, jb->h_io, Nn * 16);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const LoopState& hs = *jb->h_ls;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->long_steps = hs.step;
+    const long done = (hs.step <= nfull) ? (long)hs.step * M : nfull * M + Mrem;
+    st->z = (double)done * dz;
+    st->iters_total = hs.iters_total;
+    st->iters_min = hs.step > 0 ? hs.iters_min : 0;
+    st->iters_max = hs.iters_max;
+    std::memcpy(st->iter_hist, hs.hist, sizeof(st->iter_hist));
+    st->eps_max = hs.eps_max;
+    st->eps_last = hs.eps;
+    st->energy_in = hs.spec[0] * c->prm.dt / c->n;
+    st->photons_in = hs.spec[1];
+    st->energy_out = hs.spec[2] * c->prm.dt / c->n;
+    st->photons_out = hs.spec[3];
+    st->ms = ms;
+  }
+  if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
+  if (hs.status == ST_NONFINITE) return GMMNLSE_E_NONFINITE;
+  return GMMNLSE_OK;
+}
+
+int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                     double* Aout, gmmnlse_stats* st, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  if (M > jb->Mcap) return GMMNLSE_E_INVALID;
+  if (c->fp64) {
+    return c->ept == 16 ? propagate_impl<double, 16>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
+                        : propagate_impl<double, 32>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
+  }
+  return c->ept == 16 ? propagate_impl<float, 16>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
+                      : propagate_impl<float, 32>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
+}
+
+// ---------------------------------------------------------------------------
+// Per-kernel timing of one MPA iteration (used for the roofline report)
+// ---------------------------------------------------------------------------
+template <typename R, int EPT>
+static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes) {
+  cudaStream_t s = c->stream;
+  const double dz = jb->tab_dz > 0 ? jb->tab_dz : 1e-5;
+  const Geo g = make_geo<R>(c, M, dz);
+  const double rs = sizeof(R), cs = 2 * rs;
+  const double Nn = (double)c->N * c->n;
+  // algorithmic bytes per launch of an iteration (substeps j = 1..M)
+  bytes[0] = M * Nn * (16 + 3 * cs);
+  bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->KK * c->n * rs) : 0.0;
+  bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->KK * rs : 0.0));
+  bytes[3] = M * Nn * 3 * cs;
+  bytes[4] = Nn * ((M + 1) * cs + 2 * M * cs + 16);
+  bytes[5] = Nn * (16 + cs + 16 + 16);
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  const int one = 1;
+  const size_t Nsz = (size_t)c->N * c->n;
+  const int n = c->n, T = n / EPT, CT = c->contract_threads;
+  const size_t sm = fft_smem<R>(n);
+  const cplx<R>* tw = twid<R>(c);
+  dim3 gridNM(c->N, M + 1);
+  for (int k = 0; k < 6; ++k) {
+    ms[k] = 0.0;
+    if (k == 1 && !c->raman_mode) continue;
+    for (int r = -1; r < reps; ++r) {
+      // iteration state: iter = 1 (substeps 1..M, the shape of every iteration after the first)
+      CK(cudaMemcpyAsync(&jb->ls->iter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(cudaEventRecord(a, s));
+      switch (k) {
+        case 0:
+          k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, jb->psi0, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E,
+                                                      (cplx<R>*)jb->A, tw, jb->ls);
+          break;
+        case 1:
+          k_pairs_raman<R, EPT><<<dim3((c->K + 1) / 2, M + 1), T, sm, s>>>(
+              g, (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, tw, c->pairs, jb->ls);
+          break;
+        case 2:
+          k_contract<R><<<(unsigned)(((size_t)(M + 1) * n + CT - 1) / CT), CT, c->contract_smem, s>>>(
+              g, (const cplx<R>*)jb->A, (const R*)jb->V, (const R*)c->G, c->rows, c->pairs, (cplx<R>*)jb->NL,
+              jb->ls);
+          break;
+        case 3:
+          k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E,
+                                                    (cplx<R>*)jb->I, tw, jb->ls);
+          break;
+        case 4:
+          k_trapz_norm<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->dpsi,
+                                                                  (const cplx<R>*)jb->I, jb->ls, 0, 0);
+          break;
+        default:
+          k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (const cplx<R>*)jb->dpsi, jb->EM64,
+                                                               jb->ls, 0, 0);
+          break;
+      }
+      CK(cudaGetLastError());
+      CK(cudaEventRecord(b, s));
+      CK(cudaEventSynchronize(b));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, a, b));
+      if (r >= 0) ms[k] += t / reps;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return GMMNLSE_OK;
+}
+
+extern "C" int gmmnlse_profile(gmmnlse_ctx* c, int M, int reps, double* ms, double* bytes) {
+  if (!c || !ms || !bytes || reps < 1 || M < 1 || M > kMaxM) return GMMNLSE_E_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (!c->job || c->job->Mcap < M || c->job->tab_M < M) return GMMNLSE_E_INVALID;
+  if (c->fp64) return c->ept == 16 ? profile_impl<double, 16>(c, c->job, M, reps, ms, bytes)
+                                   : profile_impl<double, 32>(c, c->job, M, reps, ms, bytes);
+  return c->ept == 16 ? profile_impl<float, 16>(c, c->job, M, reps, ms, bytes)
+                      : profile_impl<float, 32>(c, c->job, M, reps, ms, bytes);
+}
+
+int gm_ctx_device(const gmmnlse_ctx* c) { return c->prm.device; }
+int gm_ctx_modes(const gmmnlse_ctx* c) { return c->N; }
+int gm_ctx_samples(const gmmnlse_ctx* c) { return c->n; }
+
+extern "C" int gmmnlse_propagate(gmmnlse_ctx* c, const double* A0, double L, double dz, int M, double tol,
+                                 double* Aout, gmmnlse_stats* st) {
+  if (!c || !A0 || !Aout) return GMMNLSE_E_INVALID;
+  long nf;
+  int mr;
+  int rc = gm_schedule(L, dz, M, &nf, &mr);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (c->job && c->job->Mcap < M) {
+    cudaStreamSynchronize(c->stream);
+    free_job(c->job);
+    c->job = nullptr;
+  }
+  if (!c->job) {
+    rc = gm_job_create(c, M, &c->job);
+    if (rc) return rc;
+  }
+  return gm_job_propagate(c->job, A0, c->prm.io_device != 0, L, dz, M, tol, Aout, st, c->stream);
+}
+
+extern "C" const char* gmmnlse_strerror(int s) {
+  switch (s) {
+    case GMMNLSE_OK: return "ok";
+    case GMMNLSE_PENDING: return "pending";
+    case GMMNLSE_E_INVALID: return "invalid argument";
+    case GMMNLSE_E_NOMEM: return "out of device memory or over the memory budget";
+    case GMMNLSE_E_UNSUPPORTED: return "unsupported configuration";
+    case GMMNLSE_E_NOT_CONVERGED: return "MPA iteration did not converge within max_iter";
+    case GMMNLSE_E_NONFINITE: return "non-finite value in the field";
+    case GMMNLSE_E_CUDA: return "CUDA error";
+    case GMMNLSE_E_BUSY: return "server queue full";
+    case GMMNLSE_E_CANCELLED: return "request cancelled";
+    default: return "unknown status";
+  }
+}

@@ -1,0 +1,18 @@
+// Internal interface between the solver engine and the request server.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/gmmnlse.h"
+
+struct gm_job;
+
+void gm_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out);
+void gm_job_destroy(gm_job* jb);
+int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                     double* Aout, gmmnlse_stats* st, cudaStream_t s);
+int gm_schedule(double L, double dz, int M, long* nfull, int* Mrem);
+int gm_ctx_device(const gmmnlse_ctx* c);
+int gm_ctx_modes(const gmmnlse_ctx* c);
+int gm_ctx_samples(const gmmnlse_ctx* c);

@@ -1,0 +1,461 @@
+// Device kernels of one MPA long step (Sec. III.D), templated on the working
+// real type R (float or double) and on the FFT elements per thread EPT.
+//
+// Data (row-major, all resident on the device for the whole propagation):
+//   psi0 [N][n]      double2  running spectrum A~(z0, w): FP64 between long steps
+//   dpsi [M][N][n]   cplx<R>  psi_j - psi0, j = 1..M (the iterate)
+//   E    [M+1][N][n] cplx<R>  exp(i beta_p(w) j dz), phase reduced in FP64
+//   A    [M+1][N][n] cplx<R>  A_j(t) = F^-1{psi_j E_j}
+//   V    [M+1][KK][n] R       pair products after the Raman convolution
+//   NL   [M+1][N][n] cplx<R>  bracket of Eq. 1 at z_j
+//   I    [M+1][N][n] cplx<R>  integrand of Eq. MPA_eq at z_j
+// Substep j = 0 (z0 itself) is evaluated only in the first iteration of a
+// long step: I_0 does not change while psi_j, j >= 1, is iterated.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace gm {
+
+constexpr double C_LIGHT = 299792458.0;
+
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = -4, ST_NONFINITE = -5 };
+
+// Iteration control shared by the kernels of a propagation (device memory).
+struct LoopState {
+  double diff, nrm;        // sum |psi^(n+1) - psi^(n)|^2, sum |psi^(n+1)|^2 (this iteration)
+  double eps, prev_eps;    // eps of this and the previous iteration
+  double eps_max;          // largest final eps of a completed long step
+  double tol, floor_eps;   // threshold; rounding floor of the working precision
+  unsigned int arrive5;    // blocks of the trapezoid kernel that have finished
+  unsigned int arrive6;    // blocks of the advance kernel that have finished
+  int iter;                // updates made in the current long step
+  int done;                // current long step has stopped iterating
+  int status;              // ST_*
+  int step, nsteps;        // long steps completed / to do (in this launch)
+  int max_iter, fixed_iters;
+  int iters_total, iters_min, iters_max;
+  int hist[33];
+  double spec[4];          // sum |psi0|^2, photon sum (filled by k_spec_sums)
+};
+
+struct Geo {
+  int N, n, K, P, KK, M;  // modes, samples, pairs, unique (p,l) rows, V rows, substeps
+  int raman_mode;         // 0: Kerr only; 1: V = (1-fR) U + fR h*U; 2: V = [U; h*U]
+  int ss;                 // self-steepening
+  double fR, gamma0, omega0, dt, hdz;  // hdz = dz / 2
+};
+
+__device__ __forceinline__ double omega_of(int q, int n, double dt) {
+  const int s = (q < n / 2) ? q : q - n;
+  return 2.0 * 3.14159265358979323846 * (double)s / ((double)n * dt);
+}
+
+// ---------------------------------------------------------------------------
+// K0: phase tables E_j = exp(i beta (j dz)) for j = 0..M (argument formed in
+// FP64 as beta * (j * dz); sincos reduces it mod 2 pi), plus FP64 copies of
+// the long-step propagators exp(i beta M dz) and exp(i beta Mrem dz).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_phase_tables(const double* __restrict__ beta, int Nn, int M, double dz, int Mrem,
+                               cplx<R>* __restrict__ E, double2* __restrict__ EM64) {
+  const size_t total = (size_t)(M + 1) * Nn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i / Nn);
+    const size_t e = i - (size_t)j * Nn;
+    const double zj = (double)j * dz;
+    double s, c;
+    sincos(beta[e] * zj, &s, &c);
+    E[i] = mk<R>((R)c, (R)s);
+    if (j == M) EM64[e] = make_double2(c, s);
+    if (Mrem > 0 && j == Mrem) EM64[Nn + e] = make_double2(c, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N, M+1)
+// ---------------------------------------------------------------------------
+template <typename R, int EPT>
+__global__ void __launch_bounds__(1024) k_ip_to_time(Geo g, const double2* __restrict__ psi0,
+                                                     const cplx<R>* __restrict__ dpsi,
+                                                     const cplx<R>* __restrict__ E, cplx<R>* __restrict__ A,
+                                                     const cplx<R>* __restrict__ tw,
+                                                     const LoopState* __restrict__ ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  const int p = blockIdx.x, j = blockIdx.y;
+  const int iter = ls->iter;
+  if (iter > 0 && j == 0) return;
+  const int n = g.n;
+  const size_t off = ((size_t)j * g.N + p) * n;
+  const double2* ps = psi0 + (size_t)p * n;
+  const cplx<R>* dp = (iter > 0) ? dpsi + ((size_t)(j - 1) * g.N + p) * n : nullptr;
+  const cplx<R>* e = E + off;
+  const R inv_n = (R)1.0 / (R)n;
+  auto load = [&](int q) {
+    double2 x = ps[q];
+    if (dp) {
+      const cplx<R> d = dp[q];
+      x.x += (double)d.x;
+      x.y += (double)d.y;
+    }
+    return cmul<R>(mk<R>((R)x.x, (R)x.y), e[q]);
+  };
+  auto store = [&](int t, cplx<R> v) { A[off + t] = cscale<R>(v, inv_n); };
+  fft_block<R, -1, EPT>(sm, n, tw, load, store);
+}
+
+// U_k(t): |A_m|^2 for m == n, 2 Re(A_m A_n^*) for m < n (pairs k = (m <= n))
+template <typename R>
+__device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, int2 mn, int t) {
+  const cplx<R> am = a[(size_t)mn.x * n + t];
+  if (mn.x == mn.y) return am.x * am.x + am.y * am.y;
+  const cplx<R> an = a[(size_t)mn.y * n + t];
+  return (R)2.0 * (am.x * an.x + am.y * an.y);
+}
+
+// ---------------------------------------------------------------------------
+// K2: pair products and the Raman convolution h_R * U_k for two pairs at once
+// (U_k1 + i U_k2 is transformed, multiplied by H = (dt/n) DFT(h_R), and
+// transformed back; h_R is real so the real and imaginary parts stay apart).
+// grid (ceil(K/2), M+1)
+// ---------------------------------------------------------------------------
+template <typename R, int EPT>
+__global__ void __launch_bounds__(1024) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V,
+                                                      const cplx<R>* __restrict__ H,
+                                                      const cplx<R>* __restrict__ tw,
+                                                      const int2* __restrict__ pairs,
+                                                      const LoopState* __restrict__ ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  const int j = blockIdx.y;
+  if (ls->iter > 0 && j == 0) return;
+  const int n = g.n;
+  const int k1 = 2 * blockIdx.x, k2 = k1 + 1;
+  const bool has2 = k2 < g.K;
+  const int2 mn1 = pairs[k1];
+  const int2 mn2 = has2 ? pairs[k2] : mn1;
+  const cplx<R>* a = A + (size_t)j * g.N * n;
+  auto load = [&](int t) {
+    return mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+  };
+  auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
+  fft_block<R, -1, EPT>(sm, n, tw, load, to_smem);
+  auto from_smem = [&](int q) { return sm[pad16(q)]; };
+  R* v = V + (size_t)j * g.KK * n;
+  const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
+  auto store = [&](int t, cplx<R> y) {
+    const R u1 = pair_product<R>(a, n, mn1, t);
+    if (g.raman_mode == 1) {
+      v[(size_t)k1 * n + t] = fK * u1 + fR * y.x;
+      if (has2) v[(size_t)k2 * n + t] = fK * pair_product<R>(a, n, mn2, t) + fR * y.y;
+    } else {
+      v[(size_t)k1 * n + t] = u1;
+      v[(size_t)(g.K + k1) * n + t] = y.x;
+      if (has2) {
+        v[(size_t)k2 * n + t] = pair_product<R>(a, n, mn2, t);
+        v[(size_t)(g.K + k2) * n + t] = y.y;
+      }
+    }
+  };
+  fft_block<R, +1, EPT>(sm, n, tw, from_smem, store);
+}
+
+// ---------------------------------------------------------------------------
+// K3: NL_p(t) = sum_l A_l R_pl, R_pl = sum_k G[(p,l)][k] V_k  (Eq. 1 bracket,
+// symmetry-reduced: rows (p <= l), columns (m <= n) or [U; h*U]).
+// One thread per (j, t); per-thread operands in shared memory.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_contract(Geo g, const cplx<R>* __restrict__ A, const R* __restrict__ V,
+                           const R* __restrict__ Gm, const int2* __restrict__ rows,
+                           const int2* __restrict__ pairs, cplx<R>* __restrict__ NL,
+                           const LoopState* __restrict__ ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int N = g.N, KK = g.KK, P = g.P, n = g.n;
+  int2* rs = reinterpret_cast<int2*>(smraw);  // [P]
+  R* Gs = reinterpret_cast<R*>(rs + P);       // [P][KK]
+  R* as = Gs + P * KK;                         // [2N][T]
+  R* vs = as + 2 * N * T;                      // [KK][T]
+  R* ns = vs + KK * T;                         // [2N][T]
+  for (int i = tid; i < P * KK; i += T) Gs[i] = Gm[i];
+  for (int i = tid; i < P; i += T) rs[i] = rows[i];
+  __syncthreads();
+  const size_t pt = (size_t)blockIdx.x * T + tid;
+  const size_t npts = (size_t)(g.M + 1) * n;
+  if (pt >= npts) return;
+  const int j = (int)(pt / n), t = (int)(pt - (size_t)j * n);
+  if (ls->iter > 0 && j == 0) return;
+  const cplx<R>* a = A + (size_t)j * N * n;
+  for (int l = 0; l < N; ++l) {
+    const cplx<R> x = a[(size_t)l * n + t];
+    as[(2 * l) * T + tid] = x.x;
+    as[(2 * l + 1) * T + tid] = x.y;
+    ns[(2 * l) * T + tid] = (R)0;
+    ns[(2 * l + 1) * T + tid] = (R)0;
+  }
+  if (g.raman_mode == 0) {
+    for (int k = 0; k < KK; ++k) vs[k * T + tid] = pair_product<R>(a, n, pairs[k], t);
+  } else {
+    const R* v = V + (size_t)j * KK * n;
+    for (int k = 0; k < KK; ++k) vs[k * T + tid] = v[(size_t)k * n + t];
+  }
+  for (int r = 0; r < P; ++r) {
+    const R* gr = Gs + r * KK;
+    R acc = (R)0;
+    for (int k = 0; k < KK; ++k) acc += gr[k] * vs[k * T + tid];
+    const int2 pl = rs[r];
+    ns[(2 * pl.x) * T + tid] += as[(2 * pl.y) * T + tid] * acc;
+    ns[(2 * pl.x + 1) * T + tid] += as[(2 * pl.y + 1) * T + tid] * acc;
+    if (pl.x != pl.y) {
+      ns[(2 * pl.y) * T + tid] += as[(2 * pl.x) * T + tid] * acc;
+      ns[(2 * pl.y + 1) * T + tid] += as[(2 * pl.x + 1) * T + tid] * acc;
+    }
+  }
+  cplx<R>* out = NL + (size_t)j * N * n;
+  for (int p = 0; p < N; ++p) out[(size_t)p * n + t] = mk<R>(ns[(2 * p) * T + tid], ns[(2 * p + 1) * T + tid]);
+}
+
+// ---------------------------------------------------------------------------
+// K4: I_j(w) = i gamma0 s(w) F{NL_p}(w) exp(-i beta j dz)   (Eq. MPA_eq)
+// grid (N, M+1)
+// ---------------------------------------------------------------------------
+template <typename R, int EPT>
+__global__ void __launch_bounds__(1024) k_integrand(Geo g, const cplx<R>* __restrict__ NL,
+                                                    const cplx<R>* __restrict__ E, cplx<R>* __restrict__ I,
+                                                    const cplx<R>* __restrict__ tw,
+                                                    const LoopState* __restrict__ ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  const int p = blockIdx.x, j = blockIdx.y;
+  if (ls->iter > 0 && j == 0) return;
+  const int n = g.n;
+  const size_t off = ((size_t)j * g.N + p) * n;
+  const cplx<R>* src = NL + off;
+  const cplx<R>* e = E + off;
+  auto load = [&](int t) { return src[t]; };
+  auto store = [&](int q, cplx<R> X) {
+    const R f = (R)(g.ss ? g.gamma0 * (1.0 + omega_of(q, n, g.dt) / g.omega0) : g.gamma0);
+    const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
+    I[off + q] = cmulc<R>(iX, e[q]);
+  };
+  fft_block<R, +1, EPT>(sm, n, tw, load, store);
+}
+
+// ---------------------------------------------------------------------------
+// K5: trapezoid over z' and the convergence measure (Sec. III.D)
+//   dpsi_j <- (dz/2) sum_{k=1..j} (I_{k-1} + I_k),
+//   eps = ||new - old|| / ||psi0 + new|| over j, p, w (FP64 sums).
+// The last block to finish decides whether the long step keeps iterating.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finish_iteration(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  const double diff = ls->diff, nrm = ls->nrm;
+  const bool finite = isfinite(diff) && isfinite(nrm);
+  const double eps = finite ? (nrm > 0.0 ? sqrt(diff / nrm) : 0.0) : nan("");
+  const int it = ls->iter + 1;
+  bool stop = false;
+  if (!finite) {
+    ls->status = ST_NONFINITE;
+    stop = true;
+  } else if (ls->fixed_iters > 0) {
+    stop = it >= ls->fixed_iters;
+  } else if (eps < ls->tol) {
+    stop = true;
+  } else if (eps < ls->floor_eps && eps > 0.5 * ls->prev_eps) {
+    stop = true;  // rounding-limited: eps no longer contracts
+  } else if (it >= ls->max_iter) {
+    ls->status = ST_NOT_CONVERGED;
+    stop = true;
+  }
+  ls->eps = eps;
+  ls->prev_eps = eps;
+  ls->iter = it;
+  ls->done = stop ? 1 : 0;
+  ls->diff = 0.0;
+  ls->nrm = 0.0;
+  ls->arrive5 = 0;
+  __threadfence();
+  if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __restrict__ psi0,
+                                                    cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
+                                                    LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  const size_t Nn = (size_t)g.N * g.n;
+  const int iter = ls->iter;
+  double diff = 0.0, nrm = 0.0;
+  const R hdz = (R)g.hdz;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
+    cplx<R> Ip = I[e];
+    cplx<R> acc = mk<R>(0, 0);
+    const double2 p0 = psi0[e];
+    for (int j = 1; j <= g.M; ++j) {
+      const cplx<R> Ij = I[(size_t)j * Nn + e];
+      acc = cadd<R>(acc, cscale<R>(cadd<R>(Ip, Ij), hdz));
+      Ip = Ij;
+      cplx<R>* slot = dpsi + (size_t)(j - 1) * Nn + e;
+      const cplx<R> old = iter > 0 ? *slot : mk<R>(0, 0);
+      const double dx = (double)acc.x - (double)old.x, dy = (double)acc.y - (double)old.y;
+      diff += dx * dx + dy * dy;
+      const double px = p0.x + (double)acc.x, py = p0.y + (double)acc.y;
+      nrm += px * px + py * py;
+      *slot = acc;
+    }
+  }
+  diff = block_sum(diff, red);
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ls->diff, diff);
+    atomicAdd(&ls->nrm, nrm);
+    __threadfence();
+    last = (atomicAdd(&ls->arrive5, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    finish_iteration(ls, h, use_cond);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K6: end of a long step (Sec. III.D): A~(z0 + L) = (psi0 + dpsi_M) exp(i beta M dz)
+// in FP64; becomes the next psi0.  Skipped when the long step failed.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0,
+                                                 const cplx<R>* __restrict__ dpsi,
+                                                 const double2* __restrict__ EM, LoopState* ls,
+                                                 cudaGraphConditionalHandle h, int use_cond) {
+  __shared__ bool last;
+  const size_t Nn = (size_t)g.N * g.n;
+  const int status = ls->status;
+  if (status == ST_OK) {
+    const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
+      const double2 p0 = psi0[e];
+      const cplx<R> dd = d[e];
+      const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
+      const double2 w = EM[e];
+      psi0[e] = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(&ls->arrive6, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const int it = ls->iter;
+    if (status == ST_OK) {
+      ls->step += 1;
+      ls->iters_total += it;
+      ls->iters_min = min(ls->iters_min, it);
+      ls->iters_max = max(ls->iters_max, it);
+      ls->hist[min(it, 32)] += 1;
+      ls->eps_max = fmax(ls->eps_max, ls->eps);
+    }
+    ls->iter = 0;
+    ls->done = 0;
+    ls->prev_eps = INFINITY;
+    ls->arrive6 = 0;
+    __threadfence();
+    if (use_cond) cudaGraphSetConditional(h, (status == ST_OK && ls->step < ls->nsteps) ? 1u : 0u);
+  }
+}
+
+// Start of a long step inside a graph: re-arm the iteration loop.
+__global__ void k_step_begin(cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 helpers used once per propagation
+// ---------------------------------------------------------------------------
+// out_p = scale * DFT_DIR(in_p) for each mode row p (grid N), n <= 8192.
+template <int DIR, int EPT>
+__global__ void __launch_bounds__(1024) k_fft64_rows(const double2* __restrict__ in, double2* __restrict__ out,
+                                                     int n, double scale, const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  const size_t off = (size_t)blockIdx.x * n;
+  auto load = [&](int i) { return in[off + i]; };
+  auto store = [&](int i, double2 v) { out[off + i] = make_double2(v.x * scale, v.y * scale); };
+  fft_block<double, DIR, EPT>(sm, n, tw, load, store);
+}
+
+// Half-length transforms of the even and odd samples (for n = 16384 in FP64):
+// out[2][rows][n/2]; blockIdx.y selects even (0) / odd (1).
+template <int DIR, int EPT>
+__global__ void __launch_bounds__(1024) k_fft64_halves(const double2* __restrict__ in, double2* __restrict__ out,
+                                                       int n, const double2* __restrict__ tw_half) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* sm = reinterpret_cast<double2*>(smraw);
+  const int h = n / 2, par = blockIdx.y;
+  const double2* src = in + (size_t)blockIdx.x * n;
+  double2* dst = out + ((size_t)par * gridDim.x + blockIdx.x) * h;
+  auto load = [&](int i) { return src[2 * i + par]; };
+  auto store = [&](int i, double2 v) { dst[i] = v; };
+  fft_block<double, DIR, EPT>(sm, h, tw_half, load, store);
+}
+
+// X_q = scale (Y_e[q mod h] + W^q Y_o[q mod h]), W = exp(DIR 2 pi i / n); tw[m] = exp(-2 pi i m/n)
+template <int DIR>
+__global__ void k_fft64_combine(const double2* __restrict__ half, double2* __restrict__ out, int rows, int n,
+                                double scale, const double2* __restrict__ tw) {
+  const int h = n / 2;
+  const size_t total = (size_t)rows * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / n), q = (int)(i - (size_t)r * n);
+    const int qm = q & (h - 1);
+    const double2 ye = half[(size_t)r * h + qm];
+    const double2 yo = half[((size_t)rows + r) * h + qm];
+    double2 w = tw[q];
+    if (DIR > 0) w.y = -w.y;
+    out[i] = make_double2(scale * (ye.x + w.x * yo.x - w.y * yo.y), scale * (ye.y + w.x * yo.y + w.y * yo.x));
+  }
+}
+
+// Energy-like sums of the spectrum: spec[0] = sum |psi|^2,
+// spec[1] = sum_{w0 + w > 0} |psi|^2 / (w0 + w).
+__global__ void k_spec_sums(const double2* __restrict__ psi, int N, int n, double dt, double omega0,
+                            double* __restrict__ spec) {
+  __shared__ double red[32];
+  double s0 = 0.0, s1 = 0.0;
+  const size_t total = (size_t)N * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i % n);
+    const double a2 = psi[i].x * psi[i].x + psi[i].y * psi[i].y;
+    s0 += a2;
+    const double w = omega0 + omega_of(q, n, dt);
+    if (w > 0.0) s1 += a2 / w;
+  }
+  s0 = block_sum(s0, red);
+  s1 = block_sum(s1, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&spec[0], s0);
+    atomicAdd(&spec[1], s1);
+  }
+}
+
+// Raman transfer function H[q] = (dt/n) DFT_-(h_R)[q] from an FP64 spectrum.
+template <typename R>
+__global__ void k_raman_H(const double2* __restrict__ hspec, cplx<R>* __restrict__ H, int n, double dt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) H[q] = mk<R>((R)(hspec[q].x * dt / n), (R)(hspec[q].y * dt / n));
+}
+
+// Check a field for NaN / Inf (flag set to 1 if any).
+__global__ void k_nonfinite(const double2* __restrict__ x, size_t count, int* flag) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i].x) || !isfinite(x[i].y)) *flag = 1;
+}
+
+}  // namespace gm

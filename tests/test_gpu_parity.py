@@ -1,0 +1,230 @@
+"""CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Bars (relative L2 over all modes and samples): FP64 <= 1e-10, FP32 <= 1e-5.
+Sizes span several FFT passes (the leading radix-2/4/8 pass and radix-16
+passes), odd pair counts, a separate Raman tensor, ragged long steps and the
+largest transform (Nt = 2^14).
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1708_05324_b300 import binding as B
+from paper_1708_05324_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_run(prob, precision, L=None, dz=None, M=None, tol=None, **kw):
+    ctx = B.Context.from_problem(prob, precision=precision, **{k: v for k, v in kw.items()
+                                                              if k in ("max_iter", "fixed_iters")})
+    try:
+        out, st, rc = ctx.propagate(prob.A0, L or prob.L, dz or prob.dz, M or prob.M,
+                                    prob.tol if tol is None else tol, check=False)
+    finally:
+        ctx.close()
+    return out, st, rc
+
+
+def oracle_run(prob, L=None, dz=None, M=None, tol=None, **kw):
+    fib = O.Fiber.from_problem(prob)
+    return O.mpa_propagate(fib, prob.A0, L or prob.L, dz or prob.dz, M or prob.M,
+                           prob.tol if tol is None else tol, **kw)
+
+
+@functools.lru_cache(maxsize=None)
+def small(name, N, Nt, fR, ss=1, seed=11, energy=20e-9, split_raman=False):
+    prob = I.grin_problem(name, N=N, Nt=Nt, dt=2e-12 / Nt, kind="gaussian", fwhm=150e-15,
+                          energy=energy, L=2e-3, dz=1e-4, M=5, tol=1e-13, seed=seed, fR=fR,
+                          self_steepening=ss, s_from="gh")
+    if split_raman:
+        # a different (still fully symmetric) Raman tensor: S^R = 0.7 S^K + 0.3 S_iso
+        iso = np.zeros_like(prob.SK)
+        for p in range(N):
+            iso[p, p, p, p] = prob.SK[0, 0, 0, 0]
+        prob.SR = 0.7 * prob.SK + 0.3 * iso
+    return prob
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_small(key):
+    prob = small(*key)
+    return oracle_run(prob)
+
+
+# ----------------------------------------------------------------------------
+def test_linear_propagation_fp64_matches_oracle():
+    """n2 = 0: the output is the input times exp(i beta L), with beta L ~ 1e4
+    rad at the grid edge; dz = 2^-10 m and M = 8 make every z_j exact."""
+    lin = I.grin_problem("lin", N=3, Nt=256, dt=2e-12 / 256, kind="gaussian", fwhm=150e-15,
+                         energy=20e-9, L=0.1, dz=2.0 ** -10, M=8, tol=1e-13, seed=11, s_from="gh")
+    lin.n2 = 0.0
+    L = 100 * 8 * 2.0 ** -10
+    out, st, rc = gpu_run(lin, "fp64", L=L)
+    assert rc == B.OK and st["iters_max"] == 1
+    ref, _ = O.mpa_propagate(O.Fiber.from_problem(lin), lin.A0, L, 2.0 ** -10, 8, 1e-13)
+    assert rel(out, ref) < 1e-12
+
+
+@pytest.mark.parametrize("Nt", [16, 32, 64, 128, 1024])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_fft_pass_structure(Nt, precision):
+    """Nt = 16 (one radix-16 pass), 32/64/128 (leading radix 2/4/8), 1024."""
+    key = ("p", 3, Nt, 0.18)
+    prob = small(*key)
+    ref, sref = oracle_small(key)
+    out, st, rc = gpu_run(prob, precision, tol=1e-13 if precision == "fp64" else 1e-9)
+    assert rc == B.OK
+    assert rel(out, ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("N,fR,ss,split", [(1, 0.0, 1, False), (1, 0.18, 0, False), (2, 0.18, 1, False),
+                                           (4, 0.0, 0, False), (4, 0.18, 1, True), (6, 0.18, 1, False)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_modes_raman_and_steepening_variants(N, fR, ss, split, precision):
+    key = ("v", N, 256, fR, ss, 11, 20e-9, split)
+    prob = small(*key)
+    ref, sref = oracle_small(key)
+    out, st, rc = gpu_run(prob, precision, tol=1e-13 if precision == "fp64" else 1e-9)
+    assert rc == B.OK
+    assert rel(out, ref) < TOL[precision]
+    if precision == "fp64":
+        assert st["iters_total"] == sum(sref["iters"])
+
+
+def test_ragged_last_long_step_and_M1():
+    key = ("p", 3, 128, 0.18)
+    prob = small(*key)
+    for L, M in ((2.3e-3, 5), (7e-4, 1), (1.2e-3, 7)):
+        ref, sref = oracle_run(prob, L=L, M=M)
+        out, st, rc = gpu_run(prob, "fp64", L=L, M=M)
+        assert rc == B.OK
+        assert rel(out, ref) < 1e-10
+        assert st["long_steps"] == len(sref["iters"])
+        assert st["z"] == pytest.approx(L, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_largest_transform_2_14(precision):
+    if precision == "fp64":
+        pytest.skip("FP64 iterates are built for Nt <= 8192")
+    prob = I.grin_problem("big", N=2, Nt=16384, dt=20e-12 / 16384, kind="gaussian", fwhm=300e-15,
+                          energy=50e-9, L=5e-4, dz=2.5e-5, M=10, tol=1e-13, seed=3, fR=0.18, s_from="gh")
+    ref, _ = oracle_run(prob)
+    out, st, rc = gpu_run(prob, precision, tol=1e-9)
+    assert rc == B.OK
+    assert rel(out, ref) < TOL[precision]
+
+
+@functools.lru_cache(maxsize=None)
+def c2_prefix():
+    prob = I.workload("C2", L=4 * 10 * 25e-6)  # 4 long steps of the 0.5 m run
+    ref, sref = oracle_run(prob, tol=1e-13)
+    return prob, ref, sref
+
+
+def test_c2_prefix_fp64():
+    """Kerr + Raman, N = 6, Nt = 2^13: the benchmark workload, 4 long steps."""
+    prob, ref, sref = c2_prefix()
+    out, st, rc = gpu_run(prob, "fp64", tol=1e-13)
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-10
+    assert st["long_steps"] == 4
+
+
+def test_c2_prefix_fp32():
+    prob, ref, sref = c2_prefix()
+    out, st, rc = gpu_run(prob, "fp32", tol=1e-8)
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-5
+
+
+def test_c1_full_length_fp64():
+    """Kerr only, N = 3, Nt = 2^10, 5 cm in 20 long steps of M = 5."""
+    prob = I.workload("C1")
+    ref, sref = oracle_run(prob)
+    out, st, rc = gpu_run(prob, "fp64")
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-10
+    assert st["long_steps"] == 20
+    assert st["iters_total"] == sum(sref["iters"])
+
+
+# ----------------------------------------------------------------------------
+def test_not_converged_returns_field_of_last_completed_step():
+    prob = small("p", 3, 128, 0.18)
+    out, st, rc = gpu_run(prob, "fp64", tol=1e-300, max_iter=2)
+    assert rc == B.E_NOT_CONVERGED
+    assert st["z"] == 0.0 and st["long_steps"] == 0
+    assert rel(out, prob.A0) < 1e-14
+
+
+def test_nonfinite_input_is_rejected():
+    prob = small("p", 3, 128, 0.18)
+    bad = prob.A0.copy()
+    bad[1, 7] = np.nan
+    ctx = B.Context.from_problem(prob, precision="fp32")
+    _, _, rc = ctx.propagate(bad, prob.L, prob.dz, prob.M, 1e-8, check=False)
+    ctx.close()
+    assert rc == B.E_INVALID
+
+
+def test_fixed_iterations_match_oracle():
+    key = ("p", 3, 256, 0.18)
+    prob = small(*key)
+    ref, sref = oracle_run(prob, fixed_iters=3)
+    out, st, rc = gpu_run(prob, "fp64", fixed_iters=3)
+    assert rc == B.OK and st["iters_min"] == st["iters_max"] == 3
+    assert rel(out, ref) < 1e-10
+
+
+def test_statistics_energy_and_photon_number():
+    prob = small("p", 3, 256, 0.18)
+    out, st, rc = gpu_run(prob, "fp64")
+    assert st["energy_in"] == pytest.approx(prob.dt * np.sum(abs(prob.A0) ** 2), rel=1e-12)
+    assert st["energy_out"] == pytest.approx(prob.dt * np.sum(abs(out) ** 2), rel=1e-12)
+    fib = O.Fiber.from_problem(prob)
+    assert st["photons_in"] == pytest.approx(O.photon_number(fib, O.freq_from_time(prob.A0)), rel=1e-12)
+    assert sum(st["iter_hist"]) == st["long_steps"]
+
+
+def test_graph_and_host_loop_agree_bitwise(monkeypatch):
+    prob = small("p", 3, 256, 0.18)
+    a, sa, _ = gpu_run(prob, "fp64")
+    monkeypatch.setenv("GMMNLSE_NO_GRAPH", "1")
+    b, sb, _ = gpu_run(prob, "fp64")
+    assert np.array_equal(a, b)
+    assert sa["iter_hist"] == sb["iter_hist"]
+
+
+def test_repeat_is_deterministic():
+    prob = small("p", 4, 256, 0.18)
+    ctx = B.Context.from_problem(prob, precision="fp64")
+    a, _, _ = ctx.propagate(prob.A0, prob.L, prob.dz, prob.M, prob.tol)
+    b, _, _ = ctx.propagate(prob.A0, prob.L, prob.dz, prob.M, prob.tol)
+    ctx.close()
+    assert np.array_equal(a, b)
+
+
+def test_device_pointers_and_torch_stream():
+    import torch
+    prob = small("p", 3, 256, 0.18)
+    ref, _ = oracle_small(("p", 3, 256, 0.18))
+    s = torch.cuda.Stream()
+    ctx = B.Context(prob.N, prob.Nt, prob.dt, prob.lam0, prob.n2, prob.beta, prob.SK, None, prob.fR,
+                    prob.hR, True, "fp64", stream=s.cuda_stream, io_device=True)
+    a0 = torch.from_numpy(prob.A0).cuda()
+    out = torch.empty_like(a0)
+    torch.cuda.synchronize()
+    ctx.propagate(a0, prob.L, prob.dz, prob.M, prob.tol, out=out)
+    ctx.close()
+    assert rel(out.cpu().numpy(), ref) < 1e-10
