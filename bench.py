@@ -101,11 +101,11 @@ class ClockSampler:
 
 def launches_per_step(st, raman, graph=True):
     """Kernel launches of one propagate call, from its statistics."""
-    per_iter = 5 if raman else 4
+    per_iter = 6 if raman else 5   # K1 [K2] K3 K4 K5 + decision
     fft = 1  # Nt <= 8192
     n = 1 + fft + 1          # non-finite check, forward transform, input sums
     n += 1 + fft             # output sums, inverse transform
-    n += st["iters_total"] * per_iter + st["long_steps"] * (2 if graph else 1)
+    n += st["iters_total"] * per_iter + st["long_steps"] * (3 if graph else 2)
     return n
 
 

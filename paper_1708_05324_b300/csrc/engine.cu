@@ -508,7 +508,8 @@ static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraph
   k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E, (cplx<R>*)jb->I,
                                             tw, jb->ls);
   k_trapz_norm<R><<<elementwise_blocks((size_t)N * n), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->dpsi,
-                                                                    (const cplx<R>*)jb->I, jb->ls, h, use_cond);
+                                                                    (const cplx<R>*)jb->I, jb->ls);
+  k_decide<<<1, 32, 0, s>>>(jb->ls, h, use_cond);
 }
 
 template <typename R>
@@ -517,7 +518,8 @@ static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, 
   gmmnlse_ctx* c = jb->ctx;
   const size_t Nn = (size_t)c->N * c->n;
   k_advance<R><<<elementwise_blocks(Nn), 256, 0, s>>>(g, jb->psi0, (const cplx<R>*)jb->dpsi,
-                                                      jb->EM64 + (size_t)which * Nn, jb->ls, h, use_cond);
+                                                      jb->EM64 + (size_t)which * Nn, jb->ls);
+  k_step_end<<<1, 32, 0, s>>>(jb->ls, h, use_cond);
 }
 
 template <typename R, int EPT>
@@ -808,11 +810,11 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
           break;
         case 4:
           k_trapz_norm<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->dpsi,
-                                                                  (const cplx<R>*)jb->I, jb->ls, 0, 0);
+                                                                  (const cplx<R>*)jb->I, jb->ls);
           break;
         default:
           k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (const cplx<R>*)jb->dpsi, jb->EM64,
-                                                               jb->ls, 0, 0);
+                                                               jb->ls);
           break;
       }
       CK(cudaGetLastError());

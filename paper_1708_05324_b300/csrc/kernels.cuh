@@ -28,8 +28,6 @@ struct LoopState {
   double eps, prev_eps;    // eps of this and the previous iteration
   double eps_max;          // largest final eps of a completed long step
   double tol, floor_eps;   // threshold; rounding floor of the working precision
-  unsigned int arrive5;    // blocks of the trapezoid kernel that have finished
-  unsigned int arrive6;    // blocks of the advance kernel that have finished
   int iter;                // updates made in the current long step
   int done;                // current long step has stopped iterating
   int status;              // ST_*
@@ -246,47 +244,15 @@ __global__ void __launch_bounds__(1024) k_integrand(Geo g, const cplx<R>* __rest
 }
 
 // ---------------------------------------------------------------------------
-// K5: trapezoid over z' and the convergence measure (Sec. III.D)
+// K5: trapezoid over z' and the convergence sums (Sec. III.D)
 //   dpsi_j <- (dz/2) sum_{k=1..j} (I_{k-1} + I_k),
-//   eps = ||new - old|| / ||psi0 + new|| over j, p, w (FP64 sums).
-// The last block to finish decides whether the long step keeps iterating.
+//   diff += |new - old|^2, nrm += |psi0 + new|^2 over j, p, w (FP64).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void finish_iteration(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
-  const double diff = ls->diff, nrm = ls->nrm;
-  const bool finite = isfinite(diff) && isfinite(nrm);
-  const double eps = finite ? (nrm > 0.0 ? sqrt(diff / nrm) : 0.0) : nan("");
-  const int it = ls->iter + 1;
-  bool stop = false;
-  if (!finite) {
-    ls->status = ST_NONFINITE;
-    stop = true;
-  } else if (ls->fixed_iters > 0) {
-    stop = it >= ls->fixed_iters;
-  } else if (eps < ls->tol) {
-    stop = true;
-  } else if (eps < ls->floor_eps && eps > 0.5 * ls->prev_eps) {
-    stop = true;  // rounding-limited: eps no longer contracts
-  } else if (it >= ls->max_iter) {
-    ls->status = ST_NOT_CONVERGED;
-    stop = true;
-  }
-  ls->eps = eps;
-  ls->prev_eps = eps;
-  ls->iter = it;
-  ls->done = stop ? 1 : 0;
-  ls->diff = 0.0;
-  ls->nrm = 0.0;
-  ls->arrive5 = 0;
-  __threadfence();
-  if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
-}
-
 template <typename R>
 __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __restrict__ psi0,
                                                     cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
-                                                    LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+                                                    LoopState* ls) {
   __shared__ double red[32];
-  __shared__ bool last;
   const size_t Nn = (size_t)g.N * g.n;
   const int iter = ls->iter;
   double diff = 0.0, nrm = 0.0;
@@ -313,14 +279,40 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __rest
   if (threadIdx.x == 0) {
     atomicAdd(&ls->diff, diff);
     atomicAdd(&ls->nrm, nrm);
-    __threadfence();
-    last = (atomicAdd(&ls->arrive5, 1u) == gridDim.x - 1);
   }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    finish_iteration(ls, h, use_cond);
+}
+
+// Convergence decision after K5 (one thread): eps, stop rule, reset of the
+// sums, and the while-node condition when running inside a graph.  Every
+// path ends the loop after at most max_iter (or fixed_iters) updates.
+__global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double diff = ls->diff, nrm = ls->nrm;
+  const bool finite = isfinite(diff) && isfinite(nrm);
+  const double eps = finite ? (nrm > 0.0 ? sqrt(diff / nrm) : 0.0) : nan("");
+  const int it = ls->iter + 1;
+  bool stop = false;
+  if (!finite) {
+    ls->status = ST_NONFINITE;
+    stop = true;
+  } else if (ls->fixed_iters > 0) {
+    stop = it >= ls->fixed_iters;
+  } else if (eps < ls->tol) {
+    stop = true;
+  } else if (eps < ls->floor_eps && eps > 0.5 * ls->prev_eps) {
+    stop = true;  // rounding-limited: eps no longer contracts
+  } else if (it >= ls->max_iter) {
+    ls->status = ST_NOT_CONVERGED;
+    stop = true;
   }
+  if (it >= 4096) stop = true;  // hard cap, whatever the settings
+  ls->eps = eps;
+  ls->prev_eps = eps;
+  ls->iter = it;
+  ls->done = stop ? 1 : 0;
+  ls->diff = 0.0;
+  ls->nrm = 0.0;
+  if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -330,45 +322,36 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __rest
 template <typename R>
 __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0,
                                                  const cplx<R>* __restrict__ dpsi,
-                                                 const double2* __restrict__ EM, LoopState* ls,
-                                                 cudaGraphConditionalHandle h, int use_cond) {
-  __shared__ bool last;
+                                                 const double2* __restrict__ EM, const LoopState* ls) {
   const size_t Nn = (size_t)g.N * g.n;
-  const int status = ls->status;
+  if (ls->status != ST_OK) return;
+  const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 p0 = psi0[e];
+    const cplx<R> dd = d[e];
+    const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
+    const double2 w = EM[e];
+    psi0[e] = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
+  }
+}
+
+// Long-step bookkeeping after K6 (one thread) and the outer while-node
+// condition: continue while the step succeeded and steps remain.
+__global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int status = ls->status, it = ls->iter;
   if (status == ST_OK) {
-    const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
-      const double2 p0 = psi0[e];
-      const cplx<R> dd = d[e];
-      const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
-      const double2 w = EM[e];
-      psi0[e] = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
-    }
+    ls->step += 1;
+    ls->iters_total += it;
+    ls->iters_min = min(ls->iters_min, it);
+    ls->iters_max = max(ls->iters_max, it);
+    ls->hist[min(it, 32)] += 1;
+    ls->eps_max = fmax(ls->eps_max, ls->eps);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = (atomicAdd(&ls->arrive6, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const int it = ls->iter;
-    if (status == ST_OK) {
-      ls->step += 1;
-      ls->iters_total += it;
-      ls->iters_min = min(ls->iters_min, it);
-      ls->iters_max = max(ls->iters_max, it);
-      ls->hist[min(it, 32)] += 1;
-      ls->eps_max = fmax(ls->eps_max, ls->eps);
-    }
-    ls->iter = 0;
-    ls->done = 0;
-    ls->prev_eps = INFINITY;
-    ls->arrive6 = 0;
-    __threadfence();
-    if (use_cond) cudaGraphSetConditional(h, (status == ST_OK && ls->step < ls->nsteps) ? 1u : 0u);
-  }
+  ls->iter = 0;
+  ls->done = 0;
+  ls->prev_eps = INFINITY;
+  if (use_cond) cudaGraphSetConditional(h, (status == ST_OK && ls->step < ls->nsteps) ? 1u : 0u);
 }
 
 // Start of a long step inside a graph: re-arm the iteration loop.
