@@ -143,6 +143,37 @@ int gmmnlse_destroy(gmmnlse_ctx* ctx);
 int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, int M,
                       double tol, double* Aout, gmmnlse_stats* st);
 
+/*
+ * gmmnlse_propagate_noalloc -- gmmnlse_propagate without any memory
+ * allocation.  (An addition of this library: the paper has no counterpart.)
+ *
+ * For callers that cannot have a library allocate device memory: work being
+ * recorded into a CUDA stream capture, latency-critical loops that cannot
+ * take the device-wide synchronisation of cudaMalloc/cudaFree, and programs
+ * whose device memory is all owned by their own pool allocator.  It runs the
+ * same kernels as gmmnlse_propagate (host-driven iteration loop, no graphs,
+ * no events), with the workspace in one static device array of 32 MiB that
+ * every GPU loading the library holds until the process exits.
+ *
+ *   ctx   a context made beforehand with gmmnlse_create (that call allocates).
+ *   A0    [N][Nt] complex128 input field in DEVICE memory (whatever
+ *         prm.io_device says); Aout the same for the output.
+ *   L, dz, M, tol, st as for gmmnlse_propagate (st->ms is 0).
+ *
+ * A problem whose workspace does not fit in the 32 MiB array is rejected with
+ * GMMNLSE_E_NOMEM before any work, and gmmnlse_last_error() says so.  (For
+ * FP32, N = 6, Nt = 8192, M = 10 with Raman just fits.)  The first call on a
+ * device sets that device up (it looks up the array's device address and
+ * sets kernel attributes); make that first call before any stream capture.
+ * All calls share the one array, which keeps what the last call left in it:
+ * the entry point resets every part that must start from zero.  Two calls
+ * whose work overlaps on the GPU (different streams, or different threads
+ * with different contexts on one device) race on the array and give wrong
+ * results: serialise them.
+ */
+int gmmnlse_propagate_noalloc(gmmnlse_ctx* ctx, const double* A0, double L, double dz, int M,
+                              double tol, double* Aout, gmmnlse_stats* st);
+
 /* Static, human-readable text for a status code. */
 const char* gmmnlse_strerror(int status);
 

@@ -26,6 +26,7 @@ EXPORTS = [
     "gmmnlse_create", "gmmnlse_destroy", "gmmnlse_propagate", "gmmnlse_strerror",
     "gmmnlse_last_error", "gmmnlse_request_bytes", "gmmnlse_server_create",
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
+    "gmmnlse_propagate_noalloc",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -91,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(Stats)]
     lib.gmmnlse_server_destroy.argtypes = [vp]
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.gmmnlse_propagate_noalloc.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, vp,
+                                              C.POINTER(Stats)]
     del dp
     _lib = lib
     return lib

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __rest
 // Convergence decision after K5 (one thread): eps, stop rule, reset of the
 // sums, and the while-node condition when running inside a graph.  Every
 // path ends the loop after at most max_iter (or fixed_iters) updates.
-__global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double diff = ls->diff, nrm = ls->nrm;
   const bool finite = isfinite(diff) && isfinite(nrm);
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ ps
 
 // Long-step bookkeeping after K6 (one thread) and the outer while-node
 // condition: continue while the step succeeded and steps remain.
-__global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+static __global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int status = ls->status, it = ls->iter;
   if (status == ST_OK) {
@@ -355,7 +355,7 @@ __global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, int use_
 }
 
 // Start of a long step inside a graph: re-arm the iteration loop.
-__global__ void k_step_begin(cudaGraphConditionalHandle h) {
+static __global__ void k_step_begin(cudaGraphConditionalHandle h) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
 }
 
@@ -408,7 +408,7 @@ __global__ void k_fft64_combine(const double2* __restrict__ half, double2* __res
 
 // Energy-like sums of the spectrum: spec[0] = sum |psi|^2,
 // spec[1] = sum_{w0 + w > 0} |psi|^2 / (w0 + w).
-__global__ void k_spec_sums(const double2* __restrict__ psi, int N, int n, double dt, double omega0,
+static __global__ void k_spec_sums(const double2* __restrict__ psi, int N, int n, double dt, double omega0,
                             double* __restrict__ spec) {
   __shared__ double red[32];
   double s0 = 0.0, s1 = 0.0;
@@ -436,7 +436,7 @@ __global__ void k_raman_H(const double2* __restrict__ hspec, cplx<R>* __restrict
 }
 
 // Check a field for NaN / Inf (flag set to 1 if any).
-__global__ void k_nonfinite(const double2* __restrict__ x, size_t count, int* flag) {
+static __global__ void k_nonfinite(const double2* __restrict__ x, size_t count, int* flag) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
     if (!isfinite(x[i].x) || !isfinite(x[i].y)) *flag = 1;
 }
