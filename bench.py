@@ -171,6 +171,8 @@ def main():
     ap.add_argument("--length", type=float, default=0.5, help="fiber length per step [m]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only the timed propagations and the per-kernel profile (for ncu captures)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -238,6 +240,17 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_s = float(t.item())
     value = u * args.steps * world / dev_s
+
+    if args.profile_run:
+        prof = ctx.profile(prob.M, reps=5)
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": 1e3 * dev_s / args.steps,
+                              "kernels_ms": {k: v[0] for k, v in prof.items()},
+                              "kernels_bytes": {k: v[1] for k, v in prof.items()}}))
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     ctx_h = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream)

@@ -187,8 +187,8 @@ const char* gmmnlse_last_error(void);
  * coupling contraction; forward FFT x integrand prefactor; trapezoid +
  * convergence norm; long-step advance) on the workspace of its last
  * gmmnlse_propagate, which must have used at least M substeps.  Each kernel
- * is launched reps times (after one untimed launch) on the context's stream,
- * bracketed by CUDA events.  ms[6] receives the mean duration of each kernel
+ * is launched reps times back to back (after one untimed launch) on the
+ * context's stream between two CUDA events.  ms[6] receives the mean duration of each kernel
  * [ms]; bytes[6] its algorithmic bytes per launch (each operand read or
  * written once).  Leaves the workspace iterate in an arbitrary state (the
  * next gmmnlse_propagate starts afresh).

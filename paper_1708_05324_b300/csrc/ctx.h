@@ -16,6 +16,7 @@ struct gm_job {
   gmmnlse_ctx* ctx = nullptr;
   int Mcap = 0;
   double2* psi0 = nullptr;  // [N][n]
+  void* psiR = nullptr;     // [N][n] cplx<R> (aliases psi0 in FP64)
   void* dpsi = nullptr;     // [M][N][n]
   void* A = nullptr;        // [M+1][N][n]
   void* V = nullptr;        // [M+1][KK][n]
@@ -52,6 +53,7 @@ struct gmmnlse_ctx {
   double2* tw64h = nullptr;     // [n/2]
   float2* tw32 = nullptr;       // [n]
   void* H = nullptr;            // [n] cplx<R>
+  void* fac = nullptr;          // [n] R: gamma0 s(w_q)
   void* G = nullptr;            // [P][KK] R
   int2* rows = nullptr;         // [P]
   int2* pairs = nullptr;        // [K]
@@ -63,3 +65,43 @@ struct gmmnlse_ctx {
   std::mutex mu;
 };
 
+
+// ---------------------------------------------------------------------------
+// Coupling contraction launch: registers for N <= 8, shared memory otherwise
+// ---------------------------------------------------------------------------
+template <typename R, int N, int MODE>
+static inline void launch_contract_reg(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V,
+                                       void* NL, const gm::LoopState* ls, cudaStream_t s) {
+  const size_t pts = (size_t)(g.M + 1) * g.n;
+  gm::k_contract_reg<R, N, MODE><<<(unsigned)((pts + 255) / 256), 256, 0, s>>>(
+      g, (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (gm::cplx<R>*)NL, ls);
+}
+
+template <typename R, int N>
+static inline void launch_contract_n(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V, void* NL,
+                                     const gm::LoopState* ls, cudaStream_t s) {
+  if (c->raman_mode == 0) launch_contract_reg<R, N, 0>(g, c, A, V, NL, ls, s);
+  else if (c->raman_mode == 1) launch_contract_reg<R, N, 1>(g, c, A, V, NL, ls, s);
+  else launch_contract_reg<R, N, 2>(g, c, A, V, NL, ls, s);
+}
+
+template <typename R>
+static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V, void* NL,
+                                   const gm::LoopState* ls, cudaStream_t s) {
+  switch (c->N) {
+    case 1: launch_contract_n<R, 1>(g, c, A, V, NL, ls, s); return;
+    case 2: launch_contract_n<R, 2>(g, c, A, V, NL, ls, s); return;
+    case 3: launch_contract_n<R, 3>(g, c, A, V, NL, ls, s); return;
+    case 4: launch_contract_n<R, 4>(g, c, A, V, NL, ls, s); return;
+    case 5: launch_contract_n<R, 5>(g, c, A, V, NL, ls, s); return;
+    case 6: launch_contract_n<R, 6>(g, c, A, V, NL, ls, s); return;
+    case 7: launch_contract_n<R, 7>(g, c, A, V, NL, ls, s); return;
+    case 8: launch_contract_n<R, 8>(g, c, A, V, NL, ls, s); return;
+    default: {
+      const int CT = c->contract_threads;
+      const size_t pts = (size_t)(g.M + 1) * g.n;
+      gm::k_contract<R><<<(unsigned)((pts + CT - 1) / CT), CT, c->contract_smem, s>>>(
+          g, (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, c->rows, c->pairs, (gm::cplx<R>*)NL, ls);
+    }
+  }
+}

@@ -135,13 +135,33 @@ template <typename R, int DIR> struct Dft<R, DIR, 16> {
   }
 };
 
-// One radix-RAD pass.  tw[m] = exp(-2 pi i m / n), m < n.
+// One radix-RAD pass.  tw[m] = exp(-2 pi i m / n), m < n.  The twiddle loads
+// of the pass do not depend on the data, so they are issued first and their
+// latency overlaps the data reads and the barrier.
 template <typename R, int DIR, int RAD, int EPT, bool FIRST, bool LAST, class Load, class Store>
 __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<R>* __restrict__ tw,
                                          const Load& load, const Store& store) {
   constexpr int B = EPT / RAD;  // butterflies per thread
+  constexpr int NW = RAD == 16 ? 4 : RAD - 1;  // table reads per butterfly
   const int T = blockDim.x;
   const int stride = n / RAD;
+  cplx<R> wt[B][NW];
+  if (Ns > 1) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = threadIdx.x + b * T;
+      const int step = (j & (Ns - 1)) * (n / (Ns * RAD));
+      if (RAD == 16) {
+        wt[b][0] = tw[step];
+        wt[b][1] = tw[2 * step];
+        wt[b][2] = tw[4 * step];
+        wt[b][3] = tw[8 * step];
+      } else {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) wt[b][r - 1] = tw[r * step];
+      }
+    }
+  }
   cplx<R> v[B][RAD];
 #pragma unroll
   for (int b = 0; b < B; ++b) {
@@ -158,12 +178,29 @@ __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<
     const int j = threadIdx.x + b * T;
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      const int step = n / (Ns * RAD);
+      cplx<R> w[RAD];
+      if (RAD == 16) {
+        // W^r for r = 1..15 from W, W^2, W^4, W^8 with at most three
+        // products each (error <= 4 ulp)
+        w[1] = wt[b][0];
+        w[2] = wt[b][1];
+        w[4] = wt[b][2];
+        w[8] = wt[b][3];
+        w[3] = cmul<R>(w[1], w[2]);
+        w[5] = cmul<R>(w[1], w[4]);
+        w[6] = cmul<R>(w[2], w[4]);
+        w[7] = cmul<R>(w[3], w[4]);
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul<R>(w[r - 8], w[8]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) w[r] = wt[b][r - 1];
+      }
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        cplx<R> w = tw[(r * k) * step];
-        if (DIR > 0) w.y = -w.y;
-        v[b][r] = cmul<R>(v[b][r], w);
+        cplx<R> x = w[r];
+        if (DIR > 0) x.y = -x.y;
+        v[b][r] = cmul<R>(v[b][r], x);
       }
     }
     Dft<R, DIR, RAD>::run(v[b]);

@@ -3,6 +3,7 @@
 //
 // Data (row-major, all resident on the device for the whole propagation):
 //   psi0 [N][n]      double2  running spectrum A~(z0, w): FP64 between long steps
+//   psiR [N][n]      cplx<R>  psi0 rounded to the working precision (= psi0 in FP64)
 //   dpsi [M][N][n]   cplx<R>  psi_j - psi0, j = 1..M (the iterate)
 //   E    [M+1][N][n] cplx<R>  exp(i beta_p(w) j dz), phase reduced in FP64
 //   A    [M+1][N][n] cplx<R>  A_j(t) = F^-1{psi_j E_j}
@@ -76,7 +77,7 @@ __global__ void k_phase_tables(const double* __restrict__ beta, int Nn, int M, d
 // K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N, M+1)
 // ---------------------------------------------------------------------------
 template <typename R, int EPT>
-__global__ void __launch_bounds__(1024) k_ip_to_time(Geo g, const double2* __restrict__ psi0,
+__global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __restrict__ psiR,
                                                      const cplx<R>* __restrict__ dpsi,
                                                      const cplx<R>* __restrict__ E, cplx<R>* __restrict__ A,
                                                      const cplx<R>* __restrict__ tw,
@@ -88,18 +89,14 @@ __global__ void __launch_bounds__(1024) k_ip_to_time(Geo g, const double2* __res
   if (iter > 0 && j == 0) return;
   const int n = g.n;
   const size_t off = ((size_t)j * g.N + p) * n;
-  const double2* ps = psi0 + (size_t)p * n;
+  const cplx<R>* ps = psiR + (size_t)p * n;
   const cplx<R>* dp = (iter > 0) ? dpsi + ((size_t)(j - 1) * g.N + p) * n : nullptr;
   const cplx<R>* e = E + off;
   const R inv_n = (R)1.0 / (R)n;
   auto load = [&](int q) {
-    double2 x = ps[q];
-    if (dp) {
-      const cplx<R> d = dp[q];
-      x.x += (double)d.x;
-      x.y += (double)d.y;
-    }
-    return cmul<R>(mk<R>((R)x.x, (R)x.y), e[q]);
+    cplx<R> x = ps[q];
+    if (dp) x = cadd<R>(x, dp[q]);
+    return cmul<R>(x, e[q]);
   };
   auto store = [&](int t, cplx<R> v) { A[off + t] = cscale<R>(v, inv_n); };
   fft_block<R, -1, EPT>(sm, n, tw, load, store);
@@ -121,7 +118,7 @@ __device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, 
 // grid (ceil(K/2), M+1)
 // ---------------------------------------------------------------------------
 template <typename R, int EPT>
-__global__ void __launch_bounds__(1024) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V,
+__global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V,
                                                       const cplx<R>* __restrict__ H,
                                                       const cplx<R>* __restrict__ tw,
                                                       const int2* __restrict__ pairs,
@@ -217,13 +214,73 @@ __global__ void k_contract(Geo g, const cplx<R>* __restrict__ A, const R* __rest
   for (int p = 0; p < N; ++p) out[(size_t)p * n + t] = mk<R>(ns[(2 * p) * T + tid], ns[(2 * p + 1) * T + tid]);
 }
 
+// K3 for N <= 8: the same contraction with every operand in registers
+// (compile-time N) and the reduced coupling matrix read from shared memory
+// as a broadcast.  One thread per (j, t).
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __restrict__ A,
+                                                      const R* __restrict__ V, const R* __restrict__ Gm,
+                                                      cplx<R>* __restrict__ NL, const LoopState* __restrict__ ls) {
+  constexpr int K = N * (N + 1) / 2;
+  constexpr int KK = MODE == 2 ? 2 * K : K;
+  __shared__ R Gs[K * KK];
+  for (int i = threadIdx.x; i < K * KK; i += blockDim.x) Gs[i] = Gm[i];
+  __syncthreads();
+  const int n = g.n;
+  const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= (size_t)(g.M + 1) * n) return;
+  const int j = (int)(pt / n), t = (int)(pt - (size_t)j * n);
+  if (ls->iter > 0 && j == 0) return;
+  const cplx<R>* a = A + (size_t)j * N * n + t;
+  cplx<R> av[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) av[l] = a[(size_t)l * n];
+  R v[KK];
+  if (MODE == 0) {
+    int k = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m)
+#pragma unroll
+      for (int q = m; q < N; ++q, ++k)
+        v[k] = (m == q) ? av[m].x * av[m].x + av[m].y * av[m].y
+                        : (R)2 * (av[m].x * av[q].x + av[m].y * av[q].y);
+  } else {
+    const R* vp = V + (size_t)j * KK * n + t;
+#pragma unroll
+    for (int k = 0; k < KK; ++k) v[k] = vp[(size_t)k * n];
+  }
+  cplx<R> nl[N];
+#pragma unroll
+  for (int p = 0; p < N; ++p) nl[p] = mk<R>(0, 0);
+  int r = 0;
+#pragma unroll
+  for (int p = 0; p < N; ++p)
+#pragma unroll
+    for (int l = p; l < N; ++l, ++r) {
+      R acc = (R)0;
+#pragma unroll
+      for (int k = 0; k < KK; ++k) acc += Gs[r * KK + k] * v[k];
+      nl[p].x += av[l].x * acc;
+      nl[p].y += av[l].y * acc;
+      if (l != p) {
+        nl[l].x += av[p].x * acc;
+        nl[l].y += av[p].y * acc;
+      }
+    }
+  cplx<R>* out = NL + (size_t)j * N * n + t;
+#pragma unroll
+  for (int p = 0; p < N; ++p) out[(size_t)p * n] = nl[p];
+}
+
 // ---------------------------------------------------------------------------
 // K4: I_j(w) = i gamma0 s(w) F{NL_p}(w) exp(-i beta j dz)   (Eq. MPA_eq)
-// grid (N, M+1)
+// grid (N, M+1); fac[q] = gamma0 (1 + w_q/omega0) (or gamma0 without
+// self-steepening), tabulated in FP64 and rounded once.
 // ---------------------------------------------------------------------------
 template <typename R, int EPT>
-__global__ void __launch_bounds__(1024) k_integrand(Geo g, const cplx<R>* __restrict__ NL,
-                                                    const cplx<R>* __restrict__ E, cplx<R>* __restrict__ I,
+__global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restrict__ NL,
+                                                    const cplx<R>* __restrict__ E, const R* __restrict__ fac,
+                                                    cplx<R>* __restrict__ I,
                                                     const cplx<R>* __restrict__ tw,
                                                     const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -236,7 +293,7 @@ __global__ void __launch_bounds__(1024) k_integrand(Geo g, const cplx<R>* __rest
   const cplx<R>* e = E + off;
   auto load = [&](int t) { return src[t]; };
   auto store = [&](int q, cplx<R> X) {
-    const R f = (R)(g.ss ? g.gamma0 * (1.0 + omega_of(q, n, g.dt) / g.omega0) : g.gamma0);
+    const R f = fac[q];  // gamma0 s(w_q)
     const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
     I[off + q] = cmulc<R>(iX, e[q]);
   };
@@ -246,10 +303,11 @@ __global__ void __launch_bounds__(1024) k_integrand(Geo g, const cplx<R>* __rest
 // ---------------------------------------------------------------------------
 // K5: trapezoid over z' and the convergence sums (Sec. III.D)
 //   dpsi_j <- (dz/2) sum_{k=1..j} (I_{k-1} + I_k),
-//   diff += |new - old|^2, nrm += |psi0 + new|^2 over j, p, w (FP64).
+//   diff += |new - old|^2, nrm += |psi0 + new|^2 over j, p, w: the terms of
+//   one element in the working precision, the sums over elements in FP64.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __restrict__ psi0,
+__global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __restrict__ psiR,
                                                     cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
                                                     LoopState* ls) {
   __shared__ double red[32];
@@ -260,19 +318,23 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const double2* __rest
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
     cplx<R> Ip = I[e];
     cplx<R> acc = mk<R>(0, 0);
-    const double2 p0 = psi0[e];
+    const cplx<R> p0 = psiR[e];
+    R dsum = 0, nsum = 0;  // this element's terms in the working precision
+#pragma unroll 4
     for (int j = 1; j <= g.M; ++j) {
       const cplx<R> Ij = I[(size_t)j * Nn + e];
       acc = cadd<R>(acc, cscale<R>(cadd<R>(Ip, Ij), hdz));
       Ip = Ij;
       cplx<R>* slot = dpsi + (size_t)(j - 1) * Nn + e;
       const cplx<R> old = iter > 0 ? *slot : mk<R>(0, 0);
-      const double dx = (double)acc.x - (double)old.x, dy = (double)acc.y - (double)old.y;
-      diff += dx * dx + dy * dy;
-      const double px = p0.x + (double)acc.x, py = p0.y + (double)acc.y;
-      nrm += px * px + py * py;
+      const R dx = acc.x - old.x, dy = acc.y - old.y;
+      dsum += dx * dx + dy * dy;
+      const R px = p0.x + acc.x, py = p0.y + acc.y;
+      nsum += px * px + py * py;
       *slot = acc;
     }
+    diff += (double)dsum;  // sums over elements in FP64
+    nrm += (double)nsum;
   }
   diff = block_sum(diff, red);
   nrm = block_sum(nrm, red);
@@ -320,7 +382,7 @@ static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int
 // in FP64; becomes the next psi0.  Skipped when the long step failed.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0,
+__global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0, cplx<R>* psiR,
                                                  const cplx<R>* __restrict__ dpsi,
                                                  const double2* __restrict__ EM, const LoopState* ls) {
   const size_t Nn = (size_t)g.N * g.n;
@@ -331,8 +393,17 @@ __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ ps
     const cplx<R> dd = d[e];
     const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
     const double2 w = EM[e];
-    psi0[e] = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
+    const double2 v = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
+    psi0[e] = v;
+    if ((const void*)psiR != (const void*)psi0) psiR[e] = mk<R>((R)v.x, (R)v.y);
   }
+}
+
+// psiR = psi0 rounded to the working precision (start of a propagation).
+template <typename R>
+__global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restrict__ psiR, size_t count) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    psiR[e] = mk<R>((R)psi0[e].x, (R)psi0[e].y);
 }
 
 // Long-step bookkeeping after K6 (one thread) and the outer while-node
@@ -364,7 +435,7 @@ static __global__ void k_step_begin(cudaGraphConditionalHandle h) {
 // ---------------------------------------------------------------------------
 // out_p = scale * DFT_DIR(in_p) for each mode row p (grid N), n <= 8192.
 template <int DIR, int EPT>
-__global__ void __launch_bounds__(1024) k_fft64_rows(const double2* __restrict__ in, double2* __restrict__ out,
+__global__ void __launch_bounds__(512) k_fft64_rows(const double2* __restrict__ in, double2* __restrict__ out,
                                                      int n, double scale, const double2* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* sm = reinterpret_cast<double2*>(smraw);
@@ -377,7 +448,7 @@ __global__ void __launch_bounds__(1024) k_fft64_rows(const double2* __restrict__
 // Half-length transforms of the even and odd samples (for n = 16384 in FP64):
 // out[2][rows][n/2]; blockIdx.y selects even (0) / odd (1).
 template <int DIR, int EPT>
-__global__ void __launch_bounds__(1024) k_fft64_halves(const double2* __restrict__ in, double2* __restrict__ out,
+__global__ void __launch_bounds__(512) k_fft64_halves(const double2* __restrict__ in, double2* __restrict__ out,
                                                        int n, const double2* __restrict__ tw_half) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* sm = reinterpret_cast<double2*>(smraw);

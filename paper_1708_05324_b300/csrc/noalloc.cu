@@ -95,6 +95,7 @@ struct Carve {
 
 struct Work {
   double2* psi0;
+  void* psiR;
   void *dpsi, *A, *NL, *I, *E, *V;
   double2 *EM64, *io;
   int* flag;
@@ -106,6 +107,7 @@ template <typename R> static size_t layout(const gmmnlse_ctx* c, int M, unsigned
   Carve cv;
   cv.base = base;
   w->psi0 = cv.take<double2>(Nn);
+  w->psiR = c->fp64 ? (void*)w->psi0 : (void*)cv.take<cplx<R>>(Nn);
   w->dpsi = cv.take<cplx<R>>((size_t)M * Nn);
   w->A = cv.take<cplx<R>>((size_t)(M + 1) * Nn);
   w->NL = cv.take<cplx<R>>((size_t)(M + 1) * Nn);
@@ -167,7 +169,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
   layout<R>(c, M, base, &w);
   cudaStream_t s = c->stream;
   const size_t Nn = (size_t)c->N * c->n;
-  const int n = c->n, N = c->N, T = n / EPT, CT = c->contract_threads;
+  const int n = c->n, N = c->N, T = n / EPT;
   const size_t sm = fft_bytes<R>(n);
   const cplx<R>* tw = twiddles<R>(c);
 
@@ -179,6 +181,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
   CKN(cudaStreamSynchronize(s));
   if (hflag) return GMMNLSE_E_INVALID;
   fft64_noalloc(c, w.io + Nn, w.io, w.psi0, +1, 1.0, s);
+  if (!c->fp64) k_round_psi<R><<<blocks_for(Nn), 256, 0, s>>>(w.psi0, (cplx<R>*)w.psiR, Nn);
   k_phase_tables<R><<<blocks_for((size_t)(M + 1) * Nn), 256, 0, s>>>(c->beta, (int)Nn, M, dz, Mrem,
                                                                        (cplx<R>*)w.E, w.EM64);
   // every field of the loop state starts from these values (the scratch
@@ -208,24 +211,24 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
     g.fR = c->fR; g.gamma0 = c->gamma0; g.omega0 = c->omega0; g.dt = c->prm.dt; g.hdz = 0.5 * dz;
     const dim3 gridNM(N, Mj + 1);
     for (;;) {
-      k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, w.psi0, (const cplx<R>*)w.dpsi, (const cplx<R>*)w.E,
-                                                  (cplx<R>*)w.A, tw, w.ls);
+      k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
+                                                  (const cplx<R>*)w.E, (cplx<R>*)w.A, tw, w.ls);
       if (c->raman_mode)
         k_pairs_raman<R, EPT><<<dim3((c->K + 1) / 2, Mj + 1), T, sm, s>>>(
             g, (const cplx<R>*)w.A, (R*)w.V, (const cplx<R>*)c->H, tw, c->pairs, w.ls);
-      k_contract<R><<<(unsigned)(((size_t)(Mj + 1) * n + CT - 1) / CT), CT, c->contract_smem, s>>>(
-          g, (const cplx<R>*)w.A, (const R*)w.V, (const R*)c->G, c->rows, c->pairs, (cplx<R>*)w.NL, w.ls);
-      k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.NL, (const cplx<R>*)w.E, (cplx<R>*)w.I, tw,
-                                                w.ls);
-      k_trapz_norm<R><<<blocks_for(Nn), 256, 0, s>>>(g, w.psi0, (cplx<R>*)w.dpsi, (const cplx<R>*)w.I, w.ls);
+      launch_contract<R>(g, c, w.A, w.V, w.NL, w.ls, s);
+      k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.NL, (const cplx<R>*)w.E, (const R*)c->fac,
+                                                (cplx<R>*)w.I, tw, w.ls);
+      k_trapz_norm<R><<<blocks_for(Nn), 256, 0, s>>>(g, (const cplx<R>*)w.psiR, (cplx<R>*)w.dpsi,
+                                                     (const cplx<R>*)w.I, w.ls);
       k_decide<<<1, 32, 0, s>>>(w.ls, 0, 0);
       CKN(cudaGetLastError());
       CKN(cudaMemcpyAsync(&hs, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
       CKN(cudaStreamSynchronize(s));
       if (hs.done) break;
     }
-    k_advance<R><<<blocks_for(Nn), 256, 0, s>>>(g, w.psi0, (const cplx<R>*)w.dpsi, w.EM64 + (size_t)which * Nn,
-                                               w.ls);
+    k_advance<R><<<blocks_for(Nn), 256, 0, s>>>(g, w.psi0, (cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
+                                               w.EM64 + (size_t)which * Nn, w.ls);
     k_step_end<<<1, 32, 0, s>>>(w.ls, 0, 0);
     CKN(cudaGetLastError());
     CKN(cudaMemcpyAsync(&hs, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
