@@ -172,7 +172,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-run", action="store_true",
-                    help="only the timed propagations and the per-kernel profile (for ncu captures)")
+                    help="only the timed propagations (for ncu captures)")
+    ap.add_argument("--kernel-profile", action="store_true",
+                    help="with --profile-run: also time each kernel of one iteration")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -242,11 +244,15 @@ def main():
     value = u * args.steps * world / dev_s
 
     if args.profile_run:
-        prof = ctx.profile(prob.M, reps=5)
+        line = {"profile_run": True, "precision": args.precision, "length_m": args.length,
+                "ms_per_step": 1e3 * dev_s / args.steps, "value": value,
+                "iters_total": stats[-1]["iters_total"], "long_steps": stats[-1]["long_steps"]}
+        if args.kernel_profile:
+            prof = ctx.profile(prob.M, reps=20)
+            line["kernels_ms"] = {k: v[0] for k, v in prof.items()}
+            line["kernels_bytes"] = {k: v[1] for k, v in prof.items()}
         if rank == 0:
-            print(json.dumps({"profile_run": True, "ms_per_step": 1e3 * dev_s / args.steps,
-                              "kernels_ms": {k: v[0] for k, v in prof.items()},
-                              "kernels_bytes": {k: v[1] for k, v in prof.items()}}))
+            print(json.dumps(line))
         ctx.close()
         if dist:
             dist.destroy_process_group()

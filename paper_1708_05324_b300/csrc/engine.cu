@@ -96,24 +96,23 @@ static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* o
   return GMMNLSE_OK;
 }
 
+// The dynamic shared-memory limit is a property of each kernel function on
+// the device, shared by every context, so it is raised once to the device's
+// opt-in maximum (this reserves nothing; each launch asks for what it uses).
 template <typename R> static int set_smem_attrs(gmmnlse_ctx* c) {
-  const int n = c->n;
-  const int sm = (int)fft_smem<R>(n);
-  if (c->ept == 16) {
-    CK(cudaFuncSetAttribute(k_ip_to_time<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CK(cudaFuncSetAttribute(k_integrand<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  } else {
-    CK(cudaFuncSetAttribute(k_ip_to_time<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CK(cudaFuncSetAttribute(k_integrand<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  }
-  CK(cudaFuncSetAttribute(k_contract<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->contract_smem));
-  const int sm64 = (int)fft_smem<double>(std::min(n, 8192));
-  CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
-  CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
-  CK(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
-  CK(cudaFuncSetAttribute(k_fft64_halves<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64));
+  int sm = 0;
+  CK(cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->prm.device));
+  CK(cudaFuncSetAttribute(k_ip_to_time<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_integrand<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_ip_to_time<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_integrand<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_contract<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fft64_halves<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   return GMMNLSE_OK;
 }
 

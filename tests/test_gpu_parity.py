@@ -101,6 +101,19 @@ def test_modes_raman_and_steepening_variants(N, fR, ss, split, precision):
         assert st["iters_total"] == sum(sref["iters"])
 
 
+@pytest.mark.parametrize("N", [10, 15])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_generic_contraction_path_many_modes(N, precision):
+    """N > 8 takes the shared-memory contraction kernel (mode groups 0-3 and
+    0-4 of the GRIN fiber, as in the 15-mode workload)."""
+    key = ("m", N, 256, 0.18)
+    prob = small(*key)
+    ref, _ = oracle_small(key)
+    out, st, rc = gpu_run(prob, precision, tol=1e-13 if precision == "fp64" else 1e-9)
+    assert rc == B.OK
+    assert rel(out, ref) < TOL[precision]
+
+
 def test_ragged_last_long_step_and_M1():
     key = ("p", 3, 128, 0.18)
     prob = small(*key)
