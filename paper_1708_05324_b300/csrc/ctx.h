@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "../../include/gmmnlse.h"
@@ -67,14 +68,42 @@ struct gmmnlse_ctx {
 
 
 // ---------------------------------------------------------------------------
+// Launch as a programmatic dependent of the previous kernel in the stream
+// (kernels start with pdl_enter), unless GMMNLSE_NO_PDL=1.
+// ---------------------------------------------------------------------------
+static inline bool pdl_disabled() {
+  static const bool off = [] {
+    const char* v = getenv("GMMNLSE_NO_PDL");
+    return v && v[0] == '1';
+  }();
+  return off;
+}
+
+template <typename... KArgs, typename... Args>
+static inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_disabled() ? 0 : 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// ---------------------------------------------------------------------------
 // Coupling contraction launch: registers for N <= 8, shared memory otherwise
 // ---------------------------------------------------------------------------
 template <typename R, int N, int MODE>
 static inline void launch_contract_reg(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V,
                                        void* NL, const gm::LoopState* ls, cudaStream_t s) {
   const size_t pts = (size_t)(g.M + 1) * g.n;
-  gm::k_contract_reg<R, N, MODE><<<(unsigned)((pts + 255) / 256), 256, 0, s>>>(
-      g, (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (gm::cplx<R>*)NL, ls);
+  pdl_launch(gm::k_contract_reg<R, N, MODE>, dim3((unsigned)((pts + 255) / 256)), dim3(256), 0, s, g,
+             (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (gm::cplx<R>*)NL, ls);
 }
 
 template <typename R, int N>
@@ -100,8 +129,9 @@ static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const
     default: {
       const int CT = c->contract_threads;
       const size_t pts = (size_t)(g.M + 1) * g.n;
-      gm::k_contract<R><<<(unsigned)((pts + CT - 1) / CT), CT, c->contract_smem, s>>>(
-          g, (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, c->rows, c->pairs, (gm::cplx<R>*)NL, ls);
+      pdl_launch(gm::k_contract<R>, dim3((unsigned)((pts + CT - 1) / CT)), dim3(CT), c->contract_smem, s, g,
+                 (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (const int2*)c->rows, (const int2*)c->pairs,
+                 (gm::cplx<R>*)NL, ls);
     }
   }
 }

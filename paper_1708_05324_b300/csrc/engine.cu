@@ -99,21 +99,15 @@ static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* o
 // The dynamic shared-memory limit is a property of each kernel function on
 // the device, shared by every context, so it is raised once to the device's
 // opt-in maximum (this reserves nothing; each launch asks for what it uses).
-template <typename R> static int set_smem_attrs(gmmnlse_ctx* c) {
+// The iteration kernels are set up by their own translation units.
+static int set_smem_attrs(gmmnlse_ctx* c) {
   int sm = 0;
   CK(cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->prm.device));
-  CK(cudaFuncSetAttribute(k_ip_to_time<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_integrand<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_ip_to_time<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_integrand<R, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_contract<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft64_halves<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  return GMMNLSE_OK;
+  return c->fp64 ? gm_prop_setup_f64(c->prm.device) : gm_prop_setup_f32(c->prm.device);
 }
 
 // ---------------------------------------------------------------------------
@@ -309,7 +303,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   CKC(cudaMalloc(&c->pairs, c->K * sizeof(int2)));
   CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
   rc = fp64 ? upload_tables<double>(c, Gd) : upload_tables<float>(c, Gd);
-  if (!rc) rc = fp64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
+  if (!rc) rc = set_smem_attrs(c);
   if (!rc) rc = fp64 ? compute_H<double>(c, hR) : compute_H<float>(c, hR);
   if (rc) {
     free_ctx(c);
@@ -421,173 +415,6 @@ void gm_job_destroy(gm_job* jb) { free_job(jb); }
 // ---------------------------------------------------------------------------
 // Kernel chain of one iteration and the long-step driver
 // ---------------------------------------------------------------------------
-template <typename R>
-static Geo make_geo(const gmmnlse_ctx* c, int Mj, double dz) {
-  Geo g;
-  g.N = c->N;
-  g.n = c->n;
-  g.K = c->K;
-  g.P = c->P;
-  g.KK = c->KK;
-  g.M = Mj;
-  g.raman_mode = c->raman_mode;
-  g.ss = c->prm.self_steepening ? 1 : 0;
-  g.fR = c->fR;
-  g.gamma0 = c->gamma0;
-  g.omega0 = c->omega0;
-  g.dt = c->prm.dt;
-  g.hdz = 0.5 * dz;
-  return g;
-}
-
-template <typename R> static const cplx<R>* twid(const gmmnlse_ctx* c);
-template <> const cplx<float>* twid<float>(const gmmnlse_ctx* c) { return c->tw32; }
-template <> const cplx<double>* twid<double>(const gmmnlse_ctx* c) { return c->tw64; }
-
-static int elementwise_blocks(size_t count) {
-  const size_t b = (count + 255) / 256;
-  return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
-}
-
-template <typename R, int EPT>
-static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
-  gmmnlse_ctx* c = jb->ctx;
-  const int n = c->n, N = c->N, Mj = g.M;
-  const size_t sm = fft_smem<R>(n);
-  const int T = n / EPT;
-  const cplx<R>* tw = twid<R>(c);
-  dim3 gridNM(N, Mj + 1);
-  k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
-                                              (const cplx<R>*)jb->E, (cplx<R>*)jb->A, tw, jb->ls);
-  if (c->raman_mode) {
-    dim3 gridK((c->K + 1) / 2, Mj + 1);
-    k_pairs_raman<R, EPT><<<gridK, T, sm, s>>>(g, (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, tw,
-                                               c->pairs, jb->ls);
-  }
-  launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
-  k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E, (const R*)c->fac,
-                                            (cplx<R>*)jb->I, tw, jb->ls);
-  k_trapz_norm<R><<<elementwise_blocks((size_t)N * n), 256, 0, s>>>(g, (const cplx<R>*)jb->psiR,
-                                                                    (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I,
-                                                                    jb->ls);
-  k_decide<<<1, 32, 0, s>>>(jb->ls, h, use_cond);
-}
-
-template <typename R>
-static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle h,
-                           int use_cond) {
-  gmmnlse_ctx* c = jb->ctx;
-  const size_t Nn = (size_t)c->N * c->n;
-  k_advance<R><<<elementwise_blocks(Nn), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
-                                                      jb->EM64 + (size_t)which * Nn, jb->ls);
-  k_step_end<<<1, 32, 0, s>>>(jb->ls, h, use_cond);
-}
-
-template <typename R, int EPT>
-static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
-  cudaStream_t cs = jb->cap;
-  cudaGraph_t root = nullptr;
-  CK(cudaGraphCreate(&root, 0));
-  cudaGraphConditionalHandle hStep, hIter;
-  CK(cudaGraphConditionalHandleCreate(&hStep, root, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = hStep;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t nStep;
-  CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
-  cudaGraph_t gS = cp.conditional.phGraph_out[0];
-  CK(cudaGraphConditionalHandleCreate(&hIter, gS, 0, 0));
-  // long-step body: re-arm the iteration loop
-  CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  k_step_begin<<<1, 32, 0, cs>>>(hIter);
-  CK(cudaStreamEndCapture(cs, &gS));
-  cudaGraphNode_t nBegin;
-  size_t cnt = 1;
-  CK(cudaGraphGetNodes(gS, &nBegin, &cnt));
-  cudaGraphNodeParams ci = {};
-  ci.type = cudaGraphNodeTypeConditional;
-  ci.conditional.handle = hIter;
-  ci.conditional.type = cudaGraphCondTypeWhile;
-  ci.conditional.size = 1;
-  cudaGraphNode_t nIter;
-  CK(cudaGraphAddNode(&nIter, gS, &nBegin, nullptr, 1, &ci));
-  cudaGraph_t gI = ci.conditional.phGraph_out[0];
-  // iteration body: K1..K5
-  CK(cudaStreamBeginCaptureToGraph(cs, gI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  launch_iteration<R, EPT>(jb, g, cs, hIter, 1);
-  CK(cudaStreamEndCapture(cs, &gI));
-  // after the loop: K6
-  CK(cudaStreamBeginCaptureToGraph(cs, gS, &nIter, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-  launch_advance<R>(jb, g, which, cs, hStep, 1);
-  CK(cudaStreamEndCapture(cs, &gS));
-  cudaGraphExec_t exec = nullptr;
-  CK(cudaGraphInstantiate(&exec, root, 0));
-  out.graph = root;
-  out.exec = exec;
-  out.Mj = g.M;
-  out.which = which;
-  return GMMNLSE_OK;
-}
-
-static bool graphs_disabled() {
-  const char* v = getenv("GMMNLSE_NO_GRAPH");
-  return v && v[0] == '1';
-}
-
-// Run `count` long steps of Mj substeps starting from the current psi0.
-template <typename R, int EPT>
-static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, cudaStream_t s) {
-  if (count <= 0) return GMMNLSE_OK;
-  const Geo g = make_geo<R>(jb->ctx, Mj, dz);
-  // the step target for this launch
-  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (jb->h_ls->status != ST_OK) return GMMNLSE_OK;
-  const int target = jb->h_ls->step + count;
-  CK(cudaMemcpyAsync(&jb->ls->nsteps, &target, sizeof(int), cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));
-  if (!graphs_disabled()) {
-    gm_job::G* gr = nullptr;
-    for (auto& x : jb->graphs)
-      if (x.exec && x.Mj == Mj && x.which == which) gr = &x;
-    if (!gr) {
-      gm_job::G& slot = jb->graphs[which];
-      if (slot.exec) {
-        cudaGraphExecDestroy(slot.exec);
-        cudaGraphDestroy(slot.graph);
-        slot = gm_job::G();
-      }
-      if (build_graph<R, EPT>(jb, g, which, slot) == GMMNLSE_OK) gr = &slot;
-      else {
-        cudaGetLastError();
-        if (getenv("GMMNLSE_VERBOSE")) fprintf(stderr, "gmmnlse: graph build failed, host loop\n");
-      }
-    }
-    if (gr) {
-      CK(cudaGraphLaunch(gr->exec, s));
-      return GMMNLSE_OK;
-    }
-  }
-  // host-driven loop over the same kernels
-  for (int st = 0; st < count; ++st) {
-    for (;;) {
-      launch_iteration<R, EPT>(jb, g, s, 0, 0);
-      CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (jb->h_ls->done) break;
-    }
-    launch_advance<R>(jb, g, which, s, 0, 0);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (jb->h_ls->status != ST_OK) break;
-  }
-  return GMMNLSE_OK;
-}
-
 // Substep schedule: round(L/dz) substeps of dz, long steps of M, remainder last.
 int gm_schedule(double L, double dz, int M, long* nfull, int* Mrem) {
   if (!(L > 0) || !(dz > 0) || M < 1 || M > kMaxM || !std::isfinite(L) || !std::isfinite(dz))
@@ -601,195 +428,12 @@ int gm_schedule(double L, double dz, int M, long* nfull, int* Mrem) {
   return GMMNLSE_OK;
 }
 
-template <typename R, int EPT>
-static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
-                          double* Aout, gmmnlse_stats* st, cudaStream_t s) {
-  gmmnlse_ctx* c = jb->ctx;
-  long nfull = 0;
-  int Mrem = 0;
-  int rc = gm_schedule(L, dz, M, &nfull, &Mrem);
-  if (rc) return rc;
-  if (!(tol >= 0) || !std::isfinite(tol)) return GMMNLSE_E_INVALID;
-  const size_t Nn = (size_t)c->N * c->n;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, s));
-  // input: time-domain FP64 field -> io[0]
-  double2* tin = jb->io;
-  if (dev_io) {
-    CK(cudaMemcpyAsync(tin, A0, Nn * 16, cudaMemcpyDeviceToDevice, s));
-  } else {
-    std::memcpy(jb->h_io, A0, Nn * 16);
-    CK(cudaMemcpyAsync(tin, jb->h_io, Nn * 16, cudaMemcpyHostToDevice, s));
-  }
-  CK(cudaMemsetAsync(jb->flag, 0, sizeof(int), s));
-  k_nonfinite<<<elementwise_blocks(Nn), 256, 0, s>>>(tin, Nn, jb->flag);
-  int hflag = 0;
-  CK(cudaMemcpyAsync(&hflag, jb->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (hflag) {
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return GMMNLSE_E_INVALID;
-  }
-  // psi0 = F{A0} (FP64)
-  rc = fft64(c, jb->io + Nn, tin, jb->psi0, c->N, +1, 1.0, s);
-  if (rc) return rc;
-  if (!c->fp64) k_round_psi<R><<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, (cplx<R>*)jb->psiR, Nn);
-  // phase tables for (dz, M, Mrem)
-  if (jb->tab_dz != dz || jb->tab_M != M || jb->tab_Mrem != Mrem) {
-    k_phase_tables<R><<<elementwise_blocks((size_t)(M + 1) * Nn), 256, 0, s>>>(
-        c->beta, (int)Nn, M, dz, Mrem, (cplx<R>*)jb->E, jb->EM64);
-    CK(cudaGetLastError());
-    jb->tab_dz = dz;
-    jb->tab_M = M;
-    jb->tab_Mrem = Mrem;
-  }
-  // loop state
-  LoopState h = {};
-  h.tol = tol;
-  h.floor_eps = c->fp64 ? 1e-14 : (c->prm.precision == GMMNLSE_FP32 ? 1e-6 : 1e-5);
-  h.max_iter = c->prm.max_iter > 0 ? c->prm.max_iter : 50;
-  h.fixed_iters = c->prm.fixed_iters;
-  h.prev_eps = INFINITY;
-  h.iters_min = 1 << 30;
-  h.status = ST_OK;
-  *jb->h_ls = h;
-  CK(cudaMemcpyAsync(jb->ls, jb->h_ls, sizeof(LoopState), cudaMemcpyHostToDevice, s));
-  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0, jb->ls->spec);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(s));
-  rc = run_long_steps<R, EPT>(jb, M, 0, dz, (int)nfull, s);
-  if (rc) return rc;
-  if (Mrem > 0) {
-    rc = run_long_steps<R, EPT>(jb, Mrem, 1, dz, 1, s);
-    if (rc) return rc;
-  }
-  // output sums and Aout = F^-1{psi0}
-  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0,
-                                                     jb->ls->spec + 2);
-  rc = fft64(c, jb->io + Nn, jb->psi0, jb->io, c->N, -1, 1.0 / c->n, s);
-  if (rc) return rc;
-  if (dev_io) {
-    CK(cudaMemcpyAsync(Aout, jb->io, Nn * 16, cudaMemcpyDeviceToDevice, s));
-  } else {
-    CK(cudaMemcpyAsync(jb->h_io, jb->io, Nn * 16, cudaMemcpyDeviceToHost, s));
-  }
-  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
-  CK(cudaEventRecord(e1, s));
-  CK(cudaStreamSynchronize(s));
-  if (!dev_io) std::memcpy(Aout, jb->h_io, Nn * 16);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  const LoopState& hs = *jb->h_ls;
-  if (st) {
-    std::memset(st, 0, sizeof(*st));
-    st->long_steps = hs.step;
-    const long done = (hs.step <= nfull) ? (long)hs.step * M : nfull * M + Mrem;
-    st->z = (double)done * dz;
-    st->iters_total = hs.iters_total;
-    st->iters_min = hs.step > 0 ? hs.iters_min : 0;
-    st->iters_max = hs.iters_max;
-    std::memcpy(st->iter_hist, hs.hist, sizeof(st->iter_hist));
-    st->eps_max = hs.eps_max;
-    st->eps_last = hs.eps;
-    st->energy_in = hs.spec[0] * c->prm.dt / c->n;
-    st->photons_in = hs.spec[1];
-    st->energy_out = hs.spec[2] * c->prm.dt / c->n;
-    st->photons_out = hs.spec[3];
-    st->ms = ms;
-  }
-  if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
-  if (hs.status == ST_NONFINITE) return GMMNLSE_E_NONFINITE;
-  return GMMNLSE_OK;
-}
-
 int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
                      double* Aout, gmmnlse_stats* st, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   if (M > jb->Mcap) return GMMNLSE_E_INVALID;
-  if (c->fp64) {
-    return c->ept == 16 ? propagate_impl<double, 16>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
-                        : propagate_impl<double, 32>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
-  }
-  return c->ept == 16 ? propagate_impl<float, 16>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
-                      : propagate_impl<float, 32>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
-}
-
-// ---------------------------------------------------------------------------
-// Per-kernel timing of one MPA iteration (used for the roofline report)
-// ---------------------------------------------------------------------------
-template <typename R, int EPT>
-static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes) {
-  cudaStream_t s = c->stream;
-  const double dz = jb->tab_dz > 0 ? jb->tab_dz : 1e-5;
-  const Geo g = make_geo<R>(c, M, dz);
-  const double rs = sizeof(R), cs = 2 * rs;
-  const double Nn = (double)c->N * c->n;
-  // algorithmic bytes per launch of an iteration (substeps j = 1..M)
-  bytes[0] = M * Nn * 4 * cs;                     // psiR, dpsi, E -> A
-  bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->KK * c->n * rs) : 0.0;
-  bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->KK * rs : 0.0));
-  bytes[3] = M * Nn * 3 * cs + c->n * rs;         // NL, E -> I; prefactor table
-  bytes[4] = Nn * ((M + 1) * cs + 2 * M * cs + cs); // I, dpsi old/new, psiR
-  bytes[5] = Nn * (16 + cs + 16 + 16 + (c->fp64 ? 0 : cs));
-  cudaEvent_t a, b;
-  CK(cudaEventCreate(&a));
-  CK(cudaEventCreate(&b));
-  const int one = 1;
-  const size_t Nsz = (size_t)c->N * c->n;
-  const int n = c->n, T = n / EPT;
-  const size_t sm = fft_smem<R>(n);
-  const cplx<R>* tw = twid<R>(c);
-  dim3 gridNM(c->N, M + 1);
-  for (int k = 0; k < 6; ++k) {
-    ms[k] = 0.0;
-    if (k == 1 && !c->raman_mode) continue;
-    // iteration state: iter = 1 (substeps 1..M, the shape of every iteration after the first)
-    CK(cudaMemcpyAsync(&jb->ls->iter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
-    for (int r = -1; r < reps; ++r) {
-      if (r == 0) CK(cudaEventRecord(a, s));  // reps launches back to back after one warm-up
-      switch (k) {
-        case 0:
-          k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
-                                                      (const cplx<R>*)jb->E, (cplx<R>*)jb->A, tw, jb->ls);
-          break;
-        case 1:
-          k_pairs_raman<R, EPT><<<dim3((c->K + 1) / 2, M + 1), T, sm, s>>>(
-              g, (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, tw, c->pairs, jb->ls);
-          break;
-        case 2:
-          launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
-          break;
-        case 3:
-          k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E,
-                                                    (const R*)c->fac, (cplx<R>*)jb->I, tw, jb->ls);
-          break;
-        case 4:
-          k_trapz_norm<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, (const cplx<R>*)jb->psiR,
-                                                                  (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I,
-                                                                  jb->ls);
-          break;
-        default:
-          k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR,
-                                                               (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls);
-          break;
-      }
-      CK(cudaGetLastError());
-    }
-    CK(cudaEventRecord(b, s));
-    CK(cudaEventSynchronize(b));
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, a, b));
-    ms[k] = t / reps;
-  }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  return GMMNLSE_OK;
+  return c->fp64 ? gm_propagate_f64(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
+                 : gm_propagate_f32(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
 }
 
 extern "C" int gmmnlse_profile(gmmnlse_ctx* c, int M, int reps, double* ms, double* bytes) {
@@ -798,10 +442,7 @@ extern "C" int gmmnlse_profile(gmmnlse_ctx* c, int M, int reps, double* ms, doub
   int rc = set_device(c->prm.device);
   if (rc) return rc;
   if (!c->job || c->job->Mcap < M || c->job->tab_M < M) return GMMNLSE_E_INVALID;
-  if (c->fp64) return c->ept == 16 ? profile_impl<double, 16>(c, c->job, M, reps, ms, bytes)
-                                   : profile_impl<double, 32>(c, c->job, M, reps, ms, bytes);
-  return c->ept == 16 ? profile_impl<float, 16>(c, c->job, M, reps, ms, bytes)
-                      : profile_impl<float, 32>(c, c->job, M, reps, ms, bytes);
+  return c->fp64 ? gm_profile_f64(c, c->job, M, reps, ms, bytes) : gm_profile_f32(c, c->job, M, reps, ms, bytes);
 }
 
 int gm_ctx_device(const gmmnlse_ctx* c) { return c->prm.device; }

@@ -14,6 +14,14 @@ void gm_job_destroy(gm_job* jb);
 int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
                      double* Aout, gmmnlse_stats* st, cudaStream_t s);
 int gm_schedule(double L, double dz, int M, long* nfull, int* Mrem);
+int gm_propagate_f32(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                     double* Aout, gmmnlse_stats* st, cudaStream_t s);
+int gm_propagate_f64(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                     double* Aout, gmmnlse_stats* st, cudaStream_t s);
+int gm_profile_f32(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes);
+int gm_profile_f64(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes);
+int gm_prop_setup_f32(int device);
+int gm_prop_setup_f64(int device);
 int gm_ctx_device(const gmmnlse_ctx* c);
 int gm_ctx_modes(const gmmnlse_ctx* c);
 int gm_ctx_samples(const gmmnlse_ctx* c);

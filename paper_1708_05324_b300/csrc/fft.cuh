@@ -139,7 +139,7 @@ template <typename R, int DIR> struct Dft<R, DIR, 16> {
 // of the pass do not depend on the data, so they are issued first and their
 // latency overlaps the data reads and the barrier.
 template <typename R, int DIR, int RAD, int EPT, bool FIRST, bool LAST, class Load, class Store>
-__device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<R>* __restrict__ tw,
+__device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<R>* __restrict__ tw, int tws,
                                          const Load& load, const Store& store) {
   constexpr int B = EPT / RAD;  // butterflies per thread
   constexpr int NW = RAD == 16 ? 4 : RAD - 1;  // table reads per butterfly
@@ -150,7 +150,7 @@ __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = threadIdx.x + b * T;
-      const int step = (j & (Ns - 1)) * (n / (Ns * RAD));
+      const int step = (j & (Ns - 1)) * (n / (Ns * RAD)) * tws;
       if (RAD == 16) {
         wt[b][0] = tw[step];
         wt[b][1] = tw[2 * step];
@@ -216,10 +216,11 @@ __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<
 }
 
 // Full transform: load(i) gives input element i (natural order), store(i, x)
-// takes output element i.  Starts with a barrier, so the buffer may have been
-// used just before by the same block.
+// takes output element i.  tw is the table exp(-2 pi i m / (n tws)); tws > 1
+// uses every tws-th entry of a longer table.  Starts with a barrier, so the
+// buffer may have been used just before by the same block.
 template <typename R, int DIR, int EPT, class Load, class Store>
-__device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __restrict__ tw,
+__device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __restrict__ tw, int tws,
                                           const Load& load, const Store& store) {
   __syncthreads();
   const int logn = 31 - __clz(n);
@@ -231,26 +232,73 @@ __device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __r
   if (lead) {
     const bool last = (passes == 1);
     if (lead == 1) {
-      if (last) fft_pass<R, DIR, 2, EPT, true, true>(sm, n, Ns, tw, load, store);
-      else fft_pass<R, DIR, 2, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+      if (last) fft_pass<R, DIR, 2, EPT, true, true>(sm, n, Ns, tw, tws, load, store);
+      else fft_pass<R, DIR, 2, EPT, true, false>(sm, n, Ns, tw, tws, load, no_store);
     } else if (lead == 2) {
-      if (last) fft_pass<R, DIR, 4, EPT, true, true>(sm, n, Ns, tw, load, store);
-      else fft_pass<R, DIR, 4, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+      if (last) fft_pass<R, DIR, 4, EPT, true, true>(sm, n, Ns, tw, tws, load, store);
+      else fft_pass<R, DIR, 4, EPT, true, false>(sm, n, Ns, tw, tws, load, no_store);
     } else {
-      if (last) fft_pass<R, DIR, 8, EPT, true, true>(sm, n, Ns, tw, load, store);
-      else fft_pass<R, DIR, 8, EPT, true, false>(sm, n, Ns, tw, load, no_store);
+      if (last) fft_pass<R, DIR, 8, EPT, true, true>(sm, n, Ns, tw, tws, load, store);
+      else fft_pass<R, DIR, 8, EPT, true, false>(sm, n, Ns, tw, tws, load, no_store);
     }
     Ns <<= lead;
     ++p;
   }
   for (; p < passes; ++p) {
     const bool first = (p == 0), last = (p == passes - 1);
-    if (first && last) fft_pass<R, DIR, 16, EPT, true, true>(sm, n, Ns, tw, load, store);
-    else if (first) fft_pass<R, DIR, 16, EPT, true, false>(sm, n, Ns, tw, load, no_store);
-    else if (last) fft_pass<R, DIR, 16, EPT, false, true>(sm, n, Ns, tw, no_load, store);
-    else fft_pass<R, DIR, 16, EPT, false, false>(sm, n, Ns, tw, no_load, no_store);
+    if (first && last) fft_pass<R, DIR, 16, EPT, true, true>(sm, n, Ns, tw, tws, load, store);
+    else if (first) fft_pass<R, DIR, 16, EPT, true, false>(sm, n, Ns, tw, tws, load, no_store);
+    else if (last) fft_pass<R, DIR, 16, EPT, false, true>(sm, n, Ns, tw, tws, no_load, store);
+    else fft_pass<R, DIR, 16, EPT, false, false>(sm, n, Ns, tw, tws, no_load, no_store);
     Ns <<= 4;
   }
+}
+
+template <typename R, int DIR, int EPT, class Load, class Store>
+__device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __restrict__ tw, const Load& load,
+                                          const Store& store) {
+  fft_block<R, DIR, EPT>(sm, n, tw, 1, load, store);
+}
+
+// Output-residue split of an n-point transform over S blocks (radix-S
+// decimation in frequency): block s (0 <= s < S) computes X[S k + s],
+// k < n/S, as the (n/S)-point transform of
+//   y_s[t] = W^{DIR t s} sum_{u<S} x[t + u n/S] W_S^{DIR u s},  W = exp(2 pi i / n).
+// Each block reads all n inputs; no data moves between blocks.  tw is the
+// n-point table.  S = 1 is the plain transform.
+template <typename R, int DIR, int EPT, int S, class Load, class Store>
+__device__ __forceinline__ void fft_block_split(cplx<R>* sm, int n, int s, const cplx<R>* __restrict__ tw,
+                                                const Load& load, const Store& store) {
+  if (S == 1) {
+    fft_block<R, DIR, EPT>(sm, n, tw, 1, load, store);
+    return;
+  }
+  const int np = n / S;
+  auto load_s = [&](int t) {
+    cplx<R> acc = load(t);
+    if (S == 2) {
+      const cplx<R> b = load(t + np);
+      acc = s ? csub<R>(acc, b) : cadd<R>(acc, b);
+    } else {  // S == 4: W_4^{DIR u s} = (DIR i)^{u s}
+      const cplx<R> b = load(t + np), c = load(t + 2 * np), d = load(t + 3 * np);
+      const cplx<R> ac = cadd<R>(acc, c), amc = csub<R>(acc, c);
+      const cplx<R> bd = cadd<R>(b, d), ibmd = mul_i<R, DIR>(csub<R>(b, d));
+      switch (s) {
+        case 0: acc = cadd<R>(ac, bd); break;
+        case 1: acc = cadd<R>(amc, ibmd); break;
+        case 2: acc = csub<R>(ac, bd); break;
+        default: acc = csub<R>(amc, ibmd); break;
+      }
+    }
+    if (s) {
+      cplx<R> w = tw[t * s];
+      if (DIR > 0) w.y = -w.y;
+      acc = cmul<R>(acc, w);
+    }
+    return acc;
+  };
+  auto store_s = [&](int k, cplx<R> v) { store(S * k + s, v); };
+  fft_block<R, DIR, EPT>(sm, np, tw, S, load_s, store_s);
 }
 
 }  // namespace gm

@@ -14,6 +14,8 @@
 // long step: I_0 does not change while psi_j, j >= 1, is iterated.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -46,6 +48,15 @@ struct Geo {
   double fR, gamma0, omega0, dt, hdz;  // hdz = dz / 2
 };
 
+// Programmatic dependent launch: let the next kernel in the stream start
+// launching now, then wait until every kernel this one depends on has
+// finished and its writes are visible.  Both are no-ops for a kernel that
+// was not launched as a programmatic dependent.
+__device__ __forceinline__ void pdl_enter() {
+  cudaTriggerProgrammaticLaunchCompletion();
+  cudaGridDependencySynchronize();
+}
+
 __device__ __forceinline__ double omega_of(int q, int n, double dt) {
   const int s = (q < n / 2) ? q : q - n;
   return 2.0 * 3.14159265358979323846 * (double)s / ((double)n * dt);
@@ -74,9 +85,10 @@ __global__ void k_phase_tables(const double* __restrict__ beta, int Nn, int M, d
 }
 
 // ---------------------------------------------------------------------------
-// K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N, M+1)
+// K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N S, M+1): block
+// x = p S + s computes the output residue class s mod S (fft_block_split).
 // ---------------------------------------------------------------------------
-template <typename R, int EPT>
+template <typename R, int EPT, int S>
 __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __restrict__ psiR,
                                                      const cplx<R>* __restrict__ dpsi,
                                                      const cplx<R>* __restrict__ E, cplx<R>* __restrict__ A,
@@ -84,7 +96,8 @@ __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __rest
                                                      const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
-  const int p = blockIdx.x, j = blockIdx.y;
+  pdl_enter();
+  const int p = blockIdx.x / S, sp = blockIdx.x % S, j = blockIdx.y;
   const int iter = ls->iter;
   if (iter > 0 && j == 0) return;
   const int n = g.n;
@@ -99,7 +112,7 @@ __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __rest
     return cmul<R>(x, e[q]);
   };
   auto store = [&](int t, cplx<R> v) { A[off + t] = cscale<R>(v, inv_n); };
-  fft_block<R, -1, EPT>(sm, n, tw, load, store);
+  fft_block_split<R, -1, EPT, S>(sm, n, sp, tw, load, store);
 }
 
 // U_k(t): |A_m|^2 for m == n, 2 Re(A_m A_n^*) for m < n (pairs k = (m <= n))
@@ -125,6 +138,7 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
                                                       const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  pdl_enter();
   const int j = blockIdx.y;
   if (ls->iter > 0 && j == 0) return;
   const int n = g.n;
@@ -158,6 +172,74 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
   fft_block<R, +1, EPT>(sm, n, tw, from_smem, store);
 }
 
+// K2 on a 2-block cluster: block s does the even (s = 0) or odd (s = 1)
+// half of the spectrum.  Forward: Y_s[k] = X[2k + s] by the radix-2
+// decimation-in-frequency split; times H[2k + s]; inverse n/2-point
+// transform z_s.  The inverse of the full spectrum is the radix-2
+// decimation-in-time combination x[t' + s n/2] = z_0[t'] + (-1)^s W^{t'} z_1[t']
+// (W = exp(2 pi i / n)), for which block s reads its partner's z through
+// distributed shared memory.  grid (2 ceil(K/2), M+1).
+template <typename R, int EPT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
+    k_pairs_raman_cl(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V, const cplx<R>* __restrict__ H,
+                     const cplx<R>* __restrict__ tw, const int2* __restrict__ pairs,
+                     const LoopState* __restrict__ ls) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  cg::cluster_group cluster = cg::this_cluster();
+  pdl_enter();
+  const int j = blockIdx.y;
+  if (ls->iter > 0 && j == 0) return;  // the same for both blocks of a cluster
+  const int s = (int)cluster.block_rank();
+  const int n = g.n, np = n / 2;
+  const int k1 = 2 * (blockIdx.x / 2), k2 = k1 + 1;
+  const bool has2 = k2 < g.K;
+  const int2 mn1 = pairs[k1];
+  const int2 mn2 = has2 ? pairs[k2] : mn1;
+  const cplx<R>* a = A + (size_t)j * g.N * n;
+  auto x_at = [&](int t) {
+    return mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+  };
+  auto load = [&](int t) {
+    const cplx<R> u = x_at(t), w = x_at(t + np);
+    cplx<R> y = s ? csub<R>(u, w) : cadd<R>(u, w);
+    if (s) y = cmul<R>(y, tw[t]);  // W^{-t} for the forward (DIR = -1) transform
+    return y;
+  };
+  auto to_smem = [&](int k, cplx<R> y) { sm[pad16(k)] = cmul<R>(y, H[2 * k + s]); };
+  fft_block<R, -1, EPT>(sm, np, tw, 2, load, to_smem);
+  auto from_smem = [&](int k) { return sm[pad16(k)]; };
+  auto keep = [&](int t, cplx<R> z) { sm[pad16(t)] = z; };
+  fft_block<R, +1, EPT>(sm, np, tw, 2, from_smem, keep);
+  cluster.sync();  // both halves z_0, z_1 complete and visible in the cluster
+  const cplx<R>* z0 = cluster.map_shared_rank(sm, 0);
+  const cplx<R>* z1 = cluster.map_shared_rank(sm, 1);
+  R* v = V + (size_t)j * g.KK * n;
+  const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
+  for (int tp = threadIdx.x; tp < np; tp += blockDim.x) {
+    cplx<R> w = tw[tp];
+    w.y = -w.y;  // W^{+t'}
+    cplx<R> z = cmul<R>(w, z1[pad16(tp)]);
+    if (s) z = mk<R>(-z.x, -z.y);
+    const cplx<R> y = cadd<R>(z0[pad16(tp)], z);
+    const int t = tp + s * np;
+    const R u1 = pair_product<R>(a, n, mn1, t);
+    if (g.raman_mode == 1) {
+      v[(size_t)k1 * n + t] = fK * u1 + fR * y.x;
+      if (has2) v[(size_t)k2 * n + t] = fK * pair_product<R>(a, n, mn2, t) + fR * y.y;
+    } else {
+      v[(size_t)k1 * n + t] = u1;
+      v[(size_t)(g.K + k1) * n + t] = y.x;
+      if (has2) {
+        v[(size_t)k2 * n + t] = pair_product<R>(a, n, mn2, t);
+        v[(size_t)(g.K + k2) * n + t] = y.y;
+      }
+    }
+  }
+  cluster.sync();  // the partner may still be reading this block's z
+}
+
 // ---------------------------------------------------------------------------
 // K3: NL_p(t) = sum_l A_l R_pl, R_pl = sum_k G[(p,l)][k] V_k  (Eq. 1 bracket,
 // symmetry-reduced: rows (p <= l), columns (m <= n) or [U; h*U]).
@@ -178,6 +260,7 @@ __global__ void k_contract(Geo g, const cplx<R>* __restrict__ A, const R* __rest
   R* ns = vs + KK * T;                         // [2N][T]
   for (int i = tid; i < P * KK; i += T) Gs[i] = Gm[i];
   for (int i = tid; i < P; i += T) rs[i] = rows[i];
+  pdl_enter();
   __syncthreads();
   const size_t pt = (size_t)blockIdx.x * T + tid;
   const size_t npts = (size_t)(g.M + 1) * n;
@@ -225,6 +308,7 @@ __global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __re
   constexpr int KK = MODE == 2 ? 2 * K : K;
   __shared__ R Gs[K * KK];
   for (int i = threadIdx.x; i < K * KK; i += blockDim.x) Gs[i] = Gm[i];
+  pdl_enter();
   __syncthreads();
   const int n = g.n;
   const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,10 +358,10 @@ __global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __re
 
 // ---------------------------------------------------------------------------
 // K4: I_j(w) = i gamma0 s(w) F{NL_p}(w) exp(-i beta j dz)   (Eq. MPA_eq)
-// grid (N, M+1); fac[q] = gamma0 (1 + w_q/omega0) (or gamma0 without
+// grid (N S, M+1) as K1; fac[q] = gamma0 (1 + w_q/omega0) (or gamma0 without
 // self-steepening), tabulated in FP64 and rounded once.
 // ---------------------------------------------------------------------------
-template <typename R, int EPT>
+template <typename R, int EPT, int S>
 __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restrict__ NL,
                                                     const cplx<R>* __restrict__ E, const R* __restrict__ fac,
                                                     cplx<R>* __restrict__ I,
@@ -285,7 +369,8 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
                                                     const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
-  const int p = blockIdx.x, j = blockIdx.y;
+  pdl_enter();
+  const int p = blockIdx.x / S, sp = blockIdx.x % S, j = blockIdx.y;
   if (ls->iter > 0 && j == 0) return;
   const int n = g.n;
   const size_t off = ((size_t)j * g.N + p) * n;
@@ -297,7 +382,7 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
     const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
     I[off + q] = cmulc<R>(iX, e[q]);
   };
-  fft_block<R, +1, EPT>(sm, n, tw, load, store);
+  fft_block_split<R, +1, EPT, S>(sm, n, sp, tw, load, store);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,6 +396,7 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __rest
                                                     cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
                                                     LoopState* ls) {
   __shared__ double red[32];
+  pdl_enter();
   const size_t Nn = (size_t)g.N * g.n;
   const int iter = ls->iter;
   double diff = 0.0, nrm = 0.0;
@@ -348,6 +434,7 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __rest
 // sums, and the while-node condition when running inside a graph.  Every
 // path ends the loop after at most max_iter (or fixed_iters) updates.
 static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double diff = ls->diff, nrm = ls->nrm;
   const bool finite = isfinite(diff) && isfinite(nrm);
@@ -385,6 +472,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0, cplx<R>* psiR,
                                                  const cplx<R>* __restrict__ dpsi,
                                                  const double2* __restrict__ EM, const LoopState* ls) {
+  pdl_enter();
   const size_t Nn = (size_t)g.N * g.n;
   if (ls->status != ST_OK) return;
   const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
@@ -409,6 +497,7 @@ __global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restric
 // Long-step bookkeeping after K6 (one thread) and the outer while-node
 // condition: continue while the step succeeded and steps remain.
 static __global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int status = ls->status, it = ls->iter;
   if (status == ST_OK) {

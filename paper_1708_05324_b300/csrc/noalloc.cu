@@ -50,9 +50,9 @@ static unsigned char* g_scratch_addr[kMaxDevices];  // device address per device
 template <typename R> static size_t fft_bytes(int n) { return (size_t)fft_smem_elems(n) * sizeof(cplx<R>); }
 
 template <typename R, int EPT> static int set_attrs(int maxsm) {
-  CKN(cudaFuncSetAttribute(k_ip_to_time<R, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  CKN(cudaFuncSetAttribute(k_ip_to_time<R, EPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
   CKN(cudaFuncSetAttribute(k_pairs_raman<R, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-  CKN(cudaFuncSetAttribute(k_integrand<R, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  CKN(cudaFuncSetAttribute(k_integrand<R, EPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
   return GMMNLSE_OK;
 }
 
@@ -211,13 +211,13 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
     g.fR = c->fR; g.gamma0 = c->gamma0; g.omega0 = c->omega0; g.dt = c->prm.dt; g.hdz = 0.5 * dz;
     const dim3 gridNM(N, Mj + 1);
     for (;;) {
-      k_ip_to_time<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
+      k_ip_to_time<R, EPT, 1><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
                                                   (const cplx<R>*)w.E, (cplx<R>*)w.A, tw, w.ls);
       if (c->raman_mode)
         k_pairs_raman<R, EPT><<<dim3((c->K + 1) / 2, Mj + 1), T, sm, s>>>(
             g, (const cplx<R>*)w.A, (R*)w.V, (const cplx<R>*)c->H, tw, c->pairs, w.ls);
       launch_contract<R>(g, c, w.A, w.V, w.NL, w.ls, s);
-      k_integrand<R, EPT><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.NL, (const cplx<R>*)w.E, (const R*)c->fac,
+      k_integrand<R, EPT, 1><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.NL, (const cplx<R>*)w.E, (const R*)c->fac,
                                                 (cplx<R>*)w.I, tw, w.ls);
       k_trapz_norm<R><<<blocks_for(Nn), 256, 0, s>>>(g, (const cplx<R>*)w.psiR, (cplx<R>*)w.dpsi,
                                                      (const cplx<R>*)w.I, w.ls);

@@ -1,0 +1,13 @@
+// MPA long-step driver instantiated for float iterates.
+#include "prop_impl.cuh"
+
+int gm_propagate_f32(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                     double* Aout, gmmnlse_stats* st, cudaStream_t s) {
+  return gm_prop::propagate_impl<float>(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
+}
+
+int gm_profile_f32(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes) {
+  return gm_prop::profile_impl<float>(c, jb, M, reps, ms, bytes);
+}
+
+int gm_prop_setup_f32(int device) { return gm_prop::setup_device<float>(device); }

@@ -1,0 +1,489 @@
+// Templated host driver of the MPA long steps (Sec. III.D) for one working
+// precision R; instantiated once per precision (prop_fp32.cu, prop_fp64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/gmmnlse.h"
+#include "ctx.h"
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace gm_prop {
+
+using namespace gm;
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) {                                            \
+      gm_set_last_cuda_error(e_, #call, __FILE__, __LINE__);            \
+      return GMMNLSE_E_CUDA;                                            \
+    }                                                                   \
+  } while (0)
+
+template <typename R> static size_t fft_smem(int n) { return (size_t)fft_smem_elems(n) * sizeof(cplx<R>); }
+
+// FP64 transforms of the N rows of a [N][n] field (input / output of a call).
+static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* out, int rows, int dir,
+                 double scale, cudaStream_t s) {
+  const int n = c->n;
+  if (n <= 8192) {
+    const size_t sm = fft_smem<double>(n);
+    if (dir > 0) k_fft64_rows<+1, 16><<<rows, n / 16, sm, s>>>(in, out, n, scale, c->tw64);
+    else k_fft64_rows<-1, 16><<<rows, n / 16, sm, s>>>(in, out, n, scale, c->tw64);
+  } else {
+    const int h = n / 2;
+    const size_t sm = fft_smem<double>(h);
+    dim3 grid(rows, 2);
+    if (dir > 0) {
+      k_fft64_halves<+1, 16><<<grid, h / 16, sm, s>>>(in, scratch, n, c->tw64h);
+      k_fft64_combine<+1><<<(rows * n + 255) / 256, 256, 0, s>>>(scratch, out, rows, n, scale, c->tw64);
+    } else {
+      k_fft64_halves<-1, 16><<<grid, h / 16, sm, s>>>(in, scratch, n, c->tw64h);
+      k_fft64_combine<-1><<<(rows * n + 255) / 256, 256, 0, s>>>(scratch, out, rows, n, scale, c->tw64);
+    }
+  }
+  CK(cudaGetLastError());
+  return GMMNLSE_OK;
+}
+
+// Once per device: raise the shared-memory limit of this unit's kernels.
+template <typename R>
+static int setup_device(int dev) {
+  static std::mutex mu;
+  static bool done[64];
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64) return GMMNLSE_E_INVALID;
+  if (done[dev]) return GMMNLSE_OK;
+  int sm = 0;
+  CK(cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  CK(cudaFuncSetAttribute(k_ip_to_time<R, 16, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_ip_to_time<R, 16, 2>, A, sm));
+  CK(cudaFuncSetAttribute(k_ip_to_time<R, 16, 4>, A, sm));
+  CK(cudaFuncSetAttribute(k_ip_to_time<R, 32, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_integrand<R, 16, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_integrand<R, 16, 2>, A, sm));
+  CK(cudaFuncSetAttribute(k_integrand<R, 16, 4>, A, sm));
+  CK(cudaFuncSetAttribute(k_integrand<R, 32, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract<R>, A, sm));
+  CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, A, sm));
+  CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, A, sm));
+  CK(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, A, sm));
+  CK(cudaFuncSetAttribute(k_fft64_halves<-1, 16>, A, sm));
+  done[dev] = true;
+  return GMMNLSE_OK;
+}
+
+// Blocks per transform for K1/K4 (output-residue split) so that a launch
+// fills the 148 SMs: 1, 2 or 4.
+// GMMNLSE_UNSPLIT=1 selects the one-block-per-transform kernels everywhere
+// (the same arithmetic; used to test both variants).
+static inline bool unsplit_forced() {
+  const char* v = getenv("GMMNLSE_UNSPLIT");
+  return v && v[0] == '1';
+}
+
+static inline int split_for(int transforms, int n) {
+  if (unsplit_forced()) return 1;
+  // only for launches far too small to fill the GPU: each split block reads
+  // the whole input, so for larger launches one block per transform is faster
+  if (transforms < 16 && n >= 128) return 4;
+  if (transforms < 32 && n >= 64) return 2;
+  return 1;
+}
+
+template <typename R>
+static Geo make_geo(const gmmnlse_ctx* c, int Mj, double dz) {
+  Geo g;
+  g.N = c->N;
+  g.n = c->n;
+  g.K = c->K;
+  g.P = c->P;
+  g.KK = c->KK;
+  g.M = Mj;
+  g.raman_mode = c->raman_mode;
+  g.ss = c->prm.self_steepening ? 1 : 0;
+  g.fR = c->fR;
+  g.gamma0 = c->gamma0;
+  g.omega0 = c->omega0;
+  g.dt = c->prm.dt;
+  g.hdz = 0.5 * dz;
+  return g;
+}
+
+template <typename R> static const cplx<R>* twid(const gmmnlse_ctx* c);
+template <> const cplx<float>* twid<float>(const gmmnlse_ctx* c) { return c->tw32; }
+template <> const cplx<double>* twid<double>(const gmmnlse_ctx* c) { return c->tw64; }
+
+static int elementwise_blocks(size_t count) {
+  const size_t b = (count + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
+}
+
+// K1: phase x inverse FFT, split over S blocks per transform
+template <typename R>
+static void launch_k1(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n, N = c->N;
+  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = np > 8192 ? 32 : 16;
+  const dim3 grid(N * S, g.M + 1);
+  const size_t sm = fft_smem<R>(np);
+  auto args = [&](auto kern) {
+    pdl_launch(kern, grid, dim3(np / ept), sm, s, g, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
+               (const cplx<R>*)jb->E, (cplx<R>*)jb->A, twid<R>(c), (const LoopState*)jb->ls);
+  };
+  if (ept == 32) args(k_ip_to_time<R, 32, 1>);
+  else if (S == 1) args(k_ip_to_time<R, 16, 1>);
+  else if (S == 2) args(k_ip_to_time<R, 16, 2>);
+  else args(k_ip_to_time<R, 16, 4>);
+}
+
+// K2: pair products + Raman convolution; a 2-block cluster per transform
+// pair when one block per pair would leave SMs idle
+template <typename R>
+static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n;
+  const int pp = (c->K + 1) / 2;
+  const bool cl = n >= 64 && pp * (g.M + 1) < 32 && !unsplit_forced();
+  if (cl) {
+    const int np = n / 2;
+    pdl_launch(k_pairs_raman_cl<R, 16>, dim3(2 * pp, g.M + 1), dim3(np / 16), fft_smem<R>(np), s, g,
+               (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
+               (const LoopState*)jb->ls);
+  } else if (n > 8192) {
+    pdl_launch(k_pairs_raman<R, 32>, dim3(pp, g.M + 1), dim3(n / 32), fft_smem<R>(n), s, g,
+               (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
+               (const LoopState*)jb->ls);
+  } else {
+    pdl_launch(k_pairs_raman<R, 16>, dim3(pp, g.M + 1), dim3(n / 16), fft_smem<R>(n), s, g,
+               (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
+               (const LoopState*)jb->ls);
+  }
+}
+
+// K4: forward FFT x integrand prefactor, split as K1
+template <typename R>
+static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n, N = c->N;
+  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = np > 8192 ? 32 : 16;
+  const dim3 grid(N * S, g.M + 1);
+  const size_t sm = fft_smem<R>(np);
+  auto args = [&](auto kern) {
+    pdl_launch(kern, grid, dim3(np / ept), sm, s, g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E,
+               (const R*)c->fac, (cplx<R>*)jb->I, twid<R>(c), (const LoopState*)jb->ls);
+  };
+  if (ept == 32) args(k_integrand<R, 32, 1>);
+  else if (S == 1) args(k_integrand<R, 16, 1>);
+  else if (S == 2) args(k_integrand<R, 16, 2>);
+  else args(k_integrand<R, 16, 4>);
+}
+
+template <typename R>
+static void launch_k5(gm_job* jb, const Geo& g, cudaStream_t s) {
+  const size_t Nn = (size_t)jb->ctx->N * jb->ctx->n;
+  pdl_launch(k_trapz_norm<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, (const cplx<R>*)jb->psiR,
+             (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I, jb->ls);
+}
+
+template <typename R>
+static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  gmmnlse_ctx* c = jb->ctx;
+  launch_k1<R>(jb, g, s);
+  if (c->raman_mode) launch_k2<R>(jb, g, s);
+  launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+  launch_k4<R>(jb, g, s);
+  launch_k5<R>(jb, g, s);
+  pdl_launch(k_decide, dim3(1), dim3(32), 0, s, jb->ls, h, use_cond);
+}
+
+template <typename R>
+static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle h,
+                           int use_cond) {
+  gmmnlse_ctx* c = jb->ctx;
+  const size_t Nn = (size_t)c->N * c->n;
+  pdl_launch(k_advance<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, jb->psi0, (cplx<R>*)jb->psiR,
+             (const cplx<R>*)jb->dpsi, (const double2*)(jb->EM64 + (size_t)which * Nn), (const LoopState*)jb->ls);
+  pdl_launch(k_step_end, dim3(1), dim3(32), 0, s, jb->ls, h, use_cond);
+}
+
+template <typename R>
+static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
+  cudaStream_t cs = jb->cap;
+  cudaGraph_t root = nullptr;
+  CK(cudaGraphCreate(&root, 0));
+  cudaGraphConditionalHandle hStep, hIter;
+  CK(cudaGraphConditionalHandleCreate(&hStep, root, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hStep;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t nStep;
+  CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
+  cudaGraph_t gS = cp.conditional.phGraph_out[0];
+  CK(cudaGraphConditionalHandleCreate(&hIter, gS, 0, 0));
+  // long-step body: re-arm the iteration loop
+  CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  k_step_begin<<<1, 32, 0, cs>>>(hIter);
+  CK(cudaStreamEndCapture(cs, &gS));
+  cudaGraphNode_t nBegin;
+  size_t cnt = 1;
+  CK(cudaGraphGetNodes(gS, &nBegin, &cnt));
+  cudaGraphNodeParams ci = {};
+  ci.type = cudaGraphNodeTypeConditional;
+  ci.conditional.handle = hIter;
+  ci.conditional.type = cudaGraphCondTypeWhile;
+  ci.conditional.size = 1;
+  cudaGraphNode_t nIter;
+  CK(cudaGraphAddNode(&nIter, gS, &nBegin, nullptr, 1, &ci));
+  cudaGraph_t gI = ci.conditional.phGraph_out[0];
+  // iteration body: K1..K5
+  CK(cudaStreamBeginCaptureToGraph(cs, gI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_iteration<R>(jb, g, cs, hIter, 1);
+  CK(cudaStreamEndCapture(cs, &gI));
+  // after the loop: K6
+  CK(cudaStreamBeginCaptureToGraph(cs, gS, &nIter, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  launch_advance<R>(jb, g, which, cs, hStep, 1);
+  CK(cudaStreamEndCapture(cs, &gS));
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphInstantiate(&exec, root, 0));
+  out.graph = root;
+  out.exec = exec;
+  out.Mj = g.M;
+  out.which = which;
+  return GMMNLSE_OK;
+}
+
+static bool graphs_disabled() {
+  const char* v = getenv("GMMNLSE_NO_GRAPH");
+  return v && v[0] == '1';
+}
+
+// Run `count` long steps of Mj substeps starting from the current psi0.
+template <typename R>
+static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, cudaStream_t s) {
+  if (count <= 0) return GMMNLSE_OK;
+  const Geo g = make_geo<R>(jb->ctx, Mj, dz);
+  // the step target for this launch
+  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (jb->h_ls->status != ST_OK) return GMMNLSE_OK;
+  const int target = jb->h_ls->step + count;
+  CK(cudaMemcpyAsync(&jb->ls->nsteps, &target, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (!graphs_disabled()) {
+    gm_job::G* gr = nullptr;
+    for (auto& x : jb->graphs)
+      if (x.exec && x.Mj == Mj && x.which == which) gr = &x;
+    if (!gr) {
+      gm_job::G& slot = jb->graphs[which];
+      if (slot.exec) {
+        cudaGraphExecDestroy(slot.exec);
+        cudaGraphDestroy(slot.graph);
+        slot = gm_job::G();
+      }
+      if (build_graph<R>(jb, g, which, slot) == GMMNLSE_OK) gr = &slot;
+      else {
+        cudaGetLastError();
+        if (getenv("GMMNLSE_VERBOSE")) fprintf(stderr, "gmmnlse: graph build failed, host loop\n");
+      }
+    }
+    if (gr) {
+      CK(cudaGraphLaunch(gr->exec, s));
+      return GMMNLSE_OK;
+    }
+  }
+  // host-driven loop over the same kernels
+  for (int st = 0; st < count; ++st) {
+    for (;;) {
+      launch_iteration<R>(jb, g, s, 0, 0);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (jb->h_ls->done) break;
+    }
+    launch_advance<R>(jb, g, which, s, 0, 0);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (jb->h_ls->status != ST_OK) break;
+  }
+  return GMMNLSE_OK;
+}
+
+template <typename R>
+static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
+                          double* Aout, gmmnlse_stats* st, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  long nfull = 0;
+  int Mrem = 0;
+  int rc = gm_schedule(L, dz, M, &nfull, &Mrem);
+  if (rc) return rc;
+  if (!(tol >= 0) || !std::isfinite(tol)) return GMMNLSE_E_INVALID;
+  const size_t Nn = (size_t)c->N * c->n;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // input: time-domain FP64 field -> io[0]
+  double2* tin = jb->io;
+  if (dev_io) {
+    CK(cudaMemcpyAsync(tin, A0, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::memcpy(jb->h_io, A0, Nn * 16);
+    CK(cudaMemcpyAsync(tin, jb->h_io, Nn * 16, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(jb->flag, 0, sizeof(int), s));
+  k_nonfinite<<<elementwise_blocks(Nn), 256, 0, s>>>(tin, Nn, jb->flag);
+  int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, jb->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hflag) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GMMNLSE_E_INVALID;
+  }
+  // psi0 = F{A0} (FP64)
+  rc = fft64(c, jb->io + Nn, tin, jb->psi0, c->N, +1, 1.0, s);
+  if (rc) return rc;
+  if (!c->fp64) k_round_psi<R><<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, (cplx<R>*)jb->psiR, Nn);
+  // phase tables for (dz, M, Mrem)
+  if (jb->tab_dz != dz || jb->tab_M != M || jb->tab_Mrem != Mrem) {
+    k_phase_tables<R><<<elementwise_blocks((size_t)(M + 1) * Nn), 256, 0, s>>>(
+        c->beta, (int)Nn, M, dz, Mrem, (cplx<R>*)jb->E, jb->EM64);
+    CK(cudaGetLastError());
+    jb->tab_dz = dz;
+    jb->tab_M = M;
+    jb->tab_Mrem = Mrem;
+  }
+  // loop state
+  LoopState h = {};
+  h.tol = tol;
+  h.floor_eps = c->fp64 ? 1e-14 : (c->prm.precision == GMMNLSE_FP32 ? 1e-6 : 1e-5);
+  h.max_iter = c->prm.max_iter > 0 ? c->prm.max_iter : 50;
+  h.fixed_iters = c->prm.fixed_iters;
+  h.prev_eps = INFINITY;
+  h.iters_min = 1 << 30;
+  h.status = ST_OK;
+  *jb->h_ls = h;
+  CK(cudaMemcpyAsync(jb->ls, jb->h_ls, sizeof(LoopState), cudaMemcpyHostToDevice, s));
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0, jb->ls->spec);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  rc = run_long_steps<R>(jb, M, 0, dz, (int)nfull, s);
+  if (rc) return rc;
+  if (Mrem > 0) {
+    rc = run_long_steps<R>(jb, Mrem, 1, dz, 1, s);
+    if (rc) return rc;
+  }
+  // output sums and Aout = F^-1{psi0}
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0,
+                                                     jb->ls->spec + 2);
+  rc = fft64(c, jb->io + Nn, jb->psi0, jb->io, c->N, -1, 1.0 / c->n, s);
+  if (rc) return rc;
+  if (dev_io) {
+    CK(cudaMemcpyAsync(Aout, jb->io, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(jb->h_io, jb->io, Nn * 16, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  if (!dev_io) std::memcpy(Aout, jb->h_io, Nn * 16);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const LoopState& hs = *jb->h_ls;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->long_steps = hs.step;
+    const long done = (hs.step <= nfull) ? (long)hs.step * M : nfull * M + Mrem;
+    st->z = (double)done * dz;
+    st->iters_total = hs.iters_total;
+    st->iters_min = hs.step > 0 ? hs.iters_min : 0;
+    st->iters_max = hs.iters_max;
+    std::memcpy(st->iter_hist, hs.hist, sizeof(st->iter_hist));
+    st->eps_max = hs.eps_max;
+    st->eps_last = hs.eps;
+    st->energy_in = hs.spec[0] * c->prm.dt / c->n;
+    st->photons_in = hs.spec[1];
+    st->energy_out = hs.spec[2] * c->prm.dt / c->n;
+    st->photons_out = hs.spec[3];
+    st->ms = ms;
+  }
+  if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
+  if (hs.status == ST_NONFINITE) return GMMNLSE_E_NONFINITE;
+  return GMMNLSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Per-kernel timing of one MPA iteration (used for the roofline report)
+// ---------------------------------------------------------------------------
+template <typename R>
+static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes) {
+  cudaStream_t s = c->stream;
+  const double dz = jb->tab_dz > 0 ? jb->tab_dz : 1e-5;
+  const Geo g = make_geo<R>(c, M, dz);
+  const double rs = sizeof(R), cs = 2 * rs;
+  const double Nn = (double)c->N * c->n;
+  // algorithmic bytes per launch of an iteration (substeps j = 1..M)
+  bytes[0] = M * Nn * 4 * cs;                     // psiR, dpsi, E -> A
+  bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->KK * c->n * rs) : 0.0;
+  bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->KK * rs : 0.0));
+  bytes[3] = M * Nn * 3 * cs + c->n * rs;         // NL, E -> I; prefactor table
+  bytes[4] = Nn * ((M + 1) * cs + 2 * M * cs + cs); // I, dpsi old/new, psiR
+  bytes[5] = Nn * (16 + cs + 16 + 16 + (c->fp64 ? 0 : cs));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  const int one = 1;
+  const size_t Nsz = (size_t)c->N * c->n;
+  for (int k = 0; k < 6; ++k) {
+    ms[k] = 0.0;
+    if (k == 1 && !c->raman_mode) continue;
+    // iteration state: iter = 1 (substeps 1..M, the shape of every iteration after the first)
+    CK(cudaMemcpyAsync(&jb->ls->iter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    for (int r = -1; r < reps; ++r) {
+      if (r == 0) CK(cudaEventRecord(a, s));  // reps launches back to back after one warm-up
+      switch (k) {
+        case 0: launch_k1<R>(jb, g, s); break;
+        case 1: launch_k2<R>(jb, g, s); break;
+        case 2: launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s); break;
+        case 3: launch_k4<R>(jb, g, s); break;
+        case 4: launch_k5<R>(jb, g, s); break;
+        default:
+          k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR,
+                                                               (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls);
+          break;
+      }
+      CK(cudaGetLastError());
+    }
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    ms[k] = t / reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return GMMNLSE_OK;
+}
+
+
+}  // namespace gm_prop

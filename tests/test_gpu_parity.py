@@ -75,9 +75,19 @@ def test_linear_propagation_fp64_matches_oracle():
     assert rel(out, ref) < 1e-12
 
 
+@pytest.fixture(params=["split", "unsplit"])
+def fft_variant(request, monkeypatch):
+    """Run with the launch-time choice of kernels (transforms split over 2 or
+    4 blocks, Raman transform pairs on 2-block clusters, when a launch would
+    otherwise leave SMs idle) and with one block per transform everywhere."""
+    if request.param == "unsplit":
+        monkeypatch.setenv("GMMNLSE_UNSPLIT", "1")
+    return request.param
+
+
 @pytest.mark.parametrize("Nt", [16, 32, 64, 128, 1024])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_every_fft_pass_structure(Nt, precision):
+def test_every_fft_pass_structure(Nt, precision, fft_variant):
     """Nt = 16 (one radix-16 pass), 32/64/128 (leading radix 2/4/8), 1024."""
     key = ("p", 3, Nt, 0.18)
     prob = small(*key)
@@ -90,7 +100,7 @@ def test_every_fft_pass_structure(Nt, precision):
 @pytest.mark.parametrize("N,fR,ss,split", [(1, 0.0, 1, False), (1, 0.18, 0, False), (2, 0.18, 1, False),
                                            (4, 0.0, 0, False), (4, 0.18, 1, True), (6, 0.18, 1, False)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_modes_raman_and_steepening_variants(N, fR, ss, split, precision):
+def test_modes_raman_and_steepening_variants(N, fR, ss, split, precision, fft_variant):
     key = ("v", N, 256, fR, ss, 11, 20e-9, split)
     prob = small(*key)
     ref, sref = oracle_small(key)
@@ -127,7 +137,7 @@ def test_ragged_last_long_step_and_M1():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_largest_transform_2_14(precision):
+def test_largest_transform_2_14(precision, fft_variant):
     if precision == "fp64":
         pytest.skip("FP64 iterates are built for Nt <= 8192")
     prob = I.grin_problem("big", N=2, Nt=16384, dt=20e-12 / 16384, kind="gaussian", fwhm=300e-15,
@@ -154,7 +164,7 @@ def test_c2_prefix_fp64():
     assert st["long_steps"] == 4
 
 
-def test_c2_prefix_fp32():
+def test_c2_prefix_fp32(fft_variant):
     prob, ref, sref = c2_prefix()
     out, st, rc = gpu_run(prob, "fp32", tol=1e-8)
     assert rc == B.OK
