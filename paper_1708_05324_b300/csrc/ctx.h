@@ -7,6 +7,9 @@
 #include <cstdlib>
 #include <mutex>
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "../../include/gmmnlse.h"
 #include "kernels.cuh"
 
@@ -42,6 +45,10 @@ struct gm_job {
     cudaGraph_t graph = nullptr;
   } graphs[2];
   size_t bytes = 0;
+  // mixed precision: blocked BF16 hi/lo pair-term operand and its TMA maps
+  __nv_bfloat16* Vhi = nullptr;  // [KKp/8][(M+1) n][8]
+  __nv_bfloat16* Vlo = nullptr;
+  CUtensorMap mapHi, mapLo;
 };
 
 struct gmmnlse_ctx {
@@ -58,6 +65,10 @@ struct gmmnlse_ctx {
   void* G = nullptr;            // [P][KK] R
   int2* rows = nullptr;         // [P]
   int2* pairs = nullptr;        // [K]
+  bool tc = false;               // contraction on tensor cores (mixed precision)
+  int KKp = 0;                   // K padded to a multiple of 16
+  __nv_bfloat16* Ghi = nullptr;  // [KKp/8][128][8]
+  __nv_bfloat16* Glo = nullptr;
   int contract_threads = 128;
   size_t contract_smem = 0;
   cudaStream_t stream = nullptr;

@@ -23,6 +23,7 @@
 #include "engine.h"
 #include "kernels.cuh"
 #include "ctx.h"
+#include "tc_contract.cuh"
 
 using namespace gm;
 
@@ -151,6 +152,8 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->G);
   cudaFree(c->rows);
   cudaFree(c->pairs);
+  cudaFree(c->Ghi);
+  cudaFree(c->Glo);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -215,7 +218,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   if (!symmetric_enough(SK, N) || (SR && !symmetric_enough(SR, N))) return GMMNLSE_E_UNSUPPORTED;
   const bool fp64 = prm->precision == GMMNLSE_FP64;
   if (fp64 && n > 8192) return GMMNLSE_E_UNSUPPORTED;
-  if (prm->precision >= GMMNLSE_MIXED_BF16) return GMMNLSE_E_UNSUPPORTED;  // tensor-core path: see engine_tc
+  if (prm->precision == GMMNLSE_MIXED_FP16) return GMMNLSE_E_UNSUPPORTED;
   int rc = set_device(prm->device);
   if (rc) return rc;
 
@@ -254,6 +257,18 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
         Gd[(size_t)r * c->KK + k] = S_at(SK, p, l, m, q);
       }
     }
+  }
+
+  // mixed precision: the contraction runs on the tensor cores when the
+  // reduced coupling matrix has at most 128 rows and 160 (padded) columns
+  if (prm->precision == GMMNLSE_MIXED_BF16) {
+    const int KKp = (c->KK + 15) / 16 * 16;
+    if (c->P > TC_M || KKp > TC_KMAX || n % TC_BN != 0) {
+      delete c;
+      return GMMNLSE_E_UNSUPPORTED;
+    }
+    c->tc = true;
+    c->KKp = KKp;
   }
 
   // contraction kernel shared memory; shrink the block until it fits
@@ -303,6 +318,26 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   CKC(cudaMalloc(&c->pairs, c->K * sizeof(int2)));
   CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
   rc = fp64 ? upload_tables<double>(c, Gd) : upload_tables<float>(c, Gd);
+  if (!rc && c->tc) {
+    // G split into BF16 hi + lo, blocked [KKp/8][128][8] (K-major core matrices)
+    const int KKp = c->KKp;
+    std::vector<__nv_bfloat16> gh((size_t)TC_M * KKp), gl((size_t)TC_M * KKp);
+    for (int r = 0; r < TC_M; ++r)
+      for (int k = 0; k < KKp; ++k) {
+        const float x = (r < c->P && k < c->KK) ? (float)Gd[(size_t)r * c->KK + k] : 0.f;
+        const size_t o = ((size_t)(k / 8) * TC_M + r) * 8 + (k % 8);
+        gh[o] = __float2bfloat16_rn(x);
+        gl[o] = __float2bfloat16_rn(x - __bfloat162float(gh[o]));
+      }
+    cudaError_t e = cudaMalloc(&c->Ghi, gh.size() * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&c->Glo, gl.size() * 2);
+    if (e == cudaSuccess) e = cudaMemcpy(c->Ghi, gh.data(), gh.size() * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->Glo, gl.data(), gl.size() * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      gm_set_last_cuda_error(e, "coupling matrix upload", __FILE__, __LINE__);
+      rc = GMMNLSE_E_CUDA;
+    }
+  }
   if (!rc) rc = set_smem_attrs(c);
   if (!rc) rc = fp64 ? compute_H<double>(c, hR) : compute_H<float>(c, hR);
   if (rc) {
@@ -342,6 +377,7 @@ static size_t job_bytes(const gmmnlse_ctx* c, int M) {
   if (c->raman_mode) b += (size_t)(M + 1) * c->KK * c->n * rs;  // V
   b += 2 * Nn * 16 * 2;                          // EM64, io
   b += sizeof(LoopState) + 64;
+  if (c->tc) b += (size_t)2 * c->KKp * (M + 1) * c->n * 2;  // BF16 hi/lo operand
   return b;
 }
 
@@ -364,11 +400,50 @@ static void free_job(gm_job* jb) {
   cudaFree(jb->EM64);
   cudaFree(jb->io);
   cudaFree(jb->flag);
+  cudaFree(jb->Vhi);
+  cudaFree(jb->Vlo);
   cudaFree(jb->ls);
   cudaFreeHost(jb->h_ls);
   cudaFreeHost(jb->h_io);
   if (jb->cap) cudaStreamDestroy(jb->cap);
   delete jb;
+}
+
+// TMA maps of the blocked hi/lo operand: dims {8, (M+1) n, KKp/8}, box
+// {8, 128 points, KKp/8}; the encode function comes from the driver at run
+// time (no link dependency on libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
+  static EncodeTiledFn enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess) {
+      gm_set_last_error_text("cuTensorMapEncodeTiled is not available from the driver");
+      return GMMNLSE_E_CUDA;
+    }
+    enc = (EncodeTiledFn)fn;
+  }
+  const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
+  const cuuint64_t dims[3] = {8, npts, (cuuint64_t)(c->KKp / 8)};
+  const cuuint64_t strides[2] = {16, npts * 16};
+  const cuuint32_t box[3] = {8, (cuuint32_t)TC_BN, (cuuint32_t)(c->KKp / 8)};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r1 = enc(&jb->mapHi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, jb->Vhi, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(&jb->mapLo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, jb->Vlo, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+    gm_set_last_error_text("cuTensorMapEncodeTiled rejected the operand layout");
+    return GMMNLSE_E_CUDA;
+  }
+  return GMMNLSE_OK;
 }
 
 int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
@@ -396,6 +471,10 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
   al((void**)&jb->io, 2 * Nn * 16);
   al((void**)&jb->flag, sizeof(int));
   al((void**)&jb->ls, sizeof(LoopState));
+  if (c->tc) {
+    al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * 2);
+    al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * 2);
+  }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_ls, sizeof(LoopState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_io, Nn * 16);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&jb->cap, cudaStreamNonBlocking);
@@ -404,6 +483,13 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
     cudaGetLastError();
     free_job(jb);
     return e == cudaErrorMemoryAllocation ? GMMNLSE_E_NOMEM : GMMNLSE_E_CUDA;
+  }
+  if (c->tc) {
+    const int rc = gm_make_tc_maps(c, jb, M);
+    if (rc) {
+      free_job(jb);
+      return rc;
+    }
   }
   jb->bytes = job_bytes(c, M);
   *out = jb;

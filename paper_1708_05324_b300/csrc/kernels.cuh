@@ -39,6 +39,7 @@ struct LoopState {
   int iters_total, iters_min, iters_max;
   int hist[33];
   double spec[4];          // sum |psi0|^2, photon sum (filled by k_spec_sums)
+  unsigned tc_err;         // a tensor-core contraction wait timed out
 };
 
 struct Geo {

@@ -15,6 +15,9 @@
 #include "ctx.h"
 #include "engine.h"
 #include "kernels.cuh"
+#include "tc_contract.cuh"
+
+#include <type_traits>
 
 namespace gm_prop {
 
@@ -63,9 +66,12 @@ static int setup_device(int dev) {
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 0 || dev >= 64) return GMMNLSE_E_INVALID;
   if (done[dev]) return GMMNLSE_OK;
-  int sm = 0;
-  CK(cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int smax = 0;
+  CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // the limit covers dynamic shared memory only: leave room for each kernel's
+  // static shared variables
   auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  int sm = smax;
   CK(cudaFuncSetAttribute(k_ip_to_time<R, 16, 1>, A, sm));
   CK(cudaFuncSetAttribute(k_ip_to_time<R, 16, 2>, A, sm));
   CK(cudaFuncSetAttribute(k_ip_to_time<R, 16, 4>, A, sm));
@@ -78,6 +84,11 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_contract<R>, A, sm));
+  if (std::is_same<R, float>::value) {
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, k_tc_contract<false>));
+    CK(cudaFuncSetAttribute(k_tc_contract<false>, A, smax - (int)fa.sharedSizeBytes));
+  }
   CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, A, sm));
@@ -199,12 +210,47 @@ static void launch_k5(gm_job* jb, const Geo& g, cudaStream_t s) {
              (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I, jb->ls);
 }
 
+// K3 on the tensor cores (mixed precision): pack V to BF16 hi/lo, then the
+// tcgen05 GEMM with the l-sum in its epilogue
+template <typename R>
+static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
+  if constexpr (std::is_same<R, float>::value) {
+    gmmnlse_ctx* c = jb->ctx;
+    const int n = c->n;
+    const int npts_total = (jb->Mcap + 1) * n;
+    const int pts = (g.M + 1) * n;
+    const dim3 pgrid((pts + 255) / 256);
+    if (c->raman_mode == 0)
+      pdl_launch(k_pack_bf16<0>, pgrid, dim3(256), 0, s, g, (const float2*)jb->A, (const float*)jb->V,
+                 (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo, (const LoopState*)jb->ls);
+    else
+      pdl_launch(k_pack_bf16<1>, pgrid, dim3(256), 0, s, g, (const float2*)jb->A, (const float*)jb->V,
+                 (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo, (const LoopState*)jb->ls);
+    TcArgs a = {};
+    a.Ghi = c->Ghi;
+    a.Glo = c->Glo;
+    a.KKp = c->KKp;
+    a.P = c->P;
+    a.N = c->N;
+    a.n = n;
+    a.M = g.M;
+    a.A = (const float2*)jb->A;
+    a.NL = (float2*)jb->NL;
+    a.rows = c->rows;
+    a.err = &jb->ls->tc_err;
+    const int tiles = pts / TC_BN;
+    pdl_launch(k_tc_contract<false>, dim3(std::min(tiles, 148)), dim3(128), tc_smem_bytes(c->KKp, c->N), s,
+               jb->mapHi, jb->mapLo, a, (const LoopState*)jb->ls);
+  }
+}
+
 template <typename R>
 static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   gmmnlse_ctx* c = jb->ctx;
   launch_k1<R>(jb, g, s);
   if (c->raman_mode) launch_k2<R>(jb, g, s);
-  launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+  if (c->tc) launch_tc<R>(jb, g, s);
+  else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
   launch_k4<R>(jb, g, s);
   launch_k5<R>(jb, g, s);
   pdl_launch(k_decide, dim3(1), dim3(32), 0, s, jb->ls, h, use_cond);
@@ -426,6 +472,10 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
     st->photons_out = hs.spec[3];
     st->ms = ms;
   }
+  if (hs.tc_err) {
+    gm_set_last_error_text("tensor-core contraction: a wait for its operands timed out");
+    return GMMNLSE_E_CUDA;
+  }
   if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
   if (hs.status == ST_NONFINITE) return GMMNLSE_E_NONFINITE;
   return GMMNLSE_OK;
@@ -464,7 +514,10 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
       switch (k) {
         case 0: launch_k1<R>(jb, g, s); break;
         case 1: launch_k2<R>(jb, g, s); break;
-        case 2: launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s); break;
+        case 2:
+          if (c->tc) launch_tc<R>(jb, g, s);
+          else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+          break;
         case 3: launch_k4<R>(jb, g, s); break;
         case 4: launch_k5<R>(jb, g, s); break;
         default:

@@ -251,3 +251,36 @@ def test_device_pointers_and_torch_stream():
     ctx.propagate(a0, prob.L, prob.dz, prob.M, prob.tol, out=out)
     ctx.close()
     assert rel(out.cpu().numpy(), ref) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# Mixed precision: contraction on the tensor cores (BF16 hi/lo, FP32 accumulate)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("N,Nt,fR", [(3, 256, 0.18), (6, 512, 0.18), (6, 256, 0.0), (10, 256, 0.18),
+                                     (15, 1024, 0.18), (1, 128, 0.18)])
+def test_mixed_bf16_tensor_core_contraction(N, Nt, fR):
+    """The mixed path (FFTs in FP32, coupling contraction as a tcgen05 GEMM
+    on BF16 hi/lo operands) against the FP64 oracle: <= 1e-3 relative L2."""
+    key = ("t", N, Nt, fR)
+    prob = small(*key)
+    ref, sref = oracle_small(key)
+    out, st, rc = gpu_run(prob, "bf16", tol=1e-9)
+    assert rc == B.OK
+    err = rel(out, ref)
+    assert err < 1e-3
+    # the hi/lo split keeps it far below the bar: FP32-like accuracy
+    assert err < 1e-5
+
+
+def test_mixed_bf16_c2_prefix():
+    prob, ref, sref = c2_prefix()
+    out, st, rc = gpu_run(prob, "bf16", tol=1e-8)
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-3
+
+
+def test_mixed_rejects_what_the_tensor_core_tile_cannot_hold():
+    prob = small("p", 3, 64, 0.18)  # Nt not a multiple of the 128-point tile
+    with pytest.raises(B.GmmnlseError) as e:
+        B.Context.from_problem(prob, precision="bf16")
+    assert e.value.status == B.E_UNSUPPORTED
