@@ -34,8 +34,12 @@ WORKLOAD = ("GRIN a=25um NA=0.2 1030nm, N=6 HG modes, Nt=2^13 over 10 ps, Kerr+R
             "self-steepening, 200 fs Gaussian 50 nJ seeded weights, L=0.5 m, dz=25 um, M=10, tol=1e-8")
 
 
-def problem(seed=2, L=0.5):
-    return I.workload("C2", L=L, seed=seed)
+def problem(seed=2, L=0.5, name="C2"):
+    if name == "C2":
+        return I.workload("C2", L=L, seed=seed)
+    if name == "C3":
+        return I.workload(name, L=L, seed=seed + 1, s_from="gh")
+    return I.workload(name, L=L, npts=200)  # C4: S on a 200^2 grid for the profile runs
 
 
 def units(prob, L=None):
@@ -169,6 +173,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--length", type=float, default=0.5, help="fiber length per step [m]")
+    ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C4"],
+                    help="C3 (N=15, Nt=2^14, M=20) and C4 (N=42, Nt=2^13, M=16) are for --profile-run; the metric is quoted on C2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-run", action="store_true",
@@ -197,7 +203,7 @@ def main():
     dev = local
     torch.cuda.set_device(dev)
 
-    prob = problem(seed=2 + rank, L=args.length)
+    prob = problem(seed=2 + rank, L=args.length, name=args.workload)
     stream = torch.cuda.Stream(device=dev)
     ctx = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream,
                                  io_device=True)

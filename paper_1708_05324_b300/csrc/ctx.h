@@ -66,9 +66,11 @@ struct gmmnlse_ctx {
   int2* rows = nullptr;         // [P]
   int2* pairs = nullptr;        // [K]
   bool tc = false;               // contraction on tensor cores (mixed precision)
-  int KKp = 0;                   // K padded to a multiple of 16
-  __nv_bfloat16* Ghi = nullptr;  // [KKp/8][128][8]
+  int KKp = 0;                   // K padded to a multiple of 64
+  int tc_rows = 0;               // rows of G padded to whole row blocks
+  __nv_bfloat16* Ghi = nullptr;  // [KKp/8][tc_rows][8]
   __nv_bfloat16* Glo = nullptr;
+  CUtensorMap mapGhi, mapGlo;
   int contract_threads = 128;
   size_t contract_smem = 0;
   cudaStream_t stream = nullptr;

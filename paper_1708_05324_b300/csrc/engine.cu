@@ -262,13 +262,15 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   // mixed precision: the contraction runs on the tensor cores when the
   // reduced coupling matrix has at most 128 rows and 160 (padded) columns
   if (prm->precision == GMMNLSE_MIXED_BF16) {
-    const int KKp = (c->KK + 15) / 16 * 16;
-    if (c->P > TC_M || KKp > TC_KMAX || n % TC_BN != 0) {
+    // built for N = 1..16 and 42 (the 42-mode step-index workload)
+    if (!((N >= 1 && N <= 16) || N == 42) || n % TC_PTS != 0) {
       delete c;
       return GMMNLSE_E_UNSUPPORTED;
     }
+    const int NB = tc_row_block(c->P);
     c->tc = true;
-    c->KKp = KKp;
+    c->KKp = (c->KK + TC_KC - 1) / TC_KC * TC_KC;
+    c->tc_rows = (c->P + NB - 1) / NB * NB;
   }
 
   // contraction kernel shared memory; shrink the block until it fits
@@ -281,11 +283,17 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   };
   while (T > 32 && need(T) > (size_t)maxsm) T /= 2;
   if (need(T) > (size_t)maxsm) {
-    delete c;
-    return GMMNLSE_E_UNSUPPORTED;
+    // the CUDA-core contraction does not fit; only the tensor-core one can run
+    if (!c->tc) {
+      delete c;
+      return GMMNLSE_E_UNSUPPORTED;
+    }
+    c->contract_threads = 0;
+    c->contract_smem = 0;
+  } else {
+    c->contract_threads = T;
+    c->contract_smem = need(T);
   }
-  c->contract_threads = T;
-  c->contract_smem = need(T);
 
   // device copies
   std::vector<double2> tw(n), twh(n / 2);
@@ -319,13 +327,13 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
   rc = fp64 ? upload_tables<double>(c, Gd) : upload_tables<float>(c, Gd);
   if (!rc && c->tc) {
-    // G split into BF16 hi + lo, blocked [KKp/8][128][8] (K-major core matrices)
-    const int KKp = c->KKp;
-    std::vector<__nv_bfloat16> gh((size_t)TC_M * KKp), gl((size_t)TC_M * KKp);
-    for (int r = 0; r < TC_M; ++r)
+    // G split into BF16 hi + lo, blocked [KKp/8][rows][8] (K-major core matrices)
+    const int KKp = c->KKp, rows = c->tc_rows;
+    std::vector<__nv_bfloat16> gh((size_t)rows * KKp), gl((size_t)rows * KKp);
+    for (int r = 0; r < rows; ++r)
       for (int k = 0; k < KKp; ++k) {
         const float x = (r < c->P && k < c->KK) ? (float)Gd[(size_t)r * c->KK + k] : 0.f;
-        const size_t o = ((size_t)(k / 8) * TC_M + r) * 8 + (k % 8);
+        const size_t o = ((size_t)(k / 8) * rows + r) * 8 + (k % 8);
         gh[o] = __float2bfloat16_rn(x);
         gl[o] = __float2bfloat16_rn(x - __bfloat162float(gh[o]));
       }
@@ -337,6 +345,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
       gm_set_last_cuda_error(e, "coupling matrix upload", __FILE__, __LINE__);
       rc = GMMNLSE_E_CUDA;
     }
+    if (!rc) rc = gm_make_g_maps(c);
   }
   if (!rc) rc = set_smem_attrs(c);
   if (!rc) rc = fp64 ? compute_H<double>(c, hR) : compute_H<float>(c, hR);
@@ -416,7 +425,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
+static int tc_encoder(EncodeTiledFn* out) {
   static EncodeTiledFn enc = nullptr;
   if (!enc) {
     void* fn = nullptr;
@@ -428,22 +437,42 @@ int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
     }
     enc = (EncodeTiledFn)fn;
   }
-  const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
-  const cuuint64_t dims[3] = {8, npts, (cuuint64_t)(c->KKp / 8)};
-  const cuuint64_t strides[2] = {16, npts * 16};
-  const cuuint32_t box[3] = {8, (cuuint32_t)TC_BN, (cuuint32_t)(c->KKp / 8)};
+  *out = enc;
+  return GMMNLSE_OK;
+}
+
+// Map of a blocked [KKp/8][rows][8] BF16 operand; box = one K chunk of
+// box_rows rows.
+static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int box_rows) {
+  EncodeTiledFn enc;
+  const int rc = tc_encoder(&enc);
+  if (rc) return rc;
+  const cuuint64_t dims[3] = {8, rows, (cuuint64_t)(KKp / 8)};
+  const cuuint64_t strides[2] = {16, rows * 16};
+  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(TC_KC / 8)};
   const cuuint32_t es[3] = {1, 1, 1};
-  CUresult r1 = enc(&jb->mapHi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, jb->Vhi, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  CUresult r2 = enc(&jb->mapLo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, jb->Vlo, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
     gm_set_last_error_text("cuTensorMapEncodeTiled rejected the operand layout");
     return GMMNLSE_E_CUDA;
   }
   return GMMNLSE_OK;
+}
+
+int gm_make_g_maps(gmmnlse_ctx* c) {
+  const int NB = tc_row_block(c->P);
+  int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB);
+  if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB);
+  return rc;
+}
+
+int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
+  const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
+  int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS);
+  if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS);
+  return rc;
 }
 
 int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {

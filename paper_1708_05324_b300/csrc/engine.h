@@ -11,6 +11,7 @@ void gm_set_last_cuda_error(cudaError_t e, const char* what, const char* file, i
 void gm_set_last_error_text(const char* msg);
 int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out);
 int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M);
+int gm_make_g_maps(gmmnlse_ctx* c);
 void gm_job_destroy(gm_job* jb);
 int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
                      double* Aout, gmmnlse_stats* st, cudaStream_t s);

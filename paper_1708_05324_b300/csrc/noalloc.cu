@@ -269,6 +269,8 @@ extern "C" int gmmnlse_propagate_noalloc(gmmnlse_ctx* c, const double* A0, doubl
   int mr;
   int rc = gm_schedule(L, dz, M, &nf, &mr);
   if (rc) return rc;
+  // this entry point runs the CUDA-core contraction, which must fit
+  if (c->N > 8 && c->contract_threads == 0) return GMMNLSE_E_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(c->mu);
   CKN(cudaSetDevice(c->prm.device));
   unsigned char* base = nullptr;

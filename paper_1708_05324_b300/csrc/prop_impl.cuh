@@ -58,6 +58,20 @@ static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* o
   return GMMNLSE_OK;
 }
 
+// The tensor-core contraction is instantiated for these mode counts.
+template <class F>
+static int tc_for_each_n(F&& f) {
+  int rc = GMMNLSE_OK;
+  auto one = [&](auto kern) {
+    if (!rc) rc = f(kern);
+  };
+#define GM_TC_N(N) one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), false>);
+  GM_TC_N(1) GM_TC_N(2) GM_TC_N(3) GM_TC_N(4) GM_TC_N(5) GM_TC_N(6) GM_TC_N(7) GM_TC_N(8)
+  GM_TC_N(9) GM_TC_N(10) GM_TC_N(11) GM_TC_N(12) GM_TC_N(13) GM_TC_N(14) GM_TC_N(15) GM_TC_N(16) GM_TC_N(42)
+#undef GM_TC_N
+  return rc;
+}
+
 // Once per device: raise the shared-memory limit of this unit's kernels.
 template <typename R>
 static int setup_device(int dev) {
@@ -85,9 +99,13 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_contract<R>, A, sm));
   if (std::is_same<R, float>::value) {
-    cudaFuncAttributes fa;
-    CK(cudaFuncGetAttributes(&fa, k_tc_contract<false>));
-    CK(cudaFuncSetAttribute(k_tc_contract<false>, A, smax - (int)fa.sharedSizeBytes));
+    const int rc = tc_for_each_n([&](auto kern) -> int {
+      cudaFuncAttributes fa;
+      CK(cudaFuncGetAttributes(&fa, kern));
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smax - (int)fa.sharedSizeBytes));
+      return GMMNLSE_OK;
+    });
+    if (rc) return rc;
   }
   CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, A, sm));
@@ -227,20 +245,27 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
       pdl_launch(k_pack_bf16<1>, pgrid, dim3(256), 0, s, g, (const float2*)jb->A, (const float*)jb->V,
                  (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo, (const LoopState*)jb->ls);
     TcArgs a = {};
-    a.Ghi = c->Ghi;
-    a.Glo = c->Glo;
     a.KKp = c->KKp;
-    a.P = c->P;
-    a.N = c->N;
     a.n = n;
     a.M = g.M;
     a.A = (const float2*)jb->A;
     a.NL = (float2*)jb->NL;
-    a.rows = c->rows;
     a.err = &jb->ls->tc_err;
-    const int tiles = pts / TC_BN;
-    pdl_launch(k_tc_contract<false>, dim3(std::min(tiles, 148)), dim3(128), tc_smem_bytes(c->KKp, c->N), s,
-               jb->mapHi, jb->mapLo, a, (const LoopState*)jb->ls);
+    const dim3 grid(std::min(pts / TC_PTS, 148));
+    switch (c->N) {
+#define GM_TC_CASE(NN)                                                                                      \
+  case NN: {                                                                                                \
+    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                     \
+    pdl_launch(k_tc_contract<NN, NB, false>, grid, dim3(192), TcShape<NN, NB>::SMEM, s, jb->mapHi, jb->mapLo, \
+               c->mapGhi, c->mapGlo, a, (const LoopState*)jb->ls);                                           \
+    break;                                                                                                  \
+  }
+      GM_TC_CASE(1) GM_TC_CASE(2) GM_TC_CASE(3) GM_TC_CASE(4) GM_TC_CASE(5) GM_TC_CASE(6) GM_TC_CASE(7)
+      GM_TC_CASE(8) GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
+      GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
+#undef GM_TC_CASE
+      default: break;
+    }
   }
 }
 

@@ -1,18 +1,29 @@
 // Coupling contraction on the 5th-generation tensor cores (mixed precision).
 //
 // Per point (j, t) of the MPA iteration (Eq. 1 bracket after the symmetry
-// rewrite):  R_r = sum_k G[r][k] V_k   (r = (p <= l), k over the pair terms),
+// rewrite):  R_r = sum_k G[r][k] V_k   (rows r = (p <= l), k over pair terms),
 //            NL_p = sum_l A_l R_pl.
-// Over a tile of BN points this is the GEMM  D[128 x BN] = G[128 x KKp] .
-// V[BN x KKp]^T  with G (<= 128 rows) and V split into BF16 hi + lo parts;
-// D accumulates hi.hi + hi.lo + lo.hi in FP32 in TMEM (the lo.lo product is
-// below FP32 rounding of the result).  V tiles arrive by TMA; one thread
-// issues tcgen05.mma; the epilogue reads D with tcgen05.ld and forms the
-// l-sum, writing NL in FP32.
+// Over a tile of 128 points and a block of NB rows this is the GEMM
+//   D[128 x NB] = V[128 x K] . G[NB x K]^T
+// with V and G split into BF16 hi + lo parts; D accumulates hi.hi + lo.hi +
+// hi.lo in FP32 in TMEM (lo.lo lies below the FP32 rounding of the result).
+// Points are the MMA's M dimension, so after tcgen05.ld each epilogue thread
+// holds R_r(t) for its own point t and forms the l-sum in registers, with the
+// row -> (p, l) map resolved at compile time.
+//
+// Roles (192 threads): warp 0 issues TMA copies of K chunks (64 wide) of V
+// and G into a ring of stages; warp 1 issues tcgen05.mma from the ring into
+// one of two TMEM accumulators; warps 2-5 drain an accumulator (tcgen05.ld)
+// while the MMAs of the next work item run.  A work item is (point tile, row
+// block); NL of a tile is written after its last row block.
 //
 // Operand layout (both K-major, no swizzle): core matrices of 8 rows x 8
-// elements (16 bytes), stored [k/8][row][8], so that along K neighbouring
-// core matrices are rows*16 bytes apart (LBO) and along M/N 128 bytes (SBO).
+// elements (16 bytes), stored [k/8][row][8]; in shared memory a K chunk of R
+// rows is [8][R][8], so core matrices adjacent along K are R*16 bytes apart
+// (LBO) and along the rows 128 bytes (SBO).
+//
+// Every mbarrier wait is bounded; on a timeout the kernel records an error
+// in *err and every role stops issuing work.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -23,177 +34,250 @@
 
 namespace gm {
 
-constexpr int TC_M = 128;   // MMA M: rows of G (P padded)
-constexpr int TC_BN = 128;  // MMA N: points per tile
-constexpr int TC_KMAX = 160;
+constexpr int TC_PTS = 128;  // MMA M: points per tile
+constexpr int TC_KC = 64;    // K chunk per pipeline stage
 
 struct TcArgs {
-  const __nv_bfloat16* Ghi;  // [KKp/8][128][8]
-  const __nv_bfloat16* Glo;
-  int KKp;                   // padded K (multiple of 16, <= TC_KMAX)
-  int P;                     // live rows of G
-  int N, n, M;               // modes, samples, substeps (tiles cover j = 0..M)
-  const float2* A;           // [M+1][N][n] fields (for the l-sum)
-  float2* NL;                // [M+1][N][n] output
-  const int2* rows;          // [P] (p, l) of each row
-  float* Rout;               // probe mode: [128][npts] raw D
-  int npts;                  // total points (probe mode)
-  unsigned* err;             // set to 1 if a wait times out
+  int KKp;           // K padded to a multiple of TC_KC
+  int n, M;          // samples, substeps (tiles cover j = 0..M)
+  const float2* A;   // [M+1][N][n]
+  float2* NL;        // [M+1][N][n]
+  unsigned* err;     // set to 1 if a wait times out
+  float* Rout;       // probe mode: [npts][NRB * NB] raw D
+  int npts;          // probe mode: number of points
 };
 
-// B tiles, reused as the D staging area (128 x BN floats) after the MMAs
-__host__ __device__ __forceinline__ size_t tc_bregion_bytes(int KKp) {
-  const size_t b = (size_t)2 * TC_BN * KKp * 2, r = (size_t)TC_M * TC_BN * 4;
-  return b > r ? b : r;
-}
-__host__ __device__ __forceinline__ size_t tc_smem_bytes(int KKp, int N) {
-  return (size_t)2 * TC_M * KKp * 2            // Ghi, Glo
-         + tc_bregion_bytes(KKp)               // Bhi, Blo / D staging
-         + (size_t)4 * N * TC_BN * 4           // A values and NL accumulators
-         + (size_t)TC_M * 8                    // rows table
-         + 1024;                               // alignment of the base
-}
+__host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
 
-template <bool PROBE>
-__global__ void __launch_bounds__(128, 1) k_tc_contract(const __grid_constant__ CUtensorMap mapHi,
-                                                         const __grid_constant__ CUtensorMap mapLo, TcArgs a,
-                                                         const LoopState* __restrict__ ls) {
-  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
-  // TMA destinations and MMA operands start on a 1024-byte boundary
-  unsigned char* smraw = tc_smem_raw + ((1024 - (tc::smem_addr(tc_smem_raw) & 1023)) & 1023);
-  __shared__ __align__(8) uint64_t bar_load, bar_mma;
-  __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int KKp = a.KKp;
-  const size_t opnd = (size_t)TC_M * KKp;  // elements per operand tile
-  __nv_bfloat16* sGhi = reinterpret_cast<__nv_bfloat16*>(smraw);
-  __nv_bfloat16* sGlo = sGhi + opnd;
-  __nv_bfloat16* sBhi = sGlo + opnd;
-  __nv_bfloat16* sBlo = sBhi + opnd;
-  float* sR = reinterpret_cast<float*>(sBhi);            // D staging after the MMAs (128 x BN floats)
-  float* sA = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sBhi) + tc_bregion_bytes(KKp));  // [2N][BN]
-  float* sNL = sA + 2 * a.N * TC_BN;                      // [2N][BN]
-  int2* sRows = reinterpret_cast<int2*>(sNL + 2 * a.N * TC_BN);
+template <int N, int NB>
+struct TcShape {
+  static constexpr int P = N * (N + 1) / 2;
+  static constexpr int NRB = (P + NB - 1) / NB;       // row blocks
+  static constexpr int V_BYTES = TC_PTS * TC_KC * 2;  // one of hi / lo
+  static constexpr int G_BYTES = NB * TC_KC * 2;
+  static constexpr int STAGE = 2 * (V_BYTES + G_BYTES);
+  static constexpr int FIT = 200 * 1024 / STAGE;
+  static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 4 ? 4 : FIT);
+  static constexpr int TMEM_COLS =
+      2 * NB <= 32 ? 32 : (2 * NB <= 64 ? 64 : (2 * NB <= 128 ? 128 : (2 * NB <= 256 ? 256 : 512)));
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
+};
 
-  // constant operand and tables (before waiting on the previous kernel)
-  {
-    const uint4* gh = reinterpret_cast<const uint4*>(a.Ghi);
-    const uint4* gl = reinterpret_cast<const uint4*>(a.Glo);
-    uint4* sh = reinterpret_cast<uint4*>(sGhi);
-    uint4* sl = reinterpret_cast<uint4*>(sGlo);
-    const int chunks = (int)(opnd / 8);
-    for (int i = tid; i < chunks; i += blockDim.x) {
-      sh[i] = gh[i];
-      sl[i] = gl[i];
+// Row r of the reduced coupling matrix is the pair (p, l), p <= l, in the
+// order (0,0), (0,1), ..., (0,N-1), (1,1), ...
+template <int N>
+struct RowPair {
+  __host__ __device__ static constexpr int p_of(int r) {
+    int p = 0;
+    while (r >= N - p) {
+      r -= N - p;
+      ++p;
     }
-    if (!PROBE)
-      for (int i = tid; i < a.P; i += blockDim.x) sRows[i] = a.rows[i];
+    return p;
   }
+  __host__ __device__ static constexpr int l_of(int r) {
+    int p = 0;
+    while (r >= N - p) {
+      r -= N - p;
+      ++p;
+    }
+    return p + r;
+  }
+};
+
+// NL_p += A_l R_r (and NL_l += A_p R_r) for rows R .. R0 + 15, compile-time.
+template <int N, int R, int REND>
+struct LSum {
+  __device__ __forceinline__ static void run(const float* v, const float2* a, float2* nl) {
+    if constexpr (R < REND && R < N * (N + 1) / 2) {
+      constexpr int p = RowPair<N>::p_of(R), l = RowPair<N>::l_of(R);
+      constexpr int i = R % 16;
+      nl[p].x += a[l].x * v[i];
+      nl[p].y += a[l].y * v[i];
+      if constexpr (p != l) {
+        nl[l].x += a[p].x * v[i];
+        nl[l].y += a[p].y * v[i];
+      }
+      LSum<N, R + 1, REND>::run(v, a, nl);
+    }
+  }
+};
+
+// Columns C .. NB-1 of an accumulator holding row block RB.
+template <int N, int NB, int RB, int C>
+struct Drain {
+  __device__ __forceinline__ static void run(uint32_t taddr, const float2* a, float2* nl) {
+    constexpr int R0 = RB * NB + C;
+    if constexpr (C < NB && R0 < N * (N + 1) / 2) {
+      float v[16];
+      tc::tmem_ld16(taddr + C, v);
+      LSum<N, R0, R0 + 16>::run(v, a, nl);
+      Drain<N, NB, RB, C + 16>::run(taddr, a, nl);
+    }
+  }
+};
+
+template <int N, int NB, int RB>
+__device__ __forceinline__ void drain_rb(int rb, uint32_t taddr, const float2* a, float2* nl) {
+  if constexpr (RB < TcShape<N, NB>::NRB) {
+    if (rb == RB) Drain<N, NB, RB, 0>::run(taddr, a, nl);
+    else drain_rb<N, NB, RB + 1>(rb, taddr, a, nl);
+  }
+}
+
+template <int N, int NB, bool PROBE>
+__global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ CUtensorMap mapVhi,
+                                                         const __grid_constant__ CUtensorMap mapVlo,
+                                                         const __grid_constant__ CUtensorMap mapGhi,
+                                                         const __grid_constant__ CUtensorMap mapGlo, TcArgs a,
+                                                         const LoopState* __restrict__ ls) {
+  using S = TcShape<N, NB>;
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  unsigned char* smem = tc_smem_raw + ((1024 - (tc::smem_addr(tc_smem_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t full[S::STAGES], empty[S::STAGES], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int stop_flag;
+  volatile int* stop = &stop_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
   if (tid == 0) {
-    tc::mbar_init(&bar_load, 1);
-    tc::mbar_init(&bar_mma, 1);
+    for (int s = 0; s < S::STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 128);
+    }
     tc::fence_mbar_init();
-    abort_flag = 0;
+    stop_flag = 0;
   }
-  // generic-proxy writes of G become visible to the tensor core (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (warp == 0) tc::tmem_alloc(&tmem_base, TC_BN);
+  if (warp == 1) tc::tmem_alloc(&tmem_base, S::TMEM_COLS);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   pdl_enter();
   const uint32_t tmem = tmem_base;
   const int iter = PROBE ? 0 : ls->iter;
-  const int tiles_per_j = a.n / TC_BN;
-  const int ntiles = PROBE ? a.npts / TC_BN : (a.M + 1) * tiles_per_j;
-  const uint32_t idesc = tc::idesc_f16(TC_M, TC_BN, true);
-  const uint32_t lboA = TC_M * 16, lboB = TC_BN * 16, sbo = 128;
-  const unsigned tx_bytes = (unsigned)(2 * opnd * sizeof(__nv_bfloat16));
-  unsigned phase = 0;
+  const int n = a.n;
+  const int ntiles = PROBE ? a.npts / TC_PTS : (a.M + 1) * (n / TC_PTS);
+  const int kchunks = a.KKp / TC_KC;
+  // z0 tiles are skipped after the first iteration (their integrand is known)
+  auto live = [&](int tile) { return PROBE || iter == 0 || tile * TC_PTS >= n; };
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int pt0 = tile * TC_BN;
-    const int j = PROBE ? 0 : pt0 / a.n;
-    if (!PROBE && iter > 0 && j == 0) continue;
-    if (tid == 0) {
-      tc::mbar_arrive_expect_tx(&bar_load, tx_bytes);
-      tc::tma_load_3d(sBhi, &mapHi, 0, pt0, 0, &bar_load);
-      tc::tma_load_3d(sBlo, &mapLo, 0, pt0, 0, &bar_load);
-      if (!tc::mbar_wait(&bar_load, phase)) {
-        abort_flag = 1;
-      } else {
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int c = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
+        if (!live(tile)) continue;
+        for (int rb = 0; rb < S::NRB && !*stop; ++rb)
+          for (int kc = 0; kc < kchunks; ++kc, ++c) {
+            const int s = c % S::STAGES, round = c / S::STAGES;
+            if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1)) {
+              *stop = 1;
+              atomicExch(a.err, 1u);
+              break;
+            }
+            unsigned char* st = smem + (size_t)s * S::STAGE;
+            tc::mbar_arrive_expect_tx(&full[s], S::STAGE);
+            tc::tma_load_3d(st, &mapVhi, 0, tile * TC_PTS, kc * (TC_KC / 8), &full[s]);
+            tc::tma_load_3d(st + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kc * (TC_KC / 8), &full[s]);
+            tc::tma_load_3d(st + 2 * S::V_BYTES, &mapGhi, 0, rb * NB, kc * (TC_KC / 8), &full[s]);
+            tc::tma_load_3d(st + 2 * S::V_BYTES + S::G_BYTES, &mapGlo, 0, rb * NB, kc * (TC_KC / 8), &full[s]);
+          }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16(TC_PTS, NB, true);
+      const uint32_t lboV = TC_PTS * 16, lboG = NB * 16, sbo = 128;
+      int c = 0, w = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
+        if (!live(tile)) continue;
+        for (int rb = 0; rb < S::NRB && !*stop; ++rb, ++w) {
+          const int acc = w & 1, use = w >> 1;
+          if (use > 0 && !tc::mbar_wait(&acc_empty[acc], (use - 1) & 1)) {
+            *stop = 1;
+            atomicExch(a.err, 1u);
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t d = tmem + (uint32_t)(acc * NB);
+          for (int kc = 0; kc < kchunks; ++kc, ++c) {
+            const int s = c % S::STAGES, round = c / S::STAGES;
+            if (!tc::mbar_wait(&full[s], round & 1)) {
+              *stop = 1;
+              atomicExch(a.err, 1u);
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t base = tc::smem_addr(smem + (size_t)s * S::STAGE);
+            const uint32_t vH = base, vL = base + S::V_BYTES, gH = base + 2 * S::V_BYTES, gL = gH + S::G_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_KC / 16; ++kk) {
+              const uint32_t oV = (uint32_t)kk * 2 * lboV, oG = (uint32_t)kk * 2 * lboG;
+              tc::mma_f16(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
+                          (kc > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_f16(d, tc::smem_desc(vL + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc, 1u);
+              tc::mma_f16(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gL + oG, lboG, sbo), idesc, 1u);
+            }
+            tc::mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+          }
+          if (*stop) break;
+          tc::mma_commit(&acc_full[acc]);  // accumulator complete
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, one point per thread ----------------
+    const int quarter = warp & 3;  // this warp may access TMEM lanes 32 quarter ..
+    const int row_in_tile = quarter * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    int w = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
+      if (!live(tile)) continue;
+      const int pt = tile * TC_PTS + row_in_tile;
+      const int j = PROBE ? 0 : pt / n, t = PROBE ? 0 : pt - j * n;
+      float2 av[N], nl[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        av[l] = PROBE ? make_float2(0.f, 0.f) : a.A[((size_t)j * N + l) * n + t];
+        nl[l] = make_float2(0.f, 0.f);
+      }
+      for (int rb = 0; rb < S::NRB; ++rb, ++w) {
+        const int acc = w & 1, use = w >> 1;
+        if (!tc::mbar_wait(&acc_full[acc], use & 1)) {
+          *stop = 1;
+          atomicExch(a.err, 1u);
+          break;
+        }
         tc::fence_after_sync();
-        const uint32_t aH = tc::smem_addr(sGhi), aL = tc::smem_addr(sGlo);
-        const uint32_t bH = tc::smem_addr(sBhi), bL = tc::smem_addr(sBlo);
-        for (int kk = 0; kk < KKp / 16; ++kk) {
-          const uint32_t offA = (uint32_t)kk * 2 * lboA, offB = (uint32_t)kk * 2 * lboB;
-          tc::mma_f16(tmem, tc::smem_desc(aH + offA, lboA, sbo), tc::smem_desc(bH + offB, lboB, sbo), idesc,
-                      kk > 0 ? 1u : 0u);
-          tc::mma_f16(tmem, tc::smem_desc(aH + offA, lboA, sbo), tc::smem_desc(bL + offB, lboB, sbo), idesc, 1u);
-          tc::mma_f16(tmem, tc::smem_desc(aL + offA, lboA, sbo), tc::smem_desc(bH + offB, lboB, sbo), idesc, 1u);
+        const uint32_t taddr = tmem + lane_off + (uint32_t)(acc * NB);
+        if (PROBE) {
+          for (int c0 = 0; c0 < NB; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c0, v);
+            for (int i = 0; i < 16; ++i) a.Rout[(size_t)pt * (S::NRB * NB) + rb * NB + c0 + i] = v[i];
+          }
+        } else {
+          drain_rb<N, NB, 0>(rb, taddr, av, nl);
         }
-        tc::mma_commit(&bar_mma);
+        tc::fence_before_sync();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&acc_empty[acc])) : "memory");
       }
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    if (!tc::mbar_wait(&bar_mma, phase)) {
-      atomicExch(a.err, 1u);
-      abort_flag = 1;
-    }
-    phase ^= 1;
-    __syncthreads();
-    if (abort_flag) break;
-    tc::fence_after_sync();
-    // D row r = 32 warp + lane lives in TMEM lane r
-    const int r = warp * 32 + lane;
-    for (int c = 0; c < TC_BN; c += 16) {
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      if (PROBE) {
+      if (*stop) break;
+      if (!PROBE) {
+        float2* out = a.NL + (size_t)j * N * n + t;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) a.Rout[(size_t)r * a.npts + pt0 + c + i] = v[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) sR[r * TC_BN + c + i] = v[i];
+        for (int p = 0; p < N; ++p) out[(size_t)p * n] = nl[p];
       }
     }
-    tc::fence_before_sync();
-    if (!PROBE) {
-      // l-sum: thread t owns point t of the tile
-      const int t = tid;
-      const int t0 = pt0 - j * a.n;
-      const float2* Aj = a.A + (size_t)j * a.N * a.n;
-      for (int l = 0; l < a.N; ++l) {
-        const float2 x = Aj[(size_t)l * a.n + t0 + t];
-        sA[(2 * l) * TC_BN + t] = x.x;
-        sA[(2 * l + 1) * TC_BN + t] = x.y;
-        sNL[(2 * l) * TC_BN + t] = 0.f;
-        sNL[(2 * l + 1) * TC_BN + t] = 0.f;
-      }
-      __syncthreads();  // sR complete
-      for (int rr = 0; rr < a.P; ++rr) {
-        const float Rv = sR[rr * TC_BN + t];
-        const int2 pl = sRows[rr];
-        sNL[(2 * pl.x) * TC_BN + t] += sA[(2 * pl.y) * TC_BN + t] * Rv;
-        sNL[(2 * pl.x + 1) * TC_BN + t] += sA[(2 * pl.y + 1) * TC_BN + t] * Rv;
-        if (pl.x != pl.y) {
-          sNL[(2 * pl.y) * TC_BN + t] += sA[(2 * pl.x) * TC_BN + t] * Rv;
-          sNL[(2 * pl.y + 1) * TC_BN + t] += sA[(2 * pl.x + 1) * TC_BN + t] * Rv;
-        }
-      }
-      float2* out = a.NL + (size_t)j * a.N * a.n + t0 + t;
-      for (int p = 0; p < a.N; ++p)
-        out[(size_t)p * a.n] = make_float2(sNL[(2 * p) * TC_BN + t], sNL[(2 * p + 1) * TC_BN + t]);
-    }
-    __syncthreads();  // sR / B buffers and TMEM free for the next tile
-    tc::fence_after_sync();
   }
-  if (abort_flag && tid == 0) atomicExch(a.err, 1u);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, TC_BN);
+  if (warp == 1) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 // V (FP32: [M+1][KK][n], or the pair products of A when Kerr only) to the

@@ -276,18 +276,25 @@ def step_index_beta_coeffs(radius, na, lam0, modes, order=3, rel_step=2e-3):
     """Taylor coefficients of each LP mode's beta(omega): the characteristic
     equation is re-solved at 7 frequencies around omega0 (silica cladding,
     NA held constant) and differentiated by the same stencils as the GRIN
-    closed form."""
+    closed form.  Roots are found once per (azimuthal order, frequency)."""
     omega0 = 2 * np.pi * C_LIGHT / lam0
+    cache = {}
+
+    def roots(ell, om):
+        key = (ell, om)
+        if key not in cache:
+            V = om / C_LIGHT * radius * na
+            cache[key] = _lp_eigen_u(ell, V)
+        return cache[key]
+
     coeffs = []
     for md in modes:
         def beta_fn(om, md=md):
             lam = 2 * np.pi * C_LIGHT / om
             k = om / C_LIGHT
-            V = k * radius * na
             n_cl = float(silica_index(lam))
             n_co = math.sqrt(n_cl ** 2 + na ** 2)
-            us = _lp_eigen_u(md["l"], V)
-            u = us[md["m"] - 1]
+            u = roots(md["l"], float(om))[md["m"] - 1]
             return math.sqrt((k * n_co) ** 2 - (u / radius) ** 2)
         coeffs.append(taylor_coefficients(beta_fn, omega0, order, rel_step))
     return coeffs

@@ -284,3 +284,21 @@ def test_mixed_rejects_what_the_tensor_core_tile_cannot_hold():
     with pytest.raises(B.GmmnlseError) as e:
         B.Context.from_problem(prob, precision="bf16")
     assert e.value.status == B.E_UNSUPPORTED
+
+
+@functools.lru_cache(maxsize=None)
+def c4_small():
+    """The 42-mode step-index fiber of the dense-contraction workload on a
+    small grid (Nt = 256): 903 x 903 reduced coupling matrix, four row blocks
+    of the tensor-core tile.  One long step of M = 4 with 3 fixed updates
+    keeps the oracle's naive N^4 sums to seconds."""
+    prob = I.workload("C4", Nt=256, dt=4e-12 / 256, L=4 * 37.5e-6, M=4, npts=160)
+    ref, sref = oracle_run(prob, fixed_iters=3)
+    return prob, ref
+
+
+def test_mixed_bf16_dense_42_mode_contraction():
+    prob, ref = c4_small()
+    out, st, rc = gpu_run(prob, "bf16", fixed_iters=3)
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-3
