@@ -165,6 +165,134 @@ def cpu_baseline(seconds=15.0):
             "sample": f"first {steps} long steps ({steps * prob.M} substeps) of the 0.5 m run, {dt:.1f} s"}
 
 
+# ----------------------------------------------------------------------------
+# Serving (continuous batching through gmmnlse_submit / gmmnlse_poll)
+# ----------------------------------------------------------------------------
+SERVE_NS = (1, 3, 6, 10, 15)
+SERVE_NTS = (1024, 2048, 4096, 8192, 16384)
+
+
+def serving_requests(count, seed=5, max_substeps=2000, M=10):
+    """Seeded requests with the C5 mix: N in {1,3,6,10,15} and Nt in 2^10..2^14
+    (uniform), dt = 4.8828125 fs, Gaussian FWHM log-uniform 100-500 fs, energy
+    log-uniform 1-200 nJ, L log-uniform 1 cm - 1 m, M = 10,
+    dz = L / (M ceil(L / (M z_NL / 200))).  A request longer than max_substeps
+    substeps is cut to that many (same dz), so the pass fits in minutes."""
+    g = I.SplitMix64(seed)
+    dt = 4.8828125e-15
+    reqs = []
+    for i in range(count):
+        N = SERVE_NS[min(int(g.uniform() * 5), 4)]
+        Nt = SERVE_NTS[min(int(g.uniform() * 5), 4)]
+        fwhm = 100e-15 * 5.0 ** g.uniform()
+        energy = 1e-9 * 200.0 ** g.uniform()
+        L = 0.01 * 100.0 ** g.uniform()
+        A0 = I.launch_field(N, Nt, dt, "gaussian", fwhm, energy, seed * 1000 + i)
+        P0 = float(np.max(np.sum(np.abs(A0) ** 2, axis=0)))
+        w = I.grin_mode_width(25e-6, 0.2, 1030e-9)
+        gamma = 2.3e-20 * 2 * math.pi / 1030e-9 / (math.pi * w * w)
+        znl = 1.0 / (gamma * P0)
+        nsub = M * math.ceil(L / (M * znl / 200))
+        dz = L / nsub
+        if nsub > max_substeps:
+            nsub = max_substeps
+            L = nsub * dz
+        reqs.append(dict(N=N, Nt=Nt, dt=dt, A0=A0, L=L, dz=dz, M=M, units=N * Nt * nsub))
+    return reqs
+
+
+def run_serving(B, dev, count=32, max_substeps=2000, inflight=8, load=0.9, seed=5):
+    reqs = serving_requests(count, seed=seed, max_substeps=max_substeps)
+    ctxs = {}
+    for r in reqs:
+        key = (r["N"], r["Nt"])
+        if key not in ctxs:
+            prob = I.grin_problem("serve", N=r["N"], Nt=r["Nt"], dt=r["dt"], kind="gaussian", fwhm=200e-15,
+                                  energy=1e-9, L=0.01, dz=1e-3, M=10, tol=1e-6, seed=1, fR=0.18, s_from="gh")
+            ctxs[key] = B.Context.from_problem(prob, precision="bf16", device=dev)
+    srv = B.Server(hbm_budget=32 << 30, max_inflight=inflight)
+
+    def submit(r):
+        return srv.submit(ctxs[(r["N"], r["Nt"])], r["A0"], r["L"], r["dz"], r["M"], 1e-6)
+
+    def drain(tickets, t_submit):
+        done = {}
+        while len(done) < len(tickets):
+            for t in tickets:
+                if t in done:
+                    continue
+                rc, out, st = srv.poll(t, *shapes[t])
+                if rc != B.PENDING:
+                    done[t] = (time.perf_counter() - t_submit[t], rc)
+            time.sleep(0.0005)
+        return done
+
+    # warm-up (graphs, workspaces)
+    shapes = {}
+    warm = []
+    for r in reqs[:4]:
+        t = submit(r)
+        shapes[t] = (r["N"], r["Nt"])
+        warm.append(t)
+    drain(warm, {t: time.perf_counter() for t in warm})
+    # capacity: all requests at once
+    t0 = time.perf_counter()
+    tickets, t_submit = [], {}
+    for r in reqs:
+        t = submit(r)
+        shapes[t] = (r["N"], r["Nt"])
+        t_submit[t] = time.perf_counter()
+        tickets.append(t)
+    done = drain(tickets, t_submit)
+    cap_s = time.perf_counter() - t0
+    units = sum(r["units"] for r in reqs)
+    status = {}
+    for _, rc in done.values():
+        status[rc] = status.get(rc, 0) + 1
+    capacity = len(reqs) / cap_s
+    # open loop: Poisson arrivals at load x capacity
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / (load * capacity), size=len(reqs))
+    tickets, t_submit = [], {}
+    t0 = time.perf_counter()
+    next_t = t0
+    for r, gap in zip(reqs, gaps):
+        next_t += gap
+        while time.perf_counter() < next_t:
+            time.sleep(0.0002)
+        t = submit(r)
+        shapes[t] = (r["N"], r["Nt"])
+        t_submit[t] = time.perf_counter()
+        tickets.append(t)
+    done = drain(tickets, t_submit)
+    open_s = time.perf_counter() - t0
+    lat = np.array([done[t][0] for t in tickets]) * 1e3
+    srv.close()
+    for c in ctxs.values():
+        c.close()
+    # serial plain FP64 MPA on the same requests (FP64 iterates are built for Nt <= 8192)
+    sub = [r for r in reqs if r["Nt"] <= 8192][:8]
+    t64 = 0.0
+    for r in sub:
+        prob = I.grin_problem("serve", N=r["N"], Nt=r["Nt"], dt=r["dt"], kind="gaussian", fwhm=200e-15,
+                              energy=1e-9, L=0.01, dz=1e-3, M=10, tol=1e-6, seed=1, fR=0.18, s_from="gh")
+        c = B.Context.from_problem(prob, precision="fp64", device=dev)
+        c.propagate(r["A0"], r["L"], r["dz"], r["M"], 1e-6, check=False)  # warm-up
+        t1 = time.perf_counter()
+        c.propagate(r["A0"], r["L"], r["dz"], r["M"], 1e-6, check=False)
+        t64 += time.perf_counter() - t1
+        c.close()
+    fp64_serial = sum(r["units"] for r in sub) / t64
+    return {"requests": len(reqs), "precision": "bf16", "max_inflight": inflight,
+            "max_substeps_per_request": max_substeps,
+            "closed_loop_units_per_s": units / cap_s, "closed_loop_s": cap_s,
+            "offered_load": load, "open_loop_units_per_s": units / open_s,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "status_counts": {B.load().gmmnlse_strerror(k).decode(): v for k, v in status.items()},
+            "fp64_serial_units_per_s": fp64_serial, "fp64_serial_requests": len(sub),
+            "mix": "C5: N in {1,3,6,10,15}, Nt 2^10..2^14, FWHM 100-500 fs, 1-200 nJ, L 1 cm-1 m, dz = z_NL/200"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,6 +304,7 @@ def main():
     ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C4"],
                     help="C3 (N=15, Nt=2^14, M=20) and C4 (N=42, Nt=2^13, M=16) are for --profile-run; the metric is quoted on C2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving pass (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-run", action="store_true",
                     help="only the timed propagations (for ncu captures)")
@@ -323,6 +452,8 @@ def main():
                      "all_kernels_ms": {k: v[0] for k, v in prof.items()}},
         "clocks": clk.summary(),
     }
+    if args.serve_requests > 0:
+        line["serving"] = run_serving(B, dev, count=args.serve_requests)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line))

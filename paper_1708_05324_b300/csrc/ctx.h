@@ -41,6 +41,7 @@ struct gm_job {
   struct G {
     int Mj = -1;
     int which = 0;
+    double dz = 0.0;  // the kernels' parameters (dz/2 of the trapezoid) are baked into the graph
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
   } graphs[2];

@@ -336,6 +336,7 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   out.exec = exec;
   out.Mj = g.M;
   out.which = which;
+  out.dz = 2.0 * g.hdz;
   return GMMNLSE_OK;
 }
 
@@ -359,7 +360,7 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
   if (!graphs_disabled()) {
     gm_job::G* gr = nullptr;
     for (auto& x : jb->graphs)
-      if (x.exec && x.Mj == Mj && x.which == which) gr = &x;
+      if (x.exec && x.Mj == Mj && x.which == which && x.dz == dz) gr = &x;
     if (!gr) {
       gm_job::G& slot = jb->graphs[which];
       if (slot.exec) {

@@ -229,6 +229,21 @@ def test_graph_and_host_loop_agree_bitwise(monkeypatch):
     assert sa["iter_hist"] == sb["iter_hist"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_one_context_many_step_sizes(precision):
+    """A context (and its cached launch graphs) reused with different dz, M
+    and L gives the same result as a fresh context for each call."""
+    prob = small("p", 3, 256, 0.18)
+    ctx = B.Context.from_problem(prob, precision=precision)
+    calls = [(2e-3, 1e-4, 5), (2e-3, 2e-4, 5), (1.2e-3, 1e-4, 7), (2e-3, 1e-4, 5), (8e-4, 4e-5, 5)]
+    for L, dz, M in calls:
+        a, _, rc = ctx.propagate(prob.A0, L, dz, M, prob.tol, check=False)
+        b, _, rcb = gpu_run(prob, precision, L=L, dz=dz, M=M)
+        assert rc == rcb == B.OK
+        assert np.array_equal(a, b)
+    ctx.close()
+
+
 def test_repeat_is_deterministic():
     prob = small("p", 4, 256, 0.18)
     ctx = B.Context.from_problem(prob, precision="fp64")
