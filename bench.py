@@ -105,10 +105,11 @@ class ClockSampler:
 
 def launches_per_step(st, raman, graph=True):
     """Kernel launches of one propagate call, from its statistics."""
-    per_iter = 6 if raman else 5   # K1 [K2] K3 K4 K5 + decision
+    per_iter = 5 if raman else 4   # K1 [K2] K3 K4 K5 (decision in K5's last block)
     fft = 1  # Nt <= 8192
     n = 1 + fft + 1          # non-finite check, forward transform, input sums
     n += 1 + fft             # output sums, inverse transform
+    # per long step: loop re-arm (graph only), advance, bookkeeping
     n += st["iters_total"] * per_iter + st["long_steps"] * (3 if graph else 2)
     return n
 

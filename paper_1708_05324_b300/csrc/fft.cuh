@@ -21,6 +21,8 @@
 // separates its reads from its writes with a barrier.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace gm {
@@ -264,41 +266,66 @@ __device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __r
 // decimation in frequency): block s (0 <= s < S) computes X[S k + s],
 // k < n/S, as the (n/S)-point transform of
 //   y_s[t] = W^{DIR t s} sum_{u<S} x[t + u n/S] W_S^{DIR u s},  W = exp(2 pi i / n).
-// Each block reads all n inputs; no data moves between blocks.  tw is the
-// n-point table.  S = 1 is the plain transform.
-template <typename R, int DIR, int EPT, int S, class Load, class Store>
-__device__ __forceinline__ void fft_block_split(cplx<R>* sm, int n, int s, const cplx<R>* __restrict__ tw,
-                                                const Load& load, const Store& store) {
-  if (S == 1) {
-    fft_block<R, DIR, EPT>(sm, n, tw, 1, load, store);
-    return;
+// x_at(u, t) supplies x[t + u n/S].
+template <typename R, int DIR, int S, class XAt>
+__device__ __forceinline__ cplx<R> dif_input(int s, int t, const cplx<R>* __restrict__ tw, const XAt& x_at) {
+  cplx<R> acc = x_at(0, t);
+  if (S == 2) {
+    const cplx<R> b = x_at(1, t);
+    acc = s ? csub<R>(acc, b) : cadd<R>(acc, b);
+  } else if (S == 4) {  // W_4^{DIR u s} = (DIR i)^{u s}
+    const cplx<R> b = x_at(1, t), c = x_at(2, t), d = x_at(3, t);
+    const cplx<R> ac = cadd<R>(acc, c), amc = csub<R>(acc, c);
+    const cplx<R> bd = cadd<R>(b, d), ibmd = mul_i<R, DIR>(csub<R>(b, d));
+    switch (s) {
+      case 0: acc = cadd<R>(ac, bd); break;
+      case 1: acc = cadd<R>(amc, ibmd); break;
+      case 2: acc = csub<R>(ac, bd); break;
+      default: acc = csub<R>(amc, ibmd); break;
+    }
   }
+  if (s) {
+    cplx<R> w = tw[t * s];
+    if (DIR > 0) w.y = -w.y;
+    acc = cmul<R>(acc, w);
+  }
+  return acc;
+}
+
+// An n-point transform spread over the S blocks of a thread-block cluster
+// (S = 2 or 4).  Block s reads only the input slice t in [s n/S, (s+1) n/S)
+// (load(t), into xbuf), forms its residue-s input of the radix-S first stage
+// from all slices through distributed shared memory, transforms n/S points
+// locally, and finally gathers the output slice q in [s n/S, (s+1) n/S)
+// (X[q] = Y_{q mod S}[q div S]) from the blocks' results, handing each to
+// store(q).  xbuf: n/S elements; sm: fft_smem_elems(n/S) elements.  Every
+// block of the cluster must call it.
+template <typename R, int DIR, int EPT, int S, class Load, class Store>
+__device__ __forceinline__ void fft_cluster(cplx<R>* xbuf, cplx<R>* sm, int n, const cplx<R>* __restrict__ tw,
+                                            const Load& load, const Store& store) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = (int)cluster.block_rank();
   const int np = n / S;
-  auto load_s = [&](int t) {
-    cplx<R> acc = load(t);
-    if (S == 2) {
-      const cplx<R> b = load(t + np);
-      acc = s ? csub<R>(acc, b) : cadd<R>(acc, b);
-    } else {  // S == 4: W_4^{DIR u s} = (DIR i)^{u s}
-      const cplx<R> b = load(t + np), c = load(t + 2 * np), d = load(t + 3 * np);
-      const cplx<R> ac = cadd<R>(acc, c), amc = csub<R>(acc, c);
-      const cplx<R> bd = cadd<R>(b, d), ibmd = mul_i<R, DIR>(csub<R>(b, d));
-      switch (s) {
-        case 0: acc = cadd<R>(ac, bd); break;
-        case 1: acc = cadd<R>(amc, ibmd); break;
-        case 2: acc = csub<R>(ac, bd); break;
-        default: acc = csub<R>(amc, ibmd); break;
-      }
-    }
-    if (s) {
-      cplx<R> w = tw[t * s];
-      if (DIR > 0) w.y = -w.y;
-      acc = cmul<R>(acc, w);
-    }
-    return acc;
-  };
-  auto store_s = [&](int k, cplx<R> v) { store(S * k + s, v); };
-  fft_block<R, DIR, EPT>(sm, np, tw, S, load_s, store_s);
+  for (int t = threadIdx.x; t < np; t += blockDim.x) xbuf[t] = load(s * np + t);
+  cluster.sync();  // every slice loaded
+  const cplx<R>* xs[S];
+  const cplx<R>* ys[S];
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    xs[u] = cluster.map_shared_rank(xbuf, u);
+    ys[u] = cluster.map_shared_rank(sm, u);
+  }
+  auto x_at = [&](int u, int t) { return xs[u][t]; };
+  auto first = [&](int t) { return dif_input<R, DIR, S>(s, t, tw, x_at); };
+  auto keep = [&](int k, cplx<R> v) { sm[pad16(k)] = v; };
+  fft_block<R, DIR, EPT>(sm, np, tw, S, first, keep);
+  cluster.sync();  // every block's Y_s complete
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    const int q = s * np + i;
+    store(q, ys[q % S][pad16(q / S)]);
+  }
+  cluster.sync();  // partners are done reading this block's buffers
 }
 
 }  // namespace gm

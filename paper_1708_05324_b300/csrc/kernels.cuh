@@ -40,6 +40,7 @@ struct LoopState {
   int hist[33];
   double spec[4];          // sum |psi0|^2, photon sum (filled by k_spec_sums)
   unsigned tc_err;         // a tensor-core contraction wait timed out
+  unsigned arrive;         // blocks of k_trapz_decide that have added their sums
 };
 
 struct Geo {
@@ -86,8 +87,8 @@ __global__ void k_phase_tables(const double* __restrict__ beta, int Nn, int M, d
 }
 
 // ---------------------------------------------------------------------------
-// K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N S, M+1): block
-// x = p S + s computes the output residue class s mod S (fft_block_split).
+// K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N S, M+1); with
+// S > 1 the S blocks of a cluster share one transform (fft_cluster).
 // ---------------------------------------------------------------------------
 template <typename R, int EPT, int S>
 __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __restrict__ psiR,
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __rest
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
-  const int p = blockIdx.x / S, sp = blockIdx.x % S, j = blockIdx.y;
+  const int p = blockIdx.x / S, j = blockIdx.y;
   const int iter = ls->iter;
   if (iter > 0 && j == 0) return;
   const int n = g.n;
@@ -113,7 +114,8 @@ __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __rest
     return cmul<R>(x, e[q]);
   };
   auto store = [&](int t, cplx<R> v) { A[off + t] = cscale<R>(v, inv_n); };
-  fft_block_split<R, -1, EPT, S>(sm, n, sp, tw, load, store);
+  if (S == 1) fft_block<R, -1, EPT>(sm, n, tw, load, store);
+  else fft_cluster<R, -1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
 }
 
 // U_k(t): |A_m|^2 for m == n, 2 Re(A_m A_n^*) for m < n (pairs k = (m <= n))
@@ -173,58 +175,38 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
   fft_block<R, +1, EPT>(sm, n, tw, from_smem, store);
 }
 
-// K2 on a 2-block cluster: block s does the even (s = 0) or odd (s = 1)
-// half of the spectrum.  Forward: Y_s[k] = X[2k + s] by the radix-2
-// decimation-in-frequency split; times H[2k + s]; inverse n/2-point
-// transform z_s.  The inverse of the full spectrum is the radix-2
-// decimation-in-time combination x[t' + s n/2] = z_0[t'] + (-1)^s W^{t'} z_1[t']
-// (W = exp(2 pi i / n)), for which block s reads its partner's z through
-// distributed shared memory.  grid (2 ceil(K/2), M+1).
-template <typename R, int EPT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
-    k_pairs_raman_cl(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V, const cplx<R>* __restrict__ H,
-                     const cplx<R>* __restrict__ tw, const int2* __restrict__ pairs,
-                     const LoopState* __restrict__ ls) {
-  namespace cg = cooperative_groups;
+// K2 with the two transforms of a pair spread over an S-block cluster
+// (fft_cluster): block s loads the pair products of its time slice, the
+// spectrum slice it ends up holding is multiplied by H in place, and the
+// inverse returns its time slice of h_R * U.  grid (S ceil(K/2), M+1).
+template <typename R, int EPT, int S>
+__global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V,
+                                                        const cplx<R>* __restrict__ H,
+                                                        const cplx<R>* __restrict__ tw,
+                                                        const int2* __restrict__ pairs,
+                                                        const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
-  cg::cluster_group cluster = cg::this_cluster();
   pdl_enter();
   const int j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;  // the same for both blocks of a cluster
-  const int s = (int)cluster.block_rank();
-  const int n = g.n, np = n / 2;
-  const int k1 = 2 * (blockIdx.x / 2), k2 = k1 + 1;
+  if (ls->iter > 0 && j == 0) return;  // the same for every block of a cluster
+  const int n = g.n, np = n / S;
+  const int s = (int)(blockIdx.x % S);
+  cplx<R>* xbuf = sm + fft_smem_elems(np);
+  const int k1 = 2 * (blockIdx.x / S), k2 = k1 + 1;
   const bool has2 = k2 < g.K;
   const int2 mn1 = pairs[k1];
   const int2 mn2 = has2 ? pairs[k2] : mn1;
   const cplx<R>* a = A + (size_t)j * g.N * n;
-  auto x_at = [&](int t) {
+  auto load = [&](int t) {
     return mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
   };
-  auto load = [&](int t) {
-    const cplx<R> u = x_at(t), w = x_at(t + np);
-    cplx<R> y = s ? csub<R>(u, w) : cadd<R>(u, w);
-    if (s) y = cmul<R>(y, tw[t]);  // W^{-t} for the forward (DIR = -1) transform
-    return y;
-  };
-  auto to_smem = [&](int k, cplx<R> y) { sm[pad16(k)] = cmul<R>(y, H[2 * k + s]); };
-  fft_block<R, -1, EPT>(sm, np, tw, 2, load, to_smem);
-  auto from_smem = [&](int k) { return sm[pad16(k)]; };
-  auto keep = [&](int t, cplx<R> z) { sm[pad16(t)] = z; };
-  fft_block<R, +1, EPT>(sm, np, tw, 2, from_smem, keep);
-  cluster.sync();  // both halves z_0, z_1 complete and visible in the cluster
-  const cplx<R>* z0 = cluster.map_shared_rank(sm, 0);
-  const cplx<R>* z1 = cluster.map_shared_rank(sm, 1);
+  auto spectrum = [&](int q, cplx<R> x) { xbuf[q - s * np] = cmul<R>(x, H[q]); };
+  fft_cluster<R, -1, EPT, S>(xbuf, sm, n, tw, load, spectrum);
+  auto own = [&](int q) { return xbuf[q - s * np]; };
   R* v = V + (size_t)j * g.KK * n;
   const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
-  for (int tp = threadIdx.x; tp < np; tp += blockDim.x) {
-    cplx<R> w = tw[tp];
-    w.y = -w.y;  // W^{+t'}
-    cplx<R> z = cmul<R>(w, z1[pad16(tp)]);
-    if (s) z = mk<R>(-z.x, -z.y);
-    const cplx<R> y = cadd<R>(z0[pad16(tp)], z);
-    const int t = tp + s * np;
+  auto store = [&](int t, cplx<R> y) {
     const R u1 = pair_product<R>(a, n, mn1, t);
     if (g.raman_mode == 1) {
       v[(size_t)k1 * n + t] = fK * u1 + fR * y.x;
@@ -237,8 +219,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
         v[(size_t)(g.K + k2) * n + t] = y.y;
       }
     }
-  }
-  cluster.sync();  // the partner may still be reading this block's z
+  };
+  fft_cluster<R, +1, EPT, S>(xbuf, sm, n, tw, own, store);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,7 +353,7 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
-  const int p = blockIdx.x / S, sp = blockIdx.x % S, j = blockIdx.y;
+  const int p = blockIdx.x / S, j = blockIdx.y;
   if (ls->iter > 0 && j == 0) return;
   const int n = g.n;
   const size_t off = ((size_t)j * g.N + p) * n;
@@ -383,7 +365,8 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
     const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
     I[off + q] = cmulc<R>(iX, e[q]);
   };
-  fft_block_split<R, +1, EPT, S>(sm, n, sp, tw, load, store);
+  if (S == 1) fft_block<R, +1, EPT>(sm, n, tw, load, store);
+  else fft_cluster<R, +1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,15 +376,12 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
 //   one element in the working precision, the sums over elements in FP64.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __restrict__ psiR,
-                                                    cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
-                                                    LoopState* ls) {
-  __shared__ double red[32];
-  pdl_enter();
+__device__ __forceinline__ void trapz_sums(const Geo& g, const cplx<R>* __restrict__ psiR, cplx<R>* __restrict__ dpsi,
+                                           const cplx<R>* __restrict__ I, int iter, double& diff, double& nrm) {
   const size_t Nn = (size_t)g.N * g.n;
-  const int iter = ls->iter;
-  double diff = 0.0, nrm = 0.0;
   const R hdz = (R)g.hdz;
+  diff = 0.0;
+  nrm = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
     cplx<R> Ip = I[e];
     cplx<R> acc = mk<R>(0, 0);
@@ -423,6 +403,16 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __rest
     diff += (double)dsum;  // sums over elements in FP64
     nrm += (double)nsum;
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __restrict__ psiR,
+                                                    cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
+                                                    LoopState* ls) {
+  __shared__ double red[32];
+  pdl_enter();
+  double diff, nrm;
+  trapz_sums<R>(g, psiR, dpsi, I, ls->iter, diff, nrm);
   diff = block_sum(diff, red);
   nrm = block_sum(nrm, red);
   if (threadIdx.x == 0) {
@@ -431,13 +421,11 @@ __global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __rest
   }
 }
 
-// Convergence decision after K5 (one thread): eps, stop rule, reset of the
-// sums, and the while-node condition when running inside a graph.  Every
-// path ends the loop after at most max_iter (or fixed_iters) updates.
-static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
-  pdl_enter();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double diff = ls->diff, nrm = ls->nrm;
+// Convergence decision (one thread): eps, stop rule, reset of the sums, and
+// the while-node condition when running inside a graph.  Every path ends the
+// loop after at most max_iter (or fixed_iters) updates.
+__device__ __forceinline__ void decide(LoopState* ls, double diff, double nrm, cudaGraphConditionalHandle h,
+                                       int use_cond) {
   const bool finite = isfinite(diff) && isfinite(nrm);
   const double eps = finite ? (nrm > 0.0 ? sqrt(diff / nrm) : 0.0) : nan("");
   const int it = ls->iter + 1;
@@ -463,6 +451,42 @@ static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int
   ls->diff = 0.0;
   ls->nrm = 0.0;
   if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  pdl_enter();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  decide(ls, ls->diff, ls->nrm, h, use_cond);
+}
+
+// K5 with the convergence decision in the last block to finish (every block
+// adds its sums with atomics; the last one reads them back from L2).  Used by
+// the graph-driven loop, where it saves a kernel per iteration.  Every block
+// reads iter before it arrives, so the last block may update it.
+template <typename R>
+__global__ void __launch_bounds__(256) k_trapz_decide(Geo g, const cplx<R>* __restrict__ psiR,
+                                                      cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
+                                                      LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  pdl_enter();
+  double diff, nrm;
+  trapz_sums<R>(g, psiR, dpsi, I, ls->iter, diff, nrm);
+  diff = block_sum(diff, red);
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ls->diff, diff);
+    atomicAdd(&ls->nrm, nrm);
+    __threadfence();
+    last = atomicAdd(&ls->arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const double dsum = __ldcg(&ls->diff), nsum = __ldcg(&ls->nrm);
+    ls->arrive = 0;
+    decide(ls, dsum, nsum, h, use_cond);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -94,9 +94,11 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_integrand<R, 16, 2>, A, sm));
   CK(cudaFuncSetAttribute(k_integrand<R, 16, 4>, A, sm));
   CK(cudaFuncSetAttribute(k_integrand<R, 32, 1>, A, sm));
+
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, A, sm));
-  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 2>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 4>, A, sm));
   CK(cudaFuncSetAttribute(k_contract<R>, A, sm));
   if (std::is_same<R, float>::value) {
     const int rc = tc_for_each_n([&](auto kern) -> int {
@@ -117,19 +119,20 @@ static int setup_device(int dev) {
 
 // Blocks per transform for K1/K4 (output-residue split) so that a launch
 // fills the 148 SMs: 1, 2 or 4.
-// GMMNLSE_UNSPLIT=1 selects the one-block-per-transform kernels everywhere
-// (the same arithmetic; used to test both variants).
-static inline bool unsplit_forced() {
-  const char* v = getenv("GMMNLSE_UNSPLIT");
+// GMMNLSE_CLUSTER_FFT=1 spreads each transform of a launch that would leave
+// SMs idle over a 2- or 4-block cluster (fft_cluster).  Measured slower than
+// one block per transform at the benchmark sizes (every kernel has a fixed
+// in-GPU cost of a few microseconds and the cluster synchronisations add to
+// it), so it is off by default; the tests run both.
+static inline bool cluster_fft() {
+  const char* v = getenv("GMMNLSE_CLUSTER_FFT");
   return v && v[0] == '1';
 }
 
 static inline int split_for(int transforms, int n) {
-  if (unsplit_forced()) return 1;
-  // only for launches far too small to fill the GPU: each split block reads
-  // the whole input, so for larger launches one block per transform is faster
-  if (transforms < 16 && n >= 128) return 4;
-  if (transforms < 32 && n >= 64) return 2;
+  if (!cluster_fft()) return 1;
+  if (transforms <= 74 && n >= 128) return 4;
+  if (transforms <= 148 && n >= 64) return 2;
   return 1;
 }
 
@@ -161,45 +164,49 @@ static int elementwise_blocks(size_t count) {
   return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
 }
 
-// K1: phase x inverse FFT, split over S blocks per transform
+// bytes of shared memory of a transform of n points over S blocks
+template <typename R> static size_t fft_cluster_smem(int n, int S) {
+  return S == 1 ? fft_smem<R>(n) : fft_smem<R>(n / S) + (size_t)(n / S) * sizeof(cplx<R>);
+}
+
+// K1: phase x inverse FFT; one transform per block or per S-block cluster
 template <typename R>
 static void launch_k1(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
   const int S = split_for(N * (g.M + 1), n), np = n / S, ept = np > 8192 ? 32 : 16;
   const dim3 grid(N * S, g.M + 1);
-  const size_t sm = fft_smem<R>(np);
-  auto args = [&](auto kern) {
-    pdl_launch(kern, grid, dim3(np / ept), sm, s, g, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
-               (const cplx<R>*)jb->E, (cplx<R>*)jb->A, twid<R>(c), (const LoopState*)jb->ls);
+  const size_t sm = fft_cluster_smem<R>(n, S);
+  auto go = [&](auto kern) {
+    pdl_launch_cl(kern, grid, dim3(np / ept), sm, s, S, g, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
+                  (const cplx<R>*)jb->E, (cplx<R>*)jb->A, twid<R>(c), (const LoopState*)jb->ls);
   };
-  if (ept == 32) args(k_ip_to_time<R, 32, 1>);
-  else if (S == 1) args(k_ip_to_time<R, 16, 1>);
-  else if (S == 2) args(k_ip_to_time<R, 16, 2>);
-  else args(k_ip_to_time<R, 16, 4>);
+  if (ept == 32) go(k_ip_to_time<R, 32, 1>);
+  else if (S == 1) go(k_ip_to_time<R, 16, 1>);
+  else if (S == 2) go(k_ip_to_time<R, 16, 2>);
+  else go(k_ip_to_time<R, 16, 4>);
 }
 
-// K2: pair products + Raman convolution; a 2-block cluster per transform
-// pair when one block per pair would leave SMs idle
+// K2: pair products + Raman convolution, a cluster per transform pair when
+// one block per pair would leave SMs idle
 template <typename R>
 static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n;
   const int pp = (c->K + 1) / 2;
-  const bool cl = n >= 64 && pp * (g.M + 1) < 32 && !unsplit_forced();
-  if (cl) {
-    const int np = n / 2;
-    pdl_launch(k_pairs_raman_cl<R, 16>, dim3(2 * pp, g.M + 1), dim3(np / 16), fft_smem<R>(np), s, g,
-               (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
-               (const LoopState*)jb->ls);
+  const int S = split_for(pp * (g.M + 1), n);
+  auto args = [&](auto kern, dim3 grid, int threads, size_t sm, int cl) {
+    pdl_launch_cl(kern, grid, dim3(threads), sm, s, cl, g, (const cplx<R>*)jb->A, (R*)jb->V,
+                  (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const LoopState*)jb->ls);
+  };
+  if (S > 1) {
+    const int np = n / S;
+    if (S == 2) args(k_pairs_raman_cl<R, 16, 2>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
+    else args(k_pairs_raman_cl<R, 16, 4>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
   } else if (n > 8192) {
-    pdl_launch(k_pairs_raman<R, 32>, dim3(pp, g.M + 1), dim3(n / 32), fft_smem<R>(n), s, g,
-               (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
-               (const LoopState*)jb->ls);
+    args(k_pairs_raman<R, 32>, dim3(pp, g.M + 1), n / 32, fft_smem<R>(n), 1);
   } else {
-    pdl_launch(k_pairs_raman<R, 16>, dim3(pp, g.M + 1), dim3(n / 16), fft_smem<R>(n), s, g,
-               (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
-               (const LoopState*)jb->ls);
+    args(k_pairs_raman<R, 16>, dim3(pp, g.M + 1), n / 16, fft_smem<R>(n), 1);
   }
 }
 
@@ -210,22 +217,15 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   const int n = c->n, N = c->N;
   const int S = split_for(N * (g.M + 1), n), np = n / S, ept = np > 8192 ? 32 : 16;
   const dim3 grid(N * S, g.M + 1);
-  const size_t sm = fft_smem<R>(np);
-  auto args = [&](auto kern) {
-    pdl_launch(kern, grid, dim3(np / ept), sm, s, g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E,
-               (const R*)c->fac, (cplx<R>*)jb->I, twid<R>(c), (const LoopState*)jb->ls);
+  const size_t sm = fft_cluster_smem<R>(n, S);
+  auto go = [&](auto kern) {
+    pdl_launch_cl(kern, grid, dim3(np / ept), sm, s, S, g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E,
+                  (const R*)c->fac, (cplx<R>*)jb->I, twid<R>(c), (const LoopState*)jb->ls);
   };
-  if (ept == 32) args(k_integrand<R, 32, 1>);
-  else if (S == 1) args(k_integrand<R, 16, 1>);
-  else if (S == 2) args(k_integrand<R, 16, 2>);
-  else args(k_integrand<R, 16, 4>);
-}
-
-template <typename R>
-static void launch_k5(gm_job* jb, const Geo& g, cudaStream_t s) {
-  const size_t Nn = (size_t)jb->ctx->N * jb->ctx->n;
-  pdl_launch(k_trapz_norm<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, (const cplx<R>*)jb->psiR,
-             (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I, jb->ls);
+  if (ept == 32) go(k_integrand<R, 32, 1>);
+  else if (S == 1) go(k_integrand<R, 16, 1>);
+  else if (S == 2) go(k_integrand<R, 16, 2>);
+  else go(k_integrand<R, 16, 4>);
 }
 
 // K3 on the tensor cores (mixed precision): pack V to BF16 hi/lo, then the
@@ -269,6 +269,17 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
   }
 }
 
+// K5 with the convergence decision in its last block
+template <typename R>
+static void launch_k5(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  const size_t Nn = (size_t)jb->ctx->N * jb->ctx->n;
+  pdl_launch(k_trapz_decide<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, (const cplx<R>*)jb->psiR,
+             (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I, jb->ls, h, use_cond);
+}
+
+// One MPA iteration (Sec. III.D): transform to the time domain, pair
+// products and Raman convolution, coupling contraction, integrand, and the
+// trapezoid with the convergence decision.
 template <typename R>
 static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   gmmnlse_ctx* c = jb->ctx;
@@ -277,8 +288,7 @@ static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraph
   if (c->tc) launch_tc<R>(jb, g, s);
   else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
   launch_k4<R>(jb, g, s);
-  launch_k5<R>(jb, g, s);
-  pdl_launch(k_decide, dim3(1), dim3(32), 0, s, jb->ls, h, use_cond);
+  launch_k5<R>(jb, g, s, h, use_cond);
 }
 
 template <typename R>
@@ -310,10 +320,16 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   // long-step body: re-arm the iteration loop
   CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   k_step_begin<<<1, 32, 0, cs>>>(hIter);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd));
+  cudaGraphNode_t nBegin = nd == 1 ? deps[0] : nullptr;
   CK(cudaStreamEndCapture(cs, &gS));
-  cudaGraphNode_t nBegin;
-  size_t cnt = 1;
-  CK(cudaGraphGetNodes(gS, &nBegin, &cnt));
+  if (!nBegin) {
+    gm_set_last_error_text("graph capture: unexpected dependency set");
+    return GMMNLSE_E_CUDA;
+  }
   cudaGraphNodeParams ci = {};
   ci.type = cudaGraphNodeTypeConditional;
   ci.conditional.handle = hIter;
@@ -322,7 +338,7 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   cudaGraphNode_t nIter;
   CK(cudaGraphAddNode(&nIter, gS, &nBegin, nullptr, 1, &ci));
   cudaGraph_t gI = ci.conditional.phGraph_out[0];
-  // iteration body: K1..K5
+  // iteration body: K1 .. K5
   CK(cudaStreamBeginCaptureToGraph(cs, gI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   launch_iteration<R>(jb, g, cs, hIter, 1);
   CK(cudaStreamEndCapture(cs, &gI));
@@ -545,7 +561,7 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
           else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
           break;
         case 3: launch_k4<R>(jb, g, s); break;
-        case 4: launch_k5<R>(jb, g, s); break;
+        case 4: launch_k5<R>(jb, g, s, 0, 0); break;
         default:
           k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR,
                                                                (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls);

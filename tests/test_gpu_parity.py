@@ -75,13 +75,12 @@ def test_linear_propagation_fp64_matches_oracle():
     assert rel(out, ref) < 1e-12
 
 
-@pytest.fixture(params=["split", "unsplit"])
+@pytest.fixture(params=["one_block", "cluster"])
 def fft_variant(request, monkeypatch):
-    """Run with the launch-time choice of kernels (transforms split over 2 or
-    4 blocks, Raman transform pairs on 2-block clusters, when a launch would
-    otherwise leave SMs idle) and with one block per transform everywhere."""
-    if request.param == "unsplit":
-        monkeypatch.setenv("GMMNLSE_UNSPLIT", "1")
+    """Run with one block per transform (default) and with transforms of small
+    launches spread over 2- or 4-block clusters (GMMNLSE_CLUSTER_FFT=1)."""
+    if request.param == "cluster":
+        monkeypatch.setenv("GMMNLSE_CLUSTER_FFT", "1")
     return request.param
 
 
