@@ -6,12 +6,14 @@
 
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "../../include/gmmnlse.h"
 #include "kernels.cuh"
+#include "contract_tile.cuh"
 
 // ---------------------------------------------------------------------------
 // Workspace of one propagation in flight
@@ -23,7 +25,7 @@ struct gm_job {
   void* psiR = nullptr;     // [N][n] cplx<R> (aliases psi0 in FP64)
   void* dpsi = nullptr;     // [M][N][n]
   void* A = nullptr;        // [M+1][N][n]
-  void* V = nullptr;        // [M+1][KK][n]
+  void* V = nullptr;        // Y = h_R * U: [M+1][K][n]
   void* NL = nullptr;       // [M+1][N][n]
   void* I = nullptr;        // [M+1][N][n]
   void* E = nullptr;        // [M+1][N][n]
@@ -31,6 +33,7 @@ struct gm_job {
   double2* io = nullptr;    // [2][N][n] staging / FP64 FFT scratch
   int* flag = nullptr;
   gm::LoopState* ls = nullptr;      // device
+  double2* part = nullptr;          // [TRAPZ_MAX_BLOCKS] per-block sums of K5
   gm::LoopState* h_ls = nullptr;    // pinned host mirror
   double2* h_io = nullptr;      // pinned host staging [N][n]
   cudaStream_t cap = nullptr;   // private stream for graph capture
@@ -72,8 +75,8 @@ struct gmmnlse_ctx {
   __nv_bfloat16* Ghi = nullptr;  // [KKp/8][tc_rows][8]
   __nv_bfloat16* Glo = nullptr;
   CUtensorMap mapGhi, mapGlo;
-  int contract_threads = 128;
-  size_t contract_smem = 0;
+  void* Gt = nullptr;            // [KKt][Pt] R: G transposed, zero-padded (N > 8, CUDA cores)
+  int KKt = 0, Pt = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   gm_job* job = nullptr;        // workspace of gmmnlse_propagate
@@ -159,11 +162,16 @@ static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const
     case 7: launch_contract_n<R, 7>(g, c, A, V, NL, ls, s); return;
     case 8: launch_contract_n<R, 8>(g, c, A, V, NL, ls, s); return;
     default: {
-      const int CT = c->contract_threads;
       const size_t pts = (size_t)(g.M + 1) * g.n;
-      pdl_launch(gm::k_contract<R>, dim3((unsigned)((pts + CT - 1) / CT)), dim3(CT), c->contract_smem, s, g,
-                 (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (const int2*)c->rows, (const int2*)c->pairs,
-                 (gm::cplx<R>*)NL, ls);
+      const dim3 grid((unsigned)((pts + gm::TileCfg<R>::TP - 1) / gm::TileCfg<R>::TP));
+      const size_t smem = gm::contract_tile_smem<R>(c->N);
+      auto go = [&](auto kern) {
+        pdl_launch(kern, grid, dim3(256), smem, s, g, (const gm::cplx<R>*)A, (const R*)V, (const R*)c->Gt, c->KKt,
+                   c->Pt, (const int2*)c->rows, (const int2*)c->pairs, (gm::cplx<R>*)NL, ls);
+      };
+      if (c->raman_mode == 0) go(gm::k_contract_tile<R, 0>);
+      else if (c->raman_mode == 1) go(gm::k_contract_tile<R, 1>);
+      else go(gm::k_contract_tile<R, 2>);
     }
   }
 }

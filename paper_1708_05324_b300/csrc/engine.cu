@@ -150,6 +150,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->H);
   cudaFree(c->fac);
   cudaFree(c->G);
+  cudaFree(c->Gt);
   cudaFree(c->rows);
   cudaFree(c->pairs);
   cudaFree(c->Ghi);
@@ -164,6 +165,13 @@ static int upload_tables(gmmnlse_ctx* c, const std::vector<double>& Gd) {
   for (size_t i = 0; i < Gd.size(); ++i) Gr[i] = (R)Gd[i];
   CK(cudaMalloc(&c->G, Gr.size() * sizeof(R) + 16));
   CK(cudaMemcpy(c->G, Gr.data(), Gr.size() * sizeof(R), cudaMemcpyHostToDevice));
+  if (c->Pt > 0) {
+    std::vector<R> Gt((size_t)c->KKt * c->Pt, (R)0);
+    for (int r = 0; r < c->P; ++r)
+      for (int k = 0; k < c->KK; ++k) Gt[(size_t)k * c->Pt + r] = (R)Gd[(size_t)r * c->KK + k];
+    CK(cudaMalloc(&c->Gt, Gt.size() * sizeof(R)));
+    CK(cudaMemcpy(c->Gt, Gt.data(), Gt.size() * sizeof(R), cudaMemcpyHostToDevice));
+  }
   CK(cudaMalloc(&c->H, (size_t)c->n * sizeof(cplx<R>)));
   // integrand prefactor gamma0 s(w_q), s = 1 + w_q/omega0 with self-steepening
   const int n = c->n;
@@ -273,26 +281,13 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     c->tc_rows = (c->P + NB - 1) / NB * NB;
   }
 
-  // contraction kernel shared memory; shrink the block until it fits
-  int maxsm = 0;
-  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, prm->device);
-  const size_t rsz = fp64 ? 8 : 4;
-  int T = 128;
-  auto need = [&](int t) {
-    return (size_t)c->P * 8 + ((size_t)c->P * c->KK + (size_t)(4 * N + c->KK) * t) * rsz;
-  };
-  while (T > 32 && need(T) > (size_t)maxsm) T /= 2;
-  if (need(T) > (size_t)maxsm) {
-    // the CUDA-core contraction does not fit; only the tensor-core one can run
-    if (!c->tc) {
-      delete c;
-      return GMMNLSE_E_UNSUPPORTED;
-    }
-    c->contract_threads = 0;
-    c->contract_smem = 0;
-  } else {
-    c->contract_threads = T;
-    c->contract_smem = need(T);
+  // CUDA-core tiled contraction (N > 8): G transposed, padded to whole tiles
+  if (N > 8) {
+    const int KC = TileCfg<float>::KC, TR = TileCfg<float>::TR;
+    static_assert(TileCfg<float>::KC == TileCfg<double>::KC && TileCfg<float>::TR == TileCfg<double>::TR,
+                  "one padding for both precisions");
+    c->KKt = (c->KK + KC - 1) / KC * KC;
+    c->Pt = (c->P + TR - 1) / TR * TR;
   }
 
   // device copies
@@ -383,9 +378,9 @@ static size_t job_bytes(const gmmnlse_ctx* c, int M) {
   if (!c->fp64) b += Nn * cs;                    // psiR
   b += (size_t)M * Nn * cs;                      // dpsi
   b += 4 * (size_t)(M + 1) * Nn * cs;            // A, NL, I, E
-  if (c->raman_mode) b += (size_t)(M + 1) * c->KK * c->n * rs;  // V
+  if (c->raman_mode) b += (size_t)(M + 1) * c->K * c->n * rs;  // Y = h_R * U
   b += 2 * Nn * 16 * 2;                          // EM64, io
-  b += sizeof(LoopState) + 64;
+  b += sizeof(LoopState) + 64 + sizeof(double2) * TRAPZ_MAX_BLOCKS;
   if (c->tc) b += (size_t)2 * c->KKp * (M + 1) * c->n * 2;  // BF16 hi/lo operand
   return b;
 }
@@ -412,6 +407,7 @@ static void free_job(gm_job* jb) {
   cudaFree(jb->Vhi);
   cudaFree(jb->Vlo);
   cudaFree(jb->ls);
+  cudaFree(jb->part);
   cudaFreeHost(jb->h_ls);
   cudaFreeHost(jb->h_io);
   if (jb->cap) cudaStreamDestroy(jb->cap);
@@ -495,11 +491,12 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
   al(&jb->NL, (size_t)(M + 1) * Nn * cs);
   al(&jb->I, (size_t)(M + 1) * Nn * cs);
   al(&jb->E, (size_t)(M + 1) * Nn * cs);
-  if (c->raman_mode) al(&jb->V, (size_t)(M + 1) * c->KK * c->n * rs);
+  if (c->raman_mode) al(&jb->V, (size_t)(M + 1) * c->K * c->n * rs);
   al((void**)&jb->EM64, 2 * Nn * 16);
   al((void**)&jb->io, 2 * Nn * 16);
   al((void**)&jb->flag, sizeof(int));
   al((void**)&jb->ls, sizeof(LoopState));
+  al((void**)&jb->part, sizeof(double2) * TRAPZ_MAX_BLOCKS);
   if (c->tc) {
     al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * 2);
     al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * 2);

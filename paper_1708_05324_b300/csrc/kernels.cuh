@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -40,7 +41,7 @@ struct LoopState {
   int hist[33];
   double spec[4];          // sum |psi0|^2, photon sum (filled by k_spec_sums)
   unsigned tc_err;         // a tensor-core contraction wait timed out
-  unsigned arrive;         // blocks of k_trapz_decide that have added their sums
+  unsigned arrive;         // blocks of k_trapz<R, true> that have added their sums
 };
 
 struct Geo {
@@ -128,13 +129,14 @@ __device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, 
 }
 
 // ---------------------------------------------------------------------------
-// K2: pair products and the Raman convolution h_R * U_k for two pairs at once
-// (U_k1 + i U_k2 is transformed, multiplied by H = (dt/n) DFT(h_R), and
-// transformed back; h_R is real so the real and imaginary parts stay apart).
+// K2: pair products and the Raman convolution Y_k = h_R * U_k for two pairs
+// at once (U_k1 + i U_k2 is transformed, multiplied by H = (dt/n) DFT(h_R),
+// and transformed back; h_R is real so the real and imaginary parts stay
+// apart).  Only Y [M+1][K][n] is written: the contraction forms U from A.
 // grid (ceil(K/2), M+1)
 // ---------------------------------------------------------------------------
 template <typename R, int EPT>
-__global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V,
+__global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
                                                       const cplx<R>* __restrict__ H,
                                                       const cplx<R>* __restrict__ tw,
                                                       const int2* __restrict__ pairs,
@@ -150,27 +152,18 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
   const int2 mn1 = pairs[k1];
   const int2 mn2 = has2 ? pairs[k2] : mn1;
   const cplx<R>* a = A + (size_t)j * g.N * n;
-  auto load = [&](int t) {
-    return mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
-  };
-  auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
-  fft_block<R, -1, EPT>(sm, n, tw, load, to_smem);
+  // the pair products are staged in shared memory first: the transform's
+  // first pass then reads no global memory, which keeps its registers free
+#pragma unroll 4
+  for (int t = threadIdx.x; t < n; t += blockDim.x)
+    sm[pad16(t)] = mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
   auto from_smem = [&](int q) { return sm[pad16(q)]; };
-  R* v = V + (size_t)j * g.KK * n;
-  const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
+  auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
+  fft_block<R, -1, EPT>(sm, n, tw, from_smem, to_smem);
+  R* y1 = Y + ((size_t)j * g.K + k1) * n;
   auto store = [&](int t, cplx<R> y) {
-    const R u1 = pair_product<R>(a, n, mn1, t);
-    if (g.raman_mode == 1) {
-      v[(size_t)k1 * n + t] = fK * u1 + fR * y.x;
-      if (has2) v[(size_t)k2 * n + t] = fK * pair_product<R>(a, n, mn2, t) + fR * y.y;
-    } else {
-      v[(size_t)k1 * n + t] = u1;
-      v[(size_t)(g.K + k1) * n + t] = y.x;
-      if (has2) {
-        v[(size_t)k2 * n + t] = pair_product<R>(a, n, mn2, t);
-        v[(size_t)(g.K + k2) * n + t] = y.y;
-      }
-    }
+    y1[t] = y.x;
+    if (has2) y1[n + t] = y.y;
   };
   fft_block<R, +1, EPT>(sm, n, tw, from_smem, store);
 }
@@ -180,7 +173,7 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
 // spectrum slice it ends up holding is multiplied by H in place, and the
 // inverse returns its time slice of h_R * U.  grid (S ceil(K/2), M+1).
 template <typename R, int EPT, int S>
-__global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ V,
+__global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
                                                         const cplx<R>* __restrict__ H,
                                                         const cplx<R>* __restrict__ tw,
                                                         const int2* __restrict__ pairs,
@@ -204,93 +197,40 @@ __global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __
   auto spectrum = [&](int q, cplx<R> x) { xbuf[q - s * np] = cmul<R>(x, H[q]); };
   fft_cluster<R, -1, EPT, S>(xbuf, sm, n, tw, load, spectrum);
   auto own = [&](int q) { return xbuf[q - s * np]; };
-  R* v = V + (size_t)j * g.KK * n;
-  const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
+  R* y1 = Y + ((size_t)j * g.K + k1) * n;
   auto store = [&](int t, cplx<R> y) {
-    const R u1 = pair_product<R>(a, n, mn1, t);
-    if (g.raman_mode == 1) {
-      v[(size_t)k1 * n + t] = fK * u1 + fR * y.x;
-      if (has2) v[(size_t)k2 * n + t] = fK * pair_product<R>(a, n, mn2, t) + fR * y.y;
-    } else {
-      v[(size_t)k1 * n + t] = u1;
-      v[(size_t)(g.K + k1) * n + t] = y.x;
-      if (has2) {
-        v[(size_t)k2 * n + t] = pair_product<R>(a, n, mn2, t);
-        v[(size_t)(g.K + k2) * n + t] = y.y;
-      }
-    }
+    y1[t] = y.x;
+    if (has2) y1[n + t] = y.y;
   };
   fft_cluster<R, +1, EPT, S>(xbuf, sm, n, tw, own, store);
 }
 
 // ---------------------------------------------------------------------------
 // K3: NL_p(t) = sum_l A_l R_pl, R_pl = sum_k G[(p,l)][k] V_k  (Eq. 1 bracket,
-// symmetry-reduced: rows (p <= l), columns (m <= n) or [U; h*U]).
-// One thread per (j, t); per-thread operands in shared memory.
+// symmetry-reduced: rows (p <= l), columns (m <= n) or [U; h*U]).  V is
+// formed from A and Y = h_R * U:
+//   raman_mode 0: V = U;  1: V = (1 - fR) U + fR Y;  2: V = [U; Y].
+// For N > 8 the tiled GEMM of contract_tile.cuh (CUDA cores) or
+// tc_contract.cuh (tensor cores) computes it.
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void k_contract(Geo g, const cplx<R>* __restrict__ A, const R* __restrict__ V,
-                           const R* __restrict__ Gm, const int2* __restrict__ rows,
-                           const int2* __restrict__ pairs, cplx<R>* __restrict__ NL,
-                           const LoopState* __restrict__ ls) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int N = g.N, KK = g.KK, P = g.P, n = g.n;
-  int2* rs = reinterpret_cast<int2*>(smraw);  // [P]
-  R* Gs = reinterpret_cast<R*>(rs + P);       // [P][KK]
-  R* as = Gs + P * KK;                         // [2N][T]
-  R* vs = as + 2 * N * T;                      // [KK][T]
-  R* ns = vs + KK * T;                         // [2N][T]
-  for (int i = tid; i < P * KK; i += T) Gs[i] = Gm[i];
-  for (int i = tid; i < P; i += T) rs[i] = rows[i];
-  pdl_enter();
-  __syncthreads();
-  const size_t pt = (size_t)blockIdx.x * T + tid;
-  const size_t npts = (size_t)(g.M + 1) * n;
-  if (pt >= npts) return;
-  const int j = (int)(pt / n), t = (int)(pt - (size_t)j * n);
-  if (ls->iter > 0 && j == 0) return;
-  const cplx<R>* a = A + (size_t)j * N * n;
-  for (int l = 0; l < N; ++l) {
-    const cplx<R> x = a[(size_t)l * n + t];
-    as[(2 * l) * T + tid] = x.x;
-    as[(2 * l + 1) * T + tid] = x.y;
-    ns[(2 * l) * T + tid] = (R)0;
-    ns[(2 * l + 1) * T + tid] = (R)0;
-  }
-  if (g.raman_mode == 0) {
-    for (int k = 0; k < KK; ++k) vs[k * T + tid] = pair_product<R>(a, n, pairs[k], t);
-  } else {
-    const R* v = V + (size_t)j * KK * n;
-    for (int k = 0; k < KK; ++k) vs[k * T + tid] = v[(size_t)k * n + t];
-  }
-  for (int r = 0; r < P; ++r) {
-    const R* gr = Gs + r * KK;
-    R acc = (R)0;
-    for (int k = 0; k < KK; ++k) acc += gr[k] * vs[k * T + tid];
-    const int2 pl = rs[r];
-    ns[(2 * pl.x) * T + tid] += as[(2 * pl.y) * T + tid] * acc;
-    ns[(2 * pl.x + 1) * T + tid] += as[(2 * pl.y + 1) * T + tid] * acc;
-    if (pl.x != pl.y) {
-      ns[(2 * pl.y) * T + tid] += as[(2 * pl.x) * T + tid] * acc;
-      ns[(2 * pl.y + 1) * T + tid] += as[(2 * pl.x + 1) * T + tid] * acc;
-    }
-  }
-  cplx<R>* out = NL + (size_t)j * N * n;
-  for (int p = 0; p < N; ++p) out[(size_t)p * n + t] = mk<R>(ns[(2 * p) * T + tid], ns[(2 * p + 1) * T + tid]);
-}
-
 // K3 for N <= 8: the same contraction with every operand in registers
-// (compile-time N) and the reduced coupling matrix read from shared memory
-// as a broadcast.  One thread per (j, t).
+// (compile-time N and raman_mode); the reduced coupling matrix is read from
+// shared memory as a broadcast, 16 bytes per load (rows padded to KKP).
+// One thread per (j, t).
 template <typename R, int N, int MODE>
 __global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __restrict__ A,
-                                                      const R* __restrict__ V, const R* __restrict__ Gm,
+                                                      const R* __restrict__ Y, const R* __restrict__ Gm,
                                                       cplx<R>* __restrict__ NL, const LoopState* __restrict__ ls) {
   constexpr int K = N * (N + 1) / 2;
   constexpr int KK = MODE == 2 ? 2 * K : K;
-  __shared__ R Gs[K * KK];
-  for (int i = threadIdx.x; i < K * KK; i += blockDim.x) Gs[i] = Gm[i];
+  constexpr int VW = 16 / (int)sizeof(R);             // values per 16-byte load
+  constexpr int KKP = (KK + VW - 1) / VW * VW;        // padded row length
+  using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+  __shared__ __align__(16) R Gs[K * KKP];
+  for (int i = threadIdx.x; i < K * KKP; i += blockDim.x) {
+    const int r = i / KKP, k = i - r * KKP;
+    Gs[i] = k < KK ? Gm[r * KK + k] : (R)0;
+  }
   pdl_enter();
   __syncthreads();
   const int n = g.n;
@@ -303,18 +243,23 @@ __global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __re
 #pragma unroll
   for (int l = 0; l < N; ++l) av[l] = a[(size_t)l * n];
   R v[KK];
-  if (MODE == 0) {
+  {
+    const R* yp = Y + (size_t)j * K * n + t;
+    const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
     int k = 0;
 #pragma unroll
     for (int m = 0; m < N; ++m)
 #pragma unroll
-      for (int q = m; q < N; ++q, ++k)
-        v[k] = (m == q) ? av[m].x * av[m].x + av[m].y * av[m].y
-                        : (R)2 * (av[m].x * av[q].x + av[m].y * av[q].y);
-  } else {
-    const R* vp = V + (size_t)j * KK * n + t;
-#pragma unroll
-    for (int k = 0; k < KK; ++k) v[k] = vp[(size_t)k * n];
+      for (int q = m; q < N; ++q, ++k) {
+        const R u = (m == q) ? av[m].x * av[m].x + av[m].y * av[m].y
+                             : (R)2 * (av[m].x * av[q].x + av[m].y * av[q].y);
+        if (MODE == 0) v[k] = u;
+        else if (MODE == 1) v[k] = fK * u + fR * yp[(size_t)k * n];
+        else {
+          v[k] = u;
+          v[K + k] = yp[(size_t)k * n];
+        }
+      }
   }
   cplx<R> nl[N];
 #pragma unroll
@@ -326,7 +271,13 @@ __global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __re
     for (int l = p; l < N; ++l, ++r) {
       R acc = (R)0;
 #pragma unroll
-      for (int k = 0; k < KK; ++k) acc += Gs[r * KK + k] * v[k];
+      for (int k4 = 0; k4 < KKP / VW; ++k4) {
+        const V16 w = *reinterpret_cast<const V16*>(Gs + r * KKP + k4 * VW);
+        const R* wv = reinterpret_cast<const R*>(&w);
+#pragma unroll
+        for (int i = 0; i < VW; ++i)
+          if (k4 * VW + i < KK) acc += wv[i] * v[k4 * VW + i];
+      }
       nl[p].x += av[l].x * acc;
       nl[p].y += av[l].y * acc;
       if (l != p) {
@@ -369,58 +320,6 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
   else fft_cluster<R, +1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
 }
 
-// ---------------------------------------------------------------------------
-// K5: trapezoid over z' and the convergence sums (Sec. III.D)
-//   dpsi_j <- (dz/2) sum_{k=1..j} (I_{k-1} + I_k),
-//   diff += |new - old|^2, nrm += |psi0 + new|^2 over j, p, w: the terms of
-//   one element in the working precision, the sums over elements in FP64.
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void trapz_sums(const Geo& g, const cplx<R>* __restrict__ psiR, cplx<R>* __restrict__ dpsi,
-                                           const cplx<R>* __restrict__ I, int iter, double& diff, double& nrm) {
-  const size_t Nn = (size_t)g.N * g.n;
-  const R hdz = (R)g.hdz;
-  diff = 0.0;
-  nrm = 0.0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
-    cplx<R> Ip = I[e];
-    cplx<R> acc = mk<R>(0, 0);
-    const cplx<R> p0 = psiR[e];
-    R dsum = 0, nsum = 0;  // this element's terms in the working precision
-#pragma unroll 4
-    for (int j = 1; j <= g.M; ++j) {
-      const cplx<R> Ij = I[(size_t)j * Nn + e];
-      acc = cadd<R>(acc, cscale<R>(cadd<R>(Ip, Ij), hdz));
-      Ip = Ij;
-      cplx<R>* slot = dpsi + (size_t)(j - 1) * Nn + e;
-      const cplx<R> old = iter > 0 ? *slot : mk<R>(0, 0);
-      const R dx = acc.x - old.x, dy = acc.y - old.y;
-      dsum += dx * dx + dy * dy;
-      const R px = p0.x + acc.x, py = p0.y + acc.y;
-      nsum += px * px + py * py;
-      *slot = acc;
-    }
-    diff += (double)dsum;  // sums over elements in FP64
-    nrm += (double)nsum;
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_trapz_norm(Geo g, const cplx<R>* __restrict__ psiR,
-                                                    cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
-                                                    LoopState* ls) {
-  __shared__ double red[32];
-  pdl_enter();
-  double diff, nrm;
-  trapz_sums<R>(g, psiR, dpsi, I, ls->iter, diff, nrm);
-  diff = block_sum(diff, red);
-  nrm = block_sum(nrm, red);
-  if (threadIdx.x == 0) {
-    atomicAdd(&ls->diff, diff);
-    atomicAdd(&ls->nrm, nrm);
-  }
-}
-
 // Convergence decision (one thread): eps, stop rule, reset of the sums, and
 // the while-node condition when running inside a graph.  Every path ends the
 // loop after at most max_iter (or fixed_iters) updates.
@@ -459,33 +358,117 @@ static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int
   decide(ls, ls->diff, ls->nrm, h, use_cond);
 }
 
-// K5 with the convergence decision in the last block to finish (every block
-// adds its sums with atomics; the last one reads them back from L2).  Used by
-// the graph-driven loop, where it saves a kernel per iteration.  Every block
-// reads iter before it arrives, so the last block may update it.
-template <typename R>
-__global__ void __launch_bounds__(256) k_trapz_decide(Geo g, const cplx<R>* __restrict__ psiR,
-                                                      cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I,
-                                                      LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
-  __shared__ double red[32];
+// ---------------------------------------------------------------------------
+// K5: trapezoid over z' and the convergence sums (Sec. III.D)
+//   dpsi_j <- (dz/2) sum_{k=1..j} (I_{k-1} + I_k),
+//   diff = sum |new - old|^2, nrm = sum |psi0 + new|^2 over j, p, w: the
+//   terms of one element in the working precision, the sums over elements
+//   and blocks in FP64.
+// One thread per element sweeps j in order; its loads are issued TRAPZ_JC
+// substeps at a time (I_j and the previous dpsi_j into registers), so a
+// long step of M <= TRAPZ_JC costs one round trip to L2.  Each block writes
+// its two sums to part[blockIdx.x]; the last block to finish adds them in a
+// fixed order (the result does not depend on block timing) and, with
+// DECIDE, takes the convergence decision, else leaves the sums in
+// ls->diff / ls->nrm.  Every block reads iter before it arrives, so the last
+// one may update it.
+// ---------------------------------------------------------------------------
+constexpr int TRAPZ_T = 256;
+constexpr int TRAPZ_MAX_BLOCKS = 148 * 8;
+template <typename R> struct TrapzJC { static constexpr int value = sizeof(R) == 4 ? 16 : 8; };
+
+inline int trapz_blocks(size_t Nn) {
+  const size_t b = (Nn + TRAPZ_T - 1) / TRAPZ_T;
+  return (int)(b < 1 ? 1 : (b > (size_t)TRAPZ_MAX_BLOCKS ? TRAPZ_MAX_BLOCKS : b));
+}
+
+// Sum of (a, b) over the block (any shape, at most 32 warps); valid in
+// thread 0.  red: 64 doubles.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nw = (blockDim.x * blockDim.y + 31) >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if ((tid & 31) == 0) {
+    red[tid >> 5] = a;
+    red[32 + (tid >> 5)] = b;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    a = tid < nw ? red[tid] : 0.0;
+    b = tid < nw ? red[32 + tid] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+}
+
+template <typename R, bool DECIDE>
+__global__ void __launch_bounds__(TRAPZ_T) k_trapz(Geo g, const cplx<R>* __restrict__ psiR, cplx<R>* __restrict__ dpsi,
+                                                   const cplx<R>* __restrict__ I, LoopState* ls, double2* part,
+                                                   cudaGraphConditionalHandle h, int use_cond) {
+  constexpr int JC = TrapzJC<R>::value;
+  __shared__ double red[64];
   __shared__ bool last;
   pdl_enter();
-  double diff, nrm;
-  trapz_sums<R>(g, psiR, dpsi, I, ls->iter, diff, nrm);
-  diff = block_sum(diff, red);
-  nrm = block_sum(nrm, red);
-  if (threadIdx.x == 0) {
-    atomicAdd(&ls->diff, diff);
-    atomicAdd(&ls->nrm, nrm);
+  const size_t Nn = (size_t)g.N * g.n;
+  const int iter = ls->iter, M = g.M;
+  const int tid = threadIdx.x;
+  const R hdz = (R)g.hdz;
+  double diff = 0.0, nrm = 0.0;
+  for (size_t e = (size_t)blockIdx.x * TRAPZ_T + tid; e < Nn; e += (size_t)gridDim.x * TRAPZ_T) {
+    const cplx<R> p0 = psiR[e];
+    cplx<R> Ip = I[e];
+    cplx<R> acc = mk<R>(0, 0);
+    R dsum = 0, nsum = 0;  // this element's terms in the working precision
+    for (int j0 = 1; j0 <= M; j0 += JC) {
+      cplx<R> ij[JC], old[JC];
+#pragma unroll
+      for (int i = 0; i < JC; ++i) {
+        const int j = j0 + i;
+        ij[i] = j <= M ? I[(size_t)j * Nn + e] : mk<R>(0, 0);
+        old[i] = (j <= M && iter > 0) ? dpsi[(size_t)(j - 1) * Nn + e] : mk<R>(0, 0);
+      }
+#pragma unroll
+      for (int i = 0; i < JC; ++i) {
+        const int j = j0 + i;
+        if (j > M) break;
+        acc = cadd<R>(acc, cscale<R>(cadd<R>(Ip, ij[i]), hdz));
+        Ip = ij[i];
+        const R dx = acc.x - old[i].x, dy = acc.y - old[i].y;
+        dsum += dx * dx + dy * dy;
+        const R px = p0.x + acc.x, py = p0.y + acc.y;
+        nsum += px * px + py * py;
+        dpsi[(size_t)(j - 1) * Nn + e] = acc;
+      }
+    }
+    diff += (double)dsum;
+    nrm += (double)nsum;
+  }
+  block_sum2(diff, nrm, red);
+  if (tid == 0) {
+    part[blockIdx.x] = make_double2(diff, nrm);
     __threadfence();
     last = atomicAdd(&ls->arrive, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const double dsum = __ldcg(&ls->diff), nsum = __ldcg(&ls->nrm);
+  if (!last) return;
+  __threadfence();
+  diff = 0.0;
+  nrm = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += TRAPZ_T) {
+    const double2 v = __ldcg(&part[b]);
+    diff += v.x;
+    nrm += v.y;
+  }
+  block_sum2(diff, nrm, red);
+  if (tid == 0) {
     ls->arrive = 0;
-    decide(ls, dsum, nsum, h, use_cond);
+    if (DECIDE) {
+      decide(ls, diff, nrm, h, use_cond);
+    } else {
+      ls->diff = diff;
+      ls->nrm = nrm;
+    }
   }
 }
 

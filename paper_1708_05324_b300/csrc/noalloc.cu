@@ -70,8 +70,10 @@ static int setup_device(int dev, unsigned char** out) {
     if (!rc) rc = set_attrs<float, 32>(maxsm);
     if (!rc) rc = set_attrs<double, 16>(maxsm);
     if (rc) return rc;
-    CKN(cudaFuncSetAttribute(k_contract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CKN(cudaFuncSetAttribute(k_contract<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    for (auto kern : {k_contract_tile<float, 0>, k_contract_tile<float, 1>, k_contract_tile<float, 2>})
+      CKN(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    for (auto kern : {k_contract_tile<double, 0>, k_contract_tile<double, 1>, k_contract_tile<double, 2>})
+      CKN(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
@@ -100,6 +102,7 @@ struct Work {
   double2 *EM64, *io;
   int* flag;
   LoopState* ls;
+  double2* part;  // per-block sums of K5
 };
 
 template <typename R> static size_t layout(const gmmnlse_ctx* c, int M, unsigned char* base, Work* w) {
@@ -113,11 +116,12 @@ template <typename R> static size_t layout(const gmmnlse_ctx* c, int M, unsigned
   w->NL = cv.take<cplx<R>>((size_t)(M + 1) * Nn);
   w->I = cv.take<cplx<R>>((size_t)(M + 1) * Nn);
   w->E = cv.take<cplx<R>>((size_t)(M + 1) * Nn);
-  w->V = c->raman_mode ? cv.take<R>((size_t)(M + 1) * c->KK * c->n) : nullptr;
+  w->V = c->raman_mode ? cv.take<R>((size_t)(M + 1) * c->K * c->n) : nullptr;
   w->EM64 = cv.take<double2>(2 * Nn);
   w->io = cv.take<double2>(2 * Nn);
   w->flag = cv.take<int>(1);
   w->ls = cv.take<LoopState>(1);
+  w->part = cv.take<double2>(TRAPZ_MAX_BLOCKS);
   return cv.off;
 }
 
@@ -219,8 +223,8 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
       launch_contract<R>(g, c, w.A, w.V, w.NL, w.ls, s);
       k_integrand<R, EPT, 1><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.NL, (const cplx<R>*)w.E, (const R*)c->fac,
                                                 (cplx<R>*)w.I, tw, w.ls);
-      k_trapz_norm<R><<<blocks_for(Nn), 256, 0, s>>>(g, (const cplx<R>*)w.psiR, (cplx<R>*)w.dpsi,
-                                                     (const cplx<R>*)w.I, w.ls);
+      k_trapz<R, false><<<trapz_blocks(Nn), TRAPZ_T, 0, s>>>(g, (const cplx<R>*)w.psiR, (cplx<R>*)w.dpsi,
+                                                             (const cplx<R>*)w.I, w.ls, w.part, 0, 0);
       k_decide<<<1, 32, 0, s>>>(w.ls, 0, 0);
       CKN(cudaGetLastError());
       CKN(cudaMemcpyAsync(&hs, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -269,8 +273,6 @@ extern "C" int gmmnlse_propagate_noalloc(gmmnlse_ctx* c, const double* A0, doubl
   int mr;
   int rc = gm_schedule(L, dz, M, &nf, &mr);
   if (rc) return rc;
-  // this entry point runs the CUDA-core contraction, which must fit
-  if (c->N > 8 && c->contract_threads == 0) return GMMNLSE_E_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(c->mu);
   CKN(cudaSetDevice(c->prm.device));
   unsigned char* base = nullptr;

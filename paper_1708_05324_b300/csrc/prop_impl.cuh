@@ -99,7 +99,9 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 2>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 4>, A, sm));
-  CK(cudaFuncSetAttribute(k_contract<R>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 2>, A, sm));
   if (std::is_same<R, float>::value) {
     const int rc = tc_for_each_n([&](auto kern) -> int {
       cudaFuncAttributes fa;
@@ -228,7 +230,7 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_integrand<R, 16, 4>);
 }
 
-// K3 on the tensor cores (mixed precision): pack V to BF16 hi/lo, then the
+// K3 on the tensor cores (mixed precision): form V and pack it to BF16 hi/lo, then the
 // tcgen05 GEMM with the l-sum in its epilogue
 template <typename R>
 static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
@@ -237,13 +239,16 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
     const int n = c->n;
     const int npts_total = (jb->Mcap + 1) * n;
     const int pts = (g.M + 1) * n;
-    const dim3 pgrid((pts + 255) / 256);
-    if (c->raman_mode == 0)
-      pdl_launch(k_pack_bf16<0>, pgrid, dim3(256), 0, s, g, (const float2*)jb->A, (const float*)jb->V,
-                 (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo, (const LoopState*)jb->ls);
-    else
-      pdl_launch(k_pack_bf16<1>, pgrid, dim3(256), 0, s, g, (const float2*)jb->A, (const float*)jb->V,
-                 (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo, (const LoopState*)jb->ls);
+    const dim3 pgrid((pts + PACK_PTS - 1) / PACK_PTS);
+    auto pack = [&](auto kern) {
+      pdl_launch(kern, pgrid, dim3(PACK_PTS * PACK_WARPS), (size_t)c->N * PACK_PTS * sizeof(float2), s, g,
+                 (const float2*)jb->A,
+                 (const float*)jb->V, (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo,
+                 (const LoopState*)jb->ls);
+    };
+    if (c->raman_mode == 0) pack(k_pack_bf16<0>);
+    else if (c->raman_mode == 1) pack(k_pack_bf16<1>);
+    else pack(k_pack_bf16<2>);
     TcArgs a = {};
     a.KKp = c->KKp;
     a.n = n;
@@ -272,9 +277,9 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
 // K5 with the convergence decision in its last block
 template <typename R>
 static void launch_k5(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
-  const size_t Nn = (size_t)jb->ctx->N * jb->ctx->n;
-  pdl_launch(k_trapz_decide<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, (const cplx<R>*)jb->psiR,
-             (cplx<R>*)jb->dpsi, (const cplx<R>*)jb->I, jb->ls, h, use_cond);
+  pdl_launch(k_trapz<R, true>, dim3(trapz_blocks((size_t)jb->ctx->N * jb->ctx->n)), dim3(TRAPZ_T), 0, s, g,
+             (const cplx<R>*)jb->psiR, (cplx<R>*)jb->dpsi,
+             (const cplx<R>*)jb->I, jb->ls, jb->part, h, use_cond);
 }
 
 // One MPA iteration (Sec. III.D): transform to the time domain, pair
@@ -535,8 +540,8 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
   const double Nn = (double)c->N * c->n;
   // algorithmic bytes per launch of an iteration (substeps j = 1..M)
   bytes[0] = M * Nn * 4 * cs;                     // psiR, dpsi, E -> A
-  bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->KK * c->n * rs) : 0.0;
-  bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->KK * rs : 0.0));
+  bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->K * c->n * rs) : 0.0;     // A -> Y
+  bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->K * rs : 0.0));  // A, Y -> NL
   bytes[3] = M * Nn * 3 * cs + c->n * rs;         // NL, E -> I; prefactor table
   bytes[4] = Nn * ((M + 1) * cs + 2 * M * cs + cs); // I, dpsi old/new, psiR
   bytes[5] = Nn * (16 + cs + 16 + 16 + (c->fp64 ? 0 : cs));

@@ -280,29 +280,55 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   if (warp == 1) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
-// V (FP32: [M+1][KK][n], or the pair products of A when Kerr only) to the
-// blocked BF16 hi/lo operand layout [KKp/8][npts][8] read by the TMA of
-// k_tc_contract.  One thread per point; each writes whole 16-byte chunks.
+// V to the blocked BF16 hi/lo operand layout [KKp/8][npts][8] read by the
+// TMA of k_tc_contract, V formed from the pair products U of A and from
+// Y = h_R * U ([M+1][K][n]) as for K3: MODE (= raman_mode) 0: V = U;
+// 1: V = (1 - fR) U + fR Y; 2: V = [U; Y].  A block takes 32 points (the
+// lanes of each warp) and stages their N mode values in shared memory
+// ([N][32]); warp w packs the 8-wide chunks kc = w, w + 8, ...  Y loads and
+// the 16-byte stores are coalesced across the lanes.
+constexpr int PACK_PTS = 32, PACK_WARPS = 8;
+
 template <int MODE>
-__global__ void __launch_bounds__(256) k_pack_bf16(Geo g, const float2* __restrict__ A, const float* __restrict__ V,
-                                                   const int2* __restrict__ pairs, int KKp, int npts_total,
-                                                   __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo,
-                                                   const LoopState* __restrict__ ls) {
+__global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_bf16(
+    Geo g, const float2* __restrict__ A, const float* __restrict__ Y, const int2* __restrict__ pairs, int KKp,
+    int npts_total, __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo,
+    const LoopState* __restrict__ ls) {
+  extern __shared__ float2 pack_as[];  // [N][PACK_PTS]
   pdl_enter();
-  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = g.n;
-  if (pt >= (g.M + 1) * n) return;
-  const int j = pt / n, t = pt - j * n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = g.n, npts = (g.M + 1) * n;
+  const int pt0 = blockIdx.x * PACK_PTS;  // n is a multiple of 128: a block lies in one substep
+  const int j = pt0 / n;
   if (ls->iter > 0 && j == 0) return;
-  const float2* a = A + (size_t)j * g.N * n;
-  const float* v = V + (size_t)j * g.KK * n + t;
-  for (int kc = 0; kc < KKp / 8; ++kc) {
+  const int pt = pt0 + lane, t = pt - j * n;
+  const bool ok = pt < npts;
+  for (int i = threadIdx.x; i < g.N * PACK_PTS; i += blockDim.x) {
+    const int l = i / PACK_PTS, q = i - l * PACK_PTS;
+    pack_as[i] = (pt0 + q < npts) ? A[((size_t)j * g.N + l) * n + (pt0 + q - j * n)] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if (!ok) return;
+  const float* y = Y + (size_t)j * g.K * n + t;
+  const float fR = (float)g.fR, fK = (float)(1.0 - g.fR);
+  auto U = [&](int k) {
+    const int2 mn = pairs[k];
+    const float2 am = pack_as[mn.x * PACK_PTS + lane];
+    if (mn.x == mn.y) return am.x * am.x + am.y * am.y;
+    const float2 an = pack_as[mn.y * PACK_PTS + lane];
+    return 2.0f * (am.x * an.x + am.y * an.y);
+  };
+  for (int kc = w; kc < KKp / 8; kc += PACK_WARPS) {
     __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = kc * 8 + i;
       float x = 0.f;
-      if (k < g.KK) x = MODE == 0 ? pair_product<float>(a, n, pairs[k], t) : v[(size_t)k * n];
+      if (k < g.KK) {
+        if (MODE == 0) x = U(k);
+        else if (MODE == 1) x = fK * U(k) + fR * y[(size_t)k * n];
+        else x = k < g.K ? U(k) : y[(size_t)(k - g.K) * n];
+      }
       hi[i] = __float2bfloat16_rn(x);
       lo[i] = __float2bfloat16_rn(x - __bfloat162float(hi[i]));
     }

@@ -110,12 +110,16 @@ def test_modes_raman_and_steepening_variants(N, fR, ss, split, precision, fft_va
         assert st["iters_total"] == sum(sref["iters"])
 
 
-@pytest.mark.parametrize("N", [10, 15])
+@pytest.mark.parametrize("N,Nt,fR,split", [(10, 256, 0.18, False), (15, 256, 0.18, False), (10, 64, 0.18, True),
+                                            (15, 32, 0.0, False), (9, 128, 0.18, False)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_generic_contraction_path_many_modes(N, precision):
-    """N > 8 takes the shared-memory contraction kernel (mode groups 0-3 and
-    0-4 of the GRIN fiber, as in the 15-mode workload)."""
-    key = ("m", N, 256, 0.18)
+def test_tiled_contraction_many_modes(N, Nt, fR, split, precision):
+    """N > 8 takes the tiled CUDA-core contraction (mode groups 0-3 and 0-4
+    of the GRIN fiber, as in the 15-mode workload).  Nt = 64 and 32 make the
+    128-point (FP32) and 64-point (FP64) tiles straddle substeps, so the z0
+    points of later iterations are skipped point by point; the separate
+    Raman tensor and the Kerr-only case cover the other two forms of V."""
+    key = ("m", N, Nt, fR, 1, 11, 20e-9, split)
     prob = small(*key)
     ref, _ = oracle_small(key)
     out, st, rc = gpu_run(prob, precision, tol=1e-13 if precision == "fp64" else 1e-9)
@@ -316,3 +320,13 @@ def test_mixed_bf16_dense_42_mode_contraction():
     out, st, rc = gpu_run(prob, "bf16", fixed_iters=3)
     assert rc == B.OK
     assert rel(out, ref) < 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_dense_42_mode_contraction_cuda_cores(precision):
+    """The FP32 and FP64 paths of the 42-mode workload: the tiled CUDA-core
+    contraction over eight 128-row blocks of the 903 x 903 matrix."""
+    prob, ref = c4_small()
+    out, st, rc = gpu_run(prob, precision, fixed_iters=3)
+    assert rc == B.OK
+    assert rel(out, ref) < TOL[precision]
