@@ -166,6 +166,16 @@ static int elementwise_blocks(size_t count) {
   return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
 }
 
+// Elements per thread of a one-block transform of np points in a launch of
+// `blocks` transforms: above 8192 points always 32; at 8192 points in FP32,
+// 32 (256 threads, two blocks per SM) when the launch has at least two
+// blocks per SM, which measured faster for throughput (the 42-mode
+// workload) and slower for a launch of fewer blocks than SMs (the 6-mode
+// workload), where 16 per thread is kept.
+template <typename R> static int fft_ept(int np, int blocks) {
+  return (np > 8192 || (sizeof(R) == 4 && np == 8192 && blocks >= 2 * 148)) ? 32 : 16;
+}
+
 // bytes of shared memory of a transform of n points over S blocks
 template <typename R> static size_t fft_cluster_smem(int n, int S) {
   return S == 1 ? fft_smem<R>(n) : fft_smem<R>(n / S) + (size_t)(n / S) * sizeof(cplx<R>);
@@ -176,7 +186,7 @@ template <typename R>
 static void launch_k1(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
-  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = np > 8192 ? 32 : 16;
+  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = fft_ept<R>(np, N * S * (g.M + 1));
   const dim3 grid(N * S, g.M + 1);
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
@@ -205,7 +215,7 @@ static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
     const int np = n / S;
     if (S == 2) args(k_pairs_raman_cl<R, 16, 2>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
     else args(k_pairs_raman_cl<R, 16, 4>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
-  } else if (n > 8192) {
+  } else if (fft_ept<R>(n, pp * (g.M + 1)) == 32) {
     args(k_pairs_raman<R, 32>, dim3(pp, g.M + 1), n / 32, fft_smem<R>(n), 1);
   } else {
     args(k_pairs_raman<R, 16>, dim3(pp, g.M + 1), n / 16, fft_smem<R>(n), 1);
@@ -217,7 +227,7 @@ template <typename R>
 static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
-  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = np > 8192 ? 32 : 16;
+  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = fft_ept<R>(np, N * S * (g.M + 1));
   const dim3 grid(N * S, g.M + 1);
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
