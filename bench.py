@@ -300,7 +300,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"])
     ap.add_argument("--length", type=float, default=0.5, help="fiber length per step [m]")
     ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C4"],
                     help="C3 (N=15, Nt=2^14, M=20) and C4 (N=42, Nt=2^13, M=16) are for --profile-run; the metric is quoted on C2")
@@ -437,7 +437,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3", "fp16": "f32+f16x3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
                    "units_per_step": u, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

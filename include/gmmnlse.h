@@ -54,7 +54,9 @@ typedef enum gmmnlse_precision {
     GMMNLSE_FP32 = 1,       /* FFTs, contraction and iterates FP32 */
     GMMNLSE_MIXED_BF16 = 2, /* FP32, coupling contraction on tensor cores in
                                BF16 with hi/lo split operands, FP32 accumulate */
-    GMMNLSE_MIXED_FP16 = 3  /* as MIXED_BF16 with FP16 operands */
+    GMMNLSE_MIXED_FP16 = 3  /* as MIXED_BF16 with FP16 hi/lo operands, each
+                               scaled by a power of two into FP16 range (exact
+                               to undo); N and Nt limits as MIXED_BF16 */
 } gmmnlse_precision;
 
 typedef struct gmmnlse_params {

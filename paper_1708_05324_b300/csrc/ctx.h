@@ -72,7 +72,9 @@ struct gmmnlse_ctx {
   bool tc = false;               // contraction on tensor cores (mixed precision)
   int KKp = 0;                   // K padded to a multiple of 64
   int tc_rows = 0;               // rows of G padded to whole row blocks
-  __nv_bfloat16* Ghi = nullptr;  // [KKp/8][tc_rows][8]
+  bool f16 = false;              // tensor-core operands FP16 (MIXED_FP16), else BF16
+  int eG = 0;                    // FP16: G scaled by 2^eG
+  __nv_bfloat16* Ghi = nullptr;  // [KKp/8][tc_rows][8] (FP16 bits when f16)
   __nv_bfloat16* Glo = nullptr;
   CUtensorMap mapGhi, mapGlo;
   void* Gt = nullptr;            // [KKt][Pt] R: G transposed, zero-padded (N > 8, CUDA cores)

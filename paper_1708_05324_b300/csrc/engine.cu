@@ -226,7 +226,6 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   if (!symmetric_enough(SK, N) || (SR && !symmetric_enough(SR, N))) return GMMNLSE_E_UNSUPPORTED;
   const bool fp64 = prm->precision == GMMNLSE_FP64;
   if (fp64 && n > 8192) return GMMNLSE_E_UNSUPPORTED;
-  if (prm->precision == GMMNLSE_MIXED_FP16) return GMMNLSE_E_UNSUPPORTED;
   int rc = set_device(prm->device);
   if (rc) return rc;
 
@@ -269,7 +268,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
 
   // mixed precision: the contraction runs on the tensor cores when the
   // reduced coupling matrix has at most 128 rows and 160 (padded) columns
-  if (prm->precision == GMMNLSE_MIXED_BF16) {
+  if (prm->precision == GMMNLSE_MIXED_BF16 || prm->precision == GMMNLSE_MIXED_FP16) {
     // built for N = 1..16 and 42 (the 42-mode step-index workload)
     if (!((N >= 1 && N <= 16) || N == 42) || n % TC_PTS != 0) {
       delete c;
@@ -277,6 +276,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     }
     const int NB = tc_row_block(c->P);
     c->tc = true;
+    c->f16 = prm->precision == GMMNLSE_MIXED_FP16;
     c->KKp = (c->KK + TC_KC - 1) / TC_KC * TC_KC;
     c->tc_rows = (c->P + NB - 1) / NB * NB;
   }
@@ -322,15 +322,29 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
   rc = fp64 ? upload_tables<double>(c, Gd) : upload_tables<float>(c, Gd);
   if (!rc && c->tc) {
-    // G split into BF16 hi + lo, blocked [KKp/8][rows][8] (K-major core matrices)
+    // G split into 16-bit hi + lo, blocked [KKp/8][rows][8] (K-major core
+    // matrices); FP16 scaled by 2^eG so that its largest entry is below 2^14
     const int KKp = c->KKp, rows = c->tc_rows;
+    double gmax = 0.0;
+    for (double x : Gd) gmax = std::max(gmax, std::fabs(x));
+    if (c->f16 && gmax > 0.0) {
+      int e;
+      std::frexp(gmax, &e);  // gmax < 2^e
+      c->eG = 14 - e;
+    }
     std::vector<__nv_bfloat16> gh((size_t)rows * KKp), gl((size_t)rows * KKp);
     for (int r = 0; r < rows; ++r)
       for (int k = 0; k < KKp; ++k) {
-        const float x = (r < c->P && k < c->KK) ? (float)Gd[(size_t)r * c->KK + k] : 0.f;
+        const float x = (r < c->P && k < c->KK) ? (float)std::ldexp(Gd[(size_t)r * c->KK + k], c->eG) : 0.f;
         const size_t o = ((size_t)(k / 8) * rows + r) * 8 + (k % 8);
-        gh[o] = __float2bfloat16_rn(x);
-        gl[o] = __float2bfloat16_rn(x - __bfloat162float(gh[o]));
+        if (c->f16) {
+          const __half h = __float2half_rn(x), l = __float2half_rn(x - __half2float(h));
+          std::memcpy(&gh[o], &h, 2);
+          std::memcpy(&gl[o], &l, 2);
+        } else {
+          gh[o] = __float2bfloat16_rn(x);
+          gl[o] = __float2bfloat16_rn(x - __bfloat162float(gh[o]));
+        }
       }
     cudaError_t e = cudaMalloc(&c->Ghi, gh.size() * 2);
     if (e == cudaSuccess) e = cudaMalloc(&c->Glo, gl.size() * 2);
@@ -437,9 +451,9 @@ static int tc_encoder(EncodeTiledFn* out) {
   return GMMNLSE_OK;
 }
 
-// Map of a blocked [KKp/8][rows][8] BF16 operand; box = one K chunk of
-// box_rows rows.
-static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int box_rows) {
+// Map of a blocked [KKp/8][rows][8] 16-bit operand (BF16 or FP16); box = one
+// K chunk of box_rows rows.
+static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int box_rows, bool f16) {
   EncodeTiledFn enc;
   const int rc = tc_encoder(&enc);
   if (rc) return rc;
@@ -447,7 +461,8 @@ static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int bo
   const cuuint64_t strides[2] = {16, rows * 16};
   const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(TC_KC / 8)};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+  const CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base,
+                         dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -459,15 +474,15 @@ static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int bo
 
 int gm_make_g_maps(gmmnlse_ctx* c) {
   const int NB = tc_row_block(c->P);
-  int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB);
-  if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB);
+  int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16);
+  if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16);
   return rc;
 }
 
 int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
   const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
-  int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS);
-  if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS);
+  int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS, c->f16);
+  if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS, c->f16);
   return rc;
 }
 

@@ -240,7 +240,7 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_integrand<R, 16, 4>);
 }
 
-// K3 on the tensor cores (mixed precision): form V and pack it to BF16 hi/lo, then the
+// K3 on the tensor cores (mixed precision): form V and pack it to 16-bit hi/lo, then the
 // tcgen05 GEMM with the l-sum in its epilogue
 template <typename R>
 static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
@@ -252,15 +252,22 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
     const dim3 pgrid((pts + PACK_PTS - 1) / PACK_PTS);
     auto pack = [&](auto kern) {
       pdl_launch(kern, pgrid, dim3(PACK_PTS * PACK_WARPS), (size_t)c->N * PACK_PTS * sizeof(float2), s, g,
-                 (const float2*)jb->A,
-                 (const float*)jb->V, (const int2*)c->pairs, c->KKp, npts_total, jb->Vhi, jb->Vlo,
-                 (const LoopState*)jb->ls);
+                 (const float2*)jb->A, (const float*)jb->V, (const int2*)c->pairs, c->KKp, npts_total,
+                 (void*)jb->Vhi, (void*)jb->Vlo, (const LoopState*)jb->ls);
     };
-    if (c->raman_mode == 0) pack(k_pack_bf16<0>);
-    else if (c->raman_mode == 1) pack(k_pack_bf16<1>);
-    else pack(k_pack_bf16<2>);
+    if (c->f16) {
+      if (c->raman_mode == 0) pack(k_pack_hilo<0, true>);
+      else if (c->raman_mode == 1) pack(k_pack_hilo<1, true>);
+      else pack(k_pack_hilo<2, true>);
+    } else {
+      if (c->raman_mode == 0) pack(k_pack_hilo<0, false>);
+      else if (c->raman_mode == 1) pack(k_pack_hilo<1, false>);
+      else pack(k_pack_hilo<2, false>);
+    }
     TcArgs a = {};
     a.KKp = c->KKp;
+    a.f16 = c->f16 ? 1 : 0;
+    a.eG = c->eG;
     a.n = n;
     a.M = g.M;
     a.A = (const float2*)jb->A;

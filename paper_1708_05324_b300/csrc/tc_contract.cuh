@@ -1,12 +1,20 @@
-// Coupling contraction on the 5th-generation tensor cores (mixed precision).
+// Coupling contraction on the 5th-generation tensor cores (mixed precision,
+// BF16 or FP16 operands).
 //
 // Per point (j, t) of the MPA iteration (Eq. 1 bracket after the symmetry
 // rewrite):  R_r = sum_k G[r][k] V_k   (rows r = (p <= l), k over pair terms),
 //            NL_p = sum_l A_l R_pl.
 // Over a tile of 128 points and a block of NB rows this is the GEMM
 //   D[128 x NB] = V[128 x K] . G[NB x K]^T
-// with V and G split into BF16 hi + lo parts; D accumulates hi.hi + lo.hi +
+// with V and G split into 16-bit hi + lo parts; D accumulates hi.hi + lo.hi +
 // hi.lo in FP32 in TMEM (lo.lo lies below the FP32 rounding of the result).
+// BF16 needs no scaling.  FP16 (11-bit significands, range 2^-24 .. 65504)
+// takes power-of-two scales: G by 2^eG (its largest entry below 2^14, set at
+// context creation) and V by 2^eV from a bound on |V|: |U_mn(t)| <=
+// sum_p |A_p(t)|^2 <= sum_t sum_p |A_p(t)|^2 = (1/Nt) sum_w |psi0|^2 and
+// |h_R * U| <= dt sum |h_R| max |U| < 2 max |U| (the energy does not grow
+// along the fiber), so 2^eV (2 x bound) < 2^14.  The epilogue undoes both
+// exactly (a power of two).
 // Points are the MMA's M dimension, so after tcgen05.ld each epilogue thread
 // holds R_r(t) for its own point t and forms the l-sum in registers, with the
 // row -> (p, l) map resolved at compile time.
@@ -27,6 +35,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -39,6 +48,8 @@ constexpr int TC_KC = 64;    // K chunk per pipeline stage
 
 struct TcArgs {
   int KKp;           // K padded to a multiple of TC_KC
+  int f16;           // operands FP16 (else BF16)
+  int eG;            // FP16: G scaled by 2^eG
   int n, M;          // samples, substeps (tiles cover j = 0..M)
   const float2* A;   // [M+1][N][n]
   float2* NL;        // [M+1][N][n]
@@ -48,6 +59,16 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
+
+// FP16 scale exponent of V: 2^eV (2 x the bound on |V|) < 2^14; the bound
+// is (1/Nt) sum_w |psi0|^2, summed at the start of the propagation.
+__device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n) {
+  double b = ls->spec[0] / (double)n;
+  if (!(b > 0.0) || !isfinite(b)) b = 1.0;
+  int e;
+  frexp(2.0 * b, &e);  // 2 b < 2^e
+  return 14 - e;
+}
 
 template <int N, int NB>
 struct TcShape {
@@ -191,7 +212,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16(TC_PTS, NB, true);
+      const uint32_t idesc = tc::idesc_f16(TC_PTS, NB, a.f16 == 0);
       const uint32_t lboV = TC_PTS * 16, lboG = NB * 16, sbo = 128;
       int c = 0, w = 0;
       for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
@@ -235,6 +256,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
     const int quarter = warp & 3;  // this warp may access TMEM lanes 32 quarter ..
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    // FP16: D = 2^(eV + eG) R; folded into the mode values of the l-sum
+    const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n) + a.eG)) : 1.0f;
     int w = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
       if (!live(tile)) continue;
@@ -244,6 +267,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
 #pragma unroll
       for (int l = 0; l < N; ++l) {
         av[l] = PROBE ? make_float2(0.f, 0.f) : a.A[((size_t)j * N + l) * n + t];
+        av[l].x *= inv;
+        av[l].y *= inv;
         nl[l] = make_float2(0.f, 0.f);
       }
       for (int rb = 0; rb < S::NRB; ++rb, ++w) {
@@ -280,20 +305,36 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   if (warp == 1) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
-// V to the blocked BF16 hi/lo operand layout [KKp/8][npts][8] read by the
-// TMA of k_tc_contract, V formed from the pair products U of A and from
-// Y = h_R * U ([M+1][K][n]) as for K3: MODE (= raman_mode) 0: V = U;
-// 1: V = (1 - fR) U + fR Y; 2: V = [U; Y].  A block takes 32 points (the
-// lanes of each warp) and stages their N mode values in shared memory
-// ([N][32]); warp w packs the 8-wide chunks kc = w, w + 8, ...  Y loads and
-// the 16-byte stores are coalesced across the lanes.
+// V to the blocked 16-bit hi/lo operand layout [KKp/8][npts][8] read by the
+// TMA of k_tc_contract (BF16, or FP16 scaled by 2^eV), V formed from the
+// pair products U of A and from Y = h_R * U ([M+1][K][n]) as for K3:
+// MODE (= raman_mode) 0: V = U; 1: V = (1 - fR) U + fR Y; 2: V = [U; Y].
+// A block takes 32 points (the lanes of each warp) and stages their N mode
+// values in shared memory ([N][32]); warp w packs the 8-wide chunks
+// kc = w, w + 8, ...  Y loads and the 16-byte stores are coalesced across
+// the lanes.
 constexpr int PACK_PTS = 32, PACK_WARPS = 8;
 
-template <int MODE>
-__global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_bf16(
+template <bool F16> struct Half16;
+template <> struct Half16<false> {
+  using T = __nv_bfloat16;
+  __device__ static T rn(float x) { return __float2bfloat16_rn(x); }
+  __device__ static float back(T h) { return __bfloat162float(h); }
+};
+template <> struct Half16<true> {
+  using T = __half;
+  __device__ static T rn(float x) { return __float2half_rn(x); }
+  __device__ static float back(T h) { return __half2float(h); }
+};
+
+template <int MODE, bool F16>
+__global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
     Geo g, const float2* __restrict__ A, const float* __restrict__ Y, const int2* __restrict__ pairs, int KKp,
-    int npts_total, __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo,
-    const LoopState* __restrict__ ls) {
+    int npts_total, void* __restrict__ Vhi_, void* __restrict__ Vlo_, const LoopState* __restrict__ ls) {
+  using H = Half16<F16>;
+  using T = typename H::T;
+  T* Vhi = reinterpret_cast<T*>(Vhi_);
+  T* Vlo = reinterpret_cast<T*>(Vlo_);
   extern __shared__ float2 pack_as[];  // [N][PACK_PTS]
   pdl_enter();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -303,6 +344,7 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_bf16(
   if (ls->iter > 0 && j == 0) return;
   const int pt = pt0 + lane, t = pt - j * n;
   const bool ok = pt < npts;
+  const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n)) : 1.0f;
   for (int i = threadIdx.x; i < g.N * PACK_PTS; i += blockDim.x) {
     const int l = i / PACK_PTS, q = i - l * PACK_PTS;
     pack_as[i] = (pt0 + q < npts) ? A[((size_t)j * g.N + l) * n + (pt0 + q - j * n)] : make_float2(0.f, 0.f);
@@ -319,7 +361,7 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_bf16(
     return 2.0f * (am.x * an.x + am.y * an.y);
   };
   for (int kc = w; kc < KKp / 8; kc += PACK_WARPS) {
-    __align__(16) __nv_bfloat16 hi[8], lo[8];
+    __align__(16) T hi[8], lo[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = kc * 8 + i;
@@ -329,8 +371,9 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_bf16(
         else if (MODE == 1) x = fK * U(k) + fR * y[(size_t)k * n];
         else x = k < g.K ? U(k) : y[(size_t)(k - g.K) * n];
       }
-      hi[i] = __float2bfloat16_rn(x);
-      lo[i] = __float2bfloat16_rn(x - __bfloat162float(hi[i]));
+      x *= scale;
+      hi[i] = H::rn(x);
+      lo[i] = H::rn(x - H::back(hi[i]));
     }
     const size_t o = ((size_t)kc * npts_total + pt) * 8;
     *reinterpret_cast<uint4*>(Vhi + o) = *reinterpret_cast<const uint4*>(hi);

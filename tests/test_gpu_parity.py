@@ -276,13 +276,15 @@ def test_device_pointers_and_torch_stream():
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("N,Nt,fR", [(3, 256, 0.18), (6, 512, 0.18), (6, 256, 0.0), (10, 256, 0.18),
                                      (15, 1024, 0.18), (1, 128, 0.18)])
-def test_mixed_bf16_tensor_core_contraction(N, Nt, fR):
-    """The mixed path (FFTs in FP32, coupling contraction as a tcgen05 GEMM
-    on BF16 hi/lo operands) against the FP64 oracle: <= 1e-3 relative L2."""
+@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+def test_mixed_tensor_core_contraction(N, Nt, fR, mixed):
+    """The mixed paths (FFTs in FP32, coupling contraction as a tcgen05 GEMM
+    on BF16 or scaled FP16 hi/lo operands) against the FP64 oracle: <= 1e-3
+    relative L2."""
     key = ("t", N, Nt, fR)
     prob = small(*key)
     ref, sref = oracle_small(key)
-    out, st, rc = gpu_run(prob, "bf16", tol=1e-9)
+    out, st, rc = gpu_run(prob, mixed, tol=1e-9)
     assert rc == B.OK
     err = rel(out, ref)
     assert err < 1e-3
@@ -290,9 +292,10 @@ def test_mixed_bf16_tensor_core_contraction(N, Nt, fR):
     assert err < 1e-5
 
 
-def test_mixed_bf16_c2_prefix():
+@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+def test_mixed_c2_prefix(mixed):
     prob, ref, sref = c2_prefix()
-    out, st, rc = gpu_run(prob, "bf16", tol=1e-8)
+    out, st, rc = gpu_run(prob, mixed, tol=1e-8)
     assert rc == B.OK
     assert rel(out, ref) < 1e-3
 
@@ -315,9 +318,10 @@ def c4_small():
     return prob, ref
 
 
-def test_mixed_bf16_dense_42_mode_contraction():
+@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+def test_mixed_dense_42_mode_contraction(mixed):
     prob, ref = c4_small()
-    out, st, rc = gpu_run(prob, "bf16", fixed_iters=3)
+    out, st, rc = gpu_run(prob, mixed, fixed_iters=3)
     assert rc == B.OK
     assert rel(out, ref) < 1e-3
 
