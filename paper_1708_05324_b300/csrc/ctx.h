@@ -139,7 +139,7 @@ template <typename R, int N, int MODE>
 static inline void launch_contract_reg(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V,
                                        void* NL, const gm::LoopState* ls, cudaStream_t s) {
   const size_t pts = (size_t)(g.M + 1) * g.n;
-  pdl_launch(gm::k_contract_reg<R, N, MODE>, dim3((unsigned)((pts + 255) / 256)), dim3(256), 0, s, g,
+  pdl_launch(gm::k_contract_reg<R, N, MODE>, dim3((unsigned)((pts + 127) / 128)), dim3(128), 0, s, g,
              (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (gm::cplx<R>*)NL, ls);
 }
 

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __
 // shared memory as a broadcast, 16 bytes per load (rows padded to KKP).
 // One thread per (j, t).
 template <typename R, int N, int MODE>
-__global__ void __launch_bounds__(256) k_contract_reg(Geo g, const cplx<R>* __restrict__ A,
+__global__ void __launch_bounds__(128) k_contract_reg(Geo g, const cplx<R>* __restrict__ A,
                                                       const R* __restrict__ Y, const R* __restrict__ Gm,
                                                       cplx<R>* __restrict__ NL, const LoopState* __restrict__ ls) {
   constexpr int K = N * (N + 1) / 2;
@@ -373,7 +373,7 @@ static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int
 // ls->diff / ls->nrm.  Every block reads iter before it arrives, so the last
 // one may update it.
 // ---------------------------------------------------------------------------
-constexpr int TRAPZ_T = 256;
+constexpr int TRAPZ_T = 128;
 constexpr int TRAPZ_MAX_BLOCKS = 148 * 8;
 template <typename R> struct TrapzJC { static constexpr int value = sizeof(R) == 4 ? 16 : 8; };
 
