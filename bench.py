@@ -32,6 +32,19 @@ from paper_1708_05324_b300 import inputs as I  # noqa: E402
 METRIC = "mode*sample*z-steps/s"
 WORKLOAD = ("GRIN a=25um NA=0.2 1030nm, N=6 HG modes, Nt=2^13 over 10 ps, Kerr+Raman fR=0.18, "
             "self-steepening, 200 fs Gaussian 50 nJ seeded weights, L=0.5 m, dz=25 um, M=10, tol=1e-8")
+WORKLOADS = {
+    "C2": WORKLOAD,
+    "C3": ("GRIN a=25um NA=0.2 1030nm, N=15 HG modes (groups 0-4), Nt=2^14 over 20 ps, Kerr+Raman fR=0.18, "
+           "self-steepening, 500 fs Gaussian 200 nJ seeded weights, dz=12.5 um, M=20, tol=1e-6"),
+    "C4": ("step-index a=25um NA=0.22 1030nm, N=42 LP modes (both orientations, S from a 200^2 grid), "
+           "Nt=2^13 over 10 ps, Kerr+Raman fR=0.18, self-steepening, 100 fs Gaussian 100 nJ seeded weights, "
+           "dz=37.5 um, M=16, tol=1e-6"),
+}
+# DRAM bytes per launch of the dominant kernel from one ncu capture (the
+# kernel unchanged since): k_pairs_raman<float, 16> on the 6-mode workload,
+# warm L2, profiles/fft_kernels_c2_fp32.md.
+TRAFFIC = {("C2", "fp32", "pairs_raman"): 256 + 3840}
+FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
 
 
 def problem(seed=2, L=0.5, name="C2"):
@@ -103,11 +116,15 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
-def launches_per_step(st, raman, graph=True):
+def launches_per_step(st, raman, mixed=False, fp64=False, graph=True):
     """Kernel launches of one propagate call, from its statistics."""
     per_iter = 5 if raman else 4   # K1 [K2] K3 K4 K5 (decision in K5's last block)
+    if mixed:
+        per_iter += 1              # K3 = operand pack + tensor-core GEMM
     fft = 1  # Nt <= 8192
     n = 1 + fft + 1          # non-finite check, forward transform, input sums
+    if not fp64:
+        n += 1               # psi0 rounded to the working precision
     n += 1 + fft             # output sums, inverse transform
     # per long step: loop re-arm (graph only), advance, bookkeeping
     n += st["iters_total"] * per_iter + st["long_steps"] * (3 if graph else 2)
@@ -414,43 +431,67 @@ def main():
             dist.destroy_process_group()
         return
 
-    # error of this path against the FP64 GPU path on a 5 mm prefix (200 long steps)
-    pre = I.workload("C2", L=5e-3)
-    c64 = B.Context.from_problem(pre, precision="fp64", device=dev)
-    ref64, st64, _ = c64.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
-    c64.close()
-    cx = B.Context.from_problem(pre, precision=args.precision, device=dev)
-    mine, _, _ = cx.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
-    cx.close()
-    err = float(np.linalg.norm(mine - ref64) / np.linalg.norm(ref64))
-    fp64_rate = units(pre) / (st64["ms"] / 1e3)
+    # error of this path against the FP64 GPU path on a prefix: 5 mm (200 long
+    # steps) of the 6-mode run, one long step of the 42-mode run; the 15-mode
+    # run has 2^14-point transforms, which the FP64 path does not build
+    err, fp64_rate, err_prefix = None, None, None
+    if args.workload in ("C2", "C4"):
+        pre = I.workload("C2", L=5e-3) if args.workload == "C2" else problem(L=16 * 37.5e-6, name="C4")
+        err_prefix = "5 mm" if args.workload == "C2" else "one long step (0.6 mm)"
+        c64 = B.Context.from_problem(pre, precision="fp64", device=dev)
+        ref64, st64, _ = c64.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
+        c64.close()
+        cx = B.Context.from_problem(pre, precision=args.precision, device=dev)
+        mine, _, _ = cx.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
+        cx.close()
+        err = float(np.linalg.norm(mine - ref64) / np.linalg.norm(ref64))
+        fp64_rate = units(pre) / (st64["ms"] / 1e3)
 
     # roofline of the dominant kernel (CUDA events on the context's stream)
     prof = ctx.profile(prob.M, reps=20)
     dom = max(prof, key=lambda k: prof[k][0])
     ms_dom, bytes_dom = prof[dom]
     peaks, src = measured_peaks()
-    achieved = bytes_dom / (ms_dom * 1e-3) / 1e9
+    mixed = args.precision in ("bf16", "fp16")
+    if dom == "contract" and prob.N > 8:
+        # a dense GEMM: 2 P KK flops per point and iteration (x3 for the hi/lo
+        # products on the tensor cores), points = M substeps x Nt
+        P = prob.N * (prob.N + 1) // 2
+        KK = P if prob.fR == 0 or prob.SR is None or prob.SR is prob.SK else 2 * P
+        flops = 2.0 * P * KK * prob.M * prob.Nt * (3 if mixed else 1)
+        achieved = flops / (ms_dom * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "tensor" if mixed else "alu", "achieved": achieved,
+                "peak": peaks["bf16_tflops"] if mixed else FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                "algorithmic_flops": flops}
+        roof["frac"] = achieved / roof["peak"]
+        roof["peak_source"] = src if mixed else "148 SMs x 128 FP32 FMA/clk x 2 x 2.032 GHz"
+    else:
+        achieved = bytes_dom / (ms_dom * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": src, "algorithmic_bytes": bytes_dom}
+    roof["traffic"] = TRAFFIC.get((args.workload, args.precision, dom))
+    roof["kernel_ms"] = ms_dom
+    roof["all_kernels_ms"] = {k: v[0] for k, v in prof.items()}
     raman = prob.fR != 0
-    launches = sum(launches_per_step(st, raman) for st in stats)
+    launches = sum(launches_per_step(st, raman, mixed, args.precision == "fp64") for st in stats)
     ctx.close()
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3", "fp16": "f32+f16x3"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+        "config": {"workload": WORKLOADS[args.workload] if args.length == 0.5 or args.workload != "C2"
+                   else WORKLOAD.replace("L=0.5 m", f"L={args.length} m"),
+                   "length_m": args.length, "precision": args.precision,
+                   "l2": "flushed between steps (256 MiB write)",
                    "units_per_step": u, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "long_steps_per_step": stats[-1]["long_steps"],
                    "iters_per_long_step": stats[-1]["iters_total"] / max(stats[-1]["long_steps"], 1),
-                   "rel_l2_err_vs_fp64_gpu_5mm": err, "fp64_gpu_value": fp64_rate,
+                   "rel_l2_err_vs_fp64_gpu": err, "err_prefix": err_prefix, "fp64_gpu_value": fp64_rate,
                    "wall_s": wall},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "peak_source": src, "kernel_ms": ms_dom, "algorithmic_bytes": bytes_dom,
-                     "all_kernels_ms": {k: v[0] for k, v in prof.items()}},
+        "roofline": roof,
         "clocks": clk.summary(),
     }
     if args.serve_requests > 0:

@@ -266,11 +266,12 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     }
   }
 
-  // mixed precision: the contraction runs on the tensor cores when the
-  // reduced coupling matrix has at most 128 rows and 160 (padded) columns
-  if (prm->precision == GMMNLSE_MIXED_BF16 || prm->precision == GMMNLSE_MIXED_FP16) {
-    // built for N = 1..16 and 42 (the 42-mode step-index workload)
-    if (!((N >= 1 && N <= 16) || N == 42) || n % TC_PTS != 0) {
+  // mixed precision: the contraction runs on the tensor cores where it is a
+  // dense GEMM, N >= 9 (built for N = 9..16 and 42, the 42-mode step-index
+  // workload, with Nt a multiple of the 128-point tile); for N <= 8 the FP32
+  // register contraction is faster than a GEMM that small and is used instead
+  if ((prm->precision == GMMNLSE_MIXED_BF16 || prm->precision == GMMNLSE_MIXED_FP16) && N > 8) {
+    if (!(N <= 16 || N == 42) || n % TC_PTS != 0) {
       delete c;
       return GMMNLSE_E_UNSUPPORTED;
     }

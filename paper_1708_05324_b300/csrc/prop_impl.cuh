@@ -66,7 +66,6 @@ static int tc_for_each_n(F&& f) {
     if (!rc) rc = f(kern);
   };
 #define GM_TC_N(N) one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), false>);
-  GM_TC_N(1) GM_TC_N(2) GM_TC_N(3) GM_TC_N(4) GM_TC_N(5) GM_TC_N(6) GM_TC_N(7) GM_TC_N(8)
   GM_TC_N(9) GM_TC_N(10) GM_TC_N(11) GM_TC_N(12) GM_TC_N(13) GM_TC_N(14) GM_TC_N(15) GM_TC_N(16) GM_TC_N(42)
 #undef GM_TC_N
   return rc;
@@ -282,8 +281,7 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
                c->mapGhi, c->mapGlo, a, (const LoopState*)jb->ls);                                           \
     break;                                                                                                  \
   }
-      GM_TC_CASE(1) GM_TC_CASE(2) GM_TC_CASE(3) GM_TC_CASE(4) GM_TC_CASE(5) GM_TC_CASE(6) GM_TC_CASE(7)
-      GM_TC_CASE(8) GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
+      GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
       GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
 #undef GM_TC_CASE
       default: break;

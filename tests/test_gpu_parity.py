@@ -274,13 +274,13 @@ def test_device_pointers_and_torch_stream():
 # ----------------------------------------------------------------------------
 # Mixed precision: contraction on the tensor cores (BF16 hi/lo, FP32 accumulate)
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("N,Nt,fR", [(3, 256, 0.18), (6, 512, 0.18), (6, 256, 0.0), (10, 256, 0.18),
-                                     (15, 1024, 0.18), (1, 128, 0.18)])
+@pytest.mark.parametrize("N,Nt,fR", [(3, 256, 0.18), (6, 512, 0.18), (9, 256, 0.0), (10, 256, 0.18),
+                                     (12, 128, 0.18), (15, 1024, 0.18), (16, 256, 0.0), (1, 128, 0.18)])
 @pytest.mark.parametrize("mixed", ["bf16", "fp16"])
 def test_mixed_tensor_core_contraction(N, Nt, fR, mixed):
     """The mixed paths (FFTs in FP32, coupling contraction as a tcgen05 GEMM
-    on BF16 or scaled FP16 hi/lo operands) against the FP64 oracle: <= 1e-3
-    relative L2."""
+    on BF16 or scaled FP16 hi/lo operands for N >= 9, the FP32 register
+    contraction below) against the FP64 oracle: <= 1e-3 relative L2."""
     key = ("t", N, Nt, fR)
     prob = small(*key)
     ref, sref = oracle_small(key)
@@ -301,10 +301,12 @@ def test_mixed_c2_prefix(mixed):
 
 
 def test_mixed_rejects_what_the_tensor_core_tile_cannot_hold():
-    prob = small("p", 3, 64, 0.18)  # Nt not a multiple of the 128-point tile
+    prob = small("p", 10, 64, 0.18)  # Nt not a multiple of the 128-point tile
     with pytest.raises(B.GmmnlseError) as e:
         B.Context.from_problem(prob, precision="bf16")
     assert e.value.status == B.E_UNSUPPORTED
+    prob = small("p", 3, 64, 0.18)  # N <= 8: the register contraction, any Nt
+    B.Context.from_problem(prob, precision="bf16").close()
 
 
 @functools.lru_cache(maxsize=None)

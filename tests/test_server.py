@@ -34,9 +34,14 @@ def _wait(srv, tickets, shapes, timeout=120):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
 def test_results_are_the_same_alone_and_in_the_mix(precision):
-    specs = [(1, 256, 1), (3, 1024, 2), (6, 512, 3), (3, 256, 4)]
+    """Alone vs in the mix: FP64 to 1e-12, FP32 to 1e-6, the mixed served
+    path (tensor-core contraction for the 10-, 12- and 15-mode requests) to
+    its stated 1e-3."""
+    mixed = precision in ("bf16", "fp16")
+    specs = ([(10, 256, 1), (15, 512, 2), (3, 256, 3), (12, 128, 4)] if mixed
+             else [(1, 256, 1), (3, 1024, 2), (6, 512, 3), (3, 256, 4)])
     ctxs = [_ctx(*s[:2], precision, s[2]) for s in specs]
     alone = []
     for prob, ctx in ctxs:
@@ -51,7 +56,7 @@ def test_results_are_the_same_alone_and_in_the_mix(precision):
             shapes.append((prob.N, prob.Nt))
             expect.append(ref[L])
     res = _wait(srv, tickets, shapes)
-    bar = 1e-12 if precision == "fp64" else 1e-6
+    bar = {"fp64": 1e-12, "fp32": 1e-6}.get(precision, 1e-3)
     for t, ref in zip(tickets, expect):
         rc, a, st = res[t]
         assert rc == B.OK
