@@ -42,7 +42,7 @@ WORKLOADS = {
 }
 # DRAM bytes per launch of the dominant kernel from one ncu capture (the
 # kernel unchanged since): k_pairs_raman<float, 16> on the 6-mode workload,
-# warm L2, profiles/fft_kernels_c2_fp32.md.
+# warm L2, profiles/pairs_raman_c2_fp32.md.
 TRAFFIC = {("C2", "fp32", "pairs_raman"): 256 + 3840}
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
 
