@@ -95,6 +95,9 @@ typedef struct gmmnlse_stats {
     double photons_in;    /* sum_{p,q: w0+w_q>0} |A~_p(w_q)|^2 / (w0 + w_q) of A0 */
     double photons_out;   /* the same of Aout */
     double ms;            /* device time of the propagation [ms] */
+    int coupling_rank;    /* rank r of the coupling G = X W the contraction
+                             used (N > 8, S^R = S^K, r <= 3K/4), else
+                             K = N(N+1)/2 (the dense reduced matrix) */
 } gmmnlse_stats;
 
 typedef struct gmmnlse_ctx gmmnlse_ctx;
@@ -156,8 +159,10 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
  * recorded into a CUDA stream capture, latency-critical loops that cannot
  * take the device-wide synchronisation of cudaMalloc/cudaFree, and programs
  * whose device memory is all owned by their own pool allocator.  It runs the
- * same kernels as gmmnlse_propagate (host-driven iteration loop, no graphs,
- * no events), with the workspace in one static device array of 32 MiB that
+ * same transforms and trapezoid as gmmnlse_propagate with the dense CUDA-core
+ * contraction (no tensor cores, no low-rank coupling; st->coupling_rank = K),
+ * a host-driven iteration loop, no graphs and no events, with the
+ * workspace in one static device array of 32 MiB that
  * every GPU loading the library holds until the process exits.
  *
  *   ctx   a context made beforehand with gmmnlse_create (that call allocates).

@@ -47,6 +47,7 @@ class Stats(C.Structure):
         ("eps_max", C.c_double), ("eps_last", C.c_double),
         ("energy_in", C.c_double), ("energy_out", C.c_double),
         ("photons_in", C.c_double), ("photons_out", C.c_double), ("ms", C.c_double),
+        ("coupling_rank", C.c_int),
     ]
 
     def as_dict(self):

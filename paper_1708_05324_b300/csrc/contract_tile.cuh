@@ -8,15 +8,26 @@
 // computed in registers (TM x TN per thread, 16 x 16 threads; thread (x, y)
 // holds points y TM + i and rows x + 16 j) from K chunks of KC staged in
 // shared memory; the global loads of the next chunk are issued before the
-// products of the current one.  V is formed while it is staged, from the
-// tile's mode values A (held in shared memory for the whole block) and from
-// Y = h_R * U:  raman_mode 0: V = U;  1: V = (1 - fR) U + fR Y;  2: V = [U; Y]
-// (U_mm = |A_m|^2, U_mn = 2 Re(A_m A_n^*)).  A block loops over every row
-// block of its points, so NL is complete in the block: each D element adds
-// A_l R_r into NL_p (and A_p R_r into NL_l) with shared-memory atomics.
+// products of the current one.  A block loops over every row block of its
+// points, so each point's result is complete in the block.
 //
-// Gt is the reduced coupling matrix transposed and zero-padded:
-// [KKp][Pp], KKp a multiple of KC and Pp a multiple of TR.
+// The operand V is formed while it is staged:
+//   SRC 0, from the tile's mode values A (held in shared memory for the whole
+//     block) and from Y = h_R * U ([M+1][K][n]):
+//     MODE 0: V = U;  1: V = (1 - fR) U + fR Y;  2: V = [U; Y]
+//     (U_mm = |A_m|^2, U_mn = 2 Re(A_m A_n^*));
+//   SRC 1 (second GEMM of the low-rank coupling), from the rows of
+//     Z = W U and Y' = h_R * Z ([M+1][r][n]):  MODE 0: V = Z;
+//     1: V = (1 - fR) Z + fR Y'.
+// The result goes:
+//   OUT 0: to the l-sum NL_p = sum_l A_l R_(p,l), formed per (point, p) in a
+//     fixed order from the accumulators staged in shared memory (rows
+//     ordered by diagonal l - p); NL written at the end;
+//   OUT 1 (first GEMM of the low-rank coupling): D rows stored as Z
+//     ([M+1][rows][n]).
+//
+// Gt is the coupling matrix transposed and zero-padded: [KKp][Pp], KKp a
+// multiple of KC and Pp a multiple of TR.
 #pragma once
 
 #include "common.cuh"
@@ -39,15 +50,28 @@ template <typename R> __host__ __device__ constexpr size_t contract_tile_smem(in
          (size_t)TileCfg<R>::KC * (TileCfg<R>::TP + TileCfg<R>::TR) * sizeof(R);
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_contract_tile(Geo g, const cplx<R>* __restrict__ A, const R* __restrict__ Y,
-                                                       const R* __restrict__ Gt, int KKp, int Pp,
-                                                       const int2* __restrict__ rows, const int2* __restrict__ pairs,
-                                                       cplx<R>* __restrict__ NL, const LoopState* __restrict__ ls) {
+// Operands of one launch.  KK: the K dimension (K, KK or r); rows: the rows
+// with a result (P, or r for OUT 1); Ys: Y (SRC 0) or Y' (SRC 1); Zs: Z
+// (SRC 1); Zout: Z (OUT 1); cnt: the row count of Ys / Zs / Zout.
+template <typename R>
+struct TileArgs {
+  const cplx<R>* A;
+  const R* Ys;
+  const R* Zs;
+  const R* Gt;
+  int KK, KKp, Pp, rows, cnt;
+  const int2* rowpl;  // (p, l) of each row (OUT 0)
+  const int2* pairs;  // (m, n) of each pair term (SRC 0)
+  cplx<R>* NL;
+  R* Zout;
+};
+
+template <typename R, int MODE, int SRC, int OUT>
+__global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, const LoopState* __restrict__ ls) {
   using C = TileCfg<R>;
   constexpr int TP = C::TP, TR = C::TR, TM = C::TM, TN = C::TN, KC = C::KC;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = g.N, n = g.n, K = g.K, KK = g.KK;
+  const int N = g.N, n = g.n, K = g.K, KK = a.KK;
   cplx<R>* As = reinterpret_cast<cplx<R>*>(smraw);  // [N][TP]
   cplx<R>* Ns = As + (size_t)N * TP;                // [N][TP]
   R* Vs = reinterpret_cast<R*>(Ns + (size_t)N * TP);  // [KC][TP]
@@ -64,12 +88,12 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, const cplx<R>* __r
   for (int i = tid; i < N * TP; i += 256) {
     const int l = i / TP, q = i - l * TP;
     const size_t pt = pt0 + q;
-    cplx<R> a = mk<R>(0, 0);
+    cplx<R> v = mk<R>(0, 0);
     if (pt < npts) {
       const size_t j = pt / n, t = pt - j * n;
-      if (!(iter > 0 && j == 0)) a = A[(j * N + l) * n + t];
+      if (!(iter > 0 && j == 0)) v = a.A[(j * N + l) * n + t];
     }
-    As[i] = a;
+    As[i] = v;
     Ns[i] = mk<R>(0, 0);
   }
   // the V-chunk elements this thread stages: point q, chunk rows
@@ -79,43 +103,54 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, const cplx<R>* __r
   const size_t ptq = pt0 + q;
   const bool okq = ptq < npts && !(iter > 0 && ptq < (size_t)n);
   const size_t jq = ptq < npts ? ptq / n : 0, tq = ptq < npts ? ptq - jq * n : 0;
-  const R* yq = Y + jq * (size_t)K * n + tq;
+  const R* yq = a.Ys + (jq * (size_t)a.cnt) * n + tq;
+  const R* zq = SRC == 1 ? a.Zs + (jq * (size_t)a.cnt) * n + tq : nullptr;
   const R fR = (R)g.fR, fK = (R)(1.0 - g.fR);
-  R yreg[NV], greg[NG];
+  R yreg[NV], zreg[NV], greg[NG];
   // global loads of chunk k0 into registers (issued one chunk ahead)
   auto fetch = [&](int rb, int k0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       const int k = k0 + kq + KSTEP * i;
-      const bool need = okq && k < KK && (MODE == 1 || (MODE == 2 && k >= K));
-      yreg[i] = need ? yq[(size_t)(MODE == 2 ? k - K : k) * n] : (R)0;
+      const bool ok = okq && k < KK;
+      if (SRC == 0) {
+        const bool need = ok && (MODE == 1 || (MODE == 2 && k >= K));
+        yreg[i] = need ? yq[(size_t)(MODE == 2 ? k - K : k) * n] : (R)0;
+      } else {
+        zreg[i] = ok ? zq[(size_t)k * n] : (R)0;
+        yreg[i] = (ok && MODE == 1) ? yq[(size_t)k * n] : (R)0;
+      }
     }
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
       const int e = tid + 256 * i, kk = e / TR, r = e - kk * TR;
-      greg[i] = Gt[(size_t)(k0 + kk) * Pp + rb + r];
+      greg[i] = a.Gt[(size_t)(k0 + kk) * a.Pp + rb + r];
     }
   };
-  // V from U (shared memory) and the fetched Y; G as fetched
+  // V from U (shared memory) and the fetched rows; G as fetched
   auto stage = [&](int k0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       const int kk = kq + KSTEP * i, k = k0 + kk;
       R v = (R)0;
       if (okq && k < KK) {
-        R u = (R)0;
-        if (MODE != 2 || k < K) {
-          const int2 mn = pairs[k];
-          const cplx<R> am = As[mn.x * TP + q];
-          if (mn.x == mn.y) u = am.x * am.x + am.y * am.y;
-          else {
-            const cplx<R> an = As[mn.y * TP + q];
-            u = (R)2 * (am.x * an.x + am.y * an.y);
+        if (SRC == 0) {
+          R u = (R)0;
+          if (MODE != 2 || k < K) {
+            const int2 mn = a.pairs[k];
+            const cplx<R> am = As[mn.x * TP + q];
+            if (mn.x == mn.y) u = am.x * am.x + am.y * am.y;
+            else {
+              const cplx<R> an = As[mn.y * TP + q];
+              u = (R)2 * (am.x * an.x + am.y * an.y);
+            }
           }
+          if (MODE == 0) v = u;
+          else if (MODE == 1) v = fK * u + fR * yreg[i];
+          else v = k < K ? u : yreg[i];
+        } else {
+          v = MODE == 1 ? fK * zreg[i] + fR * yreg[i] : zreg[i];
         }
-        if (MODE == 0) v = u;
-        else if (MODE == 1) v = fK * u + fR * yreg[i];
-        else v = k < K ? u : yreg[i];
       }
       Vs[kk * TP + q] = v;
     }
@@ -124,52 +159,119 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, const cplx<R>* __r
   };
   __syncthreads();
 
-  for (int rb = 0; rb < Pp; rb += TR) {
+  for (int rb = 0; rb < a.Pp; rb += TR) {
     R acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int jn = 0; jn < TN; ++jn) acc[i][jn] = (R)0;
     fetch(rb, 0);
-    for (int k0 = 0; k0 < KKp; k0 += KC) {
+    for (int k0 = 0; k0 < a.KKp; k0 += KC) {
       stage(k0);
       __syncthreads();
-      if (k0 + KC < KKp) fetch(rb, k0 + KC);  // in flight during the products below
+      if (k0 + KC < a.KKp) fetch(rb, k0 + KC);  // in flight during the products below
 #pragma unroll
       for (int kk = 0; kk < KC; ++kk) {
-        R a[TM], b[TN];
+        R av[TM], bv[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = Vs[kk * TP + ty * TM + i];
+        for (int i = 0; i < TM; ++i) av[i] = Vs[kk * TP + ty * TM + i];
 #pragma unroll
-        for (int jn = 0; jn < TN; ++jn) b[jn] = Gs[kk * TR + tx + 16 * jn];
+        for (int jn = 0; jn < TN; ++jn) bv[jn] = Gs[kk * TR + tx + 16 * jn];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int jn = 0; jn < TN; ++jn) acc[i][jn] += a[i] * b[jn];
+          for (int jn = 0; jn < TN; ++jn) acc[i][jn] += av[i] * bv[jn];
       }
       __syncthreads();
     }
-    // l-sum: NL_p += A_l R_(p,l), NL_l += A_p R_(p,l)
+    if (OUT == 0) {
+      // l-sum NL_p = sum_l A_l R_(p,l) over this block's rows, 32 rows at a
+      // time: the accumulators go to shared memory (the V and G chunks, free
+      // now), then each thread adds, for the (point, p) items it owns, the
+      // rows (p, p + d) and (p - d, p) of the diagonals d the 32 rows cover
+      // (rows are ordered by diagonal; row (p, p + d) is dstart(d) + p).
+      R* Ds = Vs;  // [32][TP]
+      static_assert(KC * (TP + TR) >= 32 * TP, "the row chunk fits in the V and G chunks");
 #pragma unroll
-    for (int jn = 0; jn < TN; ++jn) {
-      const int r = rb + tx + 16 * jn;
-      if (r >= g.P) continue;
-      const int2 pl = rows[r];
+      for (int c = 0; c < TR / 32; ++c) {
 #pragma unroll
-      for (int i = 0; i < TM; ++i) {
-        const int qq = ty * TM + i;
-        const R v = acc[i][jn];
-        const cplx<R> al = As[pl.y * TP + qq];
-        atomicAdd(&Ns[pl.x * TP + qq].x, al.x * v);
-        atomicAdd(&Ns[pl.x * TP + qq].y, al.y * v);
-        if (pl.x != pl.y) {
-          const cplx<R> ap = As[pl.x * TP + qq];
-          atomicAdd(&Ns[pl.y * TP + qq].x, ap.x * v);
-          atomicAdd(&Ns[pl.y * TP + qq].y, ap.y * v);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int i = 0; i < TM; ++i) Ds[(tx + 16 * h) * TP + ty * TM + i] = acc[i][2 * c + h];
+        __syncthreads();
+        const int r0 = rb + 32 * c;
+        if (r0 < a.rows) {
+          const int r1 = min(r0 + 32, a.rows) - 1;
+          const int2 first = a.rowpl[r0], last = a.rowpl[r1];
+          const int d_lo = first.y - first.x, d_hi = last.y - last.x;
+          for (int item = tid; item < N * TP; item += 256) {
+            const int p = item / TP, qq = item - p * TP;
+            cplx<R> v = Ns[item];
+            for (int d = d_lo; d <= d_hi; ++d) {
+              const int ds = d * N - d * (d - 1) / 2;
+              if (p + d < N) {
+                const int rr = ds + p;
+                if (rr >= r0 && rr <= r1) {
+                  const R x = Ds[(rr - r0) * TP + qq];
+                  const cplx<R> al = As[(p + d) * TP + qq];
+                  v.x += al.x * x;
+                  v.y += al.y * x;
+                }
+              }
+              if (d > 0 && p >= d) {
+                const int rr = ds + p - d;
+                if (rr >= r0 && rr <= r1) {
+                  const R x = Ds[(rr - r0) * TP + qq];
+                  const cplx<R> al = As[(p - d) * TP + qq];
+                  v.x += al.x * x;
+                  v.y += al.y * x;
+                }
+              }
+            }
+            Ns[item] = v;
+          }
+        }
+        __syncthreads();
+      }
+    } else {
+      // rows of Z: [M+1][cnt][n]
+      bool vec = false;
+      if constexpr (sizeof(R) == 4 && TM % 4 == 0) {
+        // the tile lies in one substep: each thread writes its TM
+        // consecutive points of a row as 16-byte vectors
+        vec = pt0 / n == (pt0 + TP - 1) / n && pt0 + TP <= npts;
+        if (vec) {
+          const size_t j = pt0 / n, t0 = pt0 - j * n + ty * TM;
+          R* z = a.Zout + (j * (size_t)a.cnt) * n + t0;
+#pragma unroll
+          for (int jn = 0; jn < TN; ++jn) {
+            const int r = rb + tx + 16 * jn;
+            if (r >= a.rows) continue;
+#pragma unroll
+            for (int i = 0; i < TM; i += 4)
+              *reinterpret_cast<float4*>(z + (size_t)r * n + i) =
+                  make_float4(acc[i][jn], acc[i + 1][jn], acc[i + 2][jn], acc[i + 3][jn]);
+          }
+        }
+      }
+      if (!vec) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          const size_t pt = pt0 + ty * TM + i;
+          if (pt >= npts) continue;
+          const size_t j = pt / n, t = pt - j * n;
+          if (iter > 0 && j == 0) continue;
+          R* z = a.Zout + (j * (size_t)a.cnt) * n + t;
+#pragma unroll
+          for (int jn = 0; jn < TN; ++jn) {
+            const int r = rb + tx + 16 * jn;
+            if (r < a.rows) z[(size_t)r * n] = acc[i][jn];
+          }
         }
       }
     }
   }
+  if (OUT != 0) return;
   __syncthreads();
   for (int i = tid; i < N * TP; i += 256) {
     const int p = i / TP, qq = i - p * TP;
@@ -177,7 +279,7 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, const cplx<R>* __r
     if (pt >= npts) continue;
     const size_t j = pt / n, t = pt - j * n;
     if (iter > 0 && j == 0) continue;
-    NL[(j * N + p) * n + t] = Ns[i];
+    a.NL[(j * N + p) * n + t] = Ns[i];
   }
 }
 

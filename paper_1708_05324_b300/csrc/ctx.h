@@ -50,9 +50,11 @@ struct gm_job {
   } graphs[2];
   size_t bytes = 0;
   // mixed precision: blocked BF16 hi/lo pair-term operand and its TMA maps
-  __nv_bfloat16* Vhi = nullptr;  // [KKp/8][(M+1) n][8]
+  __nv_bfloat16* Vhi = nullptr;  // [KKp/8][(M+1) n][8] (and [rKKp/8][..][8] for the low-rank GEMM 2)
   __nv_bfloat16* Vlo = nullptr;
   CUtensorMap mapHi, mapLo;
+  CUtensorMap mapHi2, mapLo2;    // the same buffers with rKKp columns (low-rank GEMM 2)
+  void* Z = nullptr;             // low-rank: Z = W U, [M+1][r][n] R
 };
 
 struct gmmnlse_ctx {
@@ -79,6 +81,21 @@ struct gmmnlse_ctx {
   CUtensorMap mapGhi, mapGlo;
   void* Gt = nullptr;            // [KKt][Pt] R: G transposed, zero-padded (N > 8, CUDA cores)
   int KKt = 0, Pt = 0;
+  int2* rows_t = nullptr;        // [P] (p, l) of the rows of Gt and Xt: by diagonals l - p, so that
+                                 // neighbouring rows of a tile have distinct p and l (l-sum atomics)
+  // low-rank coupling G = X W (N > 8, S^R = S^K): X [P][r] orthonormal
+  // columns, W = X^T G [r][K]; Z = W U, Y' = h_R * Z, R = X V'
+  bool lr = false;
+  int r = 0;
+  int eW = 0;                    // max_s sum_k |W[s][k]| < 2^eW (|Z| < 2^eW max |U|)
+  void* Wt = nullptr;            // [KKt][rP1] R: W^T, CUDA-core GEMM 1 (rows r padded to rP1)
+  void* Xt = nullptr;            // [rK2][Pt] R: X^T, CUDA-core GEMM 2 (K = r padded to rK2)
+  int rP1 = 0, rK2 = 0;
+  int NB1 = 0, r_rows = 0;       // tensor cores: row block of GEMM 1, r padded to whole blocks
+  int rKKp = 0;                  // tensor cores: r padded to 64 (K of GEMM 2)
+  int eW16 = 0, eX16 = 0;        // FP16 exponents of W and X
+  __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
+  CUtensorMap mapWhi, mapWlo, mapXhi, mapXlo;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   gm_job* job = nullptr;        // workspace of gmmnlse_propagate
@@ -164,16 +181,25 @@ static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const
     case 7: launch_contract_n<R, 7>(g, c, A, V, NL, ls, s); return;
     case 8: launch_contract_n<R, 8>(g, c, A, V, NL, ls, s); return;
     default: {
+      gm::TileArgs<R> a = {};
+      a.A = (const gm::cplx<R>*)A;
+      a.Ys = (const R*)V;
+      a.Gt = (const R*)c->Gt;
+      a.KK = c->KK;
+      a.KKp = c->KKt;
+      a.Pp = c->Pt;
+      a.rows = c->P;
+      a.cnt = c->K;
+      a.rowpl = (const int2*)c->rows_t;
+      a.pairs = (const int2*)c->pairs;
+      a.NL = (gm::cplx<R>*)NL;
       const size_t pts = (size_t)(g.M + 1) * g.n;
       const dim3 grid((unsigned)((pts + gm::TileCfg<R>::TP - 1) / gm::TileCfg<R>::TP));
       const size_t smem = gm::contract_tile_smem<R>(c->N);
-      auto go = [&](auto kern) {
-        pdl_launch(kern, grid, dim3(256), smem, s, g, (const gm::cplx<R>*)A, (const R*)V, (const R*)c->Gt, c->KKt,
-                   c->Pt, (const int2*)c->rows, (const int2*)c->pairs, (gm::cplx<R>*)NL, ls);
-      };
-      if (c->raman_mode == 0) go(gm::k_contract_tile<R, 0>);
-      else if (c->raman_mode == 1) go(gm::k_contract_tile<R, 1>);
-      else go(gm::k_contract_tile<R, 2>);
+      auto go = [&](auto kern) { pdl_launch(kern, grid, dim3(256), smem, s, g, a, ls); };
+      if (c->raman_mode == 0) go(gm::k_contract_tile<R, 0, 0, 0>);
+      else if (c->raman_mode == 1) go(gm::k_contract_tile<R, 1, 0, 0>);
+      else go(gm::k_contract_tile<R, 2, 0, 0>);
     }
   }
 }

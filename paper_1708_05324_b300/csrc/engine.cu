@@ -152,25 +152,148 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->G);
   cudaFree(c->Gt);
   cudaFree(c->rows);
+  cudaFree(c->rows_t);
   cudaFree(c->pairs);
   cudaFree(c->Ghi);
+  cudaFree(c->Wt);
+  cudaFree(c->Xt);
+  cudaFree(c->Whi);
+  cudaFree(c->Wlo);
+  cudaFree(c->Xhi);
+  cudaFree(c->Xlo);
   cudaFree(c->Glo);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
+// Rank-revealing factorisation G = X W of the reduced coupling matrix
+// (P x K, row-major): Gram-Schmidt with column pivoting, each new direction
+// orthogonalised twice.  X (P x r) has orthonormal columns and W = X^T G
+// (r x K), so G - X W is the residual of the projection onto the span of X,
+// whose columns are all below tol x the largest column of G.  (The pair
+// matrix of S is a Gram matrix of mode products F_p F_l, which are linearly
+// dependent for the fibres here, so r < K exactly.)
+static int lowrank(const std::vector<double>& G, int P, int K, double tol, std::vector<double>& X,
+                   std::vector<double>& W) {
+  std::vector<double> Rm((size_t)P * K);  // residual, column-major
+  for (int p = 0; p < P; ++p)
+    for (int k = 0; k < K; ++k) Rm[(size_t)k * P + p] = G[(size_t)p * K + k];
+  auto colnorm2 = [&](int k) {
+    double a = 0.0;
+    for (int p = 0; p < P; ++p) a += Rm[(size_t)k * P + p] * Rm[(size_t)k * P + p];
+    return a;
+  };
+  double n0 = 0.0;
+  for (int k = 0; k < K; ++k) n0 = std::max(n0, colnorm2(k));
+  std::vector<double> Q;  // columns of X, column-major
+  int r = 0;
+  while (r < std::min(P, K) && n0 > 0.0) {
+    int c = 0;
+    double best = -1.0;
+    for (int k = 0; k < K; ++k) {
+      const double a = colnorm2(k);
+      if (a > best) {
+        best = a;
+        c = k;
+      }
+    }
+    if (!(best > tol * tol * n0)) break;
+    std::vector<double> q(Rm.begin() + (size_t)c * P, Rm.begin() + (size_t)(c + 1) * P);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int s = 0; s < r; ++s) {
+        double d = 0.0;
+        for (int p = 0; p < P; ++p) d += Q[(size_t)s * P + p] * q[p];
+        for (int p = 0; p < P; ++p) q[p] -= d * Q[(size_t)s * P + p];
+      }
+      double nq = 0.0;
+      for (int p = 0; p < P; ++p) nq += q[p] * q[p];
+      nq = std::sqrt(nq);
+      if (!(nq > 0.0)) return r;
+      for (int p = 0; p < P; ++p) q[p] /= nq;
+    }
+    for (int k = 0; k < K; ++k) {
+      double* col = &Rm[(size_t)k * P];
+      double d = 0.0;
+      for (int p = 0; p < P; ++p) d += q[p] * col[p];
+      for (int p = 0; p < P; ++p) col[p] -= d * q[p];
+    }
+    Q.insert(Q.end(), q.begin(), q.end());
+    ++r;
+  }
+  X.assign((size_t)P * r, 0.0);
+  W.assign((size_t)r * K, 0.0);
+  for (int s = 0; s < r; ++s)
+    for (int p = 0; p < P; ++p) X[(size_t)p * r + s] = Q[(size_t)s * P + p];
+  for (int s = 0; s < r; ++s)
+    for (int k = 0; k < K; ++k) {
+      double a = 0.0;
+      for (int p = 0; p < P; ++p) a += Q[(size_t)s * P + p] * G[(size_t)p * K + k];
+      W[(size_t)s * K + k] = a;
+    }
+  return r;
+}
+
+// 14 - e for the largest |x| below 2^e: the FP16 scale exponent that puts
+// the largest entry below 2^14.
+static int f16_exp(const std::vector<double>& m) {
+  double a = 0.0;
+  for (double x : m) a = std::max(a, std::fabs(x));
+  if (!(a > 0.0)) return 0;
+  int e;
+  std::frexp(a, &e);
+  return 14 - e;
+}
+
+// A row-major [rows][cols] matrix scaled by 2^e, split into 16-bit hi + lo
+// (FP16 when f16, else BF16) in the blocked layout [cols_pad/8][rows_pad][8]
+// (K-major core matrices) read by the tensor-core GEMM; zero padding.
+static int upload_hilo(const std::vector<double>& m, int rows, int cols, int rows_pad, int cols_pad, bool f16,
+                       int e, __nv_bfloat16** hi, __nv_bfloat16** lo) {
+  std::vector<__nv_bfloat16> gh((size_t)rows_pad * cols_pad), gl((size_t)rows_pad * cols_pad);
+  for (int r = 0; r < rows_pad; ++r)
+    for (int k = 0; k < cols_pad; ++k) {
+      const float x = (r < rows && k < cols) ? (float)std::ldexp(m[(size_t)r * cols + k], e) : 0.f;
+      const size_t o = ((size_t)(k / 8) * rows_pad + r) * 8 + (k % 8);
+      if (f16) {
+        const __half h = __float2half_rn(x), l = __float2half_rn(x - __half2float(h));
+        std::memcpy(&gh[o], &h, 2);
+        std::memcpy(&gl[o], &l, 2);
+      } else {
+        gh[o] = __float2bfloat16_rn(x);
+        gl[o] = __float2bfloat16_rn(x - __bfloat162float(gh[o]));
+      }
+    }
+  CK(cudaMalloc(hi, gh.size() * 2));
+  CK(cudaMalloc(lo, gl.size() * 2));
+  CK(cudaMemcpy(*hi, gh.data(), gh.size() * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(*lo, gl.data(), gl.size() * 2, cudaMemcpyHostToDevice));
+  return GMMNLSE_OK;
+}
+
+// A row-major [rows][cols] matrix transposed to [cols_pad][rows_pad] in R,
+// zero padding (the G operand of the CUDA-core tiled GEMM).
 template <typename R>
-static int upload_tables(gmmnlse_ctx* c, const std::vector<double>& Gd) {
+static int upload_transposed(const std::vector<double>& m, int rows, int cols, int rows_pad, int cols_pad,
+                             void** out) {
+  std::vector<R> t((size_t)cols_pad * rows_pad, (R)0);
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < cols; ++k) t[(size_t)k * rows_pad + r] = (R)m[(size_t)r * cols + k];
+  CK(cudaMalloc(out, t.size() * sizeof(R)));
+  CK(cudaMemcpy(*out, t.data(), t.size() * sizeof(R), cudaMemcpyHostToDevice));
+  return GMMNLSE_OK;
+}
+
+// Gd: the reduced coupling matrix in the standard row order; Gdiag: the same
+// rows by diagonals (for the CUDA-core tiles, N > 8).
+template <typename R>
+static int upload_tables(gmmnlse_ctx* c, const std::vector<double>& Gd, const std::vector<double>& Gdiag) {
   std::vector<R> Gr(Gd.size());
   for (size_t i = 0; i < Gd.size(); ++i) Gr[i] = (R)Gd[i];
   CK(cudaMalloc(&c->G, Gr.size() * sizeof(R) + 16));
   CK(cudaMemcpy(c->G, Gr.data(), Gr.size() * sizeof(R), cudaMemcpyHostToDevice));
   if (c->Pt > 0) {
-    std::vector<R> Gt((size_t)c->KKt * c->Pt, (R)0);
-    for (int r = 0; r < c->P; ++r)
-      for (int k = 0; k < c->KK; ++k) Gt[(size_t)k * c->Pt + r] = (R)Gd[(size_t)r * c->KK + k];
-    CK(cudaMalloc(&c->Gt, Gt.size() * sizeof(R)));
-    CK(cudaMemcpy(c->Gt, Gt.data(), Gt.size() * sizeof(R), cudaMemcpyHostToDevice));
+    const int rc = upload_transposed<R>(Gdiag, c->P, c->KK, c->Pt, c->KKt, &c->Gt);
+    if (rc) return rc;
   }
   CK(cudaMalloc(&c->H, (size_t)c->n * sizeof(cplx<R>)));
   // integrand prefactor gamma0 s(w_q), s = 1 + w_q/omega0 with self-steepening
@@ -283,12 +406,41 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   }
 
   // CUDA-core tiled contraction (N > 8): G transposed, padded to whole tiles
+  const int KC = TileCfg<float>::KC, TR = TileCfg<float>::TR;
+  static_assert(TileCfg<float>::KC == TileCfg<double>::KC && TileCfg<float>::TR == TileCfg<double>::TR,
+                "one padding for both precisions");
   if (N > 8) {
-    const int KC = TileCfg<float>::KC, TR = TileCfg<float>::TR;
-    static_assert(TileCfg<float>::KC == TileCfg<double>::KC && TileCfg<float>::TR == TileCfg<double>::TR,
-                  "one padding for both precisions");
     c->KKt = (c->KK + KC - 1) / KC * KC;
     c->Pt = (c->P + TR - 1) / TR * TR;
+  }
+
+  // low-rank coupling G = X W (N > 8 with S^R = S^K), used when the rank is
+  // at most 3/4 of K; GMMNLSE_DENSE=1 keeps the dense contraction
+  std::vector<double> Xd, Wd, Gt_rows, Xt_rows;
+  const char* dense_env = getenv("GMMNLSE_DENSE");
+  if (N > 8 && c->raman_mode != 2 && !(dense_env && dense_env[0] == '1')) {
+    const int r = lowrank(Gd, c->P, c->K, 1e-12, Xd, Wd);
+    if (r > 0 && 4 * r <= 3 * c->K) {
+      c->lr = true;
+      c->r = r;
+      double ws = 0.0;
+      for (int s = 0; s < r; ++s) {
+        double a = 0.0;
+        for (int k = 0; k < c->K; ++k) a += std::fabs(Wd[(size_t)s * c->K + k]);
+        ws = std::max(ws, a);
+      }
+      int e;
+      std::frexp(ws, &e);  // ws < 2^e
+      c->eW = e;
+      c->rP1 = (r + TR - 1) / TR * TR;
+      c->rK2 = (r + KC - 1) / KC * KC;
+      if (c->tc) {
+        const int nblk = (r + 255) / 256;
+        c->NB1 = ((r + nblk - 1) / nblk + 15) / 16 * 16;
+        c->r_rows = c->NB1 * nblk;
+        c->rKKp = (r + TC_KC - 1) / TC_KC * TC_KC;
+      }
+    }
   }
 
   // device copies
@@ -321,7 +473,38 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   CKC(cudaMemcpy(c->rows, pairs.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
   CKC(cudaMalloc(&c->pairs, c->K * sizeof(int2)));
   CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
-  rc = fp64 ? upload_tables<double>(c, Gd) : upload_tables<float>(c, Gd);
+  // CUDA-core tiles take their rows by diagonals (p, p + d): G and X rows
+  // permuted to that order, with the (p, l) table to match
+  if (N > 8) {
+    std::vector<int2> diag;
+    for (int d = 0; d < N; ++d)
+      for (int p = 0; p + d < N; ++p) diag.push_back(make_int2(p, p + d));
+    auto std_row = [&](int2 pl) { return pl.x * N - pl.x * (pl.x - 1) / 2 + (pl.y - pl.x); };
+    auto permute = [&](const std::vector<double>& m, int cols) {
+      std::vector<double> out(m.size());
+      for (int i = 0; i < c->P; ++i)
+        std::memcpy(&out[(size_t)i * cols], &m[(size_t)std_row(diag[i]) * cols], cols * sizeof(double));
+      return out;
+    };
+    Gt_rows = permute(Gd, c->KK);
+    if (c->lr) Xt_rows = permute(Xd, c->r);
+    CKC(cudaMalloc(&c->rows_t, c->P * sizeof(int2)));
+    CKC(cudaMemcpy(c->rows_t, diag.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  rc = fp64 ? upload_tables<double>(c, Gd, Gt_rows) : upload_tables<float>(c, Gd, Gt_rows);
+  if (!rc && c->lr) {
+    rc = fp64 ? upload_transposed<double>(Wd, c->r, c->K, c->rP1, c->KKt, &c->Wt)
+              : upload_transposed<float>(Wd, c->r, c->K, c->rP1, c->KKt, &c->Wt);
+    if (!rc)
+      rc = fp64 ? upload_transposed<double>(Xt_rows, c->P, c->r, c->Pt, c->rK2, &c->Xt)
+                : upload_transposed<float>(Xt_rows, c->P, c->r, c->Pt, c->rK2, &c->Xt);
+    if (!rc && c->tc) {
+      c->eW16 = c->f16 ? f16_exp(Wd) : 0;
+      c->eX16 = c->f16 ? f16_exp(Xd) : 0;
+      rc = upload_hilo(Wd, c->r, c->K, c->r_rows, c->KKp, c->f16, c->eW16, &c->Whi, &c->Wlo);
+      if (!rc) rc = upload_hilo(Xd, c->P, c->r, c->tc_rows, c->rKKp, c->f16, c->eX16, &c->Xhi, &c->Xlo);
+    }
+  }
   if (!rc && c->tc) {
     // G split into 16-bit hi + lo, blocked [KKp/8][rows][8] (K-major core
     // matrices); FP16 scaled by 2^eG so that its largest entry is below 2^14
@@ -394,6 +577,7 @@ static size_t job_bytes(const gmmnlse_ctx* c, int M) {
   b += (size_t)M * Nn * cs;                      // dpsi
   b += 4 * (size_t)(M + 1) * Nn * cs;            // A, NL, I, E
   if (c->raman_mode) b += (size_t)(M + 1) * c->K * c->n * rs;  // Y = h_R * U
+  if (c->lr) b += (size_t)(M + 1) * c->r * c->n * rs;          // Z = W U
   b += 2 * Nn * 16 * 2;                          // EM64, io
   b += sizeof(LoopState) + 64 + sizeof(double2) * TRAPZ_MAX_BLOCKS;
   if (c->tc) b += (size_t)2 * c->KKp * (M + 1) * c->n * 2;  // BF16 hi/lo operand
@@ -413,6 +597,7 @@ static void free_job(gm_job* jb) {
   cudaFree(jb->dpsi);
   cudaFree(jb->A);
   cudaFree(jb->V);
+  cudaFree(jb->Z);
   cudaFree(jb->NL);
   cudaFree(jb->I);
   cudaFree(jb->E);
@@ -477,6 +662,12 @@ int gm_make_g_maps(gmmnlse_ctx* c) {
   const int NB = tc_row_block(c->P);
   int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16);
   if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16);
+  if (!rc && c->lr) {
+    rc = tc_map(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16);
+    if (!rc) rc = tc_map(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16);
+    if (!rc) rc = tc_map(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16);
+    if (!rc) rc = tc_map(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16);
+  }
   return rc;
 }
 
@@ -484,6 +675,10 @@ int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
   const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
   int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS, c->f16);
   if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS, c->f16);
+  if (!rc && c->lr) {
+    rc = tc_map(&jb->mapHi2, jb->Vhi, npts, c->rKKp, TC_PTS, c->f16);
+    if (!rc) rc = tc_map(&jb->mapLo2, jb->Vlo, npts, c->rKKp, TC_PTS, c->f16);
+  }
   return rc;
 }
 
@@ -508,6 +703,7 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
   al(&jb->I, (size_t)(M + 1) * Nn * cs);
   al(&jb->E, (size_t)(M + 1) * Nn * cs);
   if (c->raman_mode) al(&jb->V, (size_t)(M + 1) * c->K * c->n * rs);
+  if (c->lr) al(&jb->Z, (size_t)(M + 1) * c->r * c->n * rs);
   al((void**)&jb->EM64, 2 * Nn * 16);
   al((void**)&jb->io, 2 * Nn * 16);
   al((void**)&jb->flag, sizeof(int));

@@ -129,18 +129,20 @@ __device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, 
 }
 
 // ---------------------------------------------------------------------------
-// K2: pair products and the Raman convolution Y_k = h_R * U_k for two pairs
+// K2: pair products and the Raman convolution Y_k = h_R * U_k for two rows
 // at once (U_k1 + i U_k2 is transformed, multiplied by H = (dt/n) DFT(h_R),
 // and transformed back; h_R is real so the real and imaginary parts stay
-// apart).  Only Y [M+1][K][n] is written: the contraction forms U from A.
-// grid (ceil(K/2), M+1)
+// apart).  SRC 0: the rows are the K pair products, formed from A; SRC 1
+// (low-rank coupling): the rows are the cnt = r rows of Z = W U
+// ([M+1][r][n]), read from Zs.  Only Y [M+1][cnt][n] is written: the
+// contraction forms U from A.  grid (ceil(cnt/2), M+1)
 // ---------------------------------------------------------------------------
-template <typename R, int EPT>
+template <typename R, int EPT, int SRC>
 __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
                                                       const cplx<R>* __restrict__ H,
                                                       const cplx<R>* __restrict__ tw,
-                                                      const int2* __restrict__ pairs,
-                                                      const LoopState* __restrict__ ls) {
+                                                      const int2* __restrict__ pairs, const R* __restrict__ Zs,
+                                                      int cnt, const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
@@ -148,19 +150,25 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
   if (ls->iter > 0 && j == 0) return;
   const int n = g.n;
   const int k1 = 2 * blockIdx.x, k2 = k1 + 1;
-  const bool has2 = k2 < g.K;
-  const int2 mn1 = pairs[k1];
-  const int2 mn2 = has2 ? pairs[k2] : mn1;
-  const cplx<R>* a = A + (size_t)j * g.N * n;
-  // the pair products are staged in shared memory first: the transform's
-  // first pass then reads no global memory, which keeps its registers free
+  const bool has2 = k2 < cnt;
+  // the rows are staged in shared memory first: the transform's first pass
+  // then reads no global memory, which keeps its registers free
+  if (SRC == 0) {
+    const int2 mn1 = pairs[k1];
+    const int2 mn2 = has2 ? pairs[k2] : mn1;
+    const cplx<R>* a = A + (size_t)j * g.N * n;
 #pragma unroll 4
-  for (int t = threadIdx.x; t < n; t += blockDim.x)
-    sm[pad16(t)] = mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+      sm[pad16(t)] = mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+  } else {
+    const R* z1 = Zs + ((size_t)j * cnt + k1) * n;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < n; t += blockDim.x) sm[pad16(t)] = mk<R>(z1[t], has2 ? z1[n + t] : (R)0);
+  }
   auto from_smem = [&](int q) { return sm[pad16(q)]; };
   auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
   fft_block<R, -1, EPT>(sm, n, tw, from_smem, to_smem);
-  R* y1 = Y + ((size_t)j * g.K + k1) * n;
+  R* y1 = Y + ((size_t)j * cnt + k1) * n;
   auto store = [&](int t, cplx<R> y) {
     y1[t] = y.x;
     if (has2) y1[n + t] = y.y;

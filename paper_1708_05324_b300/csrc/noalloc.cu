@@ -51,7 +51,7 @@ template <typename R> static size_t fft_bytes(int n) { return (size_t)fft_smem_e
 
 template <typename R, int EPT> static int set_attrs(int maxsm) {
   CKN(cudaFuncSetAttribute(k_ip_to_time<R, EPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-  CKN(cudaFuncSetAttribute(k_pairs_raman<R, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  CKN(cudaFuncSetAttribute(k_pairs_raman<R, EPT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
   CKN(cudaFuncSetAttribute(k_integrand<R, EPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
   return GMMNLSE_OK;
 }
@@ -70,9 +70,10 @@ static int setup_device(int dev, unsigned char** out) {
     if (!rc) rc = set_attrs<float, 32>(maxsm);
     if (!rc) rc = set_attrs<double, 16>(maxsm);
     if (rc) return rc;
-    for (auto kern : {k_contract_tile<float, 0>, k_contract_tile<float, 1>, k_contract_tile<float, 2>})
+    for (auto kern : {k_contract_tile<float, 0, 0, 0>, k_contract_tile<float, 1, 0, 0>, k_contract_tile<float, 2, 0, 0>})
       CKN(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    for (auto kern : {k_contract_tile<double, 0>, k_contract_tile<double, 1>, k_contract_tile<double, 2>})
+    for (auto kern : {k_contract_tile<double, 0, 0, 0>, k_contract_tile<double, 1, 0, 0>,
+                      k_contract_tile<double, 2, 0, 0>})
       CKN(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
@@ -218,8 +219,8 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
       k_ip_to_time<R, EPT, 1><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
                                                   (const cplx<R>*)w.E, (cplx<R>*)w.A, tw, w.ls);
       if (c->raman_mode)
-        k_pairs_raman<R, EPT><<<dim3((c->K + 1) / 2, Mj + 1), T, sm, s>>>(
-            g, (const cplx<R>*)w.A, (R*)w.V, (const cplx<R>*)c->H, tw, c->pairs, w.ls);
+        k_pairs_raman<R, EPT, 0><<<dim3((c->K + 1) / 2, Mj + 1), T, sm, s>>>(
+            g, (const cplx<R>*)w.A, (R*)w.V, (const cplx<R>*)c->H, tw, c->pairs, (const R*)nullptr, c->K, w.ls);
       launch_contract<R>(g, c, w.A, w.V, w.NL, w.ls, s);
       k_integrand<R, EPT, 1><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.NL, (const cplx<R>*)w.E, (const R*)c->fac,
                                                 (cplx<R>*)w.I, tw, w.ls);
@@ -260,6 +261,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
     st->energy_out = hs.spec[2] * c->prm.dt / n;
     st->photons_out = hs.spec[3];
     st->ms = 0.0;
+    st->coupling_rank = c->K;  // this entry point runs the dense contraction
   }
   if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
   if (hs.status == ST_NONFINITE) return GMMNLSE_E_NONFINITE;

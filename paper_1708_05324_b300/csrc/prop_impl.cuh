@@ -58,16 +58,22 @@ static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* o
   return GMMNLSE_OK;
 }
 
-// The tensor-core contraction is instantiated for these mode counts.
+// The tensor-core contraction is instantiated for these mode counts (l-sum
+// epilogue) and, for the first GEMM of the low-rank coupling, for every row
+// block NB = 16 .. 256 (store epilogue).
 template <class F>
 static int tc_for_each_n(F&& f) {
   int rc = GMMNLSE_OK;
   auto one = [&](auto kern) {
     if (!rc) rc = f(kern);
   };
-#define GM_TC_N(N) one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), false>);
+#define GM_TC_N(N) one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), 0>);
   GM_TC_N(9) GM_TC_N(10) GM_TC_N(11) GM_TC_N(12) GM_TC_N(13) GM_TC_N(14) GM_TC_N(15) GM_TC_N(16) GM_TC_N(42)
 #undef GM_TC_N
+#define GM_TC_S(NB) one(&k_tc_contract<0, NB, 1>);
+  GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
+  GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
+#undef GM_TC_S
   return rc;
 }
 
@@ -94,13 +100,18 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_integrand<R, 16, 4>, A, sm));
   CK(cudaFuncSetAttribute(k_integrand<R, 32, 1>, A, sm));
 
-  CK(cudaFuncSetAttribute(k_pairs_raman<R, 16>, A, sm));
-  CK(cudaFuncSetAttribute(k_pairs_raman<R, 32>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 16, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 32, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 16, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman<R, 32, 1>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 2>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 4>, A, sm));
-  CK(cudaFuncSetAttribute(k_contract_tile<R, 0>, A, sm));
-  CK(cudaFuncSetAttribute(k_contract_tile<R, 1>, A, sm));
-  CK(cudaFuncSetAttribute(k_contract_tile<R, 2>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 0, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 0, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 2, 0, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 0, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 1, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 1, 0>, A, sm));
   if (std::is_same<R, float>::value) {
     const int rc = tc_for_each_n([&](auto kern) -> int {
       cudaFuncAttributes fa;
@@ -210,14 +221,19 @@ static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
     pdl_launch_cl(kern, grid, dim3(threads), sm, s, cl, g, (const cplx<R>*)jb->A, (R*)jb->V,
                   (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const LoopState*)jb->ls);
   };
+  auto one = [&](auto kern, int ept) {
+    pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
+               (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)nullptr, c->K,
+               (const LoopState*)jb->ls);
+  };
   if (S > 1) {
     const int np = n / S;
     if (S == 2) args(k_pairs_raman_cl<R, 16, 2>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
     else args(k_pairs_raman_cl<R, 16, 4>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
   } else if (fft_ept<R>(n, pp * (g.M + 1)) == 32) {
-    args(k_pairs_raman<R, 32>, dim3(pp, g.M + 1), n / 32, fft_smem<R>(n), 1);
+    one(k_pairs_raman<R, 32, 0>, 32);
   } else {
-    args(k_pairs_raman<R, 16>, dim3(pp, g.M + 1), n / 16, fft_smem<R>(n), 1);
+    one(k_pairs_raman<R, 16, 0>, 16);
   }
 }
 
@@ -239,54 +255,188 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_integrand<R, 16, 4>);
 }
 
-// K3 on the tensor cores (mixed precision): form V and pack it to 16-bit hi/lo, then the
-// tcgen05 GEMM with the l-sum in its epilogue
+// The tcgen05 GEMM with the l-sum epilogue: V operand maps mV*, coupling
+// operand maps mG*, over the mode count of the context.
+static void launch_tc_lsum(gm_job* jb, const Geo& g, cudaStream_t s, const CUtensorMap& mVhi,
+                           const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
+                           const TcArgs& a) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int pts = (g.M + 1) * c->n;
+  const dim3 grid(std::min(pts / TC_PTS, 148));
+  switch (c->N) {
+#define GM_TC_CASE(NN)                                                                                     \
+  case NN: {                                                                                               \
+    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                    \
+    pdl_launch(k_tc_contract<NN, NB, 0>, grid, dim3(192), TcShape<NN, NB>::SMEM, s, mVhi, mVlo, mGhi, mGlo, a, \
+               (const LoopState*)jb->ls);                                                                  \
+    break;                                                                                                 \
+  }
+    GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
+    GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
+#undef GM_TC_CASE
+    default: break;
+  }
+}
+
+static TcArgs tc_args(gm_job* jb, const Geo& g) {
+  gmmnlse_ctx* c = jb->ctx;
+  TcArgs a = {};
+  a.f16 = c->f16 ? 1 : 0;
+  a.n = c->n;
+  a.M = g.M;
+  a.A = (const float2*)jb->A;
+  a.NL = (float2*)jb->NL;
+  a.err = &jb->ls->tc_err;
+  return a;
+}
+
+// Pack of V = U / (1 - fR) U + fR Y / [U; Y] from A and Y (K columns).
+static void launch_pack_pairs(gm_job* jb, const Geo& g, cudaStream_t s, int mode) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n;
+  const int npts_total = (jb->Mcap + 1) * n;
+  const int pts = (g.M + 1) * n;
+  const dim3 pgrid((pts + PACK_PTS - 1) / PACK_PTS);
+  auto pack = [&](auto kern) {
+    pdl_launch(kern, pgrid, dim3(PACK_PTS * PACK_WARPS), (size_t)c->N * PACK_PTS * sizeof(float2), s, g,
+               (const float2*)jb->A, (const float*)jb->V, (const int2*)c->pairs, c->KKp, npts_total,
+               (void*)jb->Vhi, (void*)jb->Vlo, (const LoopState*)jb->ls);
+  };
+  if (c->f16) {
+    if (mode == 0) pack(k_pack_hilo<0, true>);
+    else if (mode == 1) pack(k_pack_hilo<1, true>);
+    else pack(k_pack_hilo<2, true>);
+  } else {
+    if (mode == 0) pack(k_pack_hilo<0, false>);
+    else if (mode == 1) pack(k_pack_hilo<1, false>);
+    else pack(k_pack_hilo<2, false>);
+  }
+}
+
+// K3 on the tensor cores (mixed precision): form V and pack it to 16-bit
+// hi/lo, then the tcgen05 GEMM with the l-sum in its epilogue
 template <typename R>
 static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
   if constexpr (std::is_same<R, float>::value) {
     gmmnlse_ctx* c = jb->ctx;
-    const int n = c->n;
-    const int npts_total = (jb->Mcap + 1) * n;
-    const int pts = (g.M + 1) * n;
-    const dim3 pgrid((pts + PACK_PTS - 1) / PACK_PTS);
-    auto pack = [&](auto kern) {
-      pdl_launch(kern, pgrid, dim3(PACK_PTS * PACK_WARPS), (size_t)c->N * PACK_PTS * sizeof(float2), s, g,
-                 (const float2*)jb->A, (const float*)jb->V, (const int2*)c->pairs, c->KKp, npts_total,
-                 (void*)jb->Vhi, (void*)jb->Vlo, (const LoopState*)jb->ls);
-    };
-    if (c->f16) {
-      if (c->raman_mode == 0) pack(k_pack_hilo<0, true>);
-      else if (c->raman_mode == 1) pack(k_pack_hilo<1, true>);
-      else pack(k_pack_hilo<2, true>);
-    } else {
-      if (c->raman_mode == 0) pack(k_pack_hilo<0, false>);
-      else if (c->raman_mode == 1) pack(k_pack_hilo<1, false>);
-      else pack(k_pack_hilo<2, false>);
-    }
-    TcArgs a = {};
+    launch_pack_pairs(jb, g, s, c->raman_mode);
+    TcArgs a = tc_args(jb, g);
     a.KKp = c->KKp;
-    a.f16 = c->f16 ? 1 : 0;
     a.eG = c->eG;
-    a.n = n;
-    a.M = g.M;
-    a.A = (const float2*)jb->A;
-    a.NL = (float2*)jb->NL;
-    a.err = &jb->ls->tc_err;
-    const dim3 grid(std::min(pts / TC_PTS, 148));
-    switch (c->N) {
-#define GM_TC_CASE(NN)                                                                                      \
-  case NN: {                                                                                                \
-    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                     \
-    pdl_launch(k_tc_contract<NN, NB, false>, grid, dim3(192), TcShape<NN, NB>::SMEM, s, jb->mapHi, jb->mapLo, \
-               c->mapGhi, c->mapGlo, a, (const LoopState*)jb->ls);                                           \
-    break;                                                                                                  \
+    launch_tc_lsum(jb, g, s, jb->mapHi, jb->mapLo, c->mapGhi, c->mapGlo, a);
   }
-      GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
-      GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
-#undef GM_TC_CASE
-      default: break;
+}
+
+// ---------------------------------------------------------------------------
+// Low-rank coupling G = X W (N > 8, S^R = S^K).  Per point the bracket of
+// Eq. 1 becomes R = X V' with V' = (1 - fR) Z + fR h_R * Z and Z = W U, which
+// holds because the Raman convolution acts on time and W on the pair index:
+//   GEMM 1: Z = W U (r rows);  K2 on the r rows of Z;  GEMM 2: R = X V' and
+//   the l-sum.
+// ---------------------------------------------------------------------------
+template <typename R>
+static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const size_t pts = (size_t)(g.M + 1) * c->n;
+  if (c->tc) {
+    if constexpr (std::is_same<R, float>::value) {
+      launch_pack_pairs(jb, g, s, 0);
+      TcArgs a = tc_args(jb, g);
+      a.KKp = c->KKp;
+      a.eG = c->eW16;
+      a.nrb = c->r_rows / c->NB1;
+      a.Zout = (float*)jb->Z;
+      a.zrows = c->r;
+      const dim3 grid((unsigned)std::min<size_t>(pts / TC_PTS, 148));
+      switch (c->NB1) {
+#define GM_TC_S(NB)                                                                                       \
+  case NB:                                                                                                \
+    pdl_launch(k_tc_contract<0, NB, 1>, grid, dim3(192), TcShape<0, NB>::SMEM, s, jb->mapHi, jb->mapLo, \
+               c->mapWhi, c->mapWlo, a, (const LoopState*)jb->ls);                                        \
+    break;
+        GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
+        GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
+#undef GM_TC_S
+        default: break;
+      }
     }
+    return;
   }
+  TileArgs<R> a = {};
+  a.A = (const cplx<R>*)jb->A;
+  a.Ys = (const R*)jb->V;
+  a.Gt = (const R*)c->Wt;
+  a.KK = c->K;
+  a.KKp = c->KKt;
+  a.Pp = c->rP1;
+  a.rows = c->r;
+  a.cnt = c->r;
+  a.pairs = (const int2*)c->pairs;
+  a.Zout = (R*)jb->Z;
+  const dim3 grid((unsigned)((pts + TileCfg<R>::TP - 1) / TileCfg<R>::TP));
+  pdl_launch(k_contract_tile<R, 0, 0, 1>, grid, dim3(256), contract_tile_smem<R>(c->N), s, g, a,
+             (const LoopState*)jb->ls);
+}
+
+template <typename R>
+static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n, pp = (c->r + 1) / 2;
+  auto one = [&](auto kern, int ept) {
+    pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
+               (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)jb->Z, c->r,
+               (const LoopState*)jb->ls);
+  };
+  if (fft_ept<R>(n, pp * (g.M + 1)) == 32) one(k_pairs_raman<R, 32, 1>, 32);
+  else one(k_pairs_raman<R, 16, 1>, 16);
+}
+
+template <typename R>
+static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const size_t pts = (size_t)(g.M + 1) * c->n;
+  const int mode = c->raman_mode ? 1 : 0;
+  if (c->tc) {
+    if constexpr (std::is_same<R, float>::value) {
+      const int npts_total = (jb->Mcap + 1) * c->n;
+      auto pack = [&](auto kern) {
+        pdl_launch(kern, dim3((unsigned)((pts + 255) / 256)), dim3(256), 0, s, g, (const float*)jb->Z,
+                   (const float*)jb->V, c->r, c->rKKp, npts_total, (void*)jb->Vhi, (void*)jb->Vlo, c->eW,
+                   (const LoopState*)jb->ls);
+      };
+      if (c->f16) {
+        if (mode) pack(k_pack_rows<1, true>);
+        else pack(k_pack_rows<0, true>);
+      } else {
+        if (mode) pack(k_pack_rows<1, false>);
+        else pack(k_pack_rows<0, false>);
+      }
+      TcArgs a = tc_args(jb, g);
+      a.KKp = c->rKKp;
+      a.eG = c->eX16;
+      a.eVoff = c->eW;
+      launch_tc_lsum(jb, g, s, jb->mapHi2, jb->mapLo2, c->mapXhi, c->mapXlo, a);
+    }
+    return;
+  }
+  TileArgs<R> a = {};
+  a.A = (const cplx<R>*)jb->A;
+  a.Ys = (const R*)jb->V;
+  a.Zs = (const R*)jb->Z;
+  a.Gt = (const R*)c->Xt;
+  a.KK = c->r;
+  a.KKp = c->rK2;
+  a.Pp = c->Pt;
+  a.rows = c->P;
+  a.cnt = c->r;
+  a.rowpl = (const int2*)c->rows_t;
+  a.NL = (cplx<R>*)jb->NL;
+  const dim3 grid((unsigned)((pts + TileCfg<R>::TP - 1) / TileCfg<R>::TP));
+  auto go = [&](auto kern) {
+    pdl_launch(kern, grid, dim3(256), contract_tile_smem<R>(c->N), s, g, a, (const LoopState*)jb->ls);
+  };
+  if (mode) go(k_contract_tile<R, 1, 1, 0>);
+  else go(k_contract_tile<R, 0, 1, 0>);
 }
 
 // K5 with the convergence decision in its last block
@@ -304,9 +454,15 @@ template <typename R>
 static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   gmmnlse_ctx* c = jb->ctx;
   launch_k1<R>(jb, g, s);
-  if (c->raman_mode) launch_k2<R>(jb, g, s);
-  if (c->tc) launch_tc<R>(jb, g, s);
-  else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+  if (c->lr) {
+    launch_lr_z<R>(jb, g, s);
+    if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
+    launch_lr_r<R>(jb, g, s);
+  } else {
+    if (c->raman_mode) launch_k2<R>(jb, g, s);
+    if (c->tc) launch_tc<R>(jb, g, s);
+    else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+  }
   launch_k4<R>(jb, g, s);
   launch_k5<R>(jb, g, s, h, use_cond);
 }
@@ -533,6 +689,7 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
     st->energy_out = hs.spec[2] * c->prm.dt / c->n;
     st->photons_out = hs.spec[3];
     st->ms = ms;
+    st->coupling_rank = c->lr ? c->r : c->K;
   }
   if (hs.tc_err) {
     gm_set_last_error_text("tensor-core contraction: a wait for its operands timed out");
@@ -557,6 +714,11 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
   bytes[0] = M * Nn * 4 * cs;                     // psiR, dpsi, E -> A
   bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->K * c->n * rs) : 0.0;     // A -> Y
   bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->K * rs : 0.0));  // A, Y -> NL
+  if (c->lr) {
+    // A -> Z (GEMM 1), Z -> Y' (Raman); A, Z, Y' -> NL (GEMM 2)
+    bytes[1] = M * (Nn * cs + (double)c->r * c->n * rs * (c->raman_mode ? 3 : 1));
+    bytes[2] = M * (double)c->n * (2 * c->N * cs + (double)c->r * rs * (c->raman_mode ? 2 : 1));
+  }
   bytes[3] = M * Nn * 3 * cs + c->n * rs;         // NL, E -> I; prefactor table
   bytes[4] = Nn * ((M + 1) * cs + 2 * M * cs + cs); // I, dpsi old/new, psiR
   bytes[5] = Nn * (16 + cs + 16 + 16 + (c->fp64 ? 0 : cs));
@@ -567,7 +729,7 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
   const size_t Nsz = (size_t)c->N * c->n;
   for (int k = 0; k < 6; ++k) {
     ms[k] = 0.0;
-    if (k == 1 && !c->raman_mode) continue;
+    if (k == 1 && !c->raman_mode && !c->lr) continue;
     // iteration state: iter = 1 (substeps 1..M, the shape of every iteration after the first)
     CK(cudaMemcpyAsync(&jb->ls->iter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -575,9 +737,17 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
       if (r == 0) CK(cudaEventRecord(a, s));  // reps launches back to back after one warm-up
       switch (k) {
         case 0: launch_k1<R>(jb, g, s); break;
-        case 1: launch_k2<R>(jb, g, s); break;
+        case 1:
+          if (c->lr) {
+            launch_lr_z<R>(jb, g, s);
+            if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
+          } else {
+            launch_k2<R>(jb, g, s);
+          }
+          break;
         case 2:
-          if (c->tc) launch_tc<R>(jb, g, s);
+          if (c->lr) launch_lr_r<R>(jb, g, s);
+          else if (c->tc) launch_tc<R>(jb, g, s);
           else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
           break;
         case 3: launch_k4<R>(jb, g, s); break;

@@ -19,6 +19,9 @@
 // holds R_r(t) for its own point t and forms the l-sum in registers, with the
 // row -> (p, l) map resolved at compile time.
 //
+// The same kernel with OUT 1 stores the accumulator rows (times the inverse
+// FP16 scales) as Z = W U, the first GEMM of the low-rank coupling.
+//
 // Roles (192 threads): warp 0 issues TMA copies of K chunks (64 wide) of V
 // and G into a ring of stages; warp 1 issues tcgen05.mma from the ring into
 // one of two TMEM accumulators; warps 2-5 drain an accumulator (tcgen05.ld)
@@ -50,12 +53,14 @@ struct TcArgs {
   int KKp;           // K padded to a multiple of TC_KC
   int f16;           // operands FP16 (else BF16)
   int eG;            // FP16: G scaled by 2^eG
+  int eVoff;         // FP16: V scaled by 2^(eV - eVoff), eV from the energy bound
   int n, M;          // samples, substeps (tiles cover j = 0..M)
   const float2* A;   // [M+1][N][n]
   float2* NL;        // [M+1][N][n]
   unsigned* err;     // set to 1 if a wait times out
-  float* Rout;       // probe mode: [npts][NRB * NB] raw D
-  int npts;          // probe mode: number of points
+  int nrb;           // OUT 1: row blocks
+  float* Zout;       // OUT 1: D rows [M+1][zrows][n]
+  int zrows;         // OUT 1: rows stored (the rest is padding)
 };
 
 __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
@@ -146,7 +151,9 @@ __device__ __forceinline__ void drain_rb(int rb, uint32_t taddr, const float2* a
   }
 }
 
-template <int N, int NB, bool PROBE>
+// OUT 0: the l-sum epilogue into NL (N modes, compile-time); OUT 1: the
+// accumulator rows stored as Z (first GEMM of the low-rank coupling; N is 0).
+template <int N, int NB, int OUT>
 __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ CUtensorMap mapVhi,
                                                          const __grid_constant__ CUtensorMap mapVlo,
                                                          const __grid_constant__ CUtensorMap mapGhi,
@@ -179,12 +186,13 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   tc::fence_after_sync();
   pdl_enter();
   const uint32_t tmem = tmem_base;
-  const int iter = PROBE ? 0 : ls->iter;
+  const int iter = ls->iter;
+  const int nrb = OUT == 0 ? S::NRB : a.nrb;
   const int n = a.n;
-  const int ntiles = PROBE ? a.npts / TC_PTS : (a.M + 1) * (n / TC_PTS);
+  const int ntiles = (a.M + 1) * (n / TC_PTS);
   const int kchunks = a.KKp / TC_KC;
   // z0 tiles are skipped after the first iteration (their integrand is known)
-  auto live = [&](int tile) { return PROBE || iter == 0 || tile * TC_PTS >= n; };
+  auto live = [&](int tile) { return iter == 0 || tile * TC_PTS >= n; };
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
       int c = 0;
       for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
         if (!live(tile)) continue;
-        for (int rb = 0; rb < S::NRB && !*stop; ++rb)
+        for (int rb = 0; rb < nrb && !*stop; ++rb)
           for (int kc = 0; kc < kchunks; ++kc, ++c) {
             const int s = c % S::STAGES, round = c / S::STAGES;
             if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1)) {
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
       int c = 0, w = 0;
       for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
         if (!live(tile)) continue;
-        for (int rb = 0; rb < S::NRB && !*stop; ++rb, ++w) {
+        for (int rb = 0; rb < nrb && !*stop; ++rb, ++w) {
           const int acc = w & 1, use = w >> 1;
           if (use > 0 && !tc::mbar_wait(&acc_empty[acc], (use - 1) & 1)) {
             *stop = 1;
@@ -257,21 +265,24 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     // FP16: D = 2^(eV + eG) R; folded into the mode values of the l-sum
-    const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n) + a.eG)) : 1.0f;
+    const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n) - a.eVoff + a.eG)) : 1.0f;
     int w = 0;
+    constexpr int NA = N > 0 ? N : 1;
     for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
       if (!live(tile)) continue;
       const int pt = tile * TC_PTS + row_in_tile;
-      const int j = PROBE ? 0 : pt / n, t = PROBE ? 0 : pt - j * n;
-      float2 av[N], nl[N];
+      const int j = pt / n, t = pt - j * n;
+      float2 av[NA], nl[NA];
+      if (OUT == 0) {
 #pragma unroll
-      for (int l = 0; l < N; ++l) {
-        av[l] = PROBE ? make_float2(0.f, 0.f) : a.A[((size_t)j * N + l) * n + t];
-        av[l].x *= inv;
-        av[l].y *= inv;
-        nl[l] = make_float2(0.f, 0.f);
+        for (int l = 0; l < N; ++l) {
+          av[l] = a.A[((size_t)j * N + l) * n + t];
+          av[l].x *= inv;
+          av[l].y *= inv;
+          nl[l] = make_float2(0.f, 0.f);
+        }
       }
-      for (int rb = 0; rb < S::NRB; ++rb, ++w) {
+      for (int rb = 0; rb < nrb; ++rb, ++w) {
         const int acc = w & 1, use = w >> 1;
         if (!tc::mbar_wait(&acc_full[acc], use & 1)) {
           *stop = 1;
@@ -280,11 +291,16 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
         }
         tc::fence_after_sync();
         const uint32_t taddr = tmem + lane_off + (uint32_t)(acc * NB);
-        if (PROBE) {
+        if (OUT == 1) {
+          float* z = a.Zout + (size_t)j * a.zrows * n + t;
           for (int c0 = 0; c0 < NB; c0 += 16) {
             float v[16];
             tc::tmem_ld16(taddr + c0, v);
-            for (int i = 0; i < 16; ++i) a.Rout[(size_t)pt * (S::NRB * NB) + rb * NB + c0 + i] = v[i];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int r = rb * NB + c0 + i;
+              if (r < a.zrows) z[(size_t)r * n] = v[i] * inv;
+            }
           }
         } else {
           drain_rb<N, NB, 0>(rb, taddr, av, nl);
@@ -293,7 +309,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&acc_empty[acc])) : "memory");
       }
       if (*stop) break;
-      if (!PROBE) {
+      if (OUT == 0) {
         float2* out = a.NL + (size_t)j * N * n + t;
 #pragma unroll
         for (int p = 0; p < N; ++p) out[(size_t)p * n] = nl[p];
@@ -371,6 +387,47 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
         else if (MODE == 1) x = fK * U(k) + fR * y[(size_t)k * n];
         else x = k < g.K ? U(k) : y[(size_t)(k - g.K) * n];
       }
+      x *= scale;
+      hi[i] = H::rn(x);
+      lo[i] = H::rn(x - H::back(hi[i]));
+    }
+    const size_t o = ((size_t)kc * npts_total + pt) * 8;
+    *reinterpret_cast<uint4*>(Vhi + o) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(Vlo + o) = *reinterpret_cast<const uint4*>(lo);
+  }
+}
+
+// Low-rank coupling, second GEMM: V' = (1 - fR) Z + fR Y' (MODE 1) or Z
+// (MODE 0) from the rows of Z = W U and Y' = h_R * Z ([M+1][r][n]) to the
+// blocked 16-bit hi/lo layout [KKp/8][npts][8] (r padded with zeros to KKp);
+// FP16 scaled by 2^(eV - eVoff), since |Z| <= 2^eVoff max |U|.  One thread
+// per point; Z / Y' loads coalesced across the threads.
+template <int MODE, bool F16>
+__global__ void __launch_bounds__(256) k_pack_rows(Geo g, const float* __restrict__ Zs, const float* __restrict__ Ys,
+                                                   int r, int KKp, int npts_total, void* __restrict__ Vhi_,
+                                                   void* __restrict__ Vlo_, int eVoff,
+                                                   const LoopState* __restrict__ ls) {
+  using H = Half16<F16>;
+  using T = typename H::T;
+  T* Vhi = reinterpret_cast<T*>(Vhi_);
+  T* Vlo = reinterpret_cast<T*>(Vlo_);
+  pdl_enter();
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = g.n;
+  if (pt >= (g.M + 1) * n) return;
+  const int j = pt / n, t = pt - j * n;
+  if (ls->iter > 0 && j == 0) return;
+  const float* z = Zs + (size_t)j * r * n + t;
+  const float* y = Ys + (size_t)j * r * n + t;
+  const float fR = (float)g.fR, fK = (float)(1.0 - g.fR);
+  const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n) - eVoff) : 1.0f;
+  for (int kc = 0; kc < KKp / 8; ++kc) {
+    __align__(16) T hi[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = kc * 8 + i;
+      float x = 0.f;
+      if (k < r) x = MODE == 1 ? fK * z[(size_t)k * n] + fR * y[(size_t)k * n] : z[(size_t)k * n];
       x *= scale;
       hi[i] = H::rn(x);
       lo[i] = H::rn(x - H::back(hi[i]));

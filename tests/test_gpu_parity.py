@@ -328,6 +328,30 @@ def test_mixed_dense_42_mode_contraction(mixed):
     assert rel(out, ref) < 1e-3
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
+def test_low_rank_coupling_matches_dense(precision, monkeypatch):
+    """The 15-mode GRIN fiber: the pair matrix of S is the Gram matrix of the
+    products of Hermite-Gauss modes of total order <= 4, which span the 45
+    monomials x^i y^j, i + j <= 8, times one Gaussian: rank 45 of K = 120.
+    The low-rank path (Z = W U, h_R * Z, R = X V') against the oracle and
+    against the dense contraction (GMMNLSE_DENSE=1)."""
+    key = ("m", 15, 256, 0.18)
+    prob = small(*key)
+    ref, _ = oracle_small(key)
+    tol = 1e-13 if precision == "fp64" else 1e-9
+    low, st_low, rc = gpu_run(prob, precision, tol=tol)
+    assert rc == B.OK
+    assert st_low["coupling_rank"] == 45
+    monkeypatch.setenv("GMMNLSE_DENSE", "1")
+    dense, st_dense, rc = gpu_run(prob, precision, tol=tol)
+    assert rc == B.OK
+    assert st_dense["coupling_rank"] == 120
+    bar = TOL.get(precision, 1e-3)
+    assert rel(low, ref) < bar
+    assert rel(dense, ref) < bar
+    assert rel(low, dense) < (1e-11 if precision == "fp64" else 1e-5)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_dense_42_mode_contraction_cuda_cores(precision):
     """The FP32 and FP64 paths of the 42-mode workload: the tiled CUDA-core
