@@ -126,8 +126,8 @@ def launches_per_step(st, raman, mixed=False, fp64=False, graph=True):
     if not fp64:
         n += 1               # psi0 rounded to the working precision
     n += 1 + fft             # output sums, inverse transform
-    # per long step: loop re-arm (graph only), advance, bookkeeping
-    n += st["iters_total"] * per_iter + st["long_steps"] * (3 if graph else 2)
+    # per long step: the advance (bookkeeping in its last block)
+    n += st["iters_total"] * per_iter + st["long_steps"]
     return n
 
 

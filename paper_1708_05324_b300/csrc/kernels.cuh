@@ -481,40 +481,12 @@ __global__ void __launch_bounds__(TRAPZ_T) k_trapz(Geo g, const cplx<R>* __restr
 }
 
 // ---------------------------------------------------------------------------
-// K6: end of a long step (Sec. III.D): A~(z0 + L) = (psi0 + dpsi_M) exp(i beta M dz)
-// in FP64; becomes the next psi0.  Skipped when the long step failed.
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0, cplx<R>* psiR,
-                                                 const cplx<R>* __restrict__ dpsi,
-                                                 const double2* __restrict__ EM, const LoopState* ls) {
-  pdl_enter();
-  const size_t Nn = (size_t)g.N * g.n;
-  if (ls->status != ST_OK) return;
-  const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
-    const double2 p0 = psi0[e];
-    const cplx<R> dd = d[e];
-    const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
-    const double2 w = EM[e];
-    const double2 v = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
-    psi0[e] = v;
-    if ((const void*)psiR != (const void*)psi0) psiR[e] = mk<R>((R)v.x, (R)v.y);
-  }
-}
-
-// psiR = psi0 rounded to the working precision (start of a propagation).
-template <typename R>
-__global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restrict__ psiR, size_t count) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
-    psiR[e] = mk<R>((R)psi0[e].x, (R)psi0[e].y);
-}
-
-// Long-step bookkeeping after K6 (one thread) and the outer while-node
-// condition: continue while the step succeeded and steps remain.
-static __global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, int use_cond) {
-  pdl_enter();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Long-step bookkeeping (one thread): statistics, the reset of the iteration
+// state, and in a graph the outer while-node condition (continue while the
+// step succeeded and steps remain) and the inner one re-armed for the next
+// long step.
+__device__ __forceinline__ void step_end(LoopState* ls, cudaGraphConditionalHandle hStep,
+                                         cudaGraphConditionalHandle hIter, int use_cond) {
   const int status = ls->status, it = ls->iter;
   if (status == ST_OK) {
     ls->step += 1;
@@ -527,12 +499,55 @@ static __global__ void k_step_end(LoopState* ls, cudaGraphConditionalHandle h, i
   ls->iter = 0;
   ls->done = 0;
   ls->prev_eps = INFINITY;
-  if (use_cond) cudaGraphSetConditional(h, (status == ST_OK && ls->step < ls->nsteps) ? 1u : 0u);
+  if (use_cond) {
+    cudaGraphSetConditional(hStep, (status == ST_OK && ls->step < ls->nsteps) ? 1u : 0u);
+    cudaGraphSetConditional(hIter, 1u);
+  }
 }
 
-// Start of a long step inside a graph: re-arm the iteration loop.
-static __global__ void k_step_begin(cudaGraphConditionalHandle h) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, 1u);
+// K6: end of a long step (Sec. III.D): A~(z0 + L) = (psi0 + dpsi_M) exp(i beta M dz)
+// in FP64; becomes the next psi0.  Skipped when the long step failed.  The
+// last block to finish does the long-step bookkeeping (every block reads the
+// status before it arrives).
+template <typename R>
+__global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0, cplx<R>* psiR,
+                                                 const cplx<R>* __restrict__ dpsi,
+                                                 const double2* __restrict__ EM, LoopState* ls,
+                                                 cudaGraphConditionalHandle hStep, cudaGraphConditionalHandle hIter,
+                                                 int use_cond) {
+  __shared__ bool last;
+  pdl_enter();
+  const size_t Nn = (size_t)g.N * g.n;
+  if (ls->status == ST_OK) {
+    const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
+      const double2 p0 = psi0[e];
+      const cplx<R> dd = d[e];
+      const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
+      const double2 w = EM[e];
+      const double2 v = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
+      psi0[e] = v;
+      if ((const void*)psiR != (const void*)psi0) psiR[e] = mk<R>((R)v.x, (R)v.y);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ls->arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    ls->arrive = 0;
+    step_end(ls, hStep, hIter, use_cond);
+  }
+}
+
+// psiR = psi0 rounded to the working precision (start of a propagation).
+template <typename R>
+__global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restrict__ psiR, size_t count) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    psiR[e] = mk<R>((R)psi0[e].x, (R)psi0[e].y);
 }
 
 // ---------------------------------------------------------------------------

@@ -233,8 +233,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
       if (hs.done) break;
     }
     k_advance<R><<<blocks_for(Nn), 256, 0, s>>>(g, w.psi0, (cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
-                                               w.EM64 + (size_t)which * Nn, w.ls);
-    k_step_end<<<1, 32, 0, s>>>(w.ls, 0, 0);
+                                               w.EM64 + (size_t)which * Nn, w.ls, 0, 0, 0);
     CKN(cudaGetLastError());
     CKN(cudaMemcpyAsync(&hs, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
     CKN(cudaStreamSynchronize(s));

@@ -467,14 +467,16 @@ static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraph
   launch_k5<R>(jb, g, s, h, use_cond);
 }
 
+// K6 with the long-step bookkeeping in its last block; in a graph it also
+// sets the outer loop's condition and re-arms the iteration loop.
 template <typename R>
-static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle h,
-                           int use_cond) {
+static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle hStep,
+                           cudaGraphConditionalHandle hIter, int use_cond) {
   gmmnlse_ctx* c = jb->ctx;
   const size_t Nn = (size_t)c->N * c->n;
   pdl_launch(k_advance<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, jb->psi0, (cplx<R>*)jb->psiR,
-             (const cplx<R>*)jb->dpsi, (const double2*)(jb->EM64 + (size_t)which * Nn), (const LoopState*)jb->ls);
-  pdl_launch(k_step_end, dim3(1), dim3(32), 0, s, jb->ls, h, use_cond);
+             (const cplx<R>*)jb->dpsi, (const double2*)(jb->EM64 + (size_t)which * Nn), jb->ls, hStep, hIter,
+             use_cond);
 }
 
 template <typename R>
@@ -492,27 +494,16 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   cudaGraphNode_t nStep;
   CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
   cudaGraph_t gS = cp.conditional.phGraph_out[0];
-  CK(cudaGraphConditionalHandleCreate(&hIter, gS, 0, 0));
-  // long-step body: re-arm the iteration loop
-  CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  k_step_begin<<<1, 32, 0, cs>>>(hIter);
-  cudaStreamCaptureStatus cst;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd));
-  cudaGraphNode_t nBegin = nd == 1 ? deps[0] : nullptr;
-  CK(cudaStreamEndCapture(cs, &gS));
-  if (!nBegin) {
-    gm_set_last_error_text("graph capture: unexpected dependency set");
-    return GMMNLSE_E_CUDA;
-  }
+  // the iteration loop's condition starts at 1 when the graph is launched;
+  // the advance kernel re-arms it at the end of every long step
+  CK(cudaGraphConditionalHandleCreate(&hIter, gS, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams ci = {};
   ci.type = cudaGraphNodeTypeConditional;
   ci.conditional.handle = hIter;
   ci.conditional.type = cudaGraphCondTypeWhile;
   ci.conditional.size = 1;
   cudaGraphNode_t nIter;
-  CK(cudaGraphAddNode(&nIter, gS, &nBegin, nullptr, 1, &ci));
+  CK(cudaGraphAddNode(&nIter, gS, nullptr, nullptr, 0, &ci));
   cudaGraph_t gI = ci.conditional.phGraph_out[0];
   // iteration body: K1 .. K5
   CK(cudaStreamBeginCaptureToGraph(cs, gI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -520,7 +511,7 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   CK(cudaStreamEndCapture(cs, &gI));
   // after the loop: K6
   CK(cudaStreamBeginCaptureToGraph(cs, gS, &nIter, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-  launch_advance<R>(jb, g, which, cs, hStep, 1);
+  launch_advance<R>(jb, g, which, cs, hStep, hIter, 1);
   CK(cudaStreamEndCapture(cs, &gS));
   cudaGraphExec_t exec = nullptr;
   CK(cudaGraphInstantiate(&exec, root, 0));
@@ -580,7 +571,7 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
       CK(cudaStreamSynchronize(s));
       if (jb->h_ls->done) break;
     }
-    launch_advance<R>(jb, g, which, s, 0, 0);
+    launch_advance<R>(jb, g, which, s, 0, 0, 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -754,7 +745,7 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
         case 4: launch_k5<R>(jb, g, s, 0, 0); break;
         default:
           k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR,
-                                                               (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls);
+                                                               (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls, 0, 0, 0);
           break;
       }
       CK(cudaGetLastError());
