@@ -72,7 +72,7 @@ struct gmmnlse_ctx {
   int2* rows = nullptr;         // [P]
   int2* pairs = nullptr;        // [K]
   bool tc = false;               // contraction on tensor cores (mixed precision)
-  int KKp = 0;                   // K padded to a multiple of 64
+  int KKp = 0;                   // K padded to a multiple of TC_KC (32)
   int tc_rows = 0;               // rows of G padded to whole row blocks
   bool f16 = false;              // tensor-core operands FP16 (MIXED_FP16), else BF16
   int eG = 0;                    // FP16: G scaled by 2^eG
@@ -92,7 +92,7 @@ struct gmmnlse_ctx {
   void* Xt = nullptr;            // [rK2][Pt] R: X^T, CUDA-core GEMM 2 (K = r padded to rK2)
   int rP1 = 0, rK2 = 0;
   int NB1 = 0, r_rows = 0;       // tensor cores: row block of GEMM 1, r padded to whole blocks
-  int rKKp = 0;                  // tensor cores: r padded to 64 (K of GEMM 2)
+  int rKKp = 0;                  // tensor cores: r padded to TC_KC (K of GEMM 2)
   int eW16 = 0, eX16 = 0;        // FP16 exponents of W and X
   __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
   CUtensorMap mapWhi, mapWlo, mapXhi, mapXlo;

@@ -22,7 +22,7 @@
 // The same kernel with OUT 1 stores the accumulator rows (times the inverse
 // FP16 scales) as Z = W U, the first GEMM of the low-rank coupling.
 //
-// Roles (192 threads): warp 0 issues TMA copies of K chunks (64 wide) of V
+// Roles (192 threads): warp 0 issues TMA copies of K chunks (32 wide) of V
 // and G into a ring of stages; warp 1 issues tcgen05.mma from the ring into
 // one of two TMEM accumulators; warps 2-5 drain an accumulator (tcgen05.ld)
 // while the MMAs of the next work item run.  A work item is (point tile, row
@@ -30,7 +30,7 @@
 //
 // Operand layout (both K-major, no swizzle): core matrices of 8 rows x 8
 // elements (16 bytes), stored [k/8][row][8]; in shared memory a K chunk of R
-// rows is [8][R][8], so core matrices adjacent along K are R*16 bytes apart
+// rows is [4][R][8], so core matrices adjacent along K are R*16 bytes apart
 // (LBO) and along the rows 128 bytes (SBO).
 //
 // Every mbarrier wait is bounded; on a timeout the kernel records an error
@@ -47,7 +47,7 @@
 namespace gm {
 
 constexpr int TC_PTS = 128;  // MMA M: points per tile
-constexpr int TC_KC = 64;    // K chunk per pipeline stage
+constexpr int TC_KC = 32;    // K chunk per pipeline stage
 
 struct TcArgs {
   int KKp;           // K padded to a multiple of TC_KC
@@ -83,7 +83,7 @@ struct TcShape {
   static constexpr int G_BYTES = NB * TC_KC * 2;
   static constexpr int STAGE = 2 * (V_BYTES + G_BYTES);
   static constexpr int FIT = 200 * 1024 / STAGE;
-  static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 4 ? 4 : FIT);
+  static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 6 ? 6 : FIT);
   static constexpr int TMEM_COLS =
       2 * NB <= 32 ? 32 : (2 * NB <= 64 ? 64 : (2 * NB <= 128 ? 128 : (2 * NB <= 256 ? 256 : 512)));
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
