@@ -63,9 +63,9 @@ struct gmmnlse_ctx {
   bool fp64;
   double fR, omega0, gamma0;
   double* beta = nullptr;       // [N][n]
-  double2* tw64 = nullptr;      // [n]
-  double2* tw64h = nullptr;     // [n/2]
-  float2* tw32 = nullptr;       // [n]
+  double2* tw64 = nullptr;      // [n] + radix-16 pass tables of n
+  double2* tw64h = nullptr;     // [n/2] + pass tables of n/2
+  float2* tw32 = nullptr;       // [n] + pass tables of n
   void* H = nullptr;            // [n] cplx<R>
   void* fac = nullptr;          // [n] R: gamma0 s(w_q)
   void* G = nullptr;            // [P][KK] R

@@ -443,15 +443,30 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     }
   }
 
-  // device copies
+  // device copies: twiddles exp(-2 pi i m / n) followed by the radix-16
+  // pass tables of the transform length (fft_block reads them at tw + n)
+  auto pass_tables = [](int len, std::vector<double2>& out) {
+    int logn = 0;
+    while ((1 << logn) < len) ++logn;
+    for (int Ns = 1 << (logn & 3); Ns < len; Ns <<= 4) {
+      if (Ns == 1) continue;
+      for (int r = 1; r < 16; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const double a = 2.0 * M_PI * (double)k * r / (16.0 * Ns);
+          out.push_back(make_double2(std::cos(a), -std::sin(a)));
+        }
+    }
+  };
   std::vector<double2> tw(n), twh(n / 2);
-  std::vector<float2> tw32(n);
   for (int m = 0; m < n; ++m) {
     const double a = 2.0 * M_PI * (double)m / (double)n;
     tw[m] = make_double2(std::cos(a), -std::sin(a));
-    tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
   }
   for (int m = 0; m < n / 2; ++m) twh[m] = tw[2 * m];
+  pass_tables(n, tw);
+  pass_tables(n / 2, twh);
+  std::vector<float2> tw32(tw.size());
+  for (size_t m = 0; m < tw.size(); ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
 #define CKC(call)                     \
   do {                                \
     cudaError_t e_ = (call);          \
@@ -463,12 +478,12 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   } while (0)
   CKC(cudaMalloc(&c->beta, (size_t)N * n * sizeof(double)));
   CKC(cudaMemcpy(c->beta, beta, (size_t)N * n * sizeof(double), cudaMemcpyHostToDevice));
-  CKC(cudaMalloc(&c->tw64, n * sizeof(double2)));
-  CKC(cudaMemcpy(c->tw64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
-  CKC(cudaMalloc(&c->tw64h, (n / 2) * sizeof(double2)));
-  CKC(cudaMemcpy(c->tw64h, twh.data(), (n / 2) * sizeof(double2), cudaMemcpyHostToDevice));
-  CKC(cudaMalloc(&c->tw32, n * sizeof(float2)));
-  CKC(cudaMemcpy(c->tw32, tw32.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->tw64, tw.size() * sizeof(double2)));
+  CKC(cudaMemcpy(c->tw64, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->tw64h, twh.size() * sizeof(double2)));
+  CKC(cudaMemcpy(c->tw64h, twh.data(), twh.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CKC(cudaMalloc(&c->tw32, tw32.size() * sizeof(float2)));
+  CKC(cudaMemcpy(c->tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice));
   CKC(cudaMalloc(&c->rows, c->P * sizeof(int2)));
   CKC(cudaMemcpy(c->rows, pairs.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
   CKC(cudaMalloc(&c->pairs, c->K * sizeof(int2)));

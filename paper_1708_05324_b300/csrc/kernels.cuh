@@ -324,7 +324,11 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
     const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
     I[off + q] = cmulc<R>(iX, e[q]);
   };
-  if (S == 1) fft_block<R, +1, EPT>(sm, n, tw, load, store);
+  // FP32 with 16 per thread keeps the product-form twiddles here: with the
+  // pass tables the last pass stacks their loads on the prefactor and phase
+  // loads of the store (measured 13.7 against 8.8 us on the 6-mode workload)
+  constexpr bool TAB = !(sizeof(R) == 4 && EPT == 16);
+  if (S == 1) fft_block<R, +1, EPT, TAB>(sm, n, tw, 1, load, store);
   else fft_cluster<R, +1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
 }
 

@@ -181,7 +181,7 @@ static int elementwise_blocks(size_t count) {
 // 32 (256 threads, two blocks per SM) when the launch has at least two
 // blocks per SM, which measured faster for throughput (the 42-mode
 // workload) and slower for a launch of fewer blocks than SMs (the 6-mode
-// workload), where 16 per thread is kept.
+// workload: 8 warps per SM), where 16 per thread is kept.
 template <typename R> static int fft_ept(int np, int blocks) {
   return (np > 8192 || (sizeof(R) == 4 && np == 8192 && blocks >= 2 * 148)) ? 32 : 16;
 }
