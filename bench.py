@@ -116,12 +116,16 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
-def launches_per_step(st, raman, mixed=False, fp64=False, graph=True):
+def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=8192):
     """Kernel launches of one propagate call, from its statistics."""
     per_iter = 5 if raman else 4   # K1 [K2] K3 K4 K5 (decision in K5's last block)
-    if mixed:
-        per_iter += 1              # K3 = operand pack + tensor-core GEMM
-    fft = 1  # Nt <= 8192
+    tc = mixed and N > 8           # the tensor cores run the contraction from 9 modes
+    lowrank = st.get("coupling_rank", 0) < N * (N + 1) // 2
+    if lowrank:
+        per_iter += 1              # two GEMMs (Z = W U, then X V')
+    if tc:
+        per_iter += 2 if lowrank else 1   # each GEMM has its operand pack
+    fft = 1 if Nt <= 8192 else 2  # FP64 input/output transforms (halves + combine above 8192)
     n = 1 + fft + 1          # non-finite check, forward transform, input sums
     if not fp64:
         n += 1               # psi0 rounded to the working precision
@@ -454,11 +458,14 @@ def main():
     peaks, src = measured_peaks()
     mixed = args.precision in ("bf16", "fp16")
     if dom == "contract" and prob.N > 8:
-        # a dense GEMM: 2 P KK flops per point and iteration (x3 for the hi/lo
-        # products on the tensor cores), points = M substeps x Nt
+        # a dense GEMM: 2 P KK flops per point and iteration, or with the
+        # low-rank coupling (rank r) the two GEMMs 2 r (K + P); x3 for the
+        # hi/lo products on the tensor cores; points = M substeps x Nt
         P = prob.N * (prob.N + 1) // 2
         KK = P if prob.fR == 0 or prob.SR is None or prob.SR is prob.SK else 2 * P
-        flops = 2.0 * P * KK * prob.M * prob.Nt * (3 if mixed else 1)
+        r = stats[-1].get("coupling_rank", P)
+        per_point = 2.0 * r * (P + P) if r < P else 2.0 * P * KK
+        flops = per_point * prob.M * prob.Nt * (3 if mixed else 1)
         achieved = flops / (ms_dom * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "tensor" if mixed else "alu", "achieved": achieved,
                 "peak": peaks["bf16_tflops"] if mixed else FP32_ALU_TFLOPS, "unit": "TFLOP/s",
@@ -473,7 +480,7 @@ def main():
     roof["kernel_ms"] = ms_dom
     roof["all_kernels_ms"] = {k: v[0] for k, v in prof.items()}
     raman = prob.fR != 0
-    launches = sum(launches_per_step(st, raman, mixed, args.precision == "fp64") for st in stats)
+    launches = sum(launches_per_step(st, raman, mixed, args.precision == "fp64", N=prob.N, Nt=prob.Nt) for st in stats)
     ctx.close()
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,

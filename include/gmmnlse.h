@@ -195,7 +195,9 @@ const char* gmmnlse_last_error(void);
  * gmmnlse_profile -- time each kernel of one MPA iteration of this context
  * (Sec. III.D: phase x inverse FFT; pair products + Raman convolution;
  * coupling contraction; forward FFT x integrand prefactor; trapezoid +
- * convergence sums and decision; long-step advance) on the workspace of its last
+ * convergence sums and decision; long-step advance; with the low-rank
+ * coupling, slot 1 is the Raman convolution of the rows of Z = W U and slot
+ * 2 both GEMMs of the contraction) on the workspace of its last
  * gmmnlse_propagate, which must have used at least M substeps.  Each kernel
  * is launched reps times back to back (after one untimed launch) on the
  * context's stream between two CUDA events.  ms[6] receives the mean duration of each kernel

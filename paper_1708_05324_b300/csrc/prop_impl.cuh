@@ -706,9 +706,9 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
   bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->K * c->n * rs) : 0.0;     // A -> Y
   bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->K * rs : 0.0));  // A, Y -> NL
   if (c->lr) {
-    // A -> Z (GEMM 1), Z -> Y' (Raman); A, Z, Y' -> NL (GEMM 2)
-    bytes[1] = M * (Nn * cs + (double)c->r * c->n * rs * (c->raman_mode ? 3 : 1));
-    bytes[2] = M * (double)c->n * (2 * c->N * cs + (double)c->r * rs * (c->raman_mode ? 2 : 1));
+    // Raman on the rows of Z (Z -> Y'); contraction: A -> Z (GEMM 1), A, Z, Y' -> NL (GEMM 2)
+    bytes[1] = c->raman_mode ? M * 2.0 * c->r * c->n * rs : 0.0;
+    bytes[2] = M * (double)c->n * (3 * c->N * cs + (double)c->r * rs * (c->raman_mode ? 3 : 2));
   }
   bytes[3] = M * Nn * 3 * cs + c->n * rs;         // NL, E -> I; prefactor table
   bytes[4] = Nn * ((M + 1) * cs + 2 * M * cs + cs); // I, dpsi old/new, psiR
@@ -720,7 +720,7 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
   const size_t Nsz = (size_t)c->N * c->n;
   for (int k = 0; k < 6; ++k) {
     ms[k] = 0.0;
-    if (k == 1 && !c->raman_mode && !c->lr) continue;
+    if (k == 1 && !c->raman_mode) continue;
     // iteration state: iter = 1 (substeps 1..M, the shape of every iteration after the first)
     CK(cudaMemcpyAsync(&jb->ls->iter, &one, sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -729,17 +729,18 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
       switch (k) {
         case 0: launch_k1<R>(jb, g, s); break;
         case 1:
-          if (c->lr) {
-            launch_lr_z<R>(jb, g, s);
-            if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
-          } else {
-            launch_k2<R>(jb, g, s);
-          }
+          if (c->lr) launch_lr_raman<R>(jb, g, s);
+          else launch_k2<R>(jb, g, s);
           break;
         case 2:
-          if (c->lr) launch_lr_r<R>(jb, g, s);
-          else if (c->tc) launch_tc<R>(jb, g, s);
-          else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+          if (c->lr) {
+            launch_lr_z<R>(jb, g, s);
+            launch_lr_r<R>(jb, g, s);
+          } else if (c->tc) {
+            launch_tc<R>(jb, g, s);
+          } else {
+            launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+          }
           break;
         case 3: launch_k4<R>(jb, g, s); break;
         case 4: launch_k5<R>(jb, g, s, 0, 0); break;
