@@ -116,6 +116,24 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(seconds, dist=None, device="cpu"):
+    """The largest of a per-rank time over the ranks of the job (the rank's
+    own without a process group): the job's time is that of its slowest
+    replica."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, steps, world, seconds):
+    """Whole-job throughput: the units every rank processed over the job's
+    (slowest rank's) time; each rank runs its own replica (weak scaling)."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=8192):
     """Kernel launches of one propagate call, from its statistics."""
     per_iter = 5 if raman else 4   # K1 [K2] K3 K4 K5 (decision in K5's last block)
@@ -393,12 +411,8 @@ def main():
         if dist:
             dist.barrier()
         wall = time.perf_counter() - t0
-    dev_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([dev_s], device=f"cuda:{dev}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = u * args.steps * world / dev_s
+    dev_s = max_over_ranks(sum(step_ms) / 1e3, dist, f"cuda:{dev}")
+    value = job_rate(u, args.steps, world, dev_s)
 
     if args.profile_run:
         line = {"profile_run": True, "precision": args.precision, "length_m": args.length,
@@ -427,7 +441,8 @@ def main():
         ctx_h.propagate(h_in, prob.L, prob.dz, prob.M, prob.tol, out=h_out)
         e2e_t.append(time.perf_counter() - t1)
     ctx_h.close()
-    e2e = {"value": u * args.steps * world / sum(e2e_t), "unit": METRIC,
+    e2e_s = max_over_ranks(sum(e2e_t), dist, f"cuda:{dev}")
+    e2e = {"value": job_rate(u, args.steps, world, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": int(h_in.nbytes), "d2h_bytes_per_step": int(h_out.nbytes)}
 
     if rank != 0:
