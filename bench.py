@@ -339,7 +339,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16", "tf32"])
     ap.add_argument("--length", type=float, default=0.5, help="fiber length per step [m]")
     ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C4"],
                     help="C3 (N=15, Nt=2^14, M=20) and C4 (N=42, Nt=2^13, M=16) are for --profile-run; the metric is quoted on C2")
@@ -471,7 +471,7 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     ms_dom, bytes_dom = prof[dom]
     peaks, src = measured_peaks()
-    mixed = args.precision in ("bf16", "fp16")
+    mixed = args.precision in ("bf16", "fp16", "tf32")
     if dom == "contract" and prob.N > 8:
         # a dense GEMM: 2 P KK flops per point and iteration, or with the
         # low-rank coupling (rank r) the two GEMMs 2 r (K + P); x3 for the
@@ -483,10 +483,12 @@ def main():
         flops = per_point * prob.M * prob.Nt * (3 if mixed else 1)
         achieved = flops / (ms_dom * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "tensor" if mixed else "alu", "achieved": achieved,
-                "peak": peaks["bf16_tflops"] if mixed else FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                "peak": (peaks["bf16_tflops"] * (1.1 / 2.25 if args.precision == "tf32" else 1.0)) if mixed
+                else FP32_ALU_TFLOPS, "unit": "TFLOP/s",
                 "algorithmic_flops": flops}
         roof["frac"] = achieved / roof["peak"]
-        roof["peak_source"] = src if mixed else "148 SMs x 128 FP32 FMA/clk x 2 x 2.032 GHz"
+        roof["peak_source"] = ((src + (", x 1.1/2.25 (nominal TF32 : BF16 dense)" if args.precision == "tf32" else ""))
+                               if mixed else "148 SMs x 128 FP32 FMA/clk x 2 x 2.032 GHz")
     else:
         achieved = bytes_dom / (ms_dom * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -500,7 +502,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3", "fp16": "f32+f16x3"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3", "fp16": "f32+f16x3", "tf32": "f32+tf32x3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] if args.length == 0.5 or args.workload != "C2"
                    else WORKLOAD.replace("L=0.5 m", f"L={args.length} m"),

@@ -57,9 +57,12 @@ typedef enum gmmnlse_precision {
                                for N = 9..16 and 42 with Nt a multiple of 128
                                (other N > 8: GMMNLSE_E_UNSUPPORTED); for N <= 8
                                the FP32 register contraction, faster there */
-    GMMNLSE_MIXED_FP16 = 3  /* as MIXED_BF16 with FP16 hi/lo operands, each
+    GMMNLSE_MIXED_FP16 = 3, /* as MIXED_BF16 with FP16 hi/lo operands, each
                                scaled by a power of two into FP16 range (exact
                                to undo); N and Nt limits as MIXED_BF16 */
+    GMMNLSE_MIXED_TF32 = 4  /* as MIXED_BF16 with TF32 hi/lo operands (FP32
+                               range, 11-bit significands: three products
+                               leave ~2^-21 relative); same limits */
 } gmmnlse_precision;
 
 typedef struct gmmnlse_params {

@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(HERE, "libgmmnlse.so")
 OK, PENDING = 0, 1
 E_INVALID, E_NOMEM, E_UNSUPPORTED, E_NOT_CONVERGED = -1, -2, -3, -4
 E_NONFINITE, E_CUDA, E_BUSY, E_CANCELLED = -5, -6, -7, -8
-FP64, FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
+FP64, FP32, MIXED_BF16, MIXED_FP16, MIXED_TF32 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16, "tf32": MIXED_TF32}
 
 # every function include/gmmnlse.h declares
 EXPORTS = [

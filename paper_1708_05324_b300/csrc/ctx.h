@@ -50,7 +50,7 @@ struct gm_job {
   } graphs[2];
   size_t bytes = 0;
   // mixed precision: blocked BF16 hi/lo pair-term operand and its TMA maps
-  __nv_bfloat16* Vhi = nullptr;  // [KKp/8][(M+1) n][8] (and [rKKp/8][..][8] for the low-rank GEMM 2)
+  __nv_bfloat16* Vhi = nullptr;  // [KKp/EPC][(M+1) n][EPC] (and rKKp columns for the low-rank GEMM 2)
   __nv_bfloat16* Vlo = nullptr;
   CUtensorMap mapHi, mapLo;
   CUtensorMap mapHi2, mapLo2;    // the same buffers with rKKp columns (low-rank GEMM 2)
@@ -75,8 +75,9 @@ struct gmmnlse_ctx {
   int KKp = 0;                   // K padded to a multiple of TC_KC (32)
   int tc_rows = 0;               // rows of G padded to whole row blocks
   bool f16 = false;              // tensor-core operands FP16 (MIXED_FP16), else BF16
+  bool tf32 = false;             // tensor-core operands TF32 (MIXED_TF32), 4-byte elements
   int eG = 0;                    // FP16: G scaled by 2^eG
-  __nv_bfloat16* Ghi = nullptr;  // [KKp/8][tc_rows][8] (FP16 bits when f16)
+  __nv_bfloat16* Ghi = nullptr;  // [KKp/EPC][tc_rows][EPC]: 16-bit (EPC 8) or TF32 words (EPC 4)
   __nv_bfloat16* Glo = nullptr;
   CUtensorMap mapGhi, mapGlo;
   void* Gt = nullptr;            // [KKt][Pt] R: G transposed, zero-padded (N > 8, CUDA cores)

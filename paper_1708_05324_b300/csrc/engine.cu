@@ -244,11 +244,41 @@ static int f16_exp(const std::vector<double>& m) {
   return 14 - e;
 }
 
-// A row-major [rows][cols] matrix scaled by 2^e, split into 16-bit hi + lo
-// (FP16 when f16, else BF16) in the blocked layout [cols_pad/8][rows_pad][8]
-// (K-major core matrices) read by the tensor-core GEMM; zero padding.
+// TF32 rounding of x (nearest, ties away from zero: the low 13 bits of the
+// FP32 significand cleared), as the device's cvt.rna.tf32.f32 does.
+static float tf32_rna(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  float y;
+  std::memcpy(&y, &u, 4);
+  return y;
+}
+
+// A row-major [rows][cols] matrix scaled by 2^e, split into hi + lo in the
+// blocked layout [cols_pad/EPC][rows_pad][EPC] (K-major core matrices of
+// 16-byte rows) read by the tensor-core GEMM, zero padding: TF32 words
+// (EPC 4) when tf32, else 16-bit FP16 (f16) or BF16 (EPC 8).
+static int upload_hilo_tf32(const std::vector<double>& m, int rows, int cols, int rows_pad, int cols_pad,
+                            __nv_bfloat16** hi, __nv_bfloat16** lo) {
+  std::vector<float> gh((size_t)rows_pad * cols_pad), gl((size_t)rows_pad * cols_pad);
+  for (int r = 0; r < rows_pad; ++r)
+    for (int k = 0; k < cols_pad; ++k) {
+      const float x = (r < rows && k < cols) ? (float)m[(size_t)r * cols + k] : 0.f;
+      const size_t o = ((size_t)(k / 4) * rows_pad + r) * 4 + (k % 4);
+      gh[o] = tf32_rna(x);
+      gl[o] = tf32_rna(x - gh[o]);
+    }
+  CK(cudaMalloc(hi, gh.size() * 4));
+  CK(cudaMalloc(lo, gl.size() * 4));
+  CK(cudaMemcpy(*hi, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(*lo, gl.data(), gl.size() * 4, cudaMemcpyHostToDevice));
+  return GMMNLSE_OK;
+}
+
 static int upload_hilo(const std::vector<double>& m, int rows, int cols, int rows_pad, int cols_pad, bool f16,
-                       int e, __nv_bfloat16** hi, __nv_bfloat16** lo) {
+                       int e, __nv_bfloat16** hi, __nv_bfloat16** lo, bool tf32 = false) {
+  if (tf32) return upload_hilo_tf32(m, rows, cols, rows_pad, cols_pad, hi, lo);
   std::vector<__nv_bfloat16> gh((size_t)rows_pad * cols_pad), gl((size_t)rows_pad * cols_pad);
   for (int r = 0; r < rows_pad; ++r)
     for (int k = 0; k < cols_pad; ++k) {
@@ -340,7 +370,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   if (!(prm->dt > 0) || !(prm->lambda0 > 0) || !std::isfinite(prm->n2)) return GMMNLSE_E_INVALID;
   if (!(fR >= 0.0 && fR < 1.0)) return GMMNLSE_E_INVALID;
   if (fR > 0 && !hR) return GMMNLSE_E_INVALID;
-  if (prm->precision < GMMNLSE_FP64 || prm->precision > GMMNLSE_MIXED_FP16) return GMMNLSE_E_INVALID;
+  if (prm->precision < GMMNLSE_FP64 || prm->precision > GMMNLSE_MIXED_TF32) return GMMNLSE_E_INVALID;
   if (prm->max_iter < 0 || prm->fixed_iters < 0) return GMMNLSE_E_INVALID;
   const size_t S4 = (size_t)N * N * N * N;
   if (!finite_all(beta, (size_t)N * n) || !finite_all(SK, S4) || (SR && !finite_all(SR, S4)) ||
@@ -393,7 +423,9 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   // dense GEMM, N >= 9 (built for N = 9..16 and 42, the 42-mode step-index
   // workload, with Nt a multiple of the 128-point tile); for N <= 8 the FP32
   // register contraction is faster than a GEMM that small and is used instead
-  if ((prm->precision == GMMNLSE_MIXED_BF16 || prm->precision == GMMNLSE_MIXED_FP16) && N > 8) {
+  const bool mixed = prm->precision == GMMNLSE_MIXED_BF16 || prm->precision == GMMNLSE_MIXED_FP16 ||
+                     prm->precision == GMMNLSE_MIXED_TF32;
+  if (mixed && N > 8) {
     if (!(N <= 16 || N == 42) || n % TC_PTS != 0) {
       delete c;
       return GMMNLSE_E_UNSUPPORTED;
@@ -401,6 +433,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     const int NB = tc_row_block(c->P);
     c->tc = true;
     c->f16 = prm->precision == GMMNLSE_MIXED_FP16;
+    c->tf32 = prm->precision == GMMNLSE_MIXED_TF32;
     c->KKp = (c->KK + TC_KC - 1) / TC_KC * TC_KC;
     c->tc_rows = (c->P + NB - 1) / NB * NB;
   }
@@ -516,43 +549,16 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     if (!rc && c->tc) {
       c->eW16 = c->f16 ? f16_exp(Wd) : 0;
       c->eX16 = c->f16 ? f16_exp(Xd) : 0;
-      rc = upload_hilo(Wd, c->r, c->K, c->r_rows, c->KKp, c->f16, c->eW16, &c->Whi, &c->Wlo);
-      if (!rc) rc = upload_hilo(Xd, c->P, c->r, c->tc_rows, c->rKKp, c->f16, c->eX16, &c->Xhi, &c->Xlo);
+      rc = upload_hilo(Wd, c->r, c->K, c->r_rows, c->KKp, c->f16, c->eW16, &c->Whi, &c->Wlo, c->tf32);
+      if (!rc)
+        rc = upload_hilo(Xd, c->P, c->r, c->tc_rows, c->rKKp, c->f16, c->eX16, &c->Xhi, &c->Xlo, c->tf32);
     }
   }
   if (!rc && c->tc) {
-    // G split into 16-bit hi + lo, blocked [KKp/8][rows][8] (K-major core
-    // matrices); FP16 scaled by 2^eG so that its largest entry is below 2^14
-    const int KKp = c->KKp, rows = c->tc_rows;
-    double gmax = 0.0;
-    for (double x : Gd) gmax = std::max(gmax, std::fabs(x));
-    if (c->f16 && gmax > 0.0) {
-      int e;
-      std::frexp(gmax, &e);  // gmax < 2^e
-      c->eG = 14 - e;
-    }
-    std::vector<__nv_bfloat16> gh((size_t)rows * KKp), gl((size_t)rows * KKp);
-    for (int r = 0; r < rows; ++r)
-      for (int k = 0; k < KKp; ++k) {
-        const float x = (r < c->P && k < c->KK) ? (float)std::ldexp(Gd[(size_t)r * c->KK + k], c->eG) : 0.f;
-        const size_t o = ((size_t)(k / 8) * rows + r) * 8 + (k % 8);
-        if (c->f16) {
-          const __half h = __float2half_rn(x), l = __float2half_rn(x - __half2float(h));
-          std::memcpy(&gh[o], &h, 2);
-          std::memcpy(&gl[o], &l, 2);
-        } else {
-          gh[o] = __float2bfloat16_rn(x);
-          gl[o] = __float2bfloat16_rn(x - __bfloat162float(gh[o]));
-        }
-      }
-    cudaError_t e = cudaMalloc(&c->Ghi, gh.size() * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&c->Glo, gl.size() * 2);
-    if (e == cudaSuccess) e = cudaMemcpy(c->Ghi, gh.data(), gh.size() * 2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->Glo, gl.data(), gl.size() * 2, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      gm_set_last_cuda_error(e, "coupling matrix upload", __FILE__, __LINE__);
-      rc = GMMNLSE_E_CUDA;
-    }
+    // G split into hi + lo in the blocked operand layout; FP16 scaled by 2^eG
+    // so that its largest entry is below 2^14
+    if (c->f16) c->eG = f16_exp(Gd);
+    rc = upload_hilo(Gd, c->P, c->KK, c->tc_rows, c->KKp, c->f16, c->eG, &c->Ghi, &c->Glo, c->tf32);
     if (!rc) rc = gm_make_g_maps(c);
   }
   if (!rc) rc = set_smem_attrs(c);
@@ -595,7 +601,7 @@ static size_t job_bytes(const gmmnlse_ctx* c, int M) {
   if (c->lr) b += (size_t)(M + 1) * c->r * c->n * rs;          // Z = W U
   b += 2 * Nn * 16 * 2;                          // EM64, io
   b += sizeof(LoopState) + 64 + sizeof(double2) * TRAPZ_MAX_BLOCKS;
-  if (c->tc) b += (size_t)2 * c->KKp * (M + 1) * c->n * 2;  // BF16 hi/lo operand
+  if (c->tc) b += (size_t)2 * c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2);  // hi/lo operand
   return b;
 }
 
@@ -652,18 +658,22 @@ static int tc_encoder(EncodeTiledFn* out) {
   return GMMNLSE_OK;
 }
 
-// Map of a blocked [KKp/8][rows][8] 16-bit operand (BF16 or FP16); box = one
-// K chunk of box_rows rows.
-static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int box_rows, bool f16) {
+// Map of a blocked [KKp/EPC][rows][EPC] operand (16-byte core-matrix rows:
+// EPC 8 for BF16 / FP16, 4 for TF32 words); box = one K chunk of box_rows
+// rows.
+static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int box_rows, bool f16,
+                  bool tf32 = false) {
   EncodeTiledFn enc;
   const int rc = tc_encoder(&enc);
   if (rc) return rc;
-  const cuuint64_t dims[3] = {8, rows, (cuuint64_t)(KKp / 8)};
+  const int epc = tf32 ? 4 : 8;
+  const cuuint64_t dims[3] = {(cuuint64_t)epc, rows, (cuuint64_t)(KKp / epc)};
   const cuuint64_t strides[2] = {16, rows * 16};
-  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(TC_KC / 8)};
+  const cuuint32_t box[3] = {(cuuint32_t)epc, (cuuint32_t)box_rows, (cuuint32_t)(TC_KC / epc)};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base,
-                         dims, strides, box, es,
+  const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const CUresult r = enc(map, dt, 3, base, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -675,24 +685,24 @@ static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int bo
 
 int gm_make_g_maps(gmmnlse_ctx* c) {
   const int NB = tc_row_block(c->P);
-  int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16);
-  if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16);
+  int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
+  if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
   if (!rc && c->lr) {
-    rc = tc_map(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16);
-    if (!rc) rc = tc_map(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16);
-    if (!rc) rc = tc_map(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16);
-    if (!rc) rc = tc_map(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16);
+    rc = tc_map(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
+    if (!rc) rc = tc_map(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
+    if (!rc) rc = tc_map(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
+    if (!rc) rc = tc_map(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
   }
   return rc;
 }
 
 int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
   const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
-  int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS, c->f16);
-  if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS, c->f16);
+  int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS, c->f16, c->tf32);
+  if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS, c->f16, c->tf32);
   if (!rc && c->lr) {
-    rc = tc_map(&jb->mapHi2, jb->Vhi, npts, c->rKKp, TC_PTS, c->f16);
-    if (!rc) rc = tc_map(&jb->mapLo2, jb->Vlo, npts, c->rKKp, TC_PTS, c->f16);
+    rc = tc_map(&jb->mapHi2, jb->Vhi, npts, c->rKKp, TC_PTS, c->f16, c->tf32);
+    if (!rc) rc = tc_map(&jb->mapLo2, jb->Vlo, npts, c->rKKp, TC_PTS, c->f16, c->tf32);
   }
   return rc;
 }
@@ -725,8 +735,8 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
   al((void**)&jb->ls, sizeof(LoopState));
   al((void**)&jb->part, sizeof(double2) * TRAPZ_MAX_BLOCKS);
   if (c->tc) {
-    al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * 2);
-    al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * 2);
+    al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
+    al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_ls, sizeof(LoopState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_io, Nn * 16);

@@ -60,17 +60,21 @@ static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* o
 
 // The tensor-core contraction is instantiated for these mode counts (l-sum
 // epilogue) and, for the first GEMM of the low-rank coupling, for every row
-// block NB = 16 .. 256 (store epilogue).
+// block NB = 16 .. 256 (store epilogue); each for 16-bit and TF32 operands.
 template <class F>
 static int tc_for_each_n(F&& f) {
   int rc = GMMNLSE_OK;
   auto one = [&](auto kern) {
     if (!rc) rc = f(kern);
   };
-#define GM_TC_N(N) one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), 0>);
+#define GM_TC_N(N)                                            \
+  one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), 0, 2>); \
+  one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), 0, 4>);
   GM_TC_N(9) GM_TC_N(10) GM_TC_N(11) GM_TC_N(12) GM_TC_N(13) GM_TC_N(14) GM_TC_N(15) GM_TC_N(16) GM_TC_N(42)
 #undef GM_TC_N
-#define GM_TC_S(NB) one(&k_tc_contract<0, NB, 1>);
+#define GM_TC_S(NB)                     \
+  one(&k_tc_contract<0, NB, 1, 2>);     \
+  one(&k_tc_contract<0, NB, 1, 4>);
   GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
   GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
 #undef GM_TC_S
@@ -256,26 +260,35 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
 }
 
 // The tcgen05 GEMM with the l-sum epilogue: V operand maps mV*, coupling
-// operand maps mG*, over the mode count of the context.
-static void launch_tc_lsum(gm_job* jb, const Geo& g, cudaStream_t s, const CUtensorMap& mVhi,
-                           const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
-                           const TcArgs& a) {
+// operand maps mG*, over the mode count of the context; ES = 2 (BF16 / FP16)
+// or 4 (TF32).
+template <int ES>
+static void launch_tc_lsum_es(gm_job* jb, const Geo& g, cudaStream_t s, const CUtensorMap& mVhi,
+                              const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
+                              const TcArgs& a) {
   gmmnlse_ctx* c = jb->ctx;
   const int pts = (g.M + 1) * c->n;
   const dim3 grid(std::min(pts / TC_PTS, 148));
   switch (c->N) {
-#define GM_TC_CASE(NN)                                                                                     \
-  case NN: {                                                                                               \
-    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                    \
-    pdl_launch(k_tc_contract<NN, NB, 0>, grid, dim3(192), TcShape<NN, NB>::SMEM, s, mVhi, mVlo, mGhi, mGlo, a, \
-               (const LoopState*)jb->ls);                                                                  \
-    break;                                                                                                 \
+#define GM_TC_CASE(NN)                                                                                          \
+  case NN: {                                                                                                    \
+    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                         \
+    pdl_launch(k_tc_contract<NN, NB, 0, ES>, grid, dim3(192), TcShape<NN, NB, ES>::SMEM, s, mVhi, mVlo, mGhi, mGlo, \
+               a, (const LoopState*)jb->ls);                                                                    \
+    break;                                                                                                      \
   }
     GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
     GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
 #undef GM_TC_CASE
     default: break;
   }
+}
+
+static void launch_tc_lsum(gm_job* jb, const Geo& g, cudaStream_t s, const CUtensorMap& mVhi,
+                           const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
+                           const TcArgs& a) {
+  if (jb->ctx->tf32) launch_tc_lsum_es<4>(jb, g, s, mVhi, mVlo, mGhi, mGlo, a);
+  else launch_tc_lsum_es<2>(jb, g, s, mVhi, mVlo, mGhi, mGlo, a);
 }
 
 static TcArgs tc_args(gm_job* jb, const Geo& g) {
@@ -302,15 +315,14 @@ static void launch_pack_pairs(gm_job* jb, const Geo& g, cudaStream_t s, int mode
                (const float2*)jb->A, (const float*)jb->V, (const int2*)c->pairs, c->KKp, npts_total,
                (void*)jb->Vhi, (void*)jb->Vlo, (const LoopState*)jb->ls);
   };
-  if (c->f16) {
-    if (mode == 0) pack(k_pack_hilo<0, true>);
-    else if (mode == 1) pack(k_pack_hilo<1, true>);
-    else pack(k_pack_hilo<2, true>);
-  } else {
-    if (mode == 0) pack(k_pack_hilo<0, false>);
-    else if (mode == 1) pack(k_pack_hilo<1, false>);
-    else pack(k_pack_hilo<2, false>);
-  }
+  auto by_mode = [&](auto k0, auto k1, auto k2) {
+    if (mode == 0) pack(k0);
+    else if (mode == 1) pack(k1);
+    else pack(k2);
+  };
+  if (c->tf32) by_mode(k_pack_hilo<0, 2>, k_pack_hilo<1, 2>, k_pack_hilo<2, 2>);
+  else if (c->f16) by_mode(k_pack_hilo<0, 1>, k_pack_hilo<1, 1>, k_pack_hilo<2, 1>);
+  else by_mode(k_pack_hilo<0, 0>, k_pack_hilo<1, 0>, k_pack_hilo<2, 0>);
 }
 
 // K3 on the tensor cores (mixed precision): form V and pack it to 16-bit
@@ -348,17 +360,22 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
       a.Zout = (float*)jb->Z;
       a.zrows = c->r;
       const dim3 grid((unsigned)std::min<size_t>(pts / TC_PTS, 148));
-      switch (c->NB1) {
-#define GM_TC_S(NB)                                                                                       \
-  case NB:                                                                                                \
-    pdl_launch(k_tc_contract<0, NB, 1>, grid, dim3(192), TcShape<0, NB>::SMEM, s, jb->mapHi, jb->mapLo, \
-               c->mapWhi, c->mapWlo, a, (const LoopState*)jb->ls);                                        \
+      auto store = [&](auto es) {
+        constexpr int ES = decltype(es)::value;
+        switch (c->NB1) {
+#define GM_TC_S(NB)                                                                                          \
+  case NB:                                                                                                   \
+    pdl_launch(k_tc_contract<0, NB, 1, ES>, grid, dim3(192), TcShape<0, NB, ES>::SMEM, s, jb->mapHi, jb->mapLo, \
+               c->mapWhi, c->mapWlo, a, (const LoopState*)jb->ls);                                           \
     break;
-        GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
-        GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
+          GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
+          GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
 #undef GM_TC_S
-        default: break;
-      }
+          default: break;
+        }
+      };
+      if (c->tf32) store(std::integral_constant<int, 4>());
+      else store(std::integral_constant<int, 2>());
     }
     return;
   }
@@ -404,12 +421,15 @@ static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
                    (const float*)jb->V, c->r, c->rKKp, npts_total, (void*)jb->Vhi, (void*)jb->Vlo, c->eW,
                    (const LoopState*)jb->ls);
       };
-      if (c->f16) {
-        if (mode) pack(k_pack_rows<1, true>);
-        else pack(k_pack_rows<0, true>);
+      if (c->tf32) {
+        if (mode) pack(k_pack_rows<1, 2>);
+        else pack(k_pack_rows<0, 2>);
+      } else if (c->f16) {
+        if (mode) pack(k_pack_rows<1, 1>);
+        else pack(k_pack_rows<0, 1>);
       } else {
-        if (mode) pack(k_pack_rows<1, false>);
-        else pack(k_pack_rows<0, false>);
+        if (mode) pack(k_pack_rows<1, 0>);
+        else pack(k_pack_rows<0, 0>);
       }
       TcArgs a = tc_args(jb, g);
       a.KKp = c->rKKp;

@@ -86,25 +86,39 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// Instruction descriptor for kind::f16: D in F32, A and B both BF16 (bf16 = 1)
-// or both F16 (bf16 = 0), both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
+// Operand formats of the instruction descriptor: kind::f16 takes F16 (0) or
+// BF16 (1), kind::tf32 takes TF32 (2); A and B have the same format.
+constexpr uint32_t FMT_F16 = 0, FMT_BF16 = 1, FMT_TF32 = 2;
+
+// Instruction descriptor for kind::f16 / kind::tf32: D in F32, A and B in
+// format fmt, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_mma(int M, int N, uint32_t fmt) {
   return (1u << 4)                          // D format: F32
-         | ((bf16 ? 1u : 0u) << 7)          // A format
-         | ((bf16 ? 1u : 0u) << 10)         // B format
+         | (fmt << 7)                       // A format
+         | (fmt << 10)                      // B format
          | (0u << 15) | (0u << 16)          // A, B K-major
          | ((uint32_t)(N >> 3) << 17)       // N / 8
          | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread: kind::f16 (K = 16
+// per instruction) or, with TF32, kind::tf32 (K = 8).
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 // Arrive on the mbarrier once all prior MMAs of this thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {

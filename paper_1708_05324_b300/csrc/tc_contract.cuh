@@ -75,12 +75,16 @@ __device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n) {
   return 14 - e;
 }
 
-template <int N, int NB>
+// ES: operand element bytes, 2 (BF16 / FP16) or 4 (TF32); a core-matrix row
+// of 16 bytes holds EPC = 16 / ES elements.
+template <int N, int NB, int ES = 2>
 struct TcShape {
   static constexpr int P = N * (N + 1) / 2;
-  static constexpr int NRB = (P + NB - 1) / NB;       // row blocks
-  static constexpr int V_BYTES = TC_PTS * TC_KC * 2;  // one of hi / lo
-  static constexpr int G_BYTES = NB * TC_KC * 2;
+  static constexpr int NRB = (P + NB - 1) / NB;        // row blocks
+  static constexpr int EPC = 16 / ES;                  // elements per core-matrix row
+  static constexpr int KSTEPS = TC_KC * ES / 32;       // MMAs of 32 bytes of K per chunk
+  static constexpr int V_BYTES = TC_PTS * TC_KC * ES;  // one of hi / lo
+  static constexpr int G_BYTES = NB * TC_KC * ES;
   static constexpr int STAGE = 2 * (V_BYTES + G_BYTES);
   static constexpr int FIT = 200 * 1024 / STAGE;
   static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 6 ? 6 : FIT);
@@ -153,13 +157,13 @@ __device__ __forceinline__ void drain_rb(int rb, uint32_t taddr, const float2* a
 
 // OUT 0: the l-sum epilogue into NL (N modes, compile-time); OUT 1: the
 // accumulator rows stored as Z (first GEMM of the low-rank coupling; N is 0).
-template <int N, int NB, int OUT>
+template <int N, int NB, int OUT, int ES = 2>
 __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ CUtensorMap mapVhi,
                                                          const __grid_constant__ CUtensorMap mapVlo,
                                                          const __grid_constant__ CUtensorMap mapGhi,
                                                          const __grid_constant__ CUtensorMap mapGlo, TcArgs a,
                                                          const LoopState* __restrict__ ls) {
-  using S = TcShape<N, NB>;
+  using S = TcShape<N, NB, ES>;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char* smem = tc_smem_raw + ((1024 - (tc::smem_addr(tc_smem_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t full[S::STAGES], empty[S::STAGES], acc_full[2], acc_empty[2];
@@ -210,17 +214,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
             }
             unsigned char* st = smem + (size_t)s * S::STAGE;
             tc::mbar_arrive_expect_tx(&full[s], S::STAGE);
-            tc::tma_load_3d(st, &mapVhi, 0, tile * TC_PTS, kc * (TC_KC / 8), &full[s]);
-            tc::tma_load_3d(st + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kc * (TC_KC / 8), &full[s]);
-            tc::tma_load_3d(st + 2 * S::V_BYTES, &mapGhi, 0, rb * NB, kc * (TC_KC / 8), &full[s]);
-            tc::tma_load_3d(st + 2 * S::V_BYTES + S::G_BYTES, &mapGlo, 0, rb * NB, kc * (TC_KC / 8), &full[s]);
+            const int kq = kc * (TC_KC / S::EPC);  // K coordinate in core-matrix rows
+            tc::tma_load_3d(st, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
+            tc::tma_load_3d(st + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
+            tc::tma_load_3d(st + 2 * S::V_BYTES, &mapGhi, 0, rb * NB, kq, &full[s]);
+            tc::tma_load_3d(st + 2 * S::V_BYTES + S::G_BYTES, &mapGlo, 0, rb * NB, kq, &full[s]);
           }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16(TC_PTS, NB, a.f16 == 0);
+      const uint32_t idesc =
+          tc::idesc_mma(TC_PTS, NB, ES == 4 ? tc::FMT_TF32 : (a.f16 ? tc::FMT_F16 : tc::FMT_BF16));
       const uint32_t lboV = TC_PTS * 16, lboG = NB * 16, sbo = 128;
       int c = 0, w = 0;
       for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
@@ -245,12 +251,13 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
             const uint32_t base = tc::smem_addr(smem + (size_t)s * S::STAGE);
             const uint32_t vH = base, vL = base + S::V_BYTES, gH = base + 2 * S::V_BYTES, gL = gH + S::G_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < TC_KC / 16; ++kk) {
+            for (int kk = 0; kk < S::KSTEPS; ++kk) {
+              // 32 bytes of K per MMA: two core matrices along K
               const uint32_t oV = (uint32_t)kk * 2 * lboV, oG = (uint32_t)kk * 2 * lboG;
-              tc::mma_f16(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
-                          (kc > 0 || kk > 0) ? 1u : 0u);
-              tc::mma_f16(d, tc::smem_desc(vL + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc, 1u);
-              tc::mma_f16(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gL + oG, lboG, sbo), idesc, 1u);
+              tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
+                               (kc > 0 || kk > 0) ? 1u : 0u);
+              tc::mma<ES == 4>(d, tc::smem_desc(vL + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc, 1u);
+              tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gL + oG, lboG, sbo), idesc, 1u);
             }
             tc::mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
           }
@@ -331,23 +338,51 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
 // the lanes.
 constexpr int PACK_PTS = 32, PACK_WARPS = 8;
 
-template <bool F16> struct Half16;
-template <> struct Half16<false> {
+// Operand types of the hi/lo split: OP 0 BF16, 1 FP16, 2 TF32 (FP32 words
+// with the low 13 mantissa bits cleared by rounding to nearest, ties away).
+template <int OP> struct Split;
+template <> struct Split<0> {
   using T = __nv_bfloat16;
+  static constexpr int EPC = 8;
   __device__ static T rn(float x) { return __float2bfloat16_rn(x); }
   __device__ static float back(T h) { return __bfloat162float(h); }
 };
-template <> struct Half16<true> {
+template <> struct Split<1> {
   using T = __half;
+  static constexpr int EPC = 8;
   __device__ static T rn(float x) { return __float2half_rn(x); }
   __device__ static float back(T h) { return __half2float(h); }
 };
+template <> struct Split<2> {
+  using T = float;
+  static constexpr int EPC = 4;
+  __device__ static T rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+  }
+  __device__ static float back(T h) { return h; }
+};
 
-template <int MODE, bool F16>
+// Eight consecutive K values of one point to the blocked layout
+// [K/EPC][npts][EPC]: one or two 16-byte pieces.
+template <int OP>
+__device__ __forceinline__ void store_chunk8(typename Split<OP>::T* V, int kc, int npts_total, int pt,
+                                             const typename Split<OP>::T* v8) {
+  constexpr int EPC = Split<OP>::EPC;
+#pragma unroll
+  for (int q = 0; q < 8 / EPC; ++q) {
+    const size_t o = ((size_t)(kc * (8 / EPC) + q) * npts_total + pt) * EPC;
+    *reinterpret_cast<uint4*>(V + o) = *reinterpret_cast<const uint4*>(v8 + q * EPC);
+  }
+}
+
+template <int MODE, int OP>
 __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
     Geo g, const float2* __restrict__ A, const float* __restrict__ Y, const int2* __restrict__ pairs, int KKp,
     int npts_total, void* __restrict__ Vhi_, void* __restrict__ Vlo_, const LoopState* __restrict__ ls) {
-  using H = Half16<F16>;
+  using H = Split<OP>;
+  constexpr bool F16 = OP == 1;
   using T = typename H::T;
   T* Vhi = reinterpret_cast<T*>(Vhi_);
   T* Vlo = reinterpret_cast<T*>(Vlo_);
@@ -391,9 +426,8 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
       hi[i] = H::rn(x);
       lo[i] = H::rn(x - H::back(hi[i]));
     }
-    const size_t o = ((size_t)kc * npts_total + pt) * 8;
-    *reinterpret_cast<uint4*>(Vhi + o) = *reinterpret_cast<const uint4*>(hi);
-    *reinterpret_cast<uint4*>(Vlo + o) = *reinterpret_cast<const uint4*>(lo);
+    store_chunk8<OP>(Vhi, kc, npts_total, pt, hi);
+    store_chunk8<OP>(Vlo, kc, npts_total, pt, lo);
   }
 }
 
@@ -402,12 +436,13 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
 // blocked 16-bit hi/lo layout [KKp/8][npts][8] (r padded with zeros to KKp);
 // FP16 scaled by 2^(eV - eVoff), since |Z| <= 2^eVoff max |U|.  One thread
 // per point; Z / Y' loads coalesced across the threads.
-template <int MODE, bool F16>
+template <int MODE, int OP>
 __global__ void __launch_bounds__(256) k_pack_rows(Geo g, const float* __restrict__ Zs, const float* __restrict__ Ys,
                                                    int r, int KKp, int npts_total, void* __restrict__ Vhi_,
                                                    void* __restrict__ Vlo_, int eVoff,
                                                    const LoopState* __restrict__ ls) {
-  using H = Half16<F16>;
+  using H = Split<OP>;
+  constexpr bool F16 = OP == 1;
   using T = typename H::T;
   T* Vhi = reinterpret_cast<T*>(Vhi_);
   T* Vlo = reinterpret_cast<T*>(Vlo_);
@@ -432,9 +467,8 @@ __global__ void __launch_bounds__(256) k_pack_rows(Geo g, const float* __restric
       hi[i] = H::rn(x);
       lo[i] = H::rn(x - H::back(hi[i]));
     }
-    const size_t o = ((size_t)kc * npts_total + pt) * 8;
-    *reinterpret_cast<uint4*>(Vhi + o) = *reinterpret_cast<const uint4*>(hi);
-    *reinterpret_cast<uint4*>(Vlo + o) = *reinterpret_cast<const uint4*>(lo);
+    store_chunk8<OP>(Vhi, kc, npts_total, pt, hi);
+    store_chunk8<OP>(Vlo, kc, npts_total, pt, lo);
   }
 }
 

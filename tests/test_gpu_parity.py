@@ -276,11 +276,12 @@ def test_device_pointers_and_torch_stream():
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("N,Nt,fR", [(3, 256, 0.18), (6, 512, 0.18), (9, 256, 0.0), (10, 256, 0.18),
                                      (12, 128, 0.18), (15, 1024, 0.18), (16, 256, 0.0), (1, 128, 0.18)])
-@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+@pytest.mark.parametrize("mixed", ["bf16", "fp16", "tf32"])
 def test_mixed_tensor_core_contraction(N, Nt, fR, mixed):
     """The mixed paths (FFTs in FP32, coupling contraction as a tcgen05 GEMM
-    on BF16 or scaled FP16 hi/lo operands for N >= 9, the FP32 register
-    contraction below) against the FP64 oracle: <= 1e-3 relative L2."""
+    on BF16, scaled FP16 or TF32 hi/lo operands for N >= 9, the FP32
+    register contraction below) against the FP64 oracle: <= 1e-3 relative
+    L2."""
     key = ("t", N, Nt, fR)
     prob = small(*key)
     ref, sref = oracle_small(key)
@@ -292,7 +293,7 @@ def test_mixed_tensor_core_contraction(N, Nt, fR, mixed):
     assert err < 1e-5
 
 
-@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+@pytest.mark.parametrize("mixed", ["bf16", "fp16", "tf32"])
 def test_mixed_c2_prefix(mixed):
     prob, ref, sref = c2_prefix()
     out, st, rc = gpu_run(prob, mixed, tol=1e-8)
@@ -320,7 +321,7 @@ def c4_small():
     return prob, ref
 
 
-@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+@pytest.mark.parametrize("mixed", ["bf16", "fp16", "tf32"])
 def test_mixed_dense_42_mode_contraction(mixed):
     prob, ref = c4_small()
     out, st, rc = gpu_run(prob, mixed, fixed_iters=3)
@@ -328,7 +329,7 @@ def test_mixed_dense_42_mode_contraction(mixed):
     assert rel(out, ref) < 1e-3
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16", "tf32"])
 def test_low_rank_coupling_matches_dense(precision, monkeypatch):
     """The 15-mode GRIN fiber: the pair matrix of S is the Gram matrix of the
     products of Hermite-Gauss modes of total order <= 4, which span the 45

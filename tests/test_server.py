@@ -34,12 +34,12 @@ def _wait(srv, tickets, shapes, timeout=120):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16", "tf32"])
 def test_results_are_the_same_alone_and_in_the_mix(precision):
     """Alone vs in the mix: FP64 to 1e-12, FP32 to 1e-6, the mixed served
     path (tensor-core contraction for the 10-, 12- and 15-mode requests) to
     its stated 1e-3."""
-    mixed = precision in ("bf16", "fp16")
+    mixed = precision in ("bf16", "fp16", "tf32")
     specs = ([(10, 256, 1), (15, 512, 2), (3, 256, 3), (12, 128, 4)] if mixed
              else [(1, 256, 1), (3, 1024, 2), (6, 512, 3), (3, 256, 4)])
     ctxs = [_ctx(*s[:2], precision, s[2]) for s in specs]
