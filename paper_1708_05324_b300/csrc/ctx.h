@@ -34,6 +34,8 @@ struct gm_job {
   int* flag = nullptr;
   gm::LoopState* ls = nullptr;      // device
   double2* part = nullptr;          // [TRAPZ_MAX_BLOCKS] per-block sums of K5
+  unsigned* bar = nullptr;          // grid-barrier counter of the long-step kernel
+  int persist_grid = -1;            // blocks of the long-step kernel (0: not used; -1: not chosen yet)
   gm::LoopState* h_ls = nullptr;    // pinned host mirror
   double2* h_io = nullptr;      // pinned host staging [N][n]
   cudaStream_t cap = nullptr;   // private stream for graph capture

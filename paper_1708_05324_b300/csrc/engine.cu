@@ -629,6 +629,7 @@ static void free_job(gm_job* jb) {
   cudaFree(jb->Vlo);
   cudaFree(jb->ls);
   cudaFree(jb->part);
+  cudaFree(jb->bar);
   cudaFreeHost(jb->h_ls);
   cudaFreeHost(jb->h_io);
   if (jb->cap) cudaStreamDestroy(jb->cap);
@@ -734,6 +735,7 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
   al((void**)&jb->flag, sizeof(int));
   al((void**)&jb->ls, sizeof(LoopState));
   al((void**)&jb->part, sizeof(double2) * TRAPZ_MAX_BLOCKS);
+  al((void**)&jb->bar, 64);
   if (c->tc) {
     al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
     al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));

@@ -41,6 +41,7 @@ struct LoopState {
   int hist[33];
   double spec[4];          // sum |psi0|^2, photon sum (filled by k_spec_sums)
   unsigned tc_err;         // a tensor-core contraction wait timed out
+  unsigned sync_err;       // a grid barrier of the long-step kernel timed out
   unsigned arrive;         // blocks of k_trapz<R, true> that have added their sums
 };
 
@@ -91,6 +92,29 @@ __global__ void k_phase_tables(const double* __restrict__ beta, int Nn, int M, d
 // K1: A_j(t) = F^-1{(psi0 + dpsi_j) E_j}   (Eq. cov), grid (N S, M+1); with
 // S > 1 the S blocks of a cluster share one transform (fft_cluster).
 // ---------------------------------------------------------------------------
+// Data written by other blocks earlier in the same kernel (the persistent
+// long-step kernel) is read through L2 (__ldcg), never a stale L1 line.
+template <typename R, int EPT, int S>
+__device__ __forceinline__ void ip_to_time_task(const Geo& g, const cplx<R>* __restrict__ psiR,
+                                                const cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ E,
+                                                cplx<R>* __restrict__ A, const cplx<R>* __restrict__ tw, int iter,
+                                                int p, int j, cplx<R>* sm) {
+  const int n = g.n;
+  const size_t off = ((size_t)j * g.N + p) * n;
+  const cplx<R>* ps = psiR + (size_t)p * n;
+  const cplx<R>* dp = (iter > 0) ? dpsi + ((size_t)(j - 1) * g.N + p) * n : nullptr;
+  const cplx<R>* e = E + off;
+  const R inv_n = (R)1.0 / (R)n;
+  auto load = [&](int q) {
+    cplx<R> x = __ldcg(ps + q);
+    if (dp) x = cadd<R>(x, __ldcg(dp + q));
+    return cmul<R>(x, e[q]);
+  };
+  auto store = [&](int t, cplx<R> v) { A[off + t] = cscale<R>(v, inv_n); };
+  if (S == 1) fft_block<R, -1, EPT>(sm, n, tw, load, store);
+  else fft_cluster<R, -1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
+}
+
 template <typename R, int EPT, int S>
 __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __restrict__ psiR,
                                                      const cplx<R>* __restrict__ dpsi,
@@ -103,28 +127,15 @@ __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __rest
   const int p = blockIdx.x / S, j = blockIdx.y;
   const int iter = ls->iter;
   if (iter > 0 && j == 0) return;
-  const int n = g.n;
-  const size_t off = ((size_t)j * g.N + p) * n;
-  const cplx<R>* ps = psiR + (size_t)p * n;
-  const cplx<R>* dp = (iter > 0) ? dpsi + ((size_t)(j - 1) * g.N + p) * n : nullptr;
-  const cplx<R>* e = E + off;
-  const R inv_n = (R)1.0 / (R)n;
-  auto load = [&](int q) {
-    cplx<R> x = ps[q];
-    if (dp) x = cadd<R>(x, dp[q]);
-    return cmul<R>(x, e[q]);
-  };
-  auto store = [&](int t, cplx<R> v) { A[off + t] = cscale<R>(v, inv_n); };
-  if (S == 1) fft_block<R, -1, EPT>(sm, n, tw, load, store);
-  else fft_cluster<R, -1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
+  ip_to_time_task<R, EPT, S>(g, psiR, dpsi, E, A, tw, iter, p, j, sm);
 }
 
 // U_k(t): |A_m|^2 for m == n, 2 Re(A_m A_n^*) for m < n (pairs k = (m <= n))
 template <typename R>
 __device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, int2 mn, int t) {
-  const cplx<R> am = a[(size_t)mn.x * n + t];
+  const cplx<R> am = __ldcg(a + (size_t)mn.x * n + t);
   if (mn.x == mn.y) return am.x * am.x + am.y * am.y;
-  const cplx<R> an = a[(size_t)mn.y * n + t];
+  const cplx<R> an = __ldcg(a + (size_t)mn.y * n + t);
   return (R)2.0 * (am.x * an.x + am.y * an.y);
 }
 
@@ -138,19 +149,14 @@ __device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, 
 // contraction forms U from A.  grid (ceil(cnt/2), M+1)
 // ---------------------------------------------------------------------------
 template <typename R, int EPT, int SRC>
-__global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
-                                                      const cplx<R>* __restrict__ H,
-                                                      const cplx<R>* __restrict__ tw,
-                                                      const int2* __restrict__ pairs, const R* __restrict__ Zs,
-                                                      int cnt, const LoopState* __restrict__ ls) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
-  pdl_enter();
-  const int j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;
+__device__ __forceinline__ void pairs_raman_task(const Geo& g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
+                                                 const cplx<R>* __restrict__ H, const cplx<R>* __restrict__ tw,
+                                                 const int2* __restrict__ pairs, const R* __restrict__ Zs, int cnt,
+                                                 int kp, int j, cplx<R>* sm) {
   const int n = g.n;
-  const int k1 = 2 * blockIdx.x, k2 = k1 + 1;
+  const int k1 = 2 * kp, k2 = k1 + 1;
   const bool has2 = k2 < cnt;
+  __syncthreads();  // the block's previous use of sm is over
   // the rows are staged in shared memory first: the transform's first pass
   // then reads no global memory, which keeps its registers free
   if (SRC == 0) {
@@ -163,7 +169,8 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
   } else {
     const R* z1 = Zs + ((size_t)j * cnt + k1) * n;
 #pragma unroll 4
-    for (int t = threadIdx.x; t < n; t += blockDim.x) sm[pad16(t)] = mk<R>(z1[t], has2 ? z1[n + t] : (R)0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+      sm[pad16(t)] = mk<R>(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : (R)0);
   }
   auto from_smem = [&](int q) { return sm[pad16(q)]; };
   auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
@@ -174,6 +181,20 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
     if (has2) y1[n + t] = y.y;
   };
   fft_block<R, +1, EPT>(sm, n, tw, from_smem, store);
+}
+
+template <typename R, int EPT, int SRC>
+__global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
+                                                      const cplx<R>* __restrict__ H,
+                                                      const cplx<R>* __restrict__ tw,
+                                                      const int2* __restrict__ pairs, const R* __restrict__ Zs,
+                                                      int cnt, const LoopState* __restrict__ ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  pdl_enter();
+  const int j = blockIdx.y;
+  if (ls->iter > 0 && j == 0) return;
+  pairs_raman_task<R, EPT, SRC>(g, A, Y, H, tw, pairs, Zs, cnt, blockIdx.x, j, sm);
 }
 
 // K2 with the two transforms of a pair spread over an S-block cluster
@@ -226,30 +247,37 @@ __global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __
 // shared memory as a broadcast, 16 bytes per load (rows padded to KKP).
 // One thread per (j, t).
 template <typename R, int N, int MODE>
-__global__ void __launch_bounds__(128) k_contract_reg(Geo g, const cplx<R>* __restrict__ A,
-                                                      const R* __restrict__ Y, const R* __restrict__ Gm,
-                                                      cplx<R>* __restrict__ NL, const LoopState* __restrict__ ls) {
-  constexpr int K = N * (N + 1) / 2;
-  constexpr int KK = MODE == 2 ? 2 * K : K;
-  constexpr int VW = 16 / (int)sizeof(R);             // values per 16-byte load
-  constexpr int KKP = (KK + VW - 1) / VW * VW;        // padded row length
-  using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-  __shared__ __align__(16) R Gs[K * KKP];
-  for (int i = threadIdx.x; i < K * KKP; i += blockDim.x) {
-    const int r = i / KKP, k = i - r * KKP;
-    Gs[i] = k < KK ? Gm[r * KK + k] : (R)0;
+struct RegShape {
+  static constexpr int K = N * (N + 1) / 2;
+  static constexpr int KK = MODE == 2 ? 2 * K : K;
+  static constexpr int VW = 16 / (int)sizeof(R);       // values per 16-byte load
+  static constexpr int KKP = (KK + VW - 1) / VW * VW;  // padded row length
+};
+
+// G [K][KK] to shared memory [K][KKP], zero padding (the whole block)
+template <typename R, int N, int MODE>
+__device__ __forceinline__ void stage_g(const R* __restrict__ Gm, R* Gs) {
+  using S = RegShape<R, N, MODE>;
+  for (int i = threadIdx.x; i < S::K * S::KKP; i += blockDim.x) {
+    const int r = i / S::KKP, k = i - r * S::KKP;
+    Gs[i] = k < S::KK ? Gm[r * S::KK + k] : (R)0;
   }
-  pdl_enter();
-  __syncthreads();
+}
+
+// NL of one point pt = j n + t (all N modes)
+template <typename R, int N, int MODE>
+__device__ __forceinline__ void contract_reg_point(const Geo& g, const cplx<R>* __restrict__ A,
+                                                   const R* __restrict__ Y, const R* Gs, cplx<R>* __restrict__ NL,
+                                                   size_t pt) {
+  using S = RegShape<R, N, MODE>;
+  constexpr int K = S::K, KK = S::KK, VW = S::VW, KKP = S::KKP;
+  using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
   const int n = g.n;
-  const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pt >= (size_t)(g.M + 1) * n) return;
   const int j = (int)(pt / n), t = (int)(pt - (size_t)j * n);
-  if (ls->iter > 0 && j == 0) return;
   const cplx<R>* a = A + (size_t)j * N * n + t;
   cplx<R> av[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) av[l] = a[(size_t)l * n];
+  for (int l = 0; l < N; ++l) av[l] = __ldcg(a + (size_t)l * n);
   R v[KK];
   {
     const R* yp = Y + (size_t)j * K * n + t;
@@ -262,10 +290,10 @@ __global__ void __launch_bounds__(128) k_contract_reg(Geo g, const cplx<R>* __re
         const R u = (m == q) ? av[m].x * av[m].x + av[m].y * av[m].y
                              : (R)2 * (av[m].x * av[q].x + av[m].y * av[q].y);
         if (MODE == 0) v[k] = u;
-        else if (MODE == 1) v[k] = fK * u + fR * yp[(size_t)k * n];
+        else if (MODE == 1) v[k] = fK * u + fR * __ldcg(yp + (size_t)k * n);
         else {
           v[k] = u;
-          v[K + k] = yp[(size_t)k * n];
+          v[K + k] = __ldcg(yp + (size_t)k * n);
         }
       }
   }
@@ -298,27 +326,37 @@ __global__ void __launch_bounds__(128) k_contract_reg(Geo g, const cplx<R>* __re
   for (int p = 0; p < N; ++p) out[(size_t)p * n] = nl[p];
 }
 
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(128) k_contract_reg(Geo g, const cplx<R>* __restrict__ A,
+                                                      const R* __restrict__ Y, const R* __restrict__ Gm,
+                                                      cplx<R>* __restrict__ NL, const LoopState* __restrict__ ls) {
+  using S = RegShape<R, N, MODE>;
+  __shared__ __align__(16) R Gs[S::K * S::KKP];
+  stage_g<R, N, MODE>(Gm, Gs);
+  pdl_enter();
+  __syncthreads();
+  const int n = g.n;
+  const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= (size_t)(g.M + 1) * n) return;
+  if (ls->iter > 0 && pt < (size_t)n) return;
+  contract_reg_point<R, N, MODE>(g, A, Y, Gs, NL, pt);
+}
+
 // ---------------------------------------------------------------------------
 // K4: I_j(w) = i gamma0 s(w) F{NL_p}(w) exp(-i beta j dz)   (Eq. MPA_eq)
 // grid (N S, M+1) as K1; fac[q] = gamma0 (1 + w_q/omega0) (or gamma0 without
 // self-steepening), tabulated in FP64 and rounded once.
 // ---------------------------------------------------------------------------
 template <typename R, int EPT, int S>
-__global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restrict__ NL,
-                                                    const cplx<R>* __restrict__ E, const R* __restrict__ fac,
-                                                    cplx<R>* __restrict__ I,
-                                                    const cplx<R>* __restrict__ tw,
-                                                    const LoopState* __restrict__ ls) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
-  pdl_enter();
-  const int p = blockIdx.x / S, j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;
+__device__ __forceinline__ void integrand_task(const Geo& g, const cplx<R>* __restrict__ NL,
+                                               const cplx<R>* __restrict__ E, const R* __restrict__ fac,
+                                               cplx<R>* __restrict__ I, const cplx<R>* __restrict__ tw, int p, int j,
+                                               cplx<R>* sm) {
   const int n = g.n;
   const size_t off = ((size_t)j * g.N + p) * n;
   const cplx<R>* src = NL + off;
   const cplx<R>* e = E + off;
-  auto load = [&](int t) { return src[t]; };
+  auto load = [&](int t) { return __ldcg(src + t); };
   auto store = [&](int q, cplx<R> X) {
     const R f = fac[q];  // gamma0 s(w_q)
     const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
@@ -331,6 +369,21 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
   if (S == 1) fft_block<R, +1, EPT, TAB>(sm, n, tw, 1, load, store);
   else fft_cluster<R, +1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
 }
+
+template <typename R, int EPT, int S>
+__global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restrict__ NL,
+                                                    const cplx<R>* __restrict__ E, const R* __restrict__ fac,
+                                                    cplx<R>* __restrict__ I,
+                                                    const cplx<R>* __restrict__ tw,
+                                                    const LoopState* __restrict__ ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
+  pdl_enter();
+  const int p = blockIdx.x / S, j = blockIdx.y;
+  if (ls->iter > 0 && j == 0) return;
+  integrand_task<R, EPT, S>(g, NL, E, fac, I, tw, p, j, sm);
+}
+
 
 // Convergence decision (one thread): eps, stop rule, reset of the sums, and
 // the while-node condition when running inside a graph.  Every path ends the
@@ -414,48 +467,57 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
   }
 }
 
+// The sweep over j of one element; its two terms added to diff and nrm.
+template <typename R>
+__device__ __forceinline__ void trapz_element(const Geo& g, const cplx<R>* __restrict__ psiR,
+                                              cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ I, int iter,
+                                              size_t e, R hdz, double& diff, double& nrm) {
+  constexpr int JC = TrapzJC<R>::value;
+  const size_t Nn = (size_t)g.N * g.n;
+  const int M = g.M;
+  const cplx<R> p0 = __ldcg(psiR + e);
+  cplx<R> Ip = __ldcg(I + e);
+  cplx<R> acc = mk<R>(0, 0);
+  R dsum = 0, nsum = 0;  // this element's terms in the working precision
+  for (int j0 = 1; j0 <= M; j0 += JC) {
+    cplx<R> ij[JC], old[JC];
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      const int j = j0 + i;
+      ij[i] = j <= M ? __ldcg(I + (size_t)j * Nn + e) : mk<R>(0, 0);
+      old[i] = (j <= M && iter > 0) ? __ldcg(dpsi + (size_t)(j - 1) * Nn + e) : mk<R>(0, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < JC; ++i) {
+      const int j = j0 + i;
+      if (j > M) break;
+      acc = cadd<R>(acc, cscale<R>(cadd<R>(Ip, ij[i]), hdz));
+      Ip = ij[i];
+      const R dx = acc.x - old[i].x, dy = acc.y - old[i].y;
+      dsum += dx * dx + dy * dy;
+      const R px = p0.x + acc.x, py = p0.y + acc.y;
+      nsum += px * px + py * py;
+      dpsi[(size_t)(j - 1) * Nn + e] = acc;
+    }
+  }
+  diff += (double)dsum;
+  nrm += (double)nsum;
+}
+
 template <typename R, bool DECIDE>
 __global__ void __launch_bounds__(TRAPZ_T) k_trapz(Geo g, const cplx<R>* __restrict__ psiR, cplx<R>* __restrict__ dpsi,
                                                    const cplx<R>* __restrict__ I, LoopState* ls, double2* part,
                                                    cudaGraphConditionalHandle h, int use_cond) {
-  constexpr int JC = TrapzJC<R>::value;
   __shared__ double red[64];
   __shared__ bool last;
   pdl_enter();
   const size_t Nn = (size_t)g.N * g.n;
-  const int iter = ls->iter, M = g.M;
+  const int iter = ls->iter;
   const int tid = threadIdx.x;
   const R hdz = (R)g.hdz;
   double diff = 0.0, nrm = 0.0;
-  for (size_t e = (size_t)blockIdx.x * TRAPZ_T + tid; e < Nn; e += (size_t)gridDim.x * TRAPZ_T) {
-    const cplx<R> p0 = psiR[e];
-    cplx<R> Ip = I[e];
-    cplx<R> acc = mk<R>(0, 0);
-    R dsum = 0, nsum = 0;  // this element's terms in the working precision
-    for (int j0 = 1; j0 <= M; j0 += JC) {
-      cplx<R> ij[JC], old[JC];
-#pragma unroll
-      for (int i = 0; i < JC; ++i) {
-        const int j = j0 + i;
-        ij[i] = j <= M ? I[(size_t)j * Nn + e] : mk<R>(0, 0);
-        old[i] = (j <= M && iter > 0) ? dpsi[(size_t)(j - 1) * Nn + e] : mk<R>(0, 0);
-      }
-#pragma unroll
-      for (int i = 0; i < JC; ++i) {
-        const int j = j0 + i;
-        if (j > M) break;
-        acc = cadd<R>(acc, cscale<R>(cadd<R>(Ip, ij[i]), hdz));
-        Ip = ij[i];
-        const R dx = acc.x - old[i].x, dy = acc.y - old[i].y;
-        dsum += dx * dx + dy * dy;
-        const R px = p0.x + acc.x, py = p0.y + acc.y;
-        nsum += px * px + py * py;
-        dpsi[(size_t)(j - 1) * Nn + e] = acc;
-      }
-    }
-    diff += (double)dsum;
-    nrm += (double)nsum;
-  }
+  for (size_t e = (size_t)blockIdx.x * TRAPZ_T + tid; e < Nn; e += (size_t)gridDim.x * TRAPZ_T)
+    trapz_element<R>(g, psiR, dpsi, I, iter, e, hdz, diff, nrm);
   block_sum2(diff, nrm, red);
   if (tid == 0) {
     part[blockIdx.x] = make_double2(diff, nrm);
@@ -490,7 +552,7 @@ __global__ void __launch_bounds__(TRAPZ_T) k_trapz(Geo g, const cplx<R>* __restr
 // step succeeded and steps remain) and the inner one re-armed for the next
 // long step.
 __device__ __forceinline__ void step_end(LoopState* ls, cudaGraphConditionalHandle hStep,
-                                         cudaGraphConditionalHandle hIter, int use_cond) {
+                                         cudaGraphConditionalHandle hIter, int use_cond, bool rearm_iter = true) {
   const int status = ls->status, it = ls->iter;
   if (status == ST_OK) {
     ls->step += 1;
@@ -505,7 +567,7 @@ __device__ __forceinline__ void step_end(LoopState* ls, cudaGraphConditionalHand
   ls->prev_eps = INFINITY;
   if (use_cond) {
     cudaGraphSetConditional(hStep, (status == ST_OK && ls->step < ls->nsteps) ? 1u : 0u);
-    cudaGraphSetConditional(hIter, 1u);
+    if (rearm_iter) cudaGraphSetConditional(hIter, 1u);
   }
 }
 

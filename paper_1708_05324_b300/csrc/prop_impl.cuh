@@ -14,6 +14,7 @@
 #include "../../include/gmmnlse.h"
 #include "ctx.h"
 #include "engine.h"
+#include "persist.cuh"
 #include "kernels.cuh"
 #include "tc_contract.cuh"
 
@@ -81,6 +82,9 @@ static int tc_for_each_n(F&& f) {
   return rc;
 }
 
+template <typename R, class F>
+static void with_long_step(const gmmnlse_ctx* c, F&& f);
+
 // Once per device: raise the shared-memory limit of this unit's kernels.
 template <typename R>
 static int setup_device(int dev) {
@@ -124,6 +128,26 @@ static int setup_device(int dev) {
       return GMMNLSE_OK;
     });
     if (rc) return rc;
+  }
+  {
+    // the long-step kernels (dynamic shared memory: one transform buffer)
+    gmmnlse_ctx probe;
+    for (int N = 1; N <= 8; ++N)
+      for (int mode = 0; mode < 3; ++mode) {
+        probe.N = N;
+        probe.raman_mode = mode;
+        int rc = GMMNLSE_OK;
+        with_long_step<R>(&probe, [&](auto kern) {
+          cudaFuncAttributes fa;
+          if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+              cudaFuncSetAttribute(kern, A, smax - (int)fa.sharedSizeBytes) != cudaSuccess)
+            rc = GMMNLSE_E_CUDA;
+        });
+        if (rc) {
+          gm_set_last_error_text("long-step kernel: shared-memory attribute");
+          return rc;
+        }
+      }
   }
   CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, A, sm));
@@ -499,6 +523,101 @@ static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, 
              use_cond);
 }
 
+// ---------------------------------------------------------------------------
+// The long step as one cooperative kernel (persist.cuh): N <= 8 on the CUDA
+// cores with one-block transforms of 16 elements per thread (2048 <= n <=
+// 8192), opt-in with GMMNLSE_PERSIST=1.  On the 6-mode workload it measured
+// 89 us per iteration against 62 us for the kernel-per-step chain (the
+// combined kernel spills ~1 KB of registers in its transform phases, and
+// every phase waits for its slowest block), so the chain is the default.
+// ---------------------------------------------------------------------------
+static bool persist_disabled() {
+  const char* v = getenv("GMMNLSE_PERSIST");
+  return !(v && v[0] == '1');
+}
+
+// Calls f with the long-step kernel of this context's N and raman_mode.
+template <typename R, class F>
+static void with_long_step(const gmmnlse_ctx* c, F&& f) {
+  auto modes = [&](auto nc) {
+    constexpr int NN = decltype(nc)::value;
+    if (c->raman_mode == 0) f(k_long_step<R, NN, 0>);
+    else if (c->raman_mode == 1) f(k_long_step<R, NN, 1>);
+    else f(k_long_step<R, NN, 2>);
+  };
+  switch (c->N) {
+    case 1: modes(std::integral_constant<int, 1>()); break;
+    case 2: modes(std::integral_constant<int, 2>()); break;
+    case 3: modes(std::integral_constant<int, 3>()); break;
+    case 4: modes(std::integral_constant<int, 4>()); break;
+    case 5: modes(std::integral_constant<int, 5>()); break;
+    case 6: modes(std::integral_constant<int, 6>()); break;
+    case 7: modes(std::integral_constant<int, 7>()); break;
+    case 8: modes(std::integral_constant<int, 8>()); break;
+    default: break;
+  }
+}
+
+// Blocks of the long-step kernel for this job (every block resident), or 0
+// where it does not apply.
+template <typename R>
+static int long_step_grid(gm_job* jb) {
+  const gmmnlse_ctx* c = jb->ctx;
+  if (persist_disabled() || c->N > 8 || c->tc || c->lr || c->n < 2048 || c->n > 8192) return 0;
+  const int threads = c->n / 16;
+  const size_t smem = fft_smem<R>(c->n);
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->prm.device) != cudaSuccess) return 0;
+  int rc = -1;
+  with_long_step<R>(c, [&](auto kern) {
+    rc = (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  });
+  if (rc != (int)cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return std::min(sms * per_sm, TRAPZ_MAX_BLOCKS);
+}
+
+// Zero the barrier counter, then the cooperative long-step kernel.
+template <typename R>
+static void launch_long_step(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle hStep,
+                             int use_cond) {
+  gmmnlse_ctx* c = jb->ctx;
+  const size_t Nn = (size_t)c->N * c->n;
+  StepArgs a;
+  a.psiR = jb->psiR;
+  a.dpsi = jb->dpsi;
+  a.E = jb->E;
+  a.A = jb->A;
+  a.Y = jb->V;
+  a.NL = jb->NL;
+  a.I = jb->I;
+  a.H = c->H;
+  a.fac = c->fac;
+  a.tw = twid<R>(c);
+  a.pairs = c->pairs;
+  a.G = c->G;
+  a.psi0 = jb->psi0;
+  a.EM = jb->EM64 + (size_t)which * Nn;
+  a.part = jb->part;
+  a.bar = jb->bar;
+  cudaMemsetAsync(jb->bar, 0, sizeof(unsigned), s);
+  with_long_step<R>(c, [&](auto kern) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(jb->persist_grid);
+    cfg.blockDim = dim3(c->n / 16);
+    cfg.dynamicSmemBytes = fft_smem<R>(c->n);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, g, a, jb->ls, hStep, use_cond);
+  });
+}
+
 template <typename R>
 static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   cudaStream_t cs = jb->cap;
@@ -514,6 +633,12 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   cudaGraphNode_t nStep;
   CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
   cudaGraph_t gS = cp.conditional.phGraph_out[0];
+  if (jb->persist_grid > 0) {
+    // long-step body: the cooperative long-step kernel (iterations inside)
+    CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_long_step<R>(jb, g, which, cs, hStep, 1);
+    CK(cudaStreamEndCapture(cs, &gS));
+  } else {
   // the iteration loop's condition starts at 1 when the graph is launched;
   // the advance kernel re-arms it at the end of every long step
   CK(cudaGraphConditionalHandleCreate(&hIter, gS, 1, cudaGraphCondAssignDefault));
@@ -533,6 +658,7 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   CK(cudaStreamBeginCaptureToGraph(cs, gS, &nIter, nullptr, 1, cudaStreamCaptureModeThreadLocal));
   launch_advance<R>(jb, g, which, cs, hStep, hIter, 1);
   CK(cudaStreamEndCapture(cs, &gS));
+  }
   cudaGraphExec_t exec = nullptr;
   CK(cudaGraphInstantiate(&exec, root, 0));
   out.graph = root;
@@ -584,6 +710,14 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
   }
   // host-driven loop over the same kernels
   for (int st = 0; st < count; ++st) {
+    if (jb->persist_grid > 0) {
+      launch_long_step<R>(jb, g, which, s, 0, 0);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (jb->h_ls->status != ST_OK || jb->h_ls->sync_err) break;
+      continue;
+    }
     for (;;) {
       launch_iteration<R>(jb, g, s, 0, 0);
       CK(cudaGetLastError());
@@ -632,6 +766,8 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
     cudaEventDestroy(e1);
     return GMMNLSE_E_INVALID;
   }
+  // the long-step kernel, where it applies (chosen once per workspace)
+  if (jb->persist_grid < 0) jb->persist_grid = long_step_grid<R>(jb);
   // psi0 = F{A0} (FP64)
   rc = fft64(c, jb->io + Nn, tin, jb->psi0, c->N, +1, 1.0, s);
   if (rc) return rc;
@@ -704,6 +840,10 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
   }
   if (hs.tc_err) {
     gm_set_last_error_text("tensor-core contraction: a wait for its operands timed out");
+    return GMMNLSE_E_CUDA;
+  }
+  if (hs.sync_err) {
+    gm_set_last_error_text("long-step kernel: a grid barrier timed out");
     return GMMNLSE_E_CUDA;
   }
   if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;

@@ -223,6 +223,24 @@ def test_statistics_energy_and_photon_number():
     assert sum(st["iter_hist"]) == st["long_steps"]
 
 
+@pytest.mark.parametrize("N,fR", [(6, 0.18), (3, 0.0), (4, 0.18)])
+def test_long_step_kernel_matches_the_kernel_chain(N, fR, monkeypatch):
+    """The opt-in cooperative long-step kernel (GMMNLSE_PERSIST=1) runs the
+    same arithmetic as the kernel-per-step chain: equal results and
+    iteration counts, and the oracle's within the FP32 bar."""
+    prob = I.grin_problem("ls", N=N, Nt=2048, dt=4e-12 / 2048, kind="gaussian", fwhm=150e-15,
+                          energy=20e-9, L=2e-3, dz=1e-4, M=5, tol=1e-9, seed=11, fR=fR, s_from="gh")
+    chain, st_chain, rc = gpu_run(prob, "fp32")
+    assert rc == B.OK
+    monkeypatch.setenv("GMMNLSE_PERSIST", "1")
+    fused, st_fused, rc = gpu_run(prob, "fp32")
+    assert rc == B.OK
+    assert st_fused["iters_total"] == st_chain["iters_total"]
+    assert rel(fused, chain) < 1e-6
+    ref, _ = oracle_run(prob)
+    assert rel(fused, ref) < TOL["fp32"]
+
+
 def test_graph_and_host_loop_agree_bitwise(monkeypatch):
     prob = small("p", 3, 256, 0.18)
     a, sa, _ = gpu_run(prob, "fp64")
