@@ -441,7 +441,8 @@ static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
     if constexpr (std::is_same<R, float>::value) {
       const int npts_total = (jb->Mcap + 1) * c->n;
       auto pack = [&](auto kern) {
-        pdl_launch(kern, dim3((unsigned)((pts + 255) / 256)), dim3(256), 0, s, g, (const float*)jb->Z,
+        pdl_launch(kern, dim3((unsigned)((pts + PACK_PTS - 1) / PACK_PTS)), dim3(PACK_PTS * PACK_WARPS), 0, s, g,
+                   (const float*)jb->Z,
                    (const float*)jb->V, c->r, c->rKKp, npts_total, (void*)jb->Vhi, (void*)jb->Vlo, c->eW,
                    (const LoopState*)jb->ls);
       };

@@ -433,22 +433,24 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
 
 // Low-rank coupling, second GEMM: V' = (1 - fR) Z + fR Y' (MODE 1) or Z
 // (MODE 0) from the rows of Z = W U and Y' = h_R * Z ([M+1][r][n]) to the
-// blocked 16-bit hi/lo layout [KKp/8][npts][8] (r padded with zeros to KKp);
-// FP16 scaled by 2^(eV - eVoff), since |Z| <= 2^eVoff max |U|.  One thread
-// per point; Z / Y' loads coalesced across the threads.
+// blocked hi/lo layout [KKp/EPC][npts][EPC] (r padded with zeros to KKp);
+// FP16 scaled by 2^(eV - eVoff), since |Z| <= 2^eVoff max |U|.  A block
+// takes 32 points (the lanes of each warp); warp w packs the 8-wide chunks
+// kc = w, w + 8, ...: Z / Y' loads coalesced across the lanes, eight warps
+// of loads in flight per 32 points.
 template <int MODE, int OP>
-__global__ void __launch_bounds__(256) k_pack_rows(Geo g, const float* __restrict__ Zs, const float* __restrict__ Ys,
-                                                   int r, int KKp, int npts_total, void* __restrict__ Vhi_,
-                                                   void* __restrict__ Vlo_, int eVoff,
-                                                   const LoopState* __restrict__ ls) {
+__global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_rows(
+    Geo g, const float* __restrict__ Zs, const float* __restrict__ Ys, int r, int KKp, int npts_total,
+    void* __restrict__ Vhi_, void* __restrict__ Vlo_, int eVoff, const LoopState* __restrict__ ls) {
   using H = Split<OP>;
-  constexpr bool F16 = OP == 1;
   using T = typename H::T;
+  constexpr bool F16 = OP == 1;
   T* Vhi = reinterpret_cast<T*>(Vhi_);
   T* Vlo = reinterpret_cast<T*>(Vlo_);
   pdl_enter();
-  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = g.n;
+  const int pt = blockIdx.x * PACK_PTS + lane;
   if (pt >= (g.M + 1) * n) return;
   const int j = pt / n, t = pt - j * n;
   if (ls->iter > 0 && j == 0) return;
@@ -456,16 +458,21 @@ __global__ void __launch_bounds__(256) k_pack_rows(Geo g, const float* __restric
   const float* y = Ys + (size_t)j * r * n + t;
   const float fR = (float)g.fR, fK = (float)(1.0 - g.fR);
   const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n) - eVoff) : 1.0f;
-  for (int kc = 0; kc < KKp / 8; ++kc) {
+  for (int kc = w; kc < KKp / 8; kc += PACK_WARPS) {
     __align__(16) T hi[8], lo[8];
+    float x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = kc * 8 + i;
-      float x = 0.f;
-      if (k < r) x = MODE == 1 ? fK * z[(size_t)k * n] + fR * y[(size_t)k * n] : z[(size_t)k * n];
-      x *= scale;
-      hi[i] = H::rn(x);
-      lo[i] = H::rn(x - H::back(hi[i]));
+      x[i] = 0.f;
+      if (k < r) x[i] = MODE == 1 ? fK * __ldcg(z + (size_t)k * n) + fR * __ldcg(y + (size_t)k * n)
+                                  : __ldcg(z + (size_t)k * n);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float v = x[i] * scale;
+      hi[i] = H::rn(v);
+      lo[i] = H::rn(v - H::back(hi[i]));
     }
     store_chunk8<OP>(Vhi, kc, npts_total, pt, hi);
     store_chunk8<OP>(Vlo, kc, npts_total, pt, lo);
