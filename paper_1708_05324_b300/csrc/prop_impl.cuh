@@ -389,7 +389,7 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
         switch (c->NB1) {
 #define GM_TC_S(NB)                                                                                          \
   case NB:                                                                                                   \
-    pdl_launch(k_tc_contract<0, NB, 1, ES>, grid, dim3(192), TcShape<0, NB, ES>::SMEM, s, jb->mapHi, jb->mapLo, \
+    pdl_launch(k_tc_contract<0, NB, 1, ES>, grid, dim3(192), TcShape<0, NB, ES, 1>::SMEM, s, jb->mapHi, jb->mapLo, \
                c->mapWhi, c->mapWlo, a, (const LoopState*)jb->ls);                                           \
     break;
           GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)

@@ -77,19 +77,26 @@ __device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n) {
 
 // ES: operand element bytes, 2 (BF16 / FP16) or 4 (TF32); a core-matrix row
 // of 16 bytes holds EPC = 16 / ES elements.
-template <int N, int NB, int ES = 2>
+// TPW: point tiles per work item, sharing each stage's coupling chunk (two
+// MMAs of M = 128 into two accumulators): 2 for the store epilogue (OUT 1)
+// when two stages still fit, else 1.  NBUF: accumulator buffers in TMEM
+// (2 lets the epilogue drain one work item while the next one's MMAs run).
+template <int N, int NB, int ES = 2, int OUT = 0>
 struct TcShape {
   static constexpr int P = N * (N + 1) / 2;
   static constexpr int NRB = (P + NB - 1) / NB;        // row blocks
   static constexpr int EPC = 16 / ES;                  // elements per core-matrix row
   static constexpr int KSTEPS = TC_KC * ES / 32;       // MMAs of 32 bytes of K per chunk
-  static constexpr int V_BYTES = TC_PTS * TC_KC * ES;  // one of hi / lo
+  static constexpr int V_BYTES = TC_PTS * TC_KC * ES;  // one of hi / lo, one tile
   static constexpr int G_BYTES = NB * TC_KC * ES;
-  static constexpr int STAGE = 2 * (V_BYTES + G_BYTES);
+  static constexpr int TPW = (OUT == 1 && 2 * 2 * (2 * V_BYTES + G_BYTES) <= 200 * 1024) ? 2 : 1;
+  static constexpr int STAGE = 2 * (TPW * V_BYTES + G_BYTES);
   static constexpr int FIT = 200 * 1024 / STAGE;
   static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 6 ? 6 : FIT);
-  static constexpr int TMEM_COLS =
-      2 * NB <= 32 ? 32 : (2 * NB <= 64 ? 64 : (2 * NB <= 128 ? 128 : (2 * NB <= 256 ? 256 : 512)));
+  static constexpr int ACC_COLS = TPW * NB;            // one accumulator buffer
+  static constexpr int NBUF = 2 * ACC_COLS <= 512 ? 2 : 1;
+  static constexpr int COLS = NBUF * ACC_COLS;
+  static constexpr int TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
 };
 
@@ -163,7 +170,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
                                                          const __grid_constant__ CUtensorMap mapGhi,
                                                          const __grid_constant__ CUtensorMap mapGlo, TcArgs a,
                                                          const LoopState* __restrict__ ls) {
-  using S = TcShape<N, NB, ES>;
+  using S = TcShape<N, NB, ES, OUT>;
+  constexpr int TPW = S::TPW, NBUF = S::NBUF;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char* smem = tc_smem_raw + ((1024 - (tc::smem_addr(tc_smem_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t full[S::STAGES], empty[S::STAGES], acc_full[2], acc_empty[2];
@@ -194,16 +202,23 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   const int nrb = OUT == 0 ? S::NRB : a.nrb;
   const int n = a.n;
   const int ntiles = (a.M + 1) * (n / TC_PTS);
+  const int nitems = (ntiles + TPW - 1) / TPW;  // work items of TPW tiles
   const int kchunks = a.KKp / TC_KC;
   // z0 tiles are skipped after the first iteration (their integrand is known)
-  auto live = [&](int tile) { return iter == 0 || tile * TC_PTS >= n; };
+  auto live = [&](int tile) { return tile < ntiles && (iter == 0 || tile * TC_PTS >= n); };
+  auto live_item = [&](int wi) {
+    bool any = false;
+#pragma unroll
+    for (int h = 0; h < TPW; ++h) any = any || live(wi * TPW + h);
+    return any;
+  };
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       int c = 0;
-      for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
-        if (!live(tile)) continue;
+      for (int wi = blockIdx.x; wi < nitems && !*stop; wi += gridDim.x) {
+        if (!live_item(wi)) continue;
         for (int rb = 0; rb < nrb && !*stop; ++rb)
           for (int kc = 0; kc < kchunks; ++kc, ++c) {
             const int s = c % S::STAGES, round = c / S::STAGES;
@@ -215,10 +230,17 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
             unsigned char* st = smem + (size_t)s * S::STAGE;
             tc::mbar_arrive_expect_tx(&full[s], S::STAGE);
             const int kq = kc * (TC_KC / S::EPC);  // K coordinate in core-matrix rows
-            tc::tma_load_3d(st, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
-            tc::tma_load_3d(st + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
-            tc::tma_load_3d(st + 2 * S::V_BYTES, &mapGhi, 0, rb * NB, kq, &full[s]);
-            tc::tma_load_3d(st + 2 * S::V_BYTES + S::G_BYTES, &mapGlo, 0, rb * NB, kq, &full[s]);
+#pragma unroll
+            for (int h = 0; h < TPW; ++h) {
+              // a tile past the end repeats the last one (its result is not stored)
+              const int tile = min(wi * TPW + h, ntiles - 1);
+              unsigned char* sv = st + (size_t)h * 2 * S::V_BYTES;
+              tc::tma_load_3d(sv, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
+              tc::tma_load_3d(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
+            }
+            unsigned char* sg = st + (size_t)TPW * 2 * S::V_BYTES;
+            tc::tma_load_3d(sg, &mapGhi, 0, rb * NB, kq, &full[s]);
+            tc::tma_load_3d(sg + S::G_BYTES, &mapGlo, 0, rb * NB, kq, &full[s]);
           }
       }
     }
@@ -229,17 +251,17 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
           tc::idesc_mma(TC_PTS, NB, ES == 4 ? tc::FMT_TF32 : (a.f16 ? tc::FMT_F16 : tc::FMT_BF16));
       const uint32_t lboV = TC_PTS * 16, lboG = NB * 16, sbo = 128;
       int c = 0, w = 0;
-      for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
-        if (!live(tile)) continue;
+      for (int wi = blockIdx.x; wi < nitems && !*stop; wi += gridDim.x) {
+        if (!live_item(wi)) continue;
         for (int rb = 0; rb < nrb && !*stop; ++rb, ++w) {
-          const int acc = w & 1, use = w >> 1;
+          const int acc = w % NBUF, use = w / NBUF;
           if (use > 0 && !tc::mbar_wait(&acc_empty[acc], (use - 1) & 1)) {
             *stop = 1;
             atomicExch(a.err, 1u);
             break;
           }
           tc::fence_after_sync();
-          const uint32_t d = tmem + (uint32_t)(acc * NB);
+          const uint32_t d0 = tmem + (uint32_t)(acc * S::ACC_COLS);
           for (int kc = 0; kc < kchunks; ++kc, ++c) {
             const int s = c % S::STAGES, round = c / S::STAGES;
             if (!tc::mbar_wait(&full[s], round & 1)) {
@@ -249,15 +271,22 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
             }
             tc::fence_after_sync();
             const uint32_t base = tc::smem_addr(smem + (size_t)s * S::STAGE);
-            const uint32_t vH = base, vL = base + S::V_BYTES, gH = base + 2 * S::V_BYTES, gL = gH + S::G_BYTES;
+            const uint32_t gH = base + TPW * 2 * S::V_BYTES, gL = gH + S::G_BYTES;
 #pragma unroll
             for (int kk = 0; kk < S::KSTEPS; ++kk) {
               // 32 bytes of K per MMA: two core matrices along K
               const uint32_t oV = (uint32_t)kk * 2 * lboV, oG = (uint32_t)kk * 2 * lboG;
-              tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
-                               (kc > 0 || kk > 0) ? 1u : 0u);
-              tc::mma<ES == 4>(d, tc::smem_desc(vL + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc, 1u);
-              tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gL + oG, lboG, sbo), idesc, 1u);
+#pragma unroll
+              for (int h = 0; h < TPW; ++h) {
+                const uint32_t d = d0 + (uint32_t)(h * NB);
+                const uint32_t vH = base + h * 2 * S::V_BYTES, vL = vH + S::V_BYTES;
+                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
+                                 (kc > 0 || kk > 0) ? 1u : 0u);
+                tc::mma<ES == 4>(d, tc::smem_desc(vL + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
+                                 1u);
+                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gL + oG, lboG, sbo), idesc,
+                                 1u);
+              }
             }
             tc::mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
           }
@@ -275,9 +304,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
     const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n) - a.eVoff + a.eG)) : 1.0f;
     int w = 0;
     constexpr int NA = N > 0 ? N : 1;
-    for (int tile = blockIdx.x; tile < ntiles && !*stop; tile += gridDim.x) {
-      if (!live(tile)) continue;
-      const int pt = tile * TC_PTS + row_in_tile;
+    for (int wi = blockIdx.x; wi < nitems && !*stop; wi += gridDim.x) {
+      if (!live_item(wi)) continue;
+      // the l-sum epilogue has one tile per work item
+      const int pt = wi * TPW * TC_PTS + row_in_tile;
       const int j = pt / n, t = pt - j * n;
       float2 av[NA], nl[NA];
       if (OUT == 0) {
@@ -290,23 +320,30 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
         }
       }
       for (int rb = 0; rb < nrb; ++rb, ++w) {
-        const int acc = w & 1, use = w >> 1;
+        const int acc = w % NBUF, use = w / NBUF;
         if (!tc::mbar_wait(&acc_full[acc], use & 1)) {
           *stop = 1;
           atomicExch(a.err, 1u);
           break;
         }
         tc::fence_after_sync();
-        const uint32_t taddr = tmem + lane_off + (uint32_t)(acc * NB);
+        const uint32_t taddr = tmem + lane_off + (uint32_t)(acc * S::ACC_COLS);
         if (OUT == 1) {
-          float* z = a.Zout + (size_t)j * a.zrows * n + t;
-          for (int c0 = 0; c0 < NB; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(taddr + c0, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int r = rb * NB + c0 + i;
-              if (r < a.zrows) z[(size_t)r * n] = v[i] * inv;
+          for (int h = 0; h < TPW; ++h) {
+            const int tile = wi * TPW + h;
+            if (!live(tile)) continue;  // (every thread of the warp skips alike)
+            const int pth = tile * TC_PTS + row_in_tile;
+            const int jh = pth / n, th = pth - jh * n;
+            float* z = a.Zout + (size_t)jh * a.zrows * n + th;
+            for (int c0 = 0; c0 < NB; c0 += 16) {
+              float v[16];
+              tc::tmem_ld16(taddr + (uint32_t)(h * NB) + c0, v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int r = rb * NB + c0 + i;
+                if (r < a.zrows) z[(size_t)r * n] = v[i] * inv;
+              }
             }
           }
         } else {
