@@ -636,9 +636,9 @@ static void free_job(gm_job* jb) {
   delete jb;
 }
 
-// TMA maps of the blocked hi/lo operand: dims {8, (M+1) n, KKp/8}, box
-// {8, 128 points, KKp/8}; the encode function comes from the driver at run
-// time (no link dependency on libcuda).
+// TMA maps of the blocked hi/lo operands ([K/EPC][rows][EPC], one K chunk
+// per box, see tc_map); the encode function comes from the CUDA driver at
+// run time (no link dependency on libcuda).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

@@ -410,9 +410,9 @@ def step_index_problem(name, N, Nt, dt, kind, fwhm, energy, L, dz, M, tol, seed,
 
 
 def workload(name: str, **over) -> Problem:
-    """The five benchmark configurations (C1..C4 here; C5 requests are made by
-    serving_requests).  Keyword overrides change any grin_problem argument
-    (e.g. a shorter fiber L for a prefix run)."""
+    """The named workloads C1..C4, each described by its sizes below (the
+    served mix C5 comes from serving_requests).  Keyword overrides change any
+    grin_problem argument (e.g. a shorter fiber L for a prefix run)."""
     if name == "C1":  # FP64 Kerr only, N=3, Nt=2^10 over 5 ps
         kw = dict(N=3, Nt=1024, dt=5e-12 / 1024, kind="sech", fwhm=100e-15, energy=10e-9,
                   L=0.05, dz=0.5e-3, M=5, tol=1e-12, seed=1, fR=0.0)
