@@ -310,8 +310,8 @@ def run_serving(B, dev, count=32, max_substeps=2000, inflight=8, load=0.9, seed=
     srv.close()
     for c in ctxs.values():
         c.close()
-    # serial plain FP64 MPA on the same requests (FP64 iterates are built for Nt <= 8192)
-    sub = [r for r in reqs if r["Nt"] <= 8192][:8]
+    # serial plain FP64 MPA on the first 8 of the same requests
+    sub = reqs[:8]
     t64 = 0.0
     for r in sub:
         prob = I.grin_problem("serve", N=r["N"], Nt=r["Nt"], dt=r["dt"], kind="gaussian", fwhm=200e-15,
@@ -451,12 +451,14 @@ def main():
         return
 
     # error of this path against the FP64 GPU path on a prefix: 5 mm (200 long
-    # steps) of the 6-mode run, one long step of the 42-mode run; the 15-mode
-    # run has 2^14-point transforms, which the FP64 path does not build
+    # steps) of the 6-mode run, 2 mm (8 long steps) of the 15-mode run, one
+    # long step of the 42-mode run
     err, fp64_rate, err_prefix = None, None, None
-    if args.workload in ("C2", "C4"):
-        pre = I.workload("C2", L=5e-3) if args.workload == "C2" else problem(L=16 * 37.5e-6, name="C4")
-        err_prefix = "5 mm" if args.workload == "C2" else "one long step (0.6 mm)"
+    if args.workload in ("C2", "C3", "C4"):
+        pre = {"C2": lambda: I.workload("C2", L=5e-3),
+               "C3": lambda: problem(L=2e-3, name="C3"),
+               "C4": lambda: problem(L=16 * 37.5e-6, name="C4")}[args.workload]()
+        err_prefix = {"C2": "5 mm", "C3": "2 mm (8 long steps)", "C4": "one long step (0.6 mm)"}[args.workload]
         c64 = B.Context.from_problem(pre, precision="fp64", device=dev)
         ref64, st64, _ = c64.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
         c64.close()

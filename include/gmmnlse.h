@@ -68,7 +68,9 @@ typedef enum gmmnlse_precision {
 typedef struct gmmnlse_params {
     int N;               /* number of modes, 1 <= N <= 64 */
     int Nt;              /* time samples: power of two, 16 <= Nt <= 16384
-                            (FP64: Nt <= 8192) */
+                            (FP64 at 16384: every transform of the iterates
+                            over a 4-block cluster; not on the no-alloc
+                            entry point) */
     double dt;           /* sample spacing [s] */
     double lambda0;      /* centre wavelength [m] (omega0 = 2 pi c / lambda0) */
     double n2;           /* nonlinear index [m^2/W] */
@@ -173,6 +175,8 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
  *         prm.io_device says); Aout the same for the output.
  *   L, dz, M, tol, st as for gmmnlse_propagate (st->ms is 0).
  *
+ * An FP64 context with Nt = 16384 is rejected with GMMNLSE_E_UNSUPPORTED
+ * (this entry point has one-block transforms only).
  * A problem whose workspace does not fit in the 32 MiB array is rejected with
  * GMMNLSE_E_NOMEM before any work, and gmmnlse_last_error() says so.  (For
  * FP32, N = 6, Nt = 8192, M = 10 with Raman just fits.)  The first call on a

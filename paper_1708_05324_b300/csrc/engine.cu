@@ -378,7 +378,6 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     return GMMNLSE_E_INVALID;
   if (!symmetric_enough(SK, N) || (SR && !symmetric_enough(SR, N))) return GMMNLSE_E_UNSUPPORTED;
   const bool fp64 = prm->precision == GMMNLSE_FP64;
-  if (fp64 && n > 8192) return GMMNLSE_E_UNSUPPORTED;
   int rc = set_device(prm->device);
   if (rc) return rc;
 

@@ -198,15 +198,16 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
 }
 
 // K2 with the two transforms of a pair spread over an S-block cluster
-// (fft_cluster): block s loads the pair products of its time slice, the
-// spectrum slice it ends up holding is multiplied by H in place, and the
-// inverse returns its time slice of h_R * U.  grid (S ceil(K/2), M+1).
-template <typename R, int EPT, int S>
+// (fft_cluster): block s loads the rows of its time slice (SRC 0: the pair
+// products of A; SRC 1: rows of Zs, cnt per substep), the spectrum slice it
+// ends up holding is multiplied by H in place, and the inverse returns its
+// time slice of h_R * U.  grid (S ceil(cnt/2), M+1).
+template <typename R, int EPT, int S, int SRC>
 __global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Y,
                                                         const cplx<R>* __restrict__ H,
                                                         const cplx<R>* __restrict__ tw,
-                                                        const int2* __restrict__ pairs,
-                                                        const LoopState* __restrict__ ls) {
+                                                        const int2* __restrict__ pairs, const R* __restrict__ Zs,
+                                                        int cnt, const LoopState* __restrict__ ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
@@ -216,17 +217,21 @@ __global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __
   const int s = (int)(blockIdx.x % S);
   cplx<R>* xbuf = sm + fft_smem_elems(np);
   const int k1 = 2 * (blockIdx.x / S), k2 = k1 + 1;
-  const bool has2 = k2 < g.K;
-  const int2 mn1 = pairs[k1];
-  const int2 mn2 = has2 ? pairs[k2] : mn1;
-  const cplx<R>* a = A + (size_t)j * g.N * n;
+  const bool has2 = k2 < cnt;
   auto load = [&](int t) {
-    return mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+    if (SRC == 0) {
+      const int2 mn1 = pairs[k1];
+      const int2 mn2 = has2 ? pairs[k2] : mn1;
+      const cplx<R>* a = A + (size_t)j * g.N * n;
+      return mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+    }
+    const R* z1 = Zs + ((size_t)j * cnt + k1) * n;
+    return mk<R>(z1[t], has2 ? z1[n + t] : (R)0);
   };
   auto spectrum = [&](int q, cplx<R> x) { xbuf[q - s * np] = cmul<R>(x, H[q]); };
   fft_cluster<R, -1, EPT, S>(xbuf, sm, n, tw, load, spectrum);
   auto own = [&](int q) { return xbuf[q - s * np]; };
-  R* y1 = Y + ((size_t)j * g.K + k1) * n;
+  R* y1 = Y + ((size_t)j * cnt + k1) * n;
   auto store = [&](int t, cplx<R> y) {
     y1[t] = y.x;
     if (has2) y1[n + t] = y.y;

@@ -270,6 +270,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
 extern "C" int gmmnlse_propagate_noalloc(gmmnlse_ctx* c, const double* A0, double L, double dz, int M, double tol,
                                          double* Aout, gmmnlse_stats* st) {
   if (!c || !A0 || !Aout) return GMMNLSE_E_INVALID;
+  if (c->fp64 && c->n > 8192) return GMMNLSE_E_UNSUPPORTED;  // needs the cluster transforms
   long nf;
   int mr;
   int rc = gm_schedule(L, dz, M, &nf, &mr);

@@ -112,8 +112,10 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 32, 0>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 16, 1>, A, sm));
   CK(cudaFuncSetAttribute(k_pairs_raman<R, 32, 1>, A, sm));
-  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 2>, A, sm));
-  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 4>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 2, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 4, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 2, 1>, A, sm));
+  CK(cudaFuncSetAttribute(k_pairs_raman_cl<R, 16, 4, 1>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 0, 0>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 0, 0>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 2, 0, 0>, A, sm));
@@ -169,7 +171,11 @@ static inline bool cluster_fft() {
   return v && v[0] == '1';
 }
 
+// An FP64 transform above 8192 points does not fit one block's shared
+// memory: it always takes a 4-block cluster (n/4 points per block).
+template <typename R>
 static inline int split_for(int transforms, int n) {
+  if (sizeof(R) == 8 && n > 8192) return 4;
   if (!cluster_fft()) return 1;
   if (transforms <= 74 && n >= 128) return 4;
   if (transforms <= 148 && n >= 64) return 2;
@@ -224,7 +230,7 @@ template <typename R>
 static void launch_k1(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
-  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = fft_ept<R>(np, N * S * (g.M + 1));
+  const int S = split_for<R>(N * (g.M + 1), n), np = n / S, ept = S > 1 ? 16 : fft_ept<R>(np, N * (g.M + 1));
   const dim3 grid(N * S, g.M + 1);
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
@@ -244,10 +250,11 @@ static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n;
   const int pp = (c->K + 1) / 2;
-  const int S = split_for(pp * (g.M + 1), n);
+  const int S = split_for<R>(pp * (g.M + 1), n);
   auto args = [&](auto kern, dim3 grid, int threads, size_t sm, int cl) {
     pdl_launch_cl(kern, grid, dim3(threads), sm, s, cl, g, (const cplx<R>*)jb->A, (R*)jb->V,
-                  (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const LoopState*)jb->ls);
+                  (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)nullptr, c->K,
+                  (const LoopState*)jb->ls);
   };
   auto one = [&](auto kern, int ept) {
     pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
@@ -256,8 +263,8 @@ static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
   };
   if (S > 1) {
     const int np = n / S;
-    if (S == 2) args(k_pairs_raman_cl<R, 16, 2>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
-    else args(k_pairs_raman_cl<R, 16, 4>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
+    if (S == 2) args(k_pairs_raman_cl<R, 16, 2, 0>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
+    else args(k_pairs_raman_cl<R, 16, 4, 0>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
   } else if (fft_ept<R>(n, pp * (g.M + 1)) == 32) {
     one(k_pairs_raman<R, 32, 0>, 32);
   } else {
@@ -270,7 +277,7 @@ template <typename R>
 static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
-  const int S = split_for(N * (g.M + 1), n), np = n / S, ept = fft_ept<R>(np, N * S * (g.M + 1));
+  const int S = split_for<R>(N * (g.M + 1), n), np = n / S, ept = S > 1 ? 16 : fft_ept<R>(np, N * (g.M + 1));
   const dim3 grid(N * S, g.M + 1);
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
@@ -428,8 +435,20 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
                (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)jb->Z, c->r,
                (const LoopState*)jb->ls);
   };
-  if (fft_ept<R>(n, pp * (g.M + 1)) == 32) one(k_pairs_raman<R, 32, 1>, 32);
-  else one(k_pairs_raman<R, 16, 1>, 16);
+  const int S = split_for<R>(pp * (g.M + 1), n);
+  if (S > 1) {
+    auto cl = [&](auto kern) {
+      pdl_launch_cl(kern, dim3(S * pp, g.M + 1), dim3(n / S / 16), fft_cluster_smem<R>(n, S), s, S, g,
+                    (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
+                    (const R*)jb->Z, c->r, (const LoopState*)jb->ls);
+    };
+    if (S == 2) cl(k_pairs_raman_cl<R, 16, 2, 1>);
+    else cl(k_pairs_raman_cl<R, 16, 4, 1>);
+  } else if (fft_ept<R>(n, pp * (g.M + 1)) == 32) {
+    one(k_pairs_raman<R, 32, 1>, 32);
+  } else {
+    one(k_pairs_raman<R, 16, 1>, 16);
+  }
 }
 
 template <typename R>

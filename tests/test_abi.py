@@ -83,9 +83,6 @@ def test_create_validates_on_the_host_before_any_cuda_call():
     asym = S.copy()
     asym[0, 0, 0, 1] += 0.1 * abs(S).max()
     assert _create(good, beta, asym)[0] == B.E_UNSUPPORTED
-    # FP64 beyond one block's shared memory
-    big = B.Params(N, 16384, 1e-15, 1030e-9, 2.3e-20, 1, B.FP64, 0, 0, 0, None, 0)
-    assert _create(big, np.zeros((N, 16384)), S)[0] == B.E_UNSUPPORTED
 
 
 def test_propagate_and_server_reject_null_handles(lib):

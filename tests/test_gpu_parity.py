@@ -141,8 +141,7 @@ def test_ragged_last_long_step_and_M1():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_largest_transform_2_14(precision, fft_variant):
-    if precision == "fp64":
-        pytest.skip("FP64 iterates are built for Nt <= 8192")
+    """Nt = 2^14; in FP64 every transform of the iterates spans a 4-block cluster."""
     prob = I.grin_problem("big", N=2, Nt=16384, dt=20e-12 / 16384, kind="gaussian", fwhm=300e-15,
                           energy=50e-9, L=5e-4, dz=2.5e-5, M=10, tol=1e-13, seed=3, fR=0.18, s_from="gh")
     ref, _ = oracle_run(prob)
@@ -369,6 +368,33 @@ def test_low_rank_coupling_matches_dense(precision, monkeypatch):
     assert rel(low, ref) < bar
     assert rel(dense, ref) < bar
     assert rel(low, dense) < (1e-11 if precision == "fp64" else 1e-5)
+
+
+@functools.lru_cache(maxsize=None)
+def fifteen_modes_2_14():
+    prob = I.grin_problem("m", N=15, Nt=16384, dt=2e-12 / 16384, kind="gaussian", fwhm=150e-15,
+                          energy=20e-9, L=5e-4, dz=1e-4, M=5, tol=1e-13, seed=11, fR=0.18, s_from="gh")
+    ref, sref = oracle_run(prob)
+    return prob, ref, sref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_15_modes_2_14_low_rank_and_dense(precision, fft_variant, monkeypatch):
+    """One long step of the 15-mode fiber at Nt = 2^14: the Raman convolution of
+    the low-rank rows (h_R * Z) and of the pair products, each through the
+    cluster transforms in FP64 (and in FP32 under the cluster variant)."""
+    prob, ref, sref = fifteen_modes_2_14()
+    tol = 1e-13 if precision == "fp64" else 1e-9
+    low, st_low, rc = gpu_run(prob, precision, tol=tol)
+    assert rc == B.OK
+    assert st_low["coupling_rank"] == 45
+    monkeypatch.setenv("GMMNLSE_DENSE", "1")
+    dense, st_dense, rc = gpu_run(prob, precision, tol=tol)
+    assert rc == B.OK
+    assert st_dense["coupling_rank"] == 120
+    assert rel(low, ref) < TOL[precision]
+    assert rel(dense, ref) < TOL[precision]
+    assert st_low["long_steps"] == st_dense["long_steps"] == len(sref["iters"]) == 1
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])

@@ -64,3 +64,18 @@ def test_noalloc_rejects_a_workspace_beyond_the_static_array():
     assert rc == B.E_NOMEM
     assert b"32 MiB" in lib.gmmnlse_last_error()
     ctx.close()
+
+
+def test_noalloc_rejects_fp64_2_14():
+    """The no-alloc entry point has one-block transforms only: FP64 at 2^14 points is refused."""
+    import torch
+    lib = B.load()
+    prob = I.grin_problem("big", N=2, Nt=16384, dt=20e-12 / 16384, kind="gaussian", fwhm=300e-15,
+                          energy=50e-9, L=5e-5, dz=2.5e-5, M=2, tol=1e-10, seed=3, fR=0.18, s_from="gh")
+    ctx = B.Context.from_problem(prob, precision="fp64", io_device=True)
+    a0 = torch.from_numpy(prob.A0).cuda()
+    out = torch.empty_like(a0)
+    rc = lib.gmmnlse_propagate_noalloc(ctx.handle, a0.data_ptr(), prob.L, prob.dz, prob.M, prob.tol,
+                                       out.data_ptr(), None)
+    assert rc == B.E_UNSUPPORTED
+    ctx.close()
