@@ -79,7 +79,7 @@ struct gmmnlse_ctx {
   bool f16 = false;              // tensor-core operands FP16 (MIXED_FP16), else BF16
   bool tf32 = false;             // tensor-core operands TF32 (MIXED_TF32), 4-byte elements
   int eG = 0;                    // FP16: G scaled by 2^eG
-  __nv_bfloat16* Ghi = nullptr;  // [KKp/EPC][tc_rows][EPC]: 16-bit (EPC 8) or TF32 words (EPC 4)
+  __nv_bfloat16* Ghi = nullptr;  // [tc_rows/8][KKp/EPC][8][EPC]: 16-bit (EPC 8) or TF32 words (EPC 4)
   __nv_bfloat16* Glo = nullptr;
   CUtensorMap mapGhi, mapGlo;
   void* Gt = nullptr;            // [KKt][Pt] R: G transposed, zero-padded (N > 8, CUDA cores)

@@ -256,16 +256,21 @@ static float tf32_rna(float x) {
 }
 
 // A row-major [rows][cols] matrix scaled by 2^e, split into hi + lo in the
-// blocked layout [cols_pad/EPC][rows_pad][EPC] (K-major core matrices of
-// 16-byte rows) read by the tensor-core GEMM, zero padding: TF32 words
-// (EPC 4) when tf32, else 16-bit FP16 (f16) or BF16 (EPC 8).
+// row-grouped layout [rows_pad/8][cols_pad/EPC][8][EPC] (K-major core
+// matrices of 8 rows x 16 bytes, the K chunks of one 8-row group adjacent)
+// read by the tensor-core GEMM as its coupling operand, zero padding: TF32
+// words (EPC 4) when tf32, else 16-bit FP16 (f16) or BF16 (EPC 8).
+static inline size_t row_grouped(int r, int k, int cols_pad, int epc) {
+  return (((size_t)(r / 8) * (cols_pad / epc) + k / epc) * 8 + r % 8) * epc + k % epc;
+}
+
 static int upload_hilo_tf32(const std::vector<double>& m, int rows, int cols, int rows_pad, int cols_pad,
                             __nv_bfloat16** hi, __nv_bfloat16** lo) {
   std::vector<float> gh((size_t)rows_pad * cols_pad), gl((size_t)rows_pad * cols_pad);
   for (int r = 0; r < rows_pad; ++r)
     for (int k = 0; k < cols_pad; ++k) {
       const float x = (r < rows && k < cols) ? (float)m[(size_t)r * cols + k] : 0.f;
-      const size_t o = ((size_t)(k / 4) * rows_pad + r) * 4 + (k % 4);
+      const size_t o = row_grouped(r, k, cols_pad, 4);
       gh[o] = tf32_rna(x);
       gl[o] = tf32_rna(x - gh[o]);
     }
@@ -283,7 +288,7 @@ static int upload_hilo(const std::vector<double>& m, int rows, int cols, int row
   for (int r = 0; r < rows_pad; ++r)
     for (int k = 0; k < cols_pad; ++k) {
       const float x = (r < rows && k < cols) ? (float)std::ldexp(m[(size_t)r * cols + k], e) : 0.f;
-      const size_t o = ((size_t)(k / 8) * rows_pad + r) * 8 + (k % 8);
+      const size_t o = row_grouped(r, k, cols_pad, 8);
       if (f16) {
         const __half h = __float2half_rn(x), l = __float2half_rn(x - __half2float(h));
         std::memcpy(&gh[o], &h, 2);
@@ -635,9 +640,10 @@ static void free_job(gm_job* jb) {
   delete jb;
 }
 
-// TMA maps of the blocked hi/lo operands ([K/EPC][rows][EPC], one K chunk
-// per box, see tc_map); the encode function comes from the CUDA driver at
-// run time (no link dependency on libcuda).
+// TMA maps of the blocked hi/lo operands (V: [K/EPC][points][EPC], see
+// tc_map; coupling: row-grouped, see tc_map_rows), one K chunk per box; the
+// encode function comes from the CUDA driver at run time (no link dependency
+// on libcuda).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -683,15 +689,40 @@ static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int bo
   return GMMNLSE_OK;
 }
 
+// Map of a row-grouped [rows/8][KKp/EPC][8][EPC] coupling operand; box = one
+// K chunk of NB / CL rows (one CTA's share of a row block of NB rows in a
+// cluster of CL = tc_cluster(NB)).
+static int tc_map_rows(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int NB, bool f16, bool tf32) {
+  EncodeTiledFn enc;
+  const int rc = tc_encoder(&enc);
+  if (rc) return rc;
+  const int epc = tf32 ? 4 : 8;
+  const cuuint64_t kq = (cuuint64_t)(KKp / epc);
+  const cuuint64_t dims[4] = {(cuuint64_t)epc, 8, kq, rows / 8};
+  const cuuint64_t strides[3] = {16, 128, kq * 128};
+  const cuuint32_t box[4] = {(cuuint32_t)epc, 8, (cuuint32_t)(TC_KC / epc), (cuuint32_t)(NB / 8 / tc_cluster(NB))};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const CUresult r = enc(map, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    gm_set_last_error_text("cuTensorMapEncodeTiled rejected the coupling operand layout");
+    return GMMNLSE_E_CUDA;
+  }
+  return GMMNLSE_OK;
+}
+
 int gm_make_g_maps(gmmnlse_ctx* c) {
   const int NB = tc_row_block(c->P);
-  int rc = tc_map(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
-  if (!rc) rc = tc_map(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
+  int rc = tc_map_rows(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
+  if (!rc) rc = tc_map_rows(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
   if (!rc && c->lr) {
-    rc = tc_map(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
-    if (!rc) rc = tc_map(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
-    if (!rc) rc = tc_map(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
-    if (!rc) rc = tc_map(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
+    rc = tc_map_rows(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
+    if (!rc) rc = tc_map_rows(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
+    if (!rc) rc = tc_map_rows(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
+    if (!rc) rc = tc_map_rows(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
   }
   return rc;
 }

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "../../include/gmmnlse.h"
@@ -290,6 +291,42 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_integrand<R, 16, 4>);
 }
 
+// CTAs of a tensor-core GEMM launch: CL x the clusters resident at once
+// (cudaOccupancyMaxActiveClusters, once per kernel), at most one cluster per
+// work item of CL x TPW point tiles.  A grid of more clusters than fit would
+// run the surplus as a second wave.
+static int tc_grid(const void* kern, size_t smem, int cl, int tpw, int ntiles) {
+  static std::mutex mu;
+  static std::map<const void*, int> resident;
+  int maxc = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = resident.find(kern);
+    if (it != resident.end()) {
+      maxc = it->second;
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(148 / cl * cl);
+      cfg.blockDim = dim3(192);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = (unsigned)cl;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) != cudaSuccess || maxc <= 0) {
+        (void)cudaGetLastError();
+        maxc = 148 / cl / 2;  // a safe guess: half the SMs
+      }
+      resident[kern] = maxc;
+    }
+  }
+  const int items = (ntiles + cl * tpw - 1) / (cl * tpw);
+  return cl * std::max(1, std::min(items, maxc));
+}
+
 // The tcgen05 GEMM with the l-sum epilogue: V operand maps mV*, coupling
 // operand maps mG*, over the mode count of the context; ES = 2 (BF16 / FP16)
 // or 4 (TF32).
@@ -298,15 +335,16 @@ static void launch_tc_lsum_es(gm_job* jb, const Geo& g, cudaStream_t s, const CU
                               const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
                               const TcArgs& a) {
   gmmnlse_ctx* c = jb->ctx;
-  const int pts = (g.M + 1) * c->n;
-  const dim3 grid(std::min(pts / TC_PTS, 148));
+  const int ntiles = (g.M + 1) * c->n / TC_PTS;
   switch (c->N) {
-#define GM_TC_CASE(NN)                                                                                          \
-  case NN: {                                                                                                    \
-    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                         \
-    pdl_launch(k_tc_contract<NN, NB, 0, ES>, grid, dim3(192), TcShape<NN, NB, ES>::SMEM, s, mVhi, mVlo, mGhi, mGlo, \
-               a, (const LoopState*)jb->ls);                                                                    \
-    break;                                                                                                      \
+#define GM_TC_CASE(NN)                                                                                           \
+  case NN: {                                                                                                     \
+    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                          \
+    using Sh = TcShape<NN, NB, ES>;                                                                              \
+    auto kern = k_tc_contract<NN, NB, 0, ES>;                                                                    \
+    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles));                              \
+    pdl_launch_cl(kern, grid, dim3(192), Sh::SMEM, s, Sh::CL, mVhi, mVlo, mGhi, mGlo, a, (const LoopState*)jb->ls); \
+    break;                                                                                                       \
   }
     GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
     GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
@@ -390,15 +428,19 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
       a.nrb = c->r_rows / c->NB1;
       a.Zout = (float*)jb->Z;
       a.zrows = c->r;
-      const dim3 grid((unsigned)std::min<size_t>(pts / TC_PTS, 148));
+      const int ntiles = (int)(pts / TC_PTS);
       auto store = [&](auto es) {
         constexpr int ES = decltype(es)::value;
         switch (c->NB1) {
-#define GM_TC_S(NB)                                                                                          \
-  case NB:                                                                                                   \
-    pdl_launch(k_tc_contract<0, NB, 1, ES>, grid, dim3(192), TcShape<0, NB, ES, 1>::SMEM, s, jb->mapHi, jb->mapLo, \
-               c->mapWhi, c->mapWlo, a, (const LoopState*)jb->ls);                                           \
-    break;
+#define GM_TC_S(NB)                                                                                           \
+  case NB: {                                                                                                  \
+    using Sh = TcShape<0, NB, ES, 1>;                                                                         \
+    auto kern = k_tc_contract<0, NB, 1, ES>;                                                                  \
+    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles));                           \
+    pdl_launch_cl(kern, grid, dim3(192), Sh::SMEM, s, Sh::CL, jb->mapHi, jb->mapLo, c->mapWhi, c->mapWlo, a,  \
+                  (const LoopState*)jb->ls);                                                                  \
+    break;                                                                                                    \
+  }
           GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
           GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
 #undef GM_TC_S

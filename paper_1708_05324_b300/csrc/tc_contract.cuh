@@ -28,10 +28,21 @@
 // while the MMAs of the next work item run.  A work item is (point tile, row
 // block); NL of a tile is written after its last row block.
 //
+// Clusters of CL CTAs (CL = 2 for row blocks of 64 rows and more) work on
+// CL point tiles at once with the same row-block and K-chunk sequence: each
+// CTA loads its own V tile and 1/CL of the coupling chunk, multicast into
+// every CTA of the cluster, so the coupling operand (the larger one, NB rows
+// against 128 points) crosses L2 once per CL tiles.  A stage is released
+// when the MMAs of every CTA of the cluster have read it (the MMA commit
+// arrives on the stage's barrier in each CTA).
+//
 // Operand layout (both K-major, no swizzle): core matrices of 8 rows x 8
-// elements (16 bytes), stored [k/8][row][8]; in shared memory a K chunk of R
-// rows is [4][R][8], so core matrices adjacent along K are R*16 bytes apart
-// (LBO) and along the rows 128 bytes (SBO).
+// elements (16 bytes).  V is stored [k/8][point][8]; in shared memory a K
+// chunk of 128 points is [4][128][8], so core matrices adjacent along K are
+// 128*16 bytes apart (LBO) and along the points 128 bytes (SBO).  The
+// coupling operand is stored row-grouped, [row/8][k/8][8][8]; a K chunk of
+// NB rows is [NB/8][4][8][8] in shared memory (LBO 128 bytes, SBO 512), and
+// the share of one CTA of a cluster (NB/CL rows) is a contiguous part of it.
 //
 // Every mbarrier wait is bounded; on a timeout the kernel records an error
 // in *err and every role stops issuing work.
@@ -64,6 +75,10 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
+
+// CTAs per cluster of the GEMM with row blocks of NB rows: 2 from 64 rows
+// (NB is a multiple of 16, so each CTA's share is whole 8-row groups).
+__host__ __device__ constexpr int tc_cluster(int NB) { return NB >= 64 ? 2 : 1; }
 
 // FP16 scale exponent of V: 2^eV (2 x the bound on |V|) < 2^14; the bound
 // is (1/Nt) sum_w |psi0|^2, summed at the start of the propagation.
@@ -98,6 +113,8 @@ struct TcShape {
   static constexpr int COLS = NBUF * ACC_COLS;
   static constexpr int TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
+  static constexpr int CL = tc_cluster(NB);           // CTAs sharing each coupling chunk
+  static constexpr int G_SHARE = G_BYTES / CL;         // one CTA's share (hi or lo)
 };
 
 // Row r of the reduced coupling matrix is the pair (p, l), p <= l, in the
@@ -171,7 +188,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
                                                          const __grid_constant__ CUtensorMap mapGlo, TcArgs a,
                                                          const LoopState* __restrict__ ls) {
   using S = TcShape<N, NB, ES, OUT>;
-  constexpr int TPW = S::TPW, NBUF = S::NBUF;
+  constexpr int TPW = S::TPW, NBUF = S::NBUF, CL = S::CL;
+  constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1);
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char* smem = tc_smem_raw + ((1024 - (tc::smem_addr(tc_smem_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t full[S::STAGES], empty[S::STAGES], acc_full[2], acc_empty[2];
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   if (tid == 0) {
     for (int s = 0; s < S::STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], CL);  // released by the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
@@ -195,21 +213,26 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   if (warp == 1) tc::tmem_alloc(&tmem_base, S::TMEM_COLS);
   tc::fence_before_sync();
   __syncthreads();
+  if (CL > 1) tc::cluster_sync();  // the peers' barriers exist before any multicast
   tc::fence_after_sync();
   pdl_enter();
   const uint32_t tmem = tmem_base;
   const int iter = ls->iter;
   const int nrb = OUT == 0 ? S::NRB : a.nrb;
   const int n = a.n;
+  const int rank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
+  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
   const int ntiles = (a.M + 1) * (n / TC_PTS);
-  const int nitems = (ntiles + TPW - 1) / TPW;  // work items of TPW tiles
+  const int nitems = (ntiles + TPW * CL - 1) / (TPW * CL);  // work items of CL x TPW tiles
   const int kchunks = a.KKp / TC_KC;
+  // this CTA's tiles of work item wi: (wi CL + rank) TPW + h
+  auto tile_of = [&](int wi, int h) { return (wi * CL + rank) * TPW + h; };
   // z0 tiles are skipped after the first iteration (their integrand is known)
   auto live = [&](int tile) { return tile < ntiles && (iter == 0 || tile * TC_PTS >= n); };
+  // an item runs in every CTA of the cluster if any of its tiles is live
   auto live_item = [&](int wi) {
     bool any = false;
-#pragma unroll
-    for (int h = 0; h < TPW; ++h) any = any || live(wi * TPW + h);
+    for (int h = 0; h < TPW * CL; ++h) any = any || live(wi * TPW * CL + h);
     return any;
   };
 
@@ -217,7 +240,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       int c = 0;
-      for (int wi = blockIdx.x; wi < nitems && !*stop; wi += gridDim.x) {
+      for (int wi = cid; wi < nitems && !*stop; wi += ncl) {
         if (!live_item(wi)) continue;
         for (int rb = 0; rb < nrb && !*stop; ++rb)
           for (int kc = 0; kc < kchunks; ++kc, ++c) {
@@ -233,25 +256,41 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
 #pragma unroll
             for (int h = 0; h < TPW; ++h) {
               // a tile past the end repeats the last one (its result is not stored)
-              const int tile = min(wi * TPW + h, ntiles - 1);
+              const int tile = min(tile_of(wi, h), ntiles - 1);
               unsigned char* sv = st + (size_t)h * 2 * S::V_BYTES;
               tc::tma_load_3d(sv, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
               tc::tma_load_3d(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
             }
-            unsigned char* sg = st + (size_t)TPW * 2 * S::V_BYTES;
-            tc::tma_load_3d(sg, &mapGhi, 0, rb * NB, kq, &full[s]);
-            tc::tma_load_3d(sg + S::G_BYTES, &mapGlo, 0, rb * NB, kq, &full[s]);
+            // this CTA's share of the coupling chunk: 8-row groups g0 .. g0 + NB/(8 CL) - 1
+            unsigned char* sg = st + (size_t)TPW * 2 * S::V_BYTES + (size_t)rank * S::G_SHARE;
+            const int g0 = rb * (NB / 8) + rank * (NB / 8 / CL);
+            if (CL == 1) {
+              tc::tma_load_4d(sg, &mapGhi, 0, 0, kq, g0, &full[s]);
+              tc::tma_load_4d(sg + S::G_BYTES, &mapGlo, 0, 0, kq, g0, &full[s]);
+            } else {
+              tc::tma_load_4d_mc(sg, &mapGhi, 0, 0, kq, g0, &full[s], CL_MASK);
+              tc::tma_load_4d_mc(sg + S::G_BYTES, &mapGlo, 0, 0, kq, g0, &full[s], CL_MASK);
+            }
           }
       }
+      // wait for the release of the last stages by every CTA of the cluster:
+      // after that no peer arrives on this CTA's barriers
+      if (CL > 1)
+        for (int i = c > S::STAGES ? c - S::STAGES : 0; i < c; ++i)
+          if (!tc::mbar_wait(&empty[i % S::STAGES], (i / S::STAGES) & 1)) {
+            atomicExch(a.err, 1u);
+            break;
+          }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc =
           tc::idesc_mma(TC_PTS, NB, ES == 4 ? tc::FMT_TF32 : (a.f16 ? tc::FMT_F16 : tc::FMT_BF16));
-      const uint32_t lboV = TC_PTS * 16, lboG = NB * 16, sbo = 128;
+      const uint32_t lboV = TC_PTS * 16, sboV = 128;
+      const uint32_t lboG = 128, sboG = (TC_KC / S::EPC) * 128;
       int c = 0, w = 0;
-      for (int wi = blockIdx.x; wi < nitems && !*stop; wi += gridDim.x) {
+      for (int wi = cid; wi < nitems && !*stop; wi += ncl) {
         if (!live_item(wi)) continue;
         for (int rb = 0; rb < nrb && !*stop; ++rb, ++w) {
           const int acc = w % NBUF, use = w / NBUF;
@@ -280,15 +319,17 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
               for (int h = 0; h < TPW; ++h) {
                 const uint32_t d = d0 + (uint32_t)(h * NB);
                 const uint32_t vH = base + h * 2 * S::V_BYTES, vL = vH + S::V_BYTES;
-                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
-                                 (kc > 0 || kk > 0) ? 1u : 0u);
-                tc::mma<ES == 4>(d, tc::smem_desc(vL + oV, lboV, sbo), tc::smem_desc(gH + oG, lboG, sbo), idesc,
-                                 1u);
-                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sbo), tc::smem_desc(gL + oG, lboG, sbo), idesc,
-                                 1u);
+                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sboV), tc::smem_desc(gH + oG, lboG, sboG),
+                                 idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc::mma<ES == 4>(d, tc::smem_desc(vL + oV, lboV, sboV), tc::smem_desc(gH + oG, lboG, sboG),
+                                 idesc, 1u);
+                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sboV), tc::smem_desc(gL + oG, lboG, sboG),
+                                 idesc, 1u);
               }
             }
-            tc::mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+            // the stage is free (in every CTA of the cluster) once these MMAs have read it
+            if (CL == 1) tc::mma_commit(&empty[s]);
+            else tc::mma_commit_mc(&empty[s], CL_MASK);
           }
           if (*stop) break;
           tc::mma_commit(&acc_full[acc]);  // accumulator complete
@@ -304,13 +345,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
     const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n) - a.eVoff + a.eG)) : 1.0f;
     int w = 0;
     constexpr int NA = N > 0 ? N : 1;
-    for (int wi = blockIdx.x; wi < nitems && !*stop; wi += gridDim.x) {
+    for (int wi = cid; wi < nitems && !*stop; wi += ncl) {
       if (!live_item(wi)) continue;
-      // the l-sum epilogue has one tile per work item
-      const int pt = wi * TPW * TC_PTS + row_in_tile;
+      // the l-sum epilogue has one tile per CTA and work item
+      const bool mine = live(tile_of(wi, 0));
+      const int pt = tile_of(wi, 0) * TC_PTS + row_in_tile;
       const int j = pt / n, t = pt - j * n;
       float2 av[NA], nl[NA];
-      if (OUT == 0) {
+      if (OUT == 0 && mine) {
 #pragma unroll
         for (int l = 0; l < N; ++l) {
           av[l] = a.A[((size_t)j * N + l) * n + t];
@@ -331,7 +373,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
         if (OUT == 1) {
 #pragma unroll
           for (int h = 0; h < TPW; ++h) {
-            const int tile = wi * TPW + h;
+            const int tile = tile_of(wi, h);
             if (!live(tile)) continue;  // (every thread of the warp skips alike)
             const int pth = tile * TC_PTS + row_in_tile;
             const int jh = pth / n, th = pth - jh * n;
@@ -346,14 +388,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
               }
             }
           }
-        } else {
+        } else if (mine) {
           drain_rb<N, NB, 0>(rb, taddr, av, nl);
         }
         tc::fence_before_sync();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&acc_empty[acc])) : "memory");
       }
       if (*stop) break;
-      if (OUT == 0) {
+      if (OUT == 0 && mine) {
         float2* out = a.NL + (size_t)j * N * n + t;
 #pragma unroll
         for (int p = 0; p < N; ++p) out[(size_t)p * n] = nl[p];
@@ -362,6 +404,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CL > 1) tc::cluster_sync();  // no CTA leaves while a peer may still write to it
   if (warp == 1) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
