@@ -76,9 +76,10 @@ struct TcArgs {
 
 __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
 
-// CTAs per cluster of the GEMM with row blocks of NB rows: 2 from 64 rows
-// (NB is a multiple of 16, so each CTA's share is whole 8-row groups).
-__host__ __device__ constexpr int tc_cluster(int NB) { return NB >= 64 ? 2 : 1; }
+// CTAs per cluster of the GEMM with row blocks of NB rows: 4 from 128 rows
+// when NB is a multiple of 32, else 2 from 64 rows (NB is a multiple of 16),
+// so that each CTA's share is whole 8-row groups.
+__host__ __device__ constexpr int tc_cluster(int NB) { return (NB >= 128 && NB % 32 == 0) ? 4 : (NB >= 64 ? 2 : 1); }
 
 // FP16 scale exponent of V: 2^eV (2 x the bound on |V|) < 2^14; the bound
 // is (1/Nt) sum_w |psi0|^2, summed at the start of the propagation.
