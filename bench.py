@@ -41,9 +41,9 @@ WORKLOADS = {
            "dz=37.5 um, M=16, tol=1e-6"),
 }
 # DRAM bytes per launch of the dominant kernel from one ncu capture (the
-# kernel unchanged since): k_pairs_raman<float, 16> on the 6-mode workload,
-# warm L2, profiles/pairs_raman_c2_fp32.md.
-TRAFFIC = {("C2", "fp32", "pairs_raman"): 256 + 3840}
+# kernel unchanged since): k_pairs_raman<float, 16, 0> on the 6-mode
+# workload, warm L2, profiles/pairs_raman_c2_fp32.md.
+TRAFFIC = {("C2", "fp32", "pairs_raman"): 1024 + 256}
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
 
 
