@@ -295,7 +295,7 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
 // (cudaOccupancyMaxActiveClusters, once per kernel), at most one cluster per
 // work item of CL x TPW point tiles.  A grid of more clusters than fit would
 // run the surplus as a second wave.
-static int tc_grid(const void* kern, size_t smem, int cl, int tpw, int ntiles) {
+static int tc_grid(const void* kern, size_t smem, int cl, int tpw, int ntiles, int threads) {
   static std::mutex mu;
   static std::map<const void*, int> resident;
   int maxc = 0;
@@ -307,7 +307,7 @@ static int tc_grid(const void* kern, size_t smem, int cl, int tpw, int ntiles) {
     } else {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(148 / cl * cl);
-      cfg.blockDim = dim3(192);
+      cfg.blockDim = dim3(threads);
       cfg.dynamicSmemBytes = smem;
       cudaLaunchAttribute at;
       at.id = cudaLaunchAttributeClusterDimension;
@@ -342,8 +342,9 @@ static void launch_tc_lsum_es(gm_job* jb, const Geo& g, cudaStream_t s, const CU
     constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                          \
     using Sh = TcShape<NN, NB, ES>;                                                                              \
     auto kern = k_tc_contract<NN, NB, 0, ES>;                                                                    \
-    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles));                              \
-    pdl_launch_cl(kern, grid, dim3(192), Sh::SMEM, s, Sh::CL, mVhi, mVlo, mGhi, mGlo, a, (const LoopState*)jb->ls); \
+    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles, Sh::THREADS));                 \
+    pdl_launch_cl(kern, grid, dim3(Sh::THREADS), Sh::SMEM, s, Sh::CL, mVhi, mVlo, mGhi, mGlo, a,                  \
+                  (const LoopState*)jb->ls);                                                                     \
     break;                                                                                                       \
   }
     GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
@@ -421,13 +422,17 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
   const size_t pts = (size_t)(g.M + 1) * c->n;
   if (c->tc) {
     if constexpr (std::is_same<R, float>::value) {
-      launch_pack_pairs(jb, g, s, 0);
+      // 16-bit operands: U is formed inside the GEMM (TcShape::FU); TF32: packed first
+      if (c->tf32) launch_pack_pairs(jb, g, s, 0);
       TcArgs a = tc_args(jb, g);
       a.KKp = c->KKp;
       a.eG = c->eW16;
       a.nrb = c->r_rows / c->NB1;
       a.Zout = (float*)jb->Z;
       a.zrows = c->r;
+      a.nmodes = c->N;
+      a.K = c->K;
+      a.pairs = (const int2*)c->pairs;
       const int ntiles = (int)(pts / TC_PTS);
       auto store = [&](auto es) {
         constexpr int ES = decltype(es)::value;
@@ -436,9 +441,10 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
   case NB: {                                                                                                  \
     using Sh = TcShape<0, NB, ES, 1>;                                                                         \
     auto kern = k_tc_contract<0, NB, 1, ES>;                                                                  \
-    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles));                           \
-    pdl_launch_cl(kern, grid, dim3(192), Sh::SMEM, s, Sh::CL, jb->mapHi, jb->mapLo, c->mapWhi, c->mapWlo, a,  \
-                  (const LoopState*)jb->ls);                                                                  \
+    static_assert(!Sh::FU || U_FIT_N >= 42, "the fused U stages the A of up to 42 modes");                \
+    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles, Sh::THREADS));              \
+    pdl_launch_cl(kern, grid, dim3(Sh::THREADS), Sh::SMEM, s, Sh::CL, jb->mapHi, jb->mapLo, c->mapWhi,        \
+                  c->mapWlo, a, (const LoopState*)jb->ls);                                                    \
     break;                                                                                                    \
   }
           GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)

@@ -72,6 +72,8 @@ struct TcArgs {
   int nrb;           // OUT 1: row blocks
   float* Zout;       // OUT 1: D rows [M+1][zrows][n]
   int zrows;         // OUT 1: rows stored (the rest is padding)
+  int nmodes, K;     // U formed in the kernel: modes of A, pair columns
+  const int2* pairs; // U formed in the kernel: (m, n) of column k
 };
 
 __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
@@ -91,12 +93,44 @@ __device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n) {
   return 14 - e;
 }
 
+// Operand types of the hi/lo split: OP 0 BF16, 1 FP16, 2 TF32 (FP32 words
+// with the low 13 mantissa bits cleared by rounding to nearest, ties away).
+template <int OP> struct Split;
+template <> struct Split<0> {
+  using T = __nv_bfloat16;
+  static constexpr int EPC = 8;
+  __device__ static T rn(float x) { return __float2bfloat16_rn(x); }
+  __device__ static float back(T h) { return __bfloat162float(h); }
+};
+template <> struct Split<1> {
+  using T = __half;
+  static constexpr int EPC = 8;
+  __device__ static T rn(float x) { return __float2half_rn(x); }
+  __device__ static float back(T h) { return __half2float(h); }
+};
+template <> struct Split<2> {
+  using T = float;
+  static constexpr int EPC = 4;
+  __device__ static T rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+  }
+  __device__ static float back(T h) { return h; }
+};
+
 // ES: operand element bytes, 2 (BF16 / FP16) or 4 (TF32); a core-matrix row
 // of 16 bytes holds EPC = 16 / ES elements.
+// FU: the store epilogue (OUT 1) with 16-bit operands forms its V operand,
+// the pair products U of A, in the kernel: eight more warps compute each K
+// chunk of U for the CTA's tile from A staged in shared memory and write it
+// to the stage as hi/lo (no packed U in HBM).  U_FIT_N bounds the modes of A
+// it stages.
 // TPW: point tiles per work item, sharing each stage's coupling chunk (two
-// MMAs of M = 128 into two accumulators): 2 for the store epilogue (OUT 1)
-// when two stages still fit, else 1.  NBUF: accumulator buffers in TMEM
+// MMAs of M = 128 into two accumulators): 2 for the store epilogue without
+// FU when two stages still fit, else 1.  NBUF: accumulator buffers in TMEM
 // (2 lets the epilogue drain one work item while the next one's MMAs run).
+constexpr int U_FIT_N = 42, U_FIT_KKP = 928;  // N(N+1)/2 = 903 padded to 32
 template <int N, int NB, int ES = 2, int OUT = 0>
 struct TcShape {
   static constexpr int P = N * (N + 1) / 2;
@@ -105,15 +139,20 @@ struct TcShape {
   static constexpr int KSTEPS = TC_KC * ES / 32;       // MMAs of 32 bytes of K per chunk
   static constexpr int V_BYTES = TC_PTS * TC_KC * ES;  // one of hi / lo, one tile
   static constexpr int G_BYTES = NB * TC_KC * ES;
-  static constexpr int TPW = (OUT == 1 && 2 * 2 * (2 * V_BYTES + G_BYTES) <= 200 * 1024) ? 2 : 1;
+  static constexpr bool FU = OUT == 1 && ES == 2;
+  static constexpr int UW = FU ? 8 : 0;                // U-producer warps
+  static constexpr int THREADS = 192 + 32 * UW;
+  // A tile ([U_FIT_N][128] float2) and column table ([KKp] int2) of FU
+  static constexpr int U_RESERVE = FU ? U_FIT_N * TC_PTS * 8 + U_FIT_KKP * 8 : 0;
+  static constexpr int TPW = (OUT == 1 && !FU && 2 * 2 * (2 * V_BYTES + G_BYTES) <= 200 * 1024) ? 2 : 1;
   static constexpr int STAGE = 2 * (TPW * V_BYTES + G_BYTES);
-  static constexpr int FIT = 200 * 1024 / STAGE;
+  static constexpr int FIT = (200 * 1024 - U_RESERVE) / STAGE;
   static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 6 ? 6 : FIT);
   static constexpr int ACC_COLS = TPW * NB;            // one accumulator buffer
   static constexpr int NBUF = 2 * ACC_COLS <= 512 ? 2 : 1;
   static constexpr int COLS = NBUF * ACC_COLS;
   static constexpr int TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + U_RESERVE;
   static constexpr int CL = tc_cluster(NB);           // CTAs sharing each coupling chunk
   static constexpr int G_SHARE = G_BYTES / CL;         // one CTA's share (hi or lo)
 };
@@ -183,7 +222,7 @@ __device__ __forceinline__ void drain_rb(int rb, uint32_t taddr, const float2* a
 // OUT 0: the l-sum epilogue into NL (N modes, compile-time); OUT 1: the
 // accumulator rows stored as Z (first GEMM of the low-rank coupling; N is 0).
 template <int N, int NB, int OUT, int ES = 2>
-__global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ CUtensorMap mapVhi,
+__global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_contract(const __grid_constant__ CUtensorMap mapVhi,
                                                          const __grid_constant__ CUtensorMap mapVlo,
                                                          const __grid_constant__ CUtensorMap mapGhi,
                                                          const __grid_constant__ CUtensorMap mapGlo, TcArgs a,
@@ -199,9 +238,12 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   volatile int* stop = &stop_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+  // FU: A tile [nmodes][128] and the column table after the stages
+  float2* As = reinterpret_cast<float2*>(smem + (size_t)S::STAGES * S::STAGE);
+  int2* Ps = reinterpret_cast<int2*>(As + (S::FU ? U_FIT_N * TC_PTS : 0));
   if (tid == 0) {
     for (int s = 0; s < S::STAGES; ++s) {
-      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&full[s], 1 + S::UW);  // the TMA producer (+ each U warp)
       tc::mbar_init(&empty[s], CL);  // released by the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
@@ -217,6 +259,22 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
   if (CL > 1) tc::cluster_sync();  // the peers' barriers exist before any multicast
   tc::fence_after_sync();
   pdl_enter();
+  if (S::FU) {
+    // column k of U: the offsets of A_m and A_n in the A tile (16 bits each)
+    // and the weight (1 on the diagonal, 2 off it, times the FP16 scale);
+    // the padding columns have weight 0
+    const float sc = a.f16 ? ldexpf(1.0f, f16_v_exp(ls, a.n)) : 1.0f;
+    for (int k = tid; k < a.KKp; k += S::THREADS) {
+      int2 e = make_int2(0, 0);
+      if (k < a.K) {
+        const int2 mn = a.pairs[k];
+        e.x = (mn.x * TC_PTS) | ((mn.y * TC_PTS) << 16);
+        e.y = __float_as_int(mn.x == mn.y ? sc : 2.0f * sc);
+      }
+      Ps[k] = e;
+    }
+    __syncthreads();
+  }
   const uint32_t tmem = tmem_base;
   const int iter = ls->iter;
   const int nrb = OUT == 0 ? S::NRB : a.nrb;
@@ -252,10 +310,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
               break;
             }
             unsigned char* st = smem + (size_t)s * S::STAGE;
-            tc::mbar_arrive_expect_tx(&full[s], S::STAGE);
+            tc::mbar_arrive_expect_tx(&full[s], S::FU ? 2 * S::G_BYTES : S::STAGE);
             const int kq = kc * (TC_KC / S::EPC);  // K coordinate in core-matrix rows
 #pragma unroll
-            for (int h = 0; h < TPW; ++h) {
+            for (int h = 0; h < (S::FU ? 0 : TPW); ++h) {
               // a tile past the end repeats the last one (its result is not stored)
               const int tile = min(tile_of(wi, h), ntiles - 1);
               unsigned char* sv = st + (size_t)h * 2 * S::V_BYTES;
@@ -337,7 +395,115 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
         }
       }
     }
-  } else {
+  } else if (S::FU && warp >= 6) {
+    // ---------------- U producers: warps 6..13, two threads per point ----------------
+    // thread (q, half) writes K columns [16 half, 16 half + 16) of each chunk
+    // for point q of the tile, as hi + lo in the stage's [4][128][8] layout.
+    // The A tile of the next work item is fetched into registers while the
+    // current one's chunks are formed.
+    constexpr int UT = 32 * (S::FU ? S::UW : 1);          // U threads
+    constexpr int AL = (U_FIT_N * TC_PTS + UT - 1) / UT;  // A values per thread and tile
+    const int u = tid - 192, q = u & (TC_PTS - 1), half = u >> 7;
+    const int nm = a.nmodes;
+    float2 nxt[AL];
+    auto fetch = [&](int wi) {
+      const int tile = min(tile_of(wi, 0), ntiles - 1);
+      const int pt0 = tile * TC_PTS, j = pt0 / n, t0 = pt0 - j * n;
+#pragma unroll
+      for (int r = 0; r < AL; ++r) {
+        const int i = u + r * UT;
+        if (i < nm * TC_PTS) {
+          const int l = i / TC_PTS, qq = i - l * TC_PTS;
+          nxt[r] = a.A[((size_t)j * nm + l) * n + t0 + qq];
+        }
+      }
+    };
+    auto next_live = [&](int wi) {
+      for (wi += ncl; wi < nitems && !live_item(wi); wi += ncl) {
+      }
+      return wi;
+    };
+    // eight K values of this point: U_k = |A_m|^2 or 2 Re(A_m conj A_n), scaled
+    auto u8 = [&](int k0, float* x) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int2 e = Ps[k0 + i];
+        const float2 am = As[(e.x & 0xffff) + q], an = As[(e.x >> 16) + q];
+        x[i] = __int_as_float(e.y) * (am.x * an.x + am.y * an.y);
+      }
+    };
+    // hi + lo of eight values, two per conversion
+    auto split8 = [&](const float* x, uint4& hw, uint4& lw) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (a.f16) {
+          const __half2 hh = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+          const float2 hb = __half22float2(hh);
+          const __half2 ll = __floats2half2_rn(x[2 * i] - hb.x, x[2 * i + 1] - hb.y);
+          h[i] = *reinterpret_cast<const uint32_t*>(&hh);
+          l[i] = *reinterpret_cast<const uint32_t*>(&ll);
+        } else {
+          const __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+          const float2 hb = __bfloat1622float2(hh);
+          const __nv_bfloat162 ll = __floats2bfloat162_rn(x[2 * i] - hb.x, x[2 * i + 1] - hb.y);
+          h[i] = *reinterpret_cast<const uint32_t*>(&hh);
+          l[i] = *reinterpret_cast<const uint32_t*>(&ll);
+        }
+      }
+      hw = make_uint4(h[0], h[1], h[2], h[3]);
+      lw = make_uint4(l[0], l[1], l[2], l[3]);
+    };
+    int wi = cid;
+    while (wi < nitems && !live_item(wi)) wi += ncl;
+    if (wi < nitems) fetch(wi);
+    int c = 0;
+    // every U thread passes the same named barriers: the item loop does not
+    // depend on the stop flag; after a stop the chunks are skipped unwaited
+    while (wi < nitems) {
+      const int wn = next_live(wi);
+      tc::named_sync(1, UT);  // every chunk of the previous tile is written
+#pragma unroll
+      for (int r = 0; r < AL; ++r) {
+        const int i = u + r * UT;
+        if (i < nm * TC_PTS) As[i] = nxt[r];
+      }
+      tc::named_sync(1, UT);
+      if (wn < nitems) fetch(wn);
+      for (int rb = 0; rb < nrb; ++rb)
+        for (int kc = 0; kc < kchunks; ++kc, ++c) {
+          const int s = c % S::STAGES, round = c / S::STAGES;
+          // lane 0 waits for the stage; the warp follows its verdict (uniform)
+          int go = 1;
+          if (lane == 0) {
+            if (*stop) {
+              go = 0;
+            } else if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1)) {
+              *stop = 1;
+              atomicExch(a.err, 1u);
+              go = 0;
+            }
+          }
+          if (!__shfl_sync(0xffffffffu, go, 0)) continue;
+          unsigned char* st = smem + (size_t)s * S::STAGE;
+#pragma unroll
+          for (int kq2 = 0; kq2 < 2; ++kq2) {
+            const int kq = 2 * half + kq2;
+            float x[8];
+            u8(kc * TC_KC + kq * 8, x);
+            uint4 hw, lw;
+            split8(x, hw, lw);
+            const size_t o = ((size_t)kq * TC_PTS + q) * 16;
+            *reinterpret_cast<uint4*>(st + o) = hw;
+            *reinterpret_cast<uint4*>(st + S::V_BYTES + o) = lw;
+          }
+          tc::fence_proxy_async();  // the stores are seen by the tensor cores' reads
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&full[s]);
+        }
+      wi = wn;
+    }
+  } else if (warp < 6) {
     // ---------------- epilogue: warps 2..5, one point per thread ----------------
     const int quarter = warp & 3;  // this warp may access TMEM lanes 32 quarter ..
     const int row_in_tile = quarter * 32 + lane;
@@ -418,32 +584,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_contract(const __grid_constant__ 
 // kc = w, w + 8, ...  Y loads and the 16-byte stores are coalesced across
 // the lanes.
 constexpr int PACK_PTS = 32, PACK_WARPS = 8;
-
-// Operand types of the hi/lo split: OP 0 BF16, 1 FP16, 2 TF32 (FP32 words
-// with the low 13 mantissa bits cleared by rounding to nearest, ties away).
-template <int OP> struct Split;
-template <> struct Split<0> {
-  using T = __nv_bfloat16;
-  static constexpr int EPC = 8;
-  __device__ static T rn(float x) { return __float2bfloat16_rn(x); }
-  __device__ static float back(T h) { return __bfloat162float(h); }
-};
-template <> struct Split<1> {
-  using T = __half;
-  static constexpr int EPC = 8;
-  __device__ static T rn(float x) { return __float2half_rn(x); }
-  __device__ static float back(T h) { return __half2float(h); }
-};
-template <> struct Split<2> {
-  using T = float;
-  static constexpr int EPC = 4;
-  __device__ static T rn(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-  }
-  __device__ static float back(T h) { return h; }
-};
 
 // Eight consecutive K values of one point to the blocked layout
 // [K/EPC][npts][EPC]: one or two 16-byte pieces.
