@@ -134,7 +134,7 @@ def job_rate(units_per_rank_step, steps, world, seconds):
     return units_per_rank_step * steps * world / seconds
 
 
-def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=8192):
+def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=8192, tf32=False):
     """Kernel launches of one propagate call, from its statistics."""
     per_iter = 5 if raman else 4   # K1 [K2] K3 K4 K5 (decision in K5's last block)
     tc = mixed and N > 8           # the tensor cores run the contraction from 9 modes
@@ -142,7 +142,9 @@ def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=81
     if lowrank:
         per_iter += 1              # two GEMMs (Z = W U, then X V')
     if tc:
-        per_iter += 2 if lowrank else 1   # each GEMM has its operand pack
+        # the operand pack of V (dense) or V' (low-rank GEMM 2); the low-rank
+        # GEMM 1 forms U itself with 16-bit operands, TF32 packs it first
+        per_iter += 1 + (1 if lowrank and tf32 else 0)
     fft = 1 if Nt <= 8192 else 2  # FP64 input/output transforms (halves + combine above 8192)
     n = 1 + fft + 1          # non-finite check, forward transform, input sums
     if not fp64:
@@ -499,7 +501,8 @@ def main():
     roof["kernel_ms"] = ms_dom
     roof["all_kernels_ms"] = {k: v[0] for k, v in prof.items()}
     raman = prob.fR != 0
-    launches = sum(launches_per_step(st, raman, mixed, args.precision == "fp64", N=prob.N, Nt=prob.Nt) for st in stats)
+    launches = sum(launches_per_step(st, raman, mixed, args.precision == "fp64", N=prob.N, Nt=prob.Nt,
+                                     tf32=args.precision == "tf32") for st in stats)
     ctx.close()
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
