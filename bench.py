@@ -516,6 +516,7 @@ def main():
                    "units_per_step": u, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "long_steps_per_step": stats[-1]["long_steps"],
                    "iters_per_long_step": stats[-1]["iters_total"] / max(stats[-1]["long_steps"], 1),
+                   "coupling_rank": stats[-1].get("coupling_rank"),
                    "rel_l2_err_vs_fp64_gpu": err, "err_prefix": err_prefix, "fp64_gpu_value": fp64_rate,
                    "wall_s": wall},
         "e2e": e2e,

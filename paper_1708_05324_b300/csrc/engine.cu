@@ -456,7 +456,13 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   std::vector<double> Xd, Wd, Gt_rows, Xt_rows;
   const char* dense_env = getenv("GMMNLSE_DENSE");
   if (N > 8 && c->raman_mode != 2 && !(dense_env && dense_env[0] == '1')) {
-    const int r = lowrank(Gd, c->P, c->K, 1e-12, Xd, Wd);
+    // the dropped part of the coupling (columns below tol x the largest)
+    // stays under the rounding of the working precision's contraction:
+    // 1e-12 for FP64; 1e-9 for FP32 and the mixed precisions, whose FP32
+    // products round at ~6e-8 (the 42-mode step-index coupling: rank 210
+    // instead of 255 of 903)
+    const double lr_tol = fp64 ? 1e-12 : 1e-9;
+    const int r = lowrank(Gd, c->P, c->K, lr_tol, Xd, Wd);
     if (r > 0 && 4 * r <= 3 * c->K) {
       c->lr = true;
       c->r = r;
