@@ -776,6 +776,10 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
     al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
     al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
   }
+  // the hi/lo operand starts at zero: with the low-rank coupling its padding
+  // columns are never written again (k_raman_vpack writes the r columns only)
+  if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vhi, 0, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
+  if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vlo, 0, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_ls, sizeof(LoopState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_io, Nn * 16);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&jb->cap, cudaStreamNonBlocking);

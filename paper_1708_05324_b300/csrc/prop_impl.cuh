@@ -124,6 +124,10 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 1, 0>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 1, 0>, A, sm));
   if (std::is_same<R, float>::value) {
+    CK(cudaFuncSetAttribute(k_raman_vpack<16, 0>, A, sm));
+    CK(cudaFuncSetAttribute(k_raman_vpack<32, 0>, A, sm));
+    CK(cudaFuncSetAttribute(k_raman_vpack<16, 1>, A, sm));
+    CK(cudaFuncSetAttribute(k_raman_vpack<32, 1>, A, sm));
     const int rc = tc_for_each_n([&](auto kern) -> int {
       cudaFuncAttributes fa;
       CK(cudaFuncGetAttributes(&fa, kern));
@@ -478,6 +482,26 @@ template <typename R>
 static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, pp = (c->r + 1) / 2;
+  if constexpr (std::is_same<R, float>::value) {
+    if (c->tc && !c->tf32) {
+      // 16-bit operands: K2 writes GEMM 2's V' operand itself (no Y', no pack)
+      const int ept = fft_ept<float>(n, pp * (g.M + 1));
+      const int npts_total = (jb->Mcap + 1) * n;
+      auto vp = [&](auto kern) {
+        pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<float>(n), s, g, (const float*)jb->Z, c->r,
+                   (const float2*)c->H, (const float2*)twid<float>(c), npts_total, (void*)jb->Vhi, (void*)jb->Vlo,
+                   c->eW, (const LoopState*)jb->ls);
+      };
+      if (c->f16) {
+        if (ept == 32) vp(k_raman_vpack<32, 1>);
+        else vp(k_raman_vpack<16, 1>);
+      } else {
+        if (ept == 32) vp(k_raman_vpack<32, 0>);
+        else vp(k_raman_vpack<16, 0>);
+      }
+      return;
+    }
+  }
   auto one = [&](auto kern, int ept) {
     pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
                (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)jb->Z, c->r,
@@ -507,7 +531,10 @@ static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
   if (c->tc) {
     if constexpr (std::is_same<R, float>::value) {
       const int npts_total = (jb->Mcap + 1) * c->n;
+      // with Raman and 16-bit operands K2 has written V' already (k_raman_vpack)
+      const bool packed = mode == 1 && !c->tf32;
       auto pack = [&](auto kern) {
+        if (packed) return;
         pdl_launch(kern, dim3((unsigned)((pts + PACK_PTS - 1) / PACK_PTS)), dim3(PACK_PTS * PACK_WARPS), 0, s, g,
                    (const float*)jb->Z,
                    (const float*)jb->V, c->r, c->rKKp, npts_total, (void*)jb->Vhi, (void*)jb->Vlo, c->eW,
