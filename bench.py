@@ -141,10 +141,12 @@ def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=81
     lowrank = st.get("coupling_rank", 0) < N * (N + 1) // 2
     if lowrank:
         per_iter += 1              # two GEMMs (Z = W U, then X V')
-    if tc:
-        # the operand pack of V (dense) or V' (low-rank GEMM 2); the low-rank
-        # GEMM 1 forms U itself with 16-bit operands, TF32 packs it first
-        per_iter += 1 + (1 if lowrank and tf32 else 0)
+    if tc and not lowrank:
+        per_iter += 1              # the operand pack of V
+    elif tc:
+        # 16-bit operands: GEMM 1 forms U itself and, with Raman, K2 writes
+        # GEMM 2's operand V'; TF32 packs both operands
+        per_iter += (1 if tf32 else 0) + (1 if tf32 or not raman else 0)
     fft = 1 if Nt <= 8192 else 2  # FP64 input/output transforms (halves + combine above 8192)
     n = 1 + fft + 1          # non-finite check, forward transform, input sums
     if not fp64:
