@@ -157,6 +157,38 @@ def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=81
     return n
 
 
+def run_error_curve(args, dev):
+    """Relative L2 difference between this precision and the FP64 GPU path
+    along the fiber.  Both propagate the same input in SEGMENTS pieces of
+    whole long steps, each piece continuing from its own previous output
+    (the field between long steps is kept in FP64 on both paths, so the
+    pieces add only FP64 transforms); the difference is printed at the end
+    of each piece.  Over long, strongly nonlinear fibers rounding differences
+    grow, so this is the curve that says how far a prefix parity carries."""
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(L=args.length, name=args.workload)
+    lstep = prob.M * prob.dz
+    nlong = int(round(prob.L / lstep))
+    nseg = max(1, min(args.error_curve, nlong))
+    per = nlong // nseg
+    c64 = B.Context.from_problem(prob, precision="fp64", device=dev)
+    cx = B.Context.from_problem(prob, precision=args.precision, device=dev)
+    a64, ax = np.ascontiguousarray(prob.A0), np.ascontiguousarray(prob.A0)
+    curve, done = [], 0
+    t0 = time.perf_counter()
+    for sgm in range(nseg):
+        nl = per if sgm < nseg - 1 else nlong - done
+        a64, _, _ = c64.propagate(a64, nl * lstep, prob.dz, prob.M, prob.tol)
+        ax, _, _ = cx.propagate(ax, nl * lstep, prob.dz, prob.M, prob.tol)
+        done += nl
+        curve.append([round(done * lstep, 9), float(np.linalg.norm(ax - a64) / np.linalg.norm(a64))])
+    c64.close()
+    cx.close()
+    print(json.dumps({"error_curve": curve, "vs": "fp64 gpu", "precision": args.precision,
+                      "workload": args.workload, "length_m": args.length, "long_steps": nlong,
+                      "wall_s": time.perf_counter() - t0}))
+
+
 def run_reference(args):
     """The CPU oracle as it stands, on a bounded sample of the workload."""
     import oracle as O
@@ -354,6 +386,8 @@ def main():
                     help="only the timed propagations (for ncu captures)")
     ap.add_argument("--kernel-profile", action="store_true",
                     help="with --profile-run: also time each kernel of one iteration")
+    ap.add_argument("--error-curve", type=int, default=0, metavar="SEGMENTS",
+                    help="print the error against the FP64 GPU path at SEGMENTS points along the fiber")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -363,6 +397,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+
+    if args.error_curve:
+        if rank == 0:
+            run_error_curve(args, local)
         return
 
     import torch
