@@ -346,6 +346,24 @@ def test_mixed_dense_42_mode_contraction(mixed):
     assert rel(out, ref) < 1e-3
 
 
+@pytest.mark.parametrize("mixed", ["bf16", "fp16"])
+def test_42_mode_low_rank_gemms_match_dense(mixed, monkeypatch):
+    """The 42-mode coupling on the low-rank path (GEMM 1 forms U in the
+    kernel, K2 writes GEMM 2's operand, GEMM 2 runs four 256-row blocks over
+    K = r) against the oracle and the dense tensor-core contraction."""
+    prob, ref = c4_small()
+    low, st_low, rc = gpu_run(prob, mixed, fixed_iters=3)
+    assert rc == B.OK
+    assert st_low["coupling_rank"] <= 224
+    monkeypatch.setenv("GMMNLSE_DENSE", "1")
+    dense, st_dense, rc = gpu_run(prob, mixed, fixed_iters=3)
+    assert rc == B.OK
+    assert st_dense["coupling_rank"] == 903
+    assert rel(low, ref) < 1e-3
+    assert rel(dense, ref) < 1e-3
+    assert rel(low, dense) < 1e-5
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16", "tf32"])
 def test_low_rank_coupling_matches_dense(precision, monkeypatch):
     """The 15-mode GRIN fiber: the pair matrix of S is the Gram matrix of the
