@@ -1,6 +1,7 @@
 // One-block, shared-memory Stockham auto-sort FFT of length n = 2^k
 // (16 <= n <= 16384): one leading radix-2/4/8 pass when log2 n is not a
-// multiple of 4, then radix-16 passes.
+// multiple of 4, then radix-16 passes; with 32 elements per thread, 8192
+// points take a leading radix-32 pass and two radix-16 passes.
 //
 // Formulation: the radix-R Stockham iteration of Govindaraju et al.
 // ("High performance discrete Fourier transforms on graphics processors",
@@ -16,9 +17,11 @@
 // block must have exactly n / EPT threads.
 //
 // Shared memory: n + n/16 elements (one padding slot per 16 removes the
-// stride-16 bank pattern of the Ns = 1 pass).  The functors may read or
-// write that same shared buffer (by pad16 of the natural index): every pass
-// separates its reads from its writes with a barrier.
+// stride-16 bank pattern of the Ns = 1 radix-16 pass; the radix-32 leading
+// pass keeps a 4-way pattern on its stores, which measured cheaper than a
+// padding of one slot per 32 for the other passes).  The functors may read
+// or write that same shared buffer (by pad16 of the natural index): every
+// pass separates its reads from its writes with a barrier.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -148,6 +151,56 @@ template <typename R, int DIR> struct Dft<R, DIR, 16> {
   }
 };
 
+// exp(DIR 2 pi i m / 32) for odd m = 1..15 (the even ones are w16(m/2))
+template <typename R, int DIR, int m> __device__ __forceinline__ cplx<R> w32odd() {
+  const R c1 = (R)0.98078528040323044913, s1 = (R)0.19509032201612826785, c3 = (R)0.83146961230254523708,
+          s3 = (R)0.55557023301960222474;
+  R x, y;
+  switch (m) {
+    case 1: x = c1; y = s1; break;
+    case 3: x = c3; y = s3; break;
+    case 5: x = s3; y = c3; break;
+    case 7: x = s1; y = c1; break;
+    case 9: x = -s1; y = c1; break;
+    case 11: x = -s3; y = c3; break;
+    case 13: x = -c3; y = s3; break;
+    default: x = -c1; y = s1; break;  // 15
+  }
+  return mk<R>(x, DIR > 0 ? y : -y);
+}
+
+template <typename R, int DIR> struct Dft<R, DIR, 32> {
+  // 32 = 2 x 16: X[2 k2 + k1] = sum_n2 W16^{n2 k2} [W32^{n2 k1} (x[n2] + (-1)^k1 x[n2 + 16])]
+  template <int n2>
+  __device__ __forceinline__ static cplx<R> tw32(cplx<R> a) {
+    if constexpr (n2 == 0) return a;
+    else if constexpr (n2 == 8) return mul_i<R, DIR>(a);
+    else if constexpr (n2 == 4) return w8<R, DIR, 1>(a);
+    else if constexpr (n2 == 12) return w8<R, DIR, 3>(a);
+    else if constexpr (n2 % 2 == 0) return cmul<R>(a, w16<R, DIR>(n2 / 2));
+    else return cmul<R>(a, w32odd<R, DIR, n2>());
+  }
+  template <int n2>
+  __device__ __forceinline__ static void first(cplx<R>* v, cplx<R>* y0, cplx<R>* y1) {
+    if constexpr (n2 < 16) {
+      y0[n2] = cadd<R>(v[n2], v[n2 + 16]);
+      y1[n2] = tw32<n2>(csub<R>(v[n2], v[n2 + 16]));
+      first<n2 + 1>(v, y0, y1);
+    }
+  }
+  __device__ __forceinline__ static void run(cplx<R>* v) {
+    cplx<R> y0[16], y1[16];
+    first<0>(v, y0, y1);
+    Dft<R, DIR, 16>::run(y0);
+    Dft<R, DIR, 16>::run(y1);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      v[2 * k2] = y0[k2];
+      v[2 * k2 + 1] = y1[k2];
+    }
+  }
+};
+
 // One radix-RAD pass.  Twiddles exp(DIR 2 pi i r k / (RAD Ns)) of the
 // butterfly at k = j mod Ns: for a radix-16 pass with a per-pass table
 // (tab[(r-1) Ns + k], r = 1..15), read from it after the barrier; otherwise
@@ -159,13 +212,14 @@ template <typename R, int DIR> struct Dft<R, DIR, 16> {
 template <typename R, int DIR, int RAD, int EPT, bool FIRST, bool LAST, bool TAB, class Load, class Store>
 __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<R>* __restrict__ tw, int tws,
                                          const cplx<R>* __restrict__ tab, const Load& load, const Store& store) {
+  static_assert(RAD != 32 || (FIRST && !LAST), "the radix-32 pass is a leading pass (Ns = 1)");
   constexpr int B = EPT / RAD;  // butterflies per thread
-  constexpr int NW = RAD == 16 ? 4 : RAD - 1;  // table reads per butterfly
+  constexpr int NW = RAD == 16 ? 4 : (RAD == 32 ? 1 : RAD - 1);  // table reads per butterfly
   const int T = blockDim.x;
   const int stride = n / RAD;
   constexpr bool use_tab = RAD == 16 && TAB;
   cplx<R> wt[B][NW];
-  if (Ns > 1 && !use_tab) {
+  if (RAD != 32 && Ns > 1 && !use_tab) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = threadIdx.x + b * T;
@@ -177,7 +231,7 @@ __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<
         wt[b][3] = tw[8 * step];
       } else {
 #pragma unroll
-        for (int r = 1; r < RAD; ++r) wt[b][r - 1] = tw[r * step];
+        for (int r = 1; r < (RAD == 32 ? 2 : RAD); ++r) wt[b][r - 1] = tw[r * step];
       }
     }
   }
@@ -203,7 +257,7 @@ __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<
         if (DIR > 0) x.y = -x.y;
         v[b][r] = cmul<R>(v[b][r], x);
       }
-    } else if (Ns > 1) {
+    } else if (RAD != 32 && Ns > 1) {
       cplx<R> w[RAD];
       if (RAD == 16) {
         // W^r for r = 1..15 from W, W^2, W^4, W^8 with at most three
@@ -220,7 +274,7 @@ __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<
         for (int r = 9; r < 16; ++r) w[r] = cmul<R>(w[r - 8], w[8]);
       } else {
 #pragma unroll
-        for (int r = 1; r < RAD; ++r) w[r] = wt[b][r - 1];
+        for (int r = 1; r < (RAD == 32 ? 1 : RAD); ++r) w[r] = wt[b][r - 1];
       }
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
@@ -259,6 +313,23 @@ __device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __r
   const cplx<R>* tabs = TAB ? tw + n : nullptr;
   const cplx<R>* none = nullptr;
   int Ns = 1, p = 0;
+  int off = 0;  // the current pass's table in tabs
+  if constexpr (EPT == 32) if (logn == 13) {
+    // 8192 = 32 x 16 x 16: a radix-32 leading pass (no twiddles) in place of
+    // the radix-2 one and the first radix-16 pass; the radix-16 passes that
+    // follow (Ns = 32, 512) use the tables of the radix-2 schedule, past
+    // its Ns = 2 table
+    fft_pass<R, DIR, 32, EPT, true, false, false>(sm, n, Ns, tw, tws, none, load, no_store);
+    Ns = 32;
+    off = 15 * 2;
+    const cplx<R>* tab = tabs ? tabs + off : nullptr;
+    fft_pass<R, DIR, 16, EPT, false, false, TAB>(sm, n, Ns, tw, tws, tab, no_load, no_store);
+    off += 15 * Ns;
+    Ns <<= 4;
+    tab = tabs ? tabs + off : nullptr;
+    fft_pass<R, DIR, 16, EPT, false, true, TAB>(sm, n, Ns, tw, tws, tab, no_load, store);
+    return;
+  }
   if (lead) {
     const bool last = (passes == 1);
     if (lead == 1) {
@@ -274,7 +345,6 @@ __device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __r
     Ns <<= lead;
     ++p;
   }
-  int off = 0;  // this pass's table in tabs
   for (; p < passes; ++p) {
     const bool first = (p == 0), last = (p == passes - 1);
     const cplx<R>* tab = tabs ? tabs + off : nullptr;
