@@ -486,8 +486,9 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     }
   }
 
-  // device copies: twiddles exp(-2 pi i m / n) followed by the radix-16
-  // pass tables of the transform length (fft_block reads them at tw + n)
+  // device copies: twiddles exp(-2 pi i m / n) followed by the pass tables
+  // of the transform length (fft_block reads them at tw + n; layout as
+  // fft_pass_table_len)
   auto pass_tables = [](int len, std::vector<double2>& out) {
     int logn = 0;
     while ((1 << logn) < len) ++logn;
@@ -499,6 +500,12 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
           out.push_back(make_double2(std::cos(a), -std::sin(a)));
         }
     }
+    if (logn == 14)  // the radix-32 pass with Ns = 32 of the 32 x 32 x 16 schedule
+      for (int r = 1; r < 32; ++r)
+        for (int k = 0; k < 32; ++k) {
+          const double a = 2.0 * M_PI * (double)k * r / (32.0 * 32.0);
+          out.push_back(make_double2(std::cos(a), -std::sin(a)));
+        }
   };
   std::vector<double2> tw(n), twh(n / 2);
   for (int m = 0; m < n; ++m) {

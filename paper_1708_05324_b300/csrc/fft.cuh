@@ -1,7 +1,8 @@
 // One-block, shared-memory Stockham auto-sort FFT of length n = 2^k
 // (16 <= n <= 16384): one leading radix-2/4/8 pass when log2 n is not a
 // multiple of 4, then radix-16 passes; with 32 elements per thread, 8192
-// points take a leading radix-32 pass and two radix-16 passes.
+// points take a leading radix-32 pass and two radix-16 passes, 16384 points
+// two radix-32 passes and a radix-16 one.
 //
 // Formulation: the radix-R Stockham iteration of Govindaraju et al.
 // ("High performance discrete Fourier transforms on graphics processors",
@@ -34,14 +35,16 @@ __host__ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 __host__ __device__ __forceinline__ int fft_smem_elems(int n) { return n + (n >> 4); }
 
 // Entries of the radix-16 pass tables of an n-point transform (the passes
-// after the leading radix-2/4/8 pass with Ns > 1: 15 Ns each; fewer than n).
+// after the leading radix-2/4/8 pass with Ns > 1: 15 Ns each; fewer than n),
+// followed for n = 16384 by the table of the radix-32 pass with Ns = 32 of
+// the 32 x 32 x 16 schedule (31 x 32 entries, [r-1][k]).
 __host__ __device__ inline int fft_pass_table_len(int n) {
   int logn = 0;
   while ((1 << logn) < n) ++logn;
   int Ns = 1 << (logn & 3), len = 0;
   for (; Ns < n; Ns <<= 4)
     if (Ns > 1) len += 15 * Ns;
-  return len;
+  return logn == 14 ? len + 31 * 32 : len;
 }
 
 template <typename R, int DIR, int RAD> struct Dft;
@@ -212,12 +215,12 @@ template <typename R, int DIR> struct Dft<R, DIR, 32> {
 template <typename R, int DIR, int RAD, int EPT, bool FIRST, bool LAST, bool TAB, class Load, class Store>
 __device__ __forceinline__ void fft_pass(cplx<R>* sm, int n, int Ns, const cplx<R>* __restrict__ tw, int tws,
                                          const cplx<R>* __restrict__ tab, const Load& load, const Store& store) {
-  static_assert(RAD != 32 || (FIRST && !LAST), "the radix-32 pass is a leading pass (Ns = 1)");
+  static_assert(RAD != 32 || (!LAST && (FIRST || TAB)), "a radix-32 pass leads (Ns = 1) or reads a table");
   constexpr int B = EPT / RAD;  // butterflies per thread
   constexpr int NW = RAD == 16 ? 4 : (RAD == 32 ? 1 : RAD - 1);  // table reads per butterfly
   const int T = blockDim.x;
   const int stride = n / RAD;
-  constexpr bool use_tab = RAD == 16 && TAB;
+  constexpr bool use_tab = (RAD == 16 || RAD == 32) && TAB;
   cplx<R> wt[B][NW];
   if (RAD != 32 && Ns > 1 && !use_tab) {
 #pragma unroll
@@ -328,6 +331,18 @@ __device__ __forceinline__ void fft_block(cplx<R>* sm, int n, const cplx<R>* __r
     Ns <<= 4;
     tab = tabs ? tabs + off : nullptr;
     fft_pass<R, DIR, 16, EPT, false, true, TAB>(sm, n, Ns, tw, tws, tab, no_load, store);
+    return;
+  }
+  if constexpr (EPT == 32 && TAB) if (logn == 14 && tws == 1) {
+    // 16384 = 32 x 32 x 16: radix-32 (Ns = 1, no twiddles), radix-32 (Ns =
+    // 32, its own table after the radix-16 ones), radix-16 (Ns = 1024, the
+    // table of the radix-4 schedule's last pass)
+    fft_pass<R, DIR, 32, EPT, true, false, false>(sm, n, Ns, tw, tws, none, load, no_store);
+    Ns = 32;
+    fft_pass<R, DIR, 32, EPT, false, false, TAB>(sm, n, Ns, tw, tws, tabs + (fft_pass_table_len(n) - 31 * 32),
+                                                 no_load, no_store);
+    Ns = 1024;
+    fft_pass<R, DIR, 16, EPT, false, true, TAB>(sm, n, Ns, tw, tws, tabs + 15 * 4 + 15 * 64, no_load, store);
     return;
   }
   if (lead) {
