@@ -282,7 +282,12 @@ template <typename R>
 static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
-  const int S = split_for<R>(N * (g.M + 1), n), np = n / S, ept = S > 1 ? 16 : fft_ept<R>(np, N * (g.M + 1));
+  // K4 takes 32 per thread at 8192 FP32 points whatever the launch size:
+  // its 32 x 16 x 16 schedule measured faster than 16 per thread even for a
+  // launch of fewer blocks than SMs (6-mode workload: 7.4 against 8.9 us),
+  // unlike K1 and K2
+  const int S = split_for<R>(N * (g.M + 1), n), np = n / S;
+  const int ept = S > 1 ? 16 : ((sizeof(R) == 4 && np == 8192) ? 32 : fft_ept<R>(np, N * (g.M + 1)));
   const dim3 grid(N * S, g.M + 1);
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
