@@ -367,11 +367,12 @@ __device__ __forceinline__ void integrand_task(const Geo& g, const cplx<R>* __re
     const cplx<R> iX = mk<R>(-X.y * f, X.x * f);
     I[off + q] = cmulc<R>(iX, e[q]);
   };
-  // FP32 with 16 per thread keeps the product-form twiddles here: with the
-  // pass tables the last pass stacks their loads on the prefactor and phase
-  // loads of the store (measured 13.7 against 8.8 us on the 6-mode workload)
-  constexpr bool TAB = !(sizeof(R) == 4 && EPT == 16);
-  if (S == 1) fft_block<R, +1, EPT, TAB>(sm, n, tw, 1, load, store);
+  // correctly rounded table twiddles: twiddles formed as products of table
+  // entries (up to 4 ulp, with a bias in their magnitude) scale the
+  // integrand by the same small factor in every long step, an error that
+  // grows linearly along the fiber in FP32 (1.2e-5 against FP64 after the
+  // 0.5 m of the 6-mode fiber, 4.4e-6 with the tables)
+  if (S == 1) fft_block<R, +1, EPT, true>(sm, n, tw, 1, load, store);
   else fft_cluster<R, +1, EPT, S>(sm + fft_smem_elems(n / S), sm, n, tw, load, store);
 }
 
