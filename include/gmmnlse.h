@@ -102,7 +102,12 @@ typedef struct gmmnlse_stats {
     double ms;            /* device time of the propagation [ms] */
     int coupling_rank;    /* rank r of the coupling G = X W the contraction
                              used (N > 8, S^R = S^K, r <= 3K/4), else
-                             K = N(N+1)/2 (the dense reduced matrix) */
+                             K = N(N+1)/2 (the dense reduced matrix).  The
+                             factorisation drops columns below 1e-12 (FP64)
+                             or 1e-9 (FP32, mixed) of the largest column of
+                             G, under the rounding of the contraction; the
+                             environment variable GMMNLSE_DENSE=1 at create
+                             keeps the dense matrix */
 } gmmnlse_stats;
 
 typedef struct gmmnlse_ctx gmmnlse_ctx;
