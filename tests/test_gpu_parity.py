@@ -151,6 +151,29 @@ def test_largest_transform_2_14(precision, fft_variant):
 
 
 @functools.lru_cache(maxsize=None)
+def ten_modes_8192():
+    prob = I.grin_problem("m10", N=10, Nt=8192, dt=10e-12 / 8192, kind="gaussian", fwhm=200e-15,
+                          energy=30e-9, L=30 * 2e-5, dz=2e-5, M=30, tol=1e-13, seed=5, fR=0.18, s_from="gh")
+    ref, _ = oracle_run(prob, fixed_iters=3)
+    return prob, ref
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("dense", [False, True])
+def test_8192_point_transforms_at_32_per_thread(precision, dense, monkeypatch):
+    """10 modes x 31 substeps: K1, K2 (pair products, or the rows of Z) and K4
+    launch at least two blocks per SM, so their 8192-point transforms take
+    32 elements per thread and the 32 x 16 x 16 schedule."""
+    if dense:
+        monkeypatch.setenv("GMMNLSE_DENSE", "1")
+    prob, ref = ten_modes_8192()
+    out, st, rc = gpu_run(prob, precision, fixed_iters=3)
+    assert rc == B.OK
+    assert (st["coupling_rank"] == 55) == dense
+    assert rel(out, ref) < TOL.get(precision, 1e-3)
+
+
+@functools.lru_cache(maxsize=None)
 def c2_prefix():
     prob = I.workload("C2", L=4 * 10 * 25e-6)  # 4 long steps of the 0.5 m run
     ref, sref = oracle_run(prob, tol=1e-13)
