@@ -189,6 +189,66 @@ def run_error_curve(args, dev):
                       "wall_s": time.perf_counter() - t0}))
 
 
+def run_m_sweep(args, dev):
+    """Speed-up of the MPA over a solver that takes one substep at a time, on
+    the same kernels (Sec. III.D, Fig. 3).  At convergence the M coupled
+    equations of a long step are the implicit trapezoid rule applied substep
+    after substep in the interaction picture, whatever the long step's origin,
+    so every M reaches the same field up to the iteration tolerance; M = 1 is
+    that sequential integrator, one dz per fixed-point solve.  Each M
+    propagates the same fiber prefix with the same dz; the line reports the
+    rate, the iterations per long step, the speed-up over M = 1 and the
+    relative L2 difference from the M = 1 field."""
+    import torch
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(L=args.length, name=args.workload)
+    Ms = sorted({int(x) for x in args.m_sweep.split(",")} | {1})
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream,
+                                 io_device=True)
+    a0 = torch.from_numpy(prob.A0).to(f"cuda:{dev}")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    u = units(prob)
+    rows, ref = [], None
+    for M in Ms:
+        out = torch.empty_like(a0)
+
+        def once():
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st, rc = ctx.propagate(a0, prob.L, prob.dz, M, prob.tol, out=out, check=False)
+            e1.record(stream)
+            e1.synchronize()
+            if rc != B.OK:
+                raise B.GmmnlseError(rc, f"propagate (M={M})")
+            return e0.elapsed_time(e1), st
+        for _ in range(max(args.warmup, 1)):
+            once()
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            t, st = once()
+            ms.append(t)
+        torch.cuda.synchronize()
+        field = out.cpu().numpy()
+        if ref is None:
+            ref = field
+        t = float(np.median(ms))
+        rows.append({"M": M, "ms": round(t, 4), "units_per_s": u / (t / 1e3),
+                     "iters_per_long_step": st["iters_total"] / max(st["long_steps"], 1),
+                     "long_steps": st["long_steps"],
+                     "rel_l2_vs_M1": float(np.linalg.norm(field - ref) / np.linalg.norm(ref))})
+    ctx.close()
+    base = rows[0]["ms"]
+    for r in rows:
+        r["speedup_vs_M1"] = round(base / r["ms"], 3)
+    print(json.dumps({"m_sweep": rows, "workload": args.workload, "precision": args.precision,
+                      "length_m": args.length, "dz": prob.dz, "tol": prob.tol, "unit": METRIC,
+                      "timing": "CUDA events per propagation, median of --steps, L2 flushed before each"}))
+
+
 def run_reference(args):
     """The CPU oracle as it stands, on a bounded sample of the workload."""
     import oracle as O
@@ -388,6 +448,8 @@ def main():
                     help="with --profile-run: also time each kernel of one iteration")
     ap.add_argument("--error-curve", type=int, default=0, metavar="SEGMENTS",
                     help="print the error against the FP64 GPU path at SEGMENTS points along the fiber")
+    ap.add_argument("--m-sweep", default="", metavar="M1,M2,...",
+                    help="time the workload at each M (and M=1) over --length: MPA speed-up over one substep at a time")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,6 +464,11 @@ def main():
     if args.error_curve:
         if rank == 0:
             run_error_curve(args, local)
+        return
+
+    if args.m_sweep:
+        if rank == 0:
+            run_m_sweep(args, local)
         return
 
     import torch
