@@ -240,12 +240,16 @@ def run_m_sweep(args, dev):
                      "iters_per_long_step": st["iters_total"] / max(st["long_steps"], 1),
                      "long_steps": st["long_steps"],
                      "rel_l2_vs_M1": float(np.linalg.norm(field - ref) / np.linalg.norm(ref))})
+    auto_M, auto_sec = ctx.choose_m(a0, prob.dz, prob.tol, Ms, trial_substeps=2 * max(Ms),
+                                    scratch=torch.empty_like(a0))
     ctx.close()
     base = rows[0]["ms"]
     for r in rows:
         r["speedup_vs_M1"] = round(base / r["ms"], 3)
     print(json.dumps({"m_sweep": rows, "workload": args.workload, "precision": args.precision,
                       "length_m": args.length, "dz": prob.dz, "tol": prob.tol, "unit": METRIC,
+                      "choose_m": {"M": auto_M, "trial_substeps": 2 * max(Ms),
+                                   "us_per_substep": {m: round(1e6 * t, 3) for m, t in auto_sec.items()}},
                       "timing": "CUDA events per propagation, median of --steps, L2 flushed before each"}))
 
 

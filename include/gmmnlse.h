@@ -162,6 +162,37 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
                       double tol, double* Aout, gmmnlse_stats* st);
 
 /*
+ * gmmnlse_choose_m -- pick the substeps per long step M that propagates
+ * fastest from this field (Sec. III.D: the M of largest speed-up depends on
+ * how z_NL compares with dz; the paper gives no rule, so it is measured).
+ *
+ *   A0          [N][Nt] complex field to start from, as for
+ *               gmmnlse_propagate (host unless prm.io_device); not changed.
+ *   dz, tol     substep and tolerance of the propagation to come.
+ *   candidates  [count] values of M to try, each 1..64.
+ *   trial_substeps  length of every trial in substeps (the same fiber
+ *               piece, trial_substeps * dz, for each candidate; a remainder
+ *               long step is taken when M does not divide it).
+ *   scratch     [N][Nt] complex buffer on the same side as A0; receives the
+ *               trial fields (contents undefined on return).
+ *   sec_per_substep  optional [count] output: device seconds per substep of
+ *               each candidate's timed trial, +inf where the trial failed.
+ *   M_best      receives the fastest candidate.
+ *
+ * Each candidate propagates the piece twice, untimed then timed with CUDA
+ * events on the context's stream, largest M first (the workspace is sized
+ * once).  Costs 2 * count trials; synchronous.  Every M converges to the
+ * same field up to tol, since the M coupled trapezoid equations of a long
+ * step are the implicit trapezoid taken substep after substep.  Returns
+ * GMMNLSE_E_INVALID for bad arguments or a non-finite A0; a candidate whose
+ * trial fails (GMMNLSE_E_NOT_CONVERGED, ...) is skipped, and if all fail the
+ * last trial's status is returned.
+ */
+int gmmnlse_choose_m(gmmnlse_ctx* ctx, const double* A0, double dz, double tol,
+                     const int* candidates, int count, int trial_substeps, double* scratch,
+                     double* sec_per_substep, int* M_best);
+
+/*
  * gmmnlse_propagate_noalloc -- gmmnlse_propagate without any memory
  * allocation.  (An addition of this library: the paper has no counterpart.)
  *

@@ -26,7 +26,7 @@ EXPORTS = [
     "gmmnlse_create", "gmmnlse_destroy", "gmmnlse_propagate", "gmmnlse_strerror",
     "gmmnlse_last_error", "gmmnlse_request_bytes", "gmmnlse_server_create",
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
-    "gmmnlse_propagate_noalloc",
+    "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(Stats)]
     lib.gmmnlse_server_destroy.argtypes = [vp]
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.gmmnlse_choose_m.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.c_int, C.c_int, vp, vp,
+                                     C.POINTER(C.c_int)]
     lib.gmmnlse_propagate_noalloc.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                               C.POINTER(Stats)]
     del dp
@@ -160,6 +162,27 @@ class Context:
         if check and rc not in (OK,):
             raise GmmnlseError(rc, "gmmnlse_propagate")
         return out, st.as_dict(), rc
+
+    def choose_m(self, A0, dz, tol, candidates, trial_substeps, scratch=None):
+        """gmmnlse_choose_m: (fastest M, {M: device seconds per substep}).
+        A0 and scratch as for propagate (scratch made like A0 if None)."""
+        if isinstance(A0, np.ndarray):
+            A0 = np.ascontiguousarray(A0, dtype=np.complex128)
+            if A0.shape != (self.N, self.Nt):
+                raise ValueError(f"A0 must be [{self.N}][{self.Nt}]")
+            if scratch is None:
+                scratch = np.empty_like(A0)
+        elif scratch is None:
+            scratch = A0.new_empty(A0.shape)
+        cand = np.ascontiguousarray(candidates, dtype=np.int32)
+        sec = np.zeros(len(cand))
+        best = C.c_int(0)
+        rc = self.lib.gmmnlse_choose_m(self.handle, _ptr(A0), float(dz), float(tol), _ptr(cand),
+                                       len(cand), int(trial_substeps), _ptr(scratch), _ptr(sec),
+                                       C.byref(best))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_choose_m")
+        return best.value, {int(m): float(t) for m, t in zip(cand, sec)}
 
     def profile(self, M, reps=20):
         """Mean device time [ms] and algorithmic bytes per launch of each

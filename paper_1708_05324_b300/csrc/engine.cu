@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -867,6 +868,64 @@ extern "C" int gmmnlse_propagate(gmmnlse_ctx* c, const double* A0, double L, dou
     if (rc) return rc;
   }
   return gm_job_propagate(c->job, A0, c->prm.io_device != 0, L, dz, M, tol, Aout, st, c->stream);
+}
+
+extern "C" int gmmnlse_choose_m(gmmnlse_ctx* c, const double* A0, double dz, double tol,
+                                const int* candidates, int count, int trial_substeps, double* scratch,
+                                double* sec_per_substep, int* M_best) {
+  if (!c || !A0 || !candidates || count < 1 || count > kMaxM || trial_substeps < 1 || !scratch || scratch == A0 ||
+      !M_best || !(dz > 0) || !std::isfinite(dz) || !(tol > 0))
+    return GMMNLSE_E_INVALID;
+  int order[kMaxM];
+  for (int i = 0; i < count; ++i) {
+    if (candidates[i] < 1 || candidates[i] > kMaxM) return GMMNLSE_E_INVALID;
+    order[i] = i;
+  }
+  // Largest M first: the first trial sizes the workspace for all the others.
+  std::sort(order, order + count, [&](int a, int b) { return candidates[a] > candidates[b]; });
+  const double L = trial_substeps * dz;
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return GMMNLSE_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return GMMNLSE_E_CUDA;
+  }
+  int best = -1, last = GMMNLSE_OK;
+  double best_t = 0;
+  for (int k = 0; k < count; ++k) {
+    const int i = order[k], M = candidates[i];
+    double t = std::numeric_limits<double>::infinity();
+    rc = gmmnlse_propagate(c, A0, L, dz, M, tol, scratch, nullptr);  // untimed: tables and graph for M
+    if (rc == GMMNLSE_OK) {
+      cudaEventRecord(e0, c->stream);
+      rc = gmmnlse_propagate(c, A0, L, dz, M, tol, scratch, nullptr);
+      cudaEventRecord(e1, c->stream);
+      float ms = 0;
+      if (rc == GMMNLSE_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        t = 1e-3 * ms / trial_substeps;
+      else if (rc == GMMNLSE_OK)
+        rc = GMMNLSE_E_CUDA;
+    }
+    if (rc == GMMNLSE_E_INVALID || rc == GMMNLSE_E_CUDA || rc == GMMNLSE_E_NOMEM) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;  // the field or the device, not the candidate, is at fault
+    }
+    last = rc;
+    if (sec_per_substep) sec_per_substep[i] = t;
+    if (rc == GMMNLSE_OK && (best < 0 || t < best_t)) {
+      best = i;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return last;
+  *M_best = candidates[best];
+  return GMMNLSE_OK;
 }
 
 extern "C" const char* gmmnlse_strerror(int s) {

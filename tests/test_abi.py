@@ -92,3 +92,10 @@ def test_propagate_and_server_reject_null_handles(lib):
     assert lib.gmmnlse_server_create(0, 1, C.byref(h)) == B.E_INVALID
     assert lib.gmmnlse_destroy(None) == 0
     assert lib.gmmnlse_server_destroy(None) == 0
+
+
+def test_choose_m_rejects_bad_arguments_before_any_cuda_call(lib):
+    cand = (C.c_int * 2)(1, 5)
+    best = C.c_int(0)
+    buf = (C.c_double * 4)()
+    assert lib.gmmnlse_choose_m(None, buf, 1e-4, 1e-8, cand, 2, 10, buf, None, C.byref(best)) == B.E_INVALID
