@@ -240,13 +240,36 @@ def run_m_sweep(args, dev):
                      "iters_per_long_step": st["iters_total"] / max(st["long_steps"], 1),
                      "long_steps": st["long_steps"],
                      "rel_l2_vs_M1": float(np.linalg.norm(field - ref) / np.linalg.norm(ref))})
+    # the split-step comparator (RK4IP, four evaluations of N per step of dz)
+    # on the same kernels, timed the same way
+    rk_out = torch.empty_like(a0)
+    rk_ms = []
+    for it in range(max(args.warmup, 1) + max(args.steps, 1)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, rk_st, rc = ctx.propagate_rk4ip(a0, prob.L, prob.dz, out=rk_out, check=False)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != B.OK:
+            raise B.GmmnlseError(rc, "propagate_rk4ip")
+        if it >= max(args.warmup, 1):
+            rk_ms.append(e0.elapsed_time(e1))
+    rk_t = float(np.median(rk_ms))
+    rk_field = rk_out.cpu().numpy()
+    rk4ip = {"h": prob.dz, "ms": round(rk_t, 4), "units_per_s": u / (rk_t / 1e3),
+             "evaluations_of_N": rk_st["iters_total"],
+             "rel_l2_vs_mpa_M1": float(np.linalg.norm(rk_field - ref) / np.linalg.norm(ref))}
     auto_M, auto_sec = ctx.choose_m(a0, prob.dz, prob.tol, Ms, trial_substeps=2 * max(Ms),
                                     scratch=torch.empty_like(a0))
     ctx.close()
     base = rows[0]["ms"]
     for r in rows:
         r["speedup_vs_M1"] = round(base / r["ms"], 3)
-    print(json.dumps({"m_sweep": rows, "workload": args.workload, "precision": args.precision,
+        r["speedup_vs_rk4ip"] = round(rk_t / r["ms"], 3)
+    print(json.dumps({"m_sweep": rows, "rk4ip": rk4ip, "workload": args.workload, "precision": args.precision,
                       "length_m": args.length, "dz": prob.dz, "tol": prob.tol, "unit": METRIC,
                       "choose_m": {"M": auto_M, "trial_substeps": 2 * max(Ms),
                                    "us_per_substep": {m: round(1e6 * t, 3) for m, t in auto_sec.items()}},

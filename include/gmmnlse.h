@@ -162,6 +162,28 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
                       double tol, double* Aout, gmmnlse_stats* st);
 
 /*
+ * gmmnlse_propagate_rk4ip -- the split-step comparator of the MPA (Sec. III.D,
+ * Fig. 3): fourth-order Runge-Kutta in the interaction picture (RK4IP), one
+ * step of h after another, each step four evaluations of the nonlinear
+ * operator N(A~) = i (n2 w0/c) s(w) F{bracket of Eq. 1 at F^-1 A~} made by
+ * the same transform, pair/Raman and contraction kernels as the MPA, and
+ * exp(i beta h/2) applied three times.
+ *
+ *   A0, Aout, st  as for gmmnlse_propagate (host unless prm.io_device).
+ *   L     fiber length [m]; a whole number of h (to 1e-9 relative).
+ *   h     step [m].
+ *
+ * The field between steps is FP64; N runs in the context's precision.
+ * st->long_steps = steps of h, st->iters_total = evaluations of N (4 per
+ * step), the energy / photon sums and st->ms as for gmmnlse_propagate.
+ * Synchronous.  Allocates 48 bytes per mode and sample of device memory for
+ * the call (GMMNLSE_E_NOMEM if that fails).  Non-finite A0 gives
+ * GMMNLSE_E_INVALID; a non-finite result GMMNLSE_E_NONFINITE.
+ */
+int gmmnlse_propagate_rk4ip(gmmnlse_ctx* ctx, const double* A0, double L, double h, double* Aout,
+                            gmmnlse_stats* st);
+
+/*
  * gmmnlse_choose_m -- pick the substeps per long step M that propagates
  * fastest from this field (Sec. III.D: the M of largest speed-up depends on
  * how z_NL compares with dz; the paper gives no rule, so it is measured).

@@ -27,6 +27,7 @@ EXPORTS = [
     "gmmnlse_last_error", "gmmnlse_request_bytes", "gmmnlse_server_create",
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
+    "gmmnlse_propagate_rk4ip",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(Stats)]
     lib.gmmnlse_server_destroy.argtypes = [vp]
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.gmmnlse_propagate_rk4ip.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(Stats)]
     lib.gmmnlse_choose_m.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.c_int, C.c_int, vp, vp,
                                      C.POINTER(C.c_int)]
     lib.gmmnlse_propagate_noalloc.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, vp,
@@ -161,6 +163,20 @@ class Context:
                                         float(tol), _ptr(out), C.byref(st))
         if check and rc not in (OK,):
             raise GmmnlseError(rc, "gmmnlse_propagate")
+        return out, st.as_dict(), rc
+
+    def propagate_rk4ip(self, A0, L, h, out=None, check=True):
+        """gmmnlse_propagate_rk4ip: (Aout, stats dict, status); A0/out as for propagate."""
+        if isinstance(A0, np.ndarray):
+            A0 = np.ascontiguousarray(A0, dtype=np.complex128)
+            if A0.shape != (self.N, self.Nt):
+                raise ValueError(f"A0 must be [{self.N}][{self.Nt}]")
+            if out is None:
+                out = np.empty_like(A0)
+        st = Stats()
+        rc = self.lib.gmmnlse_propagate_rk4ip(self.handle, _ptr(A0), float(L), float(h), _ptr(out), C.byref(st))
+        if check and rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_propagate_rk4ip")
         return out, st.as_dict(), rc
 
     def choose_m(self, A0, dz, tol, candidates, trial_substeps, scratch=None):

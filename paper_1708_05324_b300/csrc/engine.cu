@@ -870,6 +870,24 @@ extern "C" int gmmnlse_propagate(gmmnlse_ctx* c, const double* A0, double L, dou
   return gm_job_propagate(c->job, A0, c->prm.io_device != 0, L, dz, M, tol, Aout, st, c->stream);
 }
 
+extern "C" int gmmnlse_propagate_rk4ip(gmmnlse_ctx* c, const double* A0, double L, double h, double* Aout,
+                                       gmmnlse_stats* st) {
+  if (!c || !A0 || !Aout) return GMMNLSE_E_INVALID;
+  long nf;
+  int mr;
+  int rc = gm_schedule(L, h, 1, &nf, &mr);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (!c->job) {
+    rc = gm_job_create(c, 1, &c->job);
+    if (rc) return rc;
+  }
+  return c->fp64 ? gm_rk4ip_f64(c->job, A0, c->prm.io_device != 0, L, h, Aout, st, c->stream)
+                 : gm_rk4ip_f32(c->job, A0, c->prm.io_device != 0, L, h, Aout, st, c->stream);
+}
+
 extern "C" int gmmnlse_choose_m(gmmnlse_ctx* c, const double* A0, double dz, double tol,
                                 const int* candidates, int count, int trial_substeps, double* scratch,
                                 double* sec_per_substep, int* M_best) {

@@ -20,6 +20,10 @@ int gm_propagate_f32(gm_job* jb, const double* A0, bool dev_io, double L, double
                      double* Aout, gmmnlse_stats* st, cudaStream_t s);
 int gm_propagate_f64(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
                      double* Aout, gmmnlse_stats* st, cudaStream_t s);
+int gm_rk4ip_f32(gm_job* jb, const double* A0, bool dev_io, double L, double h, double* Aout, gmmnlse_stats* st,
+                 cudaStream_t s);
+int gm_rk4ip_f64(gm_job* jb, const double* A0, bool dev_io, double L, double h, double* Aout, gmmnlse_stats* st,
+                 cudaStream_t s);
 int gm_profile_f32(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes);
 int gm_profile_f64(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes);
 int gm_prop_setup_f32(int device);

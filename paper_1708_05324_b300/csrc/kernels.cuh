@@ -623,6 +623,59 @@ __global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restric
 }
 
 // ---------------------------------------------------------------------------
+// RK4IP, the split-step comparator of the MPA (Sec. III.D, Fig. 3): fourth-
+// order Runge-Kutta in the interaction picture with its origin half a step
+// in, so exp(D h/2) is applied three times per step.  The nonlinear operator
+// N(X) = i gamma0 s(w) F{NL(F^-1 X)} is K1-K4 on slice 0 (phase 1); this
+// kernel makes the elementwise combinations around its four evaluations.  A
+// is the FP64 spectral field at the start of the step, Eh = exp(i beta h/2)
+// (FP64), AI = Eh A, acc the running combination, I = N(X) of the last
+// evaluation, X the next argument of N in the working precision.
+//   stage 0: X = A
+//   stage 1: k1 = Eh N(A); AI = Eh A; acc = AI + h/6 k1; X = AI + h/2 k1
+//   stage 2: k2 = N(X); acc += h/3 k2; X = AI + h/2 k2
+//   stage 3: k3 = N(X); acc += h/3 k3; X = Eh (AI + h k3)
+//   stage 4: k4 = N(X); A = Eh acc + h/6 k4; X = A
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zaxpy(double2 y, double a, double2 x) {
+  return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+
+template <typename R>
+__global__ void k_rk4_stage(int stage, size_t count, double h, double2* __restrict__ A, double2* __restrict__ AI,
+                            double2* __restrict__ acc, const cplx<R>* __restrict__ I,
+                            const double2* __restrict__ Eh, cplx<R>* __restrict__ X) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+    double2 x;
+    if (stage == 0) {
+      x = A[e];
+    } else {
+      const double2 k = make_double2((double)I[e].x, (double)I[e].y);
+      const double2 eh = Eh[e];
+      if (stage == 1) {
+        const double2 k1 = zmul(eh, k), ai = zmul(eh, A[e]);
+        AI[e] = ai;
+        acc[e] = zaxpy(ai, h / 6.0, k1);
+        x = zaxpy(ai, 0.5 * h, k1);
+      } else if (stage == 2) {
+        acc[e] = zaxpy(acc[e], h / 3.0, k);
+        x = zaxpy(AI[e], 0.5 * h, k);
+      } else if (stage == 3) {
+        acc[e] = zaxpy(acc[e], h / 3.0, k);
+        x = zmul(eh, zaxpy(AI[e], h, k));
+      } else {
+        x = zaxpy(zmul(eh, acc[e]), h / 6.0, k);
+        A[e] = x;
+      }
+    }
+    X[e] = mk<R>((R)x.x, (R)x.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 helpers used once per propagation
 // ---------------------------------------------------------------------------
 // out_p = scale * DFT_DIR(in_p) for each mode row p (grid N), n <= 8192.

@@ -11,3 +11,8 @@ int gm_profile_f64(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, doub
 }
 
 int gm_prop_setup_f64(int device) { return gm_prop::setup_device<double>(device); }
+
+int gm_rk4ip_f64(gm_job* jb, const double* A0, bool dev_io, double L, double h, double* Aout, gmmnlse_stats* st,
+                 cudaStream_t s) {
+  return gm_prop::rk4ip_impl<double>(jb, A0, dev_io, L, h, Aout, st, s);
+}

@@ -952,6 +952,142 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
 }
 
 // ---------------------------------------------------------------------------
+// RK4IP on the same kernels (the split-step comparator of Sec. III.D): each
+// step of h evaluates N four times, one after the other, as K1 -> K2/K3 ->
+// K4 on a single slice of phase 1 (loop state at iteration 0, geometry of
+// M = 0), with k_rk4_stage between them.  The field between steps is FP64.
+// Host-driven launches, no graph; the phase tables are taken for (h/2, 1)
+// and marked stale for the next MPA call.
+// ---------------------------------------------------------------------------
+template <typename R>
+static int rk4ip_impl(gm_job* jb, const double* A0, bool dev_io, double L, double h, double* Aout,
+                      gmmnlse_stats* st, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  long steps = 0;
+  int rem = 0;
+  int rc = gm_schedule(L, h, 1, &steps, &rem);
+  if (rc) return rc;
+  const size_t Nn = (size_t)c->N * c->n;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  double2* tin = jb->io;
+  if (dev_io) {
+    CK(cudaMemcpyAsync(tin, A0, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::memcpy(jb->h_io, A0, Nn * 16);
+    CK(cudaMemcpyAsync(tin, jb->h_io, Nn * 16, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(jb->flag, 0, sizeof(int), s));
+  k_nonfinite<<<elementwise_blocks(Nn), 256, 0, s>>>(tin, Nn, jb->flag);
+  int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, jb->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hflag) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GMMNLSE_E_INVALID;
+  }
+  // RK4 state: field A, AI = Eh A, the stage sum (FP64 [N][Nt] each)
+  double2* buf = nullptr;
+  if (cudaMalloc(&buf, 3 * Nn * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GMMNLSE_E_NOMEM;
+  }
+  double2 *Ast = buf, *AI = buf + Nn, *acc = buf + 2 * Nn;
+  rc = fft64(c, jb->io + Nn, tin, jb->psi0, c->N, +1, 1.0, s);
+  if (rc) {
+    cudaFree(buf);
+    return rc;
+  }
+  CK(cudaMemcpyAsync(Ast, jb->psi0, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  // E_1 and EM64[0] = exp(i beta h/2); the MPA's tables are rebuilt next time
+  k_phase_tables<R><<<elementwise_blocks(2 * Nn), 256, 0, s>>>(c->beta, (int)Nn, 1, 0.5 * h, 0, (cplx<R>*)jb->E,
+                                                               jb->EM64);
+  CK(cudaGetLastError());
+  jb->tab_dz = -1.0;
+  jb->tab_M = -1;
+  LoopState hl = {};
+  hl.status = ST_OK;
+  *jb->h_ls = hl;
+  CK(cudaMemcpyAsync(jb->ls, jb->h_ls, sizeof(LoopState), cudaMemcpyHostToDevice, s));
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0, jb->ls->spec);
+  const Geo g = make_geo<R>(c, 0, 0.5 * h);
+  const int eb = elementwise_blocks(Nn);
+  cplx<R>* X = (cplx<R>*)jb->psiR;
+  const cplx<R>* I0 = (const cplx<R>*)jb->I;
+  k_rk4_stage<R><<<eb, 256, 0, s>>>(0, Nn, h, Ast, AI, acc, I0, jb->EM64, X);
+  for (long k = 0; k < steps; ++k) {
+    for (int q = 1; q <= 4; ++q) {
+      launch_k1<R>(jb, g, s);
+      if (c->lr) {
+        launch_lr_z<R>(jb, g, s);
+        if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
+        launch_lr_r<R>(jb, g, s);
+      } else {
+        if (c->raman_mode) launch_k2<R>(jb, g, s);
+        if (c->tc) launch_tc<R>(jb, g, s);
+        else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
+      }
+      launch_k4<R>(jb, g, s);
+      k_rk4_stage<R><<<eb, 256, 0, s>>>(q, Nn, h, Ast, AI, acc, I0, jb->EM64, X);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      cudaStreamSynchronize(s);
+      cudaFree(buf);
+      return GMMNLSE_E_CUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(jb->psi0, Ast, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, c->N, c->n, c->prm.dt, c->omega0,
+                                                     jb->ls->spec + 2);
+  CK(cudaMemsetAsync(jb->flag, 0, sizeof(int), s));
+  k_nonfinite<<<elementwise_blocks(Nn), 256, 0, s>>>(jb->psi0, Nn, jb->flag);
+  rc = fft64(c, jb->io + Nn, jb->psi0, jb->io, c->N, -1, 1.0 / c->n, s);
+  if (rc) return rc;
+  if (dev_io) {
+    CK(cudaMemcpyAsync(Aout, jb->io, Nn * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(jb->h_io, jb->io, Nn * 16, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hflag, jb->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  if (!dev_io) std::memcpy(Aout, jb->h_io, Nn * 16);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const LoopState& hs = *jb->h_ls;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->long_steps = (int)steps;
+    st->z = (double)steps * h;
+    st->iters_total = (int)(4 * steps);  // evaluations of N
+    st->iters_min = steps > 0 ? 4 : 0;
+    st->iters_max = steps > 0 ? 4 : 0;
+    st->energy_in = hs.spec[0] * c->prm.dt / c->n;
+    st->photons_in = hs.spec[1];
+    st->energy_out = hs.spec[2] * c->prm.dt / c->n;
+    st->photons_out = hs.spec[3];
+    st->ms = ms;
+    st->coupling_rank = c->lr ? c->r : c->K;
+  }
+  if (hs.tc_err) {
+    gm_set_last_error_text("tensor-core contraction: a wait for its operands timed out");
+    return GMMNLSE_E_CUDA;
+  }
+  if (hflag) return GMMNLSE_E_NONFINITE;
+  return GMMNLSE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Per-kernel timing of one MPA iteration (used for the roofline report)
 // ---------------------------------------------------------------------------
 template <typename R>

@@ -99,3 +99,7 @@ def test_choose_m_rejects_bad_arguments_before_any_cuda_call(lib):
     best = C.c_int(0)
     buf = (C.c_double * 4)()
     assert lib.gmmnlse_choose_m(None, buf, 1e-4, 1e-8, cand, 2, 10, buf, None, C.byref(best)) == B.E_INVALID
+
+
+def test_rk4ip_rejects_null_handles(lib):
+    assert lib.gmmnlse_propagate_rk4ip(None, None, 1e-3, 1e-4, None, None) == B.E_INVALID
