@@ -72,6 +72,14 @@ def random_mode_weights(num_modes: int, seed: int) -> np.ndarray:
     return w / math.sqrt(float(np.sum(np.abs(w) ** 2)))
 
 
+def coupling_matrix(num_modes: int, scale: float, seed: int, symmetric: bool = True) -> np.ndarray:
+    """Real linear mode coupling Q[n][p] [1/m] with normal entries times
+    scale (symmetrised when `symmetric`, as a real index perturbation makes
+    it), standing in for disorder coupling coefficients."""
+    g = SplitMix64(seed).normals(num_modes * num_modes).reshape(num_modes, num_modes) * scale
+    return 0.5 * (g + g.T) if symmetric else g
+
+
 # ----------------------------------------------------------------------------
 # Material and grids
 # ----------------------------------------------------------------------------

@@ -1,0 +1,84 @@
+"""Pins of the oracle's linear mode coupling C_p = i sum_n Q_np A_n (Sec. IV,
+"Linear mode coupling including disorder"), an added term of Eq. 1's right-
+hand side.  Without dispersion and nonlinearity the equation is the linear
+system dA/dz = X A with X = i Q^T, and each integrator's step has a closed
+form; with a per-mode propagation constant the exact field is a matrix
+exponential."""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle as O
+from paper_1708_05324_b300 import inputs as I
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _linear_fiber(N=3, Nt=64, beta0=None, Q=None):
+    prob = I.workload("C1", Nt=Nt, dt=2e-12 / Nt, fR=0.0, energy=1e-9)
+    beta = np.zeros((prob.N, Nt)) if beta0 is None else np.repeat(np.asarray(beta0)[:, None], Nt, axis=1)
+    fib = O.Fiber.from_problem(prob, beta=beta, n2=0.0, Q=Q)
+    return prob, fib
+
+
+Q3 = I.coupling_matrix(3, 40.0, seed=21, symmetric=False)  # not symmetric: a transpose shows
+
+
+def test_converged_mpa_is_the_cayley_step_of_the_coupling():
+    """The trapezoid rule on dA/dz = X A gives A_j = (1 - dz X/2)^-1 (1 + dz X/2) A_{j-1}."""
+    prob, fib = _linear_fiber(Q=Q3)
+    dz, steps = 1e-3, 12
+    X = 1j * Q3.T
+    C = np.linalg.solve(np.eye(3) - 0.5 * dz * X, np.eye(3) + 0.5 * dz * X)
+    exact = np.linalg.matrix_power(C, steps) @ prob.A0
+    out, st = O.mpa_propagate(fib, prob.A0, steps * dz, dz, 5, 1e-15)
+    assert rel(out, exact) < 1e-12
+
+
+def test_rk4ip_step_is_the_fourth_order_taylor_polynomial():
+    prob, fib = _linear_fiber(Q=Q3)
+    h, steps = 2e-3, 7
+    Y = 1j * h * Q3.T
+    T4 = np.eye(3) + Y + Y @ Y / 2 + Y @ Y @ Y / 6 + Y @ Y @ Y @ Y / 24
+    exact = np.linalg.matrix_power(T4, steps) @ prob.A0
+    assert rel(O.rk4ip_propagate(fib, prob.A0, steps * h, h), exact) < 1e-12
+
+
+def test_coupling_with_dispersion_converges_to_the_matrix_exponential():
+    """dA/dz = i (B + Q^T) A, B = diag(beta_p): the interaction picture must
+    rotate the coupled modes by their own beta (a swapped phase fails); the
+    MPA's error falls 4x per halving of dz, RK4IP's 16x."""
+    b = np.array([0.0, 900.0, 2100.0])
+    prob, fib = _linear_fiber(beta0=b, Q=Q3)
+    L = 6e-3
+    exact = sl.expm(1j * L * (np.diag(b) + Q3.T)) @ prob.A0
+    e = [rel(O.mpa_propagate(fib, prob.A0, L, L / k, 4, 1e-15)[0], exact) for k in (24, 48)]
+    assert e[0] < 1e-3
+    assert e[0] / e[1] == pytest.approx(4.0, rel=0.05)
+    r = [rel(O.rk4ip_propagate(fib, prob.A0, L, L / k), exact) for k in (12, 24)]
+    assert r[0] / r[1] == pytest.approx(16.0, rel=0.1)
+
+
+def test_symmetric_coupling_conserves_energy_with_kerr_and_a_skewed_one_does_not():
+    """i Q^T is anti-Hermitian exactly when Q is symmetric: then Q moves energy
+    between modes and keeps the total (Kerr without self-steepening conserves
+    it too)."""
+    prob = I.workload("C1", Nt=128, dt=2e-12 / 128, fR=0.0, energy=10e-9)
+    e0 = O.energy_spectral(O.freq_from_time(prob.A0))
+    Qs = I.coupling_matrix(3, 40.0, seed=22, symmetric=True)
+    drift = {}
+    for name, Q in (("none", None), ("sym", Qs), ("skew", Q3)):
+        fib = O.Fiber.from_problem(prob, self_steepening=False, Q=Q)
+        out, _ = O.mpa_propagate(fib, prob.A0, 4e-3, 1e-4, 10, 1e-14)
+        drift[name] = abs(O.energy_spectral(O.freq_from_time(out)) / e0 - 1)
+        if name == "sym":
+            moved = out
+    # the trapezoid's own step error with Kerr, not the coupling's
+    assert drift["sym"] < 1e-5 and drift["sym"] < 3 * drift["none"] + 1e-9
+    # energy moved between modes
+    m0 = np.sum(abs(prob.A0) ** 2, axis=1)
+    m1 = np.sum(abs(moved) ** 2, axis=1)
+    assert np.max(abs(m1 - m0)) / np.sum(m0) > 1e-3
+    assert drift["skew"] > 1e-3
