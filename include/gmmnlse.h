@@ -162,6 +162,25 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
                       double tol, double* Aout, gmmnlse_stats* st);
 
 /*
+ * gmmnlse_set_linear_coupling -- add linear mode coupling to the right-hand
+ * side of Eq. 1 (Sec. IV, "Linear mode coupling including disorder"):
+ * C_p = i sum_n Q_np A_n, with Q constant along the fiber.
+ *
+ *   Q   [N][N] real, Q[n][p] = Q_np [1/m] (row n, column p), host pointer;
+ *       NULL removes the term.  Copied; the caller keeps its array.
+ *
+ * The term joins the integrand of the MPA and the nonlinear operator of
+ * gmmnlse_propagate_rk4ip, in the context's precision.  Q symmetric keeps
+ * the total energy (i Q^T anti-Hermitian); any real Q is accepted.
+ * Call it between propagations: it waits for the context's stream and
+ * retires the context's captured graphs; server requests on this context
+ * must not be in flight.  gmmnlse_propagate_noalloc returns
+ * GMMNLSE_E_UNSUPPORTED while a Q is set.  Non-finite entries give
+ * GMMNLSE_E_INVALID; a failed device allocation GMMNLSE_E_NOMEM.
+ */
+int gmmnlse_set_linear_coupling(gmmnlse_ctx* ctx, const double* Q);
+
+/*
  * gmmnlse_propagate_rk4ip -- the split-step comparator of the MPA (Sec. III.D,
  * Fig. 3): fourth-order Runge-Kutta in the interaction picture (RK4IP), one
  * step of h after another, each step four evaluations of the nonlinear

@@ -27,7 +27,7 @@ EXPORTS = [
     "gmmnlse_last_error", "gmmnlse_request_bytes", "gmmnlse_server_create",
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
-    "gmmnlse_propagate_rk4ip",
+    "gmmnlse_propagate_rk4ip", "gmmnlse_set_linear_coupling",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(Stats)]
     lib.gmmnlse_server_destroy.argtypes = [vp]
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.gmmnlse_set_linear_coupling.argtypes = [vp, vp]
     lib.gmmnlse_propagate_rk4ip.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(Stats)]
     lib.gmmnlse_choose_m.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.c_int, C.c_int, vp, vp,
                                      C.POINTER(C.c_int)]
@@ -164,6 +165,16 @@ class Context:
         if check and rc not in (OK,):
             raise GmmnlseError(rc, "gmmnlse_propagate")
         return out, st.as_dict(), rc
+
+    def set_linear_coupling(self, Q):
+        """gmmnlse_set_linear_coupling: Q [N][N] real (Q[n][p]), or None to remove."""
+        if Q is not None:
+            Q = np.ascontiguousarray(Q, dtype=np.float64)
+            if Q.shape != (self.N, self.N):
+                raise ValueError(f"Q must be [{self.N}][{self.N}]")
+        rc = self.lib.gmmnlse_set_linear_coupling(self.handle, _ptr(Q))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_set_linear_coupling")
 
     def propagate_rk4ip(self, A0, L, h, out=None, check=True):
         """gmmnlse_propagate_rk4ip: (Aout, stats dict, status); A0/out as for propagate."""

@@ -47,6 +47,7 @@ struct gm_job {
     int Mj = -1;
     int which = 0;
     double dz = 0.0;  // the kernels' parameters (dz/2 of the trapezoid) are baked into the graph
+    int qv = -1;      // the context's Q version the graph was built with
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
   } graphs[2];
@@ -65,6 +66,8 @@ struct gmmnlse_ctx {
   bool fp64;
   double fR, omega0, gamma0;
   double* beta = nullptr;       // [N][n]
+  double* Q = nullptr;          // [N][N] linear mode coupling Q[n][p] (device), or none
+  int qv = 0;                   // bumped at every change of Q (graphs record the one they hold)
   double2* tw64 = nullptr;      // [n] + radix-16 pass tables of n
   double2* tw64h = nullptr;     // [n/2] + pass tables of n/2
   float2* tw32 = nullptr;       // [n] + pass tables of n

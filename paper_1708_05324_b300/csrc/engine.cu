@@ -145,6 +145,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   if (!c) return;
   if (c->job) free_job(c->job);
   cudaFree(c->beta);
+  cudaFree(c->Q);
   cudaFree(c->tw64);
   cudaFree(c->tw64h);
   cudaFree(c->tw32);
@@ -886,6 +887,31 @@ extern "C" int gmmnlse_propagate_rk4ip(gmmnlse_ctx* c, const double* A0, double 
   }
   return c->fp64 ? gm_rk4ip_f64(c->job, A0, c->prm.io_device != 0, L, h, Aout, st, c->stream)
                  : gm_rk4ip_f32(c->job, A0, c->prm.io_device != 0, L, h, Aout, st, c->stream);
+}
+
+extern "C" int gmmnlse_set_linear_coupling(gmmnlse_ctx* c, const double* Q) {
+  if (!c) return GMMNLSE_E_INVALID;
+  const size_t NN = (size_t)c->N * c->N;
+  if (Q)
+    for (size_t i = 0; i < NN; ++i)
+      if (!std::isfinite(Q[i])) return GMMNLSE_E_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->qv += 1;  // graphs built before this call no longer apply
+  if (!Q) {
+    cudaFree(c->Q);
+    c->Q = nullptr;
+    return GMMNLSE_OK;
+  }
+  if (!c->Q && cudaMalloc(&c->Q, NN * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->Q = nullptr;
+    return GMMNLSE_E_NOMEM;
+  }
+  if (cudaMemcpy(c->Q, Q, NN * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return GMMNLSE_E_CUDA;
+  return GMMNLSE_OK;
 }
 
 extern "C" int gmmnlse_choose_m(gmmnlse_ctx* c, const double* A0, double dz, double tol,

@@ -623,6 +623,47 @@ __global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Linear mode coupling C_p = i sum_n Q_np A_n (Sec. IV), added to the
+// integrand after K4: I_j,p += exp(-i beta_p j dz) i sum_n Q_np A~_n,j with
+// A~_n,j = (psi_n + dpsi_n,j) E_n,j, the spectrum K1 transformed (Q does not
+// depend on time, so it acts on every frequency alike).  Slices follow K1:
+// j = 0 only in the first iteration, dpsi only after it.  One thread per
+// (substep, frequency), all modes; Q[n][p] FP64, used in R.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const cplx<R>* __restrict__ psiR,
+                                  const cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ E,
+                                  cplx<R>* __restrict__ I, const LoopState* __restrict__ ls) {
+  const int N = g.N, n = g.n, iter = ls->iter;
+  const size_t total = (size_t)(g.M + 1) * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i / n), q = (int)(i - (size_t)j * n);
+    if (iter > 0 && j == 0) continue;
+    for (int p = 0; p < N; ++p) {
+      R cx = 0, cy = 0;
+      for (int m = 0; m < N; ++m) {
+        cplx<R> a = psiR[(size_t)m * n + q];
+        if (iter > 0) {
+          const cplx<R> d = dpsi[((size_t)(j - 1) * N + m) * n + q];
+          a.x += d.x;
+          a.y += d.y;
+        }
+        const cplx<R> e = E[((size_t)j * N + m) * n + q];
+        const R w = (R)Q[(size_t)m * N + p];
+        cx += w * (a.x * e.x - a.y * e.y);
+        cy += w * (a.x * e.y + a.y * e.x);
+      }
+      // i (cx + i cy) = -cy + i cx, times conj(E_p,j)
+      const cplx<R> e = E[((size_t)j * N + p) * n + q];
+      cplx<R>* o = I + ((size_t)j * N + p) * n + q;
+      const R tx = -cy, ty = cx;
+      o->x += tx * e.x + ty * e.y;
+      o->y += ty * e.x - tx * e.y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // RK4IP, the split-step comparator of the MPA (Sec. III.D, Fig. 3): fourth-
 // order Runge-Kutta in the interaction picture with its origin half a step
 // in, so exp(D h/2) is applied three times per step.  The nonlinear operator

@@ -103,3 +103,7 @@ def test_choose_m_rejects_bad_arguments_before_any_cuda_call(lib):
 
 def test_rk4ip_rejects_null_handles(lib):
     assert lib.gmmnlse_propagate_rk4ip(None, None, 1e-3, 1e-4, None, None) == B.E_INVALID
+
+
+def test_set_linear_coupling_rejects_a_null_handle(lib):
+    assert lib.gmmnlse_set_linear_coupling(None, None) == B.E_INVALID

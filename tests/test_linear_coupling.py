@@ -1,0 +1,133 @@
+"""Linear mode coupling C_p = i sum_n Q_np A_n (Sec. IV) on the GPU: the MPA
+and the RK4IP comparator with gmmnlse_set_linear_coupling, element by element
+against the oracle."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1708_05324_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+L, DZ, M, TOL = 1e-3, 1e-4, 5, 1e-13
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def problem(N, Nt, fR):
+    return I.grin_problem("lc", N=N, Nt=Nt, dt=2e-12 / Nt, kind="gaussian", fwhm=150e-15, energy=20e-9,
+                          L=L, dz=DZ, M=M, tol=TOL, seed=17, fR=fR, s_from="gh")
+
+
+def coupling(N):
+    # not symmetric, so that a transposed Q or a swapped phase shows
+    return I.coupling_matrix(N, 40.0, seed=31 + N, symmetric=False)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_mpa(N, Nt, fR, with_q=True):
+    prob = problem(N, Nt, fR)
+    fib = O.Fiber.from_problem(prob, Q=coupling(N) if with_q else None)
+    return O.mpa_propagate(fib, prob.A0, L, DZ, M, TOL)[0]
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_rk4(N, Nt, fR):
+    prob = problem(N, Nt, fR)
+    return O.rk4ip_propagate(O.Fiber.from_problem(prob, Q=coupling(N)), prob.A0, L, DZ)
+
+
+def context(prob, precision):
+    from paper_1708_05324_b300 import binding as B
+    return B.Context.from_problem(prob, precision=precision, device=0)
+
+
+CASES = [(1, 128, 0.18), (3, 256, 0.18), (6, 1024, 0.18), (10, 256, 0.18), (15, 256, 0.0)]
+
+
+@pytest.mark.parametrize("N,Nt,fR", CASES)
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_mpa_with_linear_coupling_matches_the_oracle(N, Nt, fR, precision, bar):
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(N, Nt, fR)
+    ref = oracle_mpa(N, Nt, fR)
+    assert rel(ref, oracle_mpa(N, Nt, fR, False)) > 100 * bar  # the term matters at this bar
+    ctx = context(prob, precision)
+    try:
+        ctx.set_linear_coupling(coupling(N))
+        out, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)
+    finally:
+        ctx.close()
+    assert rc == B.OK
+    assert rel(out, ref) < bar
+
+
+@pytest.mark.parametrize("N", [10, 15])
+def test_linear_coupling_beside_the_tensor_core_contraction(N):
+    from paper_1708_05324_b300 import binding as B
+    fR = 0.18 if N == 10 else 0.0
+    prob = problem(N, 256, fR)
+    ctx = context(prob, "bf16")
+    try:
+        ctx.set_linear_coupling(coupling(N))
+        out, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)
+    finally:
+        ctx.close()
+    assert rc == B.OK
+    assert rel(out, oracle_mpa(N, 256, fR)) < 1e-5
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_rk4ip_with_linear_coupling_matches_the_oracle(precision, bar):
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(6, 1024, 0.18)
+    ctx = context(prob, precision)
+    try:
+        ctx.set_linear_coupling(coupling(6))
+        out, _, rc = ctx.propagate_rk4ip(prob.A0, L, DZ)
+    finally:
+        ctx.close()
+    assert rc == B.OK
+    assert rel(out, oracle_rk4(6, 1024, 0.18)) < bar
+
+
+def test_setting_and_removing_q_between_propagations_retires_the_graphs():
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(3, 256, 0.18)
+    with_q, without = oracle_mpa(3, 256, 0.18), oracle_mpa(3, 256, 0.18, False)
+    ctx = context(prob, "fp64")
+    try:
+        a, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)  # builds the graph without the term
+        assert rc == B.OK and rel(a, without) < 1e-10
+        ctx.set_linear_coupling(coupling(3))
+        b, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)
+        assert rc == B.OK and rel(b, with_q) < 1e-10
+        ctx.set_linear_coupling(None)
+        c, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)
+        assert rc == B.OK and rel(c, without) < 1e-10
+    finally:
+        ctx.close()
+
+
+def test_linear_coupling_rejections():
+    import ctypes as C
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(3, 256, 0.18)
+    ctx = context(prob, "fp32")
+    try:
+        bad = coupling(3)
+        bad[1, 2] = np.inf
+        with pytest.raises(B.GmmnlseError):
+            ctx.set_linear_coupling(bad)
+        ctx.set_linear_coupling(coupling(3))
+        out = np.empty_like(prob.A0)
+        st = B.Stats()
+        rc = ctx.lib.gmmnlse_propagate_noalloc(ctx.handle, prob.A0.ctypes.data, L, DZ, M, TOL,
+                                               out.ctypes.data, C.byref(st))
+        assert rc == B.E_UNSUPPORTED
+    finally:
+        ctx.close()
