@@ -60,11 +60,14 @@ class Fiber:
     Raman response h_R [Nt] sampled at t_k = k dt (1/s), time step dt (s),
     centre wavelength lam0 (m), n2 (m^2/W) and the self-steepening switch."""
 
-    def __init__(self, beta, SK, SR, fR, hR, dt, lam0, n2, self_steepening=True, Q=None):
+    def __init__(self, beta, SK, SR, fR, hR, dt, lam0, n2, self_steepening=True, Q=None, gain=None):
         self.beta = np.asarray(beta, dtype=np.float64)
         # linear mode coupling Q[n][p] (Sec. IV, "Linear mode coupling"): the
         # extra right-hand-side term C_p = i sum_n Q_np A_n, or None
         self.Q = None if Q is None else np.asarray(Q, dtype=np.float64)
+        # small-signal field gain g_p [1/m] (Sec. IV, "Saturating gain", its
+        # lowest order): the extra term g_p A_p, or None
+        self.gain = None if gain is None else np.asarray(gain, dtype=np.float64)
         self.N, self.Nt = self.beta.shape
         self.SK = np.asarray(SK, dtype=np.float64)
         self.SR = None if SR is None else np.asarray(SR, dtype=np.float64)
@@ -145,13 +148,16 @@ def nonlinear_bracket(fib: Fiber, A):
 
 def nonlinear_operator(fib: Fiber, Aw):
     """N(A~) = i (n2 w0/c) s(w) F{bracket(F^-1 A~)} for a spectral field A~,
-    plus the linear mode coupling C_p = i sum_n Q_np A~_n when the fiber has
-    one (Sec. IV: a term added to the right-hand side of Eq. 1; Q does not
-    depend on time, so it acts on each frequency alike)."""
+    plus the linear mode coupling C_p = i sum_n Q_np A~_n and the small-signal
+    gain g_p A~_p when the fiber has them (Sec. IV: terms added to the right-
+    hand side of Eq. 1; neither depends on time, so each acts on every
+    frequency alike)."""
     NL = nonlinear_bracket(fib, time_from_freq(Aw))
     out = 1j * fib.gamma0 * fib.shock * freq_from_time(NL)
     if fib.Q is not None:
         out = out + 1j * (fib.Q.T @ Aw)  # (Q^T A)_p = sum_n Q[n][p] A_n
+    if fib.gain is not None:
+        out = out + fib.gain[:, None] * Aw
     return out
 
 

@@ -82,3 +82,32 @@ def test_symmetric_coupling_conserves_energy_with_kerr_and_a_skewed_one_does_not
     m1 = np.sum(abs(moved) ** 2, axis=1)
     assert np.max(abs(m1 - m0)) / np.sum(m0) > 1e-3
     assert drift["skew"] > 1e-3
+
+
+G3 = np.array([3.0, -5.0, 11.0])  # per-mode field gain [1/m]; distinct, so a mode mix-up shows
+
+
+def test_gain_steps_are_the_cayley_and_taylor_factors():
+    """dA_p/dz = g_p A_p alone: the converged trapezoid multiplies mode p by
+    (1 + g dz/2)/(1 - g dz/2) per substep, RK4IP by 1 + x + x^2/2 + x^3/6 +
+    x^4/24 (x = g h) per step."""
+    prob, fib = _linear_fiber()
+    fib = O.Fiber.from_problem(prob, beta=fib.beta, n2=0.0, gain=G3)
+    dz, steps = 1e-3, 10
+    cay = ((1 + 0.5 * dz * G3) / (1 - 0.5 * dz * G3)) ** steps
+    out, _ = O.mpa_propagate(fib, prob.A0, steps * dz, dz, 5, 1e-15)
+    assert rel(out, cay[:, None] * prob.A0) < 1e-12
+    x = G3 * dz
+    tay = (1 + x + x ** 2 / 2 + x ** 3 / 6 + x ** 4 / 24) ** steps
+    assert rel(O.rk4ip_propagate(fib, prob.A0, steps * dz, dz), tay[:, None] * prob.A0) < 1e-12
+
+
+def test_gain_with_coupling_and_dispersion_converges_to_the_matrix_exponential():
+    b = np.array([0.0, 900.0, 2100.0])
+    prob, fib = _linear_fiber(beta0=b, Q=Q3)
+    fib = O.Fiber.from_problem(prob, beta=fib.beta, n2=0.0, Q=Q3, gain=G3)
+    L = 6e-3
+    exact = sl.expm(L * (1j * np.diag(b) + 1j * Q3.T + np.diag(G3))) @ prob.A0
+    e = [rel(O.mpa_propagate(fib, prob.A0, L, L / k, 4, 1e-15)[0], exact) for k in (24, 48)]
+    assert e[0] < 1e-3
+    assert e[0] / e[1] == pytest.approx(4.0, rel=0.05)
