@@ -181,6 +181,21 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
 int gmmnlse_set_linear_coupling(gmmnlse_ctx* ctx, const double* Q);
 
 /*
+ * gmmnlse_set_gain -- add small-signal gain to the right-hand side of Eq. 1:
+ * the term g_p A_p, the lowest order of the gain of Sec. IV ("Saturating
+ * gain"; the saturation terms are not built).
+ *
+ *   g   [N] field gain g_p [1/m] per mode (energy grows as exp(2 g_p z)
+ *       alone), host pointer; NULL removes the term.  Copied.
+ *
+ * Same rules as gmmnlse_set_linear_coupling: both terms may be set at once;
+ * call between propagations; gmmnlse_propagate_noalloc returns
+ * GMMNLSE_E_UNSUPPORTED while either is set; non-finite g gives
+ * GMMNLSE_E_INVALID.
+ */
+int gmmnlse_set_gain(gmmnlse_ctx* ctx, const double* g);
+
+/*
  * gmmnlse_propagate_rk4ip -- the split-step comparator of the MPA (Sec. III.D,
  * Fig. 3): fourth-order Runge-Kutta in the interaction picture (RK4IP), one
  * step of h after another, each step four evaluations of the nonlinear

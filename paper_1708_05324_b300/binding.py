@@ -28,6 +28,7 @@ EXPORTS = [
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
     "gmmnlse_propagate_rk4ip", "gmmnlse_set_linear_coupling",
+    "gmmnlse_set_gain",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_server_destroy.argtypes = [vp]
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.gmmnlse_set_linear_coupling.argtypes = [vp, vp]
+    lib.gmmnlse_set_gain.argtypes = [vp, vp]
     lib.gmmnlse_propagate_rk4ip.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(Stats)]
     lib.gmmnlse_choose_m.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.c_int, C.c_int, vp, vp,
                                      C.POINTER(C.c_int)]
@@ -175,6 +177,16 @@ class Context:
         rc = self.lib.gmmnlse_set_linear_coupling(self.handle, _ptr(Q))
         if rc != OK:
             raise GmmnlseError(rc, "gmmnlse_set_linear_coupling")
+
+    def set_gain(self, g):
+        """gmmnlse_set_gain: g [N] field gain per mode [1/m], or None to remove."""
+        if g is not None:
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            if g.shape != (self.N,):
+                raise ValueError(f"g must be [{self.N}]")
+        rc = self.lib.gmmnlse_set_gain(self.handle, _ptr(g))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_set_gain")
 
     def propagate_rk4ip(self, A0, L, h, out=None, check=True):
         """gmmnlse_propagate_rk4ip: (Aout, stats dict, status); A0/out as for propagate."""

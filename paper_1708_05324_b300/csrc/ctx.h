@@ -67,7 +67,8 @@ struct gmmnlse_ctx {
   double fR, omega0, gamma0;
   double* beta = nullptr;       // [N][n]
   double* Q = nullptr;          // [N][N] linear mode coupling Q[n][p] (device), or none
-  int qv = 0;                   // bumped at every change of Q (graphs record the one they hold)
+  double* gain = nullptr;       // [N] small-signal field gain g_p (device), or none
+  int qv = 0;                   // bumped at every change of Q or gain (graphs record the one they hold)
   double2* tw64 = nullptr;      // [n] + radix-16 pass tables of n
   double2* tw64h = nullptr;     // [n/2] + pass tables of n/2
   float2* tw32 = nullptr;       // [n] + pass tables of n

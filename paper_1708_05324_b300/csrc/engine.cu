@@ -146,6 +146,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   if (c->job) free_job(c->job);
   cudaFree(c->beta);
   cudaFree(c->Q);
+  cudaFree(c->gain);
   cudaFree(c->tw64);
   cudaFree(c->tw64h);
   cudaFree(c->tw32);
@@ -911,6 +912,31 @@ extern "C" int gmmnlse_set_linear_coupling(gmmnlse_ctx* c, const double* Q) {
     return GMMNLSE_E_NOMEM;
   }
   if (cudaMemcpy(c->Q, Q, NN * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return GMMNLSE_E_CUDA;
+  return GMMNLSE_OK;
+}
+
+extern "C" int gmmnlse_set_gain(gmmnlse_ctx* c, const double* g) {
+  if (!c) return GMMNLSE_E_INVALID;
+  const size_t N = (size_t)c->N;
+  if (g)
+    for (size_t i = 0; i < N; ++i)
+      if (!std::isfinite(g[i])) return GMMNLSE_E_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->qv += 1;  // graphs built before this call no longer apply
+  if (!g) {
+    cudaFree(c->gain);
+    c->gain = nullptr;
+    return GMMNLSE_OK;
+  }
+  if (!c->gain && cudaMalloc(&c->gain, N * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->gain = nullptr;
+    return GMMNLSE_E_NOMEM;
+  }
+  if (cudaMemcpy(c->gain, g, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return GMMNLSE_E_CUDA;
   return GMMNLSE_OK;
 }
 

@@ -623,15 +623,18 @@ __global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Linear mode coupling C_p = i sum_n Q_np A_n (Sec. IV), added to the
-// integrand after K4: I_j,p += exp(-i beta_p j dz) i sum_n Q_np A~_n,j with
-// A~_n,j = (psi_n + dpsi_n,j) E_n,j, the spectrum K1 transformed (Q does not
-// depend on time, so it acts on every frequency alike).  Slices follow K1:
-// j = 0 only in the first iteration, dpsi only after it.  One thread per
-// (substep, frequency), all modes; Q[n][p] FP64, used in R.
+// Linear terms of Sec. IV, added to the integrand after K4: the mode
+// coupling C_p = i sum_n Q_np A_n, I_j,p += exp(-i beta_p j dz) i sum_n Q_np
+// A~_n,j with A~_n,j = (psi_n + dpsi_n,j) E_n,j, the spectrum K1 transformed,
+// and the small-signal gain g_p A_p, I_j,p += g_p (psi_p + dpsi_p,j) (its
+// phase and the interaction picture's cancel).  Neither depends on time, so
+// each acts on every frequency alike.  Slices follow K1: j = 0 only in the
+// first iteration, dpsi only after it.  One thread per (substep, frequency),
+// all modes; Q[n][p] and g_p FP64 (either may be absent), used in R.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const cplx<R>* __restrict__ psiR,
+__global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const double* __restrict__ gain,
+                                  const cplx<R>* __restrict__ psiR,
                                   const cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ E,
                                   cplx<R>* __restrict__ I, const LoopState* __restrict__ ls) {
   const int N = g.N, n = g.n, iter = ls->iter;
@@ -640,6 +643,19 @@ __global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const cpl
     const int j = (int)(i / n), q = (int)(i - (size_t)j * n);
     if (iter > 0 && j == 0) continue;
     for (int p = 0; p < N; ++p) {
+      cplx<R>* o = I + ((size_t)j * N + p) * n + q;
+      if (gain) {
+        cplx<R> a = psiR[(size_t)p * n + q];
+        if (iter > 0) {
+          const cplx<R> d = dpsi[((size_t)(j - 1) * N + p) * n + q];
+          a.x += d.x;
+          a.y += d.y;
+        }
+        const R gp = (R)gain[p];
+        o->x += gp * a.x;
+        o->y += gp * a.y;
+      }
+      if (!Q) continue;
       R cx = 0, cy = 0;
       for (int m = 0; m < N; ++m) {
         cplx<R> a = psiR[(size_t)m * n + q];
@@ -655,7 +671,6 @@ __global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const cpl
       }
       // i (cx + i cy) = -cy + i cx, times conj(E_p,j)
       const cplx<R> e = E[((size_t)j * N + p) * n + q];
-      cplx<R>* o = I + ((size_t)j * N + p) * n + q;
       const R tx = -cy, ty = cx;
       o->x += tx * e.x + ty * e.y;
       o->y += ty * e.x - tx * e.y;

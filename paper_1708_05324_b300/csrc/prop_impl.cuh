@@ -588,7 +588,7 @@ template <typename R>
 static void launch_linear_coupling(gm_job* jb, const Geo& g, cudaStream_t s) {
   const gmmnlse_ctx* c = jb->ctx;
   k_linear_coupling<R><<<elementwise_blocks((size_t)(g.M + 1) * c->n), 256, 0, s>>>(
-      g, c->Q, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E, (cplx<R>*)jb->I, jb->ls);
+      g, c->Q, c->gain, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E, (cplx<R>*)jb->I, jb->ls);
 }
 
 // K5 with the convergence decision in its last block
@@ -616,7 +616,7 @@ static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraph
     else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
   }
   launch_k4<R>(jb, g, s);
-  if (c->Q) launch_linear_coupling<R>(jb, g, s);
+  if (c->Q || c->gain) launch_linear_coupling<R>(jb, g, s);
   launch_k5<R>(jb, g, s, h, use_cond);
 }
 
@@ -672,7 +672,7 @@ static void with_long_step(const gmmnlse_ctx* c, F&& f) {
 template <typename R>
 static int long_step_grid(gm_job* jb) {
   const gmmnlse_ctx* c = jb->ctx;
-  if (persist_disabled() || c->N > 8 || c->tc || c->lr || c->Q || c->n < 2048 || c->n > 8192) return 0;
+  if (persist_disabled() || c->N > 8 || c->tc || c->lr || c->Q || c->gain || c->n < 2048 || c->n > 8192) return 0;
   const int threads = c->n / 16;
   const size_t smem = fft_smem<R>(c->n);
   int sms = 0, per_sm = 0;
@@ -742,7 +742,7 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   cudaGraphNode_t nStep;
   CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
   cudaGraph_t gS = cp.conditional.phGraph_out[0];
-  if (jb->persist_grid > 0 && !jb->ctx->Q) {
+  if (jb->persist_grid > 0 && !jb->ctx->Q && !jb->ctx->gain) {
     // long-step body: the cooperative long-step kernel (iterations inside)
     CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     launch_long_step<R>(jb, g, which, cs, hStep, 1);
@@ -822,7 +822,7 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
   }
   // host-driven loop over the same kernels
   for (int st = 0; st < count; ++st) {
-    if (jb->persist_grid > 0 && !jb->ctx->Q) {
+    if (jb->persist_grid > 0 && !jb->ctx->Q && !jb->ctx->gain) {
       launch_long_step<R>(jb, g, which, s, 0, 0);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -1045,7 +1045,7 @@ static int rk4ip_impl(gm_job* jb, const double* A0, bool dev_io, double L, doubl
         else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
       }
       launch_k4<R>(jb, g, s);
-      if (c->Q) launch_linear_coupling<R>(jb, g, s);
+      if (c->Q || c->gain) launch_linear_coupling<R>(jb, g, s);
       k_rk4_stage<R><<<eb, 256, 0, s>>>(q, Nn, h, Ast, AI, acc, I0, jb->EM64, X);
     }
     if (cudaGetLastError() != cudaSuccess) {

@@ -107,3 +107,7 @@ def test_rk4ip_rejects_null_handles(lib):
 
 def test_set_linear_coupling_rejects_a_null_handle(lib):
     assert lib.gmmnlse_set_linear_coupling(None, None) == B.E_INVALID
+
+
+def test_set_gain_rejects_a_null_handle(lib):
+    assert lib.gmmnlse_set_gain(None, None) == B.E_INVALID

@@ -131,3 +131,36 @@ def test_linear_coupling_rejections():
         assert rc == B.E_UNSUPPORTED
     finally:
         ctx.close()
+
+
+GAIN = {3: np.array([4.0, -6.0, 9.0]), 6: np.linspace(-8.0, 8.0, 6), 10: np.linspace(-5.0, 12.0, 10)}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_gain(N, Nt, fR, with_q):
+    prob = problem(N, Nt, fR)
+    fib = O.Fiber.from_problem(prob, Q=coupling(N) if with_q else None, gain=GAIN[N])
+    return O.mpa_propagate(fib, prob.A0, L, DZ, M, TOL)[0], O.rk4ip_propagate(fib, prob.A0, L, DZ)
+
+
+@pytest.mark.parametrize("N,Nt,fR,with_q", [(3, 256, 0.18, False), (6, 1024, 0.18, True), (10, 256, 0.18, True)])
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_gain_matches_the_oracle_in_the_mpa_and_rk4ip(N, Nt, fR, with_q, precision, bar):
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(N, Nt, fR)
+    ref_mpa, ref_rk = oracle_gain(N, Nt, fR, with_q)
+    assert rel(ref_mpa, oracle_mpa(N, Nt, fR, with_q)) > 100 * bar
+    ctx = context(prob, precision)
+    try:
+        ctx.set_gain(GAIN[N])
+        if with_q:
+            ctx.set_linear_coupling(coupling(N))
+        out, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)
+        assert rc == B.OK and rel(out, ref_mpa) < bar
+        out, _, rc = ctx.propagate_rk4ip(prob.A0, L, DZ)
+        assert rc == B.OK and rel(out, ref_rk) < bar
+        ctx.set_gain(None)  # back to the coupling alone (or nothing)
+        out, _, rc = ctx.propagate(prob.A0, L, DZ, M, TOL)
+        assert rc == B.OK and rel(out, oracle_mpa(N, Nt, fR, with_q)) < bar
+    finally:
+        ctx.close()
