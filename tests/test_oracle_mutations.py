@@ -69,8 +69,8 @@ MUTATIONS = {
         ("self.gamma0 = self.n2 * self.omega0 / C_LIGHT", "self.gamma0 = self.n2 * 1.8e15 / C_LIGHT * 1.01"),
     ],
     "nonlinear_sign": [
-        ("return 1j * fib.gamma0 * fib.shock * freq_from_time(NL)",
-         "return -1j * fib.gamma0 * fib.shock * freq_from_time(NL)"),
+        ("out = 1j * fib.gamma0 * fib.shock * freq_from_time(NL)",
+         "out = -1j * fib.gamma0 * fib.shock * freq_from_time(NL)"),
     ],
     "eps_not_relative": [
         ("eps = math.sqrt(diff / size) if (finite and size > 0)", "eps = math.sqrt(diff) if (finite and size > 0)"),
@@ -123,5 +123,38 @@ def test_planted_mistake_is_caught(name, monkeypatch):
                 try:
                     _run_pin(fn)
                 except Exception as e:  # AssertionError, or a blow-up
+                    caught.append((fn.__name__, type(e).__name__))
+    assert caught, f"no pin detects the planted mistake {name!r}"
+
+
+# Planted mistakes in the added right-hand-side terms of Sec. IV (mode
+# coupling and gain), run against the pins of tests/test_oracle_coupling.py.
+import test_oracle_coupling as coupling_pins  # noqa: E402
+
+COUPLING_MUTATIONS = {
+    "coupling_transposed": [("out = out + 1j * (fib.Q.T @ Aw)", "out = out + 1j * (fib.Q @ Aw)")],
+    "coupling_sign": [("out = out + 1j * (fib.Q.T @ Aw)", "out = out - 1j * (fib.Q.T @ Aw)")],
+    "gain_on_the_wrong_modes": [("out = out + fib.gain[:, None] * Aw", "out = out + fib.gain[::-1, None] * Aw")],
+}
+
+COUPLING_PIN_TESTS = [getattr(coupling_pins, name) for name in dir(coupling_pins)
+                      if name.startswith("test_") and callable(getattr(coupling_pins, name))]
+
+
+@pytest.mark.parametrize("name", sorted(COUPLING_MUTATIONS))
+def test_planted_mistake_in_an_added_term_is_caught(name, monkeypatch):
+    mod = _mutated_module(COUPLING_MUTATIONS[name])
+    for attr in dir(oracle):
+        if not attr.startswith("_") and hasattr(mod, attr) and attr != "gmmnlse":
+            monkeypatch.setattr(oracle, attr, getattr(mod, attr))
+    monkeypatch.setattr(oracle, "gmmnlse", mod)
+    caught = []
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        with np.errstate(all="ignore"):
+            for fn in COUPLING_PIN_TESTS:
+                try:
+                    _run_pin(fn)
+                except Exception as e:
                     caught.append((fn.__name__, type(e).__name__))
     assert caught, f"no pin detects the planted mistake {name!r}"
