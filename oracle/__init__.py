@@ -8,7 +8,9 @@ arrays (paper_1708_05324_b300.inputs), which hold none of the method's
 arithmetic.
 
 Parity status per function: every public function in oracle.gmmnlse is pinned
-by a test in tests/test_oracle_pins.py against closed forms, invariants or
+by a test in tests/test_oracle_pins.py (the added Sec. IV terms in
+tests/test_oracle_coupling.py, the overlap tensor in tests/test_oracle_overlap.py)
+against closed forms, invariants or
 brute force (see each docstring).  None is "parity unpinned".
 """
 from .gmmnlse import (  # noqa: F401
@@ -18,6 +20,7 @@ from .gmmnlse import (  # noqa: F401
     energy_spectral,
     freq_from_time,
     integrand,
+    overlap_tensor,
     iptrap_propagate,
     kerr_sum,
     mpa_long_step,

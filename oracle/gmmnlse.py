@@ -297,6 +297,20 @@ def rk4ip_propagate(fib: Fiber, A0, L, h):
 
 
 # ----------------------------------------------------------------------------
+# Mode overlap tensor (Eq. 2)
+# ----------------------------------------------------------------------------
+def overlap_tensor(F, dA):
+    """S_plmn = int F_p F_l F_m F_n dA / sqrt(int F_p^2 dA int F_l^2 dA
+    int F_m^2 dA int F_n^2 dA) (Eq. 2) for real profiles F [N][G] sampled on
+    G grid cells of area dA: the integrals as plain sums over the cells."""
+    F = np.asarray(F, dtype=np.float64)
+    norm = np.sum(F * F, axis=1) * dA
+    quad = np.einsum("pg,lg,mg,ng->plmn", F, F, F, F) * dA
+    den = np.sqrt(np.einsum("p,l,m,n->plmn", norm, norm, norm, norm))
+    return quad / den
+
+
+# ----------------------------------------------------------------------------
 # Invariants
 # ----------------------------------------------------------------------------
 def energy_spectral(Aw):
