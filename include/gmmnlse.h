@@ -196,6 +196,25 @@ int gmmnlse_set_linear_coupling(gmmnlse_ctx* ctx, const double* Q);
 int gmmnlse_set_gain(gmmnlse_ctx* ctx, const double* g);
 
 /*
+ * gmmnlse_overlap_tensor -- the mode overlap tensor of Eq. 2 from mode
+ * profiles on a grid, computed on the GPU: S_plmn = int F_p F_l F_m F_n dA /
+ * sqrt(int F_p^2 dA int F_l^2 dA int F_m^2 dA int F_n^2 dA), the integrals
+ * as sums over the grid cells (one FP64 Gram GEMM of the N(N+1)/2 pair
+ * products F_m F_n over the cells, then spread with the norms).
+ *
+ *   device  CUDA device to run on.
+ *   F       [N][G] real mode profiles (any scale), host pointer.
+ *   N       modes, 1..64.   G  grid cells (>= 1).   dA  cell area [m^2].
+ *   S       [N][N][N][N] output [1/m^2], host pointer, ready for
+ *           gmmnlse_create (real and fully symmetric up to rounding).
+ *
+ * Synchronous; allocates device memory for the call (8 (N G + K^2) bytes,
+ * K = N(N+1)/2; GMMNLSE_E_NOMEM if that fails).  Non-finite F, a profile
+ * that is zero everywhere, or bad sizes give GMMNLSE_E_INVALID.
+ */
+int gmmnlse_overlap_tensor(int device, const double* F, int N, long long G, double dA, double* S);
+
+/*
  * gmmnlse_propagate_rk4ip -- the split-step comparator of the MPA (Sec. III.D,
  * Fig. 3): fourth-order Runge-Kutta in the interaction picture (RK4IP), one
  * step of h after another, each step four evaluations of the nonlinear

@@ -28,7 +28,7 @@ EXPORTS = [
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
     "gmmnlse_propagate_rk4ip", "gmmnlse_set_linear_coupling",
-    "gmmnlse_set_gain",
+    "gmmnlse_set_gain", "gmmnlse_overlap_tensor",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.gmmnlse_set_linear_coupling.argtypes = [vp, vp]
     lib.gmmnlse_set_gain.argtypes = [vp, vp]
+    lib.gmmnlse_overlap_tensor.argtypes = [C.c_int, vp, C.c_int, C.c_longlong, C.c_double, vp]
     lib.gmmnlse_propagate_rk4ip.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(Stats)]
     lib.gmmnlse_choose_m.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.c_int, C.c_int, vp, vp,
                                      C.POINTER(C.c_int)]
@@ -120,6 +121,19 @@ def _ptr(a):
             raise ValueError("tensor must be contiguous")
         return a.data_ptr()
     raise TypeError(type(a))
+
+
+def overlap_tensor(F, dA, device=0):
+    """gmmnlse_overlap_tensor: S [N][N][N][N] (Eq. 2) from profiles F [N][G]."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    if F.ndim != 2:
+        raise ValueError("F must be [N][G]")
+    N, G = F.shape
+    S = np.empty((N, N, N, N))
+    rc = load().gmmnlse_overlap_tensor(int(device), _ptr(F), N, G, float(dA), _ptr(S))
+    if rc != OK:
+        raise GmmnlseError(rc, "gmmnlse_overlap_tensor")
+    return S
 
 
 class Context:

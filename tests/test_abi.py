@@ -111,3 +111,11 @@ def test_set_linear_coupling_rejects_a_null_handle(lib):
 
 def test_set_gain_rejects_a_null_handle(lib):
     assert lib.gmmnlse_set_gain(None, None) == B.E_INVALID
+
+
+def test_overlap_tensor_validates_on_the_host(lib):
+    F = np.ones(6)
+    S = np.empty(16)
+    assert lib.gmmnlse_overlap_tensor(0, None, 2, 3, 1e-12, S.ctypes.data) == B.E_INVALID
+    assert lib.gmmnlse_overlap_tensor(0, F.ctypes.data, 0, 3, 1e-12, S.ctypes.data) == B.E_INVALID
+    assert lib.gmmnlse_overlap_tensor(0, F.ctypes.data, 2, 3, -1.0, S.ctypes.data) == B.E_INVALID
