@@ -164,3 +164,38 @@ def test_gain_matches_the_oracle_in_the_mpa_and_rk4ip(N, Nt, fR, with_q, precisi
         assert rc == B.OK and rel(out, oracle_mpa(N, Nt, fR, with_q)) < bar
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_served_requests_take_the_linear_terms(precision, bar):
+    """Server requests build their own graphs from the context: with Q and a
+    gain set, each served result equals the oracle, in a mix with a context
+    that has neither."""
+    import time
+    from paper_1708_05324_b300 import binding as B
+    pq, p0 = problem(6, 1024, 0.18), problem(3, 256, 0.18)
+    cq, c0 = context(pq, precision), context(p0, precision)
+    srv = B.Server(hbm_budget=1 << 30, max_inflight=4)
+    try:
+        cq.set_linear_coupling(coupling(6))
+        cq.set_gain(GAIN[6])
+        jobs = []
+        for _ in range(2):
+            jobs.append((srv.submit(cq, pq.A0, L, DZ, M, TOL), 6, 1024, oracle_gain(6, 1024, 0.18, True)[0]))
+            jobs.append((srv.submit(c0, p0.A0, L, DZ, M, TOL), 3, 256, oracle_mpa(3, 256, 0.18, False)))
+        t0 = time.time()
+        left = list(jobs)
+        while left:
+            for job in list(left):
+                t, N, Nt, ref = job
+                rc, a, _ = srv.poll(t, N, Nt)
+                if rc == B.PENDING:
+                    continue
+                assert rc == B.OK and rel(a, ref) < bar
+                left.remove(job)
+            assert time.time() - t0 < 120, "requests did not finish"
+            time.sleep(0.002)
+    finally:
+        srv.close()
+        cq.close()
+        c0.close()
