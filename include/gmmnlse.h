@@ -54,9 +54,10 @@ typedef enum gmmnlse_precision {
     GMMNLSE_FP32 = 1,       /* FFTs, contraction and iterates FP32 */
     GMMNLSE_MIXED_BF16 = 2, /* FP32, coupling contraction on tensor cores in
                                BF16 with hi/lo split operands, FP32 accumulate,
-                               for N = 9..16 and 42 with Nt a multiple of 128
-                               (other N > 8: GMMNLSE_E_UNSUPPORTED); for N <= 8
-                               the FP32 register contraction, faster there */
+                               for every N = 9..64 with Nt a multiple of 128
+                               (Nt not a multiple of 128 with N > 8:
+                               GMMNLSE_E_UNSUPPORTED); for N <= 8 the FP32
+                               register contraction, faster there */
     GMMNLSE_MIXED_FP16 = 3, /* as MIXED_BF16 with FP16 hi/lo operands, each
                                scaled by a power of two into FP16 range (exact
                                to undo); N and Nt limits as MIXED_BF16 */

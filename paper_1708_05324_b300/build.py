@@ -6,6 +6,7 @@ import hashlib
 import os
 import subprocess
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -31,6 +32,29 @@ def sources():
     return out
 
 
+def _includes(path, seen=None):
+    """The file and every local header it includes, transitively."""
+    import re
+    seen = set() if seen is None else seen
+    if path in seen or not os.path.exists(path):
+        return seen
+    seen.add(path)
+    with open(path) as f:
+        for inc in re.findall(r'^\s*#\s*include\s+"([^"]+)"', f.read(), re.M):
+            _includes(os.path.normpath(os.path.join(os.path.dirname(path), inc)), seen)
+    return seen
+
+
+def _unit_stamp(src):
+    h = hashlib.sha256()
+    h.update(" ".join(FLAGS).encode())
+    for p in sorted(_includes(src)):
+        h.update(p.encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _stamp():
     h = hashlib.sha256()
     for p in sources():
@@ -41,7 +65,9 @@ def _stamp():
     return h.hexdigest()
 
 
-def build(force=False, verbose=False):
+def build(force=False, verbose=False, jobs=None):
+    """Compile every translation unit under csrc/ whose sources changed (its
+    own hash of the unit and the headers it includes) and link the library."""
     stamp_file = LIB + ".stamp"
     stamp = _stamp()
     if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
@@ -51,20 +77,44 @@ def build(force=False, verbose=False):
     build_dir = os.path.join(HERE, "_build")
     os.makedirs(build_dir, exist_ok=True)
     cu = [p for p in sources() if p.endswith(".cu")]
-    procs = []
+    todo = []
     for src in cu:
         obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         objs.append(obj)
-        cmd = [NVCC, *FLAGS, "-c", src, "-o", obj]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-    for cmd, pr in procs:
-        out, _ = pr.communicate()
-        if pr.returncode != 0:
-            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + out.decode(errors="replace"))
-        if verbose and out:
-            sys.stdout.write(out.decode(errors="replace"))
+        us = _unit_stamp(src)
+        ok = (not force and os.path.exists(obj) and os.path.exists(obj + ".stamp")
+              and open(obj + ".stamp").read().strip() == us)
+        if not ok:
+            cmd = [NVCC, *FLAGS, "-c", src, "-o", obj]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            todo.append((cmd, obj, us))
+    # the slowest units first (the long-step drivers and the widest GEMM
+    # instantiations), at most `jobs` compilers at once
+    slow = ("persist_", "prop_", "tc_lsum_", "tc_store", "noalloc")
+    todo.sort(key=lambda t: next((i for i, k in enumerate(slow) if k in os.path.basename(t[1])), len(slow)))
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    running, failed = [], None
+    while (todo and failed is None) or running:
+        while todo and failed is None and len(running) < jobs:
+            cmd, obj, us = todo.pop(0)
+            running.append((cmd, obj, us, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        time.sleep(0.2)
+        for r in list(running):
+            cmd, obj, us, pr = r
+            if pr.poll() is None:
+                continue
+            running.remove(r)
+            out = pr.stdout.read()
+            if pr.returncode != 0:
+                failed = failed or ("nvcc failed:\n" + " ".join(cmd) + "\n" + out.decode(errors="replace"))
+                continue
+            if verbose and out:
+                sys.stdout.write(out.decode(errors="replace"))
+            with open(obj + ".stamp", "w") as f:
+                f.write(us)
+    if failed:
+        raise RuntimeError(failed)
     tmp = LIB + ".tmp"
     cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs, "-lcuda"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)

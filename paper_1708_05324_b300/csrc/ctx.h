@@ -103,6 +103,12 @@ struct gmmnlse_ctx {
   int eW16 = 0, eX16 = 0;        // FP16 exponents of W and X
   __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
   CUtensorMap mapWhi, mapWlo, mapXhi, mapXlo;
+  // limit of every mbarrier wait of the tensor-core GEMMs [ns] (1 s;
+  // GMMNLSE_TC_WAIT_MS at create), and the test hook GMMNLSE_TC_STALL that
+  // makes their MMA issuer wait on a barrier nothing completes (1: in the
+  // single-CTA GEMMs, 2: in all of them)
+  unsigned long long tc_wait_ns = 1000000000ull;
+  int tc_stall = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   gm_job* job = nullptr;        // workspace of gmmnlse_propagate

@@ -25,6 +25,7 @@
 #include "kernels.cuh"
 #include "ctx.h"
 #include "tc_contract.cuh"
+#include "tc_gemm.h"
 
 using namespace gm;
 
@@ -427,13 +428,13 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   }
 
   // mixed precision: the contraction runs on the tensor cores where it is a
-  // dense GEMM, N >= 9 (built for N = 9..16 and 42, the 42-mode step-index
-  // workload, with Nt a multiple of the 128-point tile); for N <= 8 the FP32
-  // register contraction is faster than a GEMM that small and is used instead
+  // dense GEMM, N >= 9 (with Nt a multiple of the 128-point tile); for N <= 8
+  // the FP32 register contraction is faster than a GEMM that small and is
+  // used instead
   const bool mixed = prm->precision == GMMNLSE_MIXED_BF16 || prm->precision == GMMNLSE_MIXED_FP16 ||
                      prm->precision == GMMNLSE_MIXED_TF32;
   if (mixed && N > 8) {
-    if (!(N <= 16 || N == 42) || n % TC_PTS != 0) {
+    if (N < TC_MIN_N || N > TC_MAX_N || n % TC_PTS != 0) {
       delete c;
       return GMMNLSE_E_UNSUPPORTED;
     }
@@ -443,6 +444,12 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     c->tf32 = prm->precision == GMMNLSE_MIXED_TF32;
     c->KKp = (c->KK + TC_KC - 1) / TC_KC * TC_KC;
     c->tc_rows = (c->P + NB - 1) / NB * NB;
+    if (const char* w = getenv("GMMNLSE_TC_WAIT_MS")) {
+      const double ms = atof(w);
+      if (ms > 0 && ms <= 60000) c->tc_wait_ns = (unsigned long long)(ms * 1e6);
+    }
+    const char* stall = getenv("GMMNLSE_TC_STALL");
+    c->tc_stall = stall ? std::max(0, std::min(2, atoi(stall))) : 0;
   }
 
   // CUDA-core tiled contraction (N > 8): G transposed, padded to whole tiles
@@ -458,7 +465,11 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   // at most 3/4 of K; GMMNLSE_DENSE=1 keeps the dense contraction
   std::vector<double> Xd, Wd, Gt_rows, Xt_rows;
   const char* dense_env = getenv("GMMNLSE_DENSE");
-  if (N > 8 && c->raman_mode != 2 && !(dense_env && dense_env[0] == '1')) {
+  // (with 16-bit tensor-core operands the first GEMM forms U from A in the
+  // kernel, which stages the A of at most U_FIT_N modes: more modes keep the
+  // dense coupling)
+  const bool lr_fits = !(c->tc && !c->tf32 && N > U_FIT_N);
+  if (N > 8 && c->raman_mode != 2 && lr_fits && !(dense_env && dense_env[0] == '1')) {
     // the dropped part of the coupling (columns below tol x the largest)
     // stays under the rounding of the working precision's contraction:
     // 1e-12 for FP64; 1e-9 for FP32 and the mixed precisions, whose FP32
@@ -706,9 +717,9 @@ static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int bo
 }
 
 // Map of a row-grouped [rows/8][KKp/EPC][8][EPC] coupling operand; box = one
-// K chunk of NB / CL rows (one CTA's share of a row block of NB rows in a
-// cluster of CL = tc_cluster(NB)).
-static int tc_map_rows(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int NB, bool f16, bool tf32) {
+// K chunk of NB / cl rows (one CTA's share of a row block of NB rows when
+// cl = 2 CTAs share each MMA).
+static int tc_map_rows(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int NB, bool f16, bool tf32, int cl) {
   EncodeTiledFn enc;
   const int rc = tc_encoder(&enc);
   if (rc) return rc;
@@ -716,7 +727,7 @@ static int tc_map_rows(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, i
   const cuuint64_t kq = (cuuint64_t)(KKp / epc);
   const cuuint64_t dims[4] = {(cuuint64_t)epc, 8, kq, rows / 8};
   const cuuint64_t strides[3] = {16, 128, kq * 128};
-  const cuuint32_t box[4] = {(cuuint32_t)epc, 8, (cuuint32_t)(TC_KC / epc), (cuuint32_t)(NB / 8 / tc_cluster(NB))};
+  const cuuint32_t box[4] = {(cuuint32_t)epc, 8, (cuuint32_t)(TC_KC / epc), (cuuint32_t)(NB / 8 / cl)};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                       : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
@@ -732,13 +743,16 @@ static int tc_map_rows(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, i
 
 int gm_make_g_maps(gmmnlse_ctx* c) {
   const int NB = tc_row_block(c->P);
-  int rc = tc_map_rows(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
-  if (!rc) rc = tc_map_rows(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32);
+  // CTAs that share each MMA: as TcShape<..>::CL (the first low-rank GEMM
+  // with 16-bit operands forms U in the kernel and runs on single CTAs)
+  const int cl = tc_cluster(NB), cl1 = c->tf32 ? tc_cluster(c->NB1) : 1;
+  int rc = tc_map_rows(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32, cl);
+  if (!rc) rc = tc_map_rows(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32, cl);
   if (!rc && c->lr) {
-    rc = tc_map_rows(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
-    if (!rc) rc = tc_map_rows(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32);
-    if (!rc) rc = tc_map_rows(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
-    if (!rc) rc = tc_map_rows(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32);
+    rc = tc_map_rows(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32, cl1);
+    if (!rc) rc = tc_map_rows(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32, cl1);
+    if (!rc) rc = tc_map_rows(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32, cl);
+    if (!rc) rc = tc_map_rows(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32, cl);
   }
   return rc;
 }

@@ -15,9 +15,10 @@
 #include "../../include/gmmnlse.h"
 #include "ctx.h"
 #include "engine.h"
-#include "persist.cuh"
+#include "persist_api.h"
 #include "kernels.cuh"
 #include "tc_contract.cuh"
+#include "tc_gemm.h"
 
 #include <type_traits>
 
@@ -60,32 +61,6 @@ static int fft64(gmmnlse_ctx* c, double2* scratch, const double2* in, double2* o
   return GMMNLSE_OK;
 }
 
-// The tensor-core contraction is instantiated for these mode counts (l-sum
-// epilogue) and, for the first GEMM of the low-rank coupling, for every row
-// block NB = 16 .. 256 (store epilogue); each for 16-bit and TF32 operands.
-template <class F>
-static int tc_for_each_n(F&& f) {
-  int rc = GMMNLSE_OK;
-  auto one = [&](auto kern) {
-    if (!rc) rc = f(kern);
-  };
-#define GM_TC_N(N)                                            \
-  one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), 0, 2>); \
-  one(&k_tc_contract<N, tc_row_block(N * (N + 1) / 2), 0, 4>);
-  GM_TC_N(9) GM_TC_N(10) GM_TC_N(11) GM_TC_N(12) GM_TC_N(13) GM_TC_N(14) GM_TC_N(15) GM_TC_N(16) GM_TC_N(42)
-#undef GM_TC_N
-#define GM_TC_S(NB)                     \
-  one(&k_tc_contract<0, NB, 1, 2>);     \
-  one(&k_tc_contract<0, NB, 1, 4>);
-  GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
-  GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
-#undef GM_TC_S
-  return rc;
-}
-
-template <typename R, class F>
-static void with_long_step(const gmmnlse_ctx* c, F&& f);
-
 // Once per device: raise the shared-memory limit of this unit's kernels.
 template <typename R>
 static int setup_device(int dev) {
@@ -123,38 +98,20 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 0, 1>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 1, 0>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 1, 0>, A, sm));
-  if (std::is_same<R, float>::value) {
+  if constexpr (std::is_same<R, float>::value) {
     CK(cudaFuncSetAttribute(k_raman_vpack<16, 0>, A, sm));
     CK(cudaFuncSetAttribute(k_raman_vpack<32, 0>, A, sm));
     CK(cudaFuncSetAttribute(k_raman_vpack<16, 1>, A, sm));
     CK(cudaFuncSetAttribute(k_raman_vpack<32, 1>, A, sm));
-    const int rc = tc_for_each_n([&](auto kern) -> int {
-      cudaFuncAttributes fa;
-      CK(cudaFuncGetAttributes(&fa, kern));
-      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smax - (int)fa.sharedSizeBytes));
-      return GMMNLSE_OK;
-    });
-    if (rc) return rc;
+    if (gm_tc_setup(smax)) {
+      gm_set_last_error_text("tensor-core GEMM: shared-memory attribute");
+      return GMMNLSE_E_CUDA;
+    }
   }
-  {
-    // the long-step kernels (dynamic shared memory: one transform buffer)
-    gmmnlse_ctx probe;
-    for (int N = 1; N <= 8; ++N)
-      for (int mode = 0; mode < 3; ++mode) {
-        probe.N = N;
-        probe.raman_mode = mode;
-        int rc = GMMNLSE_OK;
-        with_long_step<R>(&probe, [&](auto kern) {
-          cudaFuncAttributes fa;
-          if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
-              cudaFuncSetAttribute(kern, A, smax - (int)fa.sharedSizeBytes) != cudaSuccess)
-            rc = GMMNLSE_E_CUDA;
-        });
-        if (rc) {
-          gm_set_last_error_text("long-step kernel: shared-memory attribute");
-          return rc;
-        }
-      }
+  // the long-step kernels (dynamic shared memory: one transform buffer)
+  if (persist_setup<R>(smax)) {
+    gm_set_last_error_text("long-step kernel: shared-memory attribute");
+    return GMMNLSE_E_CUDA;
   }
   CK(cudaFuncSetAttribute(k_fft64_rows<+1, 16>, A, sm));
   CK(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, A, sm));
@@ -300,74 +257,14 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_integrand<R, 16, 4>);
 }
 
-// CTAs of a tensor-core GEMM launch: CL x the clusters resident at once
-// (cudaOccupancyMaxActiveClusters, once per kernel), at most one cluster per
-// work item of CL x TPW point tiles.  A grid of more clusters than fit would
-// run the surplus as a second wave.
-static int tc_grid(const void* kern, size_t smem, int cl, int tpw, int ntiles, int threads) {
-  static std::mutex mu;
-  static std::map<const void*, int> resident;
-  int maxc = 0;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = resident.find(kern);
-    if (it != resident.end()) {
-      maxc = it->second;
-    } else {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(148 / cl * cl);
-      cfg.blockDim = dim3(threads);
-      cfg.dynamicSmemBytes = smem;
-      cudaLaunchAttribute at;
-      at.id = cudaLaunchAttributeClusterDimension;
-      at.val.clusterDim.x = (unsigned)cl;
-      at.val.clusterDim.y = 1;
-      at.val.clusterDim.z = 1;
-      cfg.attrs = &at;
-      cfg.numAttrs = 1;
-      if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) != cudaSuccess || maxc <= 0) {
-        (void)cudaGetLastError();
-        maxc = 148 / cl / 2;  // a safe guess: half the SMs
-      }
-      resident[kern] = maxc;
-    }
-  }
-  const int items = (ntiles + cl * tpw - 1) / (cl * tpw);
-  return cl * std::max(1, std::min(items, maxc));
-}
-
 // The tcgen05 GEMM with the l-sum epilogue: V operand maps mV*, coupling
-// operand maps mG*, over the mode count of the context; ES = 2 (BF16 / FP16)
-// or 4 (TF32).
-template <int ES>
-static void launch_tc_lsum_es(gm_job* jb, const Geo& g, cudaStream_t s, const CUtensorMap& mVhi,
-                              const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
-                              const TcArgs& a) {
-  gmmnlse_ctx* c = jb->ctx;
-  const int ntiles = (g.M + 1) * c->n / TC_PTS;
-  switch (c->N) {
-#define GM_TC_CASE(NN)                                                                                           \
-  case NN: {                                                                                                     \
-    constexpr int NB = tc_row_block(NN * (NN + 1) / 2);                                                          \
-    using Sh = TcShape<NN, NB, ES>;                                                                              \
-    auto kern = k_tc_contract<NN, NB, 0, ES>;                                                                    \
-    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles, Sh::THREADS));                 \
-    pdl_launch_cl(kern, grid, dim3(Sh::THREADS), Sh::SMEM, s, Sh::CL, mVhi, mVlo, mGhi, mGlo, a,                  \
-                  (const LoopState*)jb->ls);                                                                     \
-    break;                                                                                                       \
-  }
-    GM_TC_CASE(9) GM_TC_CASE(10) GM_TC_CASE(11) GM_TC_CASE(12) GM_TC_CASE(13) GM_TC_CASE(14)
-    GM_TC_CASE(15) GM_TC_CASE(16) GM_TC_CASE(42)
-#undef GM_TC_CASE
-    default: break;
-  }
-}
-
+// operand maps mG*, over the mode count of the context.
 static void launch_tc_lsum(gm_job* jb, const Geo& g, cudaStream_t s, const CUtensorMap& mVhi,
                            const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
                            const TcArgs& a) {
-  if (jb->ctx->tf32) launch_tc_lsum_es<4>(jb, g, s, mVhi, mVlo, mGhi, mGlo, a);
-  else launch_tc_lsum_es<2>(jb, g, s, mVhi, mVlo, mGhi, mGlo, a);
+  gmmnlse_ctx* c = jb->ctx;
+  TcLaunch L = {&mVhi, &mVlo, &mGhi, &mGlo, a, (const LoopState*)jb->ls, s, (g.M + 1) * c->n / TC_PTS, c->tf32};
+  gm_tc_lsum(c->N, L);
 }
 
 static TcArgs tc_args(gm_job* jb, const Geo& g) {
@@ -379,6 +276,8 @@ static TcArgs tc_args(gm_job* jb, const Geo& g) {
   a.A = (const float2*)jb->A;
   a.NL = (float2*)jb->NL;
   a.err = &jb->ls->tc_err;
+  a.wait_ns = c->tc_wait_ns;
+  a.stall = c->tc_stall;
   return a;
 }
 
@@ -442,28 +341,9 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
       a.nmodes = c->N;
       a.K = c->K;
       a.pairs = (const int2*)c->pairs;
-      const int ntiles = (int)(pts / TC_PTS);
-      auto store = [&](auto es) {
-        constexpr int ES = decltype(es)::value;
-        switch (c->NB1) {
-#define GM_TC_S(NB)                                                                                           \
-  case NB: {                                                                                                  \
-    using Sh = TcShape<0, NB, ES, 1>;                                                                         \
-    auto kern = k_tc_contract<0, NB, 1, ES>;                                                                  \
-    static_assert(!Sh::FU || U_FIT_N >= 42, "the fused U stages the A of up to 42 modes");                \
-    const dim3 grid(tc_grid((const void*)kern, Sh::SMEM, Sh::CL, Sh::TPW, ntiles, Sh::THREADS));              \
-    pdl_launch_cl(kern, grid, dim3(Sh::THREADS), Sh::SMEM, s, Sh::CL, jb->mapHi, jb->mapLo, c->mapWhi,        \
-                  c->mapWlo, a, (const LoopState*)jb->ls);                                                    \
-    break;                                                                                                    \
-  }
-          GM_TC_S(16) GM_TC_S(32) GM_TC_S(48) GM_TC_S(64) GM_TC_S(80) GM_TC_S(96) GM_TC_S(112) GM_TC_S(128)
-          GM_TC_S(144) GM_TC_S(160) GM_TC_S(176) GM_TC_S(192) GM_TC_S(208) GM_TC_S(224) GM_TC_S(240) GM_TC_S(256)
-#undef GM_TC_S
-          default: break;
-        }
-      };
-      if (c->tf32) store(std::integral_constant<int, 4>());
-      else store(std::integral_constant<int, 2>());
+      TcLaunch L = {&jb->mapHi, &jb->mapLo, &c->mapWhi, &c->mapWlo, a, (const LoopState*)jb->ls, s,
+                    (int)(pts / TC_PTS), c->tf32};
+      gm_tc_store(c->NB1, L);
     }
     return;
   }
@@ -630,101 +510,6 @@ static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, 
   pdl_launch(k_advance<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, jb->psi0, (cplx<R>*)jb->psiR,
              (const cplx<R>*)jb->dpsi, (const double2*)(jb->EM64 + (size_t)which * Nn), jb->ls, hStep, hIter,
              use_cond);
-}
-
-// ---------------------------------------------------------------------------
-// The long step as one cooperative kernel (persist.cuh): N <= 8 on the CUDA
-// cores with one-block transforms of 16 elements per thread (2048 <= n <=
-// 8192), opt-in with GMMNLSE_PERSIST=1.  On the 6-mode workload it measured
-// 89 us per iteration against 62 us for the kernel-per-step chain (the
-// combined kernel spills ~1 KB of registers in its transform phases, and
-// every phase waits for its slowest block), so the chain is the default.
-// ---------------------------------------------------------------------------
-static bool persist_disabled() {
-  const char* v = getenv("GMMNLSE_PERSIST");
-  return !(v && v[0] == '1');
-}
-
-// Calls f with the long-step kernel of this context's N and raman_mode.
-template <typename R, class F>
-static void with_long_step(const gmmnlse_ctx* c, F&& f) {
-  auto modes = [&](auto nc) {
-    constexpr int NN = decltype(nc)::value;
-    if (c->raman_mode == 0) f(k_long_step<R, NN, 0>);
-    else if (c->raman_mode == 1) f(k_long_step<R, NN, 1>);
-    else f(k_long_step<R, NN, 2>);
-  };
-  switch (c->N) {
-    case 1: modes(std::integral_constant<int, 1>()); break;
-    case 2: modes(std::integral_constant<int, 2>()); break;
-    case 3: modes(std::integral_constant<int, 3>()); break;
-    case 4: modes(std::integral_constant<int, 4>()); break;
-    case 5: modes(std::integral_constant<int, 5>()); break;
-    case 6: modes(std::integral_constant<int, 6>()); break;
-    case 7: modes(std::integral_constant<int, 7>()); break;
-    case 8: modes(std::integral_constant<int, 8>()); break;
-    default: break;
-  }
-}
-
-// Blocks of the long-step kernel for this job (every block resident), or 0
-// where it does not apply.
-template <typename R>
-static int long_step_grid(gm_job* jb) {
-  const gmmnlse_ctx* c = jb->ctx;
-  if (persist_disabled() || c->N > 8 || c->tc || c->lr || c->Q || c->gain || c->n < 2048 || c->n > 8192) return 0;
-  const int threads = c->n / 16;
-  const size_t smem = fft_smem<R>(c->n);
-  int sms = 0, per_sm = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->prm.device) != cudaSuccess) return 0;
-  int rc = -1;
-  with_long_step<R>(c, [&](auto kern) {
-    rc = (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-  });
-  if (rc != (int)cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    return 0;
-  }
-  return std::min(sms * per_sm, TRAPZ_MAX_BLOCKS);
-}
-
-// Zero the barrier counter, then the cooperative long-step kernel.
-template <typename R>
-static void launch_long_step(gm_job* jb, const Geo& g, int which, cudaStream_t s, cudaGraphConditionalHandle hStep,
-                             int use_cond) {
-  gmmnlse_ctx* c = jb->ctx;
-  const size_t Nn = (size_t)c->N * c->n;
-  StepArgs a;
-  a.psiR = jb->psiR;
-  a.dpsi = jb->dpsi;
-  a.E = jb->E;
-  a.A = jb->A;
-  a.Y = jb->V;
-  a.NL = jb->NL;
-  a.I = jb->I;
-  a.H = c->H;
-  a.fac = c->fac;
-  a.tw = twid<R>(c);
-  a.pairs = c->pairs;
-  a.G = c->G;
-  a.psi0 = jb->psi0;
-  a.EM = jb->EM64 + (size_t)which * Nn;
-  a.part = jb->part;
-  a.bar = jb->bar;
-  cudaMemsetAsync(jb->bar, 0, sizeof(unsigned), s);
-  with_long_step<R>(c, [&](auto kern) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(jb->persist_grid);
-    cfg.blockDim = dim3(c->n / 16);
-    cfg.dynamicSmemBytes = fft_smem<R>(c->n);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, g, a, jb->ls, hStep, use_cond);
-  });
 }
 
 template <typename R>

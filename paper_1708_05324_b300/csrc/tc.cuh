@@ -1,10 +1,13 @@
 // Blackwell (sm_100 family) tensor-core primitives used by the mixed-precision
-// coupling contraction: mbarriers, TMA tensor copies, TMEM allocation,
-// tcgen05.mma (kind::f16 / kind::tf32), tcgen05.ld and cluster multicast, as
-// inline PTX.
+// coupling contraction: mbarriers (local and remote arrivals), TMA tensor
+// copies, TMEM allocation, tcgen05.mma (kind::f16 / kind::tf32) issued by one
+// CTA or by a CTA pair (cta_group::2: one MMA of M = 256 over the two SMs of
+// a 2-CTA cluster, each CTA holding half of each operand), tcgen05.commit and
+// tcgen05.ld, as inline PTX.  No operand is multicast: every CTA loads its
+// own share of each tile from global memory.
 //
-// Every wait is bounded: a spin that exceeds its limit returns false and the
-// caller records an error instead of hanging the GPU.
+// Every wait is bounded in time (%globaltimer): a wait that exceeds its limit
+// returns false and the caller records an error instead of hanging the GPU.
 #pragma once
 
 #include <cuda.h>
@@ -14,7 +17,6 @@
 namespace gm {
 namespace tc {
 
-constexpr unsigned kSpinLimit = 1u << 26;  // ~tens of ms; far beyond any real wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -43,19 +45,47 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
-// Wait for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase with the given parity to complete (acquire at cluster
+// scope, so arrivals released by the peer CTA are seen); false once more
+// than limit_ns nanoseconds have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t limit_ns) {
   const uint32_t a = smem_addr(bar);
-  for (unsigned i = 0; i < kSpinLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+  for (int i = 0; i < 32; ++i)
+    if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try(a, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
-  return false;
+}
+
+// ---- cluster addressing ---------------------------------------------------
+// The shared::cluster address of the same shared-memory location in CTA
+// `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+// One arrival on an mbarrier of any CTA of the cluster (shared::cluster
+// address), releasing this thread's prior memory operations at cluster scope.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
 // ---- TMA -------------------------------------------------------------------
@@ -78,15 +108,24 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
       : "memory");
 }
-// The same copy multicast to the CTAs of the cluster in `mask`: the box lands
-// at the same shared-memory offset in each of them and counts on the
-// mbarrier at the same offset in each.
-__device__ __forceinline__ void tma_load_4d_mc(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                               uint64_t* bar, uint16_t mask) {
+
+// CTA-pair forms: the box lands in this CTA's shared memory and its bytes
+// count on the mbarrier at shared::cluster address `cbar`, which may be in
+// the peer CTA of the pair (the MMA-issuing CTA's barrier).
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                 uint32_t cbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
-      "[%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar)), "h"(mask)
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(cbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d_pair(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                                 uint32_t cbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(cbar)
       : "memory");
 }
 
@@ -102,15 +141,29 @@ __device__ __forceinline__ void cluster_sync() {
 }
 
 // ---- TMEM ------------------------------------------------------------------
-// Allocate ncols (power of two >= 32) TMEM columns; one full warp executes.
+// Allocate ncols (power of two >= 32) TMEM columns; one full warp executes
+// (with PAIR, one warp in each CTA of the pair, the same ncols: the columns
+// are allocated in both CTAs' TMEM at the same address).
+template <bool PAIR>
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, unsigned ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  if constexpr (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
 }
+template <bool PAIR>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, unsigned ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+  if constexpr (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 __device__ __forceinline__ void fence_before_sync() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -147,11 +200,27 @@ __host__ __device__ constexpr uint32_t idesc_mma(int M, int N, uint32_t fmt) {
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread: kind::f16 (K = 16
-// per instruction) or, with TF32, kind::tf32 (K = 8).
-template <bool TF32>
+// per instruction) or, with TF32, kind::tf32 (K = 8).  With PAIR the MMA
+// spans the CTA pair (cta_group::2): A has M = 256 rows, 128 in each CTA's
+// shared memory at the descriptor's address, B has its first N/2 rows in the
+// issuing CTA and the other N/2 in the peer, and D's rows 0..127 go to the
+// issuing CTA's TMEM, 128..255 to the peer's, at the same TMEM address.
+template <bool TF32, bool PAIR = false>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                     uint32_t accumulate) {
-  if constexpr (TF32) {
+  if constexpr (PAIR && TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else if constexpr (PAIR) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else if constexpr (TF32) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             d_tmem),
@@ -165,19 +234,15 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bd
         : "memory");
   }
 }
-// Arrive on the mbarrier once all prior MMAs of this thread have completed.
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-               : "memory");
-}
-
-// The same arrive on the mbarrier at this offset in every CTA of `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_addr(bar)),
-      "h"(mask)
-      : "memory");
+// One arrival on the mbarrier at shared::cluster address `cbar` (this CTA's
+// or, with PAIR, the peer's) once all prior MMAs of this thread have
+// completed.
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit(uint32_t cbar) {
+  if constexpr (PAIR)
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cbar) : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cbar) : "memory");
 }
 
 // 32 lanes x 32 bit, 16 consecutive columns: thread i of the warp receives row

@@ -28,24 +28,30 @@
 // while the MMAs of the next work item run.  A work item is (point tile, row
 // block); NL of a tile is written after its last row block.
 //
-// Clusters of CL CTAs (CL = 2 for row blocks of 64 rows and more) work on
-// CL point tiles at once with the same row-block and K-chunk sequence: each
-// CTA loads its own V tile and 1/CL of the coupling chunk, multicast into
-// every CTA of the cluster, so the coupling operand (the larger one, NB rows
-// against 128 points) crosses L2 once per CL tiles.  A stage is released
-// when the MMAs of every CTA of the cluster have read it (the MMA commit
-// arrives on the stage's barrier in each CTA).
+// Row blocks of NB >= 32 rows run on CTA pairs (2-CTA clusters, cta_group::2):
+// one MMA of M = 256 points (a 128-point tile in each CTA) by NB rows, the
+// first NB/2 coupling rows of each K chunk in the shared memory of CTA 0 and
+// the other NB/2 in CTA 1, so each CTA loads its own V tile and half of the
+// coupling chunk (plain TMA loads, no multicast) and the MMA reads both
+// halves.  Per SM and K chunk that is 16 KB of V and NB/2 rows of G instead of
+// NB rows, and the tensor cores read half of B from each SM's shared memory.
+// CTA 0 issues the MMAs; the copies of both CTAs count on CTA 0's stage
+// barrier; CTA 0's MMA commits release the stage in both CTAs and announce a
+// finished accumulator to both; each CTA's epilogue drains its own TMEM
+// (its tile's 128 points) and reports to CTA 0 by a remote arrival.
+// Row blocks below 32 rows, and the GEMM that forms U in the kernel, run on
+// single CTAs (cta_group::1).
 //
 // Operand layout (both K-major, no swizzle): core matrices of 8 rows x 8
 // elements (16 bytes).  V is stored [k/8][point][8]; in shared memory a K
 // chunk of 128 points is [4][128][8], so core matrices adjacent along K are
 // 128*16 bytes apart (LBO) and along the points 128 bytes (SBO).  The
 // coupling operand is stored row-grouped, [row/8][k/8][8][8]; a K chunk of
-// NB rows is [NB/8][4][8][8] in shared memory (LBO 128 bytes, SBO 512), and
-// the share of one CTA of a cluster (NB/CL rows) is a contiguous part of it.
+// NB/CL rows is [NB/(8 CL)][4][8][8] in shared memory (LBO 128 bytes, SBO
+// 512), one contiguous box of the row-grouped layout.
 //
-// Every mbarrier wait is bounded; on a timeout the kernel records an error
-// in *err and every role stops issuing work.
+// Every mbarrier wait is bounded in time (TcArgs::wait_ns); on a timeout the
+// kernel records an error in *err and every role stops issuing work.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -74,14 +80,17 @@ struct TcArgs {
   int zrows;         // OUT 1: rows stored (the rest is padding)
   int nmodes, K;     // U formed in the kernel: modes of A, pair columns
   const int2* pairs; // U formed in the kernel: (m, n) of column k
+  unsigned long long wait_ns;  // limit of every mbarrier wait [ns]
+  int stall;         // test hook: the MMA issuer waits on a barrier nothing completes,
+                     // 1: in single-CTA GEMMs, 2: in every GEMM
 };
 
 __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 15) / 16 * 16 : 256; }
 
-// CTAs per cluster of the GEMM with row blocks of NB rows: 4 from 128 rows
-// when NB is a multiple of 32, else 2 from 64 rows (NB is a multiple of 16),
-// so that each CTA's share is whole 8-row groups.
-__host__ __device__ constexpr int tc_cluster(int NB) { return (NB >= 128 && NB % 32 == 0) ? 4 : (NB >= 64 ? 2 : 1); }
+// CTAs per MMA of the GEMM with row blocks of NB rows (NB a multiple of 16):
+// a CTA pair from 32 rows (each CTA holds NB/2 rows, whole 8-row groups),
+// else one CTA.
+__host__ __device__ constexpr int tc_cluster(int NB) { return NB >= 32 ? 2 : 1; }
 
 // FP16 scale exponent of V: 2^eV (2 x the bound on |V|) < 2^14; the bound
 // is (1/Nt) sum_w |psi0|^2, summed at the start of the propagation.
@@ -126,10 +135,10 @@ template <> struct Split<2> {
 // chunk of U for the CTA's tile from A staged in shared memory and write it
 // to the stage as hi/lo (no packed U in HBM).  U_FIT_N bounds the modes of A
 // it stages.
-// TPW: point tiles per work item, sharing each stage's coupling chunk (two
-// MMAs of M = 128 into two accumulators): 2 for the store epilogue without
-// FU when two stages still fit, else 1.  NBUF: accumulator buffers in TMEM
-// (2 lets the epilogue drain one work item while the next one's MMAs run).
+// TPW: point tiles per work item and CTA, sharing each stage's coupling chunk
+// (TPW MMAs into TPW accumulators): 2 for the store epilogue without FU when
+// two stages still fit, else 1.  NBUF: accumulator buffers in TMEM (2 lets
+// the epilogue drain one work item while the next one's MMAs run).
 constexpr int U_FIT_N = 42, U_FIT_KKP = 928;  // N(N+1)/2 = 903 padded to 32
 template <int N, int NB, int ES = 2, int OUT = 0>
 struct TcShape {
@@ -138,14 +147,19 @@ struct TcShape {
   static constexpr int EPC = 16 / ES;                  // elements per core-matrix row
   static constexpr int KSTEPS = TC_KC * ES / 32;       // MMAs of 32 bytes of K per chunk
   static constexpr int V_BYTES = TC_PTS * TC_KC * ES;  // one of hi / lo, one tile
-  static constexpr int G_BYTES = NB * TC_KC * ES;
+  static constexpr int G_BYTES = NB * TC_KC * ES;      // one of hi / lo, all NB rows
   static constexpr bool FU = OUT == 1 && ES == 2;
+  // CTAs per MMA (2: CTA pair); the GEMM that forms U in the kernel runs on
+  // single CTAs (measured faster: its U producers are the limit, and a pair
+  // makes every K chunk wait for those of both CTAs)
+  static constexpr int CL = FU ? 1 : tc_cluster(NB);
+  static constexpr int G_HALF = G_BYTES / CL;          // this CTA's rows of a chunk (hi or lo)
   static constexpr int UW = FU ? 8 : 0;                // U-producer warps
   static constexpr int THREADS = 192 + 32 * UW;
   // A tile ([U_FIT_N][128] float2) and column table ([KKp] int2) of FU
   static constexpr int U_RESERVE = FU ? U_FIT_N * TC_PTS * 8 + U_FIT_KKP * 8 : 0;
-  static constexpr int TPW = (OUT == 1 && !FU && 2 * 2 * (2 * V_BYTES + G_BYTES) <= 200 * 1024) ? 2 : 1;
-  static constexpr int STAGE = 2 * (TPW * V_BYTES + G_BYTES);
+  static constexpr int TPW = (OUT == 1 && !FU && 2 * 2 * (2 * V_BYTES + G_HALF) <= 200 * 1024) ? 2 : 1;
+  static constexpr int STAGE = 2 * (TPW * V_BYTES + G_HALF);
   static constexpr int FIT = (200 * 1024 - U_RESERVE) / STAGE;
   static constexpr int STAGES = FIT < 2 ? 2 : (FIT > 6 ? 6 : FIT);
   static constexpr int ACC_COLS = TPW * NB;            // one accumulator buffer
@@ -153,8 +167,9 @@ struct TcShape {
   static constexpr int COLS = NBUF * ACC_COLS;
   static constexpr int TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + U_RESERVE;
-  static constexpr int CL = tc_cluster(NB);           // CTAs sharing each coupling chunk
-  static constexpr int G_SHARE = G_BYTES / CL;         // one CTA's share (hi or lo)
+  // bytes that complete a stage's barrier: both CTAs' copies (V tiles unless
+  // FU, and every coupling row of the chunk, hi and lo)
+  static constexpr int TX = FU ? 2 * G_BYTES : CL * STAGE;
 };
 
 // Row r of the reduced coupling matrix is the pair (p, l), p <= l, in the
@@ -229,34 +244,39 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
                                                          const LoopState* __restrict__ ls) {
   using S = TcShape<N, NB, ES, OUT>;
   constexpr int TPW = S::TPW, NBUF = S::NBUF, CL = S::CL;
-  constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1);
+  constexpr bool PAIR = CL == 2;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char* smem = tc_smem_raw + ((1024 - (tc::smem_addr(tc_smem_raw) & 1023)) & 1023);
-  __shared__ __align__(8) uint64_t full[S::STAGES], empty[S::STAGES], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t full[S::STAGES], empty[S::STAGES], acc_full[2], acc_empty[2], never;
   __shared__ uint32_t tmem_base;
   __shared__ int stop_flag;
   volatile int* stop = &stop_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t wait_ns = a.wait_ns;
 
   // FU: A tile [nmodes][128] and the column table after the stages
   float2* As = reinterpret_cast<float2*>(smem + (size_t)S::STAGES * S::STAGE);
   int2* Ps = reinterpret_cast<int2*>(As + (S::FU ? U_FIT_N * TC_PTS : 0));
+  const unsigned rank = PAIR ? tc::cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
   if (tid == 0) {
     for (int s = 0; s < S::STAGES; ++s) {
-      tc::mbar_init(&full[s], 1 + S::UW);  // the TMA producer (+ each U warp)
-      tc::mbar_init(&empty[s], CL);  // released by the MMAs of every CTA of the cluster
+      // (used in CTA 0) the TMA producer's arrival, plus one per U warp of each CTA
+      tc::mbar_init(&full[s], 1 + CL * S::UW);
+      tc::mbar_init(&empty[s], 1);  // one MMA commit releases the stage
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], 128);
+      tc::mbar_init(&acc_empty[b], 4 * CL);  // (used in CTA 0) one arrival per epilogue warp of each CTA
     }
+    tc::mbar_init(&never, 1);  // nothing arrives on it (the stall test hook)
     tc::fence_mbar_init();
     stop_flag = 0;
   }
-  if (warp == 1) tc::tmem_alloc(&tmem_base, S::TMEM_COLS);
+  if (warp == 1) tc::tmem_alloc<PAIR>(&tmem_base, S::TMEM_COLS);
   tc::fence_before_sync();
   __syncthreads();
-  if (CL > 1) tc::cluster_sync();  // the peers' barriers exist before any multicast
+  if (PAIR) tc::cluster_sync();  // the peer's barriers exist before any remote arrival or copy
   tc::fence_after_sync();
   pdl_enter();
   if (S::FU) {
@@ -275,20 +295,27 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
     }
     __syncthreads();
   }
+  // shared::cluster addresses of CTA 0's barriers (the MMA issuer's), and of
+  // a barrier in CTA `r`
+  auto at0 = [&](uint64_t* bar) { return PAIR ? tc::mapa(tc::smem_addr(bar), 0) : tc::smem_addr(bar); };
+  auto at = [&](uint64_t* bar, unsigned r) { return PAIR ? tc::mapa(tc::smem_addr(bar), r) : tc::smem_addr(bar); };
+  auto fail = [&]() {
+    *stop = 1;
+    atomicExch(a.err, 1u);
+  };
   const uint32_t tmem = tmem_base;
   const int iter = ls->iter;
   const int nrb = OUT == 0 ? S::NRB : a.nrb;
   const int n = a.n;
-  const int rank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
   const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
   const int ntiles = (a.M + 1) * (n / TC_PTS);
   const int nitems = (ntiles + TPW * CL - 1) / (TPW * CL);  // work items of CL x TPW tiles
   const int kchunks = a.KKp / TC_KC;
   // this CTA's tiles of work item wi: (wi CL + rank) TPW + h
-  auto tile_of = [&](int wi, int h) { return (wi * CL + rank) * TPW + h; };
+  auto tile_of = [&](int wi, int h) { return (wi * CL + (int)rank) * TPW + h; };
   // z0 tiles are skipped after the first iteration (their integrand is known)
   auto live = [&](int tile) { return tile < ntiles && (iter == 0 || tile * TC_PTS >= n); };
-  // an item runs in every CTA of the cluster if any of its tiles is live
+  // an item runs in both CTAs of a pair if any of its tiles is live
   auto live_item = [&](int wi) {
     bool any = false;
     for (int h = 0; h < TPW * CL; ++h) any = any || live(wi * TPW * CL + h);
@@ -296,7 +323,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
   };
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer (each CTA loads its own shares) ----------------
     if (lane == 0) {
       int c = 0;
       for (int wi = cid; wi < nitems && !*stop; wi += ncl) {
@@ -304,72 +331,79 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
         for (int rb = 0; rb < nrb && !*stop; ++rb)
           for (int kc = 0; kc < kchunks; ++kc, ++c) {
             const int s = c % S::STAGES, round = c / S::STAGES;
-            if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1)) {
-              *stop = 1;
-              atomicExch(a.err, 1u);
+            if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1, wait_ns)) {
+              fail();
               break;
             }
             unsigned char* st = smem + (size_t)s * S::STAGE;
-            tc::mbar_arrive_expect_tx(&full[s], S::FU ? 2 * S::G_BYTES : S::STAGE);
+            if (leader) tc::mbar_arrive_expect_tx(&full[s], S::TX);
+            const uint32_t fb = at0(&full[s]);
             const int kq = kc * (TC_KC / S::EPC);  // K coordinate in core-matrix rows
 #pragma unroll
             for (int h = 0; h < (S::FU ? 0 : TPW); ++h) {
               // a tile past the end repeats the last one (its result is not stored)
               const int tile = min(tile_of(wi, h), ntiles - 1);
               unsigned char* sv = st + (size_t)h * 2 * S::V_BYTES;
-              tc::tma_load_3d(sv, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
-              tc::tma_load_3d(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
+              if (PAIR) {
+                tc::tma_load_3d_pair(sv, &mapVhi, 0, tile * TC_PTS, kq, fb);
+                tc::tma_load_3d_pair(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, fb);
+              } else {
+                tc::tma_load_3d(sv, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
+                tc::tma_load_3d(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
+              }
             }
-            // this CTA's share of the coupling chunk: 8-row groups g0 .. g0 + NB/(8 CL) - 1
-            unsigned char* sg = st + (size_t)TPW * 2 * S::V_BYTES + (size_t)rank * S::G_SHARE;
-            const int g0 = rb * (NB / 8) + rank * (NB / 8 / CL);
-            if (CL == 1) {
-              tc::tma_load_4d(sg, &mapGhi, 0, 0, kq, g0, &full[s]);
-              tc::tma_load_4d(sg + S::G_BYTES, &mapGlo, 0, 0, kq, g0, &full[s]);
+            // this CTA's rows of the coupling chunk: 8-row groups g0 .. g0 + NB/(8 CL) - 1
+            unsigned char* sg = st + (size_t)TPW * 2 * S::V_BYTES;
+            const int g0 = rb * (NB / 8) + (int)rank * (NB / 8 / CL);
+            if (PAIR) {
+              tc::tma_load_4d_pair(sg, &mapGhi, 0, 0, kq, g0, fb);
+              tc::tma_load_4d_pair(sg + S::G_HALF, &mapGlo, 0, 0, kq, g0, fb);
             } else {
-              tc::tma_load_4d_mc(sg, &mapGhi, 0, 0, kq, g0, &full[s], CL_MASK);
-              tc::tma_load_4d_mc(sg + S::G_BYTES, &mapGlo, 0, 0, kq, g0, &full[s], CL_MASK);
+              tc::tma_load_4d(sg, &mapGhi, 0, 0, kq, g0, &full[s]);
+              tc::tma_load_4d(sg + S::G_HALF, &mapGlo, 0, 0, kq, g0, &full[s]);
             }
           }
       }
-      // wait for the release of the last stages by every CTA of the cluster:
-      // after that no peer arrives on this CTA's barriers
-      if (CL > 1)
-        for (int i = c > S::STAGES ? c - S::STAGES : 0; i < c; ++i)
-          if (!tc::mbar_wait(&empty[i % S::STAGES], (i / S::STAGES) & 1)) {
-            atomicExch(a.err, 1u);
-            break;
-          }
+      // wait for the release of the last stages: after that the MMAs have
+      // read this CTA's shared memory for the last time (and every copy
+      // into it has landed).  After a failure, give copies in flight time
+      // to land before the CTA exits.
+      const int first = c > S::STAGES ? c - S::STAGES : 0;
+      for (int i = first; i < c && !*stop; ++i)
+        if (!tc::mbar_wait(&empty[i % S::STAGES], (i / S::STAGES) & 1, wait_ns)) fail();
+      if (*stop) {
+        const uint64_t t0 = tc::globaltimer_ns();
+        while (tc::globaltimer_ns() - t0 < 200000) __nanosleep(1000);
+      }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    // ---------------- MMA issuer (CTA 0 of a pair) ----------------
+    if (lane == 0 && leader) {
       const uint32_t idesc =
-          tc::idesc_mma(TC_PTS, NB, ES == 4 ? tc::FMT_TF32 : (a.f16 ? tc::FMT_F16 : tc::FMT_BF16));
+          tc::idesc_mma(TC_PTS * CL, NB, ES == 4 ? tc::FMT_TF32 : (a.f16 ? tc::FMT_F16 : tc::FMT_BF16));
       const uint32_t lboV = TC_PTS * 16, sboV = 128;
       const uint32_t lboG = 128, sboG = (TC_KC / S::EPC) * 128;
+      if ((a.stall == 2 || (a.stall == 1 && !PAIR)) && !tc::mbar_wait(&never, 0, wait_ns)) fail();
       int c = 0, w = 0;
       for (int wi = cid; wi < nitems && !*stop; wi += ncl) {
         if (!live_item(wi)) continue;
         for (int rb = 0; rb < nrb && !*stop; ++rb, ++w) {
           const int acc = w % NBUF, use = w / NBUF;
-          if (use > 0 && !tc::mbar_wait(&acc_empty[acc], (use - 1) & 1)) {
-            *stop = 1;
-            atomicExch(a.err, 1u);
+          if (use > 0 && !tc::mbar_wait(&acc_empty[acc], (use - 1) & 1, wait_ns)) {
+            fail();
             break;
           }
           tc::fence_after_sync();
           const uint32_t d0 = tmem + (uint32_t)(acc * S::ACC_COLS);
           for (int kc = 0; kc < kchunks; ++kc, ++c) {
             const int s = c % S::STAGES, round = c / S::STAGES;
-            if (!tc::mbar_wait(&full[s], round & 1)) {
-              *stop = 1;
-              atomicExch(a.err, 1u);
+            if (!tc::mbar_wait(&full[s], round & 1, wait_ns)) {
+              fail();
               break;
             }
             tc::fence_after_sync();
             const uint32_t base = tc::smem_addr(smem + (size_t)s * S::STAGE);
-            const uint32_t gH = base + TPW * 2 * S::V_BYTES, gL = gH + S::G_BYTES;
+            const uint32_t gH = base + TPW * 2 * S::V_BYTES, gL = gH + S::G_HALF;
 #pragma unroll
             for (int kk = 0; kk < S::KSTEPS; ++kk) {
               // 32 bytes of K per MMA: two core matrices along K
@@ -378,20 +412,22 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
               for (int h = 0; h < TPW; ++h) {
                 const uint32_t d = d0 + (uint32_t)(h * NB);
                 const uint32_t vH = base + h * 2 * S::V_BYTES, vL = vH + S::V_BYTES;
-                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sboV), tc::smem_desc(gH + oG, lboG, sboG),
-                                 idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                tc::mma<ES == 4>(d, tc::smem_desc(vL + oV, lboV, sboV), tc::smem_desc(gH + oG, lboG, sboG),
-                                 idesc, 1u);
-                tc::mma<ES == 4>(d, tc::smem_desc(vH + oV, lboV, sboV), tc::smem_desc(gL + oG, lboG, sboG),
-                                 idesc, 1u);
+                tc::mma<ES == 4, PAIR>(d, tc::smem_desc(vH + oV, lboV, sboV), tc::smem_desc(gH + oG, lboG, sboG),
+                                       idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc::mma<ES == 4, PAIR>(d, tc::smem_desc(vL + oV, lboV, sboV), tc::smem_desc(gH + oG, lboG, sboG),
+                                       idesc, 1u);
+                tc::mma<ES == 4, PAIR>(d, tc::smem_desc(vH + oV, lboV, sboV), tc::smem_desc(gL + oG, lboG, sboG),
+                                       idesc, 1u);
               }
             }
-            // the stage is free (in every CTA of the cluster) once these MMAs have read it
-            if (CL == 1) tc::mma_commit(&empty[s]);
-            else tc::mma_commit_mc(&empty[s], CL_MASK);
+            // the stage is free in each CTA once these MMAs have read it
+            tc::mma_commit<PAIR>(tc::smem_addr(&empty[s]));
+            if (PAIR) tc::mma_commit<PAIR>(at(&empty[s], 1));
           }
           if (*stop) break;
-          tc::mma_commit(&acc_full[acc]);  // accumulator complete
+          // accumulator complete (in both CTAs' TMEM)
+          tc::mma_commit<PAIR>(tc::smem_addr(&acc_full[acc]));
+          if (PAIR) tc::mma_commit<PAIR>(at(&acc_full[acc], 1));
         }
       }
     }
@@ -478,9 +514,8 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
           if (lane == 0) {
             if (*stop) {
               go = 0;
-            } else if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1)) {
-              *stop = 1;
-              atomicExch(a.err, 1u);
+            } else if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1, wait_ns)) {
+              fail();
               go = 0;
             }
           }
@@ -499,7 +534,10 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
           }
           tc::fence_proxy_async();  // the stores are seen by the tensor cores' reads
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&full[s]);
+          if (lane == 0) {
+            if (PAIR) tc::mbar_arrive_cluster(at0(&full[s]));  // CTA 0's barrier, released at cluster scope
+            else tc::mbar_arrive(&full[s]);
+          }
         }
       wi = wn;
     }
@@ -530,9 +568,10 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
       }
       for (int rb = 0; rb < nrb; ++rb, ++w) {
         const int acc = w % NBUF, use = w / NBUF;
-        if (!tc::mbar_wait(&acc_full[acc], use & 1)) {
-          *stop = 1;
-          atomicExch(a.err, 1u);
+        int ok = 1;
+        if (lane == 0) ok = tc::mbar_wait(&acc_full[acc], use & 1, wait_ns) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) fail();
           break;
         }
         tc::fence_after_sync();
@@ -558,8 +597,14 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
         } else if (mine) {
           drain_rb<N, NB, 0>(rb, taddr, av, nl);
         }
+        // this warp's reads of the accumulator are done: one arrival on
+        // CTA 0's barrier
         tc::fence_before_sync();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&acc_empty[acc])) : "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR) tc::mbar_arrive_cluster(at0(&acc_empty[acc]));
+          else tc::mbar_arrive(&acc_empty[acc]);
+        }
       }
       if (*stop) break;
       if (OUT == 0 && mine) {
@@ -571,8 +616,8 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CL > 1) tc::cluster_sync();  // no CTA leaves while a peer may still write to it
-  if (warp == 1) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+  if (PAIR) tc::cluster_sync();  // no CTA leaves while its peer may still signal it or read its memory
+  if (warp == 1) tc::tmem_dealloc<PAIR>(tmem, S::TMEM_COLS);
 }
 
 // V to the blocked 16-bit hi/lo operand layout [KKp/8][npts][8] read by the

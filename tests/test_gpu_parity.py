@@ -333,6 +333,31 @@ def test_mixed_tensor_core_contraction(N, Nt, fR, mixed):
     assert err < 1e-5
 
 
+@functools.lru_cache(maxsize=None)
+def wide_grin(N):
+    """GRIN fibers of 20, 30 and 64 Hermite-Gauss modes (the last mode group
+    partly filled) on a 128-point grid, one long step of M = 4 with three
+    fixed updates (the oracle's N^2 x N^2 products stay at seconds)."""
+    prob = I.grin_problem("w", N=N, Nt=128, dt=2e-12 / 128, kind="gaussian", fwhm=150e-15,
+                          energy=20e-9, L=4e-4, dz=1e-4, M=4, tol=1e-13, seed=13, fR=0.18, s_from="gh")
+    ref, _ = oracle_run(prob, fixed_iters=3)
+    return prob, ref
+
+
+@pytest.mark.parametrize("N", [20, 30, 64])
+@pytest.mark.parametrize("mixed", ["bf16", "fp16", "tf32"])
+def test_mixed_tensor_core_any_mode_count(N, mixed):
+    """Every N from 9 to 64 takes the tensor cores: 20 and 30 modes on the
+    low-rank coupling (and 64 modes with TF32), 64 modes with 16-bit operands
+    on the dense one (2080 x 2080 reduced matrix, nine row blocks of 256),
+    against the FP64 oracle at the mixed bar."""
+    prob, ref = wide_grin(N)
+    out, st, rc = gpu_run(prob, mixed, fixed_iters=3)
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-3
+    assert rel(out, ref) < 1e-5
+
+
 @pytest.mark.parametrize("mixed", ["bf16", "fp16", "tf32"])
 def test_mixed_c2_prefix(mixed):
     prob, ref, sref = c2_prefix()
