@@ -72,7 +72,9 @@ struct gmmnlse_ctx {
   double2* tw64 = nullptr;      // [n] + radix-16 pass tables of n
   double2* tw64h = nullptr;     // [n/2] + pass tables of n/2
   float2* tw32 = nullptr;       // [n] + pass tables of n
-  void* H = nullptr;            // [n] cplx<R>
+  void* H = nullptr;            // [n] cplx<R>: (dt/n) DFT(h_R), the Raman transfer function with the inverse 1/n
+  void* Hv = nullptr;           // [n] float2 (FP32 contexts): (1 - fR)/n + fR H, the transfer function of
+                                // V' = (1 - fR) Z + fR h_R * Z (the low-rank operand of 16-bit GEMM 2)
   void* fac = nullptr;          // [n] R: gamma0 s(w_q)
   void* G = nullptr;            // [P][KK] R
   int2* rows = nullptr;         // [P]

@@ -18,6 +18,7 @@
 #include <limits>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gmmnlse.h"
@@ -152,6 +153,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->tw64h);
   cudaFree(c->tw32);
   cudaFree(c->H);
+  cudaFree(c->Hv);
   cudaFree(c->fac);
   cudaFree(c->G);
   cudaFree(c->Gt);
@@ -360,7 +362,8 @@ static int compute_H(gmmnlse_ctx* c, const double* hR) {
   CK(cudaMemcpy(hin, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
   int rc = fft64(c, scr, hin, hsp, 1, -1, 1.0, 0);
   if (rc) return rc;
-  k_raman_H<R><<<(n + 255) / 256, 256>>>(hsp, (cplx<R>*)c->H, n, c->prm.dt);
+  if (std::is_same<R, float>::value) CK(cudaMalloc(&c->Hv, (size_t)n * sizeof(float2)));
+  k_raman_H<R><<<(n + 255) / 256, 256>>>(hsp, (cplx<R>*)c->H, (float2*)c->Hv, n, c->prm.dt, c->fR);
   CK(cudaGetLastError());
   CK(cudaDeviceSynchronize());
   cudaFree(hin);

@@ -157,24 +157,25 @@ __device__ __forceinline__ void pairs_raman_task(const Geo& g, const cplx<R>* __
   const int k1 = 2 * kp, k2 = k1 + 1;
   const bool has2 = k2 < cnt;
   __syncthreads();  // the block's previous use of sm is over
-  // the rows are staged in shared memory first: the transform's first pass
-  // then reads no global memory, which keeps its registers free
+  auto from_smem = [&](int q) { return sm[pad16(q)]; };
+  auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
   if (SRC == 0) {
+    // the pair products are staged in shared memory first: the transform's
+    // first pass then reads no global memory, which keeps its registers free
     const int2 mn1 = pairs[k1];
     const int2 mn2 = has2 ? pairs[k2] : mn1;
     const cplx<R>* a = A + (size_t)j * g.N * n;
 #pragma unroll 4
     for (int t = threadIdx.x; t < n; t += blockDim.x)
       sm[pad16(t)] = mk<R>(pair_product<R>(a, n, mn1, t), has2 ? pair_product<R>(a, n, mn2, t) : (R)0);
+    fft_block<R, -1, EPT>(sm, n, tw, from_smem, to_smem);
   } else {
+    // rows of Z: the first pass reads them straight from global memory
+    // (every load of the pass in flight at once)
     const R* z1 = Zs + ((size_t)j * cnt + k1) * n;
-#pragma unroll 4
-    for (int t = threadIdx.x; t < n; t += blockDim.x)
-      sm[pad16(t)] = mk<R>(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : (R)0);
+    auto load = [&](int t) { return mk<R>(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : (R)0); };
+    fft_block<R, -1, EPT>(sm, n, tw, load, to_smem);
   }
-  auto from_smem = [&](int q) { return sm[pad16(q)]; };
-  auto to_smem = [&](int q, cplx<R> x) { sm[pad16(q)] = cmul<R>(x, H[q]); };
-  fft_block<R, -1, EPT>(sm, n, tw, from_smem, to_smem);
   R* y1 = Y + ((size_t)j * cnt + k1) * n;
   auto store = [&](int t, cplx<R> y) {
     y1[t] = y.x;
@@ -800,11 +801,17 @@ static __global__ void k_spec_sums(const double2* __restrict__ psi, int N, int n
   }
 }
 
-// Raman transfer function H[q] = (dt/n) DFT_-(h_R)[q] from an FP64 spectrum.
+// Raman transfer function H[q] = (dt/n) DFT_-(h_R)[q] from an FP64 spectrum,
+// and (when Hv is given) Hv[q] = (1 - fR)/n + fR H[q], the transfer function
+// of (1 - fR) x + fR h_R * x, both formed in FP64 and rounded once.
 template <typename R>
-__global__ void k_raman_H(const double2* __restrict__ hspec, cplx<R>* __restrict__ H, int n, double dt) {
+__global__ void k_raman_H(const double2* __restrict__ hspec, cplx<R>* __restrict__ H, float2* __restrict__ Hv,
+                          int n, double dt, double fR) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) H[q] = mk<R>((R)(hspec[q].x * dt / n), (R)(hspec[q].y * dt / n));
+  if (q >= n) return;
+  const double hx = hspec[q].x * dt / n, hy = hspec[q].y * dt / n;
+  H[q] = mk<R>((R)hx, (R)hy);
+  if (Hv) Hv[q] = make_float2((float)((1.0 - fR) / n + fR * hx), (float)(fR * hy));
 }
 
 // Check a field for NaN / Inf (flag set to 1 if any).

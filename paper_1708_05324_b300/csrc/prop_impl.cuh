@@ -374,7 +374,7 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
       const int npts_total = (jb->Mcap + 1) * n;
       auto vp = [&](auto kern) {
         pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<float>(n), s, g, (const float*)jb->Z, c->r,
-                   (const float2*)c->H, (const float2*)twid<float>(c), npts_total, (void*)jb->Vhi, (void*)jb->Vlo,
+                   (const float2*)c->Hv, (const float2*)twid<float>(c), npts_total, (void*)jb->Vhi, (void*)jb->Vlo,
                    c->eW, (const LoopState*)jb->ls);
       };
       if (c->f16) {

@@ -746,17 +746,21 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_rows(
 }
 
 // Low-rank coupling with 16-bit operands (OP 0 BF16, 1 FP16) and Raman: K2
-// on the rows k1 = 2 blockIdx.x and k1 + 1 of Z (Y' = h_R * Z by one complex
-// transform pair, as k_pairs_raman with SRC 1), whose inverse transform
-// writes the operand of GEMM 2 directly, V' = (1 - fR) Z + fR Y' as hi + lo
-// in the blocked layout [KKp/8][npts][8] (both rows' values of a point in
-// one 4-byte word each), so that neither Y' nor a separate pack pass goes
-// through HBM.  FP16 values are scaled by 2^(eV - eVoff) as in k_pack_rows.
-// The padding columns r .. KKp - 1 (except column r of an odd r, written
-// here as 0) are zero from the workspace's creation.  grid (ceil(r/2), M+1).
+// on the rows k1 = 2 blockIdx.x and k1 + 1 of Z, writing the operand of
+// GEMM 2 directly: V' = (1 - fR) Z + fR h_R * Z = F^-1{F{Z} Hv} with the
+// transfer function Hv = (1 - fR)/n + fR H, one complex transform pair for
+// the two real rows (as k_pairs_raman with SRC 1).  The forward transform's
+// first pass reads the two rows straight from global memory (every load of
+// the pass in flight at once), and the inverse transform's last pass writes
+// V' as hi + lo in the blocked layout [KKp/8][npts][8] (both rows' values of
+// a point in one 4-byte word each), so that neither Y' nor a separate pack
+// pass goes through HBM.  FP16 values are scaled by 2^(eV - eVoff) as in
+// k_pack_rows.  The padding columns r .. KKp - 1 (except column r of an odd
+// r, written here as 0) are zero from the workspace's creation.  grid
+// (ceil(r/2), M+1).
 template <int EPT, int OP>
 __global__ void __launch_bounds__(512) k_raman_vpack(Geo g, const float* __restrict__ Zs, int r,
-                                                      const float2* __restrict__ H, const float2* __restrict__ tw,
+                                                      const float2* __restrict__ Hv, const float2* __restrict__ tw,
                                                       int npts_total, void* __restrict__ Vhi_,
                                                       void* __restrict__ Vlo_, int eVoff,
                                                       const LoopState* __restrict__ ls) {
@@ -771,21 +775,18 @@ __global__ void __launch_bounds__(512) k_raman_vpack(Geo g, const float* __restr
   const int n = g.n, k1 = 2 * blockIdx.x;
   const bool has2 = k1 + 1 < r;
   const float* z1 = Zs + ((size_t)j * r + k1) * n;
-#pragma unroll 4
-  for (int t = threadIdx.x; t < n; t += blockDim.x)
-    sm[pad16(t)] = make_float2(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : 0.f);
+  auto load = [&](int t) { return make_float2(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : 0.f); };
   auto from_smem = [&](int q) { return sm[pad16(q)]; };
-  auto to_smem = [&](int q, float2 x) { sm[pad16(q)] = cmul<float>(x, H[q]); };
-  fft_block<float, -1, EPT>(sm, n, tw, from_smem, to_smem);
-  const float fR = (float)g.fR, fK = (float)(1.0 - g.fR);
+  auto to_smem = [&](int q, float2 x) { sm[pad16(q)] = cmul<float>(x, Hv[q]); };
+  fft_block<float, -1, EPT>(sm, n, tw, load, to_smem);
   const float scale = OP == 1 ? ldexpf(1.0f, f16_v_exp(ls, n) - eVoff) : 1.0f;
   uint32_t* Vhi = reinterpret_cast<uint32_t*>(Vhi_);
   uint32_t* Vlo = reinterpret_cast<uint32_t*>(Vlo_);
   // 4-byte word of (k1, k1 + 1) at point p: element ((k1/8) npts_total + p) 8 + k1 % 8
   const size_t w0 = ((size_t)(k1 / 8) * npts_total + (size_t)j * n) * 4 + (k1 % 8) / 2;
   auto store = [&](int t, float2 y) {
-    const float v1 = (fK * __ldcg(z1 + t) + fR * y.x) * scale;
-    const float v2 = has2 ? (fK * __ldcg(z1 + n + t) + fR * y.y) * scale : 0.f;
+    const float v1 = y.x * scale;
+    const float v2 = has2 ? y.y * scale : 0.f;
     const T h1 = Hs::rn(v1), h2 = Hs::rn(v2);
     const T l1 = Hs::rn(v1 - Hs::back(h1)), l2 = Hs::rn(v2 - Hs::back(h2));
     __align__(4) T hw[2] = {h1, h2}, lw[2] = {l1, l2};
