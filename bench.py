@@ -1,19 +1,25 @@
 """Benchmark of the MPA hot path: mode * sample * z-steps per second.
 
-Workload (the GMMNLSE Kerr + Raman propagation the metric is quoted on):
-parabolic GRIN fiber (a = 25 um, NA = 0.2, 1030 nm, n2 = 2.3e-20 m^2/W),
-N = 6 Hermite-Gauss modes, Nt = 2^13 over 10 ps, f_R = 0.18 (tau1 = 12.2 fs,
-tau2 = 32 fs), self-steepening on, 200 fs Gaussian pulse of 50 nJ with seeded
-random complex mode weights, L = 0.5 m, dz = 25 um, M = 10, tol = 1e-8.
-One bench step = one full propagation over the 0.5 m fiber (20000 substeps,
-2000 long steps) through the C ABI.  Synthetic inputs (no dataset).
+Headline workload (the largest single-GPU configuration, the dense-contraction
+stress case): step-index fiber (a = 25 um, NA = 0.22, 1030 nm, n2 = 2.3e-20
+m^2/W), the first N = 42 LP modes with both orientations solved from the LP
+characteristic equation, S_plmn on a 400 x 400 grid (computed on the GPU by
+gmmnlse_overlap_tensor), Nt = 2^13 over 10 ps, Kerr + Raman (f_R = 0.18,
+tau1 = 12.2 fs, tau2 = 32 fs), self-steepening, 100 fs Gaussian pulse of
+100 nJ with seeded random complex mode weights, L = 0.3 m, dz = 37.5 um,
+M = 16, tol = 1e-6, MIXED_BF16 (coupling contraction on the tensor cores,
+BF16 hi/lo operands, FP32 accumulate).  One bench step = one full
+propagation over the 0.3 m fiber (8000 substeps, 500 long steps) through
+the C ABI with device buffers.  Synthetic inputs (no dataset).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C4|C3|C2]
+                    [--precision bf16|fp16|tf32|fp32|fp64] [--length L]
     python bench.py --impl reference     # the CPU oracle on a bounded sample
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -30,29 +36,50 @@ sys.path.insert(0, ROOT)
 from paper_1708_05324_b300 import inputs as I  # noqa: E402
 
 METRIC = "mode*sample*z-steps/s"
-WORKLOAD = ("GRIN a=25um NA=0.2 1030nm, N=6 HG modes, Nt=2^13 over 10 ps, Kerr+Raman fR=0.18, "
-            "self-steepening, 200 fs Gaussian 50 nJ seeded weights, L=0.5 m, dz=25 um, M=10, tol=1e-8")
 WORKLOADS = {
-    "C2": WORKLOAD,
-    "C3": ("GRIN a=25um NA=0.2 1030nm, N=15 HG modes (groups 0-4), Nt=2^14 over 20 ps, Kerr+Raman fR=0.18, "
-           "self-steepening, 500 fs Gaussian 200 nJ seeded weights, dz=12.5 um, M=20, tol=1e-6"),
-    "C4": ("step-index a=25um NA=0.22 1030nm, N=42 LP modes (both orientations, S from a 200^2 grid), "
+    "C4": ("step-index a=25um NA=0.22 1030nm, N=42 LP modes (both orientations, S from a 400^2 grid), "
            "Nt=2^13 over 10 ps, Kerr+Raman fR=0.18, self-steepening, 100 fs Gaussian 100 nJ seeded weights, "
-           "dz=37.5 um, M=16, tol=1e-6"),
+           "L=0.3 m, dz=37.5 um, M=16, tol=1e-6"),
+    "C3": ("GRIN a=25um NA=0.2 1030nm, N=15 HG modes (groups 0-4), Nt=2^14 over 20 ps, Kerr+Raman fR=0.18, "
+           "self-steepening, 500 fs Gaussian 200 nJ seeded weights, L=1 m, dz=12.5 um, M=20, tol=1e-6"),
+    "C2": ("GRIN a=25um NA=0.2 1030nm, N=6 HG modes, Nt=2^13 over 10 ps, Kerr+Raman fR=0.18, "
+           "self-steepening, 200 fs Gaussian 50 nJ seeded weights, L=0.5 m, dz=25 um, M=10, tol=1e-8"),
 }
+FULL_LENGTH = {"C4": 0.3, "C3": 1.0, "C2": 0.5}
+SEED = {"C4": 4, "C3": 3, "C2": 2}
+# the precision's error against the FP64 GPU path is measured on this prefix
+ERR_PREFIX = {"C4": (16 * 37.5e-6, "one long step (0.6 mm)"), "C3": (2e-3, "2 mm (8 long steps)"),
+              "C2": (5e-3, "5 mm (20 long steps)")}
 # DRAM bytes per launch of the dominant kernel from one ncu capture (the
-# kernel unchanged since): k_pairs_raman<float, 16, 0> on the 6-mode
-# workload, warm L2, profiles/pairs_raman_c2_fp32.md.
-TRAFFIC = {("C2", "fp32", "pairs_raman"): 1024 + 256}
+# kernel unchanged since), keyed (workload, precision, kernel slot)
+TRAFFIC = {}
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
+# nominal dense TF32 : BF16 tensor rate (1.1 : 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+_PROBLEMS = {}
 
 
-def problem(seed=2, L=0.5, name="C2"):
-    if name == "C2":
-        return I.workload("C2", L=L, seed=seed)
-    if name == "C3":
-        return I.workload(name, L=L, seed=seed + 1, s_from="gh")
-    return I.workload(name, L=L, npts=200)  # C4: S on a 200^2 grid for the profile runs
+def problem(name="C4", L=None, seed=None, dev=0, gpu_overlap=True):
+    """The named workload with fiber length L (default: its full length).
+    The 42-mode fiber's overlap tensor comes from the 400^2 grid, on the GPU
+    through gmmnlse_overlap_tensor (gpu_overlap) or by the numpy sums (for
+    the oracle's inputs, which never come from the CUDA path)."""
+    L = FULL_LENGTH[name] if L is None else L
+    seed = SEED[name] if seed is None else seed
+    key = (name, seed, gpu_overlap and name == "C4")
+    if key not in _PROBLEMS:
+        if name == "C4":
+            over = None
+            if gpu_overlap:
+                from paper_1708_05324_b300 import binding as B
+                over = lambda F, dA: B.overlap_tensor(F, dA, dev)  # noqa: E731
+            _PROBLEMS[key] = I.workload("C4", seed=seed, npts=400, overlap=over)
+        elif name == "C3":
+            _PROBLEMS[key] = I.workload("C3", seed=seed, s_from="gh")
+        else:
+            _PROBLEMS[key] = I.workload(name, seed=seed)
+    return dataclasses.replace(_PROBLEMS[key], L=L)
 
 
 def units(prob, L=None):
@@ -157,6 +184,20 @@ def launches_per_step(st, raman, mixed=False, fp64=False, graph=True, N=1, Nt=81
     return n
 
 
+def contraction_flops_per_point(prob, coupling_rank, mixed):
+    """Algorithmic flops of the coupling contraction per point (substep x
+    sample) and MPA iteration, unpadded: with the low-rank coupling (rank r)
+    the two GEMMs 2 r (K + P), else the dense reduced GEMM 2 P KK; x3 for the
+    hi/lo products on the tensor cores."""
+    P = prob.N * (prob.N + 1) // 2
+    KK = P if prob.fR == 0 or prob.SR is None or prob.SR is prob.SK else 2 * P
+    per = 2.0 * coupling_rank * (P + P) if coupling_rank < P else 2.0 * P * KK
+    return per * (3 if mixed else 1)
+
+
+# ----------------------------------------------------------------------------
+# Error along the fiber and the M sweep (separate modes of bench.py)
+# ----------------------------------------------------------------------------
 def run_error_curve(args, dev):
     """Relative L2 difference between this precision and the FP64 GPU path
     along the fiber.  Both propagate the same input in SEGMENTS pieces of
@@ -166,7 +207,7 @@ def run_error_curve(args, dev):
     of each piece.  Over long, strongly nonlinear fibers rounding differences
     grow, so this is the curve that says how far a prefix parity carries."""
     from paper_1708_05324_b300 import binding as B
-    prob = problem(L=args.length, name=args.workload)
+    prob = problem(args.workload, L=args.length, dev=dev)
     lstep = prob.M * prob.dz
     nlong = int(round(prob.L / lstep))
     nseg = max(1, min(args.error_curve, nlong))
@@ -185,7 +226,7 @@ def run_error_curve(args, dev):
     c64.close()
     cx.close()
     print(json.dumps({"error_curve": curve, "vs": "fp64 gpu", "precision": args.precision,
-                      "workload": args.workload, "length_m": args.length, "long_steps": nlong,
+                      "workload": args.workload, "length_m": prob.L, "long_steps": nlong,
                       "wall_s": time.perf_counter() - t0}))
 
 
@@ -201,7 +242,7 @@ def run_m_sweep(args, dev):
     relative L2 difference from the M = 1 field."""
     import torch
     from paper_1708_05324_b300 import binding as B
-    prob = problem(L=args.length, name=args.workload)
+    prob = problem(args.workload, L=args.length, dev=dev)
     Ms = sorted({int(x) for x in args.m_sweep.split(",")} | {1})
     stream = torch.cuda.Stream(device=dev)
     ctx = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream,
@@ -270,36 +311,20 @@ def run_m_sweep(args, dev):
         r["speedup_vs_M1"] = round(base / r["ms"], 3)
         r["speedup_vs_rk4ip"] = round(rk_t / r["ms"], 3)
     print(json.dumps({"m_sweep": rows, "rk4ip": rk4ip, "workload": args.workload, "precision": args.precision,
-                      "length_m": args.length, "dz": prob.dz, "tol": prob.tol, "unit": METRIC,
+                      "length_m": prob.L, "dz": prob.dz, "tol": prob.tol, "unit": METRIC,
                       "choose_m": {"M": auto_M, "trial_substeps": 2 * max(Ms),
                                    "us_per_substep": {m: round(1e6 * t, 3) for m, t in auto_sec.items()}},
                       "timing": "CUDA events per propagation, median of --steps, L2 flushed before each"}))
 
 
-def run_reference(args):
-    """The CPU oracle as it stands, on a bounded sample of the workload."""
-    import oracle as O
-    prob = problem()
-    fib = O.Fiber.from_problem(prob)
-    sample_L = 2 * prob.M * prob.dz  # two long steps per bench step
-    for _ in range(max(args.warmup, 0)):
-        O.mpa_propagate(fib, prob.A0, sample_L, prob.dz, prob.M, prob.tol)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.mpa_propagate(fib, prob.A0, sample_L, prob.dz, prob.M, prob.tol)
-        times.append(time.perf_counter() - t0)
-    u = units(prob, sample_L)
-    value = u * len(times) / sum(times)
-    cores = _blas_threads()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64-cpu-oracle"},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
-                             "sample": "first 2 long steps (20 substeps, 0.5 mm) of the 0.5 m run per step"},
-            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+# ----------------------------------------------------------------------------
+# The CPU oracle: reference arm and cpu_baseline
+# ----------------------------------------------------------------------------
+# MPA iterations per long step of the 42-mode workload at tol = 1e-6 over the
+# whole 0.3 m fiber (3.334, measured on the GPU; 5.0 on the first
+# centimetre, 3 to 4 later), used to turn the oracle's time per integrand
+# into a rate when no GPU run of the same workload gives the count
+C4_ITERS_PER_LONG_STEP = 3.334
 
 
 def _blas_threads():
@@ -311,21 +336,84 @@ def _blas_threads():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(seconds=15.0):
-    """Oracle rate on the host cores for as many long steps as fit in ~seconds."""
+def _oracle_integrand_seconds(fib, psi, count, budget_s):
+    """Seconds per integrand evaluation (Eq. MPA_eq at one substep: the
+    oracle's unit of work) over up to `count` evaluations within budget_s."""
     import oracle as O
-    prob = problem()
+    times = []
+    t_all = time.perf_counter()
+    for k in range(count):
+        t0 = time.perf_counter()
+        O.integrand(fib, psi, (k % 16) * 37.5e-6)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget_s:
+            break
+    return float(np.median(times)), len(times)
+
+
+def _oracle_rate(prob, sec_per_integrand, iters_per_long_step):
+    """Units per second of the oracle's MPA: a long step of M substeps takes
+    iters x M integrand evaluations (plus I_0 once), all in the oracle's
+    plain sums; everything else of the step is negligible beside them."""
+    per_long_step = prob.N * prob.Nt * prob.M
+    evals = iters_per_long_step * prob.M + 1
+    return per_long_step / (sec_per_integrand * evals)
+
+
+def cpu_baseline(seconds=15.0, iters_per_long_step=C4_ITERS_PER_LONG_STEP):
+    """Oracle rate on the host cores on a bounded sample of the 42-mode
+    workload: integrand evaluations at full size (N = 42, Nt = 2^13) with
+    every BLAS thread, then one with a single thread; iters_per_long_step
+    (the GPU run's count on the same fiber) turns them into a rate."""
+    import oracle as O
+    prob = problem("C4", gpu_overlap=False)
     fib = O.Fiber.from_problem(prob)
     psi = O.freq_from_time(prob.A0)
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < seconds:
-        psi, n, trace, status = O.mpa_long_step(fib, psi, prob.dz, prob.M, prob.tol)
-        steps += 1
-    dt = time.perf_counter() - t0
-    rate = prob.N * prob.Nt * prob.M * steps / dt
+    O.integrand(fib, psi, 0.0)  # warm-up
+    sec, count = _oracle_integrand_seconds(fib, psi, 64, seconds)
+    rate = _oracle_rate(prob, sec, iters_per_long_step)
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1):
+            sec1, _ = _oracle_integrand_seconds(fib, psi, 1, 0.0)
+        one = {"value": _oracle_rate(prob, sec1, iters_per_long_step), "unit": METRIC, "cores": 1,
+               "sec_per_integrand": sec1}
+    except Exception as e:  # the figure is then missing, and says why
+        one = {"value": None, "error": f"{type(e).__name__}: {e}"}
     return {"value": rate, "unit": METRIC, "cores": _blas_threads(), "kind": "oracle",
-            "sample": f"first {steps} long steps ({steps * prob.M} substeps) of the 0.5 m run, {dt:.1f} s"}
+            "sample": (f"{count} integrand evaluations of the 42-mode field at full size (median {sec:.2f} s each), "
+                       f"scaled to the rate by {iters_per_long_step:.3f} iterations x 16 substeps + 1 per long "
+                       f"step (the GPU run's iteration count on the same fiber)"),
+            "one_core": one}
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on a bounded sample of the workload: each
+    step is one integrand evaluation of the 42-mode field at full size, the
+    rate scaled as in cpu_baseline."""
+    import oracle as O
+    prob = problem("C4", gpu_overlap=False)
+    fib = O.Fiber.from_problem(prob)
+    psi = O.freq_from_time(prob.A0)
+    for _ in range(max(args.warmup, 0)):
+        O.integrand(fib, psi, 0.0)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        O.integrand(fib, psi, (k % 16) * prob.dz)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    value = _oracle_rate(prob, sec, C4_ITERS_PER_LONG_STEP)
+    cores = _blas_threads()
+    sample = (f"one integrand evaluation of the 42-mode field at full size per step ({sec:.2f} s), scaled to "
+              f"the rate by {C4_ITERS_PER_LONG_STEP} iterations x 16 substeps + 1 per long step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS["C4"], "precision": "fp64-cpu-oracle"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 # ----------------------------------------------------------------------------
@@ -340,7 +428,8 @@ def serving_requests(count, seed=5, max_substeps=2000, M=10):
     (uniform), dt = 4.8828125 fs, Gaussian FWHM log-uniform 100-500 fs, energy
     log-uniform 1-200 nJ, L log-uniform 1 cm - 1 m, M = 10,
     dz = L / (M ceil(L / (M z_NL / 200))).  A request longer than max_substeps
-    substeps is cut to that many (same dz), so the pass fits in minutes."""
+    substeps is cut to that many (same dz); max_substeps = 0 keeps every
+    request whole."""
     g = I.SplitMix64(seed)
     dt = 4.8828125e-15
     reqs = []
@@ -357,7 +446,7 @@ def serving_requests(count, seed=5, max_substeps=2000, M=10):
         znl = 1.0 / (gamma * P0)
         nsub = M * math.ceil(L / (M * znl / 200))
         dz = L / nsub
-        if nsub > max_substeps:
+        if max_substeps and nsub > max_substeps:
             nsub = max_substeps
             L = nsub * dz
         reqs.append(dict(N=N, Nt=Nt, dt=dt, A0=A0, L=L, dz=dz, M=M, units=N * Nt * nsub))
@@ -408,7 +497,7 @@ def run_serving(B, dev, count=32, max_substeps=2000, inflight=8, load=0.9, seed=
         tickets.append(t)
     done = drain(tickets, t_submit)
     cap_s = time.perf_counter() - t0
-    units = sum(r["units"] for r in reqs)
+    total_units = sum(r["units"] for r in reqs)
     status = {}
     for _, rc in done.values():
         status[rc] = status.get(rc, 0) + 1
@@ -448,27 +537,132 @@ def run_serving(B, dev, count=32, max_substeps=2000, inflight=8, load=0.9, seed=
     fp64_serial = sum(r["units"] for r in sub) / t64
     return {"requests": len(reqs), "precision": "bf16", "max_inflight": inflight,
             "max_substeps_per_request": max_substeps,
-            "closed_loop_units_per_s": units / cap_s, "closed_loop_s": cap_s,
-            "offered_load": load, "open_loop_units_per_s": units / open_s,
+            "closed_loop_units_per_s": total_units / cap_s, "closed_loop_s": cap_s,
+            "offered_load": load, "open_loop_units_per_s": total_units / open_s,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "status_counts": {B.load().gmmnlse_strerror(k).decode(): v for k, v in status.items()},
             "fp64_serial_units_per_s": fp64_serial, "fp64_serial_requests": len(sub),
             "mix": "C5: N in {1,3,6,10,15}, Nt 2^10..2^14, FWHM 100-500 fs, 1-200 nJ, L 1 cm-1 m, dz = z_NL/200"}
 
 
+# ----------------------------------------------------------------------------
+# Timed propagations
+# ----------------------------------------------------------------------------
+def propagation_runner(B, prob, precision, dev, stream, flush):
+    """A context of the problem and one event-timed whole propagation through
+    the C ABI with device buffers (the inputs resident in HBM before the
+    timed region), L2 flushed before it: (context, step() -> (ms, stats))."""
+    import torch
+    ctx = B.Context.from_problem(prob, precision=precision, device=dev, stream=stream.cuda_stream, io_device=True)
+    a0 = torch.from_numpy(prob.A0).to(f"cuda:{dev}")
+    out = torch.empty_like(a0)
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)  # L2 flush (256 MiB write), outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st, rc = ctx.propagate(a0, prob.L, prob.dz, prob.M, prob.tol, out=out, check=False)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != B.OK:
+            raise B.GmmnlseError(rc, "propagate")
+        return e0.elapsed_time(e1), st
+
+    return ctx, one_step
+
+
+def workload_text(name, L):
+    text = WORKLOADS[name]
+    return text if L == FULL_LENGTH[name] else text + f" (a {L} m prefix of the fiber per step)"
+
+
+def prefix_error(B, name, precision, dev):
+    """Relative L2 of this precision against the FP64 GPU path on the
+    workload's prefix, and the FP64 path's rate there."""
+    L, what = ERR_PREFIX[name]
+    pre = problem(name, L=L, dev=dev)
+    c64 = B.Context.from_problem(pre, precision="fp64", device=dev)
+    ref64, st64, _ = c64.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
+    c64.close()
+    cx = B.Context.from_problem(pre, precision=precision, device=dev)
+    mine, _, _ = cx.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
+    cx.close()
+    return float(np.linalg.norm(mine - ref64) / np.linalg.norm(ref64)), units(pre) / (st64["ms"] / 1e3), what
+
+
+def roofline(prob, prof, coupling_rank, precision, peaks, src, workload):
+    """Roofline of the dominant kernel slot of one MPA iteration, from the
+    event-timed per-kernel durations of gmmnlse_profile (launches of
+    substeps 1..M).  The contraction of N > 8 modes is bound by the tensor
+    cores (mixed precisions; the sustained BF16 peak, since it runs inside a
+    seconds-long step; TF32 at the nominal TF32 : BF16 ratio) or the FP32
+    ALUs; the rest by HBM."""
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms_dom, bytes_dom = prof[dom]
+    mixed = precision in ("bf16", "fp16", "tf32")
+    if dom == "contract" and prob.N > 8:
+        flops = contraction_flops_per_point(prob, coupling_rank, mixed) * prob.M * prob.Nt
+        achieved = flops / (ms_dom * 1e-3) / 1e12
+        if mixed:
+            scale = TF32_OVER_BF16 if precision == "tf32" else 1.0
+            peak = peaks["bf16_tflops_sustained"] * scale
+            roof = {"kernel": "contract (GEMM 1 Z = W U and GEMM 2 R = X V' with the l-sum)"
+                    if coupling_rank < prob.N * (prob.N + 1) // 2 else "contract (dense GEMM with the l-sum)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "frac_of_burst": achieved / (peaks["bf16_tflops"] * scale),
+                    "peak_source": f"{src} bf16_tflops_sustained" + (" x 1.1/2.25 (nominal TF32 : BF16)"
+                                                                    if precision == "tf32" else ""),
+                    "algorithmic_flops": flops}
+        else:
+            roof = {"kernel": "contract", "bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_ALU_TFLOPS,
+                    "peak_source": "148 SMs x 128 FP32 FMA/clk x 2 x 2.032 GHz", "algorithmic_flops": flops}
+    else:
+        achieved = bytes_dom / (ms_dom * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{src} hbm_gbs", "algorithmic_bytes": bytes_dom}
+    roof["traffic"] = TRAFFIC.get((workload, precision, dom))
+    roof["kernel_ms"] = ms_dom
+    roof["all_kernels_ms"] = {k: v[0] for k, v in prof.items()}
+    # every kernel slot against its bound (HBM for all but the contraction)
+    roof["hbm_frac_by_kernel"] = {k: (v[1] / (v[0] * 1e-3) / 1e9) / peaks["hbm_gbs"] for k, v in prof.items()
+                                  if v[0] > 0 and k != "contract"}
+    return roof
+
+
+def extra_line(B, name, precision, length, dev, stream, flush, steps=2, warmup=1):
+    """A further workload and precision, event-timed like the headline on a
+    prefix of its fiber."""
+    prob = problem(name, L=length, dev=dev)
+    ctx, one_step = propagation_runner(B, prob, precision, dev, stream, flush)
+    for _ in range(warmup):
+        one_step()
+    runs = [one_step() for _ in range(steps)]
+    ctx.close()
+    t = sum(r[0] for r in runs) / steps
+    st = runs[-1][1]
+    return {"workload": workload_text(name, length), "precision": precision, "length_m": length,
+            "value": units(prob) / (t / 1e3), "unit": METRIC, "ms_per_step": t, "steps": steps, "warmup": warmup,
+            "iters_per_long_step": st["iters_total"] / max(st["long_steps"], 1),
+            "coupling_rank": st.get("coupling_rank")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16", "tf32"])
-    ap.add_argument("--length", type=float, default=0.5, help="fiber length per step [m]")
-    ap.add_argument("--workload", default="C2", choices=["C2", "C3", "C4"],
-                    help="C3 (N=15, Nt=2^14, M=20) and C4 (N=42, Nt=2^13, M=16) are for --profile-run; the metric is quoted on C2")
+    ap.add_argument("--workload", default="C4", choices=["C4", "C3", "C2"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--length", type=float, default=None, help="fiber length per step [m] (default: the full fiber)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the further workloads")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving pass (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--profile-run", action="store_true",
                     help="only the timed propagations (for ncu captures)")
     ap.add_argument("--kernel-profile", action="store_true",
@@ -509,35 +703,19 @@ def main():
     dev = local
     torch.cuda.set_device(dev)
 
-    prob = problem(seed=2 + rank, L=args.length, name=args.workload)
+    # each rank draws its own replica of the workload (seed + rank)
+    prob = problem(args.workload, L=args.length, seed=SEED[args.workload] + rank, dev=dev)
     stream = torch.cuda.Stream(device=dev)
-    ctx = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream,
-                                 io_device=True)
-    a0 = torch.from_numpy(prob.A0).to(f"cuda:{dev}")
-    out = torch.empty_like(a0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     u = units(prob)
 
-    def one_step():
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)  # L2 flush (256 MiB write), outside the timed events
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, st, rc = ctx.propagate(a0, prob.L, prob.dz, prob.M, prob.tol, out=out, check=False)
-        e1.record(stream)
-        e1.synchronize()
-        if rc != B.OK:
-            raise B.GmmnlseError(rc, "propagate")
-        return e0.elapsed_time(e1), st
-
+    ctx, one_step = propagation_runner(B, prob, args.precision, dev, stream, flush)
     for _ in range(args.warmup):
         one_step()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = []
-    stats = []
+    step_ms, stats = [], []
     with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -550,11 +728,13 @@ def main():
         wall = time.perf_counter() - t0
     dev_s = max_over_ranks(sum(step_ms) / 1e3, dist, f"cuda:{dev}")
     value = job_rate(u, args.steps, world, dev_s)
+    coupling_rank = stats[-1].get("coupling_rank")
 
     if args.profile_run:
-        line = {"profile_run": True, "precision": args.precision, "length_m": args.length,
+        line = {"profile_run": True, "workload": args.workload, "precision": args.precision, "length_m": prob.L,
                 "ms_per_step": 1e3 * dev_s / args.steps, "value": value,
-                "iters_total": stats[-1]["iters_total"], "long_steps": stats[-1]["long_steps"]}
+                "iters_total": stats[-1]["iters_total"], "long_steps": stats[-1]["long_steps"],
+                "coupling_rank": coupling_rank}
         if args.kernel_profile:
             prof = ctx.profile(prob.M, reps=20)
             line["kernels_ms"] = {k: v[0] for k, v in prof.items()}
@@ -566,6 +746,10 @@ def main():
             dist.destroy_process_group()
         return
 
+    # roofline of the dominant kernel (CUDA events on the context's stream)
+    prof = ctx.profile(prob.M, reps=20)
+    ctx.close()
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     ctx_h = B.Context.from_problem(prob, precision=args.precision, device=dev, stream=stream.cuda_stream)
     h_in = np.ascontiguousarray(prob.A0)
@@ -573,13 +757,14 @@ def main():
     ctx_h.propagate(h_in, prob.L, prob.dz, prob.M, prob.tol, out=h_out)
     torch.cuda.synchronize()
     e2e_t = []
-    for _ in range(args.steps):
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    for _ in range(e2e_steps):
         t1 = time.perf_counter()
         ctx_h.propagate(h_in, prob.L, prob.dz, prob.M, prob.tol, out=h_out)
         e2e_t.append(time.perf_counter() - t1)
     ctx_h.close()
     e2e_s = max_over_ranks(sum(e2e_t), dist, f"cuda:{dev}")
-    e2e = {"value": job_rate(u, args.steps, world, e2e_s), "unit": METRIC,
+    e2e = {"value": job_rate(u, e2e_steps, world, e2e_s), "unit": METRIC, "steps": e2e_steps,
            "h2d_bytes_per_step": int(h_in.nbytes), "d2h_bytes_per_step": int(h_out.nbytes)}
 
     if rank != 0:
@@ -587,71 +772,27 @@ def main():
             dist.destroy_process_group()
         return
 
-    # error of this path against the FP64 GPU path on a prefix: 5 mm (200 long
-    # steps) of the 6-mode run, 2 mm (8 long steps) of the 15-mode run, one
-    # long step of the 42-mode run
-    err, fp64_rate, err_prefix = None, None, None
-    if args.workload in ("C2", "C3", "C4"):
-        pre = {"C2": lambda: I.workload("C2", L=5e-3),
-               "C3": lambda: problem(L=2e-3, name="C3"),
-               "C4": lambda: problem(L=16 * 37.5e-6, name="C4")}[args.workload]()
-        err_prefix = {"C2": "5 mm", "C3": "2 mm (8 long steps)", "C4": "one long step (0.6 mm)"}[args.workload]
-        c64 = B.Context.from_problem(pre, precision="fp64", device=dev)
-        ref64, st64, _ = c64.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
-        c64.close()
-        cx = B.Context.from_problem(pre, precision=args.precision, device=dev)
-        mine, _, _ = cx.propagate(pre.A0, pre.L, pre.dz, pre.M, pre.tol)
-        cx.close()
-        err = float(np.linalg.norm(mine - ref64) / np.linalg.norm(ref64))
-        fp64_rate = units(pre) / (st64["ms"] / 1e3)
-
-    # roofline of the dominant kernel (CUDA events on the context's stream)
-    prof = ctx.profile(prob.M, reps=20)
-    dom = max(prof, key=lambda k: prof[k][0])
-    ms_dom, bytes_dom = prof[dom]
+    err, fp64_rate, err_prefix = prefix_error(B, args.workload, args.precision, dev)
     peaks, src = measured_peaks()
+    roof = roofline(prob, prof, coupling_rank, args.precision, peaks, src, args.workload)
     mixed = args.precision in ("bf16", "fp16", "tf32")
-    if dom == "contract" and prob.N > 8:
-        # a dense GEMM: 2 P KK flops per point and iteration, or with the
-        # low-rank coupling (rank r) the two GEMMs 2 r (K + P); x3 for the
-        # hi/lo products on the tensor cores; points = M substeps x Nt
-        P = prob.N * (prob.N + 1) // 2
-        KK = P if prob.fR == 0 or prob.SR is None or prob.SR is prob.SK else 2 * P
-        r = stats[-1].get("coupling_rank", P)
-        per_point = 2.0 * r * (P + P) if r < P else 2.0 * P * KK
-        flops = per_point * prob.M * prob.Nt * (3 if mixed else 1)
-        achieved = flops / (ms_dom * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "tensor" if mixed else "alu", "achieved": achieved,
-                "peak": (peaks["bf16_tflops"] * (1.1 / 2.25 if args.precision == "tf32" else 1.0)) if mixed
-                else FP32_ALU_TFLOPS, "unit": "TFLOP/s",
-                "algorithmic_flops": flops}
-        roof["frac"] = achieved / roof["peak"]
-        roof["peak_source"] = ((src + (", x 1.1/2.25 (nominal TF32 : BF16 dense)" if args.precision == "tf32" else ""))
-                               if mixed else "148 SMs x 128 FP32 FMA/clk x 2 x 2.032 GHz")
-    else:
-        achieved = bytes_dom / (ms_dom * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "peak_source": src, "algorithmic_bytes": bytes_dom}
-    roof["traffic"] = TRAFFIC.get((args.workload, args.precision, dom))
-    roof["kernel_ms"] = ms_dom
-    roof["all_kernels_ms"] = {k: v[0] for k, v in prof.items()}
-    raman = prob.fR != 0
-    launches = sum(launches_per_step(st, raman, mixed, args.precision == "fp64", N=prob.N, Nt=prob.Nt,
+    launches = sum(launches_per_step(st, prob.fR != 0, mixed, args.precision == "fp64", N=prob.N, Nt=prob.Nt,
                                      tf32=args.precision == "tf32") for st in stats)
-    ctx.close()
+    workload = workload_text(args.workload, prob.L)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3", "fp16": "f32+f16x3", "tf32": "f32+tf32x3"}[args.precision],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "f32+bf16x3", "fp16": "f32+f16x3",
+                  "tf32": "f32+tf32x3"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload] if args.length == 0.5 or args.workload != "C2"
-                   else WORKLOAD.replace("L=0.5 m", f"L={args.length} m"),
-                   "length_m": args.length, "precision": args.precision,
-                   "l2": "flushed between steps (256 MiB write)",
+        "config": {"workload": workload, "name": args.workload,
+                   "length_m": prob.L, "precision": args.precision,
+                   "l2": "flushed between steps (256 MiB write); working set above L2",
                    "units_per_step": u, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "long_steps_per_step": stats[-1]["long_steps"],
                    "iters_per_long_step": stats[-1]["iters_total"] / max(stats[-1]["long_steps"], 1),
-                   "coupling_rank": stats[-1].get("coupling_rank"),
+                   "coupling_rank": coupling_rank,
                    "rel_l2_err_vs_fp64_gpu": err, "err_prefix": err_prefix, "fp64_gpu_value": fp64_rate,
                    "wall_s": wall},
         "e2e": e2e,
@@ -659,10 +800,18 @@ def main():
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if not args.no_extra:
+        extra = {}
+        for key, (name, prec, length) in {"C4_fp32": ("C4", "fp32", 0.012), "C3_bf16": ("C3", "bf16", 0.05),
+                                          "C2_fp32": ("C2", "fp32", 0.5)}.items():
+            if (name, prec) != (args.workload, args.precision):
+                extra[key] = extra_line(B, name, prec, length, dev, stream, flush)
+        line["extra"] = extra
     if args.serve_requests > 0:
         line["serving"] = run_serving(B, dev, count=args.serve_requests)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        its = line["config"]["iters_per_long_step"] if args.workload == "C4" else C4_ITERS_PER_LONG_STEP
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, its)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -400,14 +400,17 @@ def grin_problem(name, N, Nt, dt, kind, fwhm, energy, L, dz, M, tol, seed,
 
 def step_index_problem(name, N, Nt, dt, kind, fwhm, energy, L, dz, M, tol, seed,
                        fR=0.18, self_steepening=1, radius=25e-6, na=0.22,
-                       lam0=1030e-9, n2=2.3e-20, npts=400, extent=1.5):
+                       lam0=1030e-9, n2=2.3e-20, npts=400, extent=1.5, overlap=None):
+    """`overlap(F, dA) -> S` computes Eq. 2 from the [N][G] grid profiles (for
+    instance on the GPU); by default the numpy sums of
+    overlap_tensor_from_profiles."""
     modes, info = step_index_modes(radius, na, lam0, N)
     coeffs = step_index_beta_coeffs(radius, na, lam0, modes)
     beta = beta_from_taylor(coeffs, omega_grid(Nt, dt))
     x = (np.arange(npts) - npts / 2 + 0.5) * (2 * extent * radius / npts)
     X, Y = np.meshgrid(x, x, indexing="ij")
     F = np.array([step_index_profile(m, radius, X, Y).ravel() for m in modes])
-    S = overlap_tensor_from_profiles(F, (x[1] - x[0]) ** 2)
+    S = (overlap or overlap_tensor_from_profiles)(F, (x[1] - x[0]) ** 2)
     S = 0.5 * (S + S.transpose(1, 0, 2, 3))  # symmetrise matmul rounding
     hR = raman_response(Nt, dt)
     A0 = launch_field(N, Nt, dt, kind, fwhm, energy, seed)
