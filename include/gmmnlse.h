@@ -272,28 +272,33 @@ int gmmnlse_choose_m(gmmnlse_ctx* ctx, const double* A0, double dz, double tol,
  * gmmnlse_propagate_noalloc -- gmmnlse_propagate without any memory
  * allocation.  (An addition of this library: the paper has no counterpart.)
  *
- * For callers that cannot have a library allocate device memory: work being
- * recorded into a CUDA stream capture, latency-critical loops that cannot
- * take the device-wide synchronisation of cudaMalloc/cudaFree, and programs
- * whose device memory is all owned by their own pool allocator.  It runs the
- * same transforms and trapezoid as gmmnlse_propagate with the dense CUDA-core
- * contraction (no tensor cores, no low-rank coupling; st->coupling_rank = K),
- * a host-driven iteration loop, no graphs and no events, with the
- * workspace in one static device array of 32 MiB that
- * every GPU loading the library holds until the process exits.
+ * For callers that cannot have a library allocate device memory: latency-
+ * critical loops that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree, and programs whose device memory is all owned by
+ * their own pool allocator (a framework's caching allocator, a service with
+ * a fixed memory budget per GPU).  It runs the same transforms and
+ * trapezoid as gmmnlse_propagate with the dense CUDA-core contraction (no
+ * tensor cores, no low-rank coupling; st->coupling_rank = K), a host-driven
+ * iteration loop that reads the loop state back after every iteration (the
+ * call is synchronous), no graphs and no events, with the workspace in one
+ * static device array of 32 MiB that every GPU loading the library holds
+ * until the process exits.
  *
  *   ctx   a context made beforehand with gmmnlse_create (that call allocates).
- *   A0    [N][Nt] complex128 input field in DEVICE memory (whatever
- *         prm.io_device says); Aout the same for the output.
+ *   A0    [N][Nt] complex128 input field in DEVICE memory of the context's
+ *         device (whatever prm.io_device says); Aout the same for the
+ *         output.  Any other pointer gives GMMNLSE_E_INVALID.
  *   L, dz, M, tol, st as for gmmnlse_propagate (st->ms is 0).
  *
  * An FP64 context with Nt = 16384 is rejected with GMMNLSE_E_UNSUPPORTED
- * (this entry point has one-block transforms only).
+ * (this entry point has one-block transforms only), and so is a context
+ * with a linear coupling or gain set.
  * A problem whose workspace does not fit in the 32 MiB array is rejected with
  * GMMNLSE_E_NOMEM before any work, and gmmnlse_last_error() says so.  (For
  * FP32, N = 6, Nt = 8192, M = 10 with Raman just fits.)  The first call on a
- * device sets that device up (it looks up the array's device address and
- * sets kernel attributes); make that first call before any stream capture.
+ * device sets that device up (it sets the attributes of this entry point's
+ * kernels); make that first call before any stream capture.  Every call
+ * looks up the array's device address.
  * All calls share the one array, which keeps what the last call left in it:
  * the entry point resets every part that must start from zero.  Two calls
  * whose work overlaps on the GPU (different streams, or different threads

@@ -43,6 +43,8 @@ struct LoopState {
   unsigned tc_err;         // a tensor-core contraction wait timed out
   unsigned sync_err;       // a grid barrier of the long-step kernel timed out
   unsigned arrive;         // blocks of k_trapz<R, true> that have added their sums
+  double spec_v;           // sum |psi0|^2 at the start of the current long step (0: take spec[0]),
+                           // the bound of the FP16 operand scale (set by k_advance)
 };
 
 struct Geo {
@@ -579,18 +581,23 @@ __device__ __forceinline__ void step_end(LoopState* ls, cudaGraphConditionalHand
 }
 
 // K6: end of a long step (Sec. III.D): A~(z0 + L) = (psi0 + dpsi_M) exp(i beta M dz)
-// in FP64; becomes the next psi0.  Skipped when the long step failed.  The
-// last block to finish does the long-step bookkeeping (every block reads the
-// status before it arrives).
+// in FP64; becomes the next psi0.  Skipped when the long step failed.  Each
+// block also sums |psi0|^2 of its elements (FP64) into part[blockIdx.x]; the
+// last block to finish adds those in a fixed order into ls->spec_v (the
+// energy bound of the next long step's FP16 operand scale, which a gain can
+// raise) and does the long-step bookkeeping (every block reads the status
+// before it arrives).
 template <typename R>
 __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0, cplx<R>* psiR,
                                                  const cplx<R>* __restrict__ dpsi,
                                                  const double2* __restrict__ EM, LoopState* ls,
                                                  cudaGraphConditionalHandle hStep, cudaGraphConditionalHandle hIter,
-                                                 int use_cond) {
+                                                 int use_cond, double2* part) {
   __shared__ bool last;
+  __shared__ double red[32];
   pdl_enter();
   const size_t Nn = (size_t)g.N * g.n;
+  double e2 = 0.0;
   if (ls->status == ST_OK) {
     const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
@@ -600,18 +607,25 @@ __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ ps
       const double2 w = EM[e];
       const double2 v = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
       psi0[e] = v;
+      e2 += v.x * v.x + v.y * v.y;
       if ((const void*)psiR != (const void*)psi0) psiR[e] = mk<R>((R)v.x, (R)v.y);
     }
   }
-  __syncthreads();
+  e2 = block_sum(e2, red);
   if (threadIdx.x == 0) {
+    part[blockIdx.x] = make_double2(e2, 0.0);
     __threadfence();
     last = atomicAdd(&ls->arrive, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
+  if (!last) return;
+  __threadfence();
+  double tot = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) tot += __ldcg(&part[b]).x;
+  tot = block_sum(tot, red);
+  if (threadIdx.x == 0) {
     ls->arrive = 0;
+    if (ls->status == ST_OK) ls->spec_v = tot;
     step_end(ls, hStep, hIter, use_cond);
   }
 }

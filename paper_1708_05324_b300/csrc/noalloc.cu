@@ -3,15 +3,17 @@
 // gmmnlse_propagate keeps its iteration workspace (the substep fields, pair
 // products, integrands, phase tables and loop state) in device memory that it
 // obtains with cudaMalloc on first use.  Some callers cannot let a library do
-// that: code that records work into a CUDA stream capture (where cudaMalloc
-// is not allowed), latency-critical loops that cannot afford the implicit
-// device synchronisation of cudaMalloc/cudaFree, and host applications whose
-// device memory is all handed out by their own pool allocator.  This entry
-// point runs the same kernels with the workspace placed in one fixed array in
-// device global memory, declared below; the array is part of the library
-// image, so every GPU that loads the library holds it until the process
-// exits.  The caller still provides the input and output fields (device
-// memory) and a context made beforehand with gmmnlse_create.
+// that: latency-critical loops that cannot afford the implicit device-wide
+// synchronisation of cudaMalloc/cudaFree, and host applications whose device
+// memory is all handed out by their own pool allocator (a framework's caching
+// allocator that must account for every byte, or a service with a fixed
+// memory budget per GPU).  This entry point runs the same transforms and
+// trapezoid kernels with the workspace placed in one fixed array in device
+// global memory, declared below; the array is part of the library image, so
+// every GPU that loads the library holds it until the process exits.  The
+// caller still provides the input and output fields (device memory) and a
+// context made beforehand with gmmnlse_create.  The call is synchronous: it
+// reads the iteration state back after every iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +38,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 static std::mutex g_setup_mu;
-static unsigned char* g_scratch_addr[kMaxDevices];  // device address per device, nullptr until set up
+static bool g_attrs_set[kMaxDevices];  // kernel attributes set on this device
 
 #define CKN(call)                                             \
   do {                                                        \
@@ -56,14 +58,15 @@ template <typename R, int EPT> static int set_attrs(int maxsm) {
   return GMMNLSE_OK;
 }
 
-// Once per device, with that device current: look up the device address of
-// the scratch array and allow the kernels of this file their shared memory.
+// With the device current: the device address of the scratch array (looked
+// up on every call, so that it is right for the module loaded now), and,
+// once per device, the shared-memory attributes of the kernels of this file.
 static int setup_device(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (dev < 0 || dev >= kMaxDevices) return GMMNLSE_E_INVALID;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    CKN(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  void* p = nullptr;
+  CKN(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  if (!g_attrs_set[dev]) {
     int maxsm = 0;
     CKN(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int rc = set_attrs<float, 16>(maxsm);
@@ -79,10 +82,21 @@ static int setup_device(int dev, unsigned char** out) {
     CKN(cudaFuncSetAttribute(k_fft64_rows<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_halves<+1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CKN(cudaFuncSetAttribute(k_fft64_halves<-1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    g_attrs_set[dev] = true;
   }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return GMMNLSE_OK;
+}
+
+// True if p is device (or managed) memory the device `dev` can address.
+static bool device_pointer(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Carves the workspace out of the scratch array, 256-byte aligned pieces.
@@ -233,7 +247,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
       if (hs.done) break;
     }
     k_advance<R><<<blocks_for(Nn), 256, 0, s>>>(g, w.psi0, (cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
-                                               w.EM64 + (size_t)which * Nn, w.ls, 0, 0, 0);
+                                               w.EM64 + (size_t)which * Nn, w.ls, 0, 0, 0, w.part);
     CKN(cudaGetLastError());
     CKN(cudaMemcpyAsync(&hs, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
     CKN(cudaStreamSynchronize(s));
@@ -278,6 +292,10 @@ extern "C" int gmmnlse_propagate_noalloc(gmmnlse_ctx* c, const double* A0, doubl
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(c->mu);
   CKN(cudaSetDevice(c->prm.device));
+  if (!device_pointer(A0, c->prm.device) || !device_pointer(Aout, c->prm.device)) {
+    gm_set_last_error_text("gmmnlse_propagate_noalloc: A0 and Aout must be device memory of the context's device");
+    return GMMNLSE_E_INVALID;
+  }
   unsigned char* base = nullptr;
   rc = setup_device(c->prm.device, &base);
   if (rc) return rc;

@@ -509,7 +509,7 @@ static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, 
   const size_t Nn = (size_t)c->N * c->n;
   pdl_launch(k_advance<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, jb->psi0, (cplx<R>*)jb->psiR,
              (const cplx<R>*)jb->dpsi, (const double2*)(jb->EM64 + (size_t)which * Nn), jb->ls, hStep, hIter,
-             use_cond);
+             use_cond, jb->part);
 }
 
 template <typename R>
@@ -940,7 +940,8 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
         case 4: launch_k5<R>(jb, g, s, 0, 0); break;
         default:
           k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR,
-                                                               (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls, 0, 0, 0);
+                                                               (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls, 0, 0, 0,
+                                                               jb->part);
           break;
       }
       CK(cudaGetLastError());

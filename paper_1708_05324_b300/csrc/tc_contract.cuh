@@ -12,8 +12,9 @@
 // takes power-of-two scales: G by 2^eG (its largest entry below 2^14, set at
 // context creation) and V by 2^eV from a bound on |V|: |U_mn(t)| <=
 // sum_p |A_p(t)|^2 <= sum_t sum_p |A_p(t)|^2 = (1/Nt) sum_w |psi0|^2 and
-// |h_R * U| <= dt sum |h_R| max |U| < 2 max |U| (the energy does not grow
-// along the fiber), so 2^eV (2 x bound) < 2^14.  The epilogue undoes both
+// |h_R * U| <= dt sum |h_R| max |U| < 2 max |U|, so 2^eV (2 x bound) < 2^14,
+// the bound taken anew at the start of every long step (an energy that a
+// gain raises along the fiber raises it too).  The epilogue undoes both
 // exactly (a power of two).
 // Points are the MMA's M dimension, so after tcgen05.ld each epilogue thread
 // holds R_r(t) for its own point t and forms the l-sum in registers, with the
@@ -93,9 +94,12 @@ __host__ __device__ constexpr int tc_row_block(int P) { return P <= 256 ? (P + 1
 __host__ __device__ constexpr int tc_cluster(int NB) { return NB >= 32 ? 2 : 1; }
 
 // FP16 scale exponent of V: 2^eV (2 x the bound on |V|) < 2^14; the bound
-// is (1/Nt) sum_w |psi0|^2, summed at the start of the propagation.
+// is (1/Nt) sum_w |psi0|^2 at the start of the current long step (summed by
+// the previous long step's advance; at the first, by the input sums), so it
+// follows an energy that grows along the fiber (gain); within one long step
+// the 4x headroom below the FP16 maximum covers the growth.
 __device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n) {
-  double b = ls->spec[0] / (double)n;
+  double b = (ls->spec_v > 0.0 ? ls->spec_v : ls->spec[0]) / (double)n;
   if (!(b > 0.0) || !isfinite(b)) b = 1.0;
   int e;
   frexp(2.0 * b, &e);  // 2 b < 2^e

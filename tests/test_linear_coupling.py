@@ -124,10 +124,12 @@ def test_linear_coupling_rejections():
         with pytest.raises(B.GmmnlseError):
             ctx.set_linear_coupling(bad)
         ctx.set_linear_coupling(coupling(3))
-        out = np.empty_like(prob.A0)
+        import torch
+        a0 = torch.from_numpy(prob.A0).cuda()
+        out = torch.empty_like(a0)
         st = B.Stats()
-        rc = ctx.lib.gmmnlse_propagate_noalloc(ctx.handle, prob.A0.ctypes.data, L, DZ, M, TOL,
-                                               out.ctypes.data, C.byref(st))
+        rc = ctx.lib.gmmnlse_propagate_noalloc(ctx.handle, a0.data_ptr(), L, DZ, M, TOL,
+                                               out.data_ptr(), C.byref(st))
         assert rc == B.E_UNSUPPORTED
     finally:
         ctx.close()
@@ -199,3 +201,28 @@ def test_served_requests_take_the_linear_terms(precision, bar):
         srv.close()
         cq.close()
         c0.close()
+
+
+@pytest.mark.parametrize("mixed", ["fp16", "bf16"])
+def test_fp16_scale_follows_an_energy_that_a_gain_raises_tenfold(mixed):
+    """MIXED_FP16 scales its tensor-core operands by a power of two from an
+    energy bound; with a gain that raises the energy 10x over the fiber
+    (exp(2 g L) = 10) a bound taken once at the input would overflow FP16.
+    The bound is taken anew at every long step, so the result matches the
+    oracle at the mixed-precision bar."""
+    from paper_1708_05324_b300 import binding as B
+    N, Nt, fR = 10, 256, 0.18
+    prob = problem(N, Nt, fR)
+    g = np.full(N, np.log(10.0) / (2 * L))
+    fib = O.Fiber.from_problem(prob, gain=g)
+    ref = O.mpa_propagate(fib, prob.A0, L, DZ, M, TOL)[0]
+    e_in = float(np.sum(np.abs(prob.A0) ** 2))
+    assert float(np.sum(np.abs(ref) ** 2)) > 9.0 * e_in  # the energy grew about tenfold
+    ctx = context(prob, mixed)
+    try:
+        ctx.set_gain(g)
+        out, st, rc = ctx.propagate(prob.A0, L, DZ, M, 1e-9, check=False)
+    finally:
+        ctx.close()
+    assert rc == B.OK
+    assert rel(out, ref) < 1e-3
