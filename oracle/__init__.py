@@ -17,6 +17,7 @@ from .gmmnlse import (  # noqa: F401
     Fiber,
     circular_convolution,
     circular_convolution_direct,
+    coupling_factor,
     energy_spectral,
     freq_from_time,
     integrand,
@@ -30,6 +31,7 @@ from .gmmnlse import (  # noqa: F401
     photon_number,
     raman_sum,
     rk4ip_propagate,
+    saturation_term,
     substep_schedule,
     time_from_freq,
 )

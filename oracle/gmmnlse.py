@@ -60,14 +60,24 @@ class Fiber:
     Raman response h_R [Nt] sampled at t_k = k dt (1/s), time step dt (s),
     centre wavelength lam0 (m), n2 (m^2/W) and the self-steepening switch."""
 
-    def __init__(self, beta, SK, SR, fR, hR, dt, lam0, n2, self_steepening=True, Q=None, gain=None):
+    def __init__(self, beta, SK, SR, fR, hR, dt, lam0, n2, self_steepening=True, Q=None, gain=None,
+                 Q_profile=None, Q_profile_dz=None, sat=0.0):
         self.beta = np.asarray(beta, dtype=np.float64)
         # linear mode coupling Q[n][p] (Sec. IV, "Linear mode coupling"): the
         # extra right-hand-side term C_p = i sum_n Q_np A_n, or None
         self.Q = None if Q is None else np.asarray(Q, dtype=np.float64)
+        # its longitudinal profile (Sec. IV: [n^2 - n_p^2] = eps(x, y) f(z)):
+        # Q_np(z) = Q_np f(z), f sampled at z = k Q_profile_dz and linearly
+        # interpolated (None: f = 1)
+        self.Q_profile = None if Q_profile is None else np.asarray(Q_profile, dtype=np.float64)
+        self.Q_profile_dz = Q_profile_dz
         # small-signal field gain g_p [1/m] (Sec. IV, "Saturating gain", its
         # lowest order): the extra term g_p A_p, or None
         self.gain = None if gain is None else np.asarray(gain, dtype=np.float64)
+        # its saturation (the same passage's first-order term):
+        # - sat sum_{l,m,n} S^R_plmn A_l int A_m A_n^* dtau, sat = 1/I_sat of
+        # the paper's expression (0: none)
+        self.sat = float(sat)
         self.N, self.Nt = self.beta.shape
         self.SK = np.asarray(SK, dtype=np.float64)
         self.SR = None if SR is None else np.asarray(SR, dtype=np.float64)
@@ -146,18 +156,42 @@ def nonlinear_bracket(fib: Fiber, A):
     return out
 
 
-def nonlinear_operator(fib: Fiber, Aw):
-    """N(A~) = i (n2 w0/c) s(w) F{bracket(F^-1 A~)} for a spectral field A~,
-    plus the linear mode coupling C_p = i sum_n Q_np A~_n and the small-signal
-    gain g_p A~_p when the fiber has them (Sec. IV: terms added to the right-
-    hand side of Eq. 1; neither depends on time, so each acts on every
-    frequency alike)."""
-    NL = nonlinear_bracket(fib, time_from_freq(Aw))
+def coupling_factor(fib: Fiber, z):
+    """f(z) of the coupling profile Q_np(z) = Q_np f(z): linear interpolation
+    of the samples f_k at z = k dz_f (held constant past the last sample)."""
+    if fib.Q_profile is None:
+        return 1.0
+    zs = np.arange(len(fib.Q_profile)) * fib.Q_profile_dz
+    return float(np.interp(z, zs, fib.Q_profile))
+
+
+def saturation_term(fib: Fiber, A):
+    """sum_{l,m,n} S^R_plmn A_l(t) int A_m(tau) A_n^*(tau) dtau (the
+    saturating-gain term of Sec. IV without its factor -1/I_sat), the
+    integral as the sum dt sum_k over the time window.  A: [N][Nt] time
+    domain -> [N][Nt]."""
+    N = A.shape[0]
+    SR = fib.SK if fib.SR is None else fib.SR
+    E = fib.dt * (A @ np.conj(A).T)  # E[m, n] = int A_m A_n^* dtau
+    T = (np.asarray(SR).reshape(N * N, N * N) @ E.reshape(N * N)).reshape(N, N)  # T[p, l]
+    return T @ A
+
+
+def nonlinear_operator(fib: Fiber, Aw, z=0.0):
+    """N(A~) = i (n2 w0/c) s(w) F{bracket(F^-1 A~)} for a spectral field A~ at
+    fiber position z, plus the terms Sec. IV adds to the right-hand side of
+    Eq. 1 when the fiber has them: the linear mode coupling
+    C_p = i sum_n Q_np(z) A~_n, the small-signal gain g_p A~_p and its
+    saturation - sat F{sum_lmn S^R_plmn A_l int A_m A_n^* dtau}."""
+    At = time_from_freq(Aw)
+    NL = nonlinear_bracket(fib, At)
     out = 1j * fib.gamma0 * fib.shock * freq_from_time(NL)
     if fib.Q is not None:
-        out = out + 1j * (fib.Q.T @ Aw)  # (Q^T A)_p = sum_n Q[n][p] A_n
+        out = out + 1j * coupling_factor(fib, z) * (fib.Q.T @ Aw)  # (Q^T A)_p = sum_n Q[n][p] A_n
     if fib.gain is not None:
         out = out + fib.gain[:, None] * Aw
+    if fib.sat != 0.0:
+        out = out - fib.sat * freq_from_time(saturation_term(fib, At))
     return out
 
 
@@ -171,14 +205,14 @@ def phase_factor(fib: Fiber, zrel):
     return np.exp(1j * (fib.beta * zrel))
 
 
-def integrand(fib: Fiber, psi_j, zrel):
-    """Integrand of Eq. MPA_eq at z_j: A_j = F^-1{psi_j e^{D (z_j - z0)}},
+def integrand(fib: Fiber, psi_j, zrel, z0=0.0):
+    """Integrand of Eq. MPA_eq at z_j = z0 + zrel: A_j = F^-1{psi_j e^{D (z_j - z0)}},
     I_j = i (n2 w0/c) s(w) F{NL(A_j)} e^{-D (z_j - z0)}."""
     E = phase_factor(fib, zrel)
-    return nonlinear_operator(fib, psi_j * E) * np.conj(E)
+    return nonlinear_operator(fib, psi_j * E, z0 + zrel) * np.conj(E)
 
 
-def mpa_long_step(fib: Fiber, psi0, dz, M, tol, max_iter=50, fixed_iters=0):
+def mpa_long_step(fib: Fiber, psi0, dz, M, tol, max_iter=50, fixed_iters=0, z0=0.0):
     """One long step L = M dz from z0 (Sec. III.D).  psi0 = A~(z0, omega).
 
     Returns (A~(z0 + L), iterations, eps trace, status).  Iteration n builds
@@ -187,14 +221,14 @@ def mpa_long_step(fib: Fiber, psi0, dz, M, tol, max_iter=50, fixed_iters=0):
     status E_NOT_CONVERGED after max_iter updates, E_NONFINITE on NaN/Inf."""
     zrel = [j * dz for j in range(M + 1)]
     I = [None] * (M + 1)
-    I[0] = integrand(fib, psi0, zrel[0])
+    I[0] = integrand(fib, psi0, zrel[0], z0)
     psi = [psi0] * (M + 1)  # psi^(1)(z_j) = psi(z0)
     trace = []
     n = 0
     status = OK
     while True:
         for j in range(1, M + 1):
-            I[j] = integrand(fib, psi[j], zrel[j])
+            I[j] = integrand(fib, psi[j], zrel[j], z0)
         new = [psi0]
         acc = np.zeros_like(psi0)
         for j in range(1, M + 1):
@@ -242,7 +276,7 @@ def mpa_propagate(fib: Fiber, A0, L, dz, M, tol, max_iter=50, fixed_iters=0):
     stats = dict(iters=[], eps=[], z=0.0, status=OK)
     done = 0
     for Mj in substep_schedule(L, dz, M):
-        out, n, trace, status = mpa_long_step(fib, psi, dz, Mj, tol, max_iter, fixed_iters)
+        out, n, trace, status = mpa_long_step(fib, psi, dz, Mj, tol, max_iter, fixed_iters, z0=done * dz)
         stats["iters"].append(n)
         stats["eps"].append(trace)
         if status != OK:
@@ -264,12 +298,13 @@ def iptrap_propagate(fib: Fiber, A0, L, dz, tol=1e-15, max_iter=200):
     Aw = freq_from_time(np.asarray(A0, dtype=np.complex128))
     E1 = phase_factor(fib, dz)
     steps = int(round(L / dz))
-    for _ in range(steps):
-        base = E1 * (Aw + 0.5 * dz * nonlinear_operator(fib, Aw))
-        X = base + 0.5 * dz * E1 * nonlinear_operator(fib, Aw)
+    for k in range(steps):
+        z = k * dz
+        base = E1 * (Aw + 0.5 * dz * nonlinear_operator(fib, Aw, z))
+        X = base + 0.5 * dz * E1 * nonlinear_operator(fib, Aw, z)
         prev = np.inf
         for _ in range(max_iter):
-            Xn = base + 0.5 * dz * nonlinear_operator(fib, X)
+            Xn = base + 0.5 * dz * nonlinear_operator(fib, X, z + dz)
             d = float(np.linalg.norm(Xn - X)) / max(float(np.linalg.norm(Xn)), 1e-300)
             X = Xn
             if d < tol or d >= prev:
@@ -285,13 +320,14 @@ def rk4ip_propagate(fib: Fiber, A0, L, h):
     Aw = freq_from_time(np.asarray(A0, dtype=np.complex128))
     Eh = phase_factor(fib, 0.5 * h)
     steps = int(round(L / h))
-    Nop = lambda X: nonlinear_operator(fib, X)  # noqa: E731
-    for _ in range(steps):
+    Nop = lambda X, z: nonlinear_operator(fib, X, z)  # noqa: E731
+    for k in range(steps):
+        z = k * h  # the stages sit at z, z + h/2, z + h/2, z + h
         AI = Eh * Aw
-        k1 = Eh * Nop(Aw)
-        k2 = Nop(AI + 0.5 * h * k1)
-        k3 = Nop(AI + 0.5 * h * k2)
-        k4 = Nop(Eh * (AI + h * k3))
+        k1 = Eh * Nop(Aw, z)
+        k2 = Nop(AI + 0.5 * h * k1, z + 0.5 * h)
+        k3 = Nop(AI + 0.5 * h * k2, z + 0.5 * h)
+        k4 = Nop(Eh * (AI + h * k3), z + h)
         Aw = Eh * (AI + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3)) + (h / 6.0) * k4
     return time_from_freq(Aw)
 

@@ -111,3 +111,90 @@ def test_gain_with_coupling_and_dispersion_converges_to_the_matrix_exponential()
     e = [rel(O.mpa_propagate(fib, prob.A0, L, L / k, 4, 1e-15)[0], exact) for k in (24, 48)]
     assert e[0] < 1e-3
     assert e[0] / e[1] == pytest.approx(4.0, rel=0.05)
+
+
+# ----------------------------------------------------------------------------
+# Saturating gain (Sec. IV): g_p A_p - sat sum_lmn S^R_plmn A_l int A_m A_n^* dtau
+# ----------------------------------------------------------------------------
+def _single_mode(SR_factor=2.0, Nt=128):
+    prob = I.grin_problem("sat", N=1, Nt=Nt, dt=2e-12 / Nt, kind="gaussian", fwhm=150e-15, energy=1e-9,
+                          L=1e-3, dz=1e-4, M=5, tol=1e-14, seed=7, fR=0.0, s_from="gh")
+    return prob, prob.SK * SR_factor
+
+
+def test_saturated_gain_of_one_mode_follows_the_logistic_energy_law():
+    """One mode, no dispersion, no Kerr: dA/dz = (g - sat S^R_1111 W) A with
+    W = int |A|^2 dt, so dW/dz = 2 g W - 2 sat S^R W^2, solved by
+    1/W = e^{-2gz}/W0 + (sat S^R/g)(1 - e^{-2gz}), and A keeps its shape and
+    phase: A(z, t) = A0(t) sqrt(W/W0).  S^R is taken twice S^K, so that the
+    Raman tensor (not the Kerr one) is the one that must saturate.  The MPA
+    converges to it at second order."""
+    prob, SR = _single_mode()
+    g = 20.0
+    W0 = prob.dt * float(np.sum(np.abs(prob.A0) ** 2))
+    sat = 0.2 * g / (SR[0, 0, 0, 0] * W0)  # the energy saturates towards 5 W0
+    fib = O.Fiber.from_problem(prob, beta=np.zeros_like(prob.beta), n2=0.0, SR=SR, fR=0.0, gain=np.array([g]),
+                               sat=sat)
+    L = 0.05
+    W = 1.0 / (np.exp(-2 * g * L) / W0 + (sat * SR[0, 0, 0, 0] / g) * (1 - np.exp(-2 * g * L)))
+    exact = prob.A0 * np.sqrt(W / W0)
+    assert W / W0 > 1.5 and W / W0 < 0.5 * np.exp(2 * g * L)  # gained, and clearly saturated
+    e = [rel(O.mpa_propagate(fib, prob.A0, L, L / k, 5, 1e-15)[0], exact) for k in (40, 80)]
+    assert e[1] < 1e-4
+    assert e[0] / e[1] == pytest.approx(4.0, rel=0.05)
+    r = [rel(O.rk4ip_propagate(fib, prob.A0, L, L / k), exact) for k in (20, 40)]
+    assert r[0] / r[1] == pytest.approx(16.0, rel=0.15)
+
+
+def test_saturation_energy_rate_of_several_modes():
+    """dW/dz of the total energy W = sum_p int |A_p|^2 dt under Eq. 1 plus the
+    saturating gain, at any field: Kerr without self-steepening and the
+    dispersion keep W, so dW/dz = 2 g W - 2 sat Re sum_plmn S^R_plmn E_mn E_lp
+    with E_mn = int A_m A_n^* dt (equal gain g in every mode).  The oracle's
+    operator, applied to a random three-mode field, against that sum written
+    as explicit loops."""
+    prob = I.workload("C1", Nt=64, dt=2e-12 / 64, fR=0.0, energy=2e-9)
+    N, dt = prob.N, prob.dt
+    g, sat = 7.0, 0.3
+    fib = O.Fiber.from_problem(prob, self_steepening=False, gain=np.full(N, g), sat=sat)
+    rng = np.random.default_rng(5)
+    A = prob.A0 * (1 + 0.3 * (rng.standard_normal(prob.A0.shape) + 1j * rng.standard_normal(prob.A0.shape)))
+    Aw = O.freq_from_time(A)
+    rate = 2 * float(np.real(np.sum(np.conj(Aw) * O.nonlinear_operator(fib, Aw)))) * dt / prob.Nt
+    E = np.zeros((N, N), dtype=complex)
+    for m in range(N):
+        for n in range(N):
+            E[m, n] = dt * np.sum(A[m] * np.conj(A[n]))
+    sat_sum = 0.0
+    for p in range(N):
+        for l in range(N):
+            for m in range(N):
+                for n in range(N):
+                    sat_sum += prob.SK[p, l, m, n] * (E[m, n] * E[l, p]).real
+    W = dt * float(np.sum(np.abs(A) ** 2))
+    assert rate == pytest.approx(2 * g * W - 2 * sat * sat_sum, rel=1e-10)
+    assert 2 * sat * sat_sum > 0.1 * 2 * g * W  # the saturation is a sizeable part of the rate
+
+
+# ----------------------------------------------------------------------------
+# Linear mode coupling with a longitudinal profile: Q_np(z) = Q_np f(z)
+# ----------------------------------------------------------------------------
+def test_coupling_profile_gives_the_integrated_coupling():
+    """dA/dz = i f(z) Q^T A with f(z) = 1 + z/ell (tabulated, linearly
+    interpolated: exact for a ramp) has A(z) = expm(i F(z) Q^T) A0,
+    F(z) = z + z^2 / (2 ell).  The MPA takes f at every substep z_j (second
+    order: 4x per halving of dz), RK4IP at its stage positions z, z + h/2,
+    z + h (fourth order: 16x)."""
+    ell = 2e-3
+    zs_dz = 1e-4
+    f = 1.0 + np.arange(200) * zs_dz / ell
+    prob, fib = _linear_fiber()
+    fib = O.Fiber.from_problem(prob, beta=fib.beta, n2=0.0, Q=Q3, Q_profile=f, Q_profile_dz=zs_dz)
+    L = 6e-3
+    F = L + L * L / (2 * ell)
+    exact = sl.expm(1j * F * Q3.T) @ prob.A0
+    e = [rel(O.mpa_propagate(fib, prob.A0, L, L / k, 4, 1e-15)[0], exact) for k in (24, 48)]
+    assert e[0] < 1e-3
+    assert e[0] / e[1] == pytest.approx(4.0, rel=0.05)
+    r = [rel(O.rk4ip_propagate(fib, prob.A0, L, L / k), exact) for k in (12, 24)]
+    assert r[0] / r[1] == pytest.approx(16.0, rel=0.1)

@@ -33,12 +33,12 @@ MUTATIONS = {
         ("acc = acc + 0.5 * dz * (I[j - 1] + I[j])", "acc = acc + dz * I[j - 1]"),
     ],
     "integrand_phase_sign": [
-        ("return nonlinear_operator(fib, psi_j * E) * np.conj(E)",
-         "return nonlinear_operator(fib, psi_j * E) * E"),
+        ("return nonlinear_operator(fib, psi_j * E, z0 + zrel) * np.conj(E)",
+         "return nonlinear_operator(fib, psi_j * E, z0 + zrel) * E"),
     ],
     "interaction_picture_phase_dropped": [
-        ("return nonlinear_operator(fib, psi_j * E) * np.conj(E)",
-         "return nonlinear_operator(fib, psi_j) * np.conj(E)"),
+        ("return nonlinear_operator(fib, psi_j * E, z0 + zrel) * np.conj(E)",
+         "return nonlinear_operator(fib, psi_j, z0 + zrel) * np.conj(E)"),
     ],
     "substep_index_shift": [
         ("zrel = [j * dz for j in range(M + 1)]", "zrel = [(j + 1) * dz for j in range(M + 1)]"),
@@ -76,7 +76,7 @@ MUTATIONS = {
         ("eps = math.sqrt(diff / size) if (finite and size > 0)", "eps = math.sqrt(diff) if (finite and size > 0)"),
     ],
     "initial_integrand_reused": [
-        ("I[0] = integrand(fib, psi0, zrel[0])", "I[0] = 0.0 * psi0"),
+        ("I[0] = integrand(fib, psi0, zrel[0], z0)", "I[0] = 0.0 * psi0"),
     ],
 }
 
@@ -128,13 +128,24 @@ def test_planted_mistake_is_caught(name, monkeypatch):
 
 
 # Planted mistakes in the added right-hand-side terms of Sec. IV (mode
-# coupling and gain), run against the pins of tests/test_oracle_coupling.py.
+# coupling with its longitudinal profile, gain and its saturation), run
+# against the pins of tests/test_oracle_coupling.py.
 import test_oracle_coupling as coupling_pins  # noqa: E402
 
+Q_LINE = "out = out + 1j * coupling_factor(fib, z) * (fib.Q.T @ Aw)"
 COUPLING_MUTATIONS = {
-    "coupling_transposed": [("out = out + 1j * (fib.Q.T @ Aw)", "out = out + 1j * (fib.Q @ Aw)")],
-    "coupling_sign": [("out = out + 1j * (fib.Q.T @ Aw)", "out = out - 1j * (fib.Q.T @ Aw)")],
+    "coupling_transposed": [(Q_LINE, "out = out + 1j * coupling_factor(fib, z) * (fib.Q @ Aw)")],
+    "coupling_sign": [(Q_LINE, "out = out - 1j * coupling_factor(fib, z) * (fib.Q.T @ Aw)")],
     "gain_on_the_wrong_modes": [("out = out + fib.gain[:, None] * Aw", "out = out + fib.gain[::-1, None] * Aw")],
+    "saturation_sign": [("out = out - fib.sat * freq_from_time(saturation_term(fib, At))",
+                         "out = out + fib.sat * freq_from_time(saturation_term(fib, At))")],
+    "saturation_integral_without_dt": [("E = fib.dt * (A @ np.conj(A).T)", "E = A @ np.conj(A).T")],
+    "saturation_on_the_kerr_tensor": [("SR = fib.SK if fib.SR is None else fib.SR", "SR = fib.SK")],
+    "profile_taken_at_the_long_step_origin": [
+        ("return nonlinear_operator(fib, psi_j * E, z0 + zrel) * np.conj(E)",
+         "return nonlinear_operator(fib, psi_j * E, z0) * np.conj(E)")],
+    "rk4ip_midpoint_stage_at_the_step_start": [
+        ("k2 = Nop(AI + 0.5 * h * k1, z + 0.5 * h)", "k2 = Nop(AI + 0.5 * h * k1, z)")],
 }
 
 COUPLING_PIN_TESTS = [getattr(coupling_pins, name) for name in dir(coupling_pins)
