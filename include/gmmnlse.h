@@ -176,7 +176,8 @@ int gmmnlse_propagate(gmmnlse_ctx* ctx, const double* A0, double L, double dz, i
  * Call it between propagations: it waits for the context's stream and
  * retires the context's captured graphs; server requests on this context
  * must not be in flight.  gmmnlse_propagate_noalloc returns
- * GMMNLSE_E_UNSUPPORTED while a Q is set.  Non-finite entries give
+ * GMMNLSE_E_UNSUPPORTED while a Q is set.  gmmnlse_set_coupling_profile
+ * makes Q depend on z.  Non-finite entries give
  * GMMNLSE_E_INVALID; a failed device allocation GMMNLSE_E_NOMEM.
  */
 int gmmnlse_set_linear_coupling(gmmnlse_ctx* ctx, const double* Q);
@@ -184,7 +185,7 @@ int gmmnlse_set_linear_coupling(gmmnlse_ctx* ctx, const double* Q);
 /*
  * gmmnlse_set_gain -- add small-signal gain to the right-hand side of Eq. 1:
  * the term g_p A_p, the lowest order of the gain of Sec. IV ("Saturating
- * gain"; the saturation terms are not built).
+ * gain"; its saturation is gmmnlse_set_gain_saturation).
  *
  *   g   [N] field gain g_p [1/m] per mode (energy grows as exp(2 g_p z)
  *       alone), host pointer; NULL removes the term.  Copied.
@@ -195,6 +196,49 @@ int gmmnlse_set_linear_coupling(gmmnlse_ctx* ctx, const double* Q);
  * GMMNLSE_E_INVALID.
  */
 int gmmnlse_set_gain(gmmnlse_ctx* ctx, const double* g);
+
+/*
+ * gmmnlse_set_gain_saturation -- add the saturation of the gain to the
+ * right-hand side of Eq. 1, the first-order term of Sec. IV ("Saturating
+ * gain"): - sat sum_{l,m,n} S^R_plmn A_l(t) int A_m(tau) A_n^*(tau) dtau,
+ * the integral over the time window at the current z (dt sum_k), beside the
+ * small-signal gain g_p A_p of gmmnlse_set_gain.
+ *
+ *   sat  the coefficient of the term (the paper's 1/I_sat, read as carrying
+ *        the units that make the term a rate of A: [1/(J m)] with S^R in
+ *        1/m^2); 0 removes the term.  S^R is the context's (S^K when it was
+ *        created without one).
+ *
+ * For an S^R of Eq. 2 (real, symmetric) the term is - sat sum_l R_pl A_l with
+ * the real symmetric R_pl = sum_mn S^R_plmn int A_m A_n^* dtau, constant in
+ * time within a substep: per substep the library forms the FP64 time
+ * integrals of the pair products, R_pl, and adds the term to the MPA's
+ * integrand (and to the RK4IP operator).  Same rules as
+ * gmmnlse_set_linear_coupling (call between propagations; the allocation-
+ * free entry point refuses it).  Negative or non-finite sat gives
+ * GMMNLSE_E_INVALID; the device copy of S^R (8 K P bytes) GMMNLSE_E_NOMEM if
+ * it cannot be allocated.
+ */
+int gmmnlse_set_gain_saturation(gmmnlse_ctx* ctx, double sat);
+
+/*
+ * gmmnlse_set_coupling_profile -- a longitudinal profile of the linear mode
+ * coupling (Sec. IV, "Linear mode coupling including disorder": an index
+ * perturbation eps(x, y) f(z) gives Q_np(z) = Q_np f(z), e.g. a long-period
+ * grating's cos(2 pi z / period) or a sampled disorder record).
+ *
+ *   f      [count] samples f(z_k) at z_k = k fdz from the fiber's start,
+ *          host pointer (copied), linearly interpolated between samples and
+ *          held at f[count - 1] beyond the last; NULL removes the profile
+ *          (f = 1).
+ *   fdz    sample spacing [m].
+ *
+ * Multiplies the Q of gmmnlse_set_linear_coupling (no effect without one) at
+ * every substep's position z (the MPA) or stage position (RK4IP).  Same rules
+ * as gmmnlse_set_linear_coupling; count < 1, fdz <= 0 or non-finite samples
+ * give GMMNLSE_E_INVALID.
+ */
+int gmmnlse_set_coupling_profile(gmmnlse_ctx* ctx, const double* f, int count, double fdz);
 
 /*
  * gmmnlse_overlap_tensor -- the mode overlap tensor of Eq. 2 from mode
@@ -267,6 +311,46 @@ int gmmnlse_propagate_rk4ip(gmmnlse_ctx* ctx, const double* A0, double L, double
 int gmmnlse_choose_m(gmmnlse_ctx* ctx, const double* A0, double dz, double tol,
                      const int* candidates, int count, int trial_substeps, double* scratch,
                      double* sec_per_substep, int* M_best);
+
+/* The step sizes chosen by gmmnlse_choose_step. */
+typedef struct gmmnlse_step {
+    double dz;       /* substep [m]: L divided by a whole number */
+    int M;           /* substeps per long step, 1..64 */
+    double z_nl;     /* nonlinear length 1 / (gamma0 max_p S^K_pppp P0) [m] */
+    double z_im;     /* intermode beat length 1 / max_p |db0_p| [m] (inf: one mode group) */
+    double err_est;  /* step-doubling estimate of the relative L2 error over L at
+                        the last trial dz (0 when rtol = 0) */
+    int trials;      /* trial propagations made */
+} gmmnlse_step;
+
+/*
+ * gmmnlse_choose_step -- choose the substep dz and the substeps per long step
+ * M from the problem's length scales (Sec. III.D: the long step L_long =
+ * M dz << z_NL and the substep dz << z_IM, the nonlinear length and the
+ * intermode beat length), refined to an accuracy target.
+ *
+ *   A0       [N][Nt] launched field (host unless prm.io_device); not changed.
+ *   L        fiber length [m].
+ *   rtol     target relative L2 error of the field at L; 0 keeps the length-
+ *            scale rule alone: dz = min(z_NL / 200, z_IM / 10) (the paper's
+ *            usual z_NL / dz of about 200; one tenth of the beat length).
+ *   tol      iteration tolerance of the trial propagations.
+ *   scratch  [2][N][Nt] complex buffer on the same side as A0 (trial fields).
+ *   out      the choice.
+ *
+ * With rtol > 0 the library propagates a trial piece (one nonlinear length,
+ * or L if shorter) at dz and dz/2: the trapezoid rule is second order, so
+ * (4/3) |A(dz) - A(dz/2)| / |A(dz/2)| estimates the error of A(dz), scaled
+ * linearly to L; dz shrinks (at most 4 rounds) until that meets rtol, and
+ * never exceeds the length-scale rule.  Then dz = L / ceil(L / dz) and
+ * M = floor(z_NL / (10 dz)), clamped to 1..64 and to the substep count.
+ * z_NL takes the peak power P0 = max_t sum_p |A_p(t)|^2 and gamma0 =
+ * n2 omega0 / c; db0_p = beta_p(0) - beta_1(0) of the context's beta.
+ * Synchronous.  GMMNLSE_E_INVALID for bad arguments, a zero or non-finite
+ * field, or n2 <= 0; a failing trial's status is returned.
+ */
+int gmmnlse_choose_step(gmmnlse_ctx* ctx, const double* A0, double L, double rtol, double tol,
+                        double* scratch, gmmnlse_step* out);
 
 /*
  * gmmnlse_propagate_noalloc -- gmmnlse_propagate without any memory

@@ -24,6 +24,7 @@ from .gmmnlse import (  # noqa: F401
     overlap_tensor,
     iptrap_propagate,
     kerr_sum,
+    length_scales,
     mpa_long_step,
     mpa_propagate,
     nonlinear_bracket,

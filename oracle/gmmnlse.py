@@ -360,3 +360,24 @@ def photon_number(fib: Fiber, Aw):
     w = fib.omega0 + fib.omega
     mask = w > 0
     return float(np.sum(np.abs(Aw[:, mask]) ** 2 / w[None, mask]))
+
+
+# ----------------------------------------------------------------------------
+# Length scales of the step sizes (Sec. III.D)
+# ----------------------------------------------------------------------------
+def length_scales(fib: Fiber, A0):
+    """The two length scales that set the MPA's step sizes (Sec. III.D):
+    the nonlinear length z_NL = 1 / (gamma0 S_max P0), the single-mode
+    estimate A_eff/(n2 omega0 P0) with 1/A_eff the largest self-overlap
+    S^K_pppp and the speed of light that the paper's printed form omits
+    (gamma0 = n2 omega0 / c), P0 the peak of sum_p |A_p(t)|^2; and the
+    intermode beat length z_IM = 1 / max_p |delta beta0^(p)|, delta beta0^(p)
+    = beta_p(omega = 0) - beta_1(omega = 0) (infinite for a single mode).
+    A0: [N][Nt] time domain.  Returns (z_NL, z_IM)."""
+    A0 = np.asarray(A0)
+    P0 = float(np.max(np.sum(np.abs(A0) ** 2, axis=0)))
+    S_max = max(float(fib.SK[p, p, p, p]) for p in range(fib.N))
+    z_nl = 1.0 / (fib.gamma0 * S_max * P0)
+    db0 = np.abs(fib.beta[:, 0] - fib.beta[0, 0])
+    z_im = 1.0 / float(np.max(db0)) if np.max(db0) > 0 else math.inf
+    return z_nl, z_im

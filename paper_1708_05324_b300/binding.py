@@ -28,7 +28,8 @@ EXPORTS = [
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
     "gmmnlse_propagate_rk4ip", "gmmnlse_set_linear_coupling",
-    "gmmnlse_set_gain", "gmmnlse_overlap_tensor",
+    "gmmnlse_set_gain", "gmmnlse_overlap_tensor", "gmmnlse_set_gain_saturation",
+    "gmmnlse_set_coupling_profile", "gmmnlse_choose_step",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -40,6 +41,14 @@ class Params(C.Structure):
         ("max_iter", C.c_int), ("fixed_iters", C.c_int), ("device", C.c_int),
         ("stream", C.c_void_p), ("io_device", C.c_int),
     ]
+
+
+class Step(C.Structure):
+    _fields_ = [("dz", C.c_double), ("M", C.c_int), ("z_nl", C.c_double), ("z_im", C.c_double),
+                ("err_est", C.c_double), ("trials", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -97,6 +106,9 @@ def load(path: str = LIB_PATH):
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.gmmnlse_set_linear_coupling.argtypes = [vp, vp]
     lib.gmmnlse_set_gain.argtypes = [vp, vp]
+    lib.gmmnlse_set_gain_saturation.argtypes = [vp, C.c_double]
+    lib.gmmnlse_choose_step.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, vp, C.POINTER(Step)]
+    lib.gmmnlse_set_coupling_profile.argtypes = [vp, vp, C.c_int, C.c_double]
     lib.gmmnlse_overlap_tensor.argtypes = [C.c_int, vp, C.c_int, C.c_longlong, C.c_double, vp]
     lib.gmmnlse_propagate_rk4ip.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(Stats)]
     lib.gmmnlse_choose_m.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.c_int, C.c_int, vp, vp,
@@ -202,6 +214,22 @@ class Context:
         if rc != OK:
             raise GmmnlseError(rc, "gmmnlse_set_gain")
 
+    def set_gain_saturation(self, sat):
+        """gmmnlse_set_gain_saturation: the saturation coefficient (1/I_sat), 0 removes."""
+        rc = self.lib.gmmnlse_set_gain_saturation(self.handle, float(sat))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_set_gain_saturation")
+
+    def set_coupling_profile(self, f, fdz=None):
+        """gmmnlse_set_coupling_profile: Q(z) = Q f(z), f sampled every fdz [m]; None removes."""
+        if f is None:
+            rc = self.lib.gmmnlse_set_coupling_profile(self.handle, None, 0, 0.0)
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            rc = self.lib.gmmnlse_set_coupling_profile(self.handle, _ptr(f), len(f), float(fdz))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_set_coupling_profile")
+
     def propagate_rk4ip(self, A0, L, h, out=None, check=True):
         """gmmnlse_propagate_rk4ip: (Aout, stats dict, status); A0/out as for propagate."""
         if isinstance(A0, np.ndarray):
@@ -236,6 +264,22 @@ class Context:
         if rc != OK:
             raise GmmnlseError(rc, "gmmnlse_choose_m")
         return best.value, {int(m): float(t) for m, t in zip(cand, sec)}
+
+    def choose_step(self, A0, L, rtol, tol, scratch=None):
+        """gmmnlse_choose_step: dict of dz, M, z_nl, z_im, err_est, trials.
+        A0 as for propagate; scratch [2][N][Nt] made like A0 if None."""
+        if isinstance(A0, np.ndarray):
+            A0 = np.ascontiguousarray(A0, dtype=np.complex128)
+            if scratch is None:
+                scratch = np.empty((2,) + A0.shape, dtype=np.complex128)
+        elif scratch is None:
+            scratch = A0.new_empty((2,) + tuple(A0.shape))
+        out = Step()
+        rc = self.lib.gmmnlse_choose_step(self.handle, _ptr(A0), float(L), float(rtol), float(tol), _ptr(scratch),
+                                          C.byref(out))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_choose_step")
+        return out.as_dict()
 
     def profile(self, M, reps=20):
         """Mean device time [ms] and algorithmic bytes per launch of each

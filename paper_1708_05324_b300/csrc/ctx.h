@@ -48,6 +48,7 @@ struct gm_job {
     int which = 0;
     double dz = 0.0;  // the kernels' parameters (dz/2 of the trapezoid) are baked into the graph
     int qv = -1;      // the context's Q version the graph was built with
+    int Mfull = -1;   // the propagation's full long step (z of every substep derives from it)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
   } graphs[2];
@@ -58,6 +59,9 @@ struct gm_job {
   CUtensorMap mapHi, mapLo;
   CUtensorMap mapHi2, mapLo2;    // the same buffers with rKKp columns (low-rank GEMM 2)
   void* Z = nullptr;             // low-rank: Z = W U, [M+1][r][n] R
+  double* Ubar = nullptr;        // saturation: [M+1][K] time integrals of the pair products (FP64)
+  double* Rs = nullptr;          // saturation: [M+1][P] rows R_(p<=l) (FP64)
+  int Mprop = 0;                 // substeps per full long step of the current propagation
 };
 
 struct gmmnlse_ctx {
@@ -68,7 +72,15 @@ struct gmmnlse_ctx {
   double* beta = nullptr;       // [N][n]
   double* Q = nullptr;          // [N][N] linear mode coupling Q[n][p] (device), or none
   double* gain = nullptr;       // [N] small-signal field gain g_p (device), or none
-  int qv = 0;                   // bumped at every change of Q or gain (graphs record the one they hold)
+  double* fprof = nullptr;      // [fcount] longitudinal profile f(z) of Q (device), or none (f = 1)
+  int fcount = 0;
+  double fdz = 0.0;             // spacing of the profile samples [m]
+  double sat = 0.0;             // saturation coefficient of the gain (1/I_sat), 0: none
+  double* GRt = nullptr;        // [K][P] reduced S^R transposed (FP64, device), while sat != 0
+  std::vector<double> GR_host;  // [P][K] reduced S^R (host), kept from creation for the saturation
+  std::vector<double> beta0;    // [N] beta_p(omega = 0) (host): the intermode beat lengths
+  double s_max = 0.0;           // max_p S^K_pppp (host): the nonlinear length
+  int qv = 0;                   // bumped at every change of Q, f, gain or sat (graphs record the one they hold)
   double2* tw64 = nullptr;      // [n] + radix-16 pass tables of n
   double2* tw64h = nullptr;     // [n/2] + pass tables of n/2
   float2* tw32 = nullptr;       // [n] + pass tables of n

@@ -149,6 +149,8 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->beta);
   cudaFree(c->Q);
   cudaFree(c->gain);
+  cudaFree(c->fprof);
+  cudaFree(c->GRt);
   cudaFree(c->tw64);
   cudaFree(c->tw64h);
   cudaFree(c->tw32);
@@ -430,6 +432,20 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
     }
   }
 
+  // length scales of the step sizes (gmmnlse_choose_step)
+  c->beta0.resize(N);
+  for (int p = 0; p < N; ++p) {
+    c->beta0[p] = beta[(size_t)p * n];
+    c->s_max = std::max(c->s_max, S_at(SK, p, p, p, p));
+  }
+  // the reduced S^R [P][K] kept on the host for the gain's saturation term
+  // (uploaded when gmmnlse_set_gain_saturation switches it on)
+  c->GR_host.resize((size_t)c->P * c->K);
+  for (int r = 0; r < c->P; ++r)
+    for (int k = 0; k < c->K; ++k)
+      c->GR_host[(size_t)r * c->K + k] =
+          S_at(SR ? SR : SK, pairs[r].x, pairs[r].y, pairs[k].x, pairs[k].y);
+
   // mixed precision: the contraction runs on the tensor cores where it is a
   // dense GEMM, N >= 9 (with Nt a multiple of the 128-point tile); for N <= 8
   // the FP32 register contraction is faster than a GEMM that small and is
@@ -635,6 +651,7 @@ static size_t job_bytes(const gmmnlse_ctx* c, int M) {
   if (c->lr) b += (size_t)(M + 1) * c->r * c->n * rs;          // Z = W U
   b += 2 * Nn * 16 * 2;                          // EM64, io
   b += sizeof(LoopState) + 64 + sizeof(double2) * TRAPZ_MAX_BLOCKS;
+  b += (size_t)(M + 1) * (c->K + c->P) * sizeof(double);  // saturation: Ubar, Rs
   if (c->tc) b += (size_t)2 * c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2);  // hi/lo operand
   return b;
 }
@@ -664,6 +681,8 @@ static void free_job(gm_job* jb) {
   cudaFree(jb->ls);
   cudaFree(jb->part);
   cudaFree(jb->bar);
+  cudaFree(jb->Ubar);
+  cudaFree(jb->Rs);
   cudaFreeHost(jb->h_ls);
   cudaFreeHost(jb->h_io);
   if (jb->cap) cudaStreamDestroy(jb->cap);
@@ -799,6 +818,8 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
   al((void**)&jb->ls, sizeof(LoopState));
   al((void**)&jb->part, sizeof(double2) * TRAPZ_MAX_BLOCKS);
   al((void**)&jb->bar, 64);
+  al((void**)&jb->Ubar, (size_t)(M + 1) * c->K * sizeof(double));
+  al((void**)&jb->Rs, (size_t)(M + 1) * c->P * sizeof(double));
   if (c->tc) {
     al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
     al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
@@ -957,6 +978,61 @@ extern "C" int gmmnlse_set_gain(gmmnlse_ctx* c, const double* g) {
   return GMMNLSE_OK;
 }
 
+extern "C" int gmmnlse_set_gain_saturation(gmmnlse_ctx* c, double sat) {
+  if (!c || !std::isfinite(sat) || sat < 0.0) return GMMNLSE_E_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->qv += 1;  // graphs built before this call no longer apply
+  if (sat == 0.0) {
+    c->sat = 0.0;
+    return GMMNLSE_OK;
+  }
+  if (!c->GRt) {
+    std::vector<double> t((size_t)c->K * c->P);
+    for (int r = 0; r < c->P; ++r)
+      for (int k = 0; k < c->K; ++k) t[(size_t)k * c->P + r] = c->GR_host[(size_t)r * c->K + k];
+    if (cudaMalloc(&c->GRt, t.size() * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->GRt = nullptr;
+      return GMMNLSE_E_NOMEM;
+    }
+    if (cudaMemcpy(c->GRt, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return GMMNLSE_E_CUDA;
+  }
+  c->sat = sat;
+  return GMMNLSE_OK;
+}
+
+extern "C" int gmmnlse_set_coupling_profile(gmmnlse_ctx* c, const double* f, int count, double fdz) {
+  if (!c) return GMMNLSE_E_INVALID;
+  if (f) {
+    if (count < 1 || !(fdz > 0.0) || !std::isfinite(fdz)) return GMMNLSE_E_INVALID;
+    for (int i = 0; i < count; ++i)
+      if (!std::isfinite(f[i])) return GMMNLSE_E_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->qv += 1;  // graphs built before this call no longer apply
+  cudaFree(c->fprof);
+  c->fprof = nullptr;
+  c->fcount = 0;
+  if (!f) return GMMNLSE_OK;
+  if (cudaMalloc(&c->fprof, (size_t)count * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->fprof = nullptr;
+    return GMMNLSE_E_NOMEM;
+  }
+  if (cudaMemcpy(c->fprof, f, (size_t)count * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return GMMNLSE_E_CUDA;
+  c->fcount = count;
+  c->fdz = fdz;
+  return GMMNLSE_OK;
+}
+
 extern "C" int gmmnlse_choose_m(gmmnlse_ctx* c, const double* A0, double dz, double tol,
                                 const int* candidates, int count, int trial_substeps, double* scratch,
                                 double* sec_per_substep, int* M_best) {
@@ -1012,6 +1088,99 @@ extern "C" int gmmnlse_choose_m(gmmnlse_ctx* c, const double* A0, double dz, dou
   cudaEventDestroy(e1);
   if (best < 0) return last;
   *M_best = candidates[best];
+  return GMMNLSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Step sizes from the length scales and a step-doubling error estimate
+// ---------------------------------------------------------------------------
+extern "C" int gmmnlse_choose_step(gmmnlse_ctx* c, const double* A0, double L, double rtol, double tol,
+                                   double* scratch, gmmnlse_step* out) {
+  if (!c || !A0 || !scratch || !out || scratch == A0 || !(L > 0) || !std::isfinite(L) || !(tol > 0) ||
+      !(rtol >= 0) || !std::isfinite(rtol))
+    return GMMNLSE_E_INVALID;
+  int rc = set_device(c->prm.device);
+  if (rc) return rc;
+  const size_t Nn = (size_t)c->N * c->n;
+  const bool dev = c->prm.io_device != 0;
+  // the field on the host (its peak power; the trial results are compared there)
+  std::vector<double> a0(2 * Nn), a1(2 * Nn), a2(2 * Nn);
+  auto fetch = [&](const double* src, std::vector<double>& dst) -> int {
+    if (dev) {
+      if (cudaMemcpy(dst.data(), src, Nn * 16, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        gm_set_last_cuda_error(cudaGetLastError(), "cudaMemcpy", __FILE__, __LINE__);
+        return GMMNLSE_E_CUDA;
+      }
+    } else {
+      std::memcpy(dst.data(), src, Nn * 16);
+    }
+    return GMMNLSE_OK;
+  };
+  rc = fetch(A0, a0);
+  if (rc) return rc;
+  double P0 = 0.0;
+  for (int k = 0; k < c->n; ++k) {
+    double pk = 0.0;
+    for (int p = 0; p < c->N; ++p) {
+      const double* z = &a0[2 * ((size_t)p * c->n + k)];
+      pk += z[0] * z[0] + z[1] * z[1];
+    }
+    if (!std::isfinite(pk)) return GMMNLSE_E_INVALID;
+    P0 = std::max(P0, pk);
+  }
+  if (!(P0 > 0.0) || !(c->gamma0 > 0.0) || !(c->s_max > 0.0)) return GMMNLSE_E_INVALID;
+  // Sec. III.D: L_long = M dz << z_NL (about z_NL / 10) and dz << z_IM; the
+  // paper's usual z_NL / dz is about 200
+  const double z_nl = 1.0 / (c->gamma0 * c->s_max * P0);
+  double db = 0.0;
+  for (int p = 0; p < c->N; ++p) db = std::max(db, std::fabs(c->beta0[p] - c->beta0[0]));
+  const double z_im = db > 0.0 ? 1.0 / db : std::numeric_limits<double>::infinity();
+  double dz = std::min(z_nl / 200.0, z_im / 10.0);
+  const double dz_cap = dz;
+  auto pick_M = [&](double d, long nsub) {
+    long m = (long)std::floor(z_nl / (10.0 * d));
+    return (int)std::max(1L, std::min({m, (long)kMaxM, nsub}));
+  };
+  double err = 0.0;
+  int trials = 0;
+  if (rtol > 0.0) {
+    // step doubling on a trial piece of one nonlinear length (or the whole
+    // fiber if shorter): the trapezoid is second order, so A(dz) - A_exact
+    // ~ (4/3) (A(dz) - A(dz/2)); the error grows about linearly along z
+    const double ell = std::min(L, z_nl);
+    for (int it = 0; it < 4; ++it) {
+      long ns = std::max(2L, 2 * (long)std::ceil(ell / (2.0 * dz)));
+      const double d = ell / (double)ns;
+      const int M = pick_M(d, ns);
+      double* s1 = scratch;
+      double* s2 = scratch + 2 * Nn;
+      rc = gmmnlse_propagate(c, A0, ell, d, M, tol, s1, nullptr);
+      if (!rc) rc = gmmnlse_propagate(c, A0, ell, 0.5 * d, M, tol, s2, nullptr);
+      trials += 2;
+      if (rc) return rc;
+      rc = fetch(s1, a1);
+      if (!rc) rc = fetch(s2, a2);
+      if (rc) return rc;
+      double dd = 0.0, nn = 0.0;
+      for (size_t i = 0; i < 2 * Nn; ++i) {
+        dd += (a1[i] - a2[i]) * (a1[i] - a2[i]);
+        nn += a2[i] * a2[i];
+      }
+      err = (4.0 / 3.0) * std::sqrt(dd / nn) * (L / ell);
+      dz = d;
+      if (err <= rtol) break;
+      dz = d * std::sqrt(rtol / err) * 0.9;  // second order: err ~ dz^2
+      err = err * (dz / d) * (dz / d);        // (the estimate at the new dz)
+    }
+  }
+  dz = std::min(dz, dz_cap);
+  const long nsub = std::max(1L, (long)std::ceil(L / dz - 1e-9));
+  out->dz = L / (double)nsub;
+  out->M = pick_M(out->dz, nsub);
+  out->z_nl = z_nl;
+  out->z_im = z_im;
+  out->err_est = err;
+  out->trials = trials;
   return GMMNLSE_OK;
 }
 

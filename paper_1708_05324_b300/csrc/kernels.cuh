@@ -638,40 +638,72 @@ __global__ void k_round_psi(const double2* __restrict__ psi0, cplx<R>* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Linear terms of Sec. IV, added to the integrand after K4: the mode
-// coupling C_p = i sum_n Q_np A_n, I_j,p += exp(-i beta_p j dz) i sum_n Q_np
-// A~_n,j with A~_n,j = (psi_n + dpsi_n,j) E_n,j, the spectrum K1 transformed,
-// and the small-signal gain g_p A_p, I_j,p += g_p (psi_p + dpsi_p,j) (its
-// phase and the interaction picture's cancel).  Neither depends on time, so
-// each acts on every frequency alike.  Slices follow K1: j = 0 only in the
-// first iteration, dpsi only after it.  One thread per (substep, frequency),
-// all modes; Q[n][p] and g_p FP64 (either may be absent), used in R.
+// Terms of Sec. IV added to the right-hand side of Eq. 1, none of which
+// depends on time within a substep, so each acts on every frequency alike
+// and joins the integrand after K4: the linear mode coupling
+// C_p = i sum_n Q_np(z) A_n with Q_np(z) = Q_np f(z), the small-signal gain
+// g_p A_p, and its saturation - sat sum_l R_pl A_l with
+// R_pl = sum_mn S^R_plmn int A_m A_n^* dtau (real and symmetric for an S^R
+// of Eq. 2).  In the interaction picture
+//   I_j,p += exp(-i beta_p j dz) (i f(z_j) sum_n Q_np - sat R_pl(j)) A~_n,j
+//            + g_p (psi_p + dpsi_p,j),
+// with A~_n,j = (psi_n + dpsi_n,j) E_n,j the spectrum K1 transforms (the
+// gain's phase and the interaction picture's cancel).  Slices follow K1:
+// j = 0 only in the first iteration, dpsi only after it.  One thread per
+// (substep, frequency), all modes; the coefficients FP64, used in R.
 // ---------------------------------------------------------------------------
+struct LinTerms {
+  const double* Q;       // [N][N] Q[n][p], or null
+  const double* gain;    // [N] g_p, or null
+  const double* fprof;   // f(z) at z = k fdz, k < fcount (linear interpolation), or null (f = 1)
+  int fcount;
+  double fdz;
+  const double* Rs;      // [M+1][P] saturation rows R_(p<=l)(j), or null
+  double sat;            // the saturation's coefficient (1/I_sat)
+  int Mfull;             // substeps of a full long step: z0 = (long steps done) Mfull dz
+  int use_step;          // 1: z0 from the loop state; 0: z0 = zoff
+  double zoff;
+};
+
+__device__ __forceinline__ double profile_at(const LinTerms& t, double z) {
+  if (!t.fprof) return 1.0;
+  const double u = z / t.fdz;
+  if (!(u > 0.0)) return t.fprof[0];
+  const int k = (int)u;
+  if (k >= t.fcount - 1) return t.fprof[t.fcount - 1];
+  const double w = u - (double)k;
+  return t.fprof[k] + w * (t.fprof[k + 1] - t.fprof[k]);
+}
+
 template <typename R>
-__global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const double* __restrict__ gain,
-                                  const cplx<R>* __restrict__ psiR,
+__global__ void k_linear_coupling(Geo g, LinTerms lt, const cplx<R>* __restrict__ psiR,
                                   const cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ E,
                                   cplx<R>* __restrict__ I, const LoopState* __restrict__ ls) {
   const int N = g.N, n = g.n, iter = ls->iter;
+  const double dz = 2.0 * g.hdz;
+  const double z0 = lt.use_step ? (double)ls->step * lt.Mfull * dz : lt.zoff;
   const size_t total = (size_t)(g.M + 1) * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(i / n), q = (int)(i - (size_t)j * n);
     if (iter > 0 && j == 0) continue;
+    const R fq = lt.Q ? (R)profile_at(lt, z0 + j * dz) : (R)0;
+    const double* rs = lt.Rs ? lt.Rs + (size_t)j * g.P : nullptr;
     for (int p = 0; p < N; ++p) {
       cplx<R>* o = I + ((size_t)j * N + p) * n + q;
-      if (gain) {
+      if (lt.gain) {
         cplx<R> a = psiR[(size_t)p * n + q];
         if (iter > 0) {
           const cplx<R> d = dpsi[((size_t)(j - 1) * N + p) * n + q];
           a.x += d.x;
           a.y += d.y;
         }
-        const R gp = (R)gain[p];
+        const R gp = (R)lt.gain[p];
         o->x += gp * a.x;
         o->y += gp * a.y;
       }
-      if (!Q) continue;
-      R cx = 0, cy = 0;
+      if (!lt.Q && !rs) continue;
+      // c = sum_m (i f Q_mp - sat R_pm) A~_m: cq from the coupling, cs from the saturation
+      R cqx = 0, cqy = 0, csx = 0, csy = 0;
       for (int m = 0; m < N; ++m) {
         cplx<R> a = psiR[(size_t)m * n + q];
         if (iter > 0) {
@@ -680,17 +712,62 @@ __global__ void k_linear_coupling(Geo g, const double* __restrict__ Q, const dou
           a.y += d.y;
         }
         const cplx<R> e = E[((size_t)j * N + m) * n + q];
-        const R w = (R)Q[(size_t)m * N + p];
-        cx += w * (a.x * e.x - a.y * e.y);
-        cy += w * (a.x * e.y + a.y * e.x);
+        const R ax = a.x * e.x - a.y * e.y, ay = a.x * e.y + a.y * e.x;
+        if (lt.Q) {
+          const R w = fq * (R)lt.Q[(size_t)m * N + p];
+          cqx += w * ax;
+          cqy += w * ay;
+        }
+        if (rs) {
+          const int lo = p < m ? p : m, hi = p < m ? m : p;
+          const R w = (R)(lt.sat * rs[lo * N - lo * (lo - 1) / 2 + (hi - lo)]);
+          csx += w * ax;
+          csy += w * ay;
+        }
       }
-      // i (cx + i cy) = -cy + i cx, times conj(E_p,j)
+      // i (cqx + i cqy) - (csx + i csy), times conj(E_p,j)
       const cplx<R> e = E[((size_t)j * N + p) * n + q];
-      const R tx = -cy, ty = cx;
+      const R tx = -cqy - csx, ty = cqx - csy;
       o->x += tx * e.x + ty * e.y;
       o->y += ty * e.x - tx * e.y;
     }
   }
+}
+
+// The time integrals of the pair products at every substep, for the
+// saturation: Ubar[j][k(m,n)] = dt sum_t U_mn(t) with U_mm = |A_m|^2 and
+// U_mn = 2 Re(A_m A_n^*) (m < n), so that sum_{m<=n} S^R_pl,mn Ubar_mn =
+// sum_mn S^R_plmn int A_m A_n^* dtau for an S^R symmetric in m, n.  FP64
+// sums; block (m, j) takes the pairs (m, n >= m).
+template <typename R>
+__global__ void __launch_bounds__(256) k_sat_gram(Geo g, const cplx<R>* __restrict__ A, double* __restrict__ Ubar,
+                                                  const LoopState* __restrict__ ls) {
+  __shared__ double red[32];
+  const int m = blockIdx.x, j = blockIdx.y, N = g.N, n = g.n;
+  if (ls->iter > 0 && j == 0) return;
+  const cplx<R>* a = A + (size_t)j * N * n;
+  const int k0 = m * N - m * (m - 1) / 2;
+  for (int q = m; q < N; ++q) {
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const cplx<R> am = a[(size_t)m * n + t], aq = a[(size_t)q * n + t];
+      acc += (double)am.x * (double)aq.x + (double)am.y * (double)aq.y;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) Ubar[(size_t)j * g.K + k0 + (q - m)] = g.dt * (q == m ? acc : 2.0 * acc);
+  }
+}
+
+// R_r(j) = sum_k S^R[r][k] Ubar[j][k] for the rows r = (p <= l): GRt is the
+// reduced S^R transposed, [K][P] (FP64).  One thread per (row, substep).
+static __global__ void k_sat_rows(int P, int K, const double* __restrict__ GRt, const double* __restrict__ Ubar,
+                                  double* __restrict__ Rs, const LoopState* __restrict__ ls) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (r >= P || (ls->iter > 0 && j == 0)) return;
+  const double* u = Ubar + (size_t)j * K;
+  double acc = 0.0;
+  for (int k = 0; k < K; ++k) acc += GRt[(size_t)k * P + r] * u[k];
+  Rs[(size_t)j * P + r] = acc;
 }
 
 // ---------------------------------------------------------------------------

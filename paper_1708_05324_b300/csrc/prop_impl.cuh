@@ -463,13 +463,37 @@ static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_contract_tile<R, 0, 1, 0>);
 }
 
-// Linear mode coupling added to the integrand I (after K4)
+// The Sec. IV terms added to the integrand I (after K4): linear coupling
+// (with its longitudinal profile), gain and its saturation.  z0 of the
+// substeps: from the loop state's long-step count (use_step) or zoff.
 template <typename R>
-static void launch_linear_coupling(gm_job* jb, const Geo& g, cudaStream_t s) {
+static void launch_linear_coupling(gm_job* jb, const Geo& g, cudaStream_t s, int use_step, double zoff) {
   const gmmnlse_ctx* c = jb->ctx;
+  LinTerms lt = {};
+  lt.Q = c->Q;
+  lt.gain = c->gain;
+  lt.fprof = c->fprof;
+  lt.fcount = c->fcount;
+  lt.fdz = c->fdz;
+  lt.Rs = c->sat != 0.0 ? jb->Rs : nullptr;
+  lt.sat = c->sat;
+  lt.Mfull = jb->Mprop;
+  lt.use_step = use_step;
+  lt.zoff = zoff;
   k_linear_coupling<R><<<elementwise_blocks((size_t)(g.M + 1) * c->n), 256, 0, s>>>(
-      g, c->Q, c->gain, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E, (cplx<R>*)jb->I, jb->ls);
+      g, lt, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E, (cplx<R>*)jb->I, jb->ls);
 }
+
+// The saturation's per-substep rows R_pl(j) from the time-domain field A
+// (after K1): the time integrals of the pair products, then S^R times them.
+template <typename R>
+static void launch_saturation(gm_job* jb, const Geo& g, cudaStream_t s) {
+  const gmmnlse_ctx* c = jb->ctx;
+  k_sat_gram<R><<<dim3(c->N, g.M + 1), 256, 0, s>>>(g, (const cplx<R>*)jb->A, jb->Ubar, jb->ls);
+  k_sat_rows<<<dim3((c->P + 127) / 128, g.M + 1), 128, 0, s>>>(c->P, c->K, c->GRt, jb->Ubar, jb->Rs, jb->ls);
+}
+
+static inline bool extra_terms(const gmmnlse_ctx* c) { return c->Q || c->gain || c->sat != 0.0; }
 
 // K5 with the convergence decision in its last block
 template <typename R>
@@ -486,6 +510,7 @@ template <typename R>
 static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   gmmnlse_ctx* c = jb->ctx;
   launch_k1<R>(jb, g, s);
+  if (c->sat != 0.0) launch_saturation<R>(jb, g, s);
   if (c->lr) {
     launch_lr_z<R>(jb, g, s);
     if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
@@ -496,7 +521,7 @@ static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraph
     else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
   }
   launch_k4<R>(jb, g, s);
-  if (c->Q || c->gain) launch_linear_coupling<R>(jb, g, s);
+  if (extra_terms(c)) launch_linear_coupling<R>(jb, g, s, 1, 0.0);
   launch_k5<R>(jb, g, s, h, use_cond);
 }
 
@@ -527,7 +552,7 @@ static int build_graph(gm_job* jb, const Geo& g, int which, gm_job::G& out) {
   cudaGraphNode_t nStep;
   CK(cudaGraphAddNode(&nStep, root, nullptr, nullptr, 0, &cp));
   cudaGraph_t gS = cp.conditional.phGraph_out[0];
-  if (jb->persist_grid > 0 && !jb->ctx->Q && !jb->ctx->gain) {
+  if (jb->persist_grid > 0 && !extra_terms(jb->ctx)) {
     // long-step body: the cooperative long-step kernel (iterations inside)
     CK(cudaStreamBeginCaptureToGraph(cs, gS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     launch_long_step<R>(jb, g, which, cs, hStep, 1);
@@ -583,7 +608,8 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
   if (!graphs_disabled()) {
     gm_job::G* gr = nullptr;
     for (auto& x : jb->graphs)
-      if (x.exec && x.Mj == Mj && x.which == which && x.dz == dz && x.qv == jb->ctx->qv) gr = &x;
+      if (x.exec && x.Mj == Mj && x.which == which && x.dz == dz && x.qv == jb->ctx->qv && x.Mfull == jb->Mprop)
+        gr = &x;
     if (!gr) {
       gm_job::G& slot = jb->graphs[which];
       if (slot.exec) {
@@ -593,6 +619,7 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
       }
       if (build_graph<R>(jb, g, which, slot) == GMMNLSE_OK) {
         slot.qv = jb->ctx->qv;
+        slot.Mfull = jb->Mprop;
         gr = &slot;
       }
       else {
@@ -607,7 +634,7 @@ static int run_long_steps(gm_job* jb, int Mj, int which, double dz, int count, c
   }
   // host-driven loop over the same kernels
   for (int st = 0; st < count; ++st) {
-    if (jb->persist_grid > 0 && !jb->ctx->Q && !jb->ctx->gain) {
+    if (jb->persist_grid > 0 && !extra_terms(jb->ctx)) {
       launch_long_step<R>(jb, g, which, s, 0, 0);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(jb->h_ls, jb->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
@@ -641,6 +668,7 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
   if (rc) return rc;
   if (!(tol >= 0) || !std::isfinite(tol)) return GMMNLSE_E_INVALID;
   const size_t Nn = (size_t)c->N * c->n;
+  jb->Mprop = M;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -820,6 +848,7 @@ static int rk4ip_impl(gm_job* jb, const double* A0, bool dev_io, double L, doubl
   for (long k = 0; k < steps; ++k) {
     for (int q = 1; q <= 4; ++q) {
       launch_k1<R>(jb, g, s);
+      if (c->sat != 0.0) launch_saturation<R>(jb, g, s);
       if (c->lr) {
         launch_lr_z<R>(jb, g, s);
         if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
@@ -830,7 +859,8 @@ static int rk4ip_impl(gm_job* jb, const double* A0, bool dev_io, double L, doubl
         else launch_contract<R>(g, c, jb->A, jb->V, jb->NL, jb->ls, s);
       }
       launch_k4<R>(jb, g, s);
-      if (c->Q || c->gain) launch_linear_coupling<R>(jb, g, s);
+      // the stage's position: z, z + h/2, z + h/2, z + h
+      if (extra_terms(c)) launch_linear_coupling<R>(jb, g, s, 0, h * (k + (q == 1 ? 0.0 : (q == 4 ? 1.0 : 0.5))));
       k_rk4_stage<R><<<eb, 256, 0, s>>>(q, Nn, h, Ast, AI, acc, I0, jb->EM64, X);
     }
     if (cudaGetLastError() != cudaSuccess) {

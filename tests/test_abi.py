@@ -36,8 +36,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 #include <stddef.h>
 #include "gmmnlse.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(gmmnlse_params), offsetof(gmmnlse_params, stream),
-         offsetof(gmmnlse_params, io_device), sizeof(gmmnlse_stats), offsetof(gmmnlse_stats, eps_max));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(gmmnlse_params), offsetof(gmmnlse_params, stream),
+         offsetof(gmmnlse_params, io_device), sizeof(gmmnlse_stats), offsetof(gmmnlse_stats, eps_max),
+         sizeof(gmmnlse_step), offsetof(gmmnlse_step, trials));
   return 0;
 }
 """)
@@ -45,7 +46,7 @@ int main(void) {
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(B.Params), B.Params.stream.offset, B.Params.io_device.offset,
-            C.sizeof(B.Stats), B.Stats.eps_max.offset]
+            C.sizeof(B.Stats), B.Stats.eps_max.offset, C.sizeof(B.Step), B.Step.trials.offset]
     assert got == want
 
 

@@ -226,3 +226,79 @@ def test_fp16_scale_follows_an_energy_that_a_gain_raises_tenfold(mixed):
         ctx.close()
     assert rc == B.OK
     assert rel(out, ref) < 1e-3
+
+
+def saturation_for(prob, g):
+    """A saturation coefficient that brings the energy's fixed point to about
+    five times the input energy (a clearly saturated gain)."""
+    W0 = prob.dt * float(np.sum(np.abs(prob.A0) ** 2))
+    return 0.2 * float(np.max(g)) / (prob.SK[0, 0, 0, 0] * W0)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_saturated(N, Nt, fR, with_profile):
+    prob = problem(N, Nt, fR)
+    g = GAIN.get(N, np.full(N, 6.0)) + 40.0
+    sat = saturation_for(prob, g)
+    kw = dict(gain=g, sat=sat)
+    if with_profile:
+        kw.update(Q=coupling(N), Q_profile=PROFILE, Q_profile_dz=PROFILE_DZ)
+    fib = O.Fiber.from_problem(prob, **kw)
+    return (O.mpa_propagate(fib, prob.A0, L, DZ, M, TOL)[0], O.rk4ip_propagate(fib, prob.A0, L, DZ), g, sat,
+            O.mpa_propagate(O.Fiber.from_problem(prob, gain=g), prob.A0, L, DZ, M, TOL)[0])
+
+
+# a grating-like profile of the coupling: f(z) = 1 + 0.8 sin(2 pi z / 0.4 mm)
+PROFILE_DZ = 2e-5
+PROFILE = 1.0 + 0.8 * np.sin(2 * np.pi * np.arange(80) * PROFILE_DZ / 4e-4)
+
+
+@pytest.mark.parametrize("N,Nt,fR,with_profile", [(1, 128, 0.18, False), (3, 256, 0.18, True),
+                                                  (10, 256, 0.18, True)])
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32", 1e-5), ("bf16", 1e-3)])
+def test_saturated_gain_matches_the_oracle_in_the_mpa_and_rk4ip(N, Nt, fR, with_profile, precision, bar):
+    """The saturation (per substep: FP64 time integrals of the pair
+    products, R = S^R Ubar, the term in the integrand) beside the small-signal
+    gain, with a z-dependent linear coupling Q f(z) for 3 and 10 modes (the
+    MPA takes f at every substep, RK4IP at its stage positions); 10 modes in
+    BF16 run the contraction on the tensor cores."""
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(N, Nt, fR)
+    ref_mpa, ref_rk, g, sat, unsat = oracle_saturated(N, Nt, fR, with_profile)
+    assert rel(ref_mpa, unsat) > 1e-3  # the saturation changes the field
+    ctx = context(prob, precision)
+    tol = TOL if precision == "fp64" else 1e-9
+    try:
+        ctx.set_gain(g)
+        ctx.set_gain_saturation(sat)
+        if with_profile:
+            ctx.set_linear_coupling(coupling(N))
+            ctx.set_coupling_profile(PROFILE, PROFILE_DZ)
+        out, _, rc = ctx.propagate(prob.A0, L, DZ, M, tol)
+        assert rc == B.OK and rel(out, ref_mpa) < bar
+        out, _, rc = ctx.propagate_rk4ip(prob.A0, L, DZ)
+        assert rc == B.OK and rel(out, ref_rk) < bar
+        # removing the saturation and the profile (and Q) gives the gain alone
+        ctx.set_gain_saturation(0.0)
+        ctx.set_coupling_profile(None)
+        ctx.set_linear_coupling(None)
+        out, _, rc = ctx.propagate(prob.A0, L, DZ, M, tol)
+        assert rc == B.OK and rel(out, unsat) < bar
+    finally:
+        ctx.close()
+
+
+def test_profile_and_saturation_rejections():
+    from paper_1708_05324_b300 import binding as B
+    prob = problem(3, 256, 0.18)
+    ctx = context(prob, "fp32")
+    try:
+        for bad in (-1.0, float("inf"), float("nan")):
+            with pytest.raises(B.GmmnlseError):
+                ctx.set_gain_saturation(bad)
+        with pytest.raises(B.GmmnlseError):
+            ctx.set_coupling_profile(np.array([1.0, np.nan]), 1e-4)
+        with pytest.raises(B.GmmnlseError):
+            ctx.set_coupling_profile(np.array([1.0, 2.0]), 0.0)
+    finally:
+        ctx.close()

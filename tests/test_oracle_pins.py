@@ -417,3 +417,33 @@ def test_substep_schedule():
     assert O.substep_schedule(1.2e-3, 1e-4, 5) == [5, 5, 2]
     with pytest.raises(ValueError):
         O.substep_schedule(1.25e-3, 1e-4, 5)
+
+
+# ----------------------------------------------------------------------------
+# Length scales of the two step sizes (Sec. III.D)
+# ----------------------------------------------------------------------------
+def test_length_scales_of_a_soliton_and_of_the_grin_mode_groups():
+    """z_NL of the fundamental soliton is the dispersion length (gamma P0 L_D
+    = 1, Agrawal), formed here from gamma = n2 omega0 S / c; z_IM of a GRIN
+    fiber is set by its highest mode group: the groups are spaced by
+    delta beta0 = NA / (a n) to first order (Sec. III.A, equally spaced
+    groups), so with groups 0-2 z_IM = 1 / (2 delta beta0), and a single mode
+    has none."""
+    Nt, T0, beta2 = 256, 100e-15, -2e-26
+    dt = 40 * T0 / Nt
+    fib = single_mode(Nt, dt, beta2=beta2)
+    P0 = abs(beta2) / (gamma_of() * T0 ** 2)
+    t = I.time_grid(Nt, dt)
+    A0 = (math.sqrt(P0) / np.cosh(t / T0))[None, :].astype(complex)
+    z_nl, z_im = O.length_scales(fib, A0)
+    assert z_nl == pytest.approx(T0 ** 2 / abs(beta2), rel=1e-12)
+    assert z_im == math.inf
+    prob = I.grin_problem("ls", N=6, Nt=256, dt=2e-12 / 256, kind="gaussian", fwhm=150e-15, energy=10e-9,
+                          L=1e-3, dz=1e-4, M=5, tol=1e-12, seed=3, fR=0.0, s_from="gh")
+    g6 = O.Fiber.from_problem(prob)
+    z_nl, z_im = O.length_scales(g6, prob.A0)
+    db0 = 0.2 / (25e-6 * float(I.silica_index(LAM0)))
+    assert z_im == pytest.approx(1.0 / (2 * db0), rel=2e-2)
+    P0 = float(np.max(np.sum(np.abs(prob.A0) ** 2, axis=0)))
+    w = I.grin_mode_width(25e-6, 0.2, LAM0)
+    assert z_nl == pytest.approx(1.0 / (gamma_of(s=1.0 / (math.pi * w * w)) * P0), rel=1e-9)
