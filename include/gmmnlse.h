@@ -423,11 +423,22 @@ size_t gmmnlse_request_bytes(const gmmnlse_ctx* ctx, int M);
  * Serving: continuous batching of propagation requests.
  *
  * gmmnlse_server_create(hbm_budget, max_inflight, out): a server whose
- * in-flight requests together hold at most hbm_budget device bytes (as
- * gmmnlse_request_bytes counts them) and at most max_inflight requests.
- * Requests beyond that wait in a FIFO queue and are admitted as earlier ones
- * finish; each admitted request runs on its own stream, so requests that
- * arrive while others are on the GPU overlap with them.
+ * workspaces together hold at most hbm_budget device bytes (as
+ * gmmnlse_request_bytes counts one propagation's; every workspace the
+ * server keeps, in use or idle for reuse, counts) and that runs at most
+ * max_inflight requests at once.  Requests beyond that wait in a queue and
+ * are admitted, first fit, as earlier ones finish.
+ *
+ * Same-shape requests are packed: requests on one context with the same M
+ * that run whole long steps (L a whole number of M dz; any dz, tol and
+ * field) and no linear coupling, gain or saturation share a workspace of
+ * min(max_inflight, 16) slots, and one launch (a CUDA graph captured once
+ * per workspace) advances all of them by one long step, every kernel of the
+ * MPA iteration over all slots at once; a request joins or leaves between
+ * launches.  Each slot keeps its own convergence, so its result equals that
+ * of gmmnlse_propagate on the same input.  Other requests run alone, each on
+ * its own stream.  Idle workspaces are freed, oldest first, when a new one
+ * would not fit the budget.
  *
  * gmmnlse_submit copies A0 (host) and returns at once with a ticket.  The
  * context must outlive the request.  GMMNLSE_E_BUSY if 65536 requests are
@@ -439,6 +450,14 @@ size_t gmmnlse_request_bytes(const gmmnlse_ctx* ctx, int M);
  * released by the poll that reports it; polling it again is
  * GMMNLSE_E_INVALID.
  *
+ * gmmnlse_cancel(server, ticket): a request that has not started is
+ * cancelled (its poll returns GMMNLSE_E_CANCELLED); GMMNLSE_E_BUSY if it is
+ * already running (it then completes normally), GMMNLSE_OK if it has ended.
+ *
+ * gmmnlse_server_resident_bytes(server, now, peak): the device bytes the
+ * server's workspaces hold now and the most they have held (either may be
+ * NULL); never above hbm_budget.
+ *
  * gmmnlse_server_destroy waits for admitted requests, cancels queued ones
  * and frees the server.
  */
@@ -446,6 +465,8 @@ int gmmnlse_server_create(size_t hbm_budget, int max_inflight, gmmnlse_server** 
 int gmmnlse_submit(gmmnlse_server* srv, gmmnlse_ctx* ctx, const double* A0, double L,
                    double dz, int M, double tol, uint64_t* ticket);
 int gmmnlse_poll(gmmnlse_server* srv, uint64_t ticket, double* Aout, gmmnlse_stats* st);
+int gmmnlse_cancel(gmmnlse_server* srv, uint64_t ticket);
+int gmmnlse_server_resident_bytes(gmmnlse_server* srv, size_t* now, size_t* peak);
 int gmmnlse_server_destroy(gmmnlse_server* srv);
 
 #ifdef __cplusplus

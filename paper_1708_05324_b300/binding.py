@@ -29,7 +29,8 @@ EXPORTS = [
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
     "gmmnlse_propagate_rk4ip", "gmmnlse_set_linear_coupling",
     "gmmnlse_set_gain", "gmmnlse_overlap_tensor", "gmmnlse_set_gain_saturation",
-    "gmmnlse_set_coupling_profile", "gmmnlse_choose_step",
+    "gmmnlse_set_coupling_profile", "gmmnlse_choose_step", "gmmnlse_cancel",
+    "gmmnlse_server_resident_bytes",
 ]
 KERNELS = ["ip_to_time", "pairs_raman", "contract", "integrand", "trapz_norm", "advance"]
 
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH):
                                    C.POINTER(C.c_uint64)]
     lib.gmmnlse_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(Stats)]
     lib.gmmnlse_server_destroy.argtypes = [vp]
+    lib.gmmnlse_cancel.argtypes = [vp, C.c_uint64]
+    lib.gmmnlse_server_resident_bytes.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
     lib.gmmnlse_profile.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.gmmnlse_set_linear_coupling.argtypes = [vp, vp]
     lib.gmmnlse_set_gain.argtypes = [vp, vp]
@@ -331,6 +334,18 @@ class Server:
         st = Stats()
         rc = self.lib.gmmnlse_poll(self.handle, C.c_uint64(ticket), _ptr(out), C.byref(st))
         return rc, out, st.as_dict()
+
+    def cancel(self, ticket):
+        """gmmnlse_cancel: the status code (OK, E_BUSY when already running)."""
+        return self.lib.gmmnlse_cancel(self.handle, C.c_uint64(ticket))
+
+    def resident_bytes(self):
+        """(now, peak) device bytes held by the server's workspaces."""
+        now, peak = C.c_size_t(), C.c_size_t()
+        rc = self.lib.gmmnlse_server_resident_bytes(self.handle, C.byref(now), C.byref(peak))
+        if rc != OK:
+            raise GmmnlseError(rc, "gmmnlse_server_resident_bytes")
+        return int(now.value), int(peak.value)
 
     def close(self):
         if getattr(self, "handle", None):

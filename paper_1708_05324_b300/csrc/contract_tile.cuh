@@ -78,11 +78,19 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
   R* Gs = Vs + KC * TP;                               // [KC][TR]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   pdl_enter();
-  const int iter = ls->iter;
-  const size_t npts = (size_t)(g.M + 1) * n;
+  const size_t npts = (size_t)g.B * (g.M + 1) * n;
   const size_t pt0 = (size_t)blockIdx.x * TP;
-  // the z0 points are known after the first iteration
-  if (iter > 0 && pt0 + TP <= (size_t)n) return;
+  // points whose slice does no work (the z0 points after the first
+  // iteration; in a packed launch, empty and converged slots)
+  auto skip = [&](size_t pt) {
+    int b, j;
+    slot_of(g, (int)(pt / n), b, j);
+    return slice_skipped(ls + b, j);
+  };
+  {
+    const size_t ptl = (pt0 + TP <= npts ? pt0 + TP : npts) - 1;
+    if (pt0 / n == ptl / n && skip(pt0)) return;  // the tile lies in one such slice
+  }
 
   // this block's mode values; NL accumulators cleared
   for (int i = tid; i < N * TP; i += 256) {
@@ -91,7 +99,7 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
     cplx<R> v = mk<R>(0, 0);
     if (pt < npts) {
       const size_t j = pt / n, t = pt - j * n;
-      if (!(iter > 0 && j == 0)) v = a.A[(j * N + l) * n + t];
+      if (!skip(pt)) v = a.A[(j * N + l) * n + t];
     }
     As[i] = v;
     Ns[i] = mk<R>(0, 0);
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
   const int q = tid % TP, kq = tid / TP;
   constexpr int KSTEP = 256 / TP, NV = KC / KSTEP, NG = KC * TR / 256;
   const size_t ptq = pt0 + q;
-  const bool okq = ptq < npts && !(iter > 0 && ptq < (size_t)n);
+  const bool okq = ptq < npts && !skip(ptq);
   const size_t jq = ptq < npts ? ptq / n : 0, tq = ptq < npts ? ptq - jq * n : 0;
   const R* yq = a.Ys + (jq * (size_t)a.cnt) * n + tq;
   const R* zq = SRC == 1 ? a.Zs + (jq * (size_t)a.cnt) * n + tq : nullptr;
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
           const size_t pt = pt0 + ty * TM + i;
           if (pt >= npts) continue;
           const size_t j = pt / n, t = pt - j * n;
-          if (iter > 0 && j == 0) continue;
+          if (skip(pt)) continue;
           R* z = a.Zout + (j * (size_t)a.cnt) * n + t;
 #pragma unroll
           for (int jn = 0; jn < TN; ++jn) {
@@ -278,7 +286,7 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
     const size_t pt = pt0 + qq;
     if (pt >= npts) continue;
     const size_t j = pt / n, t = pt - j * n;
-    if (iter > 0 && j == 0) continue;
+    if (skip(pt)) continue;
     a.NL[(j * N + p) * n + t] = Ns[i];
   }
 }

@@ -21,6 +21,7 @@
 struct gm_job {
   gmmnlse_ctx* ctx = nullptr;
   int Mcap = 0;
+  int slots = 1;            // propagations the workspace holds (a packed launch's B; 1 otherwise)
   double2* psi0 = nullptr;  // [N][n]
   void* psiR = nullptr;     // [N][n] cplx<R> (aliases psi0 in FP64)
   void* dpsi = nullptr;     // [M][N][n]
@@ -182,7 +183,7 @@ static inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 template <typename R, int N, int MODE>
 static inline void launch_contract_reg(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V,
                                        void* NL, const gm::LoopState* ls, cudaStream_t s) {
-  const size_t pts = (size_t)(g.M + 1) * g.n;
+  const size_t pts = (size_t)g.B * (g.M + 1) * g.n;
   pdl_launch(gm::k_contract_reg<R, N, MODE>, dim3((unsigned)((pts + 127) / 128)), dim3(128), 0, s, g,
              (const gm::cplx<R>*)A, (const R*)V, (const R*)c->G, (gm::cplx<R>*)NL, ls);
 }
@@ -220,7 +221,7 @@ static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const
       a.rowpl = (const int2*)c->rows_t;
       a.pairs = (const int2*)c->pairs;
       a.NL = (gm::cplx<R>*)NL;
-      const size_t pts = (size_t)(g.M + 1) * g.n;
+      const size_t pts = (size_t)g.B * (g.M + 1) * g.n;
       const dim3 grid((unsigned)((pts + gm::TileCfg<R>::TP - 1) / gm::TileCfg<R>::TP));
       const size_t smem = gm::contract_tile_smem<R>(c->N);
       auto go = [&](auto kern) { pdl_launch(kern, grid, dim3(256), smem, s, g, a, ls); };

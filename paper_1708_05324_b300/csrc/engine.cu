@@ -780,7 +780,7 @@ int gm_make_g_maps(gmmnlse_ctx* c) {
 }
 
 int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
-  const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n;
+  const cuuint64_t npts = (cuuint64_t)(M + 1) * c->n * jb->slots;
   int rc = tc_map(&jb->mapHi, jb->Vhi, npts, c->KKp, TC_PTS, c->f16, c->tf32);
   if (!rc) rc = tc_map(&jb->mapLo, jb->Vlo, npts, c->KKp, TC_PTS, c->f16, c->tf32);
   if (!rc && c->lr) {
@@ -790,47 +790,64 @@ int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M) {
   return rc;
 }
 
-int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
+int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) { return gm_job_create_slots(c, M, 1, out); }
+
+// A workspace of `slots` propagations with M substeps per long step: every
+// array once per slot (the per-slice arrays by slice = slot (M + 1) + j).
+int gm_job_create_slots(gmmnlse_ctx* c, int M, int slots, gm_job** out) {
   *out = nullptr;
+  if (slots < 1 || slots > 64) return GMMNLSE_E_INVALID;
   gm_job* jb = new (std::nothrow) gm_job();
   if (!jb) return GMMNLSE_E_NOMEM;
   jb->ctx = c;
   jb->Mcap = M;
+  jb->slots = slots;
   const size_t rs = c->fp64 ? 8 : 4, cs = 2 * rs;
-  const size_t Nn = (size_t)c->N * c->n;
+  const size_t Nn = (size_t)c->N * c->n, B = (size_t)slots;
+  const size_t S1 = (size_t)(M + 1) * B;  // slices
   cudaError_t e = cudaSuccess;
   auto al = [&](void** p, size_t b) {
     if (e == cudaSuccess) e = cudaMalloc(p, b ? b : 16);
   };
-  al((void**)&jb->psi0, Nn * 16);
+  al((void**)&jb->psi0, B * Nn * 16);
   if (c->fp64) jb->psiR = jb->psi0;
-  else al(&jb->psiR, Nn * cs);
-  al(&jb->dpsi, (size_t)M * Nn * cs);
-  al(&jb->A, (size_t)(M + 1) * Nn * cs);
-  al(&jb->NL, (size_t)(M + 1) * Nn * cs);
-  al(&jb->I, (size_t)(M + 1) * Nn * cs);
-  al(&jb->E, (size_t)(M + 1) * Nn * cs);
-  if (c->raman_mode) al(&jb->V, (size_t)(M + 1) * c->K * c->n * rs);
-  if (c->lr) al(&jb->Z, (size_t)(M + 1) * c->r * c->n * rs);
-  al((void**)&jb->EM64, 2 * Nn * 16);
+  else al(&jb->psiR, B * Nn * cs);
+  al(&jb->dpsi, B * (size_t)M * Nn * cs);
+  al(&jb->A, S1 * Nn * cs);
+  al(&jb->NL, S1 * Nn * cs);
+  al(&jb->I, S1 * Nn * cs);
+  al(&jb->E, S1 * Nn * cs);
+  if (c->raman_mode) al(&jb->V, S1 * c->K * c->n * rs);
+  if (c->lr) al(&jb->Z, S1 * c->r * c->n * rs);
+  al((void**)&jb->EM64, B * 2 * Nn * 16);
   al((void**)&jb->io, 2 * Nn * 16);
   al((void**)&jb->flag, sizeof(int));
-  al((void**)&jb->ls, sizeof(LoopState));
-  al((void**)&jb->part, sizeof(double2) * TRAPZ_MAX_BLOCKS);
+  al((void**)&jb->ls, B * sizeof(LoopState));
+  al((void**)&jb->part, B * sizeof(double2) * TRAPZ_MAX_BLOCKS);
   al((void**)&jb->bar, 64);
-  al((void**)&jb->Ubar, (size_t)(M + 1) * c->K * sizeof(double));
-  al((void**)&jb->Rs, (size_t)(M + 1) * c->P * sizeof(double));
+  al((void**)&jb->Ubar, S1 * c->K * sizeof(double));
+  al((void**)&jb->Rs, S1 * c->P * sizeof(double));
+  const size_t vb = (size_t)c->KKp * S1 * c->n * (c->tf32 ? 4 : 2);
   if (c->tc) {
-    al((void**)&jb->Vhi, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
-    al((void**)&jb->Vlo, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
+    al((void**)&jb->Vhi, vb);
+    al((void**)&jb->Vlo, vb);
   }
   // the hi/lo operand starts at zero: with the low-rank coupling its padding
   // columns are never written again (k_raman_vpack writes the r columns only)
-  if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vhi, 0, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
-  if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vlo, 0, (size_t)c->KKp * (M + 1) * c->n * (c->tf32 ? 4 : 2));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_ls, sizeof(LoopState));
+  if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vhi, 0, vb);
+  if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vlo, 0, vb);
+  // every slot starts empty (a packed launch skips it)
+  if (e == cudaSuccess) e = cudaMemset(jb->ls, 0, B * sizeof(LoopState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_ls, B * sizeof(LoopState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&jb->h_io, Nn * 16);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&jb->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess && slots > 1) {
+    for (int k = 0; k < slots; ++k) {
+      std::memset(&jb->h_ls[k], 0, sizeof(LoopState));
+      jb->h_ls[k].idle = 1;
+    }
+    e = cudaMemcpy(jb->ls, jb->h_ls, B * sizeof(LoopState), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     gm_set_last_cuda_error(e, "workspace allocation", __FILE__, __LINE__);
     cudaGetLastError();
@@ -844,7 +861,7 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) {
       return rc;
     }
   }
-  jb->bytes = job_bytes(c, M);
+  jb->bytes = job_bytes(c, M) * B;
   *out = jb;
   return GMMNLSE_OK;
 }
@@ -873,6 +890,37 @@ int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double
   if (M > jb->Mcap) return GMMNLSE_E_INVALID;
   return c->fp64 ? gm_propagate_f64(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
                  : gm_propagate_f32(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
+}
+
+size_t gm_job_bytes(const gm_job* jb) { return jb->bytes; }
+
+bool gm_packable(const gmmnlse_ctx* c, double L, double dz, int M) {
+  long nfull = 0;
+  int Mrem = 0;
+  if (gm_schedule(L, dz, M, &nfull, &Mrem) != GMMNLSE_OK || Mrem != 0 || nfull < 1) return false;
+  // the Sec. IV terms, the opt-in cooperative long step and FP64 at 2^14
+  // (cluster transforms) run unpacked
+  const char* persist = getenv("GMMNLSE_PERSIST");
+  if (persist && persist[0] == '1') return false;
+  if (c->fp64 && c->n > 8192) return false;
+  const char* cl = getenv("GMMNLSE_CLUSTER_FFT");
+  if (cl && cl[0] == '1') return false;
+  return !(c->Q || c->gain || c->sat != 0.0);
+}
+
+int gm_pack_admit(gm_job* jb, int slot, const double* A0, double L, double dz, double tol, cudaStream_t s) {
+  if (cudaSetDevice(jb->ctx->prm.device) != cudaSuccess) return GMMNLSE_E_CUDA;
+  return jb->ctx->fp64 ? gm_pack_admit_f64(jb, slot, A0, L, dz, tol, s) : gm_pack_admit_f32(jb, slot, A0, L, dz, tol, s);
+}
+
+int gm_pack_step(gm_job* jb, cudaStream_t s, int* finished) {
+  if (cudaSetDevice(jb->ctx->prm.device) != cudaSuccess) return GMMNLSE_E_CUDA;
+  return jb->ctx->fp64 ? gm_pack_step_f64(jb, s, finished) : gm_pack_step_f32(jb, s, finished);
+}
+
+int gm_pack_retire(gm_job* jb, int slot, double* Aout, gmmnlse_stats* st, cudaStream_t s) {
+  if (cudaSetDevice(jb->ctx->prm.device) != cudaSuccess) return GMMNLSE_E_CUDA;
+  return jb->ctx->fp64 ? gm_pack_retire_f64(jb, slot, Aout, st, s) : gm_pack_retire_f32(jb, slot, Aout, st, s);
 }
 
 extern "C" int gmmnlse_profile(gmmnlse_ctx* c, int M, int reps, double* ms, double* bytes) {

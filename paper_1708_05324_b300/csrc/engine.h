@@ -10,6 +10,14 @@ struct gm_job;
 void gm_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void gm_set_last_error_text(const char* msg);
 int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out);
+int gm_job_create_slots(gmmnlse_ctx* c, int M, int slots, gm_job** out);
+size_t gm_job_bytes(const gm_job* jb);
+// Packed propagations (serving): slots of one workspace that share the
+// context and M, each with its own field, dz and tolerance.
+bool gm_packable(const gmmnlse_ctx* c, double L, double dz, int M);
+int gm_pack_admit(gm_job* jb, int slot, const double* A0_host, double L, double dz, double tol, cudaStream_t s);
+int gm_pack_step(gm_job* jb, cudaStream_t s, int* finished);  // finished[slot]: 1 when that slot has ended
+int gm_pack_retire(gm_job* jb, int slot, double* Aout_host, gmmnlse_stats* st, cudaStream_t s);
 int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M);
 int gm_make_g_maps(gmmnlse_ctx* c);
 void gm_job_destroy(gm_job* jb);
@@ -26,6 +34,12 @@ int gm_rk4ip_f64(gm_job* jb, const double* A0, bool dev_io, double L, double h, 
                  cudaStream_t s);
 int gm_profile_f32(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes);
 int gm_profile_f64(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms, double* bytes);
+int gm_pack_admit_f32(gm_job* jb, int slot, const double* A0, double L, double dz, double tol, cudaStream_t s);
+int gm_pack_admit_f64(gm_job* jb, int slot, const double* A0, double L, double dz, double tol, cudaStream_t s);
+int gm_pack_step_f32(gm_job* jb, cudaStream_t s, int* finished);
+int gm_pack_step_f64(gm_job* jb, cudaStream_t s, int* finished);
+int gm_pack_retire_f32(gm_job* jb, int slot, double* Aout, gmmnlse_stats* st, cudaStream_t s);
+int gm_pack_retire_f64(gm_job* jb, int slot, double* Aout, gmmnlse_stats* st, cudaStream_t s);
 int gm_prop_setup_f32(int device);
 int gm_prop_setup_f64(int device);
 int gm_ctx_device(const gmmnlse_ctx* c);

@@ -45,6 +45,9 @@ struct LoopState {
   unsigned arrive;         // blocks of k_trapz<R, true> that have added their sums
   double spec_v;           // sum |psi0|^2 at the start of the current long step (0: take spec[0]),
                            // the bound of the FP16 operand scale (set by k_advance)
+  double hdz;              // dz / 2 of this propagation (the trapezoid's weight)
+  int idle;                // packed launches: 1 for a slot that holds no propagation
+  unsigned batch_arrive;   // (slot 0) slots whose trapezoid decision is made in this iteration
 };
 
 struct Geo {
@@ -52,7 +55,22 @@ struct Geo {
   int raman_mode;         // 0: Kerr only; 1: V = (1-fR) U + fR h*U; 2: V = [U; h*U]
   int ss;                 // self-steepening
   double fR, gamma0, omega0, dt, hdz;  // hdz = dz / 2
+  int B;                  // propagations packed in the launch (slots; 1 for one propagation)
 };
+
+// Packed launches stack B slots of M + 1 substep slices each: slice =
+// b (M + 1) + j.  Every per-slice array (A, NL, I, E, Y, Z, the tensor-core
+// operands) is laid out by slice; the per-propagation arrays (psi0, psiR:
+// [B][N][n]; dpsi: [B][M][N][n]) by slot; the loop state is an array of B.
+__device__ __forceinline__ void slot_of(const Geo& g, int slice, int& b, int& j) {
+  b = slice / (g.M + 1);
+  j = slice - b * (g.M + 1);
+}
+// A slice does no work when its slot is empty or has converged in this long
+// step, and z0 (j = 0) after the first iteration (its integrand is known).
+__device__ __forceinline__ bool slice_skipped(const LoopState* lb, int j) {
+  return lb->idle || lb->done || (lb->iter > 0 && j == 0);
+}
 
 // Programmatic dependent launch: let the next kernel in the stream start
 // launching now, then wait until every kernel this one depends on has
@@ -100,9 +118,10 @@ template <typename R, int EPT, int S>
 __device__ __forceinline__ void ip_to_time_task(const Geo& g, const cplx<R>* __restrict__ psiR,
                                                 const cplx<R>* __restrict__ dpsi, const cplx<R>* __restrict__ E,
                                                 cplx<R>* __restrict__ A, const cplx<R>* __restrict__ tw, int iter,
-                                                int p, int j, cplx<R>* sm) {
+                                                int p, int j, cplx<R>* sm, int slice = -1) {
+  // psiR, dpsi: this slot's; E, A: by slice (= j for one propagation)
   const int n = g.n;
-  const size_t off = ((size_t)j * g.N + p) * n;
+  const size_t off = ((size_t)(slice < 0 ? j : slice) * g.N + p) * n;
   const cplx<R>* ps = psiR + (size_t)p * n;
   const cplx<R>* dp = (iter > 0) ? dpsi + ((size_t)(j - 1) * g.N + p) * n : nullptr;
   const cplx<R>* e = E + off;
@@ -126,10 +145,13 @@ __global__ void __launch_bounds__(512) k_ip_to_time(Geo g, const cplx<R>* __rest
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
-  const int p = blockIdx.x / S, j = blockIdx.y;
-  const int iter = ls->iter;
-  if (iter > 0 && j == 0) return;
-  ip_to_time_task<R, EPT, S>(g, psiR, dpsi, E, A, tw, iter, p, j, sm);
+  const int p = blockIdx.x / S, slice = blockIdx.y;
+  int b, j;
+  slot_of(g, slice, b, j);
+  const LoopState* lb = ls + b;
+  if (slice_skipped(lb, j)) return;
+  const size_t Nn = (size_t)g.N * g.n;
+  ip_to_time_task<R, EPT, S>(g, psiR + b * Nn, dpsi + (size_t)b * g.M * Nn, E, A, tw, lb->iter, p, j, sm, slice);
 }
 
 // U_k(t): |A_m|^2 for m == n, 2 Re(A_m A_n^*) for m < n (pairs k = (m <= n))
@@ -195,9 +217,10 @@ __global__ void __launch_bounds__(512) k_pairs_raman(Geo g, const cplx<R>* __res
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
-  const int j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;
-  pairs_raman_task<R, EPT, SRC>(g, A, Y, H, tw, pairs, Zs, cnt, blockIdx.x, j, sm);
+  int b, j;
+  slot_of(g, blockIdx.y, b, j);
+  if (slice_skipped(ls + b, j)) return;
+  pairs_raman_task<R, EPT, SRC>(g, A, Y, H, tw, pairs, Zs, cnt, blockIdx.x, blockIdx.y, sm);
 }
 
 // K2 with the two transforms of a pair spread over an S-block cluster
@@ -214,8 +237,10 @@ __global__ void __launch_bounds__(512) k_pairs_raman_cl(Geo g, const cplx<R>* __
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
-  const int j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;  // the same for every block of a cluster
+  int b, jl;
+  slot_of(g, blockIdx.y, b, jl);
+  if (slice_skipped(ls + b, jl)) return;  // the same for every block of a cluster
+  const int j = blockIdx.y;  // the slice
   const int n = g.n, np = n / S;
   const int s = (int)(blockIdx.x % S);
   cplx<R>* xbuf = sm + fft_smem_elems(np);
@@ -345,8 +370,10 @@ __global__ void __launch_bounds__(128) k_contract_reg(Geo g, const cplx<R>* __re
   __syncthreads();
   const int n = g.n;
   const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pt >= (size_t)(g.M + 1) * n) return;
-  if (ls->iter > 0 && pt < (size_t)n) return;
+  if (pt >= (size_t)g.B * (g.M + 1) * n) return;
+  int b, j;
+  slot_of(g, (int)(pt / n), b, j);
+  if (slice_skipped(ls + b, j)) return;
   contract_reg_point<R, N, MODE>(g, A, Y, Gs, NL, pt);
 }
 
@@ -388,9 +415,11 @@ __global__ void __launch_bounds__(512) k_integrand(Geo g, const cplx<R>* __restr
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smraw);
   pdl_enter();
-  const int p = blockIdx.x / S, j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;
-  integrand_task<R, EPT, S>(g, NL, E, fac, I, tw, p, j, sm);
+  const int p = blockIdx.x / S;
+  int b, j;
+  slot_of(g, blockIdx.y, b, j);
+  if (slice_skipped(ls + b, j)) return;
+  integrand_task<R, EPT, S>(g, NL, E, fac, I, tw, p, blockIdx.y, sm);
 }
 
 
@@ -513,6 +542,10 @@ __device__ __forceinline__ void trapz_element(const Geo& g, const cplx<R>* __res
   nrm += (double)nsum;
 }
 
+// Packed launches: grid (blocks, B), one row of blocks per slot (per-slot
+// partial sums part[b][block] and arrival counter); a slot that is empty or
+// has converged in this long step adds nothing; the last slot to decide sets
+// the graph's loop condition: continue while any slot iterates.
 template <typename R, bool DECIDE>
 __global__ void __launch_bounds__(TRAPZ_T) k_trapz(Geo g, const cplx<R>* __restrict__ psiR, cplx<R>* __restrict__ dpsi,
                                                    const cplx<R>* __restrict__ I, LoopState* ls, double2* part,
@@ -520,37 +553,61 @@ __global__ void __launch_bounds__(TRAPZ_T) k_trapz(Geo g, const cplx<R>* __restr
   __shared__ double red[64];
   __shared__ bool last;
   pdl_enter();
+  const int b = blockIdx.y;
+  LoopState* lb = ls + b;
   const size_t Nn = (size_t)g.N * g.n;
-  const int iter = ls->iter;
+  const bool work = !lb->idle && !lb->done;
+  const int iter = lb->iter;
   const int tid = threadIdx.x;
-  const R hdz = (R)g.hdz;
   double diff = 0.0, nrm = 0.0;
-  for (size_t e = (size_t)blockIdx.x * TRAPZ_T + tid; e < Nn; e += (size_t)gridDim.x * TRAPZ_T)
-    trapz_element<R>(g, psiR, dpsi, I, iter, e, hdz, diff, nrm);
+  if (work) {
+    const R hdz = (R)lb->hdz;
+    const cplx<R>* pR = psiR + b * Nn;
+    cplx<R>* dp = dpsi + (size_t)b * g.M * Nn;
+    const cplx<R>* Ib = I + (size_t)b * (g.M + 1) * Nn;
+    for (size_t e = (size_t)blockIdx.x * TRAPZ_T + tid; e < Nn; e += (size_t)gridDim.x * TRAPZ_T)
+      trapz_element<R>(g, pR, dp, Ib, iter, e, hdz, diff, nrm);
+  }
   block_sum2(diff, nrm, red);
+  double2* pb = part + (size_t)b * TRAPZ_MAX_BLOCKS;
   if (tid == 0) {
-    part[blockIdx.x] = make_double2(diff, nrm);
+    pb[blockIdx.x] = make_double2(diff, nrm);
     __threadfence();
-    last = atomicAdd(&ls->arrive, 1u) == gridDim.x - 1;
+    last = atomicAdd(&lb->arrive, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   diff = 0.0;
   nrm = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += TRAPZ_T) {
-    const double2 v = __ldcg(&part[b]);
+  for (int k = tid; k < (int)gridDim.x; k += TRAPZ_T) {
+    const double2 v = __ldcg(&pb[k]);
     diff += v.x;
     nrm += v.y;
   }
   block_sum2(diff, nrm, red);
   if (tid == 0) {
-    ls->arrive = 0;
-    if (DECIDE) {
-      decide(ls, diff, nrm, h, use_cond);
-    } else {
-      ls->diff = diff;
-      ls->nrm = nrm;
+    lb->arrive = 0;
+    if (work) {
+      if (DECIDE) {
+        decide(lb, diff, nrm, h, use_cond && g.B == 1);
+      } else {
+        lb->diff = diff;
+        lb->nrm = nrm;
+      }
+    }
+    if (DECIDE && use_cond && g.B > 1) {
+      __threadfence();
+      if (atomicAdd(&ls->batch_arrive, 1u) == gridDim.y - 1) {
+        __threadfence();
+        ls->batch_arrive = 0;
+        bool any = false;
+        for (int k = 0; k < g.B; ++k) {
+          const volatile LoopState* v = ls + k;
+          if (!v->idle && !v->done) any = true;
+        }
+        cudaGraphSetConditional(h, any ? 1u : 0u);
+      }
     }
   }
 }
@@ -587,46 +644,57 @@ __device__ __forceinline__ void step_end(LoopState* ls, cudaGraphConditionalHand
 // energy bound of the next long step's FP16 operand scale, which a gain can
 // raise) and does the long-step bookkeeping (every block reads the status
 // before it arrives).
+// Packed launches: grid (blocks, B), slot b's psi0, psiR, dpsi and EM at
+// their slot offsets (EM + b em_stride); the graph conditions are set only
+// for one propagation (a packed launch runs one long step per launch).
 template <typename R>
 __global__ void __launch_bounds__(256) k_advance(Geo g, double2* __restrict__ psi0, cplx<R>* psiR,
                                                  const cplx<R>* __restrict__ dpsi,
                                                  const double2* __restrict__ EM, LoopState* ls,
                                                  cudaGraphConditionalHandle hStep, cudaGraphConditionalHandle hIter,
-                                                 int use_cond, double2* part) {
+                                                 int use_cond, double2* part, size_t em_stride) {
   __shared__ bool last;
   __shared__ double red[32];
   pdl_enter();
+  const int b = blockIdx.y;
+  LoopState* lb = ls + b;
   const size_t Nn = (size_t)g.N * g.n;
+  double2* p0 = psi0 + b * Nn;
+  cplx<R>* pR = psiR + b * Nn;
+  const double2* em = EM + b * em_stride;
   double e2 = 0.0;
-  if (ls->status == ST_OK) {
-    const cplx<R>* d = dpsi + (size_t)(g.M - 1) * Nn;
+  if (!lb->idle && lb->status == ST_OK) {
+    const cplx<R>* d = dpsi + ((size_t)b * g.M + (g.M - 1)) * Nn;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < Nn; e += (size_t)gridDim.x * blockDim.x) {
-      const double2 p0 = psi0[e];
+      const double2 q0 = p0[e];
       const cplx<R> dd = d[e];
-      const double x = p0.x + (double)dd.x, y = p0.y + (double)dd.y;
-      const double2 w = EM[e];
+      const double x = q0.x + (double)dd.x, y = q0.y + (double)dd.y;
+      const double2 w = em[e];
       const double2 v = make_double2(x * w.x - y * w.y, x * w.y + y * w.x);
-      psi0[e] = v;
+      p0[e] = v;
       e2 += v.x * v.x + v.y * v.y;
-      if ((const void*)psiR != (const void*)psi0) psiR[e] = mk<R>((R)v.x, (R)v.y);
+      if ((const void*)psiR != (const void*)psi0) pR[e] = mk<R>((R)v.x, (R)v.y);
     }
   }
   e2 = block_sum(e2, red);
+  double2* pb = part + (size_t)b * TRAPZ_MAX_BLOCKS;
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = make_double2(e2, 0.0);
+    pb[blockIdx.x] = make_double2(e2, 0.0);
     __threadfence();
-    last = atomicAdd(&ls->arrive, 1u) == gridDim.x - 1;
+    last = atomicAdd(&lb->arrive, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double tot = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) tot += __ldcg(&part[b]).x;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) tot += __ldcg(&pb[k]).x;
   tot = block_sum(tot, red);
   if (threadIdx.x == 0) {
-    ls->arrive = 0;
-    if (ls->status == ST_OK) ls->spec_v = tot;
-    step_end(ls, hStep, hIter, use_cond);
+    lb->arrive = 0;
+    if (!lb->idle) {
+      if (lb->status == ST_OK) lb->spec_v = tot;
+      step_end(lb, hStep, hIter, use_cond && g.B == 1);
+    }
   }
 }
 

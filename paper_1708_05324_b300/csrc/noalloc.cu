@@ -206,6 +206,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
   // every field of the loop state starts from these values (the scratch
   // keeps whatever the previous call left there)
   LoopState h = {};
+  h.hdz = 0.5 * dz;
   h.tol = tol;
   h.floor_eps = c->fp64 ? 1e-14 : (c->prm.precision == GMMNLSE_FP32 ? 1e-6 : 1e-5);
   h.max_iter = c->prm.max_iter > 0 ? c->prm.max_iter : 50;
@@ -228,6 +229,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
     g.raman_mode = c->raman_mode;
     g.ss = c->prm.self_steepening ? 1 : 0;
     g.fR = c->fR; g.gamma0 = c->gamma0; g.omega0 = c->omega0; g.dt = c->prm.dt; g.hdz = 0.5 * dz;
+    g.B = 1;
     const dim3 gridNM(N, Mj + 1);
     for (;;) {
       k_ip_to_time<R, EPT, 1><<<gridNM, T, sm, s>>>(g, (const cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
@@ -247,7 +249,7 @@ static int run(gmmnlse_ctx* c, unsigned char* base, const double* A0, double L, 
       if (hs.done) break;
     }
     k_advance<R><<<blocks_for(Nn), 256, 0, s>>>(g, w.psi0, (cplx<R>*)w.psiR, (const cplx<R>*)w.dpsi,
-                                               w.EM64 + (size_t)which * Nn, w.ls, 0, 0, 0, w.part);
+                                               w.EM64 + (size_t)which * Nn, w.ls, 0, 0, 0, w.part, 0);
     CKN(cudaGetLastError());
     CKN(cudaMemcpyAsync(&hs, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
     CKN(cudaStreamSynchronize(s));

@@ -144,9 +144,13 @@ static inline int split_for(int transforms, int n) {
   return 1;
 }
 
+// slices of a launch: B slots of M + 1 substeps
+static inline int slices(const Geo& g) { return g.B * (g.M + 1); }
+
 template <typename R>
-static Geo make_geo(const gmmnlse_ctx* c, int Mj, double dz) {
+static Geo make_geo(const gmmnlse_ctx* c, int Mj, double dz, int B = 1) {
   Geo g;
+  g.B = B;
   g.N = c->N;
   g.n = c->n;
   g.K = c->K;
@@ -192,8 +196,8 @@ template <typename R>
 static void launch_k1(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n, N = c->N;
-  const int S = split_for<R>(N * (g.M + 1), n), np = n / S, ept = S > 1 ? 16 : fft_ept<R>(np, N * (g.M + 1));
-  const dim3 grid(N * S, g.M + 1);
+  const int S = split_for<R>(N * slices(g), n), np = n / S, ept = S > 1 ? 16 : fft_ept<R>(np, N * slices(g));
+  const dim3 grid(N * S, slices(g));
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
     pdl_launch_cl(kern, grid, dim3(np / ept), sm, s, S, g, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi,
@@ -212,22 +216,22 @@ static void launch_k2(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n;
   const int pp = (c->K + 1) / 2;
-  const int S = split_for<R>(pp * (g.M + 1), n);
+  const int S = split_for<R>(pp * slices(g), n);
   auto args = [&](auto kern, dim3 grid, int threads, size_t sm, int cl) {
     pdl_launch_cl(kern, grid, dim3(threads), sm, s, cl, g, (const cplx<R>*)jb->A, (R*)jb->V,
                   (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)nullptr, c->K,
                   (const LoopState*)jb->ls);
   };
   auto one = [&](auto kern, int ept) {
-    pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
+    pdl_launch(kern, dim3(pp, slices(g)), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
                (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)nullptr, c->K,
                (const LoopState*)jb->ls);
   };
   if (S > 1) {
     const int np = n / S;
-    if (S == 2) args(k_pairs_raman_cl<R, 16, 2, 0>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
-    else args(k_pairs_raman_cl<R, 16, 4, 0>, dim3(S * pp, g.M + 1), np / 16, fft_cluster_smem<R>(n, S), S);
-  } else if (fft_ept<R>(n, pp * (g.M + 1)) == 32) {
+    if (S == 2) args(k_pairs_raman_cl<R, 16, 2, 0>, dim3(S * pp, slices(g)), np / 16, fft_cluster_smem<R>(n, S), S);
+    else args(k_pairs_raman_cl<R, 16, 4, 0>, dim3(S * pp, slices(g)), np / 16, fft_cluster_smem<R>(n, S), S);
+  } else if (fft_ept<R>(n, pp * slices(g)) == 32) {
     one(k_pairs_raman<R, 32, 0>, 32);
   } else {
     one(k_pairs_raman<R, 16, 0>, 16);
@@ -243,9 +247,9 @@ static void launch_k4(gm_job* jb, const Geo& g, cudaStream_t s) {
   // its 32 x 16 x 16 schedule measured faster than 16 per thread even for a
   // launch of fewer blocks than SMs (6-mode workload: 7.4 against 8.9 us),
   // unlike K1 and K2
-  const int S = split_for<R>(N * (g.M + 1), n), np = n / S;
-  const int ept = S > 1 ? 16 : ((sizeof(R) == 4 && np == 8192) ? 32 : fft_ept<R>(np, N * (g.M + 1)));
-  const dim3 grid(N * S, g.M + 1);
+  const int S = split_for<R>(N * slices(g), n), np = n / S;
+  const int ept = S > 1 ? 16 : ((sizeof(R) == 4 && np == 8192) ? 32 : fft_ept<R>(np, N * slices(g)));
+  const dim3 grid(N * S, slices(g));
   const size_t sm = fft_cluster_smem<R>(n, S);
   auto go = [&](auto kern) {
     pdl_launch_cl(kern, grid, dim3(np / ept), sm, s, S, g, (const cplx<R>*)jb->NL, (const cplx<R>*)jb->E,
@@ -263,7 +267,7 @@ static void launch_tc_lsum(gm_job* jb, const Geo& g, cudaStream_t s, const CUten
                            const CUtensorMap& mVlo, const CUtensorMap& mGhi, const CUtensorMap& mGlo,
                            const TcArgs& a) {
   gmmnlse_ctx* c = jb->ctx;
-  TcLaunch L = {&mVhi, &mVlo, &mGhi, &mGlo, a, (const LoopState*)jb->ls, s, (g.M + 1) * c->n / TC_PTS, c->tf32};
+  TcLaunch L = {&mVhi, &mVlo, &mGhi, &mGlo, a, (const LoopState*)jb->ls, s, slices(g) * c->n / TC_PTS, c->tf32};
   gm_tc_lsum(c->N, L);
 }
 
@@ -276,6 +280,7 @@ static TcArgs tc_args(gm_job* jb, const Geo& g) {
   a.A = (const float2*)jb->A;
   a.NL = (float2*)jb->NL;
   a.err = &jb->ls->tc_err;
+  a.B = g.B;
   a.wait_ns = c->tc_wait_ns;
   a.stall = c->tc_stall;
   return a;
@@ -285,8 +290,8 @@ static TcArgs tc_args(gm_job* jb, const Geo& g) {
 static void launch_pack_pairs(gm_job* jb, const Geo& g, cudaStream_t s, int mode) {
   gmmnlse_ctx* c = jb->ctx;
   const int n = c->n;
-  const int npts_total = (jb->Mcap + 1) * n;
-  const int pts = (g.M + 1) * n;
+  const int npts_total = (jb->Mcap + 1) * n * jb->slots;
+  const int pts = slices(g) * n;
   const dim3 pgrid((pts + PACK_PTS - 1) / PACK_PTS);
   auto pack = [&](auto kern) {
     pdl_launch(kern, pgrid, dim3(PACK_PTS * PACK_WARPS), (size_t)c->N * PACK_PTS * sizeof(float2), s, g,
@@ -327,7 +332,7 @@ static void launch_tc(gm_job* jb, const Geo& g, cudaStream_t s) {
 template <typename R>
 static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
-  const size_t pts = (size_t)(g.M + 1) * c->n;
+  const size_t pts = (size_t)slices(g) * c->n;
   if (c->tc) {
     if constexpr (std::is_same<R, float>::value) {
       // 16-bit operands: U is formed inside the GEMM (TcShape::FU); TF32: packed first
@@ -370,10 +375,10 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
   if constexpr (std::is_same<R, float>::value) {
     if (c->tc && !c->tf32) {
       // 16-bit operands: K2 writes GEMM 2's V' operand itself (no Y', no pack)
-      const int ept = fft_ept<float>(n, pp * (g.M + 1));
-      const int npts_total = (jb->Mcap + 1) * n;
+      const int ept = fft_ept<float>(n, pp * slices(g));
+      const int npts_total = (jb->Mcap + 1) * n * jb->slots;
       auto vp = [&](auto kern) {
-        pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<float>(n), s, g, (const float*)jb->Z, c->r,
+        pdl_launch(kern, dim3(pp, slices(g)), dim3(n / ept), fft_smem<float>(n), s, g, (const float*)jb->Z, c->r,
                    (const float2*)c->Hv, (const float2*)twid<float>(c), npts_total, (void*)jb->Vhi, (void*)jb->Vlo,
                    c->eW, (const LoopState*)jb->ls);
       };
@@ -388,20 +393,20 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
     }
   }
   auto one = [&](auto kern, int ept) {
-    pdl_launch(kern, dim3(pp, g.M + 1), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
+    pdl_launch(kern, dim3(pp, slices(g)), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
                (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)jb->Z, c->r,
                (const LoopState*)jb->ls);
   };
-  const int S = split_for<R>(pp * (g.M + 1), n);
+  const int S = split_for<R>(pp * slices(g), n);
   if (S > 1) {
     auto cl = [&](auto kern) {
-      pdl_launch_cl(kern, dim3(S * pp, g.M + 1), dim3(n / S / 16), fft_cluster_smem<R>(n, S), s, S, g,
+      pdl_launch_cl(kern, dim3(S * pp, slices(g)), dim3(n / S / 16), fft_cluster_smem<R>(n, S), s, S, g,
                     (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
                     (const R*)jb->Z, c->r, (const LoopState*)jb->ls);
     };
     if (S == 2) cl(k_pairs_raman_cl<R, 16, 2, 1>);
     else cl(k_pairs_raman_cl<R, 16, 4, 1>);
-  } else if (fft_ept<R>(n, pp * (g.M + 1)) == 32) {
+  } else if (fft_ept<R>(n, pp * slices(g)) == 32) {
     one(k_pairs_raman<R, 32, 1>, 32);
   } else {
     one(k_pairs_raman<R, 16, 1>, 16);
@@ -411,11 +416,11 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
 template <typename R>
 static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
-  const size_t pts = (size_t)(g.M + 1) * c->n;
+  const size_t pts = (size_t)slices(g) * c->n;
   const int mode = c->raman_mode ? 1 : 0;
   if (c->tc) {
     if constexpr (std::is_same<R, float>::value) {
-      const int npts_total = (jb->Mcap + 1) * c->n;
+      const int npts_total = (jb->Mcap + 1) * c->n * jb->slots;
       // with Raman and 16-bit operands K2 has written V' already (k_raman_vpack)
       const bool packed = mode == 1 && !c->tf32;
       auto pack = [&](auto kern) {
@@ -480,7 +485,7 @@ static void launch_linear_coupling(gm_job* jb, const Geo& g, cudaStream_t s, int
   lt.Mfull = jb->Mprop;
   lt.use_step = use_step;
   lt.zoff = zoff;
-  k_linear_coupling<R><<<elementwise_blocks((size_t)(g.M + 1) * c->n), 256, 0, s>>>(
+  k_linear_coupling<R><<<elementwise_blocks((size_t)slices(g) * c->n), 256, 0, s>>>(
       g, lt, (const cplx<R>*)jb->psiR, (const cplx<R>*)jb->dpsi, (const cplx<R>*)jb->E, (cplx<R>*)jb->I, jb->ls);
 }
 
@@ -489,8 +494,8 @@ static void launch_linear_coupling(gm_job* jb, const Geo& g, cudaStream_t s, int
 template <typename R>
 static void launch_saturation(gm_job* jb, const Geo& g, cudaStream_t s) {
   const gmmnlse_ctx* c = jb->ctx;
-  k_sat_gram<R><<<dim3(c->N, g.M + 1), 256, 0, s>>>(g, (const cplx<R>*)jb->A, jb->Ubar, jb->ls);
-  k_sat_rows<<<dim3((c->P + 127) / 128, g.M + 1), 128, 0, s>>>(c->P, c->K, c->GRt, jb->Ubar, jb->Rs, jb->ls);
+  k_sat_gram<R><<<dim3(c->N, slices(g)), 256, 0, s>>>(g, (const cplx<R>*)jb->A, jb->Ubar, jb->ls);
+  k_sat_rows<<<dim3((c->P + 127) / 128, slices(g)), 128, 0, s>>>(c->P, c->K, c->GRt, jb->Ubar, jb->Rs, jb->ls);
 }
 
 static inline bool extra_terms(const gmmnlse_ctx* c) { return c->Q || c->gain || c->sat != 0.0; }
@@ -498,7 +503,7 @@ static inline bool extra_terms(const gmmnlse_ctx* c) { return c->Q || c->gain ||
 // K5 with the convergence decision in its last block
 template <typename R>
 static void launch_k5(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
-  pdl_launch(k_trapz<R, true>, dim3(trapz_blocks((size_t)jb->ctx->N * jb->ctx->n)), dim3(TRAPZ_T), 0, s, g,
+  pdl_launch(k_trapz<R, true>, dim3(trapz_blocks((size_t)jb->ctx->N * jb->ctx->n), g.B), dim3(TRAPZ_T), 0, s, g,
              (const cplx<R>*)jb->psiR, (cplx<R>*)jb->dpsi,
              (const cplx<R>*)jb->I, jb->ls, jb->part, h, use_cond);
 }
@@ -532,9 +537,9 @@ static void launch_advance(gm_job* jb, const Geo& g, int which, cudaStream_t s, 
                            cudaGraphConditionalHandle hIter, int use_cond) {
   gmmnlse_ctx* c = jb->ctx;
   const size_t Nn = (size_t)c->N * c->n;
-  pdl_launch(k_advance<R>, dim3(elementwise_blocks(Nn)), dim3(256), 0, s, g, jb->psi0, (cplx<R>*)jb->psiR,
+  pdl_launch(k_advance<R>, dim3(elementwise_blocks(Nn), g.B), dim3(256), 0, s, g, jb->psi0, (cplx<R>*)jb->psiR,
              (const cplx<R>*)jb->dpsi, (const double2*)(jb->EM64 + (size_t)which * Nn), jb->ls, hStep, hIter,
-             use_cond, jb->part);
+             use_cond, jb->part, 2 * Nn);
 }
 
 template <typename R>
@@ -708,6 +713,7 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
   }
   // loop state
   LoopState h = {};
+  h.hdz = 0.5 * dz;
   h.tol = tol;
   h.floor_eps = c->fp64 ? 1e-14 : (c->prm.precision == GMMNLSE_FP32 ? 1e-6 : 1e-5);
   h.max_iter = c->prm.max_iter > 0 ? c->prm.max_iter : 50;
@@ -769,6 +775,187 @@ static int propagate_impl(gm_job* jb, const double* A0, bool dev_io, double L, d
   }
   if (hs.sync_err) {
     gm_set_last_error_text("long-step kernel: a grid barrier timed out");
+    return GMMNLSE_E_CUDA;
+  }
+  if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
+  if (hs.status == ST_NONFINITE) return GMMNLSE_E_NONFINITE;
+  return GMMNLSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Packed propagations: the slots of one workspace (same context and M, each
+// its own field, dz and tolerance) advance together, one long step per
+// launch, every kernel of the iteration over all slots at once; a slot
+// joins or leaves between launches.  Only whole long steps (L a multiple of
+// M dz) and contexts without the Sec. IV terms are packed.
+// ---------------------------------------------------------------------------
+template <typename R>
+static int pack_admit(gm_job* jb, int b, const double* A0, double L, double dz, double tol, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int M = jb->Mcap;
+  long nfull = 0;
+  int Mrem = 0;
+  int rc = gm_schedule(L, dz, M, &nfull, &Mrem);
+  if (rc) return rc;
+  if (Mrem != 0 || b < 0 || b >= jb->slots || !(tol >= 0) || !std::isfinite(tol)) return GMMNLSE_E_INVALID;
+  const size_t Nn = (size_t)c->N * c->n;
+  double2* tin = jb->io;
+  std::memcpy(jb->h_io, A0, Nn * 16);
+  CK(cudaMemcpyAsync(tin, jb->h_io, Nn * 16, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(jb->flag, 0, sizeof(int), s));
+  k_nonfinite<<<elementwise_blocks(Nn), 256, 0, s>>>(tin, Nn, jb->flag);
+  int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, jb->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hflag) return GMMNLSE_E_INVALID;
+  double2* p0 = jb->psi0 + (size_t)b * Nn;
+  rc = fft64(c, jb->io + Nn, tin, p0, c->N, +1, 1.0, s);
+  if (rc) return rc;
+  if (!c->fp64)
+    k_round_psi<R><<<elementwise_blocks(Nn), 256, 0, s>>>(p0, (cplx<R>*)jb->psiR + (size_t)b * Nn, Nn);
+  k_phase_tables<R><<<elementwise_blocks((size_t)(M + 1) * Nn), 256, 0, s>>>(
+      c->beta, (int)Nn, M, dz, 0, (cplx<R>*)jb->E + (size_t)b * (M + 1) * Nn, jb->EM64 + (size_t)b * 2 * Nn);
+  LoopState h = {};
+  h.hdz = 0.5 * dz;
+  h.tol = tol;
+  h.floor_eps = c->fp64 ? 1e-14 : (c->prm.precision == GMMNLSE_FP32 ? 1e-6 : 1e-5);
+  h.max_iter = c->prm.max_iter > 0 ? c->prm.max_iter : 50;
+  h.fixed_iters = c->prm.fixed_iters;
+  h.prev_eps = INFINITY;
+  h.iters_min = 1 << 30;
+  h.status = ST_OK;
+  h.nsteps = (int)nfull;
+  jb->h_ls[b] = h;
+  CK(cudaMemcpyAsync(jb->ls + b, &jb->h_ls[b], sizeof(LoopState), cudaMemcpyHostToDevice, s));
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(p0, c->N, c->n, c->prm.dt, c->omega0, (jb->ls + b)->spec);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return GMMNLSE_OK;
+}
+
+// The graph of one packed long step: the iteration loop over every slot (a
+// while-node whose condition the trapezoid kernel's last deciding slot sets:
+// continue while any slot iterates), then the advance of every slot.
+template <typename R>
+static int build_pack_graph(gm_job* jb, const Geo& g, gm_job::G& out) {
+  cudaStream_t cs = jb->cap;
+  cudaGraph_t root = nullptr;
+  CK(cudaGraphCreate(&root, 0));
+  cudaGraphConditionalHandle hIter;
+  CK(cudaGraphConditionalHandleCreate(&hIter, root, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams ci = {};
+  ci.type = cudaGraphNodeTypeConditional;
+  ci.conditional.handle = hIter;
+  ci.conditional.type = cudaGraphCondTypeWhile;
+  ci.conditional.size = 1;
+  cudaGraphNode_t nIter;
+  CK(cudaGraphAddNode(&nIter, root, nullptr, nullptr, 0, &ci));
+  cudaGraph_t gI = ci.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(cs, gI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_iteration<R>(jb, g, cs, hIter, 1);
+  CK(cudaStreamEndCapture(cs, &gI));
+  CK(cudaStreamBeginCaptureToGraph(cs, root, &nIter, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  launch_advance<R>(jb, g, 0, cs, 0, 0, 0);
+  CK(cudaStreamEndCapture(cs, &root));
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphInstantiate(&exec, root, 0));
+  out.graph = root;
+  out.exec = exec;
+  out.Mj = g.M;
+  out.which = 0;
+  out.qv = jb->ctx->qv;
+  return GMMNLSE_OK;
+}
+
+template <typename R>
+static int pack_step(gm_job* jb, cudaStream_t s, int* finished) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int B = jb->slots;
+  const Geo g = make_geo<R>(c, jb->Mcap, 0.0, B);
+  gm_job::G& slot = jb->graphs[0];
+  bool ran = false;
+  if (!graphs_disabled()) {
+    if (!slot.exec || slot.qv != c->qv) {
+      if (slot.exec) {
+        cudaGraphExecDestroy(slot.exec);
+        cudaGraphDestroy(slot.graph);
+        slot = gm_job::G();
+      }
+      if (build_pack_graph<R>(jb, g, slot) != GMMNLSE_OK) {
+        cudaGetLastError();
+        slot = gm_job::G();
+      }
+    }
+    if (slot.exec) {
+      CK(cudaGraphLaunch(slot.exec, s));
+      ran = true;
+    }
+  }
+  if (!ran) {
+    // host-driven loop over the same kernels
+    for (int it = 0; it < 4096; ++it) {
+      launch_iteration<R>(jb, g, s, 0, 0);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, B * sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool any = false;
+      for (int k = 0; k < B; ++k) any = any || (!jb->h_ls[k].idle && !jb->h_ls[k].done);
+      if (!any) break;
+    }
+    launch_advance<R>(jb, g, 0, s, 0, 0, 0);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(jb->h_ls, jb->ls, B * sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < B; ++k) {
+    const LoopState& h = jb->h_ls[k];
+    finished[k] = !h.idle && (h.status != ST_OK || h.step >= h.nsteps || h.tc_err) ? 1 : 0;
+  }
+  if (jb->h_ls[0].tc_err) {
+    gm_set_last_error_text("tensor-core contraction: a wait for its operands timed out");
+    return GMMNLSE_E_CUDA;
+  }
+  return GMMNLSE_OK;
+}
+
+template <typename R>
+static int pack_retire(gm_job* jb, int b, double* Aout, gmmnlse_stats* st, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int M = jb->Mcap;
+  const size_t Nn = (size_t)c->N * c->n;
+  double2* p0 = jb->psi0 + (size_t)b * Nn;
+  k_spec_sums<<<elementwise_blocks(Nn), 256, 0, s>>>(p0, c->N, c->n, c->prm.dt, c->omega0, (jb->ls + b)->spec + 2);
+  int rc = fft64(c, jb->io + Nn, p0, jb->io, c->N, -1, 1.0 / c->n, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(jb->h_io, jb->io, Nn * 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&jb->h_ls[b], jb->ls + b, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::memcpy(Aout, jb->h_io, Nn * 16);
+  const LoopState hs = jb->h_ls[b];
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->long_steps = hs.step;
+    st->z = (double)hs.step * M * (2.0 * hs.hdz);
+    st->iters_total = hs.iters_total;
+    st->iters_min = hs.step > 0 ? hs.iters_min : 0;
+    st->iters_max = hs.iters_max;
+    std::memcpy(st->iter_hist, hs.hist, sizeof(st->iter_hist));
+    st->eps_max = hs.eps_max;
+    st->eps_last = hs.eps;
+    st->energy_in = hs.spec[0] * c->prm.dt / c->n;
+    st->photons_in = hs.spec[1];
+    st->energy_out = hs.spec[2] * c->prm.dt / c->n;
+    st->photons_out = hs.spec[3];
+    st->coupling_rank = c->lr ? c->r : c->K;
+  }
+  // the slot is empty again
+  LoopState idle = {};
+  idle.idle = 1;
+  jb->h_ls[b] = idle;
+  CK(cudaMemcpyAsync(jb->ls + b, &jb->h_ls[b], sizeof(LoopState), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs.tc_err) {
+    gm_set_last_error_text("tensor-core contraction: a wait for its operands timed out");
     return GMMNLSE_E_CUDA;
   }
   if (hs.status == ST_NOT_CONVERGED) return GMMNLSE_E_NOT_CONVERGED;
@@ -971,7 +1158,7 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
         default:
           k_advance<R><<<elementwise_blocks(Nsz), 256, 0, s>>>(g, jb->psi0, (cplx<R>*)jb->psiR,
                                                                (const cplx<R>*)jb->dpsi, jb->EM64, jb->ls, 0, 0, 0,
-                                                               jb->part);
+                                                               jb->part, 2 * Nsz);
           break;
       }
       CK(cudaGetLastError());

@@ -80,6 +80,7 @@ struct TcArgs {
   float* Zout;       // OUT 1: D rows [M+1][zrows][n]
   int zrows;         // OUT 1: rows stored (the rest is padding)
   int nmodes, K;     // U formed in the kernel: modes of A, pair columns
+  int B;             // slots of a packed launch (1: one propagation)
   const int2* pairs; // U formed in the kernel: (m, n) of column k
   unsigned long long wait_ns;  // limit of every mbarrier wait [ns]
   int stall;         // test hook: the MMA issuer waits on a barrier nothing completes,
@@ -98,8 +99,11 @@ __host__ __device__ constexpr int tc_cluster(int NB) { return NB >= 32 ? 2 : 1; 
 // the previous long step's advance; at the first, by the input sums), so it
 // follows an energy that grows along the fiber (gain); within one long step
 // the 4x headroom below the FP16 maximum covers the growth.
-__device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n) {
-  double b = (ls->spec_v > 0.0 ? ls->spec_v : ls->spec[0]) / (double)n;
+__device__ __forceinline__ int f16_v_exp(const LoopState* ls, int n, int B = 1) {
+  // a packed launch takes the largest bound over its occupied slots
+  double b = 0.0;
+  for (int k = 0; k < B; ++k)
+    if (!ls[k].idle) b = fmax(b, (ls[k].spec_v > 0.0 ? ls[k].spec_v : ls[k].spec[0]) / (double)n);
   if (!(b > 0.0) || !isfinite(b)) b = 1.0;
   int e;
   frexp(2.0 * b, &e);  // 2 b < 2^e
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
     // column k of U: the offsets of A_m and A_n in the A tile (16 bits each)
     // and the weight (1 on the diagonal, 2 off it, times the FP16 scale);
     // the padding columns have weight 0
-    const float sc = a.f16 ? ldexpf(1.0f, f16_v_exp(ls, a.n)) : 1.0f;
+    const float sc = a.f16 ? ldexpf(1.0f, f16_v_exp(ls, a.n, a.B)) : 1.0f;
     for (int k = tid; k < a.KKp; k += S::THREADS) {
       int2 e = make_int2(0, 0);
       if (k < a.K) {
@@ -308,17 +312,21 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
     atomicExch(a.err, 1u);
   };
   const uint32_t tmem = tmem_base;
-  const int iter = ls->iter;
   const int nrb = OUT == 0 ? S::NRB : a.nrb;
   const int n = a.n;
   const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-  const int ntiles = (a.M + 1) * (n / TC_PTS);
+  const int ntiles = a.B * (a.M + 1) * (n / TC_PTS);
   const int nitems = (ntiles + TPW * CL - 1) / (TPW * CL);  // work items of CL x TPW tiles
   const int kchunks = a.KKp / TC_KC;
   // this CTA's tiles of work item wi: (wi CL + rank) TPW + h
   auto tile_of = [&](int wi, int h) { return (wi * CL + (int)rank) * TPW + h; };
-  // z0 tiles are skipped after the first iteration (their integrand is known)
-  auto live = [&](int tile) { return tile < ntiles && (iter == 0 || tile * TC_PTS >= n); };
+  // a tile (in one slice: n is a multiple of 128) is skipped when its slice
+  // does no work (z0 after the first iteration; empty or converged slots)
+  auto live = [&](int tile) {
+    if (tile >= ntiles) return false;
+    const int slice = tile * TC_PTS / n, b = slice / (a.M + 1), j = slice - b * (a.M + 1);
+    return !slice_skipped(ls + b, j);
+  };
   // an item runs in both CTAs of a pair if any of its tiles is live
   auto live_item = [&](int wi) {
     bool any = false;
@@ -551,7 +559,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     // FP16: D = 2^(eV + eG) R; folded into the mode values of the l-sum
-    const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n) - a.eVoff + a.eG)) : 1.0f;
+    const float inv = a.f16 ? ldexpf(1.0f, -(f16_v_exp(ls, a.n, a.B) - a.eVoff + a.eG)) : 1.0f;
     int w = 0;
     constexpr int NA = N > 0 ? N : 1;
     for (int wi = cid; wi < nitems && !*stop; wi += ncl) {
@@ -659,13 +667,17 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_hilo(
   extern __shared__ float2 pack_as[];  // [N][PACK_PTS]
   pdl_enter();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int n = g.n, npts = (g.M + 1) * n;
-  const int pt0 = blockIdx.x * PACK_PTS;  // n is a multiple of 128: a block lies in one substep
-  const int j = pt0 / n;
-  if (ls->iter > 0 && j == 0) return;
+  const int n = g.n, npts = g.B * (g.M + 1) * n;
+  const int pt0 = blockIdx.x * PACK_PTS;  // n is a multiple of 128: a block lies in one slice
+  const int j = pt0 / n;                  // the slice
+  {
+    int b, jl;
+    slot_of(g, j, b, jl);
+    if (slice_skipped(ls + b, jl)) return;
+  }
   const int pt = pt0 + lane, t = pt - j * n;
   const bool ok = pt < npts;
-  const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n)) : 1.0f;
+  const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n, g.B)) : 1.0f;
   for (int i = threadIdx.x; i < g.N * PACK_PTS; i += blockDim.x) {
     const int l = i / PACK_PTS, q = i - l * PACK_PTS;
     pack_as[i] = (pt0 + q < npts) ? A[((size_t)j * g.N + l) * n + (pt0 + q - j * n)] : make_float2(0.f, 0.f);
@@ -721,13 +733,17 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_rows(
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = g.n;
   const int pt = blockIdx.x * PACK_PTS + lane;
-  if (pt >= (g.M + 1) * n) return;
-  const int j = pt / n, t = pt - j * n;
-  if (ls->iter > 0 && j == 0) return;
+  if (pt >= g.B * (g.M + 1) * n) return;
+  const int j = pt / n, t = pt - j * n;  // j: the slice
+  {
+    int b, jl;
+    slot_of(g, j, b, jl);
+    if (slice_skipped(ls + b, jl)) return;
+  }
   const float* z = Zs + (size_t)j * r * n + t;
   const float* y = Ys + (size_t)j * r * n + t;
   const float fR = (float)g.fR, fK = (float)(1.0 - g.fR);
-  const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n) - eVoff) : 1.0f;
+  const float scale = F16 ? ldexpf(1.0f, f16_v_exp(ls, n, g.B) - eVoff) : 1.0f;
   for (int kc = w; kc < KKp / 8; kc += PACK_WARPS) {
     __align__(16) T hi[8], lo[8];
     float x[8];
@@ -774,8 +790,12 @@ __global__ void __launch_bounds__(512) k_raman_vpack(Geo g, const float* __restr
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   pdl_enter();
-  const int j = blockIdx.y;
-  if (ls->iter > 0 && j == 0) return;
+  const int j = blockIdx.y;  // the slice
+  {
+    int b, jl;
+    slot_of(g, j, b, jl);
+    if (slice_skipped(ls + b, jl)) return;
+  }
   const int n = g.n, k1 = 2 * blockIdx.x;
   const bool has2 = k1 + 1 < r;
   const float* z1 = Zs + ((size_t)j * r + k1) * n;
@@ -783,7 +803,7 @@ __global__ void __launch_bounds__(512) k_raman_vpack(Geo g, const float* __restr
   auto from_smem = [&](int q) { return sm[pad16(q)]; };
   auto to_smem = [&](int q, float2 x) { sm[pad16(q)] = cmul<float>(x, Hv[q]); };
   fft_block<float, -1, EPT>(sm, n, tw, load, to_smem);
-  const float scale = OP == 1 ? ldexpf(1.0f, f16_v_exp(ls, n) - eVoff) : 1.0f;
+  const float scale = OP == 1 ? ldexpf(1.0f, f16_v_exp(ls, n, g.B) - eVoff) : 1.0f;
   uint32_t* Vhi = reinterpret_cast<uint32_t*>(Vhi_);
   uint32_t* Vlo = reinterpret_cast<uint32_t*>(Vlo_);
   // 4-byte word of (k1, k1 + 1) at point p: element ((k1/8) npts_total + p) 8 + k1 % 8

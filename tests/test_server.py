@@ -98,3 +98,70 @@ def test_shutdown_with_queued_requests_does_not_hang():
     srv.close()  # waits for the running one, cancels the queued ones
     assert time.time() - t0 < 60
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-12), ("fp32", 1e-6), ("bf16", 1e-3)])
+def test_packed_requests_equal_single_propagations(precision, bar):
+    """Requests on one context with the same M share a packed workspace (one
+    launch advances every slot by a long step); each has its own dz, length,
+    tolerance and field, joins and leaves at long-step boundaries, and must
+    give what gmmnlse_propagate gives alone.  A request whose length is not a
+    whole number of long steps runs unpacked beside them."""
+    N, Nt = (10, 256) if precision == "bf16" else (3, 512)
+    prob, ctx = _ctx(N, Nt, precision, 7)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for k in range(7):
+        dz = prob.dz * (1.0 + 0.5 * k / 7)
+        nlong = 2 + (k % 4)
+        L = nlong * prob.M * dz if k != 5 else (nlong * prob.M + 2) * dz  # k = 5: a remainder long step
+        A0 = prob.A0 * (1.0 + 0.1 * rng.standard_normal())
+        tol = prob.tol if precision == "fp64" else 1e-9 * (1 + k)
+        reqs.append((A0, L, dz, tol))
+    alone = [ctx.propagate(A0, L, dz, prob.M, tol)[0] for (A0, L, dz, tol) in reqs]
+    srv = B.Server(hbm_budget=4 << 30, max_inflight=4)
+    tickets = [srv.submit(ctx, A0, L, dz, prob.M, tol) for (A0, L, dz, tol) in reqs]
+    res = _wait(srv, tickets, [(N, Nt)] * len(reqs))
+    for t, ref, (A0, L, dz, tol) in zip(tickets, alone, reqs):
+        rc, a, st = res[t]
+        assert rc == B.OK
+        assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < bar
+        assert st["z"] == pytest.approx(L, rel=1e-9)
+    srv.close()
+    ctx.close()
+
+
+def test_resident_bytes_never_exceed_the_budget():
+    """Four shapes whose packed workspaces do not all fit: the server frees
+    idle ones to admit the next shape, every request completes, and the bytes
+    its workspaces hold never exceed the budget."""
+    specs = [(3, 256, 11), (6, 512, 12), (3, 1024, 13), (1, 512, 14)]
+    ctxs = [_ctx(s[0], s[1], "fp32", s[2]) for s in specs]
+    packed = max(c.request_bytes(p.M) for p, c in ctxs) * 4
+    budget = int(packed * 2.5)  # about two packed workspaces at a time
+    srv = B.Server(hbm_budget=budget, max_inflight=4)
+    tickets, shapes = [], []
+    for rep in range(3):
+        for prob, ctx in ctxs:
+            tickets.append(srv.submit(ctx, prob.A0, prob.L * (1 + rep), prob.dz, prob.M, 1e-8))
+            shapes.append((prob.N, prob.Nt))
+    res = _wait(srv, tickets, shapes, timeout=300)
+    assert all(r[0] == B.OK for r in res.values())
+    now, peak = srv.resident_bytes()
+    assert 0 < peak <= budget
+    srv.close()
+    for _, ctx in ctxs:
+        ctx.close()
+
+
+def test_cancel_a_queued_request():
+    prob, ctx = _ctx(6, 512, "fp32", 15)
+    srv = B.Server(hbm_budget=1 << 30, max_inflight=1)
+    tickets = [srv.submit(ctx, prob.A0, 20 * prob.L, prob.dz, prob.M, prob.tol) for _ in range(3)]
+    assert srv.cancel(tickets[2]) == B.OK
+    res = _wait(srv, tickets[:1], [(6, 512)], timeout=300)
+    assert res[tickets[0]][0] == B.OK
+    rc, _, _ = srv.poll(tickets[2], 6, 512)
+    assert rc == B.E_CANCELLED
+    srv.close()
+    ctx.close()
