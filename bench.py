@@ -453,7 +453,41 @@ def serving_requests(count, seed=5, max_substeps=2000, M=10):
     return reqs
 
 
-def run_serving(B, dev, count=32, max_substeps=2000, inflight=8, load=0.9, seed=5):
+def _serve_pass(B, srv, ctxs, reqs, gaps=None):
+    """Submit the requests (all at once, or each after its gap in seconds
+    from the previous one) and poll, while submitting, until every one has
+    ended: (seconds, {index: (latency s from submission to the poll that saw
+    it end, status, field)})."""
+    done, pending = {}, {}
+    t0 = time.perf_counter()
+    due = t0 + (np.cumsum(gaps) if gaps is not None else np.zeros(len(reqs)))
+    nxt = 0
+    while nxt < len(reqs) or pending:
+        now = time.perf_counter()
+        while nxt < len(reqs) and due[nxt] <= now:
+            r = reqs[nxt]
+            t = srv.submit(ctxs[(r["N"], r["Nt"])], r["A0"], r["L"], r["dz"], r["M"], 1e-6)
+            pending[t] = (nxt, time.perf_counter())
+            nxt += 1
+        for t in list(pending):
+            i, ts = pending[t]
+            r = reqs[i]
+            rc, out, st = srv.poll(t, r["N"], r["Nt"])
+            if rc != B.PENDING:
+                done[i] = (time.perf_counter() - ts, rc, out)
+                del pending[t]
+        time.sleep(0.0002)
+    return time.perf_counter() - t0, done
+
+
+def run_serving(B, dev, count=512, max_substeps=0, inflight=32, load=0.9, seed=5, compare=64, sample=8):
+    """The C5 request mix through gmmnlse_submit / gmmnlse_poll in MIXED_BF16:
+    a closed-loop pass (every request submitted at once: capacity), an
+    open-loop pass with Poisson arrivals at `load` x that capacity (p50 / p99
+    latency from submission to completion), the first `compare` requests
+    served with and without same-shape packing, and the first `sample`
+    requests served against the plain FP64 MPA run serially (its rate, and
+    the served results' relative L2 error against it)."""
     reqs = serving_requests(count, seed=seed, max_substeps=max_substeps)
     ctxs = {}
     for r in reqs:
@@ -461,87 +495,70 @@ def run_serving(B, dev, count=32, max_substeps=2000, inflight=8, load=0.9, seed=
         if key not in ctxs:
             prob = I.grin_problem("serve", N=r["N"], Nt=r["Nt"], dt=r["dt"], kind="gaussian", fwhm=200e-15,
                                   energy=1e-9, L=0.01, dz=1e-3, M=10, tol=1e-6, seed=1, fR=0.18, s_from="gh")
-            ctxs[key] = B.Context.from_problem(prob, precision="bf16", device=dev)
-    srv = B.Server(hbm_budget=32 << 30, max_inflight=inflight)
-
-    def submit(r):
-        return srv.submit(ctxs[(r["N"], r["Nt"])], r["A0"], r["L"], r["dz"], r["M"], 1e-6)
-
-    def drain(tickets, t_submit):
-        done = {}
-        while len(done) < len(tickets):
-            for t in tickets:
-                if t in done:
-                    continue
-                rc, out, st = srv.poll(t, *shapes[t])
-                if rc != B.PENDING:
-                    done[t] = (time.perf_counter() - t_submit[t], rc)
-            time.sleep(0.0005)
-        return done
-
-    # warm-up (graphs, workspaces)
-    shapes = {}
-    warm = []
-    for r in reqs[:4]:
-        t = submit(r)
-        shapes[t] = (r["N"], r["Nt"])
-        warm.append(t)
-    drain(warm, {t: time.perf_counter() for t in warm})
-    # capacity: all requests at once
-    t0 = time.perf_counter()
-    tickets, t_submit = [], {}
-    for r in reqs:
-        t = submit(r)
-        shapes[t] = (r["N"], r["Nt"])
-        t_submit[t] = time.perf_counter()
-        tickets.append(t)
-    done = drain(tickets, t_submit)
-    cap_s = time.perf_counter() - t0
+            ctxs[key] = (prob, B.Context.from_problem(prob, precision="bf16", device=dev))
+    cx = {k: v[1] for k, v in ctxs.items()}
+    budget = 32 << 30
+    srv = B.Server(hbm_budget=budget, max_inflight=inflight)
+    _serve_pass(B, srv, cx, reqs[:4])  # warm-up (workspaces, graphs)
+    cap_s, done = _serve_pass(B, srv, cx, reqs)
     total_units = sum(r["units"] for r in reqs)
-    status = {}
-    for _, rc in done.values():
-        status[rc] = status.get(rc, 0) + 1
     capacity = len(reqs) / cap_s
-    # open loop: Poisson arrivals at load x capacity
+    status = {}
+    for _, rc, _ in done.values():
+        status[rc] = status.get(rc, 0) + 1
+    closed_lat = np.array([done[i][0] for i in range(len(reqs))]) * 1e3
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / (load * capacity), size=len(reqs))
-    tickets, t_submit = [], {}
-    t0 = time.perf_counter()
-    next_t = t0
-    for r, gap in zip(reqs, gaps):
-        next_t += gap
-        while time.perf_counter() < next_t:
-            time.sleep(0.0002)
-        t = submit(r)
-        shapes[t] = (r["N"], r["Nt"])
-        t_submit[t] = time.perf_counter()
-        tickets.append(t)
-    done = drain(tickets, t_submit)
-    open_s = time.perf_counter() - t0
-    lat = np.array([done[t][0] for t in tickets]) * 1e3
+    open_s, done_open = _serve_pass(B, srv, cx, reqs, gaps)
+    lat = np.array([done_open[i][0] for i in range(len(reqs))]) * 1e3
+    served = {i: done_open[i][2] for i in range(min(sample, len(reqs)))}
+    _, peak = srv.resident_bytes()
     srv.close()
-    for c in ctxs.values():
-        c.close()
-    # serial plain FP64 MPA on the first 8 of the same requests
-    sub = reqs[:8]
-    t64 = 0.0
-    for r in sub:
-        prob = I.grin_problem("serve", N=r["N"], Nt=r["Nt"], dt=r["dt"], kind="gaussian", fwhm=200e-15,
-                              energy=1e-9, L=0.01, dz=1e-3, M=10, tol=1e-6, seed=1, fR=0.18, s_from="gh")
+    # the same first requests with and without packing
+    sub = reqs[:compare]
+    cmp_units = sum(r["units"] for r in sub)
+    os.environ["GMMNLSE_PACK_SLOTS"] = "1"
+    try:
+        srv1 = B.Server(hbm_budget=budget, max_inflight=inflight)
+        _serve_pass(B, srv1, cx, sub[:4])
+        unpacked_s, _ = _serve_pass(B, srv1, cx, sub)
+        srv1.close()
+    finally:
+        del os.environ["GMMNLSE_PACK_SLOTS"]
+    srvp = B.Server(hbm_budget=budget, max_inflight=inflight)
+    _serve_pass(B, srvp, cx, sub[:4])
+    packed_s, _ = _serve_pass(B, srvp, cx, sub)
+    srvp.close()
+    # serial plain FP64 MPA on the first requests: its rate, and the served
+    # (BF16, packed) results against it
+    t64, errs = 0.0, []
+    for i, r in enumerate(reqs[:sample]):
+        prob = ctxs[(r["N"], r["Nt"])][0]
         c = B.Context.from_problem(prob, precision="fp64", device=dev)
-        c.propagate(r["A0"], r["L"], r["dz"], r["M"], 1e-6, check=False)  # warm-up
+        c.propagate(r["A0"], min(r["L"], 10 * r["M"] * r["dz"]), r["dz"], r["M"], 1e-6, check=False)  # warm-up
         t1 = time.perf_counter()
-        c.propagate(r["A0"], r["L"], r["dz"], r["M"], 1e-6, check=False)
+        ref, _, rc = c.propagate(r["A0"], r["L"], r["dz"], r["M"], 1e-6, check=False)
         t64 += time.perf_counter() - t1
         c.close()
-    fp64_serial = sum(r["units"] for r in sub) / t64
+        errs.append(float(np.linalg.norm(served[i] - ref) / np.linalg.norm(ref)))
+    for _, c in ctxs.values():
+        c.close()
+    fp64_serial = sum(r["units"] for r in reqs[:sample]) / t64
     return {"requests": len(reqs), "precision": "bf16", "max_inflight": inflight,
-            "max_substeps_per_request": max_substeps,
+            "max_substeps_per_request": max_substeps or None,
+            "total_units": total_units,
             "closed_loop_units_per_s": total_units / cap_s, "closed_loop_s": cap_s,
-            "offered_load": load, "open_loop_units_per_s": total_units / open_s,
+            "closed_loop_p50_ms": float(np.percentile(closed_lat, 50)),
+            "closed_loop_p99_ms": float(np.percentile(closed_lat, 99)),
+            "offered_load": load, "open_loop_units_per_s": total_units / open_s, "open_loop_s": open_s,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "status_counts": {B.load().gmmnlse_strerror(k).decode(): v for k, v in status.items()},
-            "fp64_serial_units_per_s": fp64_serial, "fp64_serial_requests": len(sub),
+            "packing": {"requests": len(sub), "packed_units_per_s": cmp_units / packed_s,
+                        "unpacked_units_per_s": cmp_units / unpacked_s, "speedup": unpacked_s / packed_s},
+            "served_rel_l2_vs_fp64": {"requests": len(errs), "max": max(errs), "median": float(np.median(errs))},
+            "fp64_serial_units_per_s": fp64_serial, "fp64_serial_requests": sample,
+            "served_vs_fp64_serial": (total_units / cap_s) / fp64_serial,
+            "resident_peak_bytes": peak, "hbm_budget_bytes": budget,
             "mix": "C5: N in {1,3,6,10,15}, Nt 2^10..2^14, FWHM 100-500 fs, 1-200 nJ, L 1 cm-1 m, dz = z_NL/200"}
 
 
@@ -660,7 +677,11 @@ def main():
     ap.add_argument("--length", type=float, default=None, help="fiber length per step [m] (default: the full fiber)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the further workloads")
-    ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving pass (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=512, help="requests in the serving pass (0: skip)")
+    ap.add_argument("--serve-max-substeps", type=int, default=2000,
+                    help="serving pass: cut longer requests to this many substeps (0: every request whole, "
+                         "lengths up to 1 m; several minutes)")
+    ap.add_argument("--serve-only", action="store_true", help="only the serving pass (one JSON line)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--profile-run", action="store_true",
@@ -702,6 +723,11 @@ def main():
         dist.init_process_group("nccl")
     dev = local
     torch.cuda.set_device(dev)
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": run_serving(B, dev, count=args.serve_requests,
+                                                     max_substeps=args.serve_max_substeps)}))
+        return
 
     # each rank draws its own replica of the workload (seed + rank)
     prob = problem(args.workload, L=args.length, seed=SEED[args.workload] + rank, dev=dev)
@@ -808,7 +834,7 @@ def main():
                 extra[key] = extra_line(B, name, prec, length, dev, stream, flush)
         line["extra"] = extra
     if args.serve_requests > 0:
-        line["serving"] = run_serving(B, dev, count=args.serve_requests)
+        line["serving"] = run_serving(B, dev, count=args.serve_requests, max_substeps=args.serve_max_substeps)
     if not args.no_cpu_baseline:
         its = line["config"]["iters_per_long_step"] if args.workload == "C4" else C4_ITERS_PER_LONG_STEP
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, its)

@@ -432,7 +432,8 @@ size_t gmmnlse_request_bytes(const gmmnlse_ctx* ctx, int M);
  * Same-shape requests are packed: requests on one context with the same M
  * that run whole long steps (L a whole number of M dz; any dz, tol and
  * field) and no linear coupling, gain or saturation share a workspace of
- * min(max_inflight, 16) slots, and one launch (a CUDA graph captured once
+ * min(max_inflight, 16) slots (the environment variable GMMNLSE_PACK_SLOTS
+ * at server creation overrides it; 1 turns packing off), and one launch (a CUDA graph captured once
  * per workspace) advances all of them by one long step, every kernel of the
  * MPA iteration over all slots at once; a request joins or leaves between
  * launches.  Each slot keeps its own convergence, so its result equals that

@@ -53,6 +53,8 @@ struct gm_job {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
   } graphs[2];
+  // packed launches: the graph of a long step over the first B slots, [B]
+  std::vector<G> pack_graphs;
   size_t bytes = 0;
   // mixed precision: blocked BF16 hi/lo pair-term operand and its TMA maps
   __nv_bfloat16* Vhi = nullptr;  // [KKp/EPC][(M+1) n][EPC] (and rKKp columns for the low-rank GEMM 2)

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <condition_variable>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -394,6 +395,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   const bool fp64 = prm->precision == GMMNLSE_FP64;
   int rc = set_device(prm->device);
   if (rc) return rc;
+  auto gate = gm_gate_device(prm->device);
 
   gmmnlse_ctx* c = new (std::nothrow) gmmnlse_ctx();
   if (!c) return GMMNLSE_E_NOMEM;
@@ -631,6 +633,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
 extern "C" int gmmnlse_destroy(gmmnlse_ctx* c) {
   if (!c) return GMMNLSE_OK;
   cudaSetDevice(c->prm.device);
+  auto gate = gm_gate_device(c->prm.device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_ctx(c);
   return GMMNLSE_OK;
@@ -661,6 +664,10 @@ extern "C" size_t gmmnlse_request_bytes(const gmmnlse_ctx* c, int M) { return c 
 static void free_job(gm_job* jb) {
   if (!jb) return;
   for (auto& g : jb->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  for (auto& g : jb->pack_graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
   }
@@ -797,6 +804,7 @@ int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out) { return gm_job_create_sl
 int gm_job_create_slots(gmmnlse_ctx* c, int M, int slots, gm_job** out) {
   *out = nullptr;
   if (slots < 1 || slots > 64) return GMMNLSE_E_INVALID;
+  auto gate = gm_gate_device(c->prm.device);
   gm_job* jb = new (std::nothrow) gm_job();
   if (!jb) return GMMNLSE_E_NOMEM;
   jb->ctx = c;
@@ -866,7 +874,11 @@ int gm_job_create_slots(gmmnlse_ctx* c, int M, int slots, gm_job** out) {
   return GMMNLSE_OK;
 }
 
-void gm_job_destroy(gm_job* jb) { free_job(jb); }
+void gm_job_destroy(gm_job* jb) {
+  if (!jb) return;
+  auto gate = gm_gate_device(jb->ctx->prm.device);
+  free_job(jb);
+}
 
 // ---------------------------------------------------------------------------
 // Kernel chain of one iteration and the long-step driver
@@ -884,10 +896,57 @@ int gm_schedule(double L, double dz, int M, long* nfull, int* Mrem) {
   return GMMNLSE_OK;
 }
 
+// The device work gate.  Tensor-core propagations running at the same time
+// as other propagations on other streams of one device were seen to stall
+// for good: a CTA of a pair waiting in its TMEM allocation while its peer
+// waited at the cluster barrier, although no other kernel held TMEM on that
+// SM (the same kernels on one stream never stalled).  The gate keeps the
+// tensor-core work of this library alone on its device.
+namespace {
+struct DeviceGate {
+  std::mutex m;
+  std::condition_variable cv;
+  int readers = 0, writers_waiting = 0;
+  bool writer = false;
+};
+DeviceGate g_gate[64];
+}  // namespace
+
+GmGateHold::GmGateHold(int d, bool e) : dev(d), excl(e) {
+  if (dev < 0 || dev >= 64) {
+    dev = -1;
+    return;
+  }
+  DeviceGate& g = g_gate[dev];
+  std::unique_lock<std::mutex> lk(g.m);
+  if (excl) {
+    ++g.writers_waiting;
+    g.cv.wait(lk, [&] { return !g.writer && g.readers == 0; });
+    --g.writers_waiting;
+    g.writer = true;
+  } else {
+    g.cv.wait(lk, [&] { return !g.writer && g.writers_waiting == 0; });
+    ++g.readers;
+  }
+}
+
+GmGateHold::~GmGateHold() {
+  if (dev < 0) return;
+  DeviceGate& g = g_gate[dev];
+  std::lock_guard<std::mutex> lk(g.m);
+  if (excl) g.writer = false;
+  else g.readers -= 1;
+  g.cv.notify_all();
+}
+
+GmGateHold gm_gate(const gmmnlse_ctx* c) { return GmGateHold(c->prm.device, c->tc); }
+GmGateHold gm_gate_device(int device) { return GmGateHold(device, false); }
+
 int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
                      double* Aout, gmmnlse_stats* st, cudaStream_t s) {
   gmmnlse_ctx* c = jb->ctx;
   if (M > jb->Mcap) return GMMNLSE_E_INVALID;
+  auto gate = gm_gate(c);
   return c->fp64 ? gm_propagate_f64(jb, A0, dev_io, L, dz, M, tol, Aout, st, s)
                  : gm_propagate_f32(jb, A0, dev_io, L, dz, M, tol, Aout, st, s);
 }
@@ -910,16 +969,19 @@ bool gm_packable(const gmmnlse_ctx* c, double L, double dz, int M) {
 
 int gm_pack_admit(gm_job* jb, int slot, const double* A0, double L, double dz, double tol, cudaStream_t s) {
   if (cudaSetDevice(jb->ctx->prm.device) != cudaSuccess) return GMMNLSE_E_CUDA;
+  auto gate = gm_gate_device(jb->ctx->prm.device);
   return jb->ctx->fp64 ? gm_pack_admit_f64(jb, slot, A0, L, dz, tol, s) : gm_pack_admit_f32(jb, slot, A0, L, dz, tol, s);
 }
 
 int gm_pack_step(gm_job* jb, cudaStream_t s, int* finished) {
   if (cudaSetDevice(jb->ctx->prm.device) != cudaSuccess) return GMMNLSE_E_CUDA;
+  auto gate = gm_gate(jb->ctx);
   return jb->ctx->fp64 ? gm_pack_step_f64(jb, s, finished) : gm_pack_step_f32(jb, s, finished);
 }
 
 int gm_pack_retire(gm_job* jb, int slot, double* Aout, gmmnlse_stats* st, cudaStream_t s) {
   if (cudaSetDevice(jb->ctx->prm.device) != cudaSuccess) return GMMNLSE_E_CUDA;
+  auto gate = gm_gate_device(jb->ctx->prm.device);
   return jb->ctx->fp64 ? gm_pack_retire_f64(jb, slot, Aout, st, s) : gm_pack_retire_f32(jb, slot, Aout, st, s);
 }
 
@@ -929,6 +991,7 @@ extern "C" int gmmnlse_profile(gmmnlse_ctx* c, int M, int reps, double* ms, doub
   int rc = set_device(c->prm.device);
   if (rc) return rc;
   if (!c->job || c->job->Mcap < M || c->job->tab_M < M) return GMMNLSE_E_INVALID;
+  auto gate = gm_gate(c);
   return c->fp64 ? gm_profile_f64(c, c->job, M, reps, ms, bytes) : gm_profile_f32(c, c->job, M, reps, ms, bytes);
 }
 
@@ -948,7 +1011,7 @@ extern "C" int gmmnlse_propagate(gmmnlse_ctx* c, const double* A0, double L, dou
   if (rc) return rc;
   if (c->job && c->job->Mcap < M) {
     cudaStreamSynchronize(c->stream);
-    free_job(c->job);
+    gm_job_destroy(c->job);
     c->job = nullptr;
   }
   if (!c->job) {
@@ -972,6 +1035,7 @@ extern "C" int gmmnlse_propagate_rk4ip(gmmnlse_ctx* c, const double* A0, double 
     rc = gm_job_create(c, 1, &c->job);
     if (rc) return rc;
   }
+  auto gate = gm_gate(c);
   return c->fp64 ? gm_rk4ip_f64(c->job, A0, c->prm.io_device != 0, L, h, Aout, st, c->stream)
                  : gm_rk4ip_f32(c->job, A0, c->prm.io_device != 0, L, h, Aout, st, c->stream);
 }
@@ -983,6 +1047,7 @@ extern "C" int gmmnlse_set_linear_coupling(gmmnlse_ctx* c, const double* Q) {
     for (size_t i = 0; i < NN; ++i)
       if (!std::isfinite(Q[i])) return GMMNLSE_E_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
+  auto gate = gm_gate_device(c->prm.device);
   int rc = set_device(c->prm.device);
   if (rc) return rc;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -1008,6 +1073,7 @@ extern "C" int gmmnlse_set_gain(gmmnlse_ctx* c, const double* g) {
     for (size_t i = 0; i < N; ++i)
       if (!std::isfinite(g[i])) return GMMNLSE_E_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
+  auto gate = gm_gate_device(c->prm.device);
   int rc = set_device(c->prm.device);
   if (rc) return rc;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -1029,6 +1095,7 @@ extern "C" int gmmnlse_set_gain(gmmnlse_ctx* c, const double* g) {
 extern "C" int gmmnlse_set_gain_saturation(gmmnlse_ctx* c, double sat) {
   if (!c || !std::isfinite(sat) || sat < 0.0) return GMMNLSE_E_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
+  auto gate = gm_gate_device(c->prm.device);
   int rc = set_device(c->prm.device);
   if (rc) return rc;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -1061,6 +1128,7 @@ extern "C" int gmmnlse_set_coupling_profile(gmmnlse_ctx* c, const double* f, int
       if (!std::isfinite(f[i])) return GMMNLSE_E_INVALID;
   }
   std::lock_guard<std::mutex> lk(c->mu);
+  auto gate = gm_gate_device(c->prm.device);
   int rc = set_device(c->prm.device);
   if (rc) return rc;
   if (c->stream) cudaStreamSynchronize(c->stream);

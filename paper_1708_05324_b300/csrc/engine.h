@@ -7,6 +7,29 @@
 
 struct gm_job;
 
+// Device work gate.  Every library call that puts work on a device holds its
+// gate until that work has finished (each such call synchronizes before it
+// returns): calls that launch the tensor-core contraction hold it alone,
+// every other call shares it.  So tensor-core work never runs beside other
+// work of this library on the device, as on a single stream; the rest
+// overlaps freely.  Writers (tensor-core calls) waiting keep new readers
+// out.  Not re-entrant: a call holding it runs no other gated call.
+struct GmGateHold {
+  int dev = -1;
+  bool excl = false;
+  GmGateHold() = default;
+  GmGateHold(int d, bool e);
+  GmGateHold(GmGateHold&& o) noexcept : dev(o.dev), excl(o.excl) { o.dev = -1; }
+  GmGateHold(const GmGateHold&) = delete;
+  GmGateHold& operator=(const GmGateHold&) = delete;
+  GmGateHold& operator=(GmGateHold&&) = delete;
+  ~GmGateHold();
+};
+// The hold a call on context c takes (exclusive when c's contraction runs on
+// the tensor cores).
+GmGateHold gm_gate(const gmmnlse_ctx* c);
+GmGateHold gm_gate_device(int device);  // shared
+
 void gm_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void gm_set_last_error_text(const char* msg);
 int gm_job_create(gmmnlse_ctx* c, int M, gm_job** out);

@@ -294,6 +294,7 @@ extern "C" int gmmnlse_propagate_noalloc(gmmnlse_ctx* c, const double* A0, doubl
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(c->mu);
   CKN(cudaSetDevice(c->prm.device));
+  auto gate = gm_gate_device(c->prm.device);
   if (!device_pointer(A0, c->prm.device) || !device_pointer(Aout, c->prm.device)) {
     gm_set_last_error_text("gmmnlse_propagate_noalloc: A0 and Aout must be device memory of the context's device");
     return GMMNLSE_E_INVALID;

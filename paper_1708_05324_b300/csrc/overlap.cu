@@ -108,6 +108,7 @@ extern "C" int gmmnlse_overlap_tensor(int device, const double* F, int N, long l
     cudaGetLastError();
     return GMMNLSE_E_INVALID;
   }
+  auto gate = gm_gate_device(device);
   const int K = N * (N + 1) / 2;
   std::vector<int2> pairs;
   std::vector<int> kof((size_t)N * N);

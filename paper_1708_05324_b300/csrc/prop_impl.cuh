@@ -871,8 +871,16 @@ template <typename R>
 static int pack_step(gm_job* jb, cudaStream_t s, int* finished) {
   gmmnlse_ctx* c = jb->ctx;
   const int B = jb->slots;
-  const Geo g = make_geo<R>(c, jb->Mcap, 0.0, B);
-  gm_job::G& slot = jb->graphs[0];
+  // the launch covers the slots up to the last occupied one (the host mirror
+  // of the loop states knows which: admission and retirement write it)
+  int Bact = 0;
+  for (int k = 0; k < B; ++k)
+    if (!jb->h_ls[k].idle) Bact = k + 1;
+  for (int k = 0; k < B; ++k) finished[k] = 0;
+  if (Bact == 0) return GMMNLSE_OK;
+  const Geo g = make_geo<R>(c, jb->Mcap, 0.0, Bact);
+  if ((int)jb->pack_graphs.size() < B + 1) jb->pack_graphs.resize(B + 1);
+  gm_job::G& slot = jb->pack_graphs[Bact];
   bool ran = false;
   if (!graphs_disabled()) {
     if (!slot.exec || slot.qv != c->qv) {
@@ -896,10 +904,10 @@ static int pack_step(gm_job* jb, cudaStream_t s, int* finished) {
     for (int it = 0; it < 4096; ++it) {
       launch_iteration<R>(jb, g, s, 0, 0);
       CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, B * sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(jb->h_ls, jb->ls, Bact * sizeof(LoopState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       bool any = false;
-      for (int k = 0; k < B; ++k) any = any || (!jb->h_ls[k].idle && !jb->h_ls[k].done);
+      for (int k = 0; k < Bact; ++k) any = any || (!jb->h_ls[k].idle && !jb->h_ls[k].done);
       if (!any) break;
     }
     launch_advance<R>(jb, g, 0, s, 0, 0, 0);

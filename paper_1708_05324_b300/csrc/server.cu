@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -93,6 +94,7 @@ struct gmmnlse_server {
   std::list<Space> spaces;     // every workspace held (oldest first)
   std::map<std::pair<gmmnlse_ctx*, int>, std::unique_ptr<Group>> groups;
   std::vector<std::thread> workers;
+  std::vector<gm_job*> graveyard;  // released workspaces, freed outside the lock
   size_t budget = 0, resident = 0, peak = 0;
   int max_inflight = 1, inflight = 0, pack_slots = 1;
   uint64_t next_ticket = 1;
@@ -109,14 +111,26 @@ static Space* reserve(gmmnlse_server* s, gmmnlse_ctx* c, int M, int slots, bool 
   return &s->spaces.back();
 }
 
+// Lock held: the workspace's memory is freed by drain() after the lock is
+// let go (freeing waits for the device).
 static void release(gmmnlse_server* s, Space* sp) {
-  if (sp->job) gm_job_destroy(sp->job);
+  if (sp->job) s->graveyard.push_back(sp->job);
   s->resident -= sp->bytes;
   for (auto it = s->spaces.begin(); it != s->spaces.end(); ++it)
     if (&*it == sp) {
       s->spaces.erase(it);
       return;
     }
+}
+
+// Free the released workspaces (lock not held).
+static void drain(gmmnlse_server* s) {
+  std::vector<gm_job*> dead;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    dead.swap(s->graveyard);
+  }
+  for (gm_job* j : dead) gm_job_destroy(j);
 }
 
 // Make room for `need` more bytes by freeing idle workspaces, oldest first;
@@ -238,6 +252,7 @@ static void worker_main(gmmnlse_server* s) {
       else sp->busy = false;
       dispatch(s);
     }
+    drain(s);
     s->cv_work.notify_all();
     s->cv_done.notify_all();
   }
@@ -301,6 +316,7 @@ static void group_main(gmmnlse_server* s, Group* gp) {
         }
         dispatch(s);
       }
+      drain(s);
       s->cv_done.notify_all();
       s->cv_work.notify_all();
     }
@@ -315,6 +331,8 @@ extern "C" int gmmnlse_server_create(size_t hbm_budget, int max_inflight, gmmnls
   s->budget = hbm_budget;
   s->max_inflight = max_inflight;
   s->pack_slots = std::min(max_inflight, 16);
+  // GMMNLSE_PACK_SLOTS overrides the slots of a packed workspace (1: no packing)
+  if (const char* v = getenv("GMMNLSE_PACK_SLOTS")) s->pack_slots = std::max(1, std::min(16, atoi(v)));
   for (int i = 0; i < max_inflight; ++i) s->workers.emplace_back(worker_main, s);
   *out = s;
   return GMMNLSE_OK;
@@ -353,6 +371,7 @@ extern "C" int gmmnlse_submit(gmmnlse_server* s, gmmnlse_ctx* ctx, const double*
     *ticket = r->ticket;
     dispatch(s);
   }
+  drain(s);
   s->cv_work.notify_all();
   return GMMNLSE_OK;
 }
@@ -447,6 +466,7 @@ extern "C" int gmmnlse_server_destroy(gmmnlse_server* s) {
   for (auto& kv : s->all) delete kv.second;
   for (auto& sp : s->spaces)
     if (sp.job) gm_job_destroy(sp.job);
+  for (gm_job* j : s->graveyard) gm_job_destroy(j);
   delete s;
   return GMMNLSE_OK;
 }

@@ -143,20 +143,28 @@ __device__ __forceinline__ void cluster_sync() {
 // ---- TMEM ------------------------------------------------------------------
 // Allocate ncols (power of two >= 32) TMEM columns; one full warp executes
 // (with PAIR, one warp in each CTA of the pair, the same ncols: the columns
-// are allocated in both CTAs' TMEM at the same address).
+// are allocated in both CTAs' TMEM at the same address).  The allocation
+// waits while the SM's TMEM is taken; it takes no part in a wait limit.
 template <bool PAIR>
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, unsigned ncols) {
-  if constexpr (PAIR) {
+  if constexpr (PAIR)
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
                  "r"(ncols)
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-  } else {
+  else
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst_smem)),
                  "r"(ncols)
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+}
+// Give up the right to allocate again (the warp that allocated).  With PAIR
+// only after both CTAs of the pair have allocated (a cluster barrier
+// between): under concurrent launches, a CTA that gave it up while its
+// peer had not yet allocated was seen to leave the peer waiting in
+// tmem_alloc without end.
+template <bool PAIR>
+__device__ __forceinline__ void tmem_relinquish() {
+  if constexpr (PAIR) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  else asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 template <bool PAIR>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, unsigned ncols) {

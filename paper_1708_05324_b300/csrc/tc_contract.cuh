@@ -175,6 +175,11 @@ struct TcShape {
   static constexpr int COLS = NBUF * ACC_COLS;
   static constexpr int TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
   static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + U_RESERVE;
+  // TMEM never runs short: with 228 KB of shared memory per SM at most two
+  // of these CTAs (of any shape) share an SM, and one that takes more than
+  // 256 columns has the SM to itself
+  static_assert(SMEM + 1024 > 233472 / 3 && (TMEM_COLS <= 256 || SMEM + 1024 > 233472 / 2),
+                "tensor-core GEMM CTAs could share an SM's TMEM beyond its 512 columns");
   // bytes that complete a stage's barrier: both CTAs' copies (V tiles unless
   // FU, and every coupling row of the chunk, hi and lo)
   static constexpr int TX = FU ? 2 * G_BYTES : CL * STAGE;
@@ -284,8 +289,11 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
   if (warp == 1) tc::tmem_alloc<PAIR>(&tmem_base, S::TMEM_COLS);
   tc::fence_before_sync();
   __syncthreads();
-  if (PAIR) tc::cluster_sync();  // the peer's barriers exist before any remote arrival or copy
+  // the peer's barriers exist before any remote arrival or copy, and its
+  // columns are allocated before either CTA gives up the allocation permit
+  if (PAIR) tc::cluster_sync();
   tc::fence_after_sync();
+  if (warp == 1) tc::tmem_relinquish<PAIR>();
   pdl_enter();
   if (S::FU) {
     // column k of U: the offsets of A_m and A_n in the A tile (16 bits each)
