@@ -54,6 +54,13 @@ def time_from_freq(af):
 # ----------------------------------------------------------------------------
 # Fiber description
 # ----------------------------------------------------------------------------
+def _coupling_tensor(S):
+    """A coupling tensor as given: complex128 if it has complex entries,
+    else float64."""
+    S = np.asarray(S)
+    return S.astype(np.complex128) if np.iscomplexobj(S) else S.astype(np.float64)
+
+
 class Fiber:
     """The inputs of Eq. 1: per-mode beta_p(omega) [N][Nt] (rad/m, FFT order,
     mode-1 frame), coupling tensors S^K, S^R [N]^4 (1/m^2), Raman fraction f_R,
@@ -79,8 +86,11 @@ class Fiber:
         # the paper's expression (0: none)
         self.sat = float(sat)
         self.N, self.Nt = self.beta.shape
-        self.SK = np.asarray(SK, dtype=np.float64)
-        self.SR = None if SR is None else np.asarray(SR, dtype=np.float64)
+        # S^K, S^R: real for one linear polarization and real mode profiles
+        # (Eq. 2), complex in general (Eq. 1 with complex or vector mode
+        # fields; no symmetry assumed)
+        self.SK = _coupling_tensor(SK)
+        self.SR = None if SR is None else _coupling_tensor(SR)
         self.fR = float(fR)
         self.hR = None if hR is None else np.asarray(hR, dtype=np.float64)
         self.dt = float(dt)
@@ -369,14 +379,14 @@ def length_scales(fib: Fiber, A0):
     """The two length scales that set the MPA's step sizes (Sec. III.D):
     the nonlinear length z_NL = 1 / (gamma0 S_max P0), the single-mode
     estimate A_eff/(n2 omega0 P0) with 1/A_eff the largest self-overlap
-    S^K_pppp and the speed of light that the paper's printed form omits
+    |S^K_pppp| and the speed of light that the paper's printed form omits
     (gamma0 = n2 omega0 / c), P0 the peak of sum_p |A_p(t)|^2; and the
     intermode beat length z_IM = 1 / max_p |delta beta0^(p)|, delta beta0^(p)
     = beta_p(omega = 0) - beta_1(omega = 0) (infinite for a single mode).
     A0: [N][Nt] time domain.  Returns (z_NL, z_IM)."""
     A0 = np.asarray(A0)
     P0 = float(np.max(np.sum(np.abs(A0) ** 2, axis=0)))
-    S_max = max(float(fib.SK[p, p, p, p]) for p in range(fib.N))
+    S_max = max(abs(complex(fib.SK[p, p, p, p])) for p in range(fib.N))
     z_nl = 1.0 / (fib.gamma0 * S_max * P0)
     db0 = np.abs(fib.beta[:, 0] - fib.beta[0, 0])
     z_im = 1.0 / float(np.max(db0)) if np.max(db0) > 0 else math.inf

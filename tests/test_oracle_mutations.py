@@ -54,6 +54,14 @@ MUTATIONS = {
         ("T = (np.asarray(SK).reshape(N * N, N * N) @ Q).reshape(N, N, -1)  # T[p,l,t]",
          "T = (np.asarray(SK).transpose(0, 3, 2, 1).reshape(N * N, N * N) @ Q).reshape(N, N, -1)"),
     ],
+    "complex_coupling_dropped": [
+        ("return S.astype(np.complex128) if np.iscomplexobj(S) else S.astype(np.float64)",
+         "return np.real(S).astype(np.float64)"),
+    ],
+    "complex_coupling_conjugated": [
+        ("return S.astype(np.complex128) if np.iscomplexobj(S) else S.astype(np.float64)",
+         "return np.conj(S).astype(np.complex128) if np.iscomplexobj(S) else S.astype(np.float64)"),
+    ],
     "raman_acausal": [
         ("return dt * np.fft.ifft(np.fft.fft(h) * np.fft.fft(q, axis=-1), axis=-1)",
          "return dt * np.fft.ifft(np.conj(np.fft.fft(h)) * np.fft.fft(q, axis=-1), axis=-1)"),

@@ -447,3 +447,82 @@ def test_length_scales_of_a_soliton_and_of_the_grin_mode_groups():
     P0 = float(np.max(np.sum(np.abs(prob.A0) ** 2, axis=0)))
     w = I.grin_mode_width(25e-6, 0.2, LAM0)
     assert z_nl == pytest.approx(1.0 / (gamma_of(s=1.0 / (math.pi * w * w)) * P0), rel=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# Complex coupling tensors (Eq. 1 without the single-polarization, real-
+# profile simplification of Eq. 2)
+# ----------------------------------------------------------------------------
+def test_p20_complex_bracket_equals_brute_force_loops():
+    """The bracket of Eq. 1 with complex, unsymmetric S^K and S^R against
+    explicit loops over (p, l, m, n, t, tau)."""
+    rng = np.random.default_rng(20)
+    N, Nt, dt = 3, 8, 2e-15
+    SK = rng.standard_normal((N, N, N, N)) + 1j * rng.standard_normal((N, N, N, N))
+    SR = rng.standard_normal((N, N, N, N)) + 1j * rng.standard_normal((N, N, N, N))
+    A = rng.standard_normal((N, Nt)) + 1j * rng.standard_normal((N, Nt))
+    h = rng.random(Nt)
+    fR = 0.3
+    fib = O.Fiber(np.zeros((N, Nt)), SK, SR, fR, h, dt, LAM0, N2, False)
+    got = O.nonlinear_bracket(fib, A)
+    want = np.zeros((N, Nt), dtype=complex)
+    for p in range(N):
+        for t in range(Nt):
+            for l in range(N):
+                for m in range(N):
+                    for n in range(N):
+                        conv = sum(h[tau] * A[m, (t - tau) % Nt] * np.conj(A[n, (t - tau) % Nt])
+                                   for tau in range(Nt)) * dt
+                        want[p, t] += A[l, t] * ((1 - fR) * SK[p, l, m, n] * A[m, t] * np.conj(A[n, t])
+                                                 + fR * SR[p, l, m, n] * conv)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13 * abs(want).max())
+
+
+def test_p21_complex_single_mode_cw_closed_form():
+    """One mode, no dispersion, a complex self-coupling s: dA/dz = i gamma0 s
+    |A|^2 A (Eq. 1 with N = 1, f_R = 0, no self-steepening) gives for CW light
+    |A(z)|^2 = I0 / (1 + 2 gamma0 Im(s) I0 z) and the phase
+    Re(s) / (2 Im(s)) ln(1 + 2 gamma0 Im(s) I0 z).  The MPA reaches it to
+    its O(dz^2) trapezoid error."""
+    Nt, dt = 32, 1e-14
+    s = (1.0 + 0.35j) / AEFF
+    fib = single_mode(Nt, dt, s=s)
+    I0, L = 2.0e4, 0.5
+    A0 = np.full((1, Nt), math.sqrt(I0), dtype=complex)
+    g = fib.gamma0
+    x = 1.0 + 2.0 * g * s.imag * I0 * L
+    want = math.sqrt(I0 / x) * np.exp(1j * s.real / (2.0 * s.imag) * math.log(x))
+    assert abs(I0 / x - 1.0) > 0.05  # the loss is visible
+    errs = []
+    for dz in (1e-3, 5e-4):
+        A, st = O.mpa_propagate(fib, A0, L, dz, 10, 1e-14, max_iter=200)
+        assert st["status"] == 0
+        errs.append(rel(A, np.full((1, Nt), want)))
+    assert errs[0] < 4e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5  # second order in dz
+
+
+def test_p22_complex_mode_basis_is_a_unitary_change_of_variables():
+    """A unitary mixing T of a degenerate pair of GRIN modes (HG10, HG01 ->
+    (HG10 +- i HG01)/sqrt(2)) turns the real S of Eq. 2 into the complex,
+    m <-> n unsymmetric S'_plmn = sum T_pa T*_lb T*_mc T_nd S_abcd, and the
+    same for S^R (Eq. 1's A_l A_m A_n^* and A_l (h_R * A_m A_n^*) transform
+    alike).  The dispersion is diagonal and equal on the pair, so it commutes
+    with T: the MPA in the mixed basis, from T A0, gives T times the MPA in
+    the original basis, with Raman and self-steepening."""
+    p = I.grin_problem("cx", N=3, Nt=256, dt=20e-15, kind="gaussian", fwhm=300e-15, energy=20e-9,
+                       L=4e-3, dz=1e-4, M=8, tol=1e-12, seed=2, fR=0.18, s_from="gh")
+    beta = p.beta.copy()
+    beta[2] = beta[1]  # exactly degenerate pair
+    r = 1.0 / math.sqrt(2.0)
+    T = np.array([[1, 0, 0], [0, r, 1j * r], [0, r, -1j * r]], dtype=complex)
+    np.testing.assert_allclose(T @ T.conj().T, np.eye(3), atol=1e-15)
+    Sp = np.einsum("pa,lb,mc,nd,abcd->plmn", T, T.conj(), T.conj(), T, p.SK)
+    assert np.abs(Sp - Sp.transpose(0, 1, 3, 2)).max() > 1e-3 * np.abs(Sp).max()  # m <-> n broken
+    fib = O.Fiber(beta, p.SK, p.SR, p.fR, p.hR, p.dt, p.lam0, p.n2, True)
+    fibp = O.Fiber(beta, Sp, Sp, p.fR, p.hR, p.dt, p.lam0, p.n2, True)
+    A, st = O.mpa_propagate(fib, p.A0, p.L, p.dz, p.M, 0.0, fixed_iters=5)
+    Ap, stp = O.mpa_propagate(fibp, T @ p.A0, p.L, p.dz, p.M, 0.0, fixed_iters=5)
+    assert st["status"] == stp["status"] == 0
+    assert rel(A, p.A0) > 1e-2  # the nonlinearity did something
+    assert rel(Ap, T @ A) < 1e-11

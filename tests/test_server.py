@@ -165,3 +165,33 @@ def test_cancel_a_queued_request():
     assert rc == B.E_CANCELLED
     srv.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("slots", ["16", "1"])
+def test_many_tensor_core_requests_in_flight(slots, monkeypatch):
+    """Forty requests, 32 in flight, on two contexts whose contraction runs on
+    the tensor cores (10 and 15 modes, MIXED_BF16) and two that run it on the
+    CUDA cores (3 and 6 modes), packed and unpacked: every request ends
+    within the deadline (tensor-core work never shares the device with other
+    work of the library) and a sample equals the same request run alone."""
+    monkeypatch.setenv("GMMNLSE_PACK_SLOTS", slots)
+    specs = [(10, 1024, 21), (15, 1024, 22), (3, 2048, 23), (6, 1024, 24)]
+    ctxs = [_ctx(N, Nt, "bf16", seed) for N, Nt, seed in specs]
+    rng = np.random.default_rng(9)
+    reqs = []
+    for k in range(40):
+        prob, ctx = ctxs[k % 4]
+        dz = prob.dz * (1.0 + 0.3 * rng.uniform())
+        steps = prob.M * int(rng.integers(2, 9)) + (3 if k % 7 == 0 else 0)  # a few with a remainder
+        reqs.append((prob, ctx, prob.A0 * (1.0 + 0.2 * rng.standard_normal()), steps * dz, dz))
+    srv = B.Server(hbm_budget=8 << 30, max_inflight=32)
+    tickets = [srv.submit(ctx, A0, L, dz, prob.M, 1e-9) for prob, ctx, A0, L, dz in reqs]
+    res = _wait(srv, tickets, [(p.N, p.Nt) for p, *_ in reqs], timeout=240)
+    srv.close()
+    assert all(res[t][0] == B.OK for t in tickets)
+    for t, (prob, ctx, A0, L, dz) in list(zip(tickets, reqs))[::5]:
+        ref = ctx.propagate(A0, L, dz, prob.M, 1e-9)[0]
+        a = res[t][1]
+        assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < 1e-3
+    for _, ctx in ctxs:
+        ctx.close()
