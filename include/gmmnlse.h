@@ -138,6 +138,30 @@ typedef struct gmmnlse_server gmmnlse_server;
 int gmmnlse_create(const gmmnlse_params* prm, const double* beta, const double* SK,
                    const double* SR, double fR, const double* hR, gmmnlse_ctx** out);
 
+/*
+ * gmmnlse_create_general -- the same, with complex coupling tensors and no
+ * symmetry assumed: Eq. 1 as written, without the single-polarization,
+ * real-profile simplification of Eq. 2 (complex or vector mode fields, a
+ * complex mode basis such as circularly polarized or orbital-angular-
+ * momentum modes).
+ *
+ *   SK    [N][N][N][N][2] S^K_plmn as (re, im) pairs [1/m^2].  Host.
+ *   SR    [N][N][N][N][2] S^R_plmn, or NULL (then S^R = S^K).  Host.
+ *   other arguments as for gmmnlse_create.
+ *
+ * The bracket is evaluated as sum_l A_l R_pl with the complex R_pl =
+ * sum_mn S_plmn A_m A_n^* formed from the N^2 real rows of the pair
+ * products (Re A_m A_n^* for m <= n, Im A_m A_n^* for m < n) and, with
+ * f_R > 0, their convolutions with h_R.  Precision GMMNLSE_FP64 or
+ * GMMNLSE_FP32 (the contraction on the CUDA cores) and N <= 32; otherwise
+ * GMMNLSE_E_UNSUPPORTED.  gmmnlse_set_gain_saturation (non-zero) and
+ * gmmnlse_propagate_noalloc return GMMNLSE_E_UNSUPPORTED on such a context;
+ * everything else (gmmnlse_propagate, the RK4IP comparator, the linear
+ * terms, the server) takes it as any other.
+ */
+int gmmnlse_create_general(const gmmnlse_params* prm, const double* beta, const double* SK,
+                           const double* SR, double fR, const double* hR, gmmnlse_ctx** out);
+
 /* Free a context and all its device memory.  NULL is accepted. */
 int gmmnlse_destroy(gmmnlse_ctx* ctx);
 

@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16
 
 # every function include/gmmnlse.h declares
 EXPORTS = [
-    "gmmnlse_create", "gmmnlse_destroy", "gmmnlse_propagate", "gmmnlse_strerror",
+    "gmmnlse_create", "gmmnlse_create_general", "gmmnlse_destroy", "gmmnlse_propagate", "gmmnlse_strerror",
     "gmmnlse_last_error", "gmmnlse_request_bytes", "gmmnlse_server_create",
     "gmmnlse_submit", "gmmnlse_poll", "gmmnlse_server_destroy", "gmmnlse_profile",
     "gmmnlse_propagate_noalloc", "gmmnlse_choose_m",
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
     dp = C.POINTER(C.c_double)
     vp = C.c_void_p
     lib.gmmnlse_create.argtypes = [C.POINTER(Params), vp, vp, vp, C.c_double, vp, C.POINTER(vp)]
+    lib.gmmnlse_create_general.argtypes = [C.POINTER(Params), vp, vp, vp, C.c_double, vp, C.POINTER(vp)]
     lib.gmmnlse_destroy.argtypes = [vp]
     lib.gmmnlse_propagate.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                       C.POINTER(Stats)]
@@ -152,7 +153,8 @@ def overlap_tensor(F, dA, device=0):
 
 
 class Context:
-    """A fiber uploaded to the device (gmmnlse_create)."""
+    """A fiber uploaded to the device (gmmnlse_create; gmmnlse_create_general
+    when S^K or S^R is complex)."""
 
     def __init__(self, N, Nt, dt, lambda0, n2, beta, SK, SR=None, fR=0.0, hR=None,
                  self_steepening=True, precision="fp64", max_iter=0, fixed_iters=0,
@@ -161,18 +163,21 @@ class Context:
         self.N, self.Nt = int(N), int(Nt)
         self._keep = []
         self.beta = np.ascontiguousarray(beta, dtype=np.float64)
-        self.SK = np.ascontiguousarray(SK, dtype=np.float64)
-        self.SR = None if SR is None else np.ascontiguousarray(SR, dtype=np.float64)
+        general = np.iscomplexobj(SK) or (SR is not None and np.iscomplexobj(SR))
+        dt_s = np.complex128 if general else np.float64
+        self.SK = np.ascontiguousarray(SK, dtype=dt_s)
+        self.SR = None if SR is None else np.ascontiguousarray(SR, dtype=dt_s)
         self.hR = None if hR is None else np.ascontiguousarray(hR, dtype=np.float64)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.params = Params(self.N, self.Nt, float(dt), float(lambda0), float(n2),
                              1 if self_steepening else 0, prec, int(max_iter), int(fixed_iters),
                              int(device), stream, 1 if io_device else 0)
         h = C.c_void_p()
-        st = self.lib.gmmnlse_create(C.byref(self.params), _ptr(self.beta), _ptr(self.SK),
-                                     _ptr(self.SR), float(fR), _ptr(self.hR), C.byref(h))
+        create = self.lib.gmmnlse_create_general if general else self.lib.gmmnlse_create
+        st = create(C.byref(self.params), _ptr(self.beta), _ptr(self.SK), _ptr(self.SR), float(fR),
+                    _ptr(self.hR), C.byref(h))
         if st != OK:
-            raise GmmnlseError(st, "gmmnlse_create")
+            raise GmmnlseError(st, "gmmnlse_create_general" if general else "gmmnlse_create")
         self.handle = h
 
     @classmethod

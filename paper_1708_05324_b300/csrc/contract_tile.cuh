@@ -16,15 +16,18 @@
 //     block) and from Y = h_R * U ([M+1][K][n]):
 //     MODE 0: V = U;  1: V = (1 - fR) U + fR Y;  2: V = [U; Y]
 //     (U_mm = |A_m|^2, U_mn = 2 Re(A_m A_n^*));
-//   SRC 1 (second GEMM of the low-rank coupling), from the rows of
-//     Z = W U and Y' = h_R * Z ([M+1][r][n]):  MODE 0: V = Z;
-//     1: V = (1 - fR) Z + fR Y'.
+//   SRC 1 (second GEMM of the low-rank coupling; the general coupling),
+//     from the rows of Z and Y' = h_R * Z ([slices][cnt][n]):  MODE 0:
+//     V = Z;  1: V = (1 - fR) Z + fR Y';  2: V = [Z; Y'] (KK = 2 cnt).
 // The result goes:
 //   OUT 0: to the l-sum NL_p = sum_l A_l R_(p,l), formed per (point, p) in a
 //     fixed order from the accumulators staged in shared memory (rows
 //     ordered by diagonal l - p); NL written at the end;
 //   OUT 1 (first GEMM of the low-rank coupling): D rows stored as Z
-//     ([M+1][rows][n]).
+//     ([M+1][rows][n]);
+//   OUT 2 (general coupling): the rows are the real and imaginary parts of
+//     a complex R_pl for every (p, l), row 2 (p N + l) + {0, 1}, and
+//     NL_p = sum_l A_l R_pl, formed per (point, p) in increasing l.
 //
 // Gt is the coupling matrix transposed and zero-padded: [KKp][Pp], KKp a
 // multiple of KC and Pp a multiple of TR.
@@ -124,6 +127,8 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
       if (SRC == 0) {
         const bool need = ok && (MODE == 1 || (MODE == 2 && k >= K));
         yreg[i] = need ? yq[(size_t)(MODE == 2 ? k - K : k) * n] : (R)0;
+      } else if (MODE == 2) {
+        zreg[i] = ok ? (k < a.cnt ? zq[(size_t)k * n] : yq[(size_t)(k - a.cnt) * n]) : (R)0;
       } else {
         zreg[i] = ok ? zq[(size_t)k * n] : (R)0;
         yreg[i] = (ok && MODE == 1) ? yq[(size_t)k * n] : (R)0;
@@ -241,6 +246,43 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
         }
         __syncthreads();
       }
+    } else if (OUT == 2) {
+      // complex l-sum: row rr = 2 (p N + l) + c holds Re (c = 0) or Im
+      // (c = 1) of R_pl; 32 rows at a time through shared memory, each
+      // (point, p) item adding the rows of its p in increasing order
+      R* Ds = Vs;  // [32][TP]
+      static_assert(KC * (TP + TR) >= 32 * TP, "the row chunk fits in the V and G chunks");
+#pragma unroll
+      for (int c = 0; c < TR / 32; ++c) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int i = 0; i < TM; ++i) Ds[(tx + 16 * h) * TP + ty * TM + i] = acc[i][2 * c + h];
+        __syncthreads();
+        const int r0 = rb + 32 * c;
+        if (r0 < a.rows) {
+          const int r1 = min(r0 + 32, a.rows) - 1;
+          for (int item = tid; item < N * TP; item += 256) {
+            const int p = item / TP, qq = item - p * TP;
+            const int lo = max(r0, 2 * p * N), hi = min(r1, 2 * p * N + 2 * N - 1);
+            if (lo > hi) continue;
+            cplx<R> v = Ns[item];
+            for (int rr = lo; rr <= hi; ++rr) {
+              const R x = Ds[(rr - r0) * TP + qq];
+              const cplx<R> al = As[((rr >> 1) - p * N) * TP + qq];
+              if (rr & 1) {  // i Im(R_pl) A_l
+                v.x -= al.y * x;
+                v.y += al.x * x;
+              } else {
+                v.x += al.x * x;
+                v.y += al.y * x;
+              }
+            }
+            Ns[item] = v;
+          }
+        }
+        __syncthreads();
+      }
     } else {
       // rows of Z: [M+1][cnt][n]
       bool vec = false;
@@ -279,7 +321,7 @@ __global__ void __launch_bounds__(256) k_contract_tile(Geo g, TileArgs<R> a, con
       }
     }
   }
-  if (OUT != 0) return;
+  if (OUT == 1) return;
   __syncthreads();
   for (int i = tid; i < N * TP; i += 256) {
     const int p = i / TP, qq = i - p * TP;

@@ -111,6 +111,14 @@ struct gmmnlse_ctx {
   // columns, W = X^T G [r][K]; Z = W U, Y' = h_R * Z, R = X V'
   bool lr = false;
   int r = 0;
+  // general coupling (complex S^K, S^R with no symmetry; Eq. 1 without the
+  // real S of Eq. 2): the N^2 real rows U_k of the pair products, Re(A_m
+  // A_n^*) for m <= n then Im(A_m A_n^*) for m < n (gpairs: (m, n), n + N
+  // for an imaginary row), rows of Gt the real and imaginary parts of R_pl
+  // for every (p, l): row 2 (p N + l) + {0, 1}
+  bool general = false;
+  int gK = 0;                    // N^2
+  int2* gpairs = nullptr;        // [N^2]
   int eW = 0;                    // max_s sum_k |W[s][k]| < 2^eW (|Z| < 2^eW max |U|)
   void* Wt = nullptr;            // [KKt][rP1] R: W^T, CUDA-core GEMM 1 (rows r padded to rP1)
   void* Xt = nullptr;            // [rK2][Pt] R: X^T, CUDA-core GEMM 2 (K = r padded to rK2)

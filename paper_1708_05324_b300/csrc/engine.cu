@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -163,6 +164,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->rows);
   cudaFree(c->rows_t);
   cudaFree(c->pairs);
+  cudaFree(c->gpairs);
   cudaFree(c->Ghi);
   cudaFree(c->Wt);
   cudaFree(c->Xt);
@@ -375,8 +377,10 @@ static int compute_H(gmmnlse_ctx* c, const double* hR) {
   return GMMNLSE_OK;
 }
 
-extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, const double* SK,
-                              const double* SR, double fR, const double* hR, gmmnlse_ctx** out) {
+// cplx: SK and SR are complex, interleaved (re, im) [N][N][N][N][2], with no
+// symmetry assumed (the general coupling); else real and symmetric (Eq. 2).
+static int create_ctx(const gmmnlse_params* prm, const double* beta, const double* SK, const double* SR, double fR,
+                      const double* hR, bool cplx, gmmnlse_ctx** out) {
   if (!prm || !beta || !SK || !out) return GMMNLSE_E_INVALID;
   *out = nullptr;
   const int N = prm->N, n = prm->Nt;
@@ -387,11 +391,17 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   if (fR > 0 && !hR) return GMMNLSE_E_INVALID;
   if (prm->precision < GMMNLSE_FP64 || prm->precision > GMMNLSE_MIXED_TF32) return GMMNLSE_E_INVALID;
   if (prm->max_iter < 0 || prm->fixed_iters < 0) return GMMNLSE_E_INVALID;
-  const size_t S4 = (size_t)N * N * N * N;
-  if (!finite_all(beta, (size_t)N * n) || !finite_all(SK, S4) || (SR && !finite_all(SR, S4)) ||
+  const size_t S4 = (size_t)N * N * N * N, SW = cplx ? 2 * S4 : S4;
+  if (!finite_all(beta, (size_t)N * n) || !finite_all(SK, SW) || (SR && !finite_all(SR, SW)) ||
       (hR && !finite_all(hR, n)))
     return GMMNLSE_E_INVALID;
-  if (!symmetric_enough(SK, N) || (SR && !symmetric_enough(SR, N))) return GMMNLSE_E_UNSUPPORTED;
+  if (cplx) {
+    // the general coupling: FP64 or FP32 on the CUDA cores, up to 32 modes
+    if (N > 32) return GMMNLSE_E_UNSUPPORTED;
+    if (prm->precision != GMMNLSE_FP64 && prm->precision != GMMNLSE_FP32) return GMMNLSE_E_UNSUPPORTED;
+  } else if (!symmetric_enough(SK, N) || (SR && !symmetric_enough(SR, N))) {
+    return GMMNLSE_E_UNSUPPORTED;
+  }
   const bool fp64 = prm->precision == GMMNLSE_FP64;
   int rc = set_device(prm->device);
   if (rc) return rc;
@@ -409,9 +419,15 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   c->gamma0 = prm->n2 * c->omega0 / C_LIGHT;
   c->K = N * (N + 1) / 2;
   c->P = c->K;
-  bool same = (SR == nullptr) || (SR == SK) || std::memcmp(SR, SK, S4 * sizeof(double)) == 0;
+  bool same = (SR == nullptr) || (SR == SK) || std::memcmp(SR, SK, SW * sizeof(double)) == 0;
   c->raman_mode = (fR == 0.0) ? 0 : (same ? 1 : 2);
   c->KK = (c->raman_mode == 2) ? 2 * c->K : c->K;
+  if (cplx) {
+    c->general = true;
+    c->gK = N * N;
+    c->KK = (c->raman_mode == 2) ? 2 * c->gK : c->gK;
+    c->P = 2 * c->gK;
+  }
 
   // pair / row enumeration (m <= n), reduced coupling matrix G [P][KK]
   std::vector<int2> pairs;
@@ -421,7 +437,45 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   auto S_at = [&](const double* S, int p, int l, int m, int q) {
     return S[(((size_t)p * N + l) * N + m) * N + q];
   };
-  for (int r = 0; r < c->P; ++r) {
+  // general coupling: sum_mn S_plmn A_m A_n^* over the real rows U of the
+  // pair products (Re A_m A_n^* for m <= n, then Im A_m A_n^* for m < n):
+  //   m = n:  S_plmm |A_m|^2
+  //   m < n:  (S_plmn + S_plnm) Re(A_m A_n^*) + i (S_plmn - S_plnm) Im(A_m A_n^*)
+  // (A_n A_m^* is the conjugate of A_m A_n^*); the complex coefficient of
+  // row k gives Gd rows 2 (p N + l) (real part of R_pl) and + 1 (imaginary)
+  std::vector<int2> gpairs;
+  if (cplx) {
+    for (int m = 0; m < N; ++m)
+      for (int q = m; q < N; ++q) gpairs.push_back(make_int2(m, q));
+    for (int m = 0; m < N; ++m)
+      for (int q = m + 1; q < N; ++q) gpairs.push_back(make_int2(m, q + N));
+    auto Sc = [&](const double* S, int p, int l, int m, int q) {
+      const size_t i = 2 * ((((size_t)p * N + l) * N + m) * N + q);
+      return std::complex<double>(S[i], S[i + 1]);
+    };
+    auto fill = [&](const double* S, double w, int col0) {
+      for (int p = 0; p < N; ++p)
+        for (int l = 0; l < N; ++l) {
+          const size_t r = 2 * ((size_t)p * N + l);
+          for (int k = 0; k < c->gK; ++k) {
+            const int m = gpairs[k].x, q = gpairs[k].y;
+            std::complex<double> coef;
+            if (q >= N) coef = std::complex<double>(0.0, 1.0) * (Sc(S, p, l, m, q - N) - Sc(S, p, l, q - N, m));
+            else if (m == q) coef = Sc(S, p, l, m, m);
+            else coef = Sc(S, p, l, m, q) + Sc(S, p, l, q, m);
+            Gd[r * c->KK + col0 + k] = w * coef.real();
+            Gd[(r + 1) * c->KK + col0 + k] = w * coef.imag();
+          }
+        }
+    };
+    if (c->raman_mode == 2) {
+      fill(SK, 1.0 - fR, 0);
+      fill(SR, fR, c->gK);
+    } else {
+      fill(SK, 1.0, 0);
+    }
+  }
+  for (int r = 0; r < c->P && !cplx; ++r) {
     const int p = pairs[r].x, l = pairs[r].y;
     for (int k = 0; k < c->K; ++k) {
       const int m = pairs[k].x, q = pairs[k].y;
@@ -438,12 +492,13 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   c->beta0.resize(N);
   for (int p = 0; p < N; ++p) {
     c->beta0[p] = beta[(size_t)p * n];
-    c->s_max = std::max(c->s_max, S_at(SK, p, p, p, p));
+    const size_t pp = (((size_t)p * N + p) * N + p) * N + p;
+    c->s_max = std::max(c->s_max, cplx ? std::hypot(SK[2 * pp], SK[2 * pp + 1]) : SK[pp]);
   }
   // the reduced S^R [P][K] kept on the host for the gain's saturation term
   // (uploaded when gmmnlse_set_gain_saturation switches it on)
-  c->GR_host.resize((size_t)c->P * c->K);
-  for (int r = 0; r < c->P; ++r)
+  if (!cplx) c->GR_host.resize((size_t)c->P * c->K);
+  for (int r = 0; r < c->P && !cplx; ++r)
     for (int k = 0; k < c->K; ++k)
       c->GR_host[(size_t)r * c->K + k] =
           S_at(SR ? SR : SK, pairs[r].x, pairs[r].y, pairs[k].x, pairs[k].y);
@@ -477,7 +532,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   const int KC = TileCfg<float>::KC, TR = TileCfg<float>::TR;
   static_assert(TileCfg<float>::KC == TileCfg<double>::KC && TileCfg<float>::TR == TileCfg<double>::TR,
                 "one padding for both precisions");
-  if (N > 8) {
+  if (N > 8 || c->general) {
     c->KKt = (c->KK + KC - 1) / KC * KC;
     c->Pt = (c->P + TR - 1) / TR * TR;
   }
@@ -490,7 +545,7 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   // kernel, which stages the A of at most U_FIT_N modes: more modes keep the
   // dense coupling)
   const bool lr_fits = !(c->tc && !c->tf32 && N > U_FIT_N);
-  if (N > 8 && c->raman_mode != 2 && lr_fits && !(dense_env && dense_env[0] == '1')) {
+  if (N > 8 && !c->general && c->raman_mode != 2 && lr_fits && !(dense_env && dense_env[0] == '1')) {
     // the dropped part of the coupling (columns below tol x the largest)
     // stays under the rounding of the working precision's contraction:
     // 1e-12 for FP64; 1e-9 for FP32 and the mixed precisions, whose FP32
@@ -569,13 +624,19 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   CKC(cudaMemcpy(c->tw64h, twh.data(), twh.size() * sizeof(double2), cudaMemcpyHostToDevice));
   CKC(cudaMalloc(&c->tw32, tw32.size() * sizeof(float2)));
   CKC(cudaMemcpy(c->tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  CKC(cudaMalloc(&c->rows, c->P * sizeof(int2)));
-  CKC(cudaMemcpy(c->rows, pairs.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
+  if (!c->general) {
+    CKC(cudaMalloc(&c->rows, c->P * sizeof(int2)));
+    CKC(cudaMemcpy(c->rows, pairs.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
+  } else {
+    CKC(cudaMalloc(&c->gpairs, c->gK * sizeof(int2)));
+    CKC(cudaMemcpy(c->gpairs, gpairs.data(), c->gK * sizeof(int2), cudaMemcpyHostToDevice));
+    Gt_rows = Gd;  // rows in their own order (the complex l-sum needs no diagonal order)
+  }
   CKC(cudaMalloc(&c->pairs, c->K * sizeof(int2)));
   CKC(cudaMemcpy(c->pairs, pairs.data(), c->K * sizeof(int2), cudaMemcpyHostToDevice));
   // CUDA-core tiles take their rows by diagonals (p, p + d): G and X rows
   // permuted to that order, with the (p, l) table to match
-  if (N > 8) {
+  if (N > 8 && !c->general) {
     std::vector<int2> diag;
     for (int d = 0; d < N; ++d)
       for (int p = 0; p + d < N; ++p) diag.push_back(make_int2(p, p + d));
@@ -630,6 +691,16 @@ extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, con
   return GMMNLSE_OK;
 }
 
+extern "C" int gmmnlse_create(const gmmnlse_params* prm, const double* beta, const double* SK,
+                              const double* SR, double fR, const double* hR, gmmnlse_ctx** out) {
+  return create_ctx(prm, beta, SK, SR, fR, hR, false, out);
+}
+
+extern "C" int gmmnlse_create_general(const gmmnlse_params* prm, const double* beta, const double* SK,
+                                      const double* SR, double fR, const double* hR, gmmnlse_ctx** out) {
+  return create_ctx(prm, beta, SK, SR, fR, hR, true, out);
+}
+
 extern "C" int gmmnlse_destroy(gmmnlse_ctx* c) {
   if (!c) return GMMNLSE_OK;
   cudaSetDevice(c->prm.device);
@@ -650,8 +721,10 @@ static size_t job_bytes(const gmmnlse_ctx* c, int M) {
   if (!c->fp64) b += Nn * cs;                    // psiR
   b += (size_t)M * Nn * cs;                      // dpsi
   b += 4 * (size_t)(M + 1) * Nn * cs;            // A, NL, I, E
-  if (c->raman_mode) b += (size_t)(M + 1) * c->K * c->n * rs;  // Y = h_R * U
+  const size_t vrows = c->general ? c->gK : c->K;
+  if (c->raman_mode) b += (size_t)(M + 1) * vrows * c->n * rs;  // Y = h_R * U
   if (c->lr) b += (size_t)(M + 1) * c->r * c->n * rs;          // Z = W U
+  if (c->general) b += (size_t)(M + 1) * c->gK * c->n * rs;    // the pair-product rows U
   b += 2 * Nn * 16 * 2;                          // EM64, io
   b += sizeof(LoopState) + 64 + sizeof(double2) * TRAPZ_MAX_BLOCKS;
   b += (size_t)(M + 1) * (c->K + c->P) * sizeof(double);  // saturation: Ubar, Rs
@@ -825,8 +898,9 @@ int gm_job_create_slots(gmmnlse_ctx* c, int M, int slots, gm_job** out) {
   al(&jb->NL, S1 * Nn * cs);
   al(&jb->I, S1 * Nn * cs);
   al(&jb->E, S1 * Nn * cs);
-  if (c->raman_mode) al(&jb->V, S1 * c->K * c->n * rs);
+  if (c->raman_mode) al(&jb->V, S1 * (c->general ? c->gK : c->K) * c->n * rs);
   if (c->lr) al(&jb->Z, S1 * c->r * c->n * rs);
+  if (c->general) al(&jb->Z, S1 * c->gK * c->n * rs);
   al((void**)&jb->EM64, B * 2 * Nn * 16);
   al((void**)&jb->io, 2 * Nn * 16);
   al((void**)&jb->flag, sizeof(int));
@@ -1094,6 +1168,7 @@ extern "C" int gmmnlse_set_gain(gmmnlse_ctx* c, const double* g) {
 
 extern "C" int gmmnlse_set_gain_saturation(gmmnlse_ctx* c, double sat) {
   if (!c || !std::isfinite(sat) || sat < 0.0) return GMMNLSE_E_INVALID;
+  if (c->general && sat != 0.0) return GMMNLSE_E_UNSUPPORTED;  // its rows use the real reduced S^R
   std::lock_guard<std::mutex> lk(c->mu);
   auto gate = gm_gate_device(c->prm.device);
   int rc = set_device(c->prm.device);

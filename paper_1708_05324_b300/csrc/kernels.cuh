@@ -164,6 +164,34 @@ __device__ __forceinline__ R pair_product(const cplx<R>* __restrict__ a, int n, 
 }
 
 // ---------------------------------------------------------------------------
+// K2 of the general coupling: the N^2 real rows of the pair products,
+// U_k = Re(A_m A_n^*) for the pairs m <= n and Im(A_m A_n^*) for m < n
+// (gpairs[k] = (m, n), n + N for an imaginary row), to Ug [slices][N^2][n].
+// grid (ceil(n / 256), slices)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_gen_pairs(Geo g, const cplx<R>* __restrict__ A, R* __restrict__ Ug,
+                                                   const int2* __restrict__ gpairs, const LoopState* __restrict__ ls) {
+  pdl_enter();
+  int b, j;
+  slot_of(g, blockIdx.y, b, j);
+  if (slice_skipped(ls + b, j)) return;
+  const int n = g.n, N = g.N, NN = N * N;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const cplx<R>* a = A + (size_t)blockIdx.y * N * n;
+  R* u = Ug + (size_t)blockIdx.y * NN * n + t;
+  for (int k = 0; k < NN; ++k) {
+    const int2 mn = gpairs[k];
+    const bool im = mn.y >= N;
+    const cplx<R> am = __ldcg(a + (size_t)mn.x * n + t);
+    const cplx<R> an = __ldcg(a + (size_t)(im ? mn.y - N : mn.y) * n + t);
+    // A_m A_n^* = (am.x an.x + am.y an.y) + i (am.y an.x - am.x an.y)
+    u[(size_t)k * n] = im ? am.y * an.x - am.x * an.y : am.x * an.x + am.y * an.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K2: pair products and the Raman convolution Y_k = h_R * U_k for two rows
 // at once (U_k1 + i U_k2 is transformed, multiplied by H = (dt/n) DFT(h_R),
 // and transformed back; h_R is real so the real and imaginary parts stay

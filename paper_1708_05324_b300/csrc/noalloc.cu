@@ -288,6 +288,7 @@ extern "C" int gmmnlse_propagate_noalloc(gmmnlse_ctx* c, const double* A0, doubl
   if (!c || !A0 || !Aout) return GMMNLSE_E_INVALID;
   if (c->fp64 && c->n > 8192) return GMMNLSE_E_UNSUPPORTED;  // needs the cluster transforms
   if (c->Q || c->gain || c->sat != 0.0) return GMMNLSE_E_UNSUPPORTED;  // Sec. IV terms: not on this path
+  if (c->general) return GMMNLSE_E_UNSUPPORTED;  // complex coupling: not on this path
   long nf;
   int mr;
   int rc = gm_schedule(L, dz, M, &nf, &mr);

@@ -60,7 +60,7 @@ static void with_long_step(const gmmnlse_ctx* c, F&& f) {
 template <typename R>
 static int long_step_grid_impl(gm_job* jb) {
   const gmmnlse_ctx* c = jb->ctx;
-  if (persist_disabled() || c->N > 8 || c->tc || c->lr || c->Q || c->gain || c->sat != 0.0 || c->n < 2048 || c->n > 8192) return 0;
+  if (persist_disabled() || c->N > 8 || c->tc || c->lr || c->general || c->Q || c->gain || c->sat != 0.0 || c->n < 2048 || c->n > 8192) return 0;
   const int threads = c->n / 16;
   const size_t smem = fft_smem<R>(c->n);
   int sms = 0, per_sm = 0;

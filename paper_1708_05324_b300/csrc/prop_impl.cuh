@@ -98,6 +98,9 @@ static int setup_device(int dev) {
   CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 0, 1>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 1, 0>, A, sm));
   CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 1, 0>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 0, 1, 2>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 1, 1, 2>, A, sm));
+  CK(cudaFuncSetAttribute(k_contract_tile<R, 2, 1, 2>, A, sm));
   if constexpr (std::is_same<R, float>::value) {
     CK(cudaFuncSetAttribute(k_raman_vpack<16, 0>, A, sm));
     CK(cudaFuncSetAttribute(k_raman_vpack<32, 0>, A, sm));
@@ -369,11 +372,14 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
 }
 
 template <typename R>
-static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
+static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s, int cnt = 0) {
   gmmnlse_ctx* c = jb->ctx;
-  const int n = c->n, pp = (c->r + 1) / 2;
+  // rows h_R * Z of Z [slices][rows][n] (cnt > 0: the general coupling's
+  // pair-product rows) to V
+  const int rows = cnt > 0 ? cnt : c->r;
+  const int n = c->n, pp = (rows + 1) / 2;
   if constexpr (std::is_same<R, float>::value) {
-    if (c->tc && !c->tf32) {
+    if (c->tc && !c->tf32 && cnt == 0) {
       // 16-bit operands: K2 writes GEMM 2's V' operand itself (no Y', no pack)
       const int ept = fft_ept<float>(n, pp * slices(g));
       const int npts_total = (jb->Mcap + 1) * n * jb->slots;
@@ -394,7 +400,7 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
   }
   auto one = [&](auto kern, int ept) {
     pdl_launch(kern, dim3(pp, slices(g)), dim3(n / ept), fft_smem<R>(n), s, g, (const cplx<R>*)jb->A, (R*)jb->V,
-               (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)jb->Z, c->r,
+               (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs, (const R*)jb->Z, rows,
                (const LoopState*)jb->ls);
   };
   const int S = split_for<R>(pp * slices(g), n);
@@ -402,7 +408,7 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s) {
     auto cl = [&](auto kern) {
       pdl_launch_cl(kern, dim3(S * pp, slices(g)), dim3(n / S / 16), fft_cluster_smem<R>(n, S), s, S, g,
                     (const cplx<R>*)jb->A, (R*)jb->V, (const cplx<R>*)c->H, twid<R>(c), (const int2*)c->pairs,
-                    (const R*)jb->Z, c->r, (const LoopState*)jb->ls);
+                    (const R*)jb->Z, rows, (const LoopState*)jb->ls);
     };
     if (S == 2) cl(k_pairs_raman_cl<R, 16, 2, 1>);
     else cl(k_pairs_raman_cl<R, 16, 4, 1>);
@@ -468,6 +474,38 @@ static void launch_lr_r(gm_job* jb, const Geo& g, cudaStream_t s) {
   else go(k_contract_tile<R, 0, 1, 0>);
 }
 
+// The general coupling (complex S^K, S^R; Eq. 1 without Eq. 2's real S):
+// the N^2 real pair-product rows U to Z, their Raman convolution to V, and
+// the CUDA-core GEMM R = G [U; h_R * U] with the complex l-sum
+// NL_p = sum_l A_l R_pl.
+template <typename R>
+static void launch_gen(gm_job* jb, const Geo& g, cudaStream_t s) {
+  gmmnlse_ctx* c = jb->ctx;
+  const int n = c->n;
+  pdl_launch(k_gen_pairs<R>, dim3((n + 255) / 256, slices(g)), dim3(256), 0, s, g, (const cplx<R>*)jb->A,
+             (R*)jb->Z, (const int2*)c->gpairs, (const LoopState*)jb->ls);
+  if (c->raman_mode) launch_lr_raman<R>(jb, g, s, c->gK);
+  TileArgs<R> a = {};
+  a.A = (const cplx<R>*)jb->A;
+  a.Ys = (const R*)jb->V;
+  a.Zs = (const R*)jb->Z;
+  a.Gt = (const R*)c->Gt;
+  a.KK = c->KK;
+  a.KKp = c->KKt;
+  a.Pp = c->Pt;
+  a.rows = c->P;
+  a.cnt = c->gK;
+  a.NL = (cplx<R>*)jb->NL;
+  const size_t pts = (size_t)slices(g) * n;
+  const dim3 grid((unsigned)((pts + TileCfg<R>::TP - 1) / TileCfg<R>::TP));
+  auto go = [&](auto kern) {
+    pdl_launch(kern, grid, dim3(256), contract_tile_smem<R>(c->N), s, g, a, (const LoopState*)jb->ls);
+  };
+  if (c->raman_mode == 0) go(k_contract_tile<R, 0, 1, 2>);
+  else if (c->raman_mode == 1) go(k_contract_tile<R, 1, 1, 2>);
+  else go(k_contract_tile<R, 2, 1, 2>);
+}
+
 // The Sec. IV terms added to the integrand I (after K4): linear coupling
 // (with its longitudinal profile), gain and its saturation.  z0 of the
 // substeps: from the loop state's long-step count (use_step) or zoff.
@@ -516,7 +554,9 @@ static void launch_iteration(gm_job* jb, const Geo& g, cudaStream_t s, cudaGraph
   gmmnlse_ctx* c = jb->ctx;
   launch_k1<R>(jb, g, s);
   if (c->sat != 0.0) launch_saturation<R>(jb, g, s);
-  if (c->lr) {
+  if (c->general) {
+    launch_gen<R>(jb, g, s);
+  } else if (c->lr) {
     launch_lr_z<R>(jb, g, s);
     if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
     launch_lr_r<R>(jb, g, s);
@@ -1044,7 +1084,9 @@ static int rk4ip_impl(gm_job* jb, const double* A0, bool dev_io, double L, doubl
     for (int q = 1; q <= 4; ++q) {
       launch_k1<R>(jb, g, s);
       if (c->sat != 0.0) launch_saturation<R>(jb, g, s);
-      if (c->lr) {
+      if (c->general) {
+        launch_gen<R>(jb, g, s);
+      } else if (c->lr) {
         launch_lr_z<R>(jb, g, s);
         if (c->raman_mode) launch_lr_raman<R>(jb, g, s);
         launch_lr_r<R>(jb, g, s);
@@ -1124,6 +1166,11 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
   bytes[0] = M * Nn * 4 * cs;                     // psiR, dpsi, E -> A
   bytes[1] = c->raman_mode ? M * (Nn * cs + (double)c->K * c->n * rs) : 0.0;     // A -> Y
   bytes[2] = M * (double)c->n * (2 * c->N * cs + (c->raman_mode ? c->K * rs : 0.0));  // A, Y -> NL
+  if (c->general) {
+    // pair rows A -> Z, Raman on them (Z -> V); contraction A, Z, V -> NL
+    bytes[1] = c->raman_mode ? M * 2.0 * c->gK * c->n * rs : 0.0;
+    bytes[2] = M * (double)c->n * (3 * c->N * cs + (double)c->gK * rs * (c->raman_mode ? 3 : 2));
+  }
   if (c->lr) {
     // Raman on the rows of Z (Z -> Y'); contraction: A -> Z (GEMM 1), A, Z, Y' -> NL (GEMM 2)
     bytes[1] = c->raman_mode ? M * 2.0 * c->r * c->n * rs : 0.0;
@@ -1148,11 +1195,14 @@ static int profile_impl(gmmnlse_ctx* c, gm_job* jb, int M, int reps, double* ms,
       switch (k) {
         case 0: launch_k1<R>(jb, g, s); break;
         case 1:
-          if (c->lr) launch_lr_raman<R>(jb, g, s);
+          if (c->general) launch_lr_raman<R>(jb, g, s, c->gK);
+          else if (c->lr) launch_lr_raman<R>(jb, g, s);
           else launch_k2<R>(jb, g, s);
           break;
         case 2:
-          if (c->lr) {
+          if (c->general) {
+            launch_gen<R>(jb, g, s);
+          } else if (c->lr) {
             launch_lr_z<R>(jb, g, s);
             launch_lr_r<R>(jb, g, s);
           } else if (c->tc) {
