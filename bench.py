@@ -50,9 +50,11 @@ SEED = {"C4": 4, "C3": 3, "C2": 2}
 # the precision's error against the FP64 GPU path is measured on this prefix
 ERR_PREFIX = {"C4": (16 * 37.5e-6, "one long step (0.6 mm)"), "C3": (2e-3, "2 mm (8 long steps)"),
               "C2": (5e-3, "5 mm (20 long steps)")}
-# DRAM bytes per launch of the dominant kernel from one ncu capture (the
-# kernel unchanged since), keyed (workload, precision, kernel slot)
-TRAFFIC = {}
+# DRAM bytes of the dominant kernel slot per iteration from one ncu capture
+# (the kernels unchanged since), keyed (workload, precision, kernel slot):
+# the 42-mode MIXED_BF16 contraction is its two GEMM launches, 303.3 MB for
+# 17 live substeps, scaled to the profile's 16
+TRAFFIC = {("C4", "bf16", "contract"): 285.4e6}
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
 # nominal dense TF32 : BF16 tensor rate (1.1 : 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
@@ -360,6 +362,39 @@ def _oracle_rate(prob, sec_per_integrand, iters_per_long_step):
     return per_long_step / (sec_per_integrand * evals)
 
 
+_ONE_THREAD_CHILD = """
+import sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle as O
+z = np.load(sys.argv[2])
+fR, dt, lam0, n2, ss = z["scal"]
+fib = O.Fiber(z["beta"], z["SK"], z["SK"], fR, z["hR"], dt, lam0, n2, bool(ss))
+psi = O.freq_from_time(z["A0"])
+O.integrand(fib, psi, 0.0)
+t0 = time.perf_counter()
+O.integrand(fib, psi, 37.5e-6)
+print(time.perf_counter() - t0)
+"""
+
+
+def _one_thread_integrand_seconds(prob):
+    """Seconds per integrand evaluation on one host thread: timed in a child
+    process whose BLAS thread counts are set to 1 before numpy loads (the
+    inputs handed over in a temporary file)."""
+    import subprocess
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        f = os.path.join(d, "fiber.npz")
+        np.savez(f, beta=prob.beta, SK=prob.SK, hR=prob.hR, A0=prob.A0,
+                 scal=np.array([prob.fR, prob.dt, prob.lam0, prob.n2, float(prob.self_steepening)]))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        out = subprocess.run([sys.executable, "-c", _ONE_THREAD_CHILD, ROOT, f], env=env, capture_output=True,
+                             text=True, timeout=600, check=True)
+        return float(out.stdout.strip().splitlines()[-1])
+
+
 def cpu_baseline(seconds=15.0, iters_per_long_step=C4_ITERS_PER_LONG_STEP):
     """Oracle rate on the host cores on a bounded sample of the 42-mode
     workload: integrand evaluations at full size (N = 42, Nt = 2^13) with
@@ -373,9 +408,7 @@ def cpu_baseline(seconds=15.0, iters_per_long_step=C4_ITERS_PER_LONG_STEP):
     sec, count = _oracle_integrand_seconds(fib, psi, 64, seconds)
     rate = _oracle_rate(prob, sec, iters_per_long_step)
     try:
-        from threadpoolctl import threadpool_limits
-        with threadpool_limits(limits=1):
-            sec1, _ = _oracle_integrand_seconds(fib, psi, 1, 0.0)
+        sec1 = _one_thread_integrand_seconds(prob)
         one = {"value": _oracle_rate(prob, sec1, iters_per_long_step), "unit": METRIC, "cores": 1,
                "sec_per_integrand": sec1}
     except Exception as e:  # the figure is then missing, and says why
