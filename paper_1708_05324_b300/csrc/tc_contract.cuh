@@ -163,7 +163,12 @@ struct TcShape {
   static constexpr int CL = FU ? 1 : tc_cluster(NB);
   static constexpr int G_HALF = G_BYTES / CL;          // this CTA's rows of a chunk (hi or lo)
   static constexpr int UW = FU ? 8 : 0;                // U-producer warps
-  static constexpr int THREADS = 192 + 32 * UW;
+  // the l-sum epilogue of more than 24 modes runs on two warps per TMEM lane
+  // quarter, each forming NL_p for half of the modes (the registers of one
+  // point's 2N mode values and 2N accumulators would spill)
+  static constexpr bool ESPLIT = OUT == 0 && N > 24;
+  static constexpr int EW = ESPLIT ? 8 : 4;            // epilogue warps
+  static constexpr int THREADS = 64 + 32 * EW + 32 * UW;
   // A tile ([U_FIT_N][128] float2) and column table ([KKp] int2) of FU
   static constexpr int U_RESERVE = FU ? U_FIT_N * TC_PTS * 8 + U_FIT_KKP * 8 : 0;
   static constexpr int TPW = (OUT == 1 && !FU && 2 * 2 * (2 * V_BYTES + G_HALF) <= 200 * 1024) ? 2 : 1;
@@ -225,6 +230,61 @@ struct LSum {
   }
 };
 
+// The same for the accumulators of modes LO .. HI - 1 only (nl[p - LO]).
+template <int N, int R, int REND, int LO, int HI>
+struct LSumH {
+  __device__ __forceinline__ static void run(const float* v, const float2* a, float2* nl) {
+    if constexpr (R < REND && R < N * (N + 1) / 2) {
+      constexpr int p = RowPair<N>::p_of(R), l = RowPair<N>::l_of(R);
+      constexpr int i = R % 16;
+      if constexpr (p >= LO && p < HI) {
+        nl[p - LO].x += a[l].x * v[i];
+        nl[p - LO].y += a[l].y * v[i];
+      }
+      if constexpr (p != l && l >= LO && l < HI) {
+        nl[l - LO].x += a[p].x * v[i];
+        nl[l - LO].y += a[p].y * v[i];
+      }
+      LSumH<N, R + 1, REND, LO, HI>::run(v, a, nl);
+    }
+  }
+};
+
+// Whether any of rows R0 .. R0 + 15 adds to a mode in LO .. HI - 1.
+template <int N>
+__host__ __device__ constexpr bool rows_touch(int R0, int LO, int HI) {
+  for (int r = R0; r < R0 + 16 && r < N * (N + 1) / 2; ++r) {
+    const int p = RowPair<N>::p_of(r), l = RowPair<N>::l_of(r);
+    if ((p >= LO && p < HI) || (l >= LO && l < HI)) return true;
+  }
+  return false;
+}
+
+// Columns C .. NB-1 of an accumulator holding row block RB, for the modes
+// LO .. HI - 1 (column chunks that add to none of them are not read).
+template <int N, int NB, int RB, int C, int LO, int HI>
+struct DrainH {
+  __device__ __forceinline__ static void run(uint32_t taddr, const float2* a, float2* nl) {
+    constexpr int R0 = RB * NB + C;
+    if constexpr (C < NB && R0 < N * (N + 1) / 2) {
+      if constexpr (rows_touch<N>(R0, LO, HI)) {
+        float v[16];
+        tc::tmem_ld16(taddr + C, v);
+        LSumH<N, R0, R0 + 16, LO, HI>::run(v, a, nl);
+      }
+      DrainH<N, NB, RB, C + 16, LO, HI>::run(taddr, a, nl);
+    }
+  }
+};
+
+template <int N, int NB, int RB, int LO, int HI>
+__device__ __forceinline__ void drain_rb_h(int rb, uint32_t taddr, const float2* a, float2* nl) {
+  if constexpr (RB < TcShape<N, NB>::NRB) {
+    if (rb == RB) DrainH<N, NB, RB, 0, LO, HI>::run(taddr, a, nl);
+    else drain_rb_h<N, NB, RB + 1, LO, HI>(rb, taddr, a, nl);
+  }
+}
+
 // Columns C .. NB-1 of an accumulator holding row block RB.
 template <int N, int NB, int RB, int C>
 struct Drain {
@@ -280,7 +340,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], 4 * CL);  // (used in CTA 0) one arrival per epilogue warp of each CTA
+      tc::mbar_init(&acc_empty[b], S::EW * CL);  // (used in CTA 0) one arrival per epilogue warp of each CTA
     }
     tc::mbar_init(&never, 1);  // nothing arrives on it (the stall test hook)
     tc::fence_mbar_init();
@@ -561,9 +621,12 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
         }
       wi = wn;
     }
-  } else if (warp < 6) {
-    // ---------------- epilogue: warps 2..5, one point per thread ----------------
+  } else if (warp < 2 + S::EW) {
+    // ---------------- epilogue: warps 2..5 (with ESPLIT 2..9), one point per thread ----------------
     const int quarter = warp & 3;  // this warp may access TMEM lanes 32 quarter ..
+    // ESPLIT: warps 6..9 form NL for the upper half of the modes
+    constexpr int NH = S::ESPLIT ? (N + 1) / 2 : (N > 0 ? N : 1);
+    const int half = S::ESPLIT && warp >= 6 ? 1 : 0;
     const int row_in_tile = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     // FP16: D = 2^(eV + eG) R; folded into the mode values of the l-sum
@@ -576,15 +639,16 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
       const bool mine = live(tile_of(wi, 0));
       const int pt = tile_of(wi, 0) * TC_PTS + row_in_tile;
       const int j = pt / n, t = pt - j * n;
-      float2 av[NA], nl[NA];
+      float2 av[NA], nl[NH];
       if (OUT == 0 && mine) {
 #pragma unroll
         for (int l = 0; l < N; ++l) {
           av[l] = a.A[((size_t)j * N + l) * n + t];
           av[l].x *= inv;
           av[l].y *= inv;
-          nl[l] = make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int p = 0; p < NH; ++p) nl[p] = make_float2(0.f, 0.f);
       }
       for (int rb = 0; rb < nrb; ++rb, ++w) {
         const int acc = w % NBUF, use = w / NBUF;
@@ -615,7 +679,12 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
             }
           }
         } else if (mine) {
-          drain_rb<N, NB, 0>(rb, taddr, av, nl);
+          if constexpr (S::ESPLIT) {
+            if (half == 0) drain_rb_h<N, NB, 0, 0, NH>(rb, taddr, av, nl);
+            else drain_rb_h<N, NB, 0, NH, N>(rb, taddr, av, nl);
+          } else {
+            drain_rb<N, NB, 0>(rb, taddr, av, nl);
+          }
         }
         // this warp's reads of the accumulator are done: one arrival on
         // CTA 0's barrier
@@ -629,8 +698,10 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
       if (*stop) break;
       if (OUT == 0 && mine) {
         float2* out = a.NL + (size_t)j * N * n + t;
+        const int p0 = half * NH;
 #pragma unroll
-        for (int p = 0; p < N; ++p) out[(size_t)p * n] = nl[p];
+        for (int p = 0; p < NH; ++p)
+          if (p0 + p < N) out[(size_t)(p0 + p) * n] = nl[p];
       }
     }
   }
