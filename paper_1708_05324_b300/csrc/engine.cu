@@ -801,10 +801,15 @@ static int tc_map(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, int bo
   EncodeTiledFn enc;
   const int rc = tc_encoder(&enc);
   if (rc) return rc;
-  const int epc = tf32 ? 4 : 8;
-  const cuuint64_t dims[3] = {(cuuint64_t)epc, rows, (cuuint64_t)(KKp / epc)};
-  const cuuint64_t strides[2] = {16, rows * 16};
-  const cuuint32_t box[3] = {(cuuint32_t)epc, (cuuint32_t)box_rows, (cuuint32_t)(TC_KC / epc)};
+  // A K plane [rows][epc] is contiguous: it is described as rows of 256
+  // elements (32 points of 8 BF16/FP16 values, or 64 points of 4 TF32 ones),
+  // so that each row of the box is one 512- or 1024-byte transfer instead of
+  // a 16-byte one; the box lands in shared memory in the same [kq][point][epc]
+  // order.  rows is a multiple of 128.
+  const int epc = tf32 ? 4 : 8, esz = tf32 ? 4 : 2;
+  const cuuint64_t dims[3] = {256, rows * epc / 256, (cuuint64_t)(KKp / epc)};
+  const cuuint64_t strides[2] = {(cuuint64_t)(256 * esz), rows * 16};
+  const cuuint32_t box[3] = {256, (cuuint32_t)(box_rows * epc / 256), (cuuint32_t)(TC_KC / epc)};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                       : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
@@ -825,15 +830,19 @@ static int tc_map_rows(CUtensorMap* map, void* base, cuuint64_t rows, int KKp, i
   EncodeTiledFn enc;
   const int rc = tc_encoder(&enc);
   if (rc) return rc;
-  const int epc = tf32 ? 4 : 8;
+  // The K chunk of an 8-row group ([TC_KC/epc][8][epc], 512 bytes for 16-bit
+  // operands, 1024 for TF32) is contiguous: the map's rows are those chunks
+  // (256 elements), so each 8-row group of the box is one transfer; the box
+  // lands in shared memory as [group][kq][8][epc] as before.
+  const int epc = tf32 ? 4 : 8, esz = tf32 ? 4 : 2;
   const cuuint64_t kq = (cuuint64_t)(KKp / epc);
-  const cuuint64_t dims[4] = {(cuuint64_t)epc, 8, kq, rows / 8};
-  const cuuint64_t strides[3] = {16, 128, kq * 128};
-  const cuuint32_t box[4] = {(cuuint32_t)epc, 8, (cuuint32_t)(TC_KC / epc), (cuuint32_t)(NB / 8 / cl)};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const cuuint64_t dims[3] = {256, (cuuint64_t)(KKp / TC_KC), rows / 8};
+  const cuuint64_t strides[2] = {(cuuint64_t)(256 * esz), kq * 128};
+  const cuuint32_t box[3] = {256, 1, (cuuint32_t)(NB / 8 / cl)};
+  const cuuint32_t es[3] = {1, 1, 1};
   const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                       : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
-  const CUresult r = enc(map, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const CUresult r = enc(map, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {

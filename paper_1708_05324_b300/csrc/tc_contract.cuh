@@ -49,7 +49,12 @@
 // 128*16 bytes apart (LBO) and along the points 128 bytes (SBO).  The
 // coupling operand is stored row-grouped, [row/8][k/8][8][8]; a K chunk of
 // NB/CL rows is [NB/(8 CL)][4][8][8] in shared memory (LBO 128 bytes, SBO
-// 512), one contiguous box of the row-grouped layout.
+// 512), one contiguous box of the row-grouped layout.  The tensor maps give
+// both operands rows of 256 elements (512 contiguous bytes: 32 points of a
+// K plane of V, or the K chunk of one 8-row group of the coupling), so the
+// TMA moves each box in 512-byte pieces; with the 16-byte rows of the core
+// matrices as map rows, the copies ran at about 14 bytes per clock and SM
+// and held both GEMMs to about a third of the tensor-core rate.
 //
 // Every mbarrier wait is bounded in time (TcArgs::wait_ns); on a timeout the
 // kernel records an error in *err and every role stops issuing work.
@@ -424,23 +429,26 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
               // a tile past the end repeats the last one (its result is not stored)
               const int tile = min(tile_of(wi, h), ntiles - 1);
               unsigned char* sv = st + (size_t)h * 2 * S::V_BYTES;
+              // the operand map's rows are 256 elements: TC_PTS EPC / 256 of them per tile
+              const int vy = tile * (TC_PTS * S::EPC / 256);
               if (PAIR) {
-                tc::tma_load_3d_pair(sv, &mapVhi, 0, tile * TC_PTS, kq, fb);
-                tc::tma_load_3d_pair(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, fb);
+                tc::tma_load_3d_pair(sv, &mapVhi, 0, vy, kq, fb);
+                tc::tma_load_3d_pair(sv + S::V_BYTES, &mapVlo, 0, vy, kq, fb);
               } else {
-                tc::tma_load_3d(sv, &mapVhi, 0, tile * TC_PTS, kq, &full[s]);
-                tc::tma_load_3d(sv + S::V_BYTES, &mapVlo, 0, tile * TC_PTS, kq, &full[s]);
+                tc::tma_load_3d(sv, &mapVhi, 0, vy, kq, &full[s]);
+                tc::tma_load_3d(sv + S::V_BYTES, &mapVlo, 0, vy, kq, &full[s]);
               }
             }
             // this CTA's rows of the coupling chunk: 8-row groups g0 .. g0 + NB/(8 CL) - 1
             unsigned char* sg = st + (size_t)TPW * 2 * S::V_BYTES;
             const int g0 = rb * (NB / 8) + (int)rank * (NB / 8 / CL);
+            // (the coupling map's rows are whole K chunks of an 8-row group)
             if (PAIR) {
-              tc::tma_load_4d_pair(sg, &mapGhi, 0, 0, kq, g0, fb);
-              tc::tma_load_4d_pair(sg + S::G_HALF, &mapGlo, 0, 0, kq, g0, fb);
+              tc::tma_load_3d_pair(sg, &mapGhi, 0, kc, g0, fb);
+              tc::tma_load_3d_pair(sg + S::G_HALF, &mapGlo, 0, kc, g0, fb);
             } else {
-              tc::tma_load_4d(sg, &mapGhi, 0, 0, kq, g0, &full[s]);
-              tc::tma_load_4d(sg + S::G_HALF, &mapGlo, 0, 0, kq, g0, &full[s]);
+              tc::tma_load_3d(sg, &mapGhi, 0, kc, g0, &full[s]);
+              tc::tma_load_3d(sg + S::G_HALF, &mapGlo, 0, kc, g0, &full[s]);
             }
           }
       }
