@@ -924,7 +924,8 @@ int gm_job_create_slots(gmmnlse_ctx* c, int M, int slots, gm_job** out) {
     al((void**)&jb->Vlo, vb);
   }
   // the hi/lo operand starts at zero: with the low-rank coupling its padding
-  // columns are never written again (k_raman_vpack writes the r columns only)
+  // columns from 8 ceil(r/8) on are never written again (k_raman_vpack
+  // writes whole 8-column groups, the columns from r as zeros)
   if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vhi, 0, vb);
   if (c->tc && e == cudaSuccess) e = cudaMemset(jb->Vlo, 0, vb);
   // every slot starts empty (a packed launch skips it)

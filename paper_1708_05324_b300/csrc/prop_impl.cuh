@@ -383,8 +383,10 @@ static void launch_lr_raman(gm_job* jb, const Geo& g, cudaStream_t s, int cnt = 
       // 16-bit operands: K2 writes GEMM 2's V' operand itself (no Y', no pack)
       const int ept = fft_ept<float>(n, pp * slices(g));
       const int npts_total = (jb->Mcap + 1) * n * jb->slots;
+      // clusters of four blocks, one per 8-row group of Z (k_raman_vpack)
       auto vp = [&](auto kern) {
-        pdl_launch(kern, dim3(pp, slices(g)), dim3(n / ept), fft_smem<float>(n), s, g, (const float*)jb->Z, c->r,
+        pdl_launch_cl(kern, dim3(4 * ((c->r + 7) / 8), slices(g)), dim3(n / ept), fft_smem<float>(n), s, 4, g,
+                      (const float*)jb->Z, c->r,
                    (const float2*)c->Hv, (const float2*)twid<float>(c), npts_total, (void*)jb->Vhi, (void*)jb->Vlo,
                    c->eW, (const LoopState*)jb->ls);
       };

@@ -853,58 +853,78 @@ __global__ void __launch_bounds__(PACK_PTS * PACK_WARPS) k_pack_rows(
 }
 
 // Low-rank coupling with 16-bit operands (OP 0 BF16, 1 FP16) and Raman: K2
-// on the rows k1 = 2 blockIdx.x and k1 + 1 of Z, writing the operand of
-// GEMM 2 directly: V' = (1 - fR) Z + fR h_R * Z = F^-1{F{Z} Hv} with the
-// transfer function Hv = (1 - fR)/n + fR H, one complex transform pair for
-// the two real rows (as k_pairs_raman with SRC 1).  The forward transform's
-// first pass reads the two rows straight from global memory (every load of
-// the pass in flight at once), and the inverse transform's last pass writes
-// V' as hi + lo in the blocked layout [KKp/8][npts][8] (both rows' values of
-// a point in one 4-byte word each), so that neither Y' nor a separate pack
-// pass goes through HBM.  FP16 values are scaled by 2^(eV - eVoff) as in
-// k_pack_rows.  The padding columns r .. KKp - 1 (except column r of an odd
-// r, written here as 0) are zero from the workspace's creation.  grid
-// (ceil(r/2), M+1).
+// on the rows of Z, writing the operand of GEMM 2 directly:
+// V' = (1 - fR) Z + fR h_R * Z = F^-1{F{Z} Hv} with the transfer function
+// Hv = (1 - fR)/n + fR H.  A cluster of four blocks takes the eight rows
+// 8 grp .. 8 grp + 7 of Z (one 16-byte core-matrix row of the blocked
+// layout [KKp/8][npts][8] per point): block `rank` transforms rows
+// 8 grp + 2 rank and + 1 as one complex transform pair (the forward
+// transform's first pass reads them straight from global memory) and keeps
+// the result in time order in its shared memory; then block `rank` writes
+// the points [rank n/4, (rank + 1) n/4) of all eight rows, reading the
+// other blocks' results through distributed shared memory, as whole 16-byte
+// hi and lo rows (coalesced across the lanes), so that neither Y' nor a
+// separate pack pass goes through HBM.  Rows r .. 8 ceil(r/8) - 1 are
+// written as zeros; the padding columns beyond are zero from the
+// workspace's creation.  FP16 values are scaled by 2^(eV - eVoff) as in
+// k_pack_rows.  grid (4 ceil(r/8), M+1) in clusters of 4 along x.
 template <int EPT, int OP>
 __global__ void __launch_bounds__(512) k_raman_vpack(Geo g, const float* __restrict__ Zs, int r,
                                                       const float2* __restrict__ Hv, const float2* __restrict__ tw,
                                                       int npts_total, void* __restrict__ Vhi_,
                                                       void* __restrict__ Vlo_, int eVoff,
                                                       const LoopState* __restrict__ ls) {
+  namespace cg = cooperative_groups;
   using Hs = Split<OP>;
   using T = typename Hs::T;
   static_assert(sizeof(T) == 2, "16-bit operands");
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   pdl_enter();
-  const int j = blockIdx.y;  // the slice
+  const int j = blockIdx.y;  // the slice (the same for every block of a cluster)
   {
     int b, jl;
     slot_of(g, j, b, jl);
     if (slice_skipped(ls + b, jl)) return;
   }
-  const int n = g.n, k1 = 2 * blockIdx.x;
-  const bool has2 = k1 + 1 < r;
-  const float* z1 = Zs + ((size_t)j * r + k1) * n;
-  auto load = [&](int t) { return make_float2(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : 0.f); };
-  auto from_smem = [&](int q) { return sm[pad16(q)]; };
-  auto to_smem = [&](int q, float2 x) { sm[pad16(q)] = cmul<float>(x, Hv[q]); };
-  fft_block<float, -1, EPT>(sm, n, tw, load, to_smem);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = g.n, grp = blockIdx.x / 4, k1 = 8 * grp + 2 * rank;
+  if (k1 < r) {
+    const bool has2 = k1 + 1 < r;
+    const float* z1 = Zs + ((size_t)j * r + k1) * n;
+    auto load = [&](int t) { return make_float2(__ldcg(z1 + t), has2 ? __ldcg(z1 + n + t) : 0.f); };
+    auto to_smem = [&](int q, float2 x) { sm[pad16(q)] = cmul<float>(x, Hv[q]); };
+    fft_block<float, -1, EPT>(sm, n, tw, load, to_smem);
+    auto from_smem = [&](int q) { return sm[pad16(q)]; };
+    auto keep = [&](int t, float2 y) { sm[pad16(t)] = y; };
+    fft_block<float, +1, EPT>(sm, n, tw, from_smem, keep);
+  }
+  cluster.sync();  // the four row pairs of the group, in time order
+  const float2* ys[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) ys[u] = cluster.map_shared_rank(sm, u);
   const float scale = OP == 1 ? ldexpf(1.0f, f16_v_exp(ls, n, g.B) - eVoff) : 1.0f;
-  uint32_t* Vhi = reinterpret_cast<uint32_t*>(Vhi_);
-  uint32_t* Vlo = reinterpret_cast<uint32_t*>(Vlo_);
-  // 4-byte word of (k1, k1 + 1) at point p: element ((k1/8) npts_total + p) 8 + k1 % 8
-  const size_t w0 = ((size_t)(k1 / 8) * npts_total + (size_t)j * n) * 4 + (k1 % 8) / 2;
-  auto store = [&](int t, float2 y) {
-    const float v1 = y.x * scale;
-    const float v2 = has2 ? y.y * scale : 0.f;
-    const T h1 = Hs::rn(v1), h2 = Hs::rn(v2);
-    const T l1 = Hs::rn(v1 - Hs::back(h1)), l2 = Hs::rn(v2 - Hs::back(h2));
-    __align__(4) T hw[2] = {h1, h2}, lw[2] = {l1, l2};
-    Vhi[w0 + (size_t)t * 4] = *reinterpret_cast<const uint32_t*>(hw);
-    Vlo[w0 + (size_t)t * 4] = *reinterpret_cast<const uint32_t*>(lw);
-  };
-  fft_block<float, +1, EPT>(sm, n, tw, from_smem, store);
+  uint4* Vhi = reinterpret_cast<uint4*>(Vhi_) + (size_t)grp * npts_total + (size_t)j * n;
+  uint4* Vlo = reinterpret_cast<uint4*>(Vlo_) + (size_t)grp * npts_total + (size_t)j * n;
+  const int q4 = n / 4;
+  for (int i = threadIdx.x; i < q4; i += blockDim.x) {
+    const int t = rank * q4 + i;
+    __align__(16) T hi[8], lo[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ku = 8 * grp + 2 * u;
+      const float2 y = ku < r ? ys[u][pad16(t)] : make_float2(0.f, 0.f);
+      const float v0 = y.x * scale, v1 = ku + 1 < r ? y.y * scale : 0.f;
+      hi[2 * u] = Hs::rn(v0);
+      hi[2 * u + 1] = Hs::rn(v1);
+      lo[2 * u] = Hs::rn(v0 - Hs::back(hi[2 * u]));
+      lo[2 * u + 1] = Hs::rn(v1 - Hs::back(hi[2 * u + 1]));
+    }
+    Vhi[t] = *reinterpret_cast<const uint4*>(hi);
+    Vlo[t] = *reinterpret_cast<const uint4*>(lo);
+  }
+  cluster.sync();  // no block leaves while the others read its shared memory
 }
 
 }  // namespace gm
