@@ -52,9 +52,9 @@ ERR_PREFIX = {"C4": (16 * 37.5e-6, "one long step (0.6 mm)"), "C3": (2e-3, "2 mm
               "C2": (5e-3, "5 mm (20 long steps)")}
 # DRAM bytes of the dominant kernel slot per iteration from one ncu capture
 # (the kernels unchanged since), keyed (workload, precision, kernel slot):
-# the 42-mode MIXED_BF16 contraction is its two GEMM launches, 303.3 MB for
+# the 42-mode MIXED_BF16 contraction is its two GEMM launches, 302.3 MB for
 # 17 live substeps, scaled to the profile's 16
-TRAFFIC = {("C4", "bf16", "contract"): 285.4e6}
+TRAFFIC = {("C4", "bf16", "contract"): 284.5e6}
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
 # nominal dense TF32 : BF16 tensor rate (1.1 : 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
@@ -676,9 +676,14 @@ def roofline(prob, prof, coupling_rank, precision, peaks, src, workload):
     roof["traffic"] = TRAFFIC.get((workload, precision, dom))
     roof["kernel_ms"] = ms_dom
     roof["all_kernels_ms"] = {k: v[0] for k, v in prof.items()}
-    # every kernel slot against its bound (HBM for all but the contraction)
+    # every kernel slot against its bound (HBM for all but the contraction);
+    # each slot is timed over back-to-back launches on the same buffers, so
+    # operands that fit the 126 MB L2 are partly served from it (K5 reads
+    # the integrand K4 writes: its fraction can exceed 1)
     roof["hbm_frac_by_kernel"] = {k: (v[1] / (v[0] * 1e-3) / 1e9) / peaks["hbm_gbs"] for k, v in prof.items()
                                   if v[0] > 0 and k != "contract"}
+    roof["hbm_frac_note"] = ("algorithmic bytes / event time of back-to-back launches on the same buffers "
+                             "(warm L2: operands below 126 MB partly hit it)")
     return roof
 
 
