@@ -126,6 +126,12 @@ struct gmmnlse_ctx {
   int NB1 = 0, r_rows = 0;       // tensor cores: row block of GEMM 1, r padded to whole blocks
   int rKKp = 0;                  // tensor cores: r padded to TC_KC (K of GEMM 2)
   int eW16 = 0, eX16 = 0;        // FP16 exponents of W and X
+  // 16-bit GEMM 1 (U formed in the kernel): the columns of U in 4 x 4 blocks
+  // of (m, n), m-block <= n-block, m-major; ublk [nublk] holds each block's
+  // first (m0, n0); W's columns follow that order (zero where m > n or a
+  // mode is past N); KKpU = 16 nublk padded to TC_KC
+  int2* ublk = nullptr;
+  int nublk = 0, KKpU = 0;
   __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
   CUtensorMap mapWhi, mapWlo, mapXhi, mapXlo;
   // limit of every mbarrier wait of the tensor-core GEMMs [ns] (1 s;

@@ -164,6 +164,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->rows);
   cudaFree(c->rows_t);
   cudaFree(c->pairs);
+  cudaFree(c->ublk);
   cudaFree(c->gpairs);
   cudaFree(c->Ghi);
   cudaFree(c->Wt);
@@ -660,9 +661,40 @@ static int create_ctx(const gmmnlse_params* prm, const double* beta, const doubl
       rc = fp64 ? upload_transposed<double>(Xt_rows, c->P, c->r, c->Pt, c->rK2, &c->Xt)
                 : upload_transposed<float>(Xt_rows, c->P, c->r, c->Pt, c->rK2, &c->Xt);
     if (!rc && c->tc) {
-      c->eW16 = c->f16 ? f16_exp(Wd) : 0;
+      // 16-bit operands: GEMM 1 forms U in the kernel in 4 x 4 blocks of
+      // (m, n) (each block from four A_m and four A_n); W's columns are
+      // reordered to match, with the weights (1 on the diagonal, 2 off it)
+      // and zeros for the block entries that are not pairs m <= n < N
+      std::vector<double> Wu;
+      int KU = c->K;
+      if (!c->tf32) {
+        const int nmb = (N + 3) / 4;
+        std::vector<int2> blk;
+        for (int bm = 0; bm < nmb; ++bm)
+          for (int bn = bm; bn < nmb; ++bn) blk.push_back(make_int2(4 * bm, 4 * bn));
+        c->nublk = (int)blk.size();
+        KU = 16 * c->nublk;
+        c->KKpU = (KU + TC_KC - 1) / TC_KC * TC_KC;
+        Wu.assign((size_t)c->r * KU, 0.0);
+        for (int b = 0; b < c->nublk; ++b)
+          for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+              const int m = blk[b].x + i, nn = blk[b].y + j, k = 16 * b + 4 * i + j;
+              if (m > nn || nn >= N) continue;
+              const int ks = m * N - m * (m - 1) / 2 + (nn - m);  // (m, nn) in the order of `pairs`
+              const double w = m == nn ? 1.0 : 2.0;
+              for (int s = 0; s < c->r; ++s) Wu[(size_t)s * KU + k] = w * Wd[(size_t)s * c->K + ks];
+            }
+        if (cudaMalloc(&c->ublk, blk.size() * sizeof(int2)) != cudaSuccess ||
+            cudaMemcpy(c->ublk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+          rc = GMMNLSE_E_NOMEM;
+      }
+      const std::vector<double>& Wup = c->tf32 ? Wd : Wu;
+      c->eW16 = c->f16 ? f16_exp(Wup) : 0;
       c->eX16 = c->f16 ? f16_exp(Xd) : 0;
-      rc = upload_hilo(Wd, c->r, c->K, c->r_rows, c->KKp, c->f16, c->eW16, &c->Whi, &c->Wlo, c->tf32);
+      if (!rc)
+        rc = upload_hilo(Wup, c->r, KU, c->r_rows, c->tf32 ? c->KKp : c->KKpU, c->f16, c->eW16, &c->Whi, &c->Wlo,
+                         c->tf32);
       if (!rc)
         rc = upload_hilo(Xd, c->P, c->r, c->tc_rows, c->rKKp, c->f16, c->eX16, &c->Xhi, &c->Xlo, c->tf32);
     }
@@ -860,8 +892,9 @@ int gm_make_g_maps(gmmnlse_ctx* c) {
   int rc = tc_map_rows(&c->mapGhi, c->Ghi, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32, cl);
   if (!rc) rc = tc_map_rows(&c->mapGlo, c->Glo, (cuuint64_t)c->tc_rows, c->KKp, NB, c->f16, c->tf32, cl);
   if (!rc && c->lr) {
-    rc = tc_map_rows(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32, cl1);
-    if (!rc) rc = tc_map_rows(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, c->KKp, c->NB1, c->f16, c->tf32, cl1);
+    const int kw = c->tf32 ? c->KKp : c->KKpU;  // K of GEMM 1 (16-bit: the blocked U columns)
+    rc = tc_map_rows(&c->mapWhi, c->Whi, (cuuint64_t)c->r_rows, kw, c->NB1, c->f16, c->tf32, cl1);
+    if (!rc) rc = tc_map_rows(&c->mapWlo, c->Wlo, (cuuint64_t)c->r_rows, kw, c->NB1, c->f16, c->tf32, cl1);
     if (!rc) rc = tc_map_rows(&c->mapXhi, c->Xhi, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32, cl);
     if (!rc) rc = tc_map_rows(&c->mapXlo, c->Xlo, (cuuint64_t)c->tc_rows, c->rKKp, NB, c->f16, c->tf32, cl);
   }

@@ -341,14 +341,15 @@ static void launch_lr_z(gm_job* jb, const Geo& g, cudaStream_t s) {
       // 16-bit operands: U is formed inside the GEMM (TcShape::FU); TF32: packed first
       if (c->tf32) launch_pack_pairs(jb, g, s, 0);
       TcArgs a = tc_args(jb, g);
-      a.KKp = c->KKp;
+      a.KKp = c->tf32 ? c->KKp : c->KKpU;
       a.eG = c->eW16;
       a.nrb = c->r_rows / c->NB1;
       a.Zout = (float*)jb->Z;
       a.zrows = c->r;
       a.nmodes = c->N;
-      a.K = c->K;
-      a.pairs = (const int2*)c->pairs;
+      // 16-bit: U formed in the kernel from the 4 x 4 blocks of (m, n)
+      a.K = c->tf32 ? c->K : c->nublk;
+      a.pairs = c->tf32 ? (const int2*)c->pairs : (const int2*)c->ublk;
       TcLaunch L = {&jb->mapHi, &jb->mapLo, &c->mapWhi, &c->mapWlo, a, (const LoopState*)jb->ls, s,
                     (int)(pts / TC_PTS), c->tf32};
       gm_tc_store(c->NB1, L);

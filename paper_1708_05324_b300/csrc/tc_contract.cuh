@@ -84,9 +84,9 @@ struct TcArgs {
   int nrb;           // OUT 1: row blocks
   float* Zout;       // OUT 1: D rows [M+1][zrows][n]
   int zrows;         // OUT 1: rows stored (the rest is padding)
-  int nmodes, K;     // U formed in the kernel: modes of A, pair columns
+  int nmodes, K;     // U formed in the kernel: modes of A, 4 x 4 blocks of U
   int B;             // slots of a packed launch (1: one propagation)
-  const int2* pairs; // U formed in the kernel: (m, n) of column k
+  const int2* pairs; // U formed in the kernel: first (m, n) of each 4 x 4 block
   unsigned long long wait_ns;  // limit of every mbarrier wait [ns]
   int stall;         // test hook: the MMA issuer waits on a barrier nothing completes,
                      // 1: in single-CTA GEMMs, 2: in every GEMM
@@ -146,13 +146,20 @@ template <> struct Split<2> {
 // FU: the store epilogue (OUT 1) with 16-bit operands forms its V operand,
 // the pair products U of A, in the kernel: eight more warps compute each K
 // chunk of U for the CTA's tile from A staged in shared memory and write it
-// to the stage as hi/lo (no packed U in HBM).  U_FIT_N bounds the modes of A
-// it stages.
+// to the stage as hi/lo (no packed U in HBM).  The columns of U come in 4 x 4
+// blocks of (m, n) (m-block <= n-block; the entries that are not pairs
+// m <= n < N have zero columns in W, which also carries the weights 1 and 2),
+// so that a thread forms 16 columns from four A_m and four A_n: half the
+// shared-memory reads per column of one column at a time, for 17% more K at
+// N = 42 (1056 columns for 903 pairs).  U_FIT_N bounds the modes of A it
+// stages (rows up to U_FIT_NP, the ones from N on zero).
 // TPW: point tiles per work item and CTA, sharing each stage's coupling chunk
 // (TPW MMAs into TPW accumulators): 2 for the store epilogue without FU when
 // two stages still fit, else 1.  NBUF: accumulator buffers in TMEM (2 lets
 // the epilogue drain one work item while the next one's MMAs run).
-constexpr int U_FIT_N = 42, U_FIT_KKP = 928;  // N(N+1)/2 = 903 padded to 32
+constexpr int U_FIT_N = 42, U_FIT_NP = (U_FIT_N + 3) / 4 * 4;
+constexpr int U_FIT_BLK = (U_FIT_NP / 4) * (U_FIT_NP / 4 + 1) / 2;  // 4 x 4 blocks of U
+constexpr int U_FIT_KKP = (16 * U_FIT_BLK + 31) / 32 * 32;         // 1056 columns
 template <int N, int NB, int ES = 2, int OUT = 0>
 struct TcShape {
   static constexpr int P = N * (N + 1) / 2;
@@ -174,8 +181,8 @@ struct TcShape {
   static constexpr bool ESPLIT = OUT == 0 && N > 24;
   static constexpr int EW = ESPLIT ? 8 : 4;            // epilogue warps
   static constexpr int THREADS = 64 + 32 * EW + 32 * UW;
-  // A tile ([U_FIT_N][128] float2) and column table ([KKp] int2) of FU
-  static constexpr int U_RESERVE = FU ? U_FIT_N * TC_PTS * 8 + U_FIT_KKP * 8 : 0;
+  // A tile ([U_FIT_NP][128] float2) and block table ([KKp/16] int2) of FU
+  static constexpr int U_RESERVE = FU ? U_FIT_NP * TC_PTS * 8 + U_FIT_KKP / 16 * 8 : 0;
   static constexpr int TPW = (OUT == 1 && !FU && 2 * 2 * (2 * V_BYTES + G_HALF) <= 200 * 1024) ? 2 : 1;
   static constexpr int STAGE = 2 * (TPW * V_BYTES + G_HALF);
   static constexpr int FIT = (200 * 1024 - U_RESERVE) / STAGE;
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
 
   // FU: A tile [nmodes][128] and the column table after the stages
   float2* As = reinterpret_cast<float2*>(smem + (size_t)S::STAGES * S::STAGE);
-  int2* Ps = reinterpret_cast<int2*>(As + (S::FU ? U_FIT_N * TC_PTS : 0));
+  int2* Ps = reinterpret_cast<int2*>(As + (S::FU ? U_FIT_NP * TC_PTS : 0));
   const unsigned rank = PAIR ? tc::cluster_ctarank() : 0u;
   const bool leader = rank == 0;
   if (tid == 0) {
@@ -361,19 +368,18 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
   if (warp == 1) tc::tmem_relinquish<PAIR>();
   pdl_enter();
   if (S::FU) {
-    // column k of U: the offsets of A_m and A_n in the A tile (16 bits each)
-    // and the weight (1 on the diagonal, 2 off it, times the FP16 scale);
-    // the padding columns have weight 0
-    const float sc = a.f16 ? ldexpf(1.0f, f16_v_exp(ls, a.n, a.B)) : 1.0f;
-    for (int k = tid; k < a.KKp; k += S::THREADS) {
+    // block b of U: the offsets of its first A_m and A_n in the A tile (16
+    // bits each); blocks past the last (the K padding) read rows 0, times
+    // zero columns of W.  The A rows from nmodes to U_FIT_NP stay zero.
+    for (int b = tid; b < a.KKp / 16; b += S::THREADS) {
       int2 e = make_int2(0, 0);
-      if (k < a.K) {
-        const int2 mn = a.pairs[k];
+      if (b < a.K) {
+        const int2 mn = a.pairs[b];
         e.x = (mn.x * TC_PTS) | ((mn.y * TC_PTS) << 16);
-        e.y = __float_as_int(mn.x == mn.y ? sc : 2.0f * sc);
       }
-      Ps[k] = e;
+      Ps[b] = e;
     }
+    for (int i = a.nmodes * TC_PTS + tid; i < U_FIT_NP * TC_PTS; i += S::THREADS) As[i] = make_float2(0.f, 0.f);
     __syncthreads();
   }
   // shared::cluster addresses of CTA 0's barriers (the MMA issuer's), and of
@@ -522,9 +528,9 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
   } else if (S::FU && warp >= 6) {
     // ---------------- U producers: warps 6..13, two threads per point ----------------
     // thread (q, half) writes K columns [16 half, 16 half + 16) of each chunk
-    // for point q of the tile, as hi + lo in the stage's [4][128][8] layout.
-    // The A tile of the next work item is fetched into registers while the
-    // current one's chunks are formed.
+    // (the 4 x 4 block 2 kc + half of U) for point q of the tile, as hi + lo
+    // in the stage's [4][128][8] layout.  The A tile of the next work item is
+    // fetched into registers while the current one's chunks are formed.
     constexpr int UT = 32 * (S::FU ? S::UW : 1);          // U threads
     constexpr int AL = (U_FIT_N * TC_PTS + UT - 1) / UT;  // A values per thread and tile
     const int u = tid - 192, q = u & (TC_PTS - 1), half = u >> 7;
@@ -547,14 +553,24 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
       }
       return wi;
     };
-    // eight K values of this point: U_k = |A_m|^2 or 2 Re(A_m conj A_n), scaled
-    auto u8 = [&](int k0, float* x) {
+    // FP16: U scaled by 2^eV (BF16: 1); the weights are in W
+    const float sc = a.f16 ? ldexpf(1.0f, f16_v_exp(ls, a.n, a.B)) : 1.0f;
+    // the 16 values Re(A_m conj A_n) of block b for this point: x[4 i + j]
+    // from A_{m0+i} and A_{n0+j}
+    auto u16 = [&](int b, float* x) {
+      const int2 e = Ps[b];
+      const float2* am = As + (e.x & 0xffff) + q;
+      const float2* an = As + (e.x >> 16) + q;
+      float2 vm[4], vn[4];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int2 e = Ps[k0 + i];
-        const float2 am = As[(e.x & 0xffff) + q], an = As[(e.x >> 16) + q];
-        x[i] = __int_as_float(e.y) * (am.x * an.x + am.y * an.y);
+      for (int i = 0; i < 4; ++i) {
+        vm[i] = am[i * TC_PTS];
+        vn[i] = an[i * TC_PTS];
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[4 * i + j] = sc * (vm[i].x * vn[j].x + vm[i].y * vn[j].y);
     };
     // hi + lo of eight values, two per conversion
     auto split8 = [&](const float* x, uint4& hw, uint4& lw) {
@@ -609,13 +625,13 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
           }
           if (!__shfl_sync(0xffffffffu, go, 0)) continue;
           unsigned char* st = smem + (size_t)s * S::STAGE;
+          float x[16];
+          u16(2 * kc + half, x);
 #pragma unroll
           for (int kq2 = 0; kq2 < 2; ++kq2) {
             const int kq = 2 * half + kq2;
-            float x[8];
-            u8(kc * TC_KC + kq * 8, x);
             uint4 hw, lw;
-            split8(x, hw, lw);
+            split8(x + 8 * kq2, hw, lw);
             const size_t o = ((size_t)kq * TC_PTS + q) * 16;
             *reinterpret_cast<uint4*>(st + o) = hw;
             *reinterpret_cast<uint4*>(st + S::V_BYTES + o) = lw;
