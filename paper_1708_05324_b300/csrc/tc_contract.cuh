@@ -224,25 +224,8 @@ struct RowPair {
   }
 };
 
-// NL_p += A_l R_r (and NL_l += A_p R_r) for rows R .. R0 + 15, compile-time.
-template <int N, int R, int REND>
-struct LSum {
-  __device__ __forceinline__ static void run(const float* v, const float2* a, float2* nl) {
-    if constexpr (R < REND && R < N * (N + 1) / 2) {
-      constexpr int p = RowPair<N>::p_of(R), l = RowPair<N>::l_of(R);
-      constexpr int i = R % 16;
-      nl[p].x += a[l].x * v[i];
-      nl[p].y += a[l].y * v[i];
-      if constexpr (p != l) {
-        nl[l].x += a[p].x * v[i];
-        nl[l].y += a[p].y * v[i];
-      }
-      LSum<N, R + 1, REND>::run(v, a, nl);
-    }
-  }
-};
-
-// The same for the accumulators of modes LO .. HI - 1 only (nl[p - LO]).
+// NL_p += A_l R_r (and NL_l += A_p R_r) for the rows R .. REND - 1 (compile
+// time), into the accumulators of modes LO .. HI - 1 only (nl[p - LO]).
 template <int N, int R, int REND, int LO, int HI>
 struct LSumH {
   __device__ __forceinline__ static void run(const float* v, const float2* a, float2* nl) {
@@ -272,51 +255,69 @@ __host__ __device__ constexpr bool rows_touch(int R0, int LO, int HI) {
   return false;
 }
 
-// Columns C .. NB-1 of an accumulator holding row block RB, for the modes
-// LO .. HI - 1 (column chunks that add to none of them are not read).
+// The first 16-column chunk from C on of an accumulator holding row block
+// RB whose rows add to a mode in LO .. HI - 1 (-1: none).
+template <int N>
+__host__ __device__ constexpr int next_chunk(int NB, int RB, int C, int LO, int HI) {
+  for (int c = C; c < NB && RB * NB + c < N * (N + 1) / 2; c += 16)
+    if (rows_touch<N>(RB * NB + c, LO, HI)) return c;
+  return -1;
+}
+
+// The l-sum of chunk C (its 16 values in r, loaded and waited for) and of
+// every later chunk that adds to the modes LO .. HI - 1 (column chunks that
+// add to none of them are not read).  Up to 24 modes the next chunk's TMEM
+// load is issued before this chunk's sums, so that its latency overlaps
+// them; above, the 16 more live registers spill (measured slower at 42
+// modes), and each chunk is loaded after the previous one's sums.
 template <int N, int NB, int RB, int C, int LO, int HI>
-struct DrainH {
-  __device__ __forceinline__ static void run(uint32_t taddr, const float2* a, float2* nl) {
+struct DrainP {
+  __device__ __forceinline__ static void run(uint32_t taddr, const float2* a, float2* nl, uint32_t (&r)[16]) {
     constexpr int R0 = RB * NB + C;
-    if constexpr (C < NB && R0 < N * (N + 1) / 2) {
-      if constexpr (rows_touch<N>(R0, LO, HI)) {
-        float v[16];
-        tc::tmem_ld16(taddr + C, v);
+    constexpr int CN = next_chunk<N>(NB, RB, C + 16, LO, HI);
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    if constexpr (CN >= 0) {
+      uint32_t rn[16];
+      if constexpr (N <= 24) {
+        tc::tmem_ld16_issue(taddr + CN, rn);
         LSumH<N, R0, R0 + 16, LO, HI>::run(v, a, nl);
+      } else {
+        LSumH<N, R0, R0 + 16, LO, HI>::run(v, a, nl);
+        tc::tmem_ld16_issue(taddr + CN, rn);
       }
-      DrainH<N, NB, RB, C + 16, LO, HI>::run(taddr, a, nl);
+      tc::tmem_wait16(rn);
+      DrainP<N, NB, RB, CN, LO, HI>::run(taddr, a, nl, rn);
+    } else {
+      LSumH<N, R0, R0 + 16, LO, HI>::run(v, a, nl);
     }
   }
 };
 
+// The l-sum of an accumulator holding row block rb (a runtime value) for the
+// modes LO .. HI - 1.
 template <int N, int NB, int RB, int LO, int HI>
 __device__ __forceinline__ void drain_rb_h(int rb, uint32_t taddr, const float2* a, float2* nl) {
   if constexpr (RB < TcShape<N, NB>::NRB) {
-    if (rb == RB) DrainH<N, NB, RB, 0, LO, HI>::run(taddr, a, nl);
-    else drain_rb_h<N, NB, RB + 1, LO, HI>(rb, taddr, a, nl);
+    if (rb == RB) {
+      constexpr int C0 = next_chunk<N>(NB, RB, 0, LO, HI);
+      if constexpr (C0 >= 0) {
+        uint32_t r[16];
+        tc::tmem_ld16_issue(taddr + C0, r);
+        tc::tmem_wait16(r);
+        DrainP<N, NB, RB, C0, LO, HI>::run(taddr, a, nl, r);
+      }
+    } else {
+      drain_rb_h<N, NB, RB + 1, LO, HI>(rb, taddr, a, nl);
+    }
   }
 }
 
-// Columns C .. NB-1 of an accumulator holding row block RB.
-template <int N, int NB, int RB, int C>
-struct Drain {
-  __device__ __forceinline__ static void run(uint32_t taddr, const float2* a, float2* nl) {
-    constexpr int R0 = RB * NB + C;
-    if constexpr (C < NB && R0 < N * (N + 1) / 2) {
-      float v[16];
-      tc::tmem_ld16(taddr + C, v);
-      LSum<N, R0, R0 + 16>::run(v, a, nl);
-      Drain<N, NB, RB, C + 16>::run(taddr, a, nl);
-    }
-  }
-};
-
+// The same for every mode.
 template <int N, int NB, int RB>
 __device__ __forceinline__ void drain_rb(int rb, uint32_t taddr, const float2* a, float2* nl) {
-  if constexpr (RB < TcShape<N, NB>::NRB) {
-    if (rb == RB) Drain<N, NB, RB, 0>::run(taddr, a, nl);
-    else drain_rb<N, NB, RB + 1>(rb, taddr, a, nl);
-  }
+  drain_rb_h<N, NB, RB, 0, N>(rb, taddr, a, nl);
 }
 
 // OUT 0: the l-sum epilogue into NL (N modes, compile-time); OUT 1: the
@@ -715,7 +716,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) {
-          if (PAIR) tc::mbar_arrive_cluster(at0(&acc_empty[acc]));
+          if (PAIR) tc::mbar_arrive_remote(at0(&acc_empty[acc]));
           else tc::mbar_arrive(&acc_empty[acc]);
         }
       }
