@@ -170,8 +170,10 @@ struct TcShape {
   static constexpr int G_BYTES = NB * TC_KC * ES;      // one of hi / lo, all NB rows
   static constexpr bool FU = OUT == 1 && ES == 2;
   // CTAs per MMA (2: CTA pair); the GEMM that forms U in the kernel runs on
-  // single CTAs (measured faster: its U producers are the limit, and a pair
-  // makes every K chunk wait for those of both CTAs)
+  // single CTAs (measured faster: on a pair every K chunk waits for both
+  // CTAs' producers, whose stage hand-over to the MMA-issuing CTA is a
+  // cluster-scope release per warp and chunk; 0.30 against 0.20 ms per
+  // 42-mode iteration)
   static constexpr int CL = FU ? 1 : tc_cluster(NB);
   static constexpr int G_HALF = G_BYTES / CL;          // this CTA's rows of a chunk (hi or lo)
   static constexpr int UW = FU ? 8 : 0;                // U-producer warps
