@@ -94,6 +94,11 @@ struct gmmnlse_ctx {
   void* G = nullptr;            // [P][KK] R
   int2* rows = nullptr;         // [P]
   int2* pairs = nullptr;        // [K]
+  // N <= 8 on the CUDA cores: the contraction kernel compiled for this
+  // context's nonzero coupling entries (nzlist.cu; CUmodule / CUfunction),
+  // null when k_contract_reg runs instead
+  void* nz_mod = nullptr;
+  void* nz_fn = nullptr;
   bool tc = false;               // contraction on tensor cores (mixed precision)
   int KKp = 0;                   // K padded to a multiple of TC_KC (32)
   int tc_rows = 0;               // rows of G padded to whole row blocks
@@ -212,9 +217,16 @@ static inline void launch_contract_n(const gm::Geo& g, const gmmnlse_ctx* c, con
   else launch_contract_reg<R, N, 2>(g, c, A, V, NL, ls, s);
 }
 
+void gm_nz_launch(const gmmnlse_ctx* c, const gm::Geo& g, const void* A, const void* V, void* NL,
+                  const gm::LoopState* ls, cudaStream_t s);
+
 template <typename R>
 static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V, void* NL,
                                    const gm::LoopState* ls, cudaStream_t s) {
+  if (c->nz_fn) {  // N <= 8: the kernel compiled for this context's nonzero coupling entries
+    gm_nz_launch(c, g, A, V, NL, ls, s);
+    return;
+  }
   switch (c->N) {
     case 1: launch_contract_n<R, 1>(g, c, A, V, NL, ls, s); return;
     case 2: launch_contract_n<R, 2>(g, c, A, V, NL, ls, s); return;

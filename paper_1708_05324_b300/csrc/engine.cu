@@ -164,6 +164,7 @@ static void free_ctx(gmmnlse_ctx* c) {
   cudaFree(c->rows);
   cudaFree(c->rows_t);
   cudaFree(c->pairs);
+  gm_nz_free(c);
   cudaFree(c->ublk);
   cudaFree(c->gpairs);
   cudaFree(c->Ghi);
@@ -654,6 +655,7 @@ static int create_ctx(const gmmnlse_params* prm, const double* beta, const doubl
     CKC(cudaMemcpy(c->rows_t, diag.data(), c->P * sizeof(int2), cudaMemcpyHostToDevice));
   }
   rc = fp64 ? upload_tables<double>(c, Gd, Gt_rows) : upload_tables<float>(c, Gd, Gt_rows);
+  if (!rc) rc = gm_nz_build(c, Gd);
   if (!rc && c->lr) {
     rc = fp64 ? upload_transposed<double>(Wd, c->r, c->K, c->rP1, c->KKt, &c->Wt)
               : upload_transposed<float>(Wd, c->r, c->K, c->rP1, c->KKt, &c->Wt);

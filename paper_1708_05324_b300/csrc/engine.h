@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/gmmnlse.h"
 
 struct gm_job;
@@ -43,6 +45,11 @@ int gm_pack_step(gm_job* jb, cudaStream_t s, int* finished);  // finished[slot]:
 int gm_pack_retire(gm_job* jb, int slot, double* Aout_host, gmmnlse_stats* st, cudaStream_t s);
 int gm_make_tc_maps(gmmnlse_ctx* c, gm_job* jb, int M);
 int gm_make_g_maps(gmmnlse_ctx* c);
+// N <= 8 on the CUDA cores: build (at context creation) and free the
+// contraction kernel compiled for the context's nonzero coupling entries
+// (nzlist.cu); Gd is the reduced coupling [P][KK] in the standard row order
+int gm_nz_build(gmmnlse_ctx* c, const std::vector<double>& Gd);
+void gm_nz_free(gmmnlse_ctx* c);
 void gm_job_destroy(gm_job* jb);
 int gm_job_propagate(gm_job* jb, const double* A0, bool dev_io, double L, double dz, int M, double tol,
                      double* Aout, gmmnlse_stats* st, cudaStream_t s);
