@@ -134,6 +134,11 @@ typedef struct gmmnlse_server gmmnlse_server;
  * non-power-of-two Nt give GMMNLSE_E_INVALID.  The context owns its device
  * memory until gmmnlse_destroy; it is read-only after creation and may be
  * shared by concurrent server requests.
+ * With N <= 8 and the contraction on the CUDA cores, create compiles a
+ * contraction kernel for the context's nonzero coupling entries (NVRTC,
+ * opened at run time; about 0.1 s); if that cannot be done the dense
+ * register kernel runs instead.  GMMNLSE_NZ=0 in the environment keeps the
+ * dense kernel; GMMNLSE_NZ=require makes a failed build GMMNLSE_E_CUDA.
  */
 int gmmnlse_create(const gmmnlse_params* prm, const double* beta, const double* SK,
                    const double* SR, double fR, const double* hR, gmmnlse_ctx** out);
