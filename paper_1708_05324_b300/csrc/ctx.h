@@ -217,16 +217,15 @@ static inline void launch_contract_n(const gm::Geo& g, const gmmnlse_ctx* c, con
   else launch_contract_reg<R, N, 2>(g, c, A, V, NL, ls, s);
 }
 
-void gm_nz_launch(const gmmnlse_ctx* c, const gm::Geo& g, const void* A, const void* V, void* NL,
+// false if the launch was refused (the caller then launches k_contract_reg)
+bool gm_nz_launch(const gmmnlse_ctx* c, const gm::Geo& g, const void* A, const void* V, void* NL,
                   const gm::LoopState* ls, cudaStream_t s);
 
 template <typename R>
 static inline void launch_contract(const gm::Geo& g, const gmmnlse_ctx* c, const void* A, const void* V, void* NL,
                                    const gm::LoopState* ls, cudaStream_t s) {
-  if (c->nz_fn) {  // N <= 8: the kernel compiled for this context's nonzero coupling entries
-    gm_nz_launch(c, g, A, V, NL, ls, s);
-    return;
-  }
+  // N <= 8: the kernel compiled for this context's nonzero coupling entries
+  if (c->nz_fn && gm_nz_launch(c, g, A, V, NL, ls, s)) return;
   switch (c->N) {
     case 1: launch_contract_n<R, 1>(g, c, A, V, NL, ls, s); return;
     case 2: launch_contract_n<R, 2>(g, c, A, V, NL, ls, s); return;

@@ -211,7 +211,7 @@ void gm_nz_free(gmmnlse_ctx* c) {
   c->nz_fn = nullptr;
 }
 
-void gm_nz_launch(const gmmnlse_ctx* c, const gm::Geo& g, const void* A, const void* V, void* NL,
+bool gm_nz_launch(const gmmnlse_ctx* c, const gm::Geo& g, const void* A, const void* V, void* NL,
                   const gm::LoopState* ls, cudaStream_t s) {
   const size_t pts = (size_t)g.B * (g.M + 1) * g.n;
   const unsigned grid = (unsigned)((pts + 127) / 128);
@@ -235,5 +235,5 @@ void gm_nz_launch(const gmmnlse_ctx* c, const gm::Geo& g, const void* A, const v
   at.value.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = &at;
   cfg.numAttrs = pdl_disabled() ? 0 : 1;  // as pdl_launch
-  nz_api().launch(&cfg, (CUfunction)c->nz_fn, args, nullptr);
+  return nz_api().launch(&cfg, (CUfunction)c->nz_fn, args, nullptr) == CUDA_SUCCESS;
 }
