@@ -570,10 +570,17 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
         vm[i] = am[i * TC_PTS];
         vn[i] = an[i * TC_PTS];
       }
+      if (sc != 1.0f) {  // FP16: a power of two, so scaling A_m equals scaling the product
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          vm[i].x *= sc;
+          vm[i].y *= sc;
+        }
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) x[4 * i + j] = sc * (vm[i].x * vn[j].x + vm[i].y * vn[j].y);
+        for (int j = 0; j < 4; ++j) x[4 * i + j] = vm[i].x * vn[j].x + vm[i].y * vn[j].y;
     };
     // hi + lo of eight values, two per conversion
     auto split8 = [&](const float* x, uint4& hw, uint4& lw) {
