@@ -702,14 +702,29 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
             const int pth = tile * TC_PTS + row_in_tile;
             const int jh = pth / n, th = pth - jh * n;
             float* z = a.Zout + (size_t)jh * a.zrows * n + th;
-            for (int c0 = 0; c0 < NB; c0 += 16) {
-              float v[16];
-              tc::tmem_ld16(taddr + (uint32_t)(h * NB) + c0, v);
+            const uint32_t tb = taddr + (uint32_t)(h * NB);
+            auto put = [&](int c0, const uint32_t (&v)[16]) {
 #pragma unroll
               for (int i = 0; i < 16; ++i) {
                 const int r = rb * NB + c0 + i;
-                if (r < a.zrows) z[(size_t)r * n] = v[i] * inv;
+                if (r < a.zrows) z[(size_t)r * n] = __uint_as_float(v[i]) * inv;
               }
+            };
+            // each 16-column TMEM load is issued before the previous chunk's
+            // stores (two register buffers in turn)
+            uint32_t va[16], vb[16];
+            tc::tmem_ld16_issue(tb, va);
+            tc::tmem_wait16(va);
+            for (int c0 = 0; c0 < NB; c0 += 32) {
+              const bool more1 = c0 + 16 < NB;
+              if (more1) tc::tmem_ld16_issue(tb + c0 + 16, vb);
+              put(c0, va);
+              if (!more1) break;
+              tc::tmem_wait16(vb);
+              const bool more2 = c0 + 32 < NB;
+              if (more2) tc::tmem_ld16_issue(tb + c0 + 32, va);
+              put(c0 + 16, vb);
+              if (more2) tc::tmem_wait16(va);
             }
           }
         } else if (mine) {
