@@ -949,6 +949,8 @@ __global__ void __launch_bounds__(512) k_raman_vpack(Geo g, const float* __restr
   uint4* Vhi = reinterpret_cast<uint4*>(Vhi_) + (size_t)grp * npts_total + (size_t)j * n;
   uint4* Vlo = reinterpret_cast<uint4*>(Vlo_) + (size_t)grp * npts_total + (size_t)j * n;
   const int q4 = n / 4;
+  // (unrolled: the partners' values of several points in flight at once)
+#pragma unroll 4
   for (int i = threadIdx.x; i < q4; i += blockDim.x) {
     const int t = rank * q4 + i;
     __align__(16) T hi[8], lo[8];
