@@ -52,9 +52,9 @@ ERR_PREFIX = {"C4": (16 * 37.5e-6, "one long step (0.6 mm)"), "C3": (2e-3, "2 mm
               "C2": (5e-3, "5 mm (20 long steps)")}
 # DRAM bytes of the dominant kernel slot per iteration from one ncu capture
 # (the kernels unchanged since), keyed (workload, precision, kernel slot):
-# the 42-mode MIXED_BF16 contraction is its two GEMM launches, 310.1 MB for
+# the 42-mode MIXED_BF16 contraction is its two GEMM launches, 302.7 MB for
 # 17 live substeps, scaled to the profile's 16
-TRAFFIC = {("C4", "bf16", "contract"): 291.9e6}
+TRAFFIC = {("C4", "bf16", "contract"): 284.9e6}
 FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032 / 1e3  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
 # nominal dense TF32 : BF16 tensor rate (1.1 : 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
