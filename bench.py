@@ -539,6 +539,14 @@ def run_serving(B, dev, count=512, max_substeps=0, inflight=32, load=0.9, seed=5
     status = {}
     for _, rc, _ in done.values():
         status[rc] = status.get(rc, 0) + 1
+    bad = sorted((done[i][0], i) for i in done if done[i][1] != B.OK)
+    if bad:  # every request was submitted at once: the first to fail ended first
+        i = bad[0][1]
+        r = reqs[i]
+        raise RuntimeError(f"closed loop: {len(bad)} of {len(reqs)} requests failed; the first: request {i} "
+                           f"(N {r['N']}, Nt {r['Nt']}, {r['units'] // (r['N'] * r['Nt'])} substeps) ended "
+                           f"after {1e3 * bad[0][0]:.0f} ms with "
+                           f"{B.load().gmmnlse_strerror(done[i][1]).decode()}")
     closed_lat = np.array([done[i][0] for i in range(len(reqs))]) * 1e3
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / (load * capacity), size=len(reqs))
@@ -573,6 +581,9 @@ def run_serving(B, dev, count=512, max_substeps=0, inflight=32, load=0.9, seed=5
         ref, _, rc = c.propagate(r["A0"], r["L"], r["dz"], r["M"], 1e-6, check=False)
         t64 += time.perf_counter() - t1
         c.close()
+        if rc != B.OK:
+            raise RuntimeError(f"FP64 serial run of request {i} (N {r['N']}, Nt {r['Nt']}): "
+                               f"{B.load().gmmnlse_strerror(rc).decode()}")
         errs.append(float(np.linalg.norm(served[i] - ref) / np.linalg.norm(ref)))
     for _, c in ctxs.values():
         c.close()
@@ -872,7 +883,12 @@ def main():
                 extra[key] = extra_line(B, name, prec, length, dev, stream, flush)
         line["extra"] = extra
     if args.serve_requests > 0:
-        line["serving"] = run_serving(B, dev, count=args.serve_requests, max_substeps=args.serve_max_substeps)
+        # the headline above is complete: a failure in the serving block is
+        # reported in its place rather than losing the line
+        try:
+            line["serving"] = run_serving(B, dev, count=args.serve_requests, max_substeps=args.serve_max_substeps)
+        except Exception as e:
+            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_cpu_baseline:
         its = line["config"]["iters_per_long_step"] if args.workload == "C4" else C4_ITERS_PER_LONG_STEP
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, its)
