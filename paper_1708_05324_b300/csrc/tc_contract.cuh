@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(TcShape<N, NB, ES, OUT>::THREADS, 1) k_tc_cont
       for (int rb = 0; rb < nrb; ++rb)
         for (int kc = 0; kc < kchunks; ++kc, ++c) {
           const int s = c % S::STAGES, round = c / S::STAGES;
-          // lane 0 waits for the stage; the warp follows its verdict (uniform)
+          // lane 0 waits for the stage; the warp follows its result (uniform)
           int go = 1;
           if (lane == 0) {
             if (*stop) {
