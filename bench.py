@@ -541,6 +541,9 @@ def run_serving(B, dev, count=512, max_substeps=0, inflight=32, load=0.9, seed=5
         status[rc] = status.get(rc, 0) + 1
     bad = sorted((done[i][0], i) for i in done if done[i][1] != B.OK)
     if bad:  # every request was submitted at once: the first to fail ended first
+        srv.close()
+        for _, c in ctxs.values():
+            c.close()
         i = bad[0][1]
         r = reqs[i]
         raise RuntimeError(f"closed loop: {len(bad)} of {len(reqs)} requests failed; the first: request {i} "
@@ -582,6 +585,8 @@ def run_serving(B, dev, count=512, max_substeps=0, inflight=32, load=0.9, seed=5
         t64 += time.perf_counter() - t1
         c.close()
         if rc != B.OK:
+            for _, cc in ctxs.values():
+                cc.close()
             raise RuntimeError(f"FP64 serial run of request {i} (N {r['N']}, Nt {r['Nt']}): "
                                f"{B.load().gmmnlse_strerror(rc).decode()}")
         errs.append(float(np.linalg.norm(served[i] - ref) / np.linalg.norm(ref)))
