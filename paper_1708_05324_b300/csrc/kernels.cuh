@@ -505,12 +505,17 @@ static __global__ void k_decide(LoopState* ls, cudaGraphConditionalHandle h, int
 // one may update it.
 // ---------------------------------------------------------------------------
 constexpr int TRAPZ_T = 128;
-constexpr int TRAPZ_MAX_BLOCKS = 148 * 8;
+constexpr int TRAPZ_MAX_BLOCKS = 148 * 8;  // partial-sum slots per propagation slot
+// K5's grid: at most one wave of resident blocks, four 128-thread blocks per
+// SM (the FP32 and FP64 forms take 128 and 119 registers a thread); a second,
+// mostly idle wave of blocks cost a third of its time at 42 modes (0.0129
+// against 0.0086 ms per iteration)
+constexpr int TRAPZ_WAVE = 148 * 4;
 template <typename R> struct TrapzJC { static constexpr int value = sizeof(R) == 4 ? 16 : 8; };
 
 inline int trapz_blocks(size_t Nn) {
   const size_t b = (Nn + TRAPZ_T - 1) / TRAPZ_T;
-  return (int)(b < 1 ? 1 : (b > (size_t)TRAPZ_MAX_BLOCKS ? TRAPZ_MAX_BLOCKS : b));
+  return (int)(b < 1 ? 1 : (b > (size_t)TRAPZ_WAVE ? TRAPZ_WAVE : b));
 }
 
 // Sum of (a, b) over the block (any shape, at most 32 warps); valid in
